@@ -1,0 +1,320 @@
+"""Benchmark of the coupled vortex-filament / lattice-Boltzmann step.
+
+Metric: coupled-step MLUPS (lattice cells x steps / s of the whole coupled
+step) on the closed-channel workload 64x64x256 (walls on all sides, heater
+v_n = 0.01, 20 seeded rings, ~1.2k filament points), with filament-point
+updates/s beside it.  One process per GPU; with N > 1 every rank runs an
+independent replica (the method has no exchange step at one-GPU scale), the
+timing is the max over ranks and the value the sum of all ranks' work.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl vlb|reference]
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on
+the same workload (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_CONFIG = "channel64x64x256"
+BYTES_PER_CELL = 152  # 19 populations x 4 B read + 19 x 4 B written per cell and pass
+LAUNCHES_PER_STEP = 32  # kernels of one coupled step (1 RK4 sub-step), see the design doc
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(units: float, seconds: float, ws: int):
+    """Sum of work over ranks and max of time over ranks."""
+    if ws == 1:
+        return units, seconds
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def k1_traffic(config_name: str):
+    """DRAM bytes per stream-collide launch from the committed ncu summary, if
+    the kernel source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"k_lbm_step_{config_name}.md")
+    src = os.path.join(ROOT, "paper_2108_04435_gb300", "csrc", "lbm.cu")
+    try:
+        txt = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        m = re.search(r"lbm\.cu sha256\[:16\]:\s*([0-9a-f]+)", txt)
+        t = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", txt)
+        if m and t and m.group(1) == digest:
+            return float(t.group(1))
+    except Exception:
+        pass
+    return None
+
+
+def run_vlb(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2108_04435_gb300 import configs, vlb
+
+    torch.cuda.set_device(local)
+    p, xyz, nxt = configs.config(args.config, seed=rank)
+    cells = p["n"][0] * p["n"][1] * p["n"][2]
+    stream = torch.cuda.current_stream()
+
+    # --- device-resident run: inputs in HBM before the timed region
+    ch = vlb.Channel(p, stream=stream)
+    ch.seed(xyz, nxt)
+    ch.step(args.warmup)
+    n_before = ch.n_points()
+    ch.set_timing(True)
+    clocks = ClockSampler(local).start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ch.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    dev_s = e0.elapsed_time(e1) / 1e3
+    k1_ms, k1_n = ch.lbm_timing()
+    ch.set_timing(False)
+    n_after = ch.n_points()
+    pts = 0.5 * (n_before + n_after) * args.steps  # filament-point updates (mean count x steps)
+    ch.close()
+
+    units, secs = aggregate(cells * args.steps, dev_s, ws)
+    pts_all, _ = aggregate(pts, dev_s, ws)
+    mlups = units / secs / 1e6
+
+    # --- end to end through the public API: seed from host, step, read the
+    # line length after every step, read the filaments back at the end
+    ch2 = vlb.Channel(p, stream=stream)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ch2.seed(xyz, nxt)
+    lengths = []
+    for _ in range(args.steps):
+        ch2.step(1)
+        lengths.append(ch2.line_length())
+    final = ch2.read(vlb.FIELD_POS)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier(ws)
+    ch2.close()
+    e2e_units, e2e_secs = aggregate(cells * args.steps, e2e_s, ws)
+    h2d = (xyz.size * 8 + nxt.size * 4) / args.steps
+    d2h = 8 + 4 * 8 + 8 * 8 + final.nbytes / args.steps
+
+    pk, pk_kind = peaks()
+    k1_avg_s = (k1_ms / 1e3) / max(k1_n, 1)
+    achieved = BYTES_PER_CELL * cells / k1_avg_s / 1e9 if k1_n else None
+    traffic = k1_traffic(args.config)
+    line = {
+        "metric": "coupled-step MLUPS",
+        "value": round(mlups, 2),
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(secs * 1e3 / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded rings, lattice initialised at uniform equilibrium)",
+        "config": {"workload": f"{args.config}: closed channel {p['n'][0]}x{p['n'][1]}x{p['n'][2]} D3Q19, "
+                               f"walls on all sides, heater v_n={p['heater_vn']}, T=1.9 K, "
+                               f"{len(nxt)} seeded filament points in 20 rings",
+                   "cells": cells, "filament_points_start": int(len(nxt)),
+                   "filament_points_timed": [int(n_before), int(n_after)],
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "working set (2 population buffers 160 MB + force/velocity 25 MB) larger than the 129 MB L2"},
+        "filament_pts_per_s": round(pts_all / secs, 1),
+        "e2e": {"value": round(e2e_units / e2e_secs / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1)},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "roofline": {"kernel": "k_lbm_step", "bound": "hbm",
+                     "achieved": round(achieved, 1) if achieved else None,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
+                     "peak_source": f"{pk_kind} hbm_gbs (copy bandwidth)",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": BYTES_PER_CELL * cells,
+                     "avg_launch_us": round(k1_avg_s * 1e6, 3), "launches": k1_n},
+        "clocks": clk,
+    }
+    return line, p, xyz, nxt
+
+
+def oracle_sample(p, xyz, nxt, budget_s: float, min_steps: int = 2, max_steps: int = 1000):
+    """Time the FP64 oracle on host cores for about budget_s seconds."""
+    import oracle
+    oracle.build()
+    ch = oracle.Channel(p)
+    ch.seed(xyz, nxt)
+    ch.step(1)  # first-touch of the arrays outside the timed part
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps and (steps < min_steps or time.perf_counter() - t0 < budget_s):
+        ch.step(1)
+        steps += 1
+    secs = time.perf_counter() - t0
+    n = ch.n_points()
+    ch.close()
+    cells = p["n"][0] * p["n"][1] * p["n"][2]
+    return cells * steps / secs / 1e6, steps, secs, n
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args, ws, rank):
+    from paper_2108_04435_gb300 import configs
+    if rank != 0:
+        return None
+    p, xyz, nxt = configs.config(args.config, seed=0)
+    import oracle
+    oracle.build()
+    ch = oracle.Channel(p)
+    ch.seed(xyz, nxt)
+    ch.step(max(args.warmup, 0))
+    t0 = time.perf_counter()
+    ch.step(args.steps)
+    secs = time.perf_counter() - t0
+    cells = p["n"][0] * p["n"][1] * p["n"][2]
+    v = cells * args.steps / secs / 1e6
+    cores = omp_threads()
+    sample = f"{args.steps} full oracle coupled steps of {args.config} after {args.warmup} warm-up steps"
+    return {
+        "impl": "reference", "metric": "coupled-step MLUPS", "value": round(v, 4), "unit": "MLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.config, "cells": cells},
+        "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
+    ap.add_argument("--impl", default="vlb", choices=["vlb", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+    else:
+        line, p, xyz, nxt = run_vlb(args, ws, rank, local)
+        if rank == 0:
+            if ws == 1 and not args.no_cpu_baseline:
+                v, steps, secs, n = oracle_sample(p, xyz, nxt, args.cpu_budget)
+                line["cpu_baseline"] = {"value": round(v, 4), "unit": "MLUPS", "cores": omp_threads(),
+                                        "kind": "oracle",
+                                        "sample": f"{steps} full FP64 oracle coupled steps of {args.config} from the "
+                                                  f"seeded state ({secs:.1f} s)"}
+            print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * vlb.h -- C ABI of the GB300 (sm_103a) coupled vortex-filament /
+ * lattice-Boltzmann step of Inui & Tsubota, arXiv 2108.04435.
+ *
+ * One "channel" holds a D3Q19 lattice of normal fluid and a set of quantized
+ * vortex filaments, resident in device memory.  vlb_step advances both by one
+ * coupled time step per iteration (Sec. II):
+ *   (a) D3Q19 BGK pull stream-collide with the split forcing of Eq. 14a-d
+ *       (Eqs. 5-9, 12-13), halfway bounce-back at walls and moving-wall heater
+ *       links on the stream-axis faces (Sec. IV), then the superfluid
+ *       counterflow V_s per stream plane (Eq. 18);
+ *   (b) the normal velocity interpolated onto filament points and the
+ *       mutual-friction reaction spread back with the 2-point delta function
+ *       (Eqs. 10-11);
+ *   (c) Biot-Savart velocity of the filaments (Eq. 3) with the local term,
+ *       the alpha/alpha' equation of motion (Eq. 4) integrated with RK4, then
+ *       remeshing to [dxi_min, dxi_max] and reconnection (Sec. II.A).
+ *
+ * Conventions
+ *  - Lattice units (dx = dt = 1).  Nodes at integer coordinates 0..n-1; a wall
+ *    sits half a cell outside the first and last node of a wall axis.
+ *  - Field arrays are structure-of-arrays with x fastest, a[c][z][y][x].
+ *  - Population order (Table I, 0-based): 0 rest; 1 +x, 2 -x, 3 +y, 4 -y,
+ *    5 +z, 6 -z; 7 (+1,+1,0) 8 (-1,-1,0) 9 (+1,-1,0) 10 (-1,+1,0)
+ *    11 (+1,0,+1) 12 (-1,0,-1) 13 (+1,0,-1) 14 (-1,0,+1) 15 (0,+1,+1)
+ *    16 (0,-1,-1) 17 (0,+1,-1) 18 (0,-1,+1).
+ *  - Filament points are stored densely 0..N-1; next[i] is the successor of
+ *    point i along its (closed) loop.
+ *  - Every call returns VLB_OK (0) or a negative VLB_ERR_* code; the message
+ *    of the last failure on the calling thread is vlb_last_error().  After any
+ *    error the channel can still be read and destroyed.
+ *  - Ownership: the caller owns every host array it passes and gets back; the
+ *    library copies in and out and keeps no host pointer.  The library owns
+ *    the device buffers of a channel (allocated at create time, through the
+ *    caller's allocator when one is given).  The stream belongs to the caller
+ *    and must outlive the channel.  A channel is not thread-safe; distinct
+ *    channels on distinct streams are independent.
+ */
+#ifndef VLB_H
+#define VLB_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    VLB_OK = 0,
+    VLB_ERR_INVALID_ARG = -1, /* bad parameter, size or handle */
+    VLB_ERR_OOM = -2,         /* device allocation failed */
+    VLB_ERR_CAPACITY = -3,    /* more filament points than max_points */
+    VLB_ERR_TOPOLOGY = -4,    /* next[] is not a permutation of closed loops */
+    VLB_ERR_MACH = -5,        /* |u|/c_s >= 0.05 somewhere (Sec. II.B validity limit) */
+    VLB_ERR_NAN = -6,         /* NaN/Inf in the lattice or on a filament */
+    VLB_ERR_TIMEOUT = -7,     /* a device-side wait gave up (kernel returned early) */
+    VLB_ERR_CUDA = -8,        /* a CUDA runtime call failed */
+    VLB_ERR_CFL = -9          /* a filament point moved >= 1 cell within one step */
+};
+
+/* Parameters of a channel.  Readings where the paper is silent are noted. */
+typedef struct {
+    int32_t n[3];            /* cells along x, y, z (>= 1) */
+    int32_t wall[3];         /* per axis: 0 periodic, 1 halfway bounce-back walls on both faces */
+    int32_t stream_axis;     /* counterflow axis; this library requires 2 (z) */
+    int32_t vfm_substeps;    /* RK4 sub-steps per lattice step (>= 1) */
+    int32_t couple;          /* 1: spread the mutual-friction reaction onto the lattice (Eqs. 10-11) */
+    int32_t force_form;      /* 0: f of Eq. 10 as printed; 1: f = rho_s kappa (rhs of Eq. 10) x s' */
+    int32_t max_points;      /* filament point capacity (device arrays are sized by it) */
+    int32_t reserved;        /* must be 0 */
+    double  tau, rho0;       /* BGK relaxation time (> 1/2, Eq. 8) and reference density */
+    double  body_force[3];   /* uniform body force added to the force grid (0 in the paper's runs) */
+    double  heater_vn;       /* Sec. IV heater: normal velocity injected at the low z face and removed at the high one */
+    double  pin_vn;          /* periodic z: plane z = 0 reset to f^eq(rho, pin_vn e_z) (Sec. III.C); 0 = off */
+    double  init_vn[3];      /* initial uniform normal velocity */
+    double  kappa, alpha, alpha_p, rho_s_over_rho_n, core_a; /* circulation, Eq. 4 friction, density ratio, core radius */
+    double  dxi_min, dxi_max;                                /* remeshing interval (Sec. III: 0.70, 0.95) */
+} vlb_params;
+
+/* Optional device allocator (e.g. PyTorch's caching allocator).  alloc returns
+ * a device pointer of at least `bytes` bytes (16-byte aligned) or NULL; free
+ * releases it.  `stream` is the channel's stream. */
+typedef struct {
+    void* ctx;
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void (*free)(void* ctx, void* ptr, void* stream);
+} vlb_allocator;
+
+typedef struct vlb_channel vlb_channel;
+
+/* Phases of one coupled step, for vlb_run_phases. */
+enum { VLB_PHASE_LBM = 1, VLB_PHASE_VFM = 2, VLB_PHASE_REMESH = 4, VLB_PHASE_RECONNECT = 8, VLB_PHASE_ALL = 15 };
+
+/* Fields for vlb_read_fields / vlb_write_fields. */
+enum {
+    VLB_FIELD_RHO = 0,      /* float32 [C]: density of the streamed populations of the current state */
+    VLB_FIELD_U = 1,        /* float32 [3][C]: their half-force shifted velocity (sum c f + F/2)/rho */
+    VLB_FIELD_FSTAR = 2,    /* float32 [19][C]: post-collision populations (read and write) */
+    VLB_FIELD_FORCE = 3,    /* float32 [3][C]: force grid of the next lattice pass (read and write) */
+    VLB_FIELD_POS = 4,      /* float64 [N][3]: filament points */
+    VLB_FIELD_NEXT = 5,     /* int32 [N]: successor of each point */
+    VLB_FIELD_PLANE_VS = 6, /* float64 [n_z]: superfluid counterflow velocity per z plane (Eq. 18) */
+    VLB_FIELD_STATS = 7,    /* float64 [16]: 0 points, 1 status bits, 2 mass, 3 line length, 4 max Mach,
+                               5 splits, 6 merges, 7 reconnections, 8 points deleted in small loops,
+                               9 steps, 10..15 reserved */
+    VLB_FIELD_VEL = 8       /* float64 [N][3]: ds/dt at the first RK stage of the last filament advance */
+};
+
+/* Create a channel (Sec. II set-up): validates p (tau > 1/2, stream_axis 2,
+ * dxi_min < dxi_max, Mach of init_vn and heater_vn below 0.05), allocates every
+ * device buffer for the lattice and max_points filament points, and fills the
+ * lattice with the uniform equilibrium f^eq(rho0, init_vn) (Eq. 7).  `alloc`
+ * may be NULL (cudaMalloc is used); `stream` is a cudaStream_t (NULL = the
+ * legacy default stream).  On success *out receives the handle. */
+int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* stream, vlb_channel** out);
+
+/* Replace the filament set (Sec. II.A): xyz is host float64 [n][3], next host
+ * int32 [n] (a permutation made of closed loops).  Points on periodic axes are
+ * wrapped into [0, n); points outside the walls are rejected.  Errors:
+ * CAPACITY (n > max_points), TOPOLOGY, INVALID_ARG (NaN, outside walls). */
+int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, int32_t n);
+
+/* Advance `nsteps` coupled steps (all phases, in order LBM, VFM, remesh,
+ * reconnect).  Work is queued on the channel's stream; the call waits for it
+ * once at the end and returns the first error the device reported (MACH, NAN,
+ * CAPACITY, CFL, TIMEOUT). */
+int vlb_step(vlb_channel* ch, int32_t nsteps);
+
+/* Run only the selected phases once (bitwise OR of VLB_PHASE_*), in the
+ * order of vlb_step; used to check each part of the step on its own. */
+int vlb_run_phases(vlb_channel* ch, int32_t phase_mask);
+
+/* Copy a field to host memory `dst` of `bytes` bytes (after a stream sync);
+ * *written (nullable) receives the byte count.  INVALID_ARG if too small. */
+int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, size_t* written);
+
+/* Overwrite FSTAR or FORCE from host memory (exact size required).  Writing
+ * FORCE marks the whole lattice as carrying force for the next pass. */
+int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t bytes);
+
+/* Total vortex line length sum |s_next(i) - s_i| in float64 (Sec. III.C line
+ * density L = length / volume), reduced on the device in a fixed order. */
+int vlb_line_length(vlb_channel* ch, double* out);
+
+/* Free every device buffer of the channel (after a stream sync).  NULL is a no-op. */
+void vlb_destroy(vlb_channel* ch);
+
+/* Message of the last error on this thread (never NULL). */
+const char* vlb_last_error(void);
+
+/* Device time of the lattice pass (Eqs. 9, 14) accumulated while `enable` is
+ * set: CUDA events recorded on the channel stream around every launch of the
+ * stream-collide kernel.  vlb_lbm_timing returns the total milliseconds and
+ * launch count since the last reset (after a stream sync). */
+int vlb_set_timing(vlb_channel* ch, int32_t enable);
+int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches);
+
+/* Stand-alone Biot-Savart velocity (Eq. 3, nonlocal part: every segment j ->
+ * next[j] except the two touching the target, minimum image on periodic axes)
+ * at every point of a device-resident filament set.
+ *   pos      device float64 SoA [3][n] (x block, then y, then z)
+ *   next     device int32 [n] successor indices (closed loops)
+ *   vel      device float32 SoA [3][n], written
+ *   scratch  device buffer of at least vlb_biot_savart_scratch_bytes(n) bytes
+ * Uses only p->n, p->wall and p->kappa.  Runs on `stream`; does not wait. */
+size_t vlb_biot_savart_scratch_bytes(int32_t n);
+int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next, int32_t n,
+                    float* vel, void* scratch, size_t scratch_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,609 @@
+// C ABI of libvlb (declared in include/vlb.h): the channel runtime.  It owns
+// the device buffers, sequences the kernels of one coupled step on the
+// caller's stream, and moves fields between host and device.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "vlb_internal.cuh"
+
+using namespace vlb;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(VLB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct vlb_channel {
+    vlb_params p;
+    vlb_allocator alloc;
+    bool has_alloc = false;
+    cudaStream_t stream = nullptr;
+    Dev d;
+    LbmParams lp;
+    VfmParams vp;
+    int cur_f = 0;     // population buffer holding the current state
+    int cur_p = 0;     // point buffer holding the current filaments
+    int cap = 0;
+    int hsize = 0;
+    int bpp = 0;
+    int nsplit_max = 1;
+    int n_hint = 0;
+    long long steps = 0;
+    std::vector<void*> blocks;
+    int* h_counters = nullptr;   // pinned
+    double* h_dstats = nullptr;  // pinned
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double timing_ms = 0.0;
+    long long timing_launches = 0;
+
+    void* dalloc(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~size_t(255);
+        void* ptr = nullptr;
+        if (has_alloc) {
+            ptr = alloc.alloc(alloc.ctx, bytes, (void*)stream);
+        } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+            ptr = nullptr;
+        }
+        if (ptr) blocks.push_back(ptr);
+        return ptr;
+    }
+};
+
+namespace {
+
+void release(vlb_channel* ch) {
+    cudaStreamSynchronize(ch->stream);
+    for (void* b : ch->blocks) {
+        if (ch->has_alloc) ch->alloc.free(ch->alloc.ctx, b, (void*)ch->stream);
+        else cudaFree(b);
+    }
+    ch->blocks.clear();
+    for (cudaEvent_t e : ch->ev) cudaEventDestroy(e);
+    ch->ev.clear();
+    if (ch->h_counters) cudaFreeHost(ch->h_counters);
+    if (ch->h_dstats) cudaFreeHost(ch->h_dstats);
+    ch->h_counters = nullptr;
+    ch->h_dstats = nullptr;
+}
+
+int status_to_code(int st, std::string* msg) {
+    if (st & ST_NAN) { *msg = "NaN/Inf in the lattice or on a filament"; return VLB_ERR_NAN; }
+    if (st & ST_TOPOLOGY) { *msg = "filament successor array corrupted"; return VLB_ERR_TOPOLOGY; }
+    if (st & ST_TIMEOUT) { *msg = "a device-side wait timed out"; return VLB_ERR_TIMEOUT; }
+    if (st & ST_CAPACITY) { *msg = "filament point capacity (max_points) exceeded"; return VLB_ERR_CAPACITY; }
+    if (st & ST_CFL) { *msg = "a filament point moved one cell or more within a step"; return VLB_ERR_CFL; }
+    if (st & ST_MACH) { *msg = "Mach number |u|/c_s reached 0.05"; return VLB_ERR_MACH; }
+    return VLB_OK;
+}
+
+// Copy the device counters and statistics to the pinned mirrors and wait.
+int sync_counters(vlb_channel* ch) {
+    cudaMemcpyAsync(ch->h_counters, ch->d.counters, sizeof(int) * CNT_COUNT, cudaMemcpyDeviceToHost, ch->stream);
+    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, sizeof(double) * DS_COUNT, cudaMemcpyDeviceToHost, ch->stream);
+    cudaError_t e = cudaStreamSynchronize(ch->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    ch->n_hint = ch->h_counters[CNT_N];
+    return VLB_OK;
+}
+
+void record_event(vlb_channel* ch) {
+    if (ch->ev_used == ch->ev.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ch->ev.push_back(e);
+    }
+    cudaEventRecord(ch->ev[ch->ev_used++], ch->stream);
+}
+
+void phase_lbm(vlb_channel* ch) {
+    Dev& d = ch->d;
+    const int nt = ch->lp.g.tnx * ch->lp.g.tny * ch->lp.g.tnz;
+    cudaMemsetAsync(d.umask, 0, (size_t)nt, ch->stream);
+    launch_mark_umask(ch->lp.g, d.pos[ch->cur_p], d.counters, ch->cap, d.umask, ch->stream);
+    if (ch->timing) record_event(ch);
+    launch_lbm_step(ch->lp, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
+    if (ch->timing) record_event(ch);
+    ch->cur_f ^= 1;
+    launch_plane_vs(ch->lp, d.part, ch->p.rho_s_over_rho_n, d.Vs, d.dstats, d.counters, ch->stream);
+}
+
+void phase_vfm(vlb_channel* ch) {
+    Dev& d = ch->d;
+    const int cap = ch->cap;
+    const int nsplit = bs_nsplit(ch->n_hint, cap) < ch->nsplit_max ? bs_nsplit(ch->n_hint, cap) : ch->nsplit_max;
+    const int nsub = ch->p.vfm_substeps > 0 ? ch->p.vfm_substeps : 1;
+    double* pos = d.pos[ch->cur_p];
+    const int* next = d.next[ch->cur_p];
+    const int* prev = d.prev[ch->cur_p];
+    for (int sub = 0; sub < nsub; ++sub) {
+        const int spread = (sub == 0 && ch->p.couple) ? 1 : 0;
+        if (spread) launch_zero_force(ch->lp.g, d.F, d.fmask, ch->stream);
+        launch_copy_pos(pos, d.s0, d.counters, cap, ch->stream);
+        for (int stage = 0; stage < 4; ++stage) {
+            const double* xs = stage == 0 ? d.s0 : d.st;
+            launch_geometry(ch->vp, xs, next, prev, d.counters, cap, d.sp, d.spp, d.dxi, d.lia, d.seglen, d.seg,
+                            ch->stream);
+            launch_biot_savart(ch->vp.g, ch->vp.kappa, d.seg, prev, d.counters, cap, nsplit, d.bsp, ch->stream);
+            launch_eom(ch->vp, stage, spread, d.s0, d.st, pos, d.acc, d.vel1, d.sp, d.dxi, d.lia, d.bsp, nsplit, d.U,
+                       d.Vs, d.F, d.fmask, d.counters, cap, ch->stream);
+        }
+    }
+}
+
+void run_phases(vlb_channel* ch, int mask) {
+    if (mask & VLB_PHASE_LBM) phase_lbm(ch);
+    if (mask & VLB_PHASE_VFM) phase_vfm(ch);
+    if (mask & VLB_PHASE_REMESH) {
+        launch_remesh(ch->vp, ch->d, ch->cur_p, ch->cap, ch->stream);
+        ch->cur_p ^= 1;
+    }
+    if (mask & VLB_PHASE_RECONNECT) {
+        launch_reconnect(ch->vp, ch->d, ch->cur_p, ch->cap, ch->hsize, ch->stream);
+        ch->cur_p ^= 1;
+    }
+}
+
+int finish(vlb_channel* ch) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    int rc = sync_counters(ch);
+    if (rc) return rc;
+    std::string msg;
+    rc = status_to_code(ch->h_counters[CNT_STATUS], &msg);
+    if (rc) return fail(rc, msg);
+    return VLB_OK;
+}
+
+bool valid_axis_params(const vlb_params* p, std::string* why) {
+    for (int a = 0; a < 3; ++a) {
+        if (p->n[a] < 1) { *why = "n must be >= 1 on every axis"; return false; }
+        if (p->wall[a] != 0 && p->wall[a] != 1) { *why = "wall must be 0 or 1"; return false; }
+    }
+    if (p->stream_axis != 2) { *why = "stream_axis must be 2 (z) in this library"; return false; }
+    if (!(p->tau > 0.5)) { *why = "tau must exceed 1/2"; return false; }
+    if (!(p->rho0 > 0.0)) { *why = "rho0 must be positive"; return false; }
+    if (!(p->dxi_min > 0.0) || !(p->dxi_max > p->dxi_min) || !(p->dxi_max < 1.0)) {
+        *why = "need 0 < dxi_min < dxi_max < 1";
+        return false;
+    }
+    if (!(p->rho_s_over_rho_n > 0.0) || !(p->core_a > 0.0) || !(p->kappa >= 0.0)) {
+        *why = "rho_s_over_rho_n, core_a must be positive and kappa >= 0";
+        return false;
+    }
+    if (p->max_points < 0 || p->vfm_substeps < 1 || p->reserved != 0) {
+        *why = "max_points >= 0, vfm_substeps >= 1, reserved == 0 required";
+        return false;
+    }
+    if (p->force_form != 0 && p->force_form != 1) { *why = "force_form must be 0 or 1"; return false; }
+    if (p->heater_vn != 0.0 && !p->wall[2]) { *why = "heater_vn needs walls on z"; return false; }
+    if (p->pin_vn != 0.0 && p->wall[2]) { *why = "pin_vn needs a periodic z axis"; return false; }
+    const double u0 = sqrt(p->init_vn[0] * p->init_vn[0] + p->init_vn[1] * p->init_vn[1] + p->init_vn[2] * p->init_vn[2]);
+    if (!(sqrt(3.0) * u0 < 0.05) || !(sqrt(3.0) * fabs(p->heater_vn) < 0.05) || !(sqrt(3.0) * fabs(p->pin_vn) < 0.05)) {
+        *why = "imposed velocities exceed Mach 0.05";
+        return false;
+    }
+    const long long cells = (long long)p->n[0] * p->n[1] * p->n[2];
+    if (cells > (1LL << 31) / 19) { *why = "lattice too large"; return false; }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vlb_last_error(void) { return g_last_error.c_str(); }
+
+int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* stream, vlb_channel** out) {
+    if (!p || !out) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    std::string why;
+    if (!valid_axis_params(p, &why)) return fail(VLB_ERR_INVALID_ARG, why);
+    if (alloc && (!alloc->alloc || !alloc->free)) return fail(VLB_ERR_INVALID_ARG, "allocator without callbacks");
+    vlb_channel* ch = new vlb_channel();
+    ch->p = *p;
+    if (alloc) {
+        ch->alloc = *alloc;
+        ch->has_alloc = true;
+    }
+    ch->stream = (cudaStream_t)stream;
+    Grid g;
+    g.nx = p->n[0];
+    g.ny = p->n[1];
+    g.nz = p->n[2];
+    for (int a = 0; a < 3; ++a) g.wall[a] = p->wall[a];
+    g.ncell = (long long)g.nx * g.ny * g.nz;
+    g.tnx = (g.nx + 7) >> TILE_SHIFT;
+    g.tny = (g.ny + 7) >> TILE_SHIFT;
+    g.tnz = (g.nz + 7) >> TILE_SHIFT;
+    LbmParams& L = ch->lp;
+    L.g = g;
+    L.omega = (float)(1.0 / p->tau);
+    L.pref = (float)(1.0 - 1.0 / (2.0 * p->tau));
+    L.rho0 = (float)p->rho0;
+    for (int a = 0; a < 3; ++a) L.body[a] = (float)p->body_force[a];
+    L.body_on = (p->body_force[0] != 0.0 || p->body_force[1] != 0.0 || p->body_force[2] != 0.0) ? 1 : 0;
+    L.heater = (float)p->heater_vn;
+    L.pin = (float)p->pin_vn;
+    L.pin_on = p->pin_vn != 0.0 ? 1 : 0;
+    {
+        // float shift constants s_i = fl(fl(w_i) rho0) as the kernels form them
+        const double wexact[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+        const float wf[3] = {1.f / 3.f, 1.f / 18.f, 1.f / 36.f};
+        const int mult[3] = {1, 6, 12};
+        double ssum = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const float sk = wf[k] * (float)p->rho0;
+            ssum += mult[k] * (double)sk;
+            L.dw[k] = (float)(wexact[k] * p->rho0 - (double)sk);
+        }
+        L.dr0 = (float)(ssum - p->rho0);
+    }
+    VfmParams& V = ch->vp;
+    V.g = g;
+    V.kappa = p->kappa;
+    V.alpha = p->alpha;
+    V.alpha_p = p->alpha_p;
+    V.ratio = p->rho_s_over_rho_n;
+    V.rho0 = p->rho0;
+    V.core_a = p->core_a;
+    V.dmin = p->dxi_min;
+    V.dmax = p->dxi_max;
+    V.dt = 1.0 / (double)p->vfm_substeps;
+    V.couple = p->couple;
+    V.force_form = p->force_form;
+
+    const long long C = g.ncell;
+    const int cap = p->max_points > 0 ? p->max_points : 1;
+    ch->cap = cap;
+    int h = 1;
+    while (h < 2 * cap) h <<= 1;
+    ch->hsize = h;
+    ch->bpp = (g.nx * g.ny + LBM_BLOCK - 1) / LBM_BLOCK;
+    int nsm = 1;
+    for (int n = 1; n <= cap; n += (n < 4096 ? 1 : 64)) {
+        const int k = bs_nsplit(n, cap);
+        if (k > nsm) nsm = k;
+    }
+    ch->nsplit_max = nsm;
+    const int ntiles = g.tnx * g.tny * g.tnz;
+    Dev& d = ch->d;
+    bool ok = true;
+    auto A = [&](size_t bytes) {
+        void* q = ch->dalloc(bytes);
+        if (!q) ok = false;
+        return q;
+    };
+    d.f[0] = (float*)A(sizeof(float) * 19 * (size_t)C);
+    d.f[1] = (float*)A(sizeof(float) * 19 * (size_t)C);
+    d.F = (float*)A(sizeof(float) * 3 * (size_t)C);
+    d.U = (float*)A(sizeof(float) * 3 * (size_t)C);
+    d.fmask = (uint8_t*)A((size_t)ntiles);
+    d.umask = (uint8_t*)A((size_t)ntiles);
+    d.part = (double*)A(sizeof(double) * 3 * (size_t)ch->bpp * g.nz);
+    d.Vs = (double*)A(sizeof(double) * (size_t)g.nz);
+    d.dstats = (double*)A(sizeof(double) * DS_COUNT);
+    d.counters = (int*)A(sizeof(int) * CNT_COUNT);
+    const size_t P3 = sizeof(double) * 3 * (size_t)cap;
+    for (int b = 0; b < 2; ++b) {
+        d.pos[b] = (double*)A(P3);
+        d.next[b] = (int*)A(sizeof(int) * (size_t)cap);
+        d.prev[b] = (int*)A(sizeof(int) * (size_t)cap);
+    }
+    d.s0 = (double*)A(P3);
+    d.st = (double*)A(P3);
+    d.acc = (double*)A(P3);
+    d.vel1 = (double*)A(P3);
+    d.sp = (double*)A(P3);
+    d.spp = (double*)A(P3);
+    d.lia = (double*)A(P3);
+    d.dxi = (double*)A(sizeof(double) * (size_t)cap);
+    d.seglen = (double*)A(sizeof(double) * (size_t)cap);
+    d.seg = (float4*)A(sizeof(float4) * 3 * (size_t)cap);
+    d.bsp = (float*)A(sizeof(float) * 3 * (size_t)cap * (size_t)nsm);
+    d.flags = (uint8_t*)A((size_t)cap);
+    d.alive = (uint8_t*)A((size_t)cap);
+    d.nnext = (int*)A(sizeof(int) * (size_t)cap);
+    d.newidx = (int*)A(sizeof(int) * (size_t)cap);
+    d.hkey = (int*)A(sizeof(int) * (size_t)cap);
+    d.hcount = (int*)A(sizeof(int) * (size_t)h);
+    d.hstart = (int*)A(sizeof(int) * (size_t)h);
+    d.hcursor = (int*)A(sizeof(int) * (size_t)h);
+    d.hentry = (int*)A(sizeof(int) * (size_t)cap);
+    d.nn = (int*)A(sizeof(int) * (size_t)cap);
+    d.nd2 = (double*)A(sizeof(double) * (size_t)cap);
+    const size_t nc = (size_t)cap / 2 + 1;
+    d.cand_i = (int*)A(sizeof(int) * nc);
+    d.cand_a = (int*)A(sizeof(int) * nc);
+    d.cand_b = (int*)A(sizeof(int) * nc);
+    d.cand_d2 = (double*)A(sizeof(double) * nc);
+    d.cand_order = (int*)A(sizeof(int) * nc);
+    d.stamp = (int*)A(sizeof(int) * (size_t)cap);
+    if (!ok) {
+        release(ch);
+        delete ch;
+        return fail(VLB_ERR_OOM, "device allocation failed");
+    }
+    if (cudaMallocHost((void**)&ch->h_counters, sizeof(int) * CNT_COUNT) != cudaSuccess ||
+        cudaMallocHost((void**)&ch->h_dstats, sizeof(double) * DS_COUNT) != cudaSuccess) {
+        release(ch);
+        delete ch;
+        return fail(VLB_ERR_OOM, "pinned host allocation failed");
+    }
+    cudaStream_t s = ch->stream;
+    cudaMemsetAsync(d.F, 0, sizeof(float) * 3 * (size_t)C, s);
+    cudaMemsetAsync(d.fmask, 0, (size_t)ntiles, s);
+    cudaMemsetAsync(d.umask, 0, (size_t)ntiles, s);
+    cudaMemsetAsync(d.counters, 0, sizeof(int) * CNT_COUNT, s);
+    cudaMemsetAsync(d.dstats, 0, sizeof(double) * DS_COUNT, s);
+    cudaMemsetAsync(d.stamp, 0, sizeof(int) * (size_t)cap, s);
+    cudaMemsetAsync(d.bsp, 0, sizeof(float) * 3 * (size_t)cap * (size_t)nsm, s);
+    launch_lbm_init(L, d.f[0], d.U, p->init_vn, s);
+    std::vector<double> vs((size_t)g.nz, -(1.0 / p->rho_s_over_rho_n) * p->init_vn[2]);
+    double mass = p->rho0 * (double)C;
+    cudaMemcpyAsync(d.Vs, vs.data(), sizeof(double) * vs.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d.dstats + DS_MASS, &mass, sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "channel initialisation");
+        release(ch);
+        delete ch;
+        return rc;
+    }
+    *out = ch;
+    return VLB_OK;
+}
+
+void vlb_destroy(vlb_channel* ch) {
+    if (!ch) return;
+    release(ch);
+    delete ch;
+}
+
+int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, int32_t n) {
+    if (!ch || n < 0 || (n > 0 && (!xyz || !next))) return fail(VLB_ERR_INVALID_ARG, "bad seed arguments");
+    if (n > ch->cap || (n > 0 && ch->p.max_points == 0)) return fail(VLB_ERR_CAPACITY, "more points than max_points");
+    std::vector<char> seen((size_t)n, 0);
+    std::vector<double> soa(3 * (size_t)ch->cap, 0.0);
+    std::vector<int> prv((size_t)(n > 0 ? n : 1), 0);
+    for (int i = 0; i < n; ++i) {
+        const int q = next[i];
+        if (q < 0 || q >= n || seen[(size_t)q]) return fail(VLB_ERR_TOPOLOGY, "next[] must be a permutation of closed loops");
+        seen[(size_t)q] = 1;
+        prv[(size_t)q] = i;
+        for (int a = 0; a < 3; ++a) {
+            double v = xyz[3 * (size_t)i + a];
+            if (v != v || isinf(v)) return fail(VLB_ERR_INVALID_ARG, "non-finite position");
+            const double L = (double)ch->p.n[a];
+            if (ch->p.wall[a]) {
+                if (v <= -0.5 || v >= L - 0.5) return fail(VLB_ERR_INVALID_ARG, "point outside the walls");
+                const double lo = -0.5 + 0.5 * ch->p.dxi_min, hi = L - 0.5 - 0.5 * ch->p.dxi_min;
+                if (v < lo) v = lo;
+                if (v > hi) v = hi;
+            } else {
+                if (v < 0.0) v += L;
+                else if (v >= L) v -= L;
+                if (v < 0.0 || v >= L) return fail(VLB_ERR_INVALID_ARG, "periodic coordinate more than one box away");
+            }
+            soa[(size_t)a * ch->cap + i] = v;
+        }
+    }
+    Dev& d = ch->d;
+    cudaStream_t s = ch->stream;
+    const int b = ch->cur_p;
+    cudaMemcpyAsync(d.pos[b], soa.data(), sizeof(double) * 3 * (size_t)ch->cap, cudaMemcpyHostToDevice, s);
+    if (n > 0) {
+        cudaMemcpyAsync(d.next[b], next, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d.prev[b], prv.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s);
+    }
+    cudaMemcpyAsync(d.counters + CNT_N, &n, sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "seed copy");
+    ch->n_hint = n;
+    return VLB_OK;
+}
+
+int vlb_step(vlb_channel* ch, int32_t nsteps) {
+    if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
+    for (int k = 0; k < nsteps; ++k) {
+        run_phases(ch, VLB_PHASE_ALL);
+        ch->steps++;
+    }
+    return finish(ch);
+}
+
+int vlb_run_phases(vlb_channel* ch, int32_t mask) {
+    if (!ch || mask < 0 || mask > VLB_PHASE_ALL) return fail(VLB_ERR_INVALID_ARG, "bad phase mask");
+    run_phases(ch, mask);
+    return finish(ch);
+}
+
+int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, size_t* written) {
+    if (!ch || !dst) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    int rc = sync_counters(ch);
+    if (rc) return rc;
+    const long long C = ch->lp.g.ncell;
+    const int N = ch->h_counters[CNT_N];
+    size_t need = 0;
+    switch (which) {
+        case VLB_FIELD_RHO: need = sizeof(float) * (size_t)C; break;
+        case VLB_FIELD_U: case VLB_FIELD_FORCE: need = sizeof(float) * 3 * (size_t)C; break;
+        case VLB_FIELD_FSTAR: need = sizeof(float) * 19 * (size_t)C; break;
+        case VLB_FIELD_POS: case VLB_FIELD_VEL: need = sizeof(double) * 3 * (size_t)N; break;
+        case VLB_FIELD_NEXT: need = sizeof(int) * (size_t)N; break;
+        case VLB_FIELD_PLANE_VS: need = sizeof(double) * (size_t)ch->lp.g.nz; break;
+        case VLB_FIELD_STATS: need = sizeof(double) * 16; break;
+        default: return fail(VLB_ERR_INVALID_ARG, "unknown field");
+    }
+    if (bytes < need) return fail(VLB_ERR_INVALID_ARG, "destination buffer too small");
+    Dev& d = ch->d;
+    cudaStream_t s = ch->stream;
+    float* tmp = d.f[ch->cur_f ^ 1];  // scratch between steps
+    cudaError_t e = cudaSuccess;
+    if (which == VLB_FIELD_RHO || which == VLB_FIELD_U) {
+        launch_moments(ch->lp, d.f[ch->cur_f], d.F, d.fmask, tmp, tmp + C, s);
+        e = cudaMemcpyAsync(dst, which == VLB_FIELD_RHO ? tmp : tmp + C, need, cudaMemcpyDeviceToHost, s);
+    } else if (which == VLB_FIELD_FSTAR) {
+        launch_unshift(ch->lp, d.f[ch->cur_f], tmp, +1, s);
+        e = cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, s);
+    } else if (which == VLB_FIELD_FORCE) {
+        e = cudaMemcpyAsync(dst, d.F, need, cudaMemcpyDeviceToHost, s);
+    } else if (which == VLB_FIELD_POS || which == VLB_FIELD_VEL) {
+        std::vector<double> soa(3 * (size_t)ch->cap);
+        const double* src = which == VLB_FIELD_POS ? d.pos[ch->cur_p] : d.vel1;
+        e = cudaMemcpyAsync(soa.data(), src, sizeof(double) * 3 * (size_t)ch->cap, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "read positions");
+        double* o = (double*)dst;
+        for (int i = 0; i < N; ++i)
+            for (int a = 0; a < 3; ++a) o[3 * (size_t)i + a] = soa[(size_t)a * ch->cap + i];
+    } else if (which == VLB_FIELD_NEXT) {
+        if (N > 0) e = cudaMemcpyAsync(dst, d.next[ch->cur_p], need, cudaMemcpyDeviceToHost, s);
+    } else if (which == VLB_FIELD_PLANE_VS) {
+        e = cudaMemcpyAsync(dst, d.Vs, need, cudaMemcpyDeviceToHost, s);
+    } else {
+        launch_line_length(ch->lp.g, d.pos[ch->cur_p], d.next[ch->cur_p], d.counters, ch->cap, d.dstats, s);
+        rc = sync_counters(ch);
+        if (rc) return rc;
+        double* o = (double*)dst;
+        for (int k = 0; k < 16; ++k) o[k] = 0.0;
+        o[0] = ch->h_counters[CNT_N];
+        o[1] = ch->h_counters[CNT_STATUS];
+        o[2] = ch->h_dstats[DS_MASS];
+        o[3] = ch->h_dstats[DS_LINE];
+        o[4] = ch->h_dstats[DS_MAXMACH];
+        o[5] = ch->h_dstats[DS_SPLITS];
+        o[6] = ch->h_dstats[DS_MERGES];
+        o[7] = ch->h_dstats[DS_RECON];
+        o[8] = ch->h_dstats[DS_SMALL];
+        o[9] = (double)ch->steps;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "read field");
+    if (written) *written = need;
+    return VLB_OK;
+}
+
+int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t bytes) {
+    if (!ch || !src) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    const long long C = ch->lp.g.ncell;
+    Dev& d = ch->d;
+    cudaStream_t s = ch->stream;
+    cudaError_t e;
+    if (which == VLB_FIELD_FSTAR) {
+        if (bytes != sizeof(float) * 19 * (size_t)C) return fail(VLB_ERR_INVALID_ARG, "FSTAR size mismatch");
+        float* tmp = d.f[ch->cur_f ^ 1];
+        e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, s);
+        launch_unshift(ch->lp, tmp, d.f[ch->cur_f], -1, s);
+    } else if (which == VLB_FIELD_FORCE) {
+        if (bytes != sizeof(float) * 3 * (size_t)C) return fail(VLB_ERR_INVALID_ARG, "FORCE size mismatch");
+        e = cudaMemcpyAsync(d.F, src, bytes, cudaMemcpyHostToDevice, s);
+        const int nt = ch->lp.g.tnx * ch->lp.g.tny * ch->lp.g.tnz;
+        cudaMemsetAsync(d.fmask, 1, (size_t)nt, s);
+    } else {
+        return fail(VLB_ERR_INVALID_ARG, "field is not writable");
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "write field");
+    return VLB_OK;
+}
+
+int vlb_line_length(vlb_channel* ch, double* out) {
+    if (!ch || !out) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    launch_line_length(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.next[ch->cur_p], ch->d.counters, ch->cap,
+                       ch->d.dstats, ch->stream);
+    cudaMemcpyAsync(ch->h_dstats + DS_LINE, ch->d.dstats + DS_LINE, sizeof(double), cudaMemcpyDeviceToHost,
+                    ch->stream);
+    cudaError_t e = cudaStreamSynchronize(ch->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "line length");
+    *out = ch->h_dstats[DS_LINE];
+    return VLB_OK;
+}
+
+int vlb_set_timing(vlb_channel* ch, int32_t enable) {
+    if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
+    cudaStreamSynchronize(ch->stream);
+    ch->timing = enable != 0;
+    ch->ev_used = 0;
+    ch->timing_ms = 0.0;
+    ch->timing_launches = 0;
+    return VLB_OK;
+}
+
+int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches) {
+    if (!ch || !total_ms || !launches) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    cudaError_t e = cudaStreamSynchronize(ch->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "timing sync");
+    for (size_t k = 0; k + 1 < ch->ev_used; k += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ch->ev[k], ch->ev[k + 1]);
+        ch->timing_ms += ms;
+        ch->timing_launches++;
+    }
+    ch->ev_used = 0;
+    *total_ms = ch->timing_ms;
+    *launches = ch->timing_launches;
+    return VLB_OK;
+}
+
+size_t vlb_biot_savart_scratch_bytes(int32_t n) {
+    if (n < 1) n = 1;
+    const int ns = bs_nsplit(n, n);
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return up(sizeof(int) * CNT_COUNT) + up(sizeof(int) * (size_t)n) + up(sizeof(float4) * 3 * (size_t)n) +
+           up(sizeof(float) * 3 * (size_t)n * (size_t)ns);
+}
+
+int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel, void* scratch,
+                    size_t scratch_bytes, void* stream) {
+    if (!p || n < 0 || (n > 0 && (!pos || !next || !vel || !scratch)))
+        return fail(VLB_ERR_INVALID_ARG, "bad Biot-Savart arguments");
+    if (n == 0) return VLB_OK;
+    if (scratch_bytes < vlb_biot_savart_scratch_bytes(n)) return fail(VLB_ERR_INVALID_ARG, "scratch too small");
+    if (((uintptr_t)scratch & 255u) != 0) return fail(VLB_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+    Grid g;
+    g.nx = p->n[0];
+    g.ny = p->n[1];
+    g.nz = p->n[2];
+    for (int a = 0; a < 3; ++a) g.wall[a] = p->wall[a];
+    g.ncell = (long long)g.nx * g.ny * g.nz;
+    g.tnx = g.tny = g.tnz = 1;
+    const int ns = bs_nsplit(n, n);
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char* base = (char*)scratch;
+    int* counters = (int*)base;
+    base += up(sizeof(int) * CNT_COUNT);
+    int* prev = (int*)base;
+    base += up(sizeof(int) * (size_t)n);
+    float4* seg = (float4*)base;
+    base += up(sizeof(float4) * 3 * (size_t)n);
+    float* bsp = (float*)base;
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, s);
+    launch_biot_savart(g, p->kappa, seg, prev, counters, n, ns, bsp, s);
+    launch_bs_reduce(bsp, ns, n, n, vel, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "Biot-Savart launch");
+    return VLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,451 @@
+// Filament topology updates of the coupled step (Sec. II.A of
+// arXiv 2108.04435): remeshing to the resolution [dxi_min, dxi_max] and
+// reconnection by leg exchange when two vortices come within dxi_max
+// (Sec. III.B), then deletion of loops with fewer than five points and a
+// stable compaction of the point arrays.
+//
+// Rules (the paper fixes only the resolution and "exchange the legs"):
+//  remesh    split every segment longer than dxi_max at its arc midpoint
+//            s_i + b/2 - (l^2/16)(s''_i + s''_q) (new points appended in
+//            ascending i); a point with a neighbouring segment shorter than
+//            dxi_min whose removal keeps the merged segment within dxi_max,
+//            and whose segments are not split, is removed unless a candidate
+//            neighbour outranks it (fmix32 priority of the index).
+//  reconnect nearest j of each i within dxi_max outside its two-link
+//            neighbourhood (ties to the smaller j); for mutual pairs the first
+//            of the segment pairs (i,j), (i,p(j)), (p(i),j), (p(i),p(j)) with
+//            the largest positive length decrease is exchanged; exchanges are
+//            applied in ascending (d^2, i), skipping any that touches a point
+//            already used.
+// All decisions are FP64 predicates evaluated in the same order as a plain
+// IEEE implementation (this file is compiled with -fmad=false), so they are
+// bit-identical to it on identical inputs.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "vlb_internal.cuh"
+
+namespace vlb {
+
+namespace {
+
+__device__ __forceinline__ double min_image(const Grid& g, int axis, double d) {
+    if (!g.wall[axis]) {
+        const double L = (double)(axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz));
+        if (d > 0.5 * L) d -= L;
+        else if (d < -0.5 * L) d += L;
+    }
+    return d;
+}
+
+__device__ __forceinline__ double dist(const Grid& g, const double* pos, int cap, int from, int to) {
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = min_image(g, k, pos[(long long)k * cap + to] - pos[(long long)k * cap + from]);
+    return sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+}
+
+// MurmurHash3 32-bit finaliser (fmix32), used as the merge priority.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ bool outranks(int a, int b) {
+    const uint32_t ha = fmix32((uint32_t)a), hb = fmix32((uint32_t)b);
+    return ha > hb || (ha == hb && a < b);
+}
+
+// Block-wide exclusive scan of one int per thread (blockDim.x == 1024).
+__device__ int block_exclusive_scan(int v, int* total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const int base = wid > 0 ? warp_sums[wid - 1] : 0;
+    const int tot = warp_sums[31];
+    __syncthreads();
+    *total = tot;
+    return base + x - v;
+}
+
+// ------------------------------------------------------------------ remesh
+
+__global__ void k_remesh_flags(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
+                               const int* __restrict__ prev, const double* __restrict__ seglen,
+                               const int* __restrict__ counters, int cap, uint8_t* __restrict__ flags) {
+    const int N = counters[CNT_N];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int p = prev[i], q = next[i];
+    const double li = seglen[i], lp = seglen[p];
+    const bool split = li > P.dmax;
+    const bool split_p = lp > P.dmax;
+    const double lmin = lp < li ? lp : li;
+    const bool cand = (lmin < P.dmin) && (dist(P.g, pos, cap, p, q) <= P.dmax) && !split_p && !split;
+    flags[i] = (uint8_t)((split ? 1 : 0) | (cand ? 2 : 0));
+}
+
+// One block: ranks of the split segments (ascending i), removals, the new
+// points' positions and the successor array of the remeshed set.
+__global__ void __launch_bounds__(1024) k_remesh_apply(VfmParams P, double* __restrict__ pos,
+                                                        const int* __restrict__ next, const int* __restrict__ prev,
+                                                        const double* __restrict__ spp,
+                                                        const double* __restrict__ seglen,
+                                                        const uint8_t* __restrict__ flags, int* __restrict__ nnext,
+                                                        uint8_t* __restrict__ alive, int* __restrict__ counters,
+                                                        double* __restrict__ dstats, int cap) {
+    __shared__ int s_removed[1024];
+    const int N = counters[CNT_N];
+    const int per = (N + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int b0 = min(N, (int)threadIdx.x * per);
+    const int b1 = min(N, b0 + per);
+    int mine = 0;
+    for (int i = b0; i < b1; ++i) mine += flags[i] & 1;
+    int S = 0;
+    int running = block_exclusive_scan(mine, &S);
+    if ((long long)N + S > (long long)cap) {
+        if (threadIdx.x == 0) atomicOr(&counters[CNT_STATUS], ST_CAPACITY);
+        S = 0;
+    }
+    int removed = 0;
+    for (int i = b0; i < b1; ++i) {
+        const uint8_t fi = flags[i];
+        const int p = prev[i], q = next[i];
+        const bool rem = (fi & 2) && !((flags[p] & 2) && outranks(p, i)) && !((flags[q] & 2) && outranks(q, i));
+        alive[i] = rem ? 0 : 1;
+        if (rem) {
+            ++removed;
+            continue;
+        }
+        if ((fi & 1) && S > 0) {
+            const int m = N + running;
+            const double l = seglen[i];
+            double ms[3];
+            for (int k = 0; k < 3; ++k) {
+                const long long oi = (long long)k * cap + i, oq = (long long)k * cap + q;
+                const double b = min_image(P.g, k, pos[oq] - pos[oi]);
+                ms[k] = pos[oi] + 0.5 * b - (l * l / 16.0) * (spp[oi] + spp[oq]);
+            }
+            for (int a = 0; a < 3; ++a) {
+                const double L = (double)(a == 0 ? P.g.nx : (a == 1 ? P.g.ny : P.g.nz));
+                if (!P.g.wall[a]) {
+                    if (ms[a] < 0.0) ms[a] += L;
+                    else if (ms[a] >= L) ms[a] -= L;
+                } else {
+                    const double lo = -0.5 + 0.5 * P.dmin, hi = L - 0.5 - 0.5 * P.dmin;
+                    if (ms[a] < lo) ms[a] = lo;
+                    if (ms[a] > hi) ms[a] = hi;
+                }
+                pos[(long long)a * cap + m] = ms[a];
+            }
+            nnext[i] = m;
+            nnext[m] = q;
+            alive[m] = 1;
+        } else {
+            const uint8_t fq = flags[q];
+            const int qp = i, qn = next[q];
+            const bool rem_q =
+                (fq & 2) && !((flags[qp] & 2) && outranks(qp, q)) && !((flags[qn] & 2) && outranks(qn, q));
+            nnext[i] = rem_q ? qn : q;
+        }
+        if (fi & 1) ++running;
+    }
+    s_removed[threadIdx.x] = removed;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s_removed[threadIdx.x] += s_removed[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        counters[CNT_TOTAL] = N + S;
+        counters[CNT_SMALL] = 0;
+        dstats[DS_SPLITS] += (double)S;
+        dstats[DS_MERGES] += (double)s_removed[0];
+    }
+}
+
+// Points of loops with fewer than five points (succ^k(i) == i for k <= 4) die.
+__global__ void k_small_loops(const int* __restrict__ succ, uint8_t* __restrict__ alive, int* __restrict__ counters) {
+    const int T = counters[CNT_TOTAL];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= T || !alive[k]) return;
+    int j = k;
+    for (int s = 1; s <= 4; ++s) {
+        j = succ[j];
+        if ((unsigned)j >= (unsigned)T) {
+            atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
+            return;
+        }
+        if (j == k) {
+            alive[k] = 0;
+            atomicAdd(&counters[CNT_SMALL], 1);
+            return;
+        }
+    }
+}
+
+// One block: stable compaction of the alive points of [0, total) into the
+// other point buffer, successor indices renumbered, predecessors rebuilt.
+__global__ void __launch_bounds__(1024) k_compact(const double* __restrict__ pin, const int* __restrict__ succ,
+                                                   const uint8_t* __restrict__ alive, int* __restrict__ newidx,
+                                                   double* __restrict__ pout, int* __restrict__ nout,
+                                                   int* __restrict__ pvout, int* __restrict__ counters,
+                                                   double* __restrict__ dstats, int cap) {
+    const int T = counters[CNT_TOTAL];
+    const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int b0 = min(T, (int)threadIdx.x * per);
+    const int b1 = min(T, b0 + per);
+    int mine = 0;
+    for (int k = b0; k < b1; ++k) mine += alive[k] ? 1 : 0;
+    int M = 0;
+    int base = block_exclusive_scan(mine, &M);
+    for (int k = b0; k < b1; ++k) newidx[k] = alive[k] ? base++ : -1;
+    __syncthreads();
+    for (int k = b0; k < b1; ++k) {
+        if (!alive[k]) continue;
+        const int n = newidx[k];
+        for (int c = 0; c < 3; ++c) pout[(long long)c * cap + n] = pin[(long long)c * cap + k];
+        const int sk = succ[k];
+        const int s = (unsigned)sk < (unsigned)T ? newidx[sk] : -1;
+        if (s < 0) {
+            atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
+            continue;
+        }
+        nout[n] = s;
+        pvout[s] = n;
+    }
+    if (threadIdx.x == 0) {
+        counters[CNT_N] = M;
+        dstats[DS_SMALL] += (double)counters[CNT_SMALL];
+        counters[CNT_SMALL] = 0;
+    }
+}
+
+// -------------------------------------------------------------- reconnect
+
+__device__ __forceinline__ uint32_t cell_hash(int cx, int cy, int cz) {
+    return ((uint32_t)cx * 73856093u) ^ ((uint32_t)cy * 19349663u) ^ ((uint32_t)cz * 83492791u);
+}
+
+__global__ void k_hash_count(const double* __restrict__ pos, const int* __restrict__ counters, int cap, uint32_t hmask,
+                             int* __restrict__ hkey, int* __restrict__ hcount) {
+    const int N = counters[CNT_N];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int cx = (int)floor(pos[i]), cy = (int)floor(pos[(long long)cap + i]), cz = (int)floor(pos[2LL * cap + i]);
+    const int h = (int)(cell_hash(cx, cy, cz) & hmask);
+    hkey[i] = h;
+    atomicAdd(&hcount[h], 1);
+}
+
+__global__ void __launch_bounds__(1024) k_hash_scan(const int* __restrict__ hcount, int hsize, int* __restrict__ hstart,
+                                                     int* __restrict__ hcursor, int* __restrict__ counters) {
+    const int per = (hsize + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int b0 = min(hsize, (int)threadIdx.x * per);
+    const int b1 = min(hsize, b0 + per);
+    int mine = 0;
+    for (int k = b0; k < b1; ++k) mine += hcount[k];
+    int tot = 0;
+    int base = block_exclusive_scan(mine, &tot);
+    for (int k = b0; k < b1; ++k) {
+        hstart[k] = base;
+        hcursor[k] = base;
+        base += hcount[k];
+    }
+    if (threadIdx.x == 0) counters[CNT_NPAIRS] = 0;
+}
+
+__global__ void k_hash_fill(const int* __restrict__ hkey, const int* __restrict__ counters, int* __restrict__ hcursor,
+                            int* __restrict__ hentry) {
+    const int N = counters[CNT_N];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int slot = atomicAdd(&hcursor[hkey[i]], 1);
+    hentry[slot] = i;
+}
+
+// Nearest point within dxi_max outside the two-link neighbourhood; every
+// point closer than dxi_max < 1 lies in one of the 27 unit cells around.
+__global__ void k_nearest(VfmParams P, double dmax2, const double* __restrict__ pos, const int* __restrict__ next,
+                          const int* __restrict__ prev, const int* __restrict__ counters, int cap, uint32_t hmask,
+                          const int* __restrict__ hstart, const int* __restrict__ hcount,
+                          const int* __restrict__ hentry, int* __restrict__ nn, double* __restrict__ nd2) {
+    const int N = counters[CNT_N];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int p = prev[i], q = next[i], pp = prev[p], qq = next[q];
+    double xi[3];
+    int c[3];
+    for (int k = 0; k < 3; ++k) {
+        xi[k] = pos[(long long)k * cap + i];
+        c[k] = (int)floor(xi[k]);
+    }
+    const int n[3] = {P.g.nx, P.g.ny, P.g.nz};
+    int best = -1;
+    double bd = 0.0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int cc[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+                for (int a = 0; a < 3; ++a)
+                    if (!P.g.wall[a]) cc[a] = ((cc[a] % n[a]) + n[a]) % n[a];
+                const int h = (int)(cell_hash(cc[0], cc[1], cc[2]) & hmask);
+                const int e0 = hstart[h], e1 = e0 + hcount[h];
+                for (int e = e0; e < e1; ++e) {
+                    const int j = hentry[e];
+                    if (j == i || j == p || j == q || j == pp || j == qq) continue;
+                    double d[3];
+                    for (int k = 0; k < 3; ++k) d[k] = min_image(P.g, k, pos[(long long)k * cap + j] - xi[k]);
+                    const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (!(d2 < dmax2)) continue;
+                    if (best < 0 || d2 < bd || (d2 == bd && j < best)) {
+                        best = j;
+                        bd = d2;
+                    }
+                }
+            }
+    nn[i] = best;
+    nd2[i] = bd;
+}
+
+__global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
+                        const int* __restrict__ prev, const int* __restrict__ nn, const double* __restrict__ nd2,
+                        int* __restrict__ counters, int cap, int* __restrict__ cand_i, int* __restrict__ cand_a,
+                        int* __restrict__ cand_b, double* __restrict__ cand_d2) {
+    const int N = counters[CNT_N];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int j = nn[i];
+    if (j <= i || nn[j] != i) return;
+    const int as[4] = {i, i, prev[i], prev[i]};
+    const int bs[4] = {j, prev[j], j, prev[j]};
+    double best = 0.0;
+    int pick = -1;
+    for (int k = 0; k < 4; ++k) {
+        const int a = as[k], b = bs[k], qa = next[a], qb = next[b];
+        const double gain = (dist(P.g, pos, cap, a, qa) + dist(P.g, pos, cap, b, qb)) -
+                            (dist(P.g, pos, cap, a, qb) + dist(P.g, pos, cap, b, qa));
+        if (gain > 0.0 && (pick < 0 || gain > best)) {
+            best = gain;
+            pick = k;
+        }
+    }
+    if (pick < 0) return;
+    const int slot = atomicAdd(&counters[CNT_NPAIRS], 1);
+    cand_i[slot] = i;
+    cand_a[slot] = as[pick];
+    cand_b[slot] = bs[pick];
+    cand_d2[slot] = nd2[i];
+}
+
+// Position of each candidate in ascending (d^2, i) order (keys are unique).
+__global__ void k_rank(const int* __restrict__ counters, const int* __restrict__ cand_i,
+                       const double* __restrict__ cand_d2, int* __restrict__ order) {
+    const int K = counters[CNT_NPAIRS];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    const double d = cand_d2[c];
+    const int ic = cand_i[c];
+    int r = 0;
+    for (int o = 0; o < K; ++o) {
+        const double e = cand_d2[o];
+        r += (e < d || (e == d && cand_i[o] < ic)) ? 1 : 0;
+    }
+    order[r] = c;
+}
+
+// Greedy pass in order; an exchange touching a point already used is skipped.
+__global__ void k_greedy(int* __restrict__ next, int* __restrict__ prev, int* __restrict__ counters,
+                         const int* __restrict__ order, const int* __restrict__ cand_a, const int* __restrict__ cand_b,
+                         int* __restrict__ stamp, double* __restrict__ dstats) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int K = counters[CNT_NPAIRS];
+    const int st = counters[CNT_STAMP] + 1;
+    counters[CNT_STAMP] = st;
+    int applied = 0;
+    for (int r = 0; r < K; ++r) {
+        const int c = order[r];
+        const int a = cand_a[c], b = cand_b[c];
+        const int qa = next[a], qb = next[b];
+        if (stamp[a] == st || stamp[qa] == st || stamp[b] == st || stamp[qb] == st) continue;
+        stamp[a] = st;
+        stamp[qa] = st;
+        stamp[b] = st;
+        stamp[qb] = st;
+        next[a] = qb;
+        prev[qb] = a;
+        next[b] = qa;
+        prev[qa] = b;
+        ++applied;
+    }
+    dstats[DS_RECON] += (double)applied;
+}
+
+__global__ void k_alive_all(uint8_t* __restrict__ alive, int* __restrict__ counters) {
+    const int N = counters[CNT_N];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) {
+        counters[CNT_TOTAL] = N;
+        counters[CNT_SMALL] = 0;
+    }
+    if (k < N) alive[k] = 1;
+}
+
+}  // namespace
+
+void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s) {
+    if (cap <= 0) return;
+    const int nb = (cap + 255) / 256;
+    launch_geometry(P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, d.sp, d.spp, d.dxi, d.lia, d.seglen,
+                    d.seg, s);
+    k_remesh_flags<<<nb, 256, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.seglen, d.counters, cap, d.flags);
+    k_remesh_apply<<<1, 1024, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
+                                      d.alive, d.counters, d.dstats, cap);
+    k_small_loops<<<nb, 256, 0, s>>>(d.nnext, d.alive, d.counters);
+    k_compact<<<1, 1024, 0, s>>>(d.pos[cur], d.nnext, d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1],
+                                 d.prev[cur ^ 1], d.counters, d.dstats, cap);
+}
+
+void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, cudaStream_t s) {
+    if (cap <= 0) return;
+    const int nb = (cap + 255) / 256;
+    const uint32_t hmask = (uint32_t)hsize - 1u;
+    const double dmax2 = P.dmax * P.dmax;
+    cudaMemsetAsync(d.hcount, 0, sizeof(int) * (size_t)hsize, s);
+    k_hash_count<<<nb, 256, 0, s>>>(d.pos[cur], d.counters, cap, hmask, d.hkey, d.hcount);
+    k_hash_scan<<<1, 1024, 0, s>>>(d.hcount, hsize, d.hstart, d.hcursor, d.counters);
+    k_hash_fill<<<nb, 256, 0, s>>>(d.hkey, d.counters, d.hcursor, d.hentry);
+    k_nearest<<<nb, 256, 0, s>>>(P, dmax2, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, hmask, d.hstart,
+                                 d.hcount, d.hentry, d.nn, d.nd2);
+    k_pairs<<<nb, 256, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap, d.cand_i,
+                               d.cand_a, d.cand_b, d.cand_d2);
+    k_rank<<<nb, 256, 0, s>>>(d.counters, d.cand_i, d.cand_d2, d.cand_order);
+    k_greedy<<<1, 32, 0, s>>>(d.next[cur], d.prev[cur], d.counters, d.cand_order, d.cand_a, d.cand_b, d.stamp,
+                              d.dstats);
+    k_alive_all<<<nb, 256, 0, s>>>(d.alive, d.counters);
+    k_small_loops<<<nb, 256, 0, s>>>(d.next[cur], d.alive, d.counters);
+    k_compact<<<1, 1024, 0, s>>>(d.pos[cur], d.next[cur], d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1],
+                                 d.prev[cur ^ 1], d.counters, d.dstats, cap);
+}
+
+}  // namespace vlb

@@ -1,0 +1,163 @@
+// Internal declarations shared by the CUDA translation units of libvlb.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vlb.h"
+
+namespace vlb {
+
+// Device status bits, OR-ed by kernels into Dev::counters[CNT_STATUS].
+enum : int {
+    ST_MACH = 1,
+    ST_NAN = 2,
+    ST_CAPACITY = 4,
+    ST_TIMEOUT = 8,
+    ST_CFL = 16,
+    ST_TOPOLOGY = 32,  // a successor index outside the live range (never expected)
+};
+
+// Device integer counters (one int array).
+enum : int {
+    CNT_N = 0,          // live filament points
+    CNT_TOTAL = 1,      // points before compaction (old + appended)
+    CNT_STATUS = 2,     // status bits
+    CNT_NPAIRS = 3,     // candidate reconnections this pass
+    CNT_STAMP = 4,      // reconnection pass counter (claim stamps)
+    CNT_SMALL = 5,      // points deleted in small loops this pass
+    CNT_COUNT = 8
+};
+
+// Device float64 statistics.
+enum : int {
+    DS_MASS = 0,
+    DS_MAXMACH = 1,
+    DS_LINE = 2,
+    DS_SPLITS = 3,
+    DS_MERGES = 4,
+    DS_RECON = 5,
+    DS_SMALL = 6,
+    DS_COUNT = 8
+};
+
+constexpr int TILE_SHIFT = 3;   // force / velocity activity tiles of 8^3 cells
+constexpr int LBM_BLOCK = 256;  // cells per stream-collide block (one z plane)
+constexpr int BS_TPB = 128;     // Biot-Savart targets per block
+constexpr int BS_TILE = 256;    // source segments per shared-memory tile
+constexpr int MAX_SPLIT = 64;   // Biot-Savart source splits
+
+// Geometry of the lattice, passed by value to kernels.
+struct Grid {
+    int nx, ny, nz;
+    int wall[3];
+    long long ncell;
+    int tnx, tny, tnz;  // activity tiles per axis
+};
+
+struct LbmParams {
+    Grid g;
+    float omega;        // 1/tau
+    float pref;         // 1 - 1/(2 tau)
+    float rho0;
+    float body[3];
+    float heater;       // heater_vn
+    float pin;          // pin_vn
+    float dr0;          // rho0 * (sum_i s_i - 1): density carried by the float shift constants s_i
+    float dw[3];        // w_i rho0 - s_i for the rest, axis and diagonal classes (exact in double, then float)
+    int body_on;
+    int pin_on;
+};
+
+struct VfmParams {
+    Grid g;
+    double kappa, alpha, alpha_p, ratio, rho0, core_a, dmin, dmax;
+    double dt;
+    int couple, force_form;
+};
+
+struct Dev {
+    // lattice
+    float* f[2];        // shifted populations f_i - w_i rho0, [19][C]
+    float* F;           // force grid [3][C]
+    float* U;           // velocity of the last pass [3][C], valid in u-active tiles
+    uint8_t* fmask;     // tiles where F may be non-zero
+    uint8_t* umask;     // tiles where U must be written
+    double* part;       // stream-collide block partials [nz][bpp][3]
+    double* Vs;         // [nz]
+    double* dstats;     // [DS_COUNT]
+    int* counters;      // [CNT_COUNT]
+    // filaments (SoA [3][cap] float64)
+    double* pos[2];
+    int* next[2];
+    int* prev[2];
+    double* s0;
+    double* st;
+    double* acc;
+    double* vel1;
+    double* sp;
+    double* spp;
+    double* lia;
+    double* dxi;
+    double* seglen;
+    float4* seg;        // Biot-Savart source records, 3 float4 per point
+    float* bsp;         // Biot-Savart partial sums [MAX_SPLIT][3][cap]
+    // topology scratch
+    uint8_t* flags;
+    uint8_t* alive;
+    int* nnext;
+    int* newidx;
+    int* hkey;
+    int* hcount;
+    int* hstart;
+    int* hcursor;
+    int* hentry;
+    int* nn;
+    double* nd2;
+    int* cand_i;
+    int* cand_a;
+    int* cand_b;
+    double* cand_d2;
+    int* cand_order;
+    int* stamp;
+    double* line_part;
+};
+
+// ---------------------------------------------------------------- launchers
+// lbm.cu
+void launch_lbm_init(const LbmParams& P, float* f, float* U, const double init_u[3], cudaStream_t s);
+void launch_lbm_step(const LbmParams& P, const float* fin, float* fout, const float* F, float* U,
+                     const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
+void launch_plane_vs(const LbmParams& P, const double* part, double ratio, double* Vs, double* dstats,
+                     int* counters, cudaStream_t s);
+void launch_moments(const LbmParams& P, const float* f, const float* F, const uint8_t* fmask, float* rho,
+                    float* U, cudaStream_t s);
+void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,
+                       cudaStream_t s);
+void launch_zero_force(const Grid& g, float* F, uint8_t* fmask, cudaStream_t s);
+void launch_unshift(const LbmParams& P, const float* fsh, float* out, int direction, cudaStream_t s);
+
+// vfm.cu
+void launch_copy_pos(const double* src, double* dst, const int* counters, int cap, cudaStream_t s);
+void launch_geometry(const VfmParams& P, const double* s, const int* next, const int* prev, const int* counters,
+                     int cap, double* sp, double* spp, double* dxi, double* lia, double* seglen, float4* seg,
+                     cudaStream_t st);
+void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, double* st, double* pos_out,
+                double* acc, double* vel1, const double* sp, const double* dxi, const double* lia, const float* bsp,
+                int nsplit, const float* U, const double* Vs, float* F, uint8_t* fmask, int* counters, int cap,
+                cudaStream_t s);
+void launch_line_length(const Grid& g, const double* pos, const int* next, const int* counters, int cap,
+                        double* dstats, cudaStream_t s);
+
+// bs.cu
+int bs_nsplit(int n_hint, int cap);
+void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
+                        int cap, int nsplit, float* bsp, cudaStream_t s);
+void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
+                               int* counters, cudaStream_t s);
+void launch_bs_reduce(const float* bsp, int nsplit, int n, int cap, float* vel, cudaStream_t s);
+
+// topo.cu
+void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s);
+void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, cudaStream_t s);
+
+}  // namespace vlb

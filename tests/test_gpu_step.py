@@ -1,0 +1,63 @@
+"""Whole coupled step through the C ABI vs the oracle, at the sizes the
+benchmark uses, plus multi-step drift and the smoke entry point."""
+import numpy as np
+import pytest
+
+from gpu_util import pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def compare_step(g, r, xyz, n, wall, tol=1e-5, line_tol=1e-9):
+    import oracle
+    from paper_2108_04435_gb300 import vlb
+    f_g = g.read(vlb.FIELD_FSTAR)
+    f_r = r.read(oracle.FIELD_FSTAR)
+    c, w, _ = oracle.lattice()
+    rest = (w * r.params["rho0"])[:, None]
+    assert rel_l2(f_g, f_r) < tol
+    assert rel_l2(f_g - rest, f_r - rest) < tol
+    assert rel_l2(g.read(vlb.FIELD_U), r.read(oracle.FIELD_U)) < tol
+    assert rel_l2(g.read(vlb.FIELD_FORCE), r.read(oracle.FIELD_FORCE)) < tol
+    assert np.array_equal(g.read(vlb.FIELD_NEXT), r.read(oracle.FIELD_NEXT))
+    pg, pr = g.read(vlb.FIELD_POS), r.read(oracle.FIELD_POS)
+    assert rel_l2(g.read(vlb.FIELD_VEL), r.read(oracle.FIELD_VEL)) < tol
+    assert abs(g.line_length() / r.line_length() - 1) < line_tol
+    return pg, pr
+
+
+def test_ring32_one_step():
+    from paper_2108_04435_gb300 import configs
+    p, xyz, nxt = configs.config("ring32")
+    g, r = pair(p, xyz, nxt)
+    g.step(1)
+    r.step(1)
+    pg, pr = compare_step(g, r, xyz, p["n"], p["wall"])
+    assert rel_l2(pg - xyz, pr - xyz) < 1e-5
+
+
+def test_ring32_twenty_steps():
+    from paper_2108_04435_gb300 import configs
+    p, xyz, nxt = configs.config("ring32")
+    g, r = pair(p, xyz, nxt)
+    g.step(20)
+    r.step(20)
+    pg, pr = compare_step(g, r, xyz, p["n"], p["wall"], tol=2e-5, line_tol=1e-7)
+    d = pg - pr
+    assert np.abs(d).max() < 1e-6
+
+
+def test_channel_64x64x256_one_step():
+    """The benchmark workload: closed channel, heater, 20 rings (~1.2k points)."""
+    from paper_2108_04435_gb300 import configs
+    p, xyz, nxt = configs.config("channel64x64x256")
+    g, r = pair(p, xyz, nxt)
+    g.step(1)
+    r.step(1)
+    pg, pr = compare_step(g, r, xyz, p["n"], p["wall"])
+    assert rel_l2(pg - xyz, pr - xyz) < 1e-5
+
+
+def test_smoke_entry():
+    import __graft_entry__
+    __graft_entry__.smoke()
