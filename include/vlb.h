@@ -103,7 +103,9 @@ enum {
     VLB_FIELD_STATS = 7,    /* float64 [16]: 0 points, 1 status bits, 2 mass, 3 line length, 4 max Mach,
                                5 splits, 6 merges, 7 reconnections, 8 points deleted in small loops,
                                9 steps, 10..15 reserved */
-    VLB_FIELD_VEL = 8       /* float64 [N][3]: ds/dt at the first RK stage of the last filament advance */
+    VLB_FIELD_VEL = 8,      /* float64 [N][3]: ds/dt at the first RK stage of the last filament advance */
+    VLB_FIELD_FDEV = 9      /* float32 [19][C]: f_i - w_i rho0 of the post-collision populations (read only;
+                               the flow signal at full float precision) */
 };
 
 /* Create a channel (Sec. II set-up): validates p (tau > 1/2, stream_axis 2,
@@ -123,8 +125,14 @@ int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, i
 /* Advance `nsteps` coupled steps (all phases, in order LBM, VFM, remesh,
  * reconnect).  Work is queued on the channel's stream; the call waits for it
  * once at the end and returns the first error the device reported (MACH, NAN,
- * CAPACITY, CFL, TIMEOUT). */
+ * CAPACITY, CFL, TIMEOUT).  On a created (non-default) stream each step is
+ * replayed from a CUDA graph captured on first use; every kernel reads the
+ * live filament count from device memory, so no host round trip is needed
+ * between steps. */
 int vlb_step(vlb_channel* ch, int32_t nsteps);
+
+/* Enable (default) or disable the graph replay of vlb_step. */
+int vlb_set_graphs(vlb_channel* ch, int32_t enable);
 
 /* Run only the selected phases once (bitwise OR of VLB_PHASE_*), in the
  * order of vlb_step; used to check each part of the step on its own. */

@@ -1,8 +1,8 @@
 """Build libvlb.so in-tree: one nvcc job per translation unit, then a link.
 
-Every kernel is compiled for sm_103a only.  vfm.cu and topo.cu are compiled
-with -fmad=false because their FP64 geometry feeds integer decisions
-(remeshing, reconnection) that must match a plain IEEE evaluation.
+Every kernel is compiled for sm_103a only.  topo.cu is compiled with
+-fmad=false because its FP64 geometry feeds integer decisions (remeshing,
+reconnection) that must match a plain IEEE evaluation.
 """
 from __future__ import annotations
 
@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = {"abi.cu": [], "lbm.cu": [], "bs.cu": [], "vfm.cu": ["-fmad=false"], "topo.cu": ["-fmad=false"]}
+SOURCES = {"abi.cu": [], "lbm.cu": [], "bs.cu": [], "vfm.cu": [], "topo.cu": ["-fmad=false"]}
 NVCC = os.environ.get("NVCC", "nvcc")
 
 

@@ -48,6 +48,9 @@ struct vlb_channel {
     int* h_counters = nullptr;   // pinned
     double* h_dstats = nullptr;  // pinned
     bool timing = false;
+    bool graphs = true;                      // replay captured steps when the stream allows capture
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [cur_f][cur_p]
+    int gclass[2][2] = {{-1, -1}, {-1, -1}};  // filament size class each graph was captured for
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
     double timing_ms = 0.0;
@@ -78,6 +81,12 @@ void release(vlb_channel* ch) {
     ch->blocks.clear();
     for (cudaEvent_t e : ch->ev) cudaEventDestroy(e);
     ch->ev.clear();
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (ch->gexec[a][b]) {
+                cudaGraphExecDestroy(ch->gexec[a][b]);
+                ch->gexec[a][b] = nullptr;
+            }
     if (ch->h_counters) cudaFreeHost(ch->h_counters);
     if (ch->h_dstats) cudaFreeHost(ch->h_dstats);
     ch->h_counters = nullptr;
@@ -122,13 +131,12 @@ void phase_lbm(vlb_channel* ch) {
     launch_lbm_step(ch->lp, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
     if (ch->timing) record_event(ch);
     ch->cur_f ^= 1;
-    launch_plane_vs(ch->lp, d.part, ch->p.rho_s_over_rho_n, d.Vs, d.dstats, d.counters, ch->stream);
+    launch_plane_vs(ch->lp, d.part, ch->stream);
 }
 
 void phase_vfm(vlb_channel* ch) {
     Dev& d = ch->d;
     const int cap = ch->cap;
-    const int nsplit = bs_nsplit(ch->n_hint, cap) < ch->nsplit_max ? bs_nsplit(ch->n_hint, cap) : ch->nsplit_max;
     const int nsub = ch->p.vfm_substeps > 0 ? ch->p.vfm_substeps : 1;
     double* pos = d.pos[ch->cur_p];
     const int* next = d.next[ch->cur_p];
@@ -136,14 +144,14 @@ void phase_vfm(vlb_channel* ch) {
     for (int sub = 0; sub < nsub; ++sub) {
         const int spread = (sub == 0 && ch->p.couple) ? 1 : 0;
         if (spread) launch_zero_force(ch->lp.g, d.F, d.fmask, ch->stream);
-        launch_copy_pos(pos, d.s0, d.counters, cap, ch->stream);
         for (int stage = 0; stage < 4; ++stage) {
-            const double* xs = stage == 0 ? d.s0 : d.st;
-            launch_geometry(ch->vp, xs, next, prev, d.counters, cap, d.sp, d.spp, d.dxi, d.lia, d.seglen, d.seg,
-                            ch->stream);
-            launch_biot_savart(ch->vp.g, ch->vp.kappa, d.seg, prev, d.counters, cap, nsplit, d.bsp, ch->stream);
-            launch_eom(ch->vp, stage, spread, d.s0, d.st, pos, d.acc, d.vel1, d.sp, d.dxi, d.lia, d.bsp, nsplit, d.U,
-                       d.Vs, d.F, d.fmask, d.counters, cap, ch->stream);
+            const double* xs = stage == 0 ? pos : d.st;
+            launch_geometry_stage(ch->vp, xs, next, prev, d.counters, cap, d.geo, d.seg, stage == 0 ? d.s0 : nullptr,
+                                  ch->stream);
+            launch_biot_savart(ch->vp.g, ch->vp.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint,
+                               d.bsp, d.vbs, ch->stream);
+            launch_eom(ch->vp, stage, spread, d.s0, d.st, pos, d.acc, d.vel1, d.geo, d.vbs, d.U, d.Vs, d.F, d.fmask,
+                       d.counters, cap, ch->stream);
         }
     }
 }
@@ -269,6 +277,11 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     V.dt = 1.0 / (double)p->vfm_substeps;
     V.couple = p->couple;
     V.force_form = p->force_form;
+    V.kq_f = (float)(p->kappa / (4.0 * 3.14159265358979323846));
+    V.inv_ea_f = (float)(1.0 / (exp(0.25) * p->core_a));
+    V.alpha_f = (float)p->alpha;
+    V.alpha_p_f = (float)p->alpha_p;
+    V.gscale_f = (float)(-p->rho_s_over_rho_n * p->rho0 * p->kappa);
 
     const long long C = g.ncell;
     const int cap = p->max_points > 0 ? p->max_points : 1;
@@ -277,11 +290,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     while (h < 2 * cap) h <<= 1;
     ch->hsize = h;
     ch->bpp = (g.nx * g.ny + LBM_BLOCK - 1) / LBM_BLOCK;
-    int nsm = 1;
-    for (int n = 1; n <= cap; n += (n < 4096 ? 1 : 64)) {
-        const int k = bs_nsplit(n, cap);
-        if (k > nsm) nsm = k;
-    }
+    const int nsm = bs_max_splits(cap);
     ch->nsplit_max = nsm;
     const int ntiles = g.tnx * g.tny * g.tnz;
     Dev& d = ch->d;
@@ -299,6 +308,8 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.umask = (uint8_t*)A((size_t)ntiles);
     d.part = (double*)A(sizeof(double) * 3 * (size_t)ch->bpp * g.nz);
     d.Vs = (double*)A(sizeof(double) * (size_t)g.nz);
+    d.plane = (double*)A(sizeof(double) * 3 * (size_t)g.nz);
+    d.plane_ticket = (int*)A(sizeof(int) * (size_t)g.nz);
     d.dstats = (double*)A(sizeof(double) * DS_COUNT);
     d.counters = (int*)A(sizeof(int) * CNT_COUNT);
     const size_t P3 = sizeof(double) * 3 * (size_t)cap;
@@ -311,22 +322,20 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.st = (double*)A(P3);
     d.acc = (double*)A(P3);
     d.vel1 = (double*)A(P3);
-    d.sp = (double*)A(P3);
     d.spp = (double*)A(P3);
-    d.lia = (double*)A(P3);
-    d.dxi = (double*)A(sizeof(double) * (size_t)cap);
     d.seglen = (double*)A(sizeof(double) * (size_t)cap);
+    d.geo = (float4*)A(sizeof(float4) * 2 * (size_t)cap);
     d.seg = (float4*)A(sizeof(float4) * 3 * (size_t)cap);
     d.bsp = (float*)A(sizeof(float) * 3 * (size_t)cap * (size_t)nsm);
+    d.vbs = (float*)A(sizeof(float) * 3 * (size_t)cap);
+    d.tile_ticket = (int*)A(sizeof(int) * (size_t)((cap + BS_TPB - 1) / BS_TPB));
     d.flags = (uint8_t*)A((size_t)cap);
     d.alive = (uint8_t*)A((size_t)cap);
     d.nnext = (int*)A(sizeof(int) * (size_t)cap);
     d.newidx = (int*)A(sizeof(int) * (size_t)cap);
     d.hkey = (int*)A(sizeof(int) * (size_t)cap);
-    d.hcount = (int*)A(sizeof(int) * (size_t)h);
-    d.hstart = (int*)A(sizeof(int) * (size_t)h);
-    d.hcursor = (int*)A(sizeof(int) * (size_t)h);
-    d.hentry = (int*)A(sizeof(int) * (size_t)cap);
+    d.hhead = (int*)A(sizeof(int) * (size_t)h);
+    d.hlink = (int*)A(sizeof(int) * (size_t)cap);
     d.nn = (int*)A(sizeof(int) * (size_t)cap);
     d.nd2 = (double*)A(sizeof(double) * (size_t)cap);
     const size_t nc = (size_t)cap / 2 + 1;
@@ -336,6 +345,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.cand_d2 = (double*)A(sizeof(double) * nc);
     d.cand_order = (int*)A(sizeof(int) * nc);
     d.stamp = (int*)A(sizeof(int) * (size_t)cap);
+    d.line_part = (double*)A(sizeof(double) * (size_t)((cap + 255) / 256));
     if (!ok) {
         release(ch);
         delete ch;
@@ -352,9 +362,18 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     cudaMemsetAsync(d.fmask, 0, (size_t)ntiles, s);
     cudaMemsetAsync(d.umask, 0, (size_t)ntiles, s);
     cudaMemsetAsync(d.counters, 0, sizeof(int) * CNT_COUNT, s);
+    cudaMemsetAsync(d.plane_ticket, 0, sizeof(int) * (size_t)g.nz, s);
+    L.plane_ticket = d.plane_ticket;
+    L.plane = d.plane;
+    L.Vs = d.Vs;
+    L.dstats = d.dstats;
+    L.counters = d.counters;
+    L.inv_ratio = 1.0 / p->rho_s_over_rho_n;
     cudaMemsetAsync(d.dstats, 0, sizeof(double) * DS_COUNT, s);
     cudaMemsetAsync(d.stamp, 0, sizeof(int) * (size_t)cap, s);
     cudaMemsetAsync(d.bsp, 0, sizeof(float) * 3 * (size_t)cap * (size_t)nsm, s);
+    cudaMemsetAsync(d.tile_ticket, 0, sizeof(int) * (size_t)((cap + BS_TPB - 1) / BS_TPB), s);
+    init_hash(d, h, s);
     launch_lbm_init(L, d.f[0], d.U, p->init_vn, s);
     std::vector<double> vs((size_t)g.nz, -(1.0 / p->rho_s_over_rho_n) * p->init_vn[2]);
     double mass = p->rho0 * (double)C;
@@ -421,13 +440,71 @@ int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, i
     return VLB_OK;
 }
 
+// One coupled step, replayed from a CUDA graph captured on first use for the
+// current buffer parities (the population buffers alternate every step; the
+// point buffers flip twice per step).  Capture needs a real stream, so the
+// legacy default stream and the timing mode launch the kernels directly.
+namespace {
+int size_class(int n) {
+    int c = 0;
+    while (n > 1) {
+        n >>= 1;
+        ++c;
+    }
+    return c;
+}
+
+bool step_graph(vlb_channel* ch) {
+    const int f = ch->cur_f, q = ch->cur_p;
+    const int cls = size_class(ch->n_hint);
+    if (ch->gexec[f][q] && ch->gclass[f][q] != cls) {
+        // the Biot-Savart grid was sized for another filament count: capture again
+        cudaGraphExecDestroy(ch->gexec[f][q]);
+        ch->gexec[f][q] = nullptr;
+    }
+    if (!ch->gexec[f][q]) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(ch->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        run_phases(ch, VLB_PHASE_ALL);
+        cudaError_t e = cudaStreamEndCapture(ch->stream, &graph);
+        ch->cur_f = f;  // the captured step has not run yet
+        ch->cur_p = q;
+        if (e != cudaSuccess || !graph) {
+            cudaGetLastError();
+            return false;
+        }
+        e = cudaGraphInstantiate(&ch->gexec[f][q], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ch->gexec[f][q] = nullptr;
+            return false;
+        }
+        ch->gclass[f][q] = cls;
+    }
+    if (cudaGraphLaunch(ch->gexec[f][q], ch->stream) != cudaSuccess) return false;
+    ch->cur_f ^= 1;  // the point buffers are back to q after remesh and reconnect
+    return true;
+}
+}  // namespace
+
 int vlb_step(vlb_channel* ch, int32_t nsteps) {
     if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
+    const bool use_graph = ch->graphs && !ch->timing && ch->stream != nullptr;
     for (int k = 0; k < nsteps; ++k) {
-        run_phases(ch, VLB_PHASE_ALL);
+        if (!(use_graph && step_graph(ch))) run_phases(ch, VLB_PHASE_ALL);
         ch->steps++;
     }
     return finish(ch);
+}
+
+int vlb_set_graphs(vlb_channel* ch, int32_t enable) {
+    if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
+    ch->graphs = enable != 0;
+    return VLB_OK;
 }
 
 int vlb_run_phases(vlb_channel* ch, int32_t mask) {
@@ -446,7 +523,7 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
     switch (which) {
         case VLB_FIELD_RHO: need = sizeof(float) * (size_t)C; break;
         case VLB_FIELD_U: case VLB_FIELD_FORCE: need = sizeof(float) * 3 * (size_t)C; break;
-        case VLB_FIELD_FSTAR: need = sizeof(float) * 19 * (size_t)C; break;
+        case VLB_FIELD_FSTAR: case VLB_FIELD_FDEV: need = sizeof(float) * 19 * (size_t)C; break;
         case VLB_FIELD_POS: case VLB_FIELD_VEL: need = sizeof(double) * 3 * (size_t)N; break;
         case VLB_FIELD_NEXT: need = sizeof(int) * (size_t)N; break;
         case VLB_FIELD_PLANE_VS: need = sizeof(double) * (size_t)ch->lp.g.nz; break;
@@ -461,8 +538,8 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
     if (which == VLB_FIELD_RHO || which == VLB_FIELD_U) {
         launch_moments(ch->lp, d.f[ch->cur_f], d.F, d.fmask, tmp, tmp + C, s);
         e = cudaMemcpyAsync(dst, which == VLB_FIELD_RHO ? tmp : tmp + C, need, cudaMemcpyDeviceToHost, s);
-    } else if (which == VLB_FIELD_FSTAR) {
-        launch_unshift(ch->lp, d.f[ch->cur_f], tmp, +1, s);
+    } else if (which == VLB_FIELD_FSTAR || which == VLB_FIELD_FDEV) {
+        launch_unshift(ch->lp, d.f[ch->cur_f], tmp, which == VLB_FIELD_FSTAR ? +1 : 0, s);
         e = cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, s);
     } else if (which == VLB_FIELD_FORCE) {
         e = cudaMemcpyAsync(dst, d.F, need, cudaMemcpyDeviceToHost, s);
@@ -480,7 +557,7 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
     } else if (which == VLB_FIELD_PLANE_VS) {
         e = cudaMemcpyAsync(dst, d.Vs, need, cudaMemcpyDeviceToHost, s);
     } else {
-        launch_line_length(ch->lp.g, d.pos[ch->cur_p], d.next[ch->cur_p], d.counters, ch->cap, d.dstats, s);
+        launch_line_length(ch->lp.g, d.pos[ch->cur_p], d.next[ch->cur_p], d.counters, ch->cap, d.line_part, d.dstats, s);
         rc = sync_counters(ch);
         if (rc) return rc;
         double* o = (double*)dst;
@@ -530,7 +607,7 @@ int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t byt
 int vlb_line_length(vlb_channel* ch, double* out) {
     if (!ch || !out) return fail(VLB_ERR_INVALID_ARG, "null argument");
     launch_line_length(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.next[ch->cur_p], ch->d.counters, ch->cap,
-                       ch->d.dstats, ch->stream);
+                       ch->d.line_part, ch->d.dstats, ch->stream);
     cudaMemcpyAsync(ch->h_dstats + DS_LINE, ch->d.dstats + DS_LINE, sizeof(double), cudaMemcpyDeviceToHost,
                     ch->stream);
     cudaError_t e = cudaStreamSynchronize(ch->stream);
@@ -567,10 +644,10 @@ int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches) {
 
 size_t vlb_biot_savart_scratch_bytes(int32_t n) {
     if (n < 1) n = 1;
-    const int ns = bs_nsplit(n, n);
+    const int ns = bs_splits(n);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     return up(sizeof(int) * CNT_COUNT) + up(sizeof(int) * (size_t)n) + up(sizeof(float4) * 3 * (size_t)n) +
-           up(sizeof(float) * 3 * (size_t)n * (size_t)ns);
+           up(sizeof(float) * 3 * (size_t)n * (size_t)ns) + up(sizeof(int) * (size_t)((n + BS_TPB - 1) / BS_TPB));
 }
 
 int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel, void* scratch,
@@ -587,7 +664,6 @@ int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next,
     for (int a = 0; a < 3; ++a) g.wall[a] = p->wall[a];
     g.ncell = (long long)g.nx * g.ny * g.nz;
     g.tnx = g.tny = g.tnz = 1;
-    const int ns = bs_nsplit(n, n);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     char* base = (char*)scratch;
     int* counters = (int*)base;
@@ -597,10 +673,12 @@ int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next,
     float4* seg = (float4*)base;
     base += up(sizeof(float4) * 3 * (size_t)n);
     float* bsp = (float*)base;
+    base += up(sizeof(float) * 3 * (size_t)n * (size_t)bs_splits(n));
+    int* tickets = (int*)base;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(tickets, 0, sizeof(int) * (size_t)((n + BS_TPB - 1) / BS_TPB), s);
     launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, s);
-    launch_biot_savart(g, p->kappa, seg, prev, counters, n, ns, bsp, s);
-    launch_bs_reduce(bsp, ns, n, n, vel, s);
+    launch_biot_savart(g, p->kappa, seg, prev, counters, tickets, n, n, bsp, vel, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "Biot-Savart launch");
     return VLB_OK;

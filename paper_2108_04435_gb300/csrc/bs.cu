@@ -76,95 +76,141 @@ __device__ __forceinline__ void issue_tile(float4* dst, const float4* seg, int j
 }
 
 template <bool PERIODIC>
+__device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, int jb, int self, int pi, float rhx,
+                                        float rhy, float rhz, float rlx, float rly, float rlz, const BoxF& box,
+                                        float kq, float& vx, float& vy, float& vz) {
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+        const float4 A = T[3 * k], B = T[3 * k + 1], D = T[3 * k + 2];
+        float r1x = (A.x - rhx) + (A.w - rlx);
+        float r1y = (A.y - rhy) + (B.x - rly);
+        float r1z = (A.z - rhz) + (B.y - rlz);
+        if (PERIODIC) {
+            r1x -= box.Lx * rintf(r1x * box.iLx);
+            r1y -= box.Ly * rintf(r1y * box.iLy);
+            r1z -= box.Lz * rintf(r1z * box.iLz);
+        }
+        const float r2x = r1x + B.z, r2y = r1y + B.w, r2z = r1z + D.x;
+        const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
+        const float b2 = r2x * r2x + r2y * r2y + r2z * r2z;
+        const float ia = rsqrtf(a2), ib = rsqrtf(b2);
+        const float la = a2 * ia, lb = b2 * ib;
+        const float ab = la * lb;
+        const float dot = r1x * r2x + r1y * r2y + r1z * r2z;
+        const float s = ab + dot;
+        const float fac = kq * (la + lb) * __frcp_rn(ab * s);
+        const int j = jb + k;
+        const bool use = (j != self) & (j != pi) & (s > 1e-6f * ab);
+        const float c = use ? fac : 0.f;
+        vx += c * (r1y * r2z - r1z * r2y);
+        vy += c * (r1z * r2x - r1x * r2z);
+        vz += c * (r1x * r2y - r1y * r2x);
+    }
+}
+
+// Work items are (target tile of BS_TPB points, source split).  Block b
+// starts with item b and takes further items from a device counter (reset by
+// the stage-geometry kernel), so the grid is fixed and no item depends on a
+// host-side estimate of N.  With several splits, each item stores its partial
+// sums and the last item of a target tile adds them in split order (fixed,
+// hence deterministic) into vel; with one split the item writes vel directly.
+template <bool PERIODIC>
 __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev,
-                                                        const int* __restrict__ counters, int cap, BoxF box, float kq,
-                                                        float* __restrict__ out, int* __restrict__ status) {
+                                                        int* __restrict__ counters, int* __restrict__ tile_ticket,
+                                                        int cap, BoxF box, float kq, float* __restrict__ part,
+                                                        float* __restrict__ vel) {
     __shared__ __align__(128) float4 tile[2][BS_TILE * 3];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_item, s_last;
     const int N = counters[CNT_N];
-    const int i0 = blockIdx.x * BS_TPB;
-    if (i0 >= N) return;
-    const int nsplit = gridDim.y, split = blockIdx.y;
-    const int chunk = (N + nsplit - 1) / nsplit;
-    const int j0 = split * chunk;
-    const int j1 = min(N, j0 + chunk);
-    const int i = i0 + threadIdx.x;
-    const bool valid = i < N;
-    float rhx = 0.f, rhy = 0.f, rhz = 0.f, rlx = 0.f, rly = 0.f, rlz = 0.f;
-    int self = -1, pi = -1;
-    if (valid) {
-        const float4 a = seg[3LL * i], b = seg[3LL * i + 1];
-        rhx = a.x; rhy = a.y; rhz = a.z; rlx = a.w; rly = b.x; rlz = b.y;
-        self = i;
-        pi = prev[i];
-    }
-    float vx = 0.f, vy = 0.f, vz = 0.f;
-    const int ntiles = j1 > j0 ? (j1 - j0 + BS_TILE - 1) / BS_TILE : 0;
+    if (N <= 0) return;
+    const int ns = bs_splits(N);
+    const int ntb = (N + BS_TPB - 1) / BS_TPB;
+    const int nitems = ntb * ns;
+    const int chunk = (N + ns - 1) / ns;
+    if ((int)blockIdx.x >= nitems) return;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && ntiles > 0) issue_tile(tile[0], seg, j0, min(BS_TILE, j1 - j0), &bar[0]);
-    int consumed = 0;
-    bool timed_out = false;
-    for (int t = 0; t < ntiles; ++t) {
-        const int b = t & 1;
-        if (threadIdx.x == 0 && t + 1 < ntiles) {
-            const int jn = j0 + (t + 1) * BS_TILE;
-            issue_tile(tile[b ^ 1], seg, jn, min(BS_TILE, j1 - jn), &bar[b ^ 1]);
+    uint32_t used = 0;  // tiles this block has consumed: buffer = used & 1, phase = (used >> 1) & 1
+    int item = blockIdx.x;
+    while (true) {
+        __syncthreads();
+        const int tb = item % ntb, split = item / ntb;
+        const int i = tb * BS_TPB + threadIdx.x;
+        const bool valid = i < N;
+        const int j0 = split * chunk;
+        const int j1 = min(N, j0 + chunk);
+        float rhx = 0.f, rhy = 0.f, rhz = 0.f, rlx = 0.f, rly = 0.f, rlz = 0.f;
+        int self = -1, pi = -1;
+        if (valid) {
+            const float4 a = seg[3LL * i], b = seg[3LL * i + 1];
+            rhx = a.x; rhy = a.y; rhz = a.z; rlx = a.w; rly = b.x; rlz = b.y;
+            self = i;
+            pi = prev[i];
         }
-        const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((t >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            timed_out = true;
-            break;
-        }
-        consumed = t + 1;
-        const int jb = j0 + t * BS_TILE;
-        const int cnt = min(BS_TILE, j1 - jb);
-        const float4* T = tile[b];
-#pragma unroll 4
-        for (int k = 0; k < cnt; ++k) {
-            const float4 A = T[3 * k], B = T[3 * k + 1], D = T[3 * k + 2];
-            float r1x = (A.x - rhx) + (A.w - rlx);
-            float r1y = (A.y - rhy) + (B.x - rly);
-            float r1z = (A.z - rhz) + (B.y - rlz);
-            if (PERIODIC) {
-                r1x -= box.Lx * rintf(r1x * box.iLx);
-                r1y -= box.Ly * rintf(r1y * box.iLy);
-                r1z -= box.Lz * rintf(r1z * box.iLz);
+        float vx = 0.f, vy = 0.f, vz = 0.f;
+        const int ntiles = j1 > j0 ? (j1 - j0 + BS_TILE - 1) / BS_TILE : 0;
+        if (threadIdx.x == 0 && ntiles > 0) issue_tile(tile[used & 1], seg, j0, min(BS_TILE, j1 - j0), &bar[used & 1]);
+        for (int t = 0; t < ntiles; ++t) {
+            const uint32_t u = used + (uint32_t)t;
+            const int b = (int)(u & 1u);
+            if (threadIdx.x == 0 && t + 1 < ntiles) {
+                const int jn = j0 + (t + 1) * BS_TILE;
+                issue_tile(tile[b ^ 1], seg, jn, min(BS_TILE, j1 - jn), &bar[b ^ 1]);
             }
-            const float r2x = r1x + B.z, r2y = r1y + B.w, r2z = r1z + D.x;
-            const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
-            const float b2 = r2x * r2x + r2y * r2y + r2z * r2z;
-            const float ia = rsqrtf(a2), ib = rsqrtf(b2);
-            const float la = a2 * ia, lb = b2 * ib;
-            const float ab = la * lb;
-            const float dot = r1x * r2x + r1y * r2y + r1z * r2z;
-            const float s = ab + dot;
-            const float fac = kq * (la + lb) * __frcp_rn(ab * s);
-            const int j = jb + k;
-            const bool use = (j != self) & (j != pi) & (s > 1e-6f * ab);
-            const float c = use ? fac : 0.f;
-            vx += c * (r1y * r2z - r1z * r2y);
-            vy += c * (r1z * r2x - r1x * r2z);
-            vz += c * (r1x * r2y - r1y * r2x);
+            const bool ok = mbar_wait_bounded(&bar[b], (u >> 1) & 1u);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicOr(&counters[CNT_STATUS], ST_TIMEOUT);
+                    // let a copy still in flight land before the block's shared memory goes away
+                    if (t + 1 < ntiles) mbar_wait_bounded(&bar[b ^ 1], ((u + 1u) >> 1) & 1u);
+                }
+                return;
+            }
+            const int jb = j0 + t * BS_TILE;
+            bs_tile<PERIODIC>(tile[b], min(BS_TILE, j1 - jb), jb, self, pi, rhx, rhy, rhz, rlx, rly, rlz, box, kq, vx,
+                              vy, vz);
+            __syncthreads();
+        }
+        used += (uint32_t)ntiles;
+        if (ns == 1) {
+            if (valid) {
+                vel[i] = vx;
+                vel[(long long)cap + i] = vy;
+                vel[2LL * cap + i] = vz;
+            }
+        } else {
+            if (valid) {
+                part[((long long)split * 3 + 0) * cap + i] = vx;
+                part[((long long)split * 3 + 1) * cap + i] = vy;
+                part[((long long)split * 3 + 2) * cap + i] = vz;
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = atomicAdd(&tile_ticket[tb], 1) == ns - 1;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                if (valid) {
+                    float a[3] = {0.f, 0.f, 0.f};
+                    for (int m = 0; m < ns; ++m)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) a[k] += __ldcg(&part[((long long)m * 3 + k) * cap + i]);
+                    vel[i] = a[0];
+                    vel[(long long)cap + i] = a[1];
+                    vel[2LL * cap + i] = a[2];
+                }
+                if (threadIdx.x == 0) tile_ticket[tb] = 0;
+            }
         }
         __syncthreads();
-    }
-    if (timed_out) {
-        if (threadIdx.x == 0) {
-            atomicOr(status, ST_TIMEOUT);
-            // let copies still in flight land before the block's shared memory goes away
-            for (int t = consumed; t < min(ntiles, consumed + 2); ++t) mbar_wait_bounded(&bar[t & 1], (uint32_t)((t >> 1) & 1));
-        }
-        return;
-    }
-    if (valid) {
-        out[((long long)split * 3 + 0) * cap + i] = vx;
-        out[((long long)split * 3 + 1) * cap + i] = vy;
-        out[((long long)split * 3 + 2) * cap + i] = vz;
+        if (threadIdx.x == 0) s_item = (int)gridDim.x + atomicAdd(&counters[CNT_BSWORK], 1);
+        __syncthreads();
+        item = s_item;
+        if (item >= nitems) break;
     }
 }
 
@@ -175,6 +221,7 @@ __global__ void k_bs_prep(Grid g, const double* __restrict__ pos, const int* __r
     if (i == 0) {
         counters[CNT_N] = n;
         counters[CNT_STATUS] = 0;
+        counters[CNT_BSWORK] = 0;
     }
     if (i >= n) return;
     const int q = next[i];
@@ -198,16 +245,6 @@ __global__ void k_bs_prep(Grid g, const double* __restrict__ pos, const int* __r
     seg[3LL * i + 2] = make_float4(d[2], 0.f, 0.f, 0.f);
 }
 
-__global__ void k_bs_reduce(const float* __restrict__ bsp, int nsplit, int n, int cap, float* __restrict__ vel) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int k = 0; k < 3; ++k) {
-        float s = 0.f;
-        for (int m = 0; m < nsplit; ++m) s += bsp[((long long)m * 3 + k) * cap + i];
-        vel[(long long)k * n + i] = s;
-    }
-}
-
 BoxF make_box(const Grid& g) {
     BoxF b;
     b.Lx = g.wall[0] ? 0.f : (float)g.nx;
@@ -221,41 +258,35 @@ BoxF make_box(const Grid& g) {
 
 }  // namespace
 
-// Source splits for a filament set of about n points: enough blocks to fill
-// the GPU (~4 per SM on 152 SMs), with at least 64 segments per split.
-int bs_nsplit(int n_hint, int cap) {
-    const int n = n_hint > 0 ? n_hint : 1;
-    const int tb = (n + BS_TPB - 1) / BS_TPB;
-    int ns = (4 * 152 + tb - 1) / tb;
-    const int by_chunk = (n + 63) / 64;
-    if (ns > by_chunk) ns = by_chunk;
-    if (ns < 1) ns = 1;
-    if (ns > MAX_SPLIT) ns = MAX_SPLIT;
-    (void)cap;
-    return ns;
+int bs_max_splits(int cap) {
+    int m = 1;
+    for (int n = 1; n <= cap; n += (n < 8192 ? 1 : 128)) {
+        const int k = bs_splits(n);
+        if (k > m) m = k;
+    }
+    return m;
 }
 
-void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters, int cap,
-                        int nsplit, float* bsp, cudaStream_t s) {
+void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
+                        int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s) {
     if (cap <= 0) return;
-    dim3 grid((cap + BS_TPB - 1) / BS_TPB, nsplit);
+    // enough blocks for every item of about n_hint points (at most 6 per SM);
+    // more points than that are still covered by the blocks' item loop
+    const int n = n_hint > 0 ? (n_hint < cap ? n_hint : cap) : 1;
+    const int items = ((n + BS_TPB - 1) / BS_TPB) * bs_splits(n);
+    const int grid = items < 6 * 152 ? items : 6 * 152;
     const float kq = (float)(kappa / (4.0 * 3.14159265358979323846));
     const BoxF box = make_box(g);
-    int* status = const_cast<int*>(counters) + CNT_STATUS;
+    int* cnt = const_cast<int*>(counters);
     if (g.wall[0] && g.wall[1] && g.wall[2])
-        k_biot_savart<false><<<grid, BS_TPB, 0, s>>>(seg, prev, counters, cap, box, kq, bsp, status);
+        k_biot_savart<false><<<grid, BS_TPB, 0, s>>>(seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
     else
-        k_biot_savart<true><<<grid, BS_TPB, 0, s>>>(seg, prev, counters, cap, box, kq, bsp, status);
+        k_biot_savart<true><<<grid, BS_TPB, 0, s>>>(seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
 }
 
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
                                int* counters, cudaStream_t s) {
     k_bs_prep<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(g, pos, next, n, prev, seg, counters);
-}
-
-void launch_bs_reduce(const float* bsp, int nsplit, int n, int cap, float* vel, cudaStream_t s) {
-    if (n <= 0) return;
-    k_bs_reduce<<<(n + 255) / 256, 256, 0, s>>>(bsp, nsplit, n, cap, vel);
 }
 
 }  // namespace vlb

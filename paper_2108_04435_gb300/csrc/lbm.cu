@@ -89,9 +89,59 @@ __device__ __forceinline__ float warp_reduce(float v) {
     return v;
 }
 
+// Source index of the population arriving along c_i (pull form of
+// Eq. 14d): 32-bit, from per-thread row/plane offsets (the host limits the
+// lattice to 19 C < 2^31).  A link leaving through a wall is replaced by the
+// opposite population of the same cell (halfway bounce-back); the moving-wall
+// term of the z faces is added by the caller.
+struct PullIdx {
+    int xo[3], yo[3], zo[3];  // offsets for c = -1, 0, +1 (index c + 1)
+    bool ox[3], oy[3], oz[3]; // source outside a wall
+};
+
+template <bool WX, bool WY, bool WZ>
+__device__ __forceinline__ void pull_index(const LbmParams& P, int x, int y, int z, PullIdx& q) {
+    const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz, nxy = nx * ny;
+    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+    // c = +1 pulls from x - 1, c = -1 from x + 1
+    q.ox[0] = q.ox[1] = q.ox[2] = false;
+    q.oy[0] = q.oy[1] = q.oy[2] = false;
+    q.oz[0] = q.oz[1] = q.oz[2] = false;
+    if (xm < 0) { if (WX) q.ox[2] = true; else xm += nx; }
+    if (xp >= nx) { if (WX) q.ox[0] = true; else xp -= nx; }
+    if (ym < 0) { if (WY) q.oy[2] = true; else ym += ny; }
+    if (yp >= ny) { if (WY) q.oy[0] = true; else yp -= ny; }
+    if (zm < 0) { if (WZ) q.oz[2] = true; else zm += nz; }
+    if (zp >= nz) { if (WZ) q.oz[0] = true; else zp -= nz; }
+    q.xo[0] = xp; q.xo[1] = x; q.xo[2] = xm;
+    q.yo[0] = yp * nx; q.yo[1] = y * nx; q.yo[2] = ym * nx;
+    q.zo[0] = zp * nxy; q.zo[1] = z * nxy; q.zo[2] = zm * nxy;
+}
+
+template <bool WX, bool WY, bool WZ>
+__device__ __forceinline__ void pull_fast(const float* __restrict__ f, const LbmParams& P, const PullIdx& q, int cell,
+                                          float g[19]) {
+    const int C = (int)P.g.ncell;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        int src = i * C + q.zo[CZ(i) + 1] + q.yo[CY(i) + 1] + q.xo[CX(i) + 1];
+        bool out = false, outz = false;
+        if (WX && CX(i) != 0) out = out || q.ox[CX(i) + 1];
+        if (WY && CY(i) != 0) out = out || q.oy[CY(i) + 1];
+        if (WZ && CZ(i) != 0) { outz = q.oz[CZ(i) + 1]; out = out || outz; }
+        if (WX || WY || WZ) src = out ? opp(i) * C + cell : src;
+        float v = __ldg(&f[src]);
+        if (WZ && CZ(i) != 0) v += outz ? 6.f * wgt(i) * P.rho0 * (float)CZ(i) * P.heater : 0.f;
+        g[i] = v;
+    }
+}
+
 // K1: one lattice pass.  One thread per cell, one block per 256 consecutive
 // (x, y) cells of one z plane, so every population array is read in coalesced
-// rows (the +-x shift of the pull is absorbed by L1) and written aligned.
+// rows (the +-x shift of the pull is absorbed by L1/L2) and written aligned.
+// The collision works on opposite pairs (i, i'): with c_i' = -c_i the even
+// parts of f^eq (Eq. 7) and of F_i (Eq. 13) are shared and the odd parts
+// change sign.
 template <bool WX, bool WY, bool WZ>
 __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict__ fin, float* __restrict__ fout,
                                                         const float* __restrict__ F, float* __restrict__ U,
@@ -99,17 +149,21 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
                                                         const uint8_t* __restrict__ umask, double* __restrict__ part,
                                                         LbmParams P) {
     const int nx = P.g.nx, ny = P.g.ny;
-    const long long C = P.g.ncell;
+    const int C = (int)P.g.ncell;
     const int z = blockIdx.y;
     const int xy = blockIdx.x * LBM_BLOCK + threadIdx.x;
     float s_drho = 0.f, s_uz = 0.f, s_u2 = 0.f;
     if (xy < nx * ny) {
         const int y = xy / nx, x = xy - y * nx;
-        const long long cell = (long long)z * nx * ny + xy;
+        const int cell = z * nx * ny + xy;
         float g[19];
-        pull<WX, WY, WZ>(fin, P, x, y, z, cell, g);
+        {
+            PullIdx q;
+            pull_index<WX, WY, WZ>(P, x, y, z, q);
+            pull_fast<WX, WY, WZ>(fin, P, q, cell, g);
+        }
         // Eqs. 5-6 with the half-force shift: rho = rho0 + sum g, j = sum c g
-        float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        float drho = P.dr0, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             drho += g[i];
@@ -117,7 +171,6 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
             if (CY(i)) jy += (float)CY(i) * g[i];
             if (CZ(i)) jz += (float)CZ(i) * g[i];
         }
-        drho += P.dr0;
         const int tile = tile_of(P.g, x, y, z);
         const bool factive = fmask[tile] != 0;
         float Fx = P.body[0], Fy = P.body[1], Fz = P.body[2];
@@ -136,25 +189,44 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
             U[C + cell] = uy;
             U[2 * C + cell] = uz;
         }
+        const float om = P.omega;
+        const float A = drho - 1.5f * rho * usq;  // even part of f^eq/w - rho0 without the (c.u)^2 term
+        const float B3 = 3.f * rho, B45 = 4.5f * rho;
         const float uF = ux * Fx + uy * Fy + uz * Fz;
         const bool pinned = P.pin_on && z == 0;
+        // rest population
+        {
+            float geq = wgt(0) * A + P.dw[0];
+            float out = g[0] + om * (geq - g[0]);
+            if (force) out += P.pref * wgt(0) * (-3.f * uF);
+            if (pinned) out = wgt(0) * (drho - 1.5f * rho * P.pin * P.pin) + P.dw[0];
+            fout[cell] = out;
+        }
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
+        for (int i = 1; i < 19; i += 2) {
+            const int j = i + 1;  // opposite of i
             const float cu = (float)CX(i) * ux + (float)CY(i) * uy + (float)CZ(i) * uz;
-            // Eq. 7 minus w_i rho0
-            const float geq = wgt(i) * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * usq)) + P.dw[wclass(i)];
-            // Eq. 14b: BGK relaxation (Eq. 8) of the streamed population
-            float out = g[i] - P.omega * (g[i] - geq);
+            const float w = wgt(i);
+            const float sym = w * (A + B45 * cu * cu) + P.dw[wclass(i)];
+            const float asym = w * B3 * cu;
+            float oi = g[i] + om * (sym + asym - g[i]);
+            float oj = g[j] + om * (sym - asym - g[j]);
             if (force) {
-                // Eq. 13 (e_i read as c_i), applied as two halves (Eqs. 14a, 14c)
                 const float cF = (float)CX(i) * Fx + (float)CY(i) * Fy + (float)CZ(i) * Fz;
-                out += P.pref * wgt(i) * (3.f * (cF - uF) + 9.f * cu * cF);
+                const float fs = P.pref * w * (9.f * cu * cF - 3.f * uF);
+                const float fa = P.pref * w * 3.f * cF;
+                oi += fs + fa;
+                oj += fs - fa;
             }
             if (pinned) {
                 const float cp = (float)CZ(i) * P.pin;
-                out = wgt(i) * (drho + rho * (3.f * cp + 4.5f * cp * cp - 1.5f * P.pin * P.pin)) + P.dw[wclass(i)];
+                const float ps = w * (drho + rho * (4.5f * cp * cp - 1.5f * P.pin * P.pin)) + P.dw[wclass(i)];
+                const float pa = w * B3 * cp;
+                oi = ps + pa;
+                oj = ps - pa;
             }
-            fout[(long long)i * C + cell] = out;
+            fout[i * C + cell] = oi;
+            fout[j * C + cell] = oj;
         }
         s_drho = drho;
         s_uz = uz;
@@ -184,6 +256,83 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
         o[0] = a;
         o[1] = b;
         o[2] = m;
+    }
+}
+
+// Eq. 18 per z plane from the stream-collide block partials, with the mass
+// and the Mach limit of Sec. II.B (|u|/c_s < 0.05).  One warp per plane
+// (lane-strided loads, fixed shuffle tree); the last block to finish reduces
+// the planes in a fixed order.  FP64 work is spread over many SMs because
+// its per-SM rate is low on this GPU.
+__global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ part, int bpp, LbmParams P) {
+    __shared__ double s_tot[256], s_mass[256], s_max[256];
+    __shared__ int s_last;
+    const int nz = P.g.nz;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int pz = blockIdx.x * 8 + wid;
+    if (pz < nz) {
+        double a = 0.0, b = 0.0, m = 0.0;
+        for (int k = lane; k < bpp; k += 32) {
+            const double* o = part + ((long long)pz * bpp + k) * 3;
+            a += o[0];
+            b += o[1];
+            m = fmax(m, o[2]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, off);
+            b += __shfl_xor_sync(0xffffffffu, b, off);
+            m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        }
+        if (lane == 0) {
+            double* pl = P.plane + 3LL * pz;
+            pl[0] = a;
+            pl[1] = b;
+            pl[2] = m;
+            if (P.g.wall[2]) P.Vs[pz] = -P.inv_ratio * (b / ((double)P.g.nx * (double)P.g.ny));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&P.counters[CNT_PLANES], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double tot = 0.0, mass = 0.0, mx = 0.0;
+    for (int q = threadIdx.x; q < nz; q += blockDim.x) {
+        const double* pl = P.plane + 3LL * q;
+        mass += __ldcg(&pl[0]);
+        tot += __ldcg(&pl[1]);
+        mx = fmax(mx, __ldcg(&pl[2]));
+    }
+    s_tot[threadIdx.x] = tot;
+    s_mass[threadIdx.x] = mass;
+    s_max[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s_tot[threadIdx.x] += s_tot[threadIdx.x + o];
+            s_mass[threadIdx.x] += s_mass[threadIdx.x + o];
+            s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (!P.g.wall[2]) {
+        const double v = -P.inv_ratio * (s_tot[0] / (double)P.g.ncell);
+        for (int q = threadIdx.x; q < nz; q += blockDim.x) P.Vs[q] = v;
+    }
+    if (threadIdx.x == 0) {
+        const double m = s_max[0];
+        const double mach = sqrt(3.0 * m);
+        P.dstats[DS_MASS] = (double)P.rho0 * (double)P.g.ncell + s_mass[0];
+        P.dstats[DS_MAXMACH] = mach;
+        int st = 0;
+        if (!(mach < 0.05)) st |= ST_MACH;
+        if (!isfinite(m) || !isfinite(s_mass[0])) st |= ST_NAN;
+        if (st) atomicOr(&P.counters[CNT_STATUS], st);
+        P.counters[CNT_PLANES] = 0;
     }
 }
 
@@ -238,7 +387,8 @@ __global__ void k_lbm_init(float* __restrict__ f, float* __restrict__ U, LbmPara
     U[2 * C + c] = uz;
 }
 
-// direction +1: out = g + w_i rho0 (export); -1: out = f - w_i rho0 (import)
+// direction +1: out = g + s_i (populations f); -1: out = f - s_i (import);
+// 0: out = g - dw_i = f - w_i rho0 (deviation from the rest state)
 __global__ void k_unshift(const float* __restrict__ in, float* __restrict__ out, LbmParams P, int direction) {
     const long long C = P.g.ncell;
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -246,55 +396,8 @@ __global__ void k_unshift(const float* __restrict__ in, float* __restrict__ out,
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const float s = wgt(i) * P.rho0;
-        out[(long long)i * C + c] = direction > 0 ? in[(long long)i * C + c] + s : in[(long long)i * C + c] - s;
-    }
-}
-
-// Eq. 18 per z plane from the block partials, in a fixed order; mass and the
-// Mach limit of Sec. II.B (|u|/c_s < 0.05) are checked here as well.
-__global__ void k_plane_vs(const double* __restrict__ part, int nz, int bpp, double area, double ncell, double rho0,
-                           double inv_ratio, int periodic, double* __restrict__ Vs, double* __restrict__ dstats,
-                           int* __restrict__ counters) {
-    __shared__ double s_tot[256], s_mass[256], s_max[256];
-    double tot = 0.0, mass = 0.0, mx = 0.0;
-    for (int p = threadIdx.x; p < nz; p += blockDim.x) {
-        double su = 0.0, sr = 0.0, m = 0.0;
-        for (int b = 0; b < bpp; ++b) {
-            const double* o = part + ((long long)p * bpp + b) * 3;
-            sr += o[0];
-            su += o[1];
-            m = fmax(m, o[2]);
-        }
-        if (!periodic) Vs[p] = -inv_ratio * (su / area);
-        tot += su;
-        mass += sr;
-        mx = fmax(mx, m);
-    }
-    s_tot[threadIdx.x] = tot;
-    s_mass[threadIdx.x] = mass;
-    s_max[threadIdx.x] = mx;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            s_tot[threadIdx.x] += s_tot[threadIdx.x + o];
-            s_mass[threadIdx.x] += s_mass[threadIdx.x + o];
-            s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
-        }
-        __syncthreads();
-    }
-    if (periodic) {
-        const double v = -inv_ratio * (s_tot[0] / ncell);
-        for (int p = threadIdx.x; p < nz; p += blockDim.x) Vs[p] = v;
-    }
-    if (threadIdx.x == 0) {
-        const double m = s_max[0];
-        const double mach = sqrt(3.0 * m);
-        dstats[DS_MASS] = rho0 * ncell + s_mass[0];
-        dstats[DS_MAXMACH] = mach;
-        int st = 0;
-        if (!(mach < 0.05)) st |= ST_MACH;
-        if (!isfinite(m) || !isfinite(s_mass[0])) st |= ST_NAN;
-        if (st) atomicOr(&counters[CNT_STATUS], st);
+        const float v = in[(long long)i * C + c];
+        out[(long long)i * C + c] = direction > 0 ? v + s : (direction < 0 ? v - s : v - P.dw[wclass(i)]);
     }
 }
 
@@ -395,12 +498,9 @@ void launch_unshift(const LbmParams& P, const float* in, float* out, int directi
     k_unshift<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(in, out, P, direction);
 }
 
-void launch_plane_vs(const LbmParams& P, const double* part, double ratio, double* Vs, double* dstats, int* counters,
-                     cudaStream_t s) {
+void launch_plane_vs(const LbmParams& P, const double* part, cudaStream_t s) {
     const int bpp = (P.g.nx * P.g.ny + LBM_BLOCK - 1) / LBM_BLOCK;
-    const double area = (double)P.g.nx * (double)P.g.ny;
-    k_plane_vs<<<1, 256, 0, s>>>(part, P.g.nz, bpp, area, (double)P.g.ncell, (double)P.rho0, 1.0 / ratio,
-                                 P.g.wall[2] ? 0 : 1, Vs, dstats, counters);
+    k_plane_vs<<<(P.g.nz + 7) / 8, 256, 0, s>>>(part, bpp, P);
 }
 
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,

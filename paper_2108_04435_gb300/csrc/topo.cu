@@ -88,6 +88,30 @@ __device__ int block_exclusive_scan(int v, int* total) {
     return base + x - v;
 }
 
+// FP64 geometry for the remeshing decisions: segment length l+ = |s_q - s_i|
+// and the three-point curvature s'' = 2 (l- b - l+ a) / (l+ l- (l+ + l-)) on
+// the non-uniform arc-length grid (a = s_i - s_p, b = s_q - s_i).
+__global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double* __restrict__ s,
+                                                       const int* __restrict__ next, const int* __restrict__ prev,
+                                                       const int* __restrict__ counters, int cap,
+                                                       double* __restrict__ spp, double* __restrict__ seglen) {
+    const int N = counters[CNT_N];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int p = prev[i], q = next[i];
+    double a[3], b[3];
+    for (int k = 0; k < 3; ++k) {
+        const double si = s[(long long)k * cap + i];
+        a[k] = min_image(P.g, k, si - s[(long long)k * cap + p]);
+        b[k] = min_image(P.g, k, s[(long long)k * cap + q] - si);
+    }
+    const double lm = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double lp = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    const double den = lp * lm * (lp + lm);
+    for (int k = 0; k < 3; ++k) spp[(long long)k * cap + i] = 2.0 * (lm * b[k] - lp * a[k]) / den;
+    seglen[i] = lp;
+}
+
 // ------------------------------------------------------------------ remesh
 
 __global__ void k_remesh_flags(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
@@ -105,16 +129,88 @@ __global__ void k_remesh_flags(VfmParams P, const double* __restrict__ pos, cons
     flags[i] = (uint8_t)((split ? 1 : 0) | (cand ? 2 : 0));
 }
 
-// One block: ranks of the split segments (ascending i), removals, the new
-// points' positions and the successor array of the remeshed set.
-__global__ void __launch_bounds__(1024) k_remesh_apply(VfmParams P, double* __restrict__ pos,
-                                                        const int* __restrict__ next, const int* __restrict__ prev,
-                                                        const double* __restrict__ spp,
-                                                        const double* __restrict__ seglen,
-                                                        const uint8_t* __restrict__ flags, int* __restrict__ nnext,
-                                                        uint8_t* __restrict__ alive, int* __restrict__ counters,
-                                                        double* __restrict__ dstats, int cap) {
-    __shared__ int s_removed[1024];
+// Points of loops with fewer than five points (succ^k(i) == i for k <= 4)
+// die; one block, strided over [0, T).  Returns this thread's count.
+__device__ int block_small_loops(const int* __restrict__ succ, uint8_t* __restrict__ alive, int T,
+                                 int* __restrict__ counters) {
+    int dead = 0;
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+        if (!alive[k]) continue;
+        int j = k;
+        for (int s = 1; s <= 4; ++s) {
+            j = succ[j];
+            if ((unsigned)j >= (unsigned)T) {
+                atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
+                break;
+            }
+            if (j == k) {
+                alive[k] = 0;
+                ++dead;
+                break;
+            }
+        }
+    }
+    return dead;
+}
+
+// One block: stable compaction of the alive points of [0, T) into the other
+// point buffer, successor indices renumbered, predecessors rebuilt.
+__device__ void block_compact(const double* __restrict__ pin, const int* __restrict__ succ,
+                              const uint8_t* __restrict__ alive, int T, int* __restrict__ newidx,
+                              double* __restrict__ pout, int* __restrict__ nout, int* __restrict__ pvout,
+                              int* __restrict__ counters, int cap) {
+    const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int b0 = min(T, (int)threadIdx.x * per);
+    const int b1 = min(T, b0 + per);
+    int mine = 0;
+    for (int k = b0; k < b1; ++k) mine += alive[k] ? 1 : 0;
+    int M = 0;
+    int base = block_exclusive_scan(mine, &M);
+    for (int k = b0; k < b1; ++k) newidx[k] = alive[k] ? base++ : -1;
+    __syncthreads();
+    for (int k = b0; k < b1; ++k) {
+        if (!alive[k]) continue;
+        const int n = newidx[k];
+        for (int c = 0; c < 3; ++c) pout[(long long)c * cap + n] = pin[(long long)c * cap + k];
+        const int sk = succ[k];
+        const int sn = (unsigned)sk < (unsigned)T ? newidx[sk] : -1;
+        if (sn < 0) {
+            atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
+            continue;
+        }
+        nout[n] = sn;
+        pvout[sn] = n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) counters[CNT_N] = M;
+}
+
+__device__ int block_sum(int v) {
+    __shared__ int s_red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    int t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// One block finishes the remesh: ranks of the split segments (ascending i),
+// removals, the new points' positions and successors, small-loop deletion and
+// the compaction into the other point buffer.
+__global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __restrict__ pos,
+                                                         const int* __restrict__ next, const int* __restrict__ prev,
+                                                         const double* __restrict__ spp,
+                                                         const double* __restrict__ seglen,
+                                                         const uint8_t* __restrict__ flags, int* __restrict__ nnext,
+                                                         uint8_t* __restrict__ alive, int* __restrict__ newidx,
+                                                         double* __restrict__ pout, int* __restrict__ nout,
+                                                         int* __restrict__ pvout, int* __restrict__ counters,
+                                                         double* __restrict__ dstats, int cap) {
     const int N = counters[CNT_N];
     const int per = (N + (int)blockDim.x - 1) / (int)blockDim.x;
     const int b0 = min(N, (int)threadIdx.x * per);
@@ -170,75 +266,18 @@ __global__ void __launch_bounds__(1024) k_remesh_apply(VfmParams P, double* __re
         }
         if (fi & 1) ++running;
     }
-    s_removed[threadIdx.x] = removed;
+    const int T = N + S;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) s_removed[threadIdx.x] += s_removed[threadIdx.x + o];
-        __syncthreads();
-    }
+    const int dead = block_small_loops(nnext, alive, T, counters);
+    const int removed_all = block_sum(removed);
+    const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) {
-        counters[CNT_TOTAL] = N + S;
-        counters[CNT_SMALL] = 0;
         dstats[DS_SPLITS] += (double)S;
-        dstats[DS_MERGES] += (double)s_removed[0];
+        dstats[DS_MERGES] += (double)removed_all;
+        dstats[DS_SMALL] += (double)dead_all;
     }
-}
-
-// Points of loops with fewer than five points (succ^k(i) == i for k <= 4) die.
-__global__ void k_small_loops(const int* __restrict__ succ, uint8_t* __restrict__ alive, int* __restrict__ counters) {
-    const int T = counters[CNT_TOTAL];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= T || !alive[k]) return;
-    int j = k;
-    for (int s = 1; s <= 4; ++s) {
-        j = succ[j];
-        if ((unsigned)j >= (unsigned)T) {
-            atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
-            return;
-        }
-        if (j == k) {
-            alive[k] = 0;
-            atomicAdd(&counters[CNT_SMALL], 1);
-            return;
-        }
-    }
-}
-
-// One block: stable compaction of the alive points of [0, total) into the
-// other point buffer, successor indices renumbered, predecessors rebuilt.
-__global__ void __launch_bounds__(1024) k_compact(const double* __restrict__ pin, const int* __restrict__ succ,
-                                                   const uint8_t* __restrict__ alive, int* __restrict__ newidx,
-                                                   double* __restrict__ pout, int* __restrict__ nout,
-                                                   int* __restrict__ pvout, int* __restrict__ counters,
-                                                   double* __restrict__ dstats, int cap) {
-    const int T = counters[CNT_TOTAL];
-    const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int b0 = min(T, (int)threadIdx.x * per);
-    const int b1 = min(T, b0 + per);
-    int mine = 0;
-    for (int k = b0; k < b1; ++k) mine += alive[k] ? 1 : 0;
-    int M = 0;
-    int base = block_exclusive_scan(mine, &M);
-    for (int k = b0; k < b1; ++k) newidx[k] = alive[k] ? base++ : -1;
     __syncthreads();
-    for (int k = b0; k < b1; ++k) {
-        if (!alive[k]) continue;
-        const int n = newidx[k];
-        for (int c = 0; c < 3; ++c) pout[(long long)c * cap + n] = pin[(long long)c * cap + k];
-        const int sk = succ[k];
-        const int s = (unsigned)sk < (unsigned)T ? newidx[sk] : -1;
-        if (s < 0) {
-            atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
-            continue;
-        }
-        nout[n] = s;
-        pvout[s] = n;
-    }
-    if (threadIdx.x == 0) {
-        counters[CNT_N] = M;
-        dstats[DS_SMALL] += (double)counters[CNT_SMALL];
-        counters[CNT_SMALL] = 0;
-    }
+    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap);
 }
 
 // -------------------------------------------------------------- reconnect
@@ -247,52 +286,34 @@ __device__ __forceinline__ uint32_t cell_hash(int cx, int cy, int cz) {
     return ((uint32_t)cx * 73856093u) ^ ((uint32_t)cy * 19349663u) ^ ((uint32_t)cz * 83492791u);
 }
 
-__global__ void k_hash_count(const double* __restrict__ pos, const int* __restrict__ counters, int cap, uint32_t hmask,
-                             int* __restrict__ hkey, int* __restrict__ hcount) {
+// Unit-cell hash of the points: bucket heads (kept at -1 between passes) and a
+// link per point, filled with atomicExch; bucket order does not matter.
+__global__ void k_hash_insert(const double* __restrict__ pos, int* __restrict__ counters, int cap,
+                              uint32_t hmask, int* __restrict__ hkey, int* __restrict__ hhead,
+                              int* __restrict__ hlink) {
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) counters[CNT_NPAIRS] = 0;
     if (i >= N) return;
     const int cx = (int)floor(pos[i]), cy = (int)floor(pos[(long long)cap + i]), cz = (int)floor(pos[2LL * cap + i]);
     const int h = (int)(cell_hash(cx, cy, cz) & hmask);
     hkey[i] = h;
-    atomicAdd(&hcount[h], 1);
+    hlink[i] = atomicExch(&hhead[h], i);
 }
 
-__global__ void __launch_bounds__(1024) k_hash_scan(const int* __restrict__ hcount, int hsize, int* __restrict__ hstart,
-                                                     int* __restrict__ hcursor, int* __restrict__ counters) {
-    const int per = (hsize + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int b0 = min(hsize, (int)threadIdx.x * per);
-    const int b1 = min(hsize, b0 + per);
-    int mine = 0;
-    for (int k = b0; k < b1; ++k) mine += hcount[k];
-    int tot = 0;
-    int base = block_exclusive_scan(mine, &tot);
-    for (int k = b0; k < b1; ++k) {
-        hstart[k] = base;
-        hcursor[k] = base;
-        base += hcount[k];
-    }
-    if (threadIdx.x == 0) counters[CNT_NPAIRS] = 0;
-}
-
-__global__ void k_hash_fill(const int* __restrict__ hkey, const int* __restrict__ counters, int* __restrict__ hcursor,
-                            int* __restrict__ hentry) {
+// Nearest point within dxi_max outside the two-link neighbourhood.  Every
+// point closer than dxi_max < 1 lies in one of the 27 unit cells around; one
+// warp per point, lane l < 27 walks the bucket of cell l, then the warp takes
+// the minimum of (d^2, j).
+__global__ void __launch_bounds__(128) k_nearest(VfmParams P, double dmax2, const double* __restrict__ pos,
+                                                 const int* __restrict__ next, const int* __restrict__ prev,
+                                                 const int* __restrict__ counters, int cap, uint32_t hmask,
+                                                 const int* __restrict__ hhead, const int* __restrict__ hlink,
+                                                 int* __restrict__ nn, double* __restrict__ nd2) {
     const int N = counters[CNT_N];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int slot = atomicAdd(&hcursor[hkey[i]], 1);
-    hentry[slot] = i;
-}
-
-// Nearest point within dxi_max outside the two-link neighbourhood; every
-// point closer than dxi_max < 1 lies in one of the 27 unit cells around.
-__global__ void k_nearest(VfmParams P, double dmax2, const double* __restrict__ pos, const int* __restrict__ next,
-                          const int* __restrict__ prev, const int* __restrict__ counters, int cap, uint32_t hmask,
-                          const int* __restrict__ hstart, const int* __restrict__ hcount,
-                          const int* __restrict__ hentry, int* __restrict__ nn, double* __restrict__ nd2) {
-    const int N = counters[CNT_N];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;  // whole warp
     const int p = prev[i], q = next[i], pp = prev[p], qq = next[q];
     double xi[3];
     int c[3];
@@ -300,32 +321,40 @@ __global__ void k_nearest(VfmParams P, double dmax2, const double* __restrict__ 
         xi[k] = pos[(long long)k * cap + i];
         c[k] = (int)floor(xi[k]);
     }
-    const int n[3] = {P.g.nx, P.g.ny, P.g.nz};
     int best = -1;
     double bd = 0.0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                int cc[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
-                for (int a = 0; a < 3; ++a)
-                    if (!P.g.wall[a]) cc[a] = ((cc[a] % n[a]) + n[a]) % n[a];
-                const int h = (int)(cell_hash(cc[0], cc[1], cc[2]) & hmask);
-                const int e0 = hstart[h], e1 = e0 + hcount[h];
-                for (int e = e0; e < e1; ++e) {
-                    const int j = hentry[e];
-                    if (j == i || j == p || j == q || j == pp || j == qq) continue;
-                    double d[3];
-                    for (int k = 0; k < 3; ++k) d[k] = min_image(P.g, k, pos[(long long)k * cap + j] - xi[k]);
-                    const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (!(d2 < dmax2)) continue;
-                    if (best < 0 || d2 < bd || (d2 == bd && j < best)) {
-                        best = j;
-                        bd = d2;
-                    }
-                }
+    if (lane < 27) {
+        const int n[3] = {P.g.nx, P.g.ny, P.g.nz};
+        int cc[3] = {c[0] + lane % 3 - 1, c[1] + (lane / 3) % 3 - 1, c[2] + lane / 9 - 1};
+        for (int a = 0; a < 3; ++a)
+            if (!P.g.wall[a]) cc[a] = ((cc[a] % n[a]) + n[a]) % n[a];
+        const int h = (int)(cell_hash(cc[0], cc[1], cc[2]) & hmask);
+        int j = hhead[h];
+        for (int guard = 0; j >= 0 && guard < N; ++guard, j = hlink[j]) {
+            if (j == i || j == p || j == q || j == pp || j == qq) continue;
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = min_image(P.g, k, pos[(long long)k * cap + j] - xi[k]);
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(d2 < dmax2)) continue;
+            if (best < 0 || d2 < bd || (d2 == bd && j < best)) {
+                best = j;
+                bd = d2;
             }
-    nn[i] = best;
-    nd2[i] = bd;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+        if (ob >= 0 && (best < 0 || od < bd || (od == bd && ob < best))) {
+            best = ob;
+            bd = od;
+        }
+    }
+    if (lane == 0) {
+        nn[i] = best;
+        nd2[i] = bd;
+    }
 }
 
 __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
@@ -358,57 +387,60 @@ __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* 
     cand_d2[slot] = nd2[i];
 }
 
-// Position of each candidate in ascending (d^2, i) order (keys are unique).
-__global__ void k_rank(const int* __restrict__ counters, const int* __restrict__ cand_i,
-                       const double* __restrict__ cand_d2, int* __restrict__ order) {
-    const int K = counters[CNT_NPAIRS];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= K) return;
-    const double d = cand_d2[c];
-    const int ic = cand_i[c];
-    int r = 0;
-    for (int o = 0; o < K; ++o) {
-        const double e = cand_d2[o];
-        r += (e < d || (e == d && cand_i[o] < ic)) ? 1 : 0;
-    }
-    order[r] = c;
-}
-
-// Greedy pass in order; an exchange touching a point already used is skipped.
-__global__ void k_greedy(int* __restrict__ next, int* __restrict__ prev, int* __restrict__ counters,
-                         const int* __restrict__ order, const int* __restrict__ cand_a, const int* __restrict__ cand_b,
-                         int* __restrict__ stamp, double* __restrict__ dstats) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int K = counters[CNT_NPAIRS];
-    const int st = counters[CNT_STAMP] + 1;
-    counters[CNT_STAMP] = st;
-    int applied = 0;
-    for (int r = 0; r < K; ++r) {
-        const int c = order[r];
-        const int a = cand_a[c], b = cand_b[c];
-        const int qa = next[a], qb = next[b];
-        if (stamp[a] == st || stamp[qa] == st || stamp[b] == st || stamp[qb] == st) continue;
-        stamp[a] = st;
-        stamp[qa] = st;
-        stamp[b] = st;
-        stamp[qb] = st;
-        next[a] = qb;
-        prev[qb] = a;
-        next[b] = qa;
-        prev[qa] = b;
-        ++applied;
-    }
-    dstats[DS_RECON] += (double)applied;
-}
-
-__global__ void k_alive_all(uint8_t* __restrict__ alive, int* __restrict__ counters) {
+// One block finishes the reconnection: candidates in ascending (d^2, i)
+// order (keys are unique), the greedy pass in that order (an exchange that
+// touches a point already used is skipped), emptying the hash buckets,
+// small-loop deletion and the compaction into the other point buffer.
+__global__ void __launch_bounds__(1024) k_reconnect_finish(
+    double* __restrict__ pos, int* __restrict__ next, int* __restrict__ prev, const int* __restrict__ cand_i,
+    const int* __restrict__ cand_a, const int* __restrict__ cand_b, const double* __restrict__ cand_d2,
+    int* __restrict__ order, int* __restrict__ stamp, const int* __restrict__ hkey, int* __restrict__ hhead,
+    uint8_t* __restrict__ alive, int* __restrict__ newidx, double* __restrict__ pout, int* __restrict__ nout,
+    int* __restrict__ pvout, int* __restrict__ counters, double* __restrict__ dstats, int cap) {
     const int N = counters[CNT_N];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) {
-        counters[CNT_TOTAL] = N;
-        counters[CNT_SMALL] = 0;
+    const int K = counters[CNT_NPAIRS];
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        const double d = cand_d2[c];
+        const int ic = cand_i[c];
+        int r = 0;
+        for (int o = 0; o < K; ++o) {
+            const double e = cand_d2[o];
+            r += (e < d || (e == d && cand_i[o] < ic)) ? 1 : 0;
+        }
+        order[r] = c;
     }
-    if (k < N) alive[k] = 1;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        alive[k] = 1;
+        hhead[hkey[k]] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int st = counters[CNT_STAMP] + 1;
+        counters[CNT_STAMP] = st;
+        int applied = 0;
+        for (int r = 0; r < K; ++r) {
+            const int c = order[r];
+            const int a = cand_a[c], b = cand_b[c];
+            const int qa = next[a], qb = next[b];
+            if (stamp[a] == st || stamp[qa] == st || stamp[b] == st || stamp[qb] == st) continue;
+            stamp[a] = st;
+            stamp[qa] = st;
+            stamp[b] = st;
+            stamp[qb] = st;
+            next[a] = qb;
+            prev[qb] = a;
+            next[b] = qa;
+            prev[qa] = b;
+            ++applied;
+        }
+        dstats[DS_RECON] += (double)applied;
+    }
+    __syncthreads();
+    const int dead = block_small_loops(next, alive, N, counters);
+    const int dead_all = block_sum(dead);
+    if (threadIdx.x == 0) dstats[DS_SMALL] += (double)dead_all;
+    __syncthreads();
+    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap);
 }
 
 }  // namespace
@@ -416,36 +448,30 @@ __global__ void k_alive_all(uint8_t* __restrict__ alive, int* __restrict__ count
 void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s) {
     if (cap <= 0) return;
     const int nb = (cap + 255) / 256;
-    launch_geometry(P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, d.sp, d.spp, d.dxi, d.lia, d.seglen,
-                    d.seg, s);
+    k_geometry_exact<<<(cap + 63) / 64, 64, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, d.spp,
+                                                     d.seglen);
     k_remesh_flags<<<nb, 256, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.seglen, d.counters, cap, d.flags);
-    k_remesh_apply<<<1, 1024, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
-                                      d.alive, d.counters, d.dstats, cap);
-    k_small_loops<<<nb, 256, 0, s>>>(d.nnext, d.alive, d.counters);
-    k_compact<<<1, 1024, 0, s>>>(d.pos[cur], d.nnext, d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1],
-                                 d.prev[cur ^ 1], d.counters, d.dstats, cap);
+    k_remesh_finish<<<1, 1024, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
+                                       d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1],
+                                       d.counters, d.dstats, cap);
 }
+
+void init_hash(Dev& d, int hsize, cudaStream_t s) { cudaMemsetAsync(d.hhead, 0xff, sizeof(int) * (size_t)hsize, s); }
 
 void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, cudaStream_t s) {
     if (cap <= 0) return;
     const int nb = (cap + 255) / 256;
     const uint32_t hmask = (uint32_t)hsize - 1u;
     const double dmax2 = P.dmax * P.dmax;
-    cudaMemsetAsync(d.hcount, 0, sizeof(int) * (size_t)hsize, s);
-    k_hash_count<<<nb, 256, 0, s>>>(d.pos[cur], d.counters, cap, hmask, d.hkey, d.hcount);
-    k_hash_scan<<<1, 1024, 0, s>>>(d.hcount, hsize, d.hstart, d.hcursor, d.counters);
-    k_hash_fill<<<nb, 256, 0, s>>>(d.hkey, d.counters, d.hcursor, d.hentry);
-    k_nearest<<<nb, 256, 0, s>>>(P, dmax2, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, hmask, d.hstart,
-                                 d.hcount, d.hentry, d.nn, d.nd2);
+    k_hash_insert<<<nb, 256, 0, s>>>(d.pos[cur], d.counters, cap, hmask, d.hkey, d.hhead, d.hlink);
+    k_nearest<<<(cap + 3) / 4, 128, 0, s>>>(P, dmax2, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, hmask,
+                                            d.hhead, d.hlink, d.nn, d.nd2);
     k_pairs<<<nb, 256, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap, d.cand_i,
                                d.cand_a, d.cand_b, d.cand_d2);
-    k_rank<<<nb, 256, 0, s>>>(d.counters, d.cand_i, d.cand_d2, d.cand_order);
-    k_greedy<<<1, 32, 0, s>>>(d.next[cur], d.prev[cur], d.counters, d.cand_order, d.cand_a, d.cand_b, d.stamp,
-                              d.dstats);
-    k_alive_all<<<nb, 256, 0, s>>>(d.alive, d.counters);
-    k_small_loops<<<nb, 256, 0, s>>>(d.next[cur], d.alive, d.counters);
-    k_compact<<<1, 1024, 0, s>>>(d.pos[cur], d.next[cur], d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1],
-                                 d.prev[cur ^ 1], d.counters, d.dstats, cap);
+    k_reconnect_finish<<<1, 1024, 0, s>>>(d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
+                                          d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
+                                          d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
+                                          cap);
 }
 
 }  // namespace vlb

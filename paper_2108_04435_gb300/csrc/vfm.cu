@@ -4,9 +4,7 @@
 // 2-point-delta interpolation of v_n and the spreading of the friction
 // reaction onto the lattice.
 //
-// This file is compiled with -fmad=false: the FP64 geometry (segment
-// lengths, curvature) feeds the integer remeshing decisions, which must match
-// a plain IEEE evaluation of the same expressions bit for bit.
+// The FP64 geometry that feeds the remeshing decisions lives in topo.cu.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -15,8 +13,6 @@
 namespace vlb {
 
 namespace {
-
-constexpr double PI_D = 3.14159265358979323846;
 
 __device__ __forceinline__ double min_image(const Grid& g, int axis, double d) {
     if (!g.wall[axis]) {
@@ -64,116 +60,106 @@ __device__ __forceinline__ void delta_axis(const Grid& g, int axis, double s, in
     i1 = a1;
 }
 
-__global__ void k_copy_pos(const double* __restrict__ src, double* __restrict__ dst, const int* __restrict__ counters,
-                           int cap) {
+// Stage geometry for the equation of motion: the same quantities as
+// k_geometry, with the neighbour differences formed in FP64 (positions are up
+// to ~1e3 cells) and everything after them in FP32, which is accurate to
+// ~1e-7 relative for segments of O(1) cells.  The remeshing decisions use the
+// FP64 k_geometry instead.
+__global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double* __restrict__ s,
+                                                       const int* __restrict__ next, const int* __restrict__ prev,
+                                                       int* __restrict__ counters, int cap,
+                                                       float4* __restrict__ geo, float4* __restrict__ seg,
+                                                       double* __restrict__ s0_copy) {
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    dst[i] = src[i];
-    dst[cap + i] = src[cap + i];
-    dst[2 * cap + i] = src[2 * cap + i];
-}
-
-// Per point i (prev p, next q): three-point derivatives s', s'' on the
-// non-uniform arc-length grid, the length dxi = (l+ + l-)/2 it represents,
-// the local term beta s' x s'' of the divergent part of Eq. 3 with
-// beta = kappa/(4 pi) ln(2 sqrt(l+ l-)/(e^{1/4} a)), and the Biot-Savart
-// source record of segment i -> q: position split into float hi + lo parts and
-// the float segment vector.
-__global__ void k_geometry(VfmParams P, const double* __restrict__ s, const int* __restrict__ next,
-                           const int* __restrict__ prev, const int* __restrict__ counters, int cap,
-                           double* __restrict__ sp, double* __restrict__ spp, double* __restrict__ dxi,
-                           double* __restrict__ lia, double* __restrict__ seglen, float4* __restrict__ seg) {
-    const int N = counters[CNT_N];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch that follows takes items from 0
     if (i >= N) return;
     const int p = prev[i], q = next[i];
-    double si[3], a[3], b[3];
+    double si[3];
+    float a[3], b[3];
     for (int k = 0; k < 3; ++k) {
         si[k] = s[(long long)k * cap + i];
-        a[k] = min_image(P.g, k, si[k] - s[(long long)k * cap + p]);
-        b[k] = min_image(P.g, k, s[(long long)k * cap + q] - si[k]);
+        if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
+        a[k] = (float)min_image(P.g, k, si[k] - s[(long long)k * cap + p]);
+        b[k] = (float)min_image(P.g, k, s[(long long)k * cap + q] - si[k]);
     }
-    const double lm = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-    const double lp = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-    const double den = lp * lm * (lp + lm);
-    double t1[3], t2[3];
+    const float lm = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const float lp = sqrtf(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    const float inv = 1.f / (lp * lm * (lp + lm));
+    float t1[3], t2[3];
     for (int k = 0; k < 3; ++k) {
-        t1[k] = (lm * lm * b[k] + lp * lp * a[k]) / den;
-        t2[k] = 2.0 * (lm * b[k] - lp * a[k]) / den;
-        sp[(long long)k * cap + i] = t1[k];
-        spp[(long long)k * cap + i] = t2[k];
+        t1[k] = (lm * lm * b[k] + lp * lp * a[k]) * inv;
+        t2[k] = 2.f * (lm * b[k] - lp * a[k]) * inv;
     }
-    dxi[i] = 0.5 * (lp + lm);
-    seglen[i] = lp;
-    const double beta = P.kappa / (4.0 * PI_D) * log(2.0 * sqrt(lp * lm) / (exp(0.25) * P.core_a));
-    lia[i] = beta * (t1[1] * t2[2] - t1[2] * t2[1]);
-    lia[(long long)cap + i] = beta * (t1[2] * t2[0] - t1[0] * t2[2]);
-    lia[2LL * cap + i] = beta * (t1[0] * t2[1] - t1[1] * t2[0]);
+    const float beta = P.kq_f * logf(2.f * sqrtf(lp * lm) * P.inv_ea_f);
+    // geo[2i] = (s'.xyz, dxi), geo[2i+1] = (local velocity beta s' x s'', 0)
+    geo[2LL * i] = make_float4(t1[0], t1[1], t1[2], 0.5f * (lp + lm));
+    geo[2LL * i + 1] = make_float4(beta * (t1[1] * t2[2] - t1[2] * t2[1]), beta * (t1[2] * t2[0] - t1[0] * t2[2]),
+                                   beta * (t1[0] * t2[1] - t1[1] * t2[0]), 0.f);
     float hi[3], lo[3];
     for (int k = 0; k < 3; ++k) {
         hi[k] = __double2float_rn(si[k]);
         lo[k] = __double2float_rn(si[k] - (double)hi[k]);
     }
     seg[3LL * i] = make_float4(hi[0], hi[1], hi[2], lo[0]);
-    seg[3LL * i + 1] = make_float4(lo[1], lo[2], __double2float_rn(b[0]), __double2float_rn(b[1]));
-    seg[3LL * i + 2] = make_float4(__double2float_rn(b[2]), 0.f, 0.f, 0.f);
+    seg[3LL * i + 1] = make_float4(lo[1], lo[2], b[0], b[1]);
+    seg[3LL * i + 2] = make_float4(b[2], 0.f, 0.f, 0.f);
 }
 
-// Equation of motion (Eq. 4) at one RK4 stage, with the Biot-Savart partial
-// sums reduced in a fixed order, the local term, V_s of Eq. 18 as the applied
-// superfluid flow, and v_n interpolated with Eq. 11.  Stage 0 also spreads
-// the reaction of Eq. 10 (when spread != 0) with warp-aggregated atomics.
-__global__ void __launch_bounds__(256) k_eom(VfmParams P, int stage, int spread, const double* __restrict__ s0,
-                                             double* __restrict__ st, double* __restrict__ pos_out,
-                                             double* __restrict__ acc, double* __restrict__ vel1,
-                                             const double* __restrict__ sp, const double* __restrict__ dxi,
-                                             const double* __restrict__ lia, const float* __restrict__ bsp, int nsplit,
-                                             const float* __restrict__ U, const double* __restrict__ Vs,
-                                             float* __restrict__ F, uint8_t* __restrict__ fmask,
-                                             int* __restrict__ counters, int cap) {
+// Equation of motion (Eq. 4) at one RK4 stage, in FP32, with the
+// Biot-Savart partial sums reduced in a fixed order, the local term, V_s of
+// Eq. 18 as the applied superfluid flow and v_n interpolated with Eq. 11; the
+// RK4 combination and the positions stay FP64.  Stage 0 also spreads the
+// reaction of Eq. 10 (when spread != 0) with warp-aggregated atomics.
+__global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, const double* __restrict__ s0,
+                                            double* __restrict__ st, double* __restrict__ pos_out,
+                                            double* __restrict__ acc, double* __restrict__ vel1,
+                                            const float4* __restrict__ geo, const float* __restrict__ vbs,
+                                            const float* __restrict__ U, const double* __restrict__ Vs,
+                                            float* __restrict__ F, uint8_t* __restrict__ fmask,
+                                            int* __restrict__ counters, int cap) {
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < N;
     const Grid& g = P.g;
     const long long C = g.ncell;
     const double* xs = stage == 0 ? s0 : st;
-    double x[3] = {0.0, 0.0, 0.0}, t[3] = {0.0, 0.0, 0.0}, fr[3] = {0.0, 0.0, 0.0}, kv[3] = {0.0, 0.0, 0.0};
-    double s1[3] = {0.0, 0.0, 0.0};
+    float s1[3] = {0.f, 0.f, 0.f}, fr[3] = {0.f, 0.f, 0.f}, dxi = 0.f;
     int ix[2] = {0, 0}, iy[2] = {0, 0}, iz[2] = {0, 0};
-    double wx[2] = {0.0, 0.0}, wy[2] = {0.0, 0.0}, wz[2] = {0.0, 0.0};
+    float wx[2] = {0.f, 0.f}, wy[2] = {0.f, 0.f}, wz[2] = {0.f, 0.f};
     if (valid) {
-        double vs[3];
+        double x[3];
+        float vs[3];
+        const float4 g0 = geo[2LL * i], g1 = geo[2LL * i + 1];
+        s1[0] = g0.x; s1[1] = g0.y; s1[2] = g0.z; dxi = g0.w;
+        const float lia[3] = {g1.x, g1.y, g1.z};
         for (int k = 0; k < 3; ++k) {
             x[k] = xs[(long long)k * cap + i];
-            s1[k] = sp[(long long)k * cap + i];
-            float b = 0.f;
-            for (int m = 0; m < nsplit; ++m) b += bsp[((long long)m * 3 + k) * cap + i];
-            vs[k] = (double)b + lia[(long long)k * cap + i];
+            vs[k] = vbs[(long long)k * cap + i] + lia[k];
         }
-        delta_axis(g, 0, x[0], ix[0], ix[1], wx[0], wx[1]);
-        delta_axis(g, 1, x[1], iy[0], iy[1], wy[0], wy[1]);
-        delta_axis(g, 2, x[2], iz[0], iz[1], wz[0], wz[1]);
-        vs[2] += wz[0] * Vs[iz[0]] + wz[1] * Vs[iz[1]];  // v_s,a (Eq. 18)
-        double vn[3] = {0.0, 0.0, 0.0};
+        double w0, w1;
+        delta_axis(g, 0, x[0], ix[0], ix[1], w0, w1); wx[0] = (float)w0; wx[1] = (float)w1;
+        delta_axis(g, 1, x[1], iy[0], iy[1], w0, w1); wy[0] = (float)w0; wy[1] = (float)w1;
+        delta_axis(g, 2, x[2], iz[0], iz[1], w0, w1); wz[0] = (float)w0; wz[1] = (float)w1;
+        vs[2] += wz[0] * (float)Vs[iz[0]] + wz[1] * (float)Vs[iz[1]];  // v_s,a (Eq. 18)
+        float vn[3] = {0.f, 0.f, 0.f};
         for (int cz = 0; cz < 2; ++cz)
             for (int cy = 0; cy < 2; ++cy)
                 for (int cx = 0; cx < 2; ++cx) {
-                    const double w = wz[cz] * wy[cy] * wx[cx];
+                    const float w = wz[cz] * wy[cy] * wx[cx];
                     const long long c = ((long long)iz[cz] * g.ny + iy[cy]) * g.nx + ix[cx];
-                    vn[0] += w * (double)U[c];
-                    vn[1] += w * (double)U[C + c];
-                    vn[2] += w * (double)U[2 * C + c];
+                    vn[0] += w * U[c];
+                    vn[1] += w * U[C + c];
+                    vn[2] += w * U[2 * C + c];
                 }
-        double w[3] = {vn[0] - vs[0], vn[1] - vs[1], vn[2] - vs[2]};
-        t[0] = s1[1] * w[2] - s1[2] * w[1];
-        t[1] = s1[2] * w[0] - s1[0] * w[2];
-        t[2] = s1[0] * w[1] - s1[1] * w[0];
-        double tt[3] = {s1[1] * t[2] - s1[2] * t[1], s1[2] * t[0] - s1[0] * t[2], s1[0] * t[1] - s1[1] * t[0]};
+        const float w[3] = {vn[0] - vs[0], vn[1] - vs[1], vn[2] - vs[2]};
+        const float t[3] = {s1[1] * w[2] - s1[2] * w[1], s1[2] * w[0] - s1[0] * w[2], s1[0] * w[1] - s1[1] * w[0]};
+        const float tt[3] = {s1[1] * t[2] - s1[2] * t[1], s1[2] * t[0] - s1[0] * t[2], s1[0] * t[1] - s1[1] * t[0]};
+        double kv[3];
         int bad = 0;
         for (int k = 0; k < 3; ++k) {
-            fr[k] = P.alpha * t[k] - P.alpha_p * tt[k];
-            kv[k] = vs[k] + fr[k];
+            fr[k] = P.alpha_f * t[k] - P.alpha_p_f * tt[k];
+            kv[k] = (double)(vs[k] + fr[k]);
             if (!(fabs(P.dt * kv[k]) < 1.0)) bad |= (kv[k] == kv[k]) ? ST_CFL : ST_NAN;
         }
         if (bad) atomicOr(&counters[CNT_STATUS], bad);
@@ -202,22 +188,22 @@ __global__ void __launch_bounds__(256) k_eom(VfmParams P, int stage, int spread,
 
     // Reaction of Eq. 10 on the normal fluid: -(rho_s/rho_n) rho0 kappa * f * dxi,
     // f = friction velocity (form 0) or friction velocity x s' (form 1).
-    double gv[3] = {fr[0], fr[1], fr[2]};
+    float gv[3] = {fr[0], fr[1], fr[2]};
     if (P.force_form == 1) {
         gv[0] = fr[1] * s1[2] - fr[2] * s1[1];
         gv[1] = fr[2] * s1[0] - fr[0] * s1[2];
         gv[2] = fr[0] * s1[1] - fr[1] * s1[0];
     }
-    const double scale = valid ? -P.ratio * P.rho0 * P.kappa * dxi[i] : 0.0;
+    const float scale = valid ? P.gscale_f * dxi : 0.f;
     float val[24];
     for (int cz = 0; cz < 2; ++cz)
         for (int cy = 0; cy < 2; ++cy)
             for (int cx = 0; cx < 2; ++cx) {
-                const double w = wz[cz] * wy[cy] * wx[cx];
+                const float w = wz[cz] * wy[cy] * wx[cx] * scale;
                 const int k = (cz * 2 + cy) * 2 + cx;
-                val[3 * k] = (float)(w * (scale * gv[0]));
-                val[3 * k + 1] = (float)(w * (scale * gv[1]));
-                val[3 * k + 2] = (float)(w * (scale * gv[2]));
+                val[3 * k] = w * gv[0];
+                val[3 * k + 1] = w * gv[1];
+                val[3 * k + 2] = w * gv[2];
             }
     // Lanes whose points share a base cell share all eight corners: sum their
     // contributions in the lowest such lane, which alone issues the atomics.
@@ -249,54 +235,70 @@ __global__ void __launch_bounds__(256) k_eom(VfmParams P, int stage, int spread,
             }
 }
 
-// Total line length sum |s_next(i) - s_i| (FP64), one block, fixed order.
-__global__ void __launch_bounds__(1024) k_line_length(Grid g, const double* __restrict__ pos,
-                                                       const int* __restrict__ next, const int* __restrict__ counters,
-                                                       int cap, double* __restrict__ dstats) {
-    __shared__ double sm[1024];
+// Total line length sum |s_next(i) - s_i| (FP64): per-block sums in a fixed
+// order, the last block to finish adds the block sums in block order.
+__global__ void __launch_bounds__(256) k_line_length(Grid g, const double* __restrict__ pos,
+                                                      const int* __restrict__ next, int* __restrict__ counters,
+                                                      int cap, double* __restrict__ part, double* __restrict__ dstats) {
+    __shared__ double sm[256];
+    __shared__ int s_last;
     const int N = counters[CNT_N];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < N) {
         const int q = next[i];
         double d[3];
         for (int k = 0; k < 3; ++k) d[k] = min_image(g, k, pos[(long long)k * cap + q] - pos[(long long)k * cap + i]);
-        acc += sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        v = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     }
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sm[0];
+        __threadfence();
+        s_last = atomicAdd(&counters[CNT_LINEDONE], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) acc += __ldcg(&part[k]);
     sm[threadIdx.x] = acc;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) dstats[DS_LINE] = sm[0];
+    if (threadIdx.x == 0) {
+        dstats[DS_LINE] = sm[0];
+        counters[CNT_LINEDONE] = 0;
+    }
 }
 
 }  // namespace
 
-void launch_copy_pos(const double* src, double* dst, const int* counters, int cap, cudaStream_t s) {
-    if (cap <= 0) return;
-    k_copy_pos<<<(cap + 255) / 256, 256, 0, s>>>(src, dst, counters, cap);
-}
 
-void launch_geometry(const VfmParams& P, const double* s, const int* next, const int* prev, const int* counters,
-                     int cap, double* sp, double* spp, double* dxi, double* lia, double* seglen, float4* seg,
-                     cudaStream_t st) {
+void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
+                           int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st) {
     if (cap <= 0) return;
-    k_geometry<<<(cap + 127) / 128, 128, 0, st>>>(P, s, next, prev, counters, cap, sp, spp, dxi, lia, seglen, seg);
+    k_geometry_stage<<<(cap + 63) / 64, 64, 0, st>>>(P, s, next, prev, counters, cap, geo, seg, s0_copy);
 }
 
 void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, double* st, double* pos_out,
-                double* acc, double* vel1, const double* sp, const double* dxi, const double* lia, const float* bsp,
-                int nsplit, const float* U, const double* Vs, float* F, uint8_t* fmask, int* counters, int cap,
-                cudaStream_t s) {
+                double* acc, double* vel1, const float4* geo, const float* vbs, const float* U, const double* Vs,
+                float* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s) {
     if (cap <= 0) return;
-    k_eom<<<(cap + 255) / 256, 256, 0, s>>>(P, stage, spread, s0, st, pos_out, acc, vel1, sp, dxi, lia, bsp, nsplit,
-                                            U, Vs, F, fmask, counters, cap);
+    k_eom<<<(cap + 63) / 64, 64, 0, s>>>(P, stage, spread, s0, st, pos_out, acc, vel1, geo, vbs, U, Vs, F, fmask,
+                                         counters, cap);
 }
 
-void launch_line_length(const Grid& g, const double* pos, const int* next, const int* counters, int cap,
+void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,
                         double* dstats, cudaStream_t s) {
-    k_line_length<<<1, 1024, 0, s>>>(g, pos, next, counters, cap, dstats);
+    k_line_length<<<(cap + 255) / 256, 256, 0, s>>>(g, pos, next, counters, cap, part, dstats);
 }
 
 }  // namespace vlb

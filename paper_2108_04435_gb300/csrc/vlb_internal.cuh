@@ -25,7 +25,10 @@ enum : int {
     CNT_NPAIRS = 3,     // candidate reconnections this pass
     CNT_STAMP = 4,      // reconnection pass counter (claim stamps)
     CNT_SMALL = 5,      // points deleted in small loops this pass
-    CNT_COUNT = 8
+    CNT_BSWORK = 6,     // Biot-Savart work-item counter (reset before each launch)
+    CNT_PLANES = 7,     // z planes reduced in the current lattice pass
+    CNT_LINEDONE = 8,   // blocks done in the line-length reduction
+    CNT_COUNT = 12
 };
 
 // Device float64 statistics.
@@ -66,14 +69,40 @@ struct LbmParams {
     float dw[3];        // w_i rho0 - s_i for the rest, axis and diagonal classes (exact in double, then float)
     int body_on;
     int pin_on;
+    double inv_ratio;   // rho_n / rho_s
+    // device buffers of the fused per-plane reduction (Eq. 18, mass, Mach)
+    int* plane_ticket;  // [nz] blocks done per plane, back to 0 after the plane is reduced
+    double* plane;      // [nz][3] plane sums (delta rho, u_z, max u^2)
+    double* Vs;         // [nz]
+    double* dstats;
+    int* counters;
 };
 
 struct VfmParams {
     Grid g;
     double kappa, alpha, alpha_p, ratio, rho0, core_a, dmin, dmax;
     double dt;
+    float kq_f;      // kappa / (4 pi)
+    float inv_ea_f;  // 1 / (e^{1/4} a)
+    float alpha_f, alpha_p_f;
+    float gscale_f;  // -(rho_s/rho_n) rho0 kappa
     int couple, force_form;
 };
+
+// Biot-Savart source splits for N points: enough (target tile, split) work
+// items to fill the GPU (~4 per SM on 152 SMs), at least 64 segments per
+// split.  Used by the Biot-Savart kernel and by the reduction that reads its
+// partial sums, so both derive it from the same device-side N.
+__host__ __device__ inline int bs_splits(int N) {
+    const int n = N > 0 ? N : 1;
+    const int tb = (n + 127) / 128;
+    int ns = (4 * 152 + tb - 1) / tb;
+    const int by_chunk = (n + 63) / 64;
+    if (ns > by_chunk) ns = by_chunk;
+    if (ns < 1) ns = 1;
+    if (ns > 64) ns = 64;
+    return ns;
+}
 
 struct Dev {
     // lattice
@@ -83,6 +112,8 @@ struct Dev {
     uint8_t* fmask;     // tiles where F may be non-zero
     uint8_t* umask;     // tiles where U must be written
     double* part;       // stream-collide block partials [nz][bpp][3]
+    double* plane;      // plane sums [nz][3]
+    int* plane_ticket;  // [nz]
     double* Vs;         // [nz]
     double* dstats;     // [DS_COUNT]
     int* counters;      // [CNT_COUNT]
@@ -94,23 +125,21 @@ struct Dev {
     double* st;
     double* acc;
     double* vel1;
-    double* sp;
-    double* spp;
-    double* lia;
-    double* dxi;
-    double* seglen;
+    double* spp;        // FP64 curvature for remeshing
+    double* seglen;     // FP64 segment lengths for remeshing
     float4* seg;        // Biot-Savart source records, 3 float4 per point
-    float* bsp;         // Biot-Savart partial sums [MAX_SPLIT][3][cap]
+    float* bsp;         // Biot-Savart partial sums [splits][3][cap]
+    float* vbs;         // Biot-Savart velocity [3][cap]
+    int* tile_ticket;   // per target tile: splits done
+    float4* geo;        // stage geometry: (s', dxi), (local velocity, 0) per point
     // topology scratch
     uint8_t* flags;
     uint8_t* alive;
     int* nnext;
     int* newidx;
     int* hkey;
-    int* hcount;
-    int* hstart;
-    int* hcursor;
-    int* hentry;
+    int* hhead;         // first point of each hash bucket (-1 empty), kept all -1 between passes
+    int* hlink;         // next point in the same bucket
     int* nn;
     double* nd2;
     int* cand_i;
@@ -127,8 +156,7 @@ struct Dev {
 void launch_lbm_init(const LbmParams& P, float* f, float* U, const double init_u[3], cudaStream_t s);
 void launch_lbm_step(const LbmParams& P, const float* fin, float* fout, const float* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
-void launch_plane_vs(const LbmParams& P, const double* part, double ratio, double* Vs, double* dstats,
-                     int* counters, cudaStream_t s);
+void launch_plane_vs(const LbmParams& P, const double* part, cudaStream_t s);
 void launch_moments(const LbmParams& P, const float* f, const float* F, const uint8_t* fmask, float* rho,
                     float* U, cudaStream_t s);
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,
@@ -137,27 +165,24 @@ void launch_zero_force(const Grid& g, float* F, uint8_t* fmask, cudaStream_t s);
 void launch_unshift(const LbmParams& P, const float* fsh, float* out, int direction, cudaStream_t s);
 
 // vfm.cu
-void launch_copy_pos(const double* src, double* dst, const int* counters, int cap, cudaStream_t s);
-void launch_geometry(const VfmParams& P, const double* s, const int* next, const int* prev, const int* counters,
-                     int cap, double* sp, double* spp, double* dxi, double* lia, double* seglen, float4* seg,
-                     cudaStream_t st);
+void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
+                           int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st);
 void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, double* st, double* pos_out,
-                double* acc, double* vel1, const double* sp, const double* dxi, const double* lia, const float* bsp,
-                int nsplit, const float* U, const double* Vs, float* F, uint8_t* fmask, int* counters, int cap,
-                cudaStream_t s);
-void launch_line_length(const Grid& g, const double* pos, const int* next, const int* counters, int cap,
+                double* acc, double* vel1, const float4* geo, const float* vbs, const float* U, const double* Vs,
+                float* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s);
+void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,
                         double* dstats, cudaStream_t s);
 
 // bs.cu
-int bs_nsplit(int n_hint, int cap);
+int bs_max_splits(int cap);
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
-                        int cap, int nsplit, float* bsp, cudaStream_t s);
+                        int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s);
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
                                int* counters, cudaStream_t s);
-void launch_bs_reduce(const float* bsp, int nsplit, int n, int cap, float* vel, cudaStream_t s);
 
 // topo.cu
 void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s);
 void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, cudaStream_t s);
+void init_hash(Dev& d, int hsize, cudaStream_t s);
 
 }  // namespace vlb

@@ -46,34 +46,83 @@ def concat(parts):
 
 
 def random_rings(n_box, wall, count: int, r_min: float, r_max: float, seed: int,
-                 spacing: float = 0.8):
+                 spacing: float = 0.8, min_sep: float = 2.0, max_tries: int = 200):
     """``count`` rings with radius ~ U[r_min, r_max], random centres and normals.
 
     Centres are uniform in the box; on wall axes they are kept R + 2 cells
-    inside the walls (walls sit half a cell outside the first/last node).
+    inside the walls (walls sit half a cell outside the first/last node).  A
+    candidate ring that would pass within ``min_sep`` cells of an earlier
+    ring is redrawn (intersecting seeds would start from near-singular
+    velocities); min_sep = 0 disables the check.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
+    box = np.asarray(n_box, np.float64)
+    periodic = np.array([not w for w in wall])
+    grid = _PointGrid(box, periodic, max(min_sep, 1e-9))
     parts = []
     for _ in range(count):
-        R = rng.uniform(r_min, r_max)
-        c = np.empty(3)
-        for a in range(3):
-            if wall[a]:
-                lo, hi = -0.5 + R + 2.0, n_box[a] - 0.5 - R - 2.0
-                if hi <= lo:
-                    raise ValueError("box too small for ring radius")
-                c[a] = rng.uniform(lo, hi)
-            else:
-                c[a] = rng.uniform(0.0, n_box[a])
-        nrm = rng.normal(size=3)
-        nrm /= np.linalg.norm(nrm)
-        phase = rng.uniform(0.0, 2.0 * np.pi)
-        parts.append(ring(c, nrm, R, spacing=spacing, phase=phase))
+        for _try in range(max_tries):
+            R = rng.uniform(r_min, r_max)
+            c = np.empty(3)
+            for a in range(3):
+                if wall[a]:
+                    lo, hi = -0.5 + R + 2.0, n_box[a] - 0.5 - R - 2.0
+                    if hi <= lo:
+                        raise ValueError("box too small for ring radius")
+                    c[a] = rng.uniform(lo, hi)
+                else:
+                    c[a] = rng.uniform(0.0, n_box[a])
+            nrm = rng.normal(size=3)
+            nrm /= np.linalg.norm(nrm)
+            phase = rng.uniform(0.0, 2.0 * np.pi)
+            xyz, nxt = ring(c, nrm, R, spacing=spacing, phase=phase)
+            if min_sep <= 0 or grid.clearance(xyz, min_sep) >= min_sep:
+                break
+        parts.append((xyz, nxt))
+        grid.add(xyz)
     xyz, nxt = concat(parts)
     for a in range(3):
         if not wall[a]:
             xyz[:, a] = np.mod(xyz[:, a], n_box[a])
     return xyz, nxt
+
+
+class _PointGrid:
+    """Uniform grid of cell size h over placed points, for clearance queries."""
+
+    def __init__(self, box, periodic, h):
+        self.box, self.periodic, self.h = box, periodic, h
+        self.ncell = np.maximum(np.floor(box / h).astype(int), 1)
+        self.cells = {}
+
+    def _key(self, c):
+        c = np.where(self.periodic, np.mod(c, self.ncell), c)
+        return tuple(int(v) for v in c)
+
+    def _cells_of(self, pts):
+        return np.floor(np.where(self.periodic, np.mod(pts, self.box), pts) / self.h).astype(int)
+
+    def add(self, pts):
+        for q, c in zip(pts, self._cells_of(pts)):
+            self.cells.setdefault(self._key(c), []).append(q)
+
+    def clearance(self, pts, stop_below=0.0):
+        """Smallest distance from pts to the placed points (stops early below stop_below)."""
+        best = np.inf
+        if not self.cells:
+            return best
+        offs = [(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]
+        for q, c in zip(pts, self._cells_of(pts)):
+            for o in offs:
+                lst = self.cells.get(self._key(c + np.array(o)))
+                if not lst:
+                    continue
+                d = np.asarray(lst) - q
+                d = np.where(self.periodic, d - self.box * np.round(d / self.box), d)
+                best = min(best, float(np.sqrt((d * d).sum(-1)).min()))
+                if best < stop_below:
+                    return best
+        return best
 
 
 def perturbed_equilibrium(ncell: int, seed: int, amp: float = 1e-3):

@@ -20,11 +20,11 @@ ERR = {-1: "INVALID_ARG", -2: "OOM", -3: "CAPACITY", -4: "TOPOLOGY", -5: "MACH",
        -7: "TIMEOUT", -8: "CUDA", -9: "CFL"}
 PHASE_LBM, PHASE_VFM, PHASE_REMESH, PHASE_RECONNECT, PHASE_ALL = 1, 2, 4, 8, 15
 FIELD_RHO, FIELD_U, FIELD_FSTAR, FIELD_FORCE, FIELD_POS, FIELD_NEXT = 0, 1, 2, 3, 4, 5
-FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL = 6, 7, 8
+FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_FDEV = 6, 7, 8, 9
 
 EXPORTS = ["vlb_create_channel", "vlb_seed_vortices", "vlb_step", "vlb_run_phases", "vlb_read_fields",
            "vlb_write_fields", "vlb_line_length", "vlb_destroy", "vlb_last_error", "vlb_set_timing",
-           "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart"]
+           "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart", "vlb_set_graphs"]
 
 
 class Params(C.Structure):
@@ -77,6 +77,7 @@ def lib():
         L.vlb_last_error.argtypes = []
         L.vlb_last_error.restype = C.c_char_p
         L.vlb_set_timing.argtypes = [vp, C.c_int32]
+        L.vlb_set_graphs.argtypes = [vp, C.c_int32]
         L.vlb_lbm_timing.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.vlb_biot_savart_scratch_bytes.argtypes = [C.c_int32]
         L.vlb_biot_savart_scratch_bytes.restype = C.c_size_t
@@ -134,7 +135,8 @@ class Channel:
         torch.cuda.set_device(device)
         self.params = dict(params)
         self._p = make_params(params)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        # a created stream by default: the step can then be replayed as a CUDA graph
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
         self._alloc = TorchAllocator(device) if torch_alloc else None
         h = C.c_void_p()
         check(lib().vlb_create_channel(C.byref(self._p), C.byref(self._alloc.struct) if self._alloc else None,
@@ -186,7 +188,8 @@ class Channel:
         N = self.n_points() if which in (FIELD_POS, FIELD_VEL, FIELD_NEXT) else None
         shapes = {
             FIELD_RHO: ((self.ncell,), np.float32), FIELD_U: ((3, self.ncell), np.float32),
-            FIELD_FSTAR: ((19, self.ncell), np.float32), FIELD_FORCE: ((3, self.ncell), np.float32),
+            FIELD_FSTAR: ((19, self.ncell), np.float32), FIELD_FDEV: ((19, self.ncell), np.float32),
+            FIELD_FORCE: ((3, self.ncell), np.float32),
             FIELD_POS: ((N, 3), np.float64), FIELD_VEL: ((N, 3), np.float64), FIELD_NEXT: ((N,), np.int32),
             FIELD_PLANE_VS: ((self.n[2],), np.float64), FIELD_STATS: ((16,), np.float64),
         }
@@ -204,6 +207,9 @@ class Channel:
         out = C.c_double()
         check(lib().vlb_line_length(self.h, C.byref(out)))
         return out.value
+
+    def set_graphs(self, enable: bool):
+        check(lib().vlb_set_graphs(self.h, 1 if enable else 0))
 
     def set_timing(self, enable: bool):
         check(lib().vlb_set_timing(self.h, 1 if enable else 0))

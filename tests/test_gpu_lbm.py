@@ -37,7 +37,7 @@ def compare_lattice(g, r):
     rest += (w * r.params["rho0"])[:, None]
     out = {
         "fstar": rel_l2(f_g, f_r),
-        "fdev": rel_l2(f_g - rest, f_r - rest),
+        "fdev": rel_l2(g.read(vlb.FIELD_FDEV), f_r - rest),
         "u": rel_l2(g.read(vlb.FIELD_U), r.read(oracle.FIELD_U)),
         "rho": rel_l2(g.read(vlb.FIELD_RHO), r.read(oracle.FIELD_RHO)),
         "vs": rel_l2(g.read(vlb.FIELD_PLANE_VS), r.read(oracle.FIELD_PLANE_VS)),

@@ -20,7 +20,7 @@ def tparams(n, wall, **kw):
 
 def jittered_tangle(n, wall, count, seed, jitter, spacing):
     from paper_2108_04435_gb300 import inputs
-    xyz, nxt = inputs.random_rings(n, wall, count, 2.0, 9.0, seed, spacing=spacing)
+    xyz, nxt = inputs.random_rings(n, wall, count, 2.0, 9.0, seed, spacing=spacing, min_sep=0.0)
     rng = np.random.default_rng(seed + 100)
     xyz = xyz + jitter * rng.uniform(-1, 1, xyz.shape)
     for a in range(3):
