@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -252,6 +253,24 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     L.pin = (float)p->pin_vn;
     L.pin_on = p->pin_vn != 0.0 ? 1 : 0;
     {
+        // Launch shape of the stream-collide kernel, chosen from measurements on
+        // GB300 (lattices of 32^3 to 128x128x1024): one cell per thread in
+        // 128-thread blocks was fastest everywhere.  VLB_LBM_VEC (1, 2, 4) and
+        // VLB_LBM_BLOCK (128, 256) override it.
+        int vec = 1;
+        if (const char* e = getenv("VLB_LBM_VEC")) {
+            const int v = atoi(e);
+            if ((v == 1 || v == 2 || v == 4) && g.nx % v == 0) vec = v;
+        }
+        int blk = 128;
+        if (const char* e = getenv("VLB_LBM_BLOCK")) {
+            const int b = atoi(e);
+            if (b == 128 || b == 256) blk = b;
+        }
+        L.vec = vec;
+        L.block = blk;
+    }
+    {
         // float shift constants s_i = fl(fl(w_i) rho0) as the kernels form them
         const double wexact[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
         const float wf[3] = {1.f / 3.f, 1.f / 18.f, 1.f / 36.f};
@@ -289,7 +308,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     int h = 1;
     while (h < 2 * cap) h <<= 1;
     ch->hsize = h;
-    ch->bpp = (g.nx * g.ny + LBM_BLOCK - 1) / LBM_BLOCK;
+    ch->bpp = lbm_blocks_per_plane(L);
     const int nsm = bs_max_splits(cap);
     ch->nsplit_max = nsm;
     const int ntiles = g.tnx * g.tny * g.tnz;
@@ -644,7 +663,7 @@ int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches) {
 
 size_t vlb_biot_savart_scratch_bytes(int32_t n) {
     if (n < 1) n = 1;
-    const int ns = bs_splits(n);
+    const int ns = bs_splits(n, BS_TPB);
     auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
     return up(sizeof(int) * CNT_COUNT) + up(sizeof(int) * (size_t)n) + up(sizeof(float4) * 3 * (size_t)n) +
            up(sizeof(float) * 3 * (size_t)n * (size_t)ns) + up(sizeof(int) * (size_t)((n + BS_TPB - 1) / BS_TPB));
@@ -673,7 +692,7 @@ int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next,
     float4* seg = (float4*)base;
     base += up(sizeof(float4) * 3 * (size_t)n);
     float* bsp = (float*)base;
-    base += up(sizeof(float) * 3 * (size_t)n * (size_t)bs_splits(n));
+    base += up(sizeof(float) * 3 * (size_t)n * (size_t)bs_splits(n, BS_TPB));
     int* tickets = (int*)base;
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(tickets, 0, sizeof(int) * (size_t)((n + BS_TPB - 1) / BS_TPB), s);

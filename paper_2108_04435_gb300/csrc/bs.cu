@@ -75,36 +75,74 @@ __device__ __forceinline__ void issue_tile(float4* dst, const float4* seg, int j
     bulk_copy_g2s(dst, seg + 3LL * jb, bytes, bar);
 }
 
-template <bool PERIODIC>
-__device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, int jb, int self, int pi, float rhx,
-                                        float rhy, float rhz, float rlx, float rly, float rlz, const BoxF& box,
-                                        float kq, float& vx, float& vy, float& vz) {
-#pragma unroll 4
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Nearest integer of |x| < 2^22 on the FMA pipe: adding and removing
+// 1.5 * 2^23 rounds to nearest even in FP32.
+__device__ __forceinline__ float round_fma(float x) {
+    const float M = 12582912.0f;
+    return __fsub_rn(__fadd_rn(x, M), M);
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// One target of a Biot-Savart tile pass (registers of one thread).
+struct BsTarget {
+    float hx, hy, hz, lx, ly, lz;  // position, float hi + lo parts
+    float vx, vy, vz;              // accumulated velocity
+    int self, prev;                // its own segment and its predecessor's (local term)
+};
+
+// Sum over the segments of one shared-memory tile for TGT targets per thread.
+// With R1 = s_j - r and d the segment vector: R1 x R2 = R1 x d,
+// R1.R2 = |R1|^2 + R1.d and |R2|^2 = |R1|^2 + 2 R1.d + |d|^2 (|d|^2 stored in
+// the record).  MASKED: the tile may hold a target's own segment or its
+// predecessor's, which belong to the local term.
+template <bool PERIODIC, bool MASKED, int TGT>
+__device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, int jb, BsTarget (&t)[TGT],
+                                        const BoxF& box, float kq) {
+#pragma unroll 2
     for (int k = 0; k < cnt; ++k) {
         const float4 A = T[3 * k], B = T[3 * k + 1], D = T[3 * k + 2];
-        float r1x = (A.x - rhx) + (A.w - rlx);
-        float r1y = (A.y - rhy) + (B.x - rly);
-        float r1z = (A.z - rhz) + (B.y - rlz);
-        if (PERIODIC) {
-            r1x -= box.Lx * rintf(r1x * box.iLx);
-            r1y -= box.Ly * rintf(r1y * box.iLy);
-            r1z -= box.Lz * rintf(r1z * box.iLz);
+        const float dx = B.z, dy = B.w, dz = D.x, dd = D.y;
+#pragma unroll
+        for (int u = 0; u < TGT; ++u) {
+            float r1x = (A.x - t[u].hx) + (A.w - t[u].lx);
+            float r1y = (A.y - t[u].hy) + (B.x - t[u].ly);
+            float r1z = (A.z - t[u].hz) + (B.y - t[u].lz);
+            if (PERIODIC) {
+                r1x -= box.Lx * round_fma(r1x * box.iLx);
+                r1y -= box.Ly * round_fma(r1y * box.iLy);
+                r1z -= box.Lz * round_fma(r1z * box.iLz);
+            }
+            const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
+            const float rd = r1x * dx + r1y * dy + r1z * dz;
+            const float b2 = fmaf(2.f, rd, a2) + dd;
+            const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
+            const float la = a2 * ia, lb = b2 * ib;
+            const float ab = la * lb;
+            const float s = ab + (a2 + rd);
+            const float fac = kq * (la + lb) * rcp_approx(ab * s);
+            // s <= 1e-6 ab: the target lies on the segment (or coincides with an
+            // end point), where the integral is not defined; NaN fails the test too
+            bool use = s > 1e-6f * ab;
+            if (MASKED) {
+                const int j = jb + k;
+                use = use & (j != t[u].self) & (j != t[u].prev);
+            }
+            const float c = use ? fac : 0.f;
+            t[u].vx += c * (r1y * dz - r1z * dy);
+            t[u].vy += c * (r1z * dx - r1x * dz);
+            t[u].vz += c * (r1x * dy - r1y * dx);
         }
-        const float r2x = r1x + B.z, r2y = r1y + B.w, r2z = r1z + D.x;
-        const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
-        const float b2 = r2x * r2x + r2y * r2y + r2z * r2z;
-        const float ia = rsqrtf(a2), ib = rsqrtf(b2);
-        const float la = a2 * ia, lb = b2 * ib;
-        const float ab = la * lb;
-        const float dot = r1x * r2x + r1y * r2y + r1z * r2z;
-        const float s = ab + dot;
-        const float fac = kq * (la + lb) * __frcp_rn(ab * s);
-        const int j = jb + k;
-        const bool use = (j != self) & (j != pi) & (s > 1e-6f * ab);
-        const float c = use ? fac : 0.f;
-        vx += c * (r1y * r2z - r1z * r2y);
-        vy += c * (r1z * r2x - r1x * r2z);
-        vz += c * (r1x * r2y - r1y * r2x);
     }
 }
 
@@ -114,7 +152,7 @@ __device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, i
 // host-side estimate of N.  With several splits, each item stores its partial
 // sums and the last item of a target tile adds them in split order (fixed,
 // hence deterministic) into vel; with one split the item writes vel directly.
-template <bool PERIODIC>
+template <bool PERIODIC, int TGT>
 __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev,
                                                         int* __restrict__ counters, int* __restrict__ tile_ticket,
                                                         int cap, BoxF box, float kq, float* __restrict__ part,
@@ -122,10 +160,11 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
     __shared__ __align__(128) float4 tile[2][BS_TILE * 3];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_item, s_last;
+    constexpr int TT = BS_TPB * TGT;  // targets per item
     const int N = counters[CNT_N];
     if (N <= 0) return;
-    const int ns = bs_splits(N);
-    const int ntb = (N + BS_TPB - 1) / BS_TPB;
+    const int ns = bs_splits(N, TT);
+    const int ntb = (N + TT - 1) / TT;
     const int nitems = ntb * ns;
     const int chunk = (N + ns - 1) / ns;
     if ((int)blockIdx.x >= nitems) return;
@@ -139,26 +178,28 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
     while (true) {
         __syncthreads();
         const int tb = item % ntb, split = item / ntb;
-        const int i = tb * BS_TPB + threadIdx.x;
-        const bool valid = i < N;
         const int j0 = split * chunk;
         const int j1 = min(N, j0 + chunk);
-        float rhx = 0.f, rhy = 0.f, rhz = 0.f, rlx = 0.f, rly = 0.f, rlz = 0.f;
-        int self = -1, pi = -1;
-        if (valid) {
-            const float4 a = seg[3LL * i], b = seg[3LL * i + 1];
-            rhx = a.x; rhy = a.y; rhz = a.z; rlx = a.w; rly = b.x; rlz = b.y;
-            self = i;
-            pi = prev[i];
+        BsTarget t[TGT];
+        bool own_any = false;
+#pragma unroll
+        for (int u = 0; u < TGT; ++u) {
+            const int i = tb * TT + u * BS_TPB + threadIdx.x;
+            t[u] = BsTarget{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1};
+            if (i < N) {
+                const float4 a = seg[3LL * i], b = seg[3LL * i + 1];
+                t[u].hx = a.x; t[u].hy = a.y; t[u].hz = a.z; t[u].lx = a.w; t[u].ly = b.x; t[u].lz = b.y;
+                t[u].self = i;
+                t[u].prev = prev[i];
+            }
         }
-        float vx = 0.f, vy = 0.f, vz = 0.f;
         const int ntiles = j1 > j0 ? (j1 - j0 + BS_TILE - 1) / BS_TILE : 0;
         if (threadIdx.x == 0 && ntiles > 0) issue_tile(tile[used & 1], seg, j0, min(BS_TILE, j1 - j0), &bar[used & 1]);
-        for (int t = 0; t < ntiles; ++t) {
-            const uint32_t u = used + (uint32_t)t;
+        for (int tt = 0; tt < ntiles; ++tt) {
+            const uint32_t u = used + (uint32_t)tt;
             const int b = (int)(u & 1u);
-            if (threadIdx.x == 0 && t + 1 < ntiles) {
-                const int jn = j0 + (t + 1) * BS_TILE;
+            if (threadIdx.x == 0 && tt + 1 < ntiles) {
+                const int jn = j0 + (tt + 1) * BS_TILE;
                 issue_tile(tile[b ^ 1], seg, jn, min(BS_TILE, j1 - jn), &bar[b ^ 1]);
             }
             const bool ok = mbar_wait_bounded(&bar[b], (u >> 1) & 1u);
@@ -166,27 +207,42 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
                 if (threadIdx.x == 0) {
                     atomicOr(&counters[CNT_STATUS], ST_TIMEOUT);
                     // let a copy still in flight land before the block's shared memory goes away
-                    if (t + 1 < ntiles) mbar_wait_bounded(&bar[b ^ 1], ((u + 1u) >> 1) & 1u);
+                    if (tt + 1 < ntiles) mbar_wait_bounded(&bar[b ^ 1], ((u + 1u) >> 1) & 1u);
                 }
                 return;
             }
-            const int jb = j0 + t * BS_TILE;
-            bs_tile<PERIODIC>(tile[b], min(BS_TILE, j1 - jb), jb, self, pi, rhx, rhy, rhz, rlx, rly, rlz, box, kq, vx,
-                              vy, vz);
+            const int jb = j0 + tt * BS_TILE;
+            const int cnt = min(BS_TILE, j1 - jb);
+            own_any = false;
+#pragma unroll
+            for (int v = 0; v < TGT; ++v)
+                own_any |= (unsigned)(t[v].self - jb) < (unsigned)cnt || (unsigned)(t[v].prev - jb) < (unsigned)cnt;
+            if (__any_sync(0xffffffffu, own_any))
+                bs_tile<PERIODIC, true, TGT>(tile[b], cnt, jb, t, box, kq);
+            else
+                bs_tile<PERIODIC, false, TGT>(tile[b], cnt, jb, t, box, kq);
             __syncthreads();
         }
         used += (uint32_t)ntiles;
         if (ns == 1) {
-            if (valid) {
-                vel[i] = vx;
-                vel[(long long)cap + i] = vy;
-                vel[2LL * cap + i] = vz;
+#pragma unroll
+            for (int v = 0; v < TGT; ++v) {
+                const int i = t[v].self;
+                if (i >= 0) {
+                    vel[i] = t[v].vx;
+                    vel[(long long)cap + i] = t[v].vy;
+                    vel[2LL * cap + i] = t[v].vz;
+                }
             }
         } else {
-            if (valid) {
-                part[((long long)split * 3 + 0) * cap + i] = vx;
-                part[((long long)split * 3 + 1) * cap + i] = vy;
-                part[((long long)split * 3 + 2) * cap + i] = vz;
+#pragma unroll
+            for (int v = 0; v < TGT; ++v) {
+                const int i = t[v].self;
+                if (i >= 0) {
+                    part[((long long)split * 3 + 0) * cap + i] = t[v].vx;
+                    part[((long long)split * 3 + 1) * cap + i] = t[v].vy;
+                    part[((long long)split * 3 + 2) * cap + i] = t[v].vz;
+                }
             }
             __threadfence();
             __syncthreads();
@@ -194,14 +250,18 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
             __syncthreads();
             if (s_last) {
                 __threadfence();
-                if (valid) {
-                    float a[3] = {0.f, 0.f, 0.f};
-                    for (int m = 0; m < ns; ++m)
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) a[k] += __ldcg(&part[((long long)m * 3 + k) * cap + i]);
-                    vel[i] = a[0];
-                    vel[(long long)cap + i] = a[1];
-                    vel[2LL * cap + i] = a[2];
+                for (int v = 0; v < TGT; ++v) {
+                    const int i = t[v].self;
+                    if (i >= 0) {
+                        float a[3] = {0.f, 0.f, 0.f};
+                        for (int m = 0; m < ns; ++m)
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) a[k] += __ldcg(&part[((long long)m * 3 + k) * cap + i]);
+                        vel[i] = a[0];
+                        vel[(long long)cap + i] = a[1];
+                        vel[2LL * cap + i] = a[2];
+                    }
                 }
                 if (threadIdx.x == 0) tile_ticket[tb] = 0;
             }
@@ -242,7 +302,7 @@ __global__ void k_bs_prep(Grid g, const double* __restrict__ pos, const int* __r
     }
     seg[3LL * i] = make_float4(hi[0], hi[1], hi[2], lo[0]);
     seg[3LL * i + 1] = make_float4(lo[1], lo[2], d[0], d[1]);
-    seg[3LL * i + 2] = make_float4(d[2], 0.f, 0.f, 0.f);
+    seg[3LL * i + 2] = make_float4(d[2], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], 0.f, 0.f);
 }
 
 BoxF make_box(const Grid& g) {
@@ -261,27 +321,39 @@ BoxF make_box(const Grid& g) {
 int bs_max_splits(int cap) {
     int m = 1;
     for (int n = 1; n <= cap; n += (n < 8192 ? 1 : 128)) {
-        const int k = bs_splits(n);
+        const int k = bs_splits(n, BS_TPB);
         if (k > m) m = k;
     }
     return m;
 }
 
+template <int TGT>
+void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int* cnt, int* tile_ticket, int cap, int n,
+               float* part, float* vel, cudaStream_t s) {
+    // enough blocks for every item of about n points (at most 8 per SM); more
+    // points than that are still covered by the blocks' item loop
+    constexpr int TT = BS_TPB * TGT;
+    const int items = ((n + TT - 1) / TT) * bs_splits(n, TT);
+    const int grid = items < 8 * 152 ? items : 8 * 152;
+    const BoxF box = make_box(g);
+    if (g.wall[0] && g.wall[1] && g.wall[2])
+        k_biot_savart<false, TGT><<<grid, BS_TPB, 0, s>>>(seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
+    else
+        k_biot_savart<true, TGT><<<grid, BS_TPB, 0, s>>>(seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
+}
+
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
                         int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s) {
     if (cap <= 0) return;
-    // enough blocks for every item of about n_hint points (at most 6 per SM);
-    // more points than that are still covered by the blocks' item loop
     const int n = n_hint > 0 ? (n_hint < cap ? n_hint : cap) : 1;
-    const int items = ((n + BS_TPB - 1) / BS_TPB) * bs_splits(n);
-    const int grid = items < 6 * 152 ? items : 6 * 152;
     const float kq = (float)(kappa / (4.0 * 3.14159265358979323846));
-    const BoxF box = make_box(g);
     int* cnt = const_cast<int*>(counters);
-    if (g.wall[0] && g.wall[1] && g.wall[2])
-        k_biot_savart<false><<<grid, BS_TPB, 0, s>>>(seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
+    // two targets per thread once there are enough points to fill the GPU with
+    // them (each shared-memory record is then read once for both)
+    if (n >= 2 * BS_TPB * 152 * 2)
+        bs_launch<2>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, s);
     else
-        k_biot_savart<true><<<grid, BS_TPB, 0, s>>>(seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
+        bs_launch<1>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, s);
 }
 
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
     const int nx = P.g.nx, ny = P.g.ny;
     const int C = (int)P.g.ncell;
     const int z = blockIdx.y;
-    const int xy = blockIdx.x * LBM_BLOCK + threadIdx.x;
+    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
     float s_drho = 0.f, s_uz = 0.f, s_u2 = 0.f;
     if (xy < nx * ny) {
         const int y = xy / nx, x = xy - y * nx;
@@ -246,8 +246,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0, m = 0.0;
-#pragma unroll
-        for (int w = 0; w < LBM_BLOCK / 32; ++w) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             a += red[0][w];
             b += red[1][w];
             m = fmax(m, red[2][w]);
@@ -333,6 +332,259 @@ __global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ par
         if (!isfinite(m) || !isfinite(s_mass[0])) st |= ST_NAN;
         if (st) atomicOr(&P.counters[CNT_STATUS], st);
         P.counters[CNT_PLANES] = 0;
+    }
+}
+
+// K1, vectorised: each thread owns VEC consecutive x-cells of one row and
+// loads every population row segment with one VEC-wide load.  The +-x
+// shifted populations come from the neighbouring lane (the previous or next
+// VEC cells of the same row) by a shuffle, with a scalar load only at warp
+// and row edges; links leaving through a wall are bounced back from the
+// cell's own opposite population.  Requires nx % VEC == 0.
+template <int VEC>
+struct VecT;
+template <>
+struct VecT<2> {
+    using T = float2;
+};
+template <>
+struct VecT<4> {
+    using T = float4;
+};
+
+template <int VEC>
+__device__ __forceinline__ void vload(const float* __restrict__ p, float (&v)[VEC]) {
+    const typename VecT<VEC>::T t = __ldg(reinterpret_cast<const typename VecT<VEC>::T*>(p));
+    const float* q = reinterpret_cast<const float*>(&t);
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) v[c] = q[c];
+}
+
+template <int VEC>
+__device__ __forceinline__ void vstore(float* p, const float (&v)[VEC]) {
+    typename VecT<VEC>::T t;
+    float* q = reinterpret_cast<float*>(&t);
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) q[c] = v[c];
+    *reinterpret_cast<typename VecT<VEC>::T*>(p) = t;
+}
+
+template <bool WX, bool WY, bool WZ, int VEC>
+__global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ fin, float* __restrict__ fout,
+                                                      const float* __restrict__ F, float* __restrict__ U,
+                                                      const uint8_t* __restrict__ fmask,
+                                                      const uint8_t* __restrict__ umask, double* __restrict__ part,
+                                                      LbmParams P) {
+    const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz, nxy = nx * ny;
+    const int C = (int)P.g.ncell;
+    const int nq = nx / VEC;  // cell groups per row
+    const int z = blockIdx.y;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool live = q < nq * ny;
+    const int y = live ? q / nq : 0;
+    const int x0 = live ? (q - y * nq) * VEC : 0;
+    const int cell0 = z * nxy + y * nx + x0;
+    // source rows for c_y, c_z = -1, 0, +1 (index c + 1); out = beyond a wall
+    int ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+    bool oym = false, oyp = false, ozm = false, ozp = false;
+    if (ym < 0) { if (WY) oym = true; else ym += ny; }
+    if (yp >= ny) { if (WY) oyp = true; else yp -= ny; }
+    if (zm < 0) { if (WZ) ozm = true; else zm += nz; }
+    if (zp >= nz) { if (WZ) ozp = true; else zp -= nz; }
+    const int yo[3] = {yp * nx, y * nx, ym * nx};
+    const int zo[3] = {zp * nxy, z * nxy, zm * nxy};
+    const bool oy[3] = {oyp, false, oym};
+    const bool oz[3] = {ozp, false, ozm};
+    const bool row_first = x0 == 0, row_last = x0 + VEC == nx;
+
+    // Phase 1: every load of the cell group is issued before any is used:
+    // the VEC-wide row segments and, for edge lanes, the scalar value beyond
+    // the segment that the neighbouring lane cannot supply.
+    float g[19][VEC];
+    float edge[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int row = i * C + zo[CZ(i) + 1] + yo[CY(i) + 1];
+        const bool rowout = (WY && oy[CY(i) + 1]) || (WZ && oz[CZ(i) + 1]);
+        if (live) {
+            vload<VEC>(rowout ? fin + opp(i) * C + cell0 : fin + row + x0, g[i]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) g[i][c] = 0.f;
+        }
+        edge[i] = 0.f;
+        if (CX(i) == 1) {
+            const bool need = live && !rowout && (lane == 0 || row_first);
+            const int a = !row_first ? row + x0 - 1 : (WX ? opp(i) * C + cell0 : row + nx - 1);
+            if (need) edge[i] = __ldg(&fin[a]);
+        } else if (CX(i) == -1) {
+            const bool need = live && !rowout && (lane == 31 || row_last);
+            const int a = !row_last ? row + x0 + VEC : (WX ? opp(i) * C + cell0 + VEC - 1 : row);
+            if (need) edge[i] = __ldg(&fin[a]);
+        }
+    }
+    // Phase 2: moving-wall terms, then the +-x shifts through the neighbouring lanes.
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const bool rowout = (WY && oy[CY(i) + 1]) || (WZ && oz[CZ(i) + 1]);
+        if (WZ && CZ(i) != 0 && oz[CZ(i) + 1]) {
+            const float h = 6.f * wgt(i) * P.rho0 * (float)CZ(i) * P.heater;
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) g[i][c] += h;
+        }
+        if (CX(i) == 1) {
+            // cells x0..x0+VEC-1 pull from x0-1..x0+VEC-2
+            const float nb = __shfl_up_sync(0xffffffffu, g[i][VEC - 1], 1);
+            const float left = (lane == 0 || row_first) ? edge[i] : nb;
+            if (!rowout) {
+#pragma unroll
+                for (int c = VEC - 1; c > 0; --c) g[i][c] = g[i][c - 1];
+                g[i][0] = left;
+            }
+        } else if (CX(i) == -1) {
+            // cells x0..x0+VEC-1 pull from x0+1..x0+VEC
+            const float nb = __shfl_down_sync(0xffffffffu, g[i][0], 1);
+            const float right = (lane == 31 || row_last) ? edge[i] : nb;
+            if (!rowout) {
+#pragma unroll
+                for (int c = 0; c < VEC - 1; ++c) g[i][c] = g[i][c + 1];
+                g[i][VEC - 1] = right;
+            }
+        }
+    }
+
+    float s_drho = 0.f, s_uz = 0.f, s_u2 = 0.f;
+    if (live) {
+        const int tile = tile_of(P.g, x0, y, z);  // VEC <= 8 cells share a tile
+        const bool factive = fmask[tile] != 0;
+        const bool force = factive || P.body_on;
+        const bool uact = umask[tile] != 0;
+        float Fx[VEC], Fy[VEC], Fz[VEC];
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) {
+            Fx[c] = P.body[0];
+            Fy[c] = P.body[1];
+            Fz[c] = P.body[2];
+        }
+        if (factive) {
+            float a[VEC];
+            vload<VEC>(F + cell0, a);
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) Fx[c] += a[c];
+            vload<VEC>(F + C + cell0, a);
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) Fy[c] += a[c];
+            vload<VEC>(F + 2 * C + cell0, a);
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) Fz[c] += a[c];
+        }
+        float drho[VEC], ux[VEC], uy[VEC], uz[VEC];
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) {
+            // Eqs. 5-6 with the half-force shift
+            float d = P.dr0, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int i = 0; i < 19; ++i) {
+                d += g[i][c];
+                if (CX(i)) jx += (float)CX(i) * g[i][c];
+                if (CY(i)) jy += (float)CY(i) * g[i][c];
+                if (CZ(i)) jz += (float)CZ(i) * g[i][c];
+            }
+            const float inv = 1.f / (P.rho0 + d);
+            drho[c] = d;
+            ux[c] = (jx + 0.5f * Fx[c]) * inv;
+            uy[c] = (jy + 0.5f * Fy[c]) * inv;
+            uz[c] = (jz + 0.5f * Fz[c]) * inv;
+        }
+        if (uact) {
+            vstore<VEC>(U + cell0, ux);
+            vstore<VEC>(U + C + cell0, uy);
+            vstore<VEC>(U + 2 * C + cell0, uz);
+        }
+        const float om = P.omega;
+        const bool pinned = P.pin_on && z == 0;
+        float A[VEC], B3[VEC], B45[VEC], uF[VEC];
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) {
+            const float rho = P.rho0 + drho[c];
+            const float usq = ux[c] * ux[c] + uy[c] * uy[c] + uz[c] * uz[c];
+            A[c] = drho[c] - 1.5f * rho * usq;
+            B3[c] = 3.f * rho;
+            B45[c] = 4.5f * rho;
+            uF[c] = ux[c] * Fx[c] + uy[c] * Fy[c] + uz[c] * Fz[c];
+            s_drho += drho[c];
+            s_uz += uz[c];
+            s_u2 = fmaxf(s_u2, (usq == usq) ? usq : INFINITY);
+        }
+        // rest population
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) {
+            float out = g[0][c] + om * (wgt(0) * A[c] + P.dw[0] - g[0][c]);
+            if (force) out += P.pref * wgt(0) * (-3.f * uF[c]);
+            if (pinned) out = wgt(0) * (drho[c] - 1.5f * (P.rho0 + drho[c]) * P.pin * P.pin) + P.dw[0];
+            g[0][c] = out;
+        }
+        vstore<VEC>(fout + cell0, g[0]);
+        // opposite pairs (i, i+1): even parts of Eqs. 7 and 13 shared, odd parts change sign
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            const int j = i + 1;
+            const float w = wgt(i);
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) {
+                const float cu = (float)CX(i) * ux[c] + (float)CY(i) * uy[c] + (float)CZ(i) * uz[c];
+                const float sym = w * (A[c] + B45[c] * cu * cu) + P.dw[wclass(i)];
+                const float asym = w * B3[c] * cu;
+                float oi = g[i][c] + om * (sym + asym - g[i][c]);
+                float oj = g[j][c] + om * (sym - asym - g[j][c]);
+                if (force) {
+                    const float cF = (float)CX(i) * Fx[c] + (float)CY(i) * Fy[c] + (float)CZ(i) * Fz[c];
+                    const float fs = P.pref * w * (9.f * cu * cF - 3.f * uF[c]);
+                    const float fa = P.pref * w * 3.f * cF;
+                    oi += fs + fa;
+                    oj += fs - fa;
+                }
+                if (pinned) {
+                    const float cp = (float)CZ(i) * P.pin;
+                    const float rho = P.rho0 + drho[c];
+                    const float ps =
+                        w * (drho[c] + rho * (4.5f * cp * cp - 1.5f * P.pin * P.pin)) + P.dw[wclass(i)];
+                    const float pa = w * B3[c] * cp;
+                    oi = ps + pa;
+                    oj = ps - pa;
+                }
+                g[i][c] = oi;
+                g[j][c] = oj;
+            }
+            vstore<VEC>(fout + i * C + cell0, g[i]);
+            vstore<VEC>(fout + j * C + cell0, g[j]);
+        }
+    }
+    // per-block partials for Eq. 18 and the mass / Mach checks
+    __shared__ double red[3][4];
+    s_drho = warp_reduce<0>(s_drho);
+    s_uz = warp_reduce<0>(s_uz);
+    s_u2 = warp_reduce<1>(s_u2);
+    const int wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = s_drho;
+        red[1][wid] = s_uz;
+        red[2][wid] = s_u2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, m = 0.0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            a += red[0][w];
+            b += red[1][w];
+            m = fmax(m, red[2][w]);
+        }
+        double* o = part + ((long long)z * gridDim.x + blockIdx.x) * 3;
+        o[0] = a;
+        o[1] = b;
+        o[2] = m;
     }
 }
 
@@ -447,9 +699,18 @@ __global__ void k_zero_force(Grid g, float* __restrict__ F, uint8_t* __restrict_
 template <bool WX, bool WY, bool WZ>
 void lbm_dispatch(const LbmParams& P, const float* fin, float* fout, const float* F, float* U, const uint8_t* fmask,
                   const uint8_t* umask, double* part, cudaStream_t s) {
-    const int bpp = (P.g.nx * P.g.ny + LBM_BLOCK - 1) / LBM_BLOCK;
-    dim3 grid(bpp, P.g.nz);
-    k_lbm_step<WX, WY, WZ><<<grid, LBM_BLOCK, 0, s>>>(fin, fout, F, U, fmask, umask, part, P);
+    const int nxy = P.g.nx * P.g.ny;
+    if (P.vec == 4 || P.vec == 2) {
+        const int groups = nxy / P.vec;
+        dim3 grid((groups + 127) / 128, P.g.nz);
+        if (P.vec == 4)
+            k_lbm_step_vec<WX, WY, WZ, 4><<<grid, 128, 0, s>>>(fin, fout, F, U, fmask, umask, part, P);
+        else
+            k_lbm_step_vec<WX, WY, WZ, 2><<<grid, 128, 0, s>>>(fin, fout, F, U, fmask, umask, part, P);
+        return;
+    }
+    dim3 grid((nxy + P.block - 1) / P.block, P.g.nz);
+    k_lbm_step<WX, WY, WZ><<<grid, P.block, 0, s>>>(fin, fout, F, U, fmask, umask, part, P);
 }
 
 template <bool WX, bool WY, bool WZ>
@@ -498,8 +759,14 @@ void launch_unshift(const LbmParams& P, const float* in, float* out, int directi
     k_unshift<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(in, out, P, direction);
 }
 
+int lbm_blocks_per_plane(const LbmParams& P) {
+    const int nxy = P.g.nx * P.g.ny;
+    if (P.vec == 4 || P.vec == 2) return (nxy / P.vec + 127) / 128;
+    return (nxy + P.block - 1) / P.block;
+}
+
 void launch_plane_vs(const LbmParams& P, const double* part, cudaStream_t s) {
-    const int bpp = (P.g.nx * P.g.ny + LBM_BLOCK - 1) / LBM_BLOCK;
+    const int bpp = lbm_blocks_per_plane(P);
     k_plane_vs<<<(P.g.nz + 7) / 8, 256, 0, s>>>(part, bpp, P);
 }
 

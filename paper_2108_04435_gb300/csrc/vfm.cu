@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double
     }
     seg[3LL * i] = make_float4(hi[0], hi[1], hi[2], lo[0]);
     seg[3LL * i + 1] = make_float4(lo[1], lo[2], b[0], b[1]);
-    seg[3LL * i + 2] = make_float4(b[2], 0.f, 0.f, 0.f);
+    seg[3LL * i + 2] = make_float4(b[2], b[0] * b[0] + b[1] * b[1] + b[2] * b[2], 0.f, 0.f);
 }
 
 // Equation of motion (Eq. 4) at one RK4 stage, in FP32, with the

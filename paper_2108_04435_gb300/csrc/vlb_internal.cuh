@@ -69,6 +69,8 @@ struct LbmParams {
     float dw[3];        // w_i rho0 - s_i for the rest, axis and diagonal classes (exact in double, then float)
     int body_on;
     int pin_on;
+    int vec;            // cells per thread of the stream-collide kernel (4, 2, or 1 = scalar kernel)
+    int block;          // threads per block of the scalar kernel (128 or 256)
     double inv_ratio;   // rho_n / rho_s
     // device buffers of the fused per-plane reduction (Eq. 18, mass, Mach)
     int* plane_ticket;  // [nz] blocks done per plane, back to 0 after the plane is reduced
@@ -89,13 +91,13 @@ struct VfmParams {
     int couple, force_form;
 };
 
-// Biot-Savart source splits for N points: enough (target tile, split) work
-// items to fill the GPU (~4 per SM on 152 SMs), at least 64 segments per
-// split.  Used by the Biot-Savart kernel and by the reduction that reads its
-// partial sums, so both derive it from the same device-side N.
-__host__ __device__ inline int bs_splits(int N) {
+// Biot-Savart source splits for N points and target tiles of `tile` points:
+// enough (target tile, split) work items to fill the GPU (~4 per SM on 152
+// SMs), at least 64 segments per split.  The kernel derives it from the
+// device-side N, so it needs no host estimate.
+__host__ __device__ inline int bs_splits(int N, int tile) {
     const int n = N > 0 ? N : 1;
-    const int tb = (n + 127) / 128;
+    const int tb = (n + tile - 1) / tile;
     int ns = (4 * 152 + tb - 1) / tb;
     const int by_chunk = (n + 63) / 64;
     if (ns > by_chunk) ns = by_chunk;
@@ -157,6 +159,7 @@ void launch_lbm_init(const LbmParams& P, float* f, float* U, const double init_u
 void launch_lbm_step(const LbmParams& P, const float* fin, float* fout, const float* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
 void launch_plane_vs(const LbmParams& P, const double* part, cudaStream_t s);
+int lbm_blocks_per_plane(const LbmParams& P);
 void launch_moments(const LbmParams& P, const float* f, const float* F, const uint8_t* fmask, float* rho,
                     float* U, cudaStream_t s);
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,
