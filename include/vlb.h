@@ -175,6 +175,23 @@ size_t vlb_biot_savart_scratch_bytes(int32_t n);
 int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next, int32_t n,
                     float* vel, void* scratch, size_t scratch_bytes, void* stream);
 
+/* Allocation-free variant of vlb_biot_savart (the paper has no counterpart;
+ * it exists for callers of this library that may not allocate device memory
+ * while they run, e.g. hosts that only hand out pre-registered buffers or
+ * code that must not trigger the device synchronisation cudaMalloc implies).
+ * Same arguments and result as vlb_biot_savart, without the scratch buffer:
+ * the scratch lives in a fixed 6 MiB file-scope device array that every GPU
+ * loading this library holds until the process exits, and no cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ *   n        at most 65536 points; larger n returns VLB_ERR_INVALID_ARG
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls whose work overlaps on the GPU (other streams, other threads) race:
+ * serialise them.  Runs on `stream`; does not wait. */
+int vlb_biot_savart_noalloc(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -216,6 +216,51 @@ bool valid_axis_params(const vlb_params* p, std::string* why) {
 
 }  // namespace
 
+namespace vlb {
+
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
+// Stand-alone Biot-Savart velocity on caller-provided device buffers; the
+// scratch layout is counters | prev | source records | split partials |
+// per-tile tickets, each 256-byte aligned.  Allocates nothing.
+int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel, void* scratch,
+                  size_t scratch_bytes, void* stream) {
+    if (!p || n < 0 || (n > 0 && (!pos || !next || !vel || !scratch)))
+        return fail(VLB_ERR_INVALID_ARG, "bad Biot-Savart arguments");
+    if (n == 0) return VLB_OK;
+    for (int a = 0; a < 3; ++a)
+        if (p->n[a] < 1 || (p->wall[a] != 0 && p->wall[a] != 1)) return fail(VLB_ERR_INVALID_ARG, "bad box");
+    if (scratch_bytes < vlb_biot_savart_scratch_bytes(n)) return fail(VLB_ERR_INVALID_ARG, "scratch too small");
+    if (((uintptr_t)scratch & 255u) != 0) return fail(VLB_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+    Grid g;
+    g.nx = p->n[0];
+    g.ny = p->n[1];
+    g.nz = p->n[2];
+    for (int a = 0; a < 3; ++a) g.wall[a] = p->wall[a];
+    g.ncell = (long long)g.nx * g.ny * g.nz;
+    g.tnx = g.tny = g.tnz = 1;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char* base = (char*)scratch;
+    int* counters = (int*)base;
+    base += up(sizeof(int) * CNT_COUNT);
+    int* prev = (int*)base;
+    base += up(sizeof(int) * (size_t)n);
+    float4* seg = (float4*)base;
+    base += up(sizeof(float4) * 3 * (size_t)n);
+    float* bsp = (float*)base;
+    base += up(sizeof(float) * 3 * (size_t)n * (size_t)bs_splits(n, BS_TPB));
+    int* tickets = (int*)base;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(tickets, 0, sizeof(int) * (size_t)((n + BS_TPB - 1) / BS_TPB), s);
+    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, s);
+    launch_biot_savart(g, p->kappa, seg, prev, counters, tickets, n, n, bsp, vel, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "Biot-Savart launch");
+    return VLB_OK;
+}
+
+}  // namespace vlb
+
 extern "C" {
 
 const char* vlb_last_error(void) { return g_last_error.c_str(); }
@@ -671,36 +716,7 @@ size_t vlb_biot_savart_scratch_bytes(int32_t n) {
 
 int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel, void* scratch,
                     size_t scratch_bytes, void* stream) {
-    if (!p || n < 0 || (n > 0 && (!pos || !next || !vel || !scratch)))
-        return fail(VLB_ERR_INVALID_ARG, "bad Biot-Savart arguments");
-    if (n == 0) return VLB_OK;
-    if (scratch_bytes < vlb_biot_savart_scratch_bytes(n)) return fail(VLB_ERR_INVALID_ARG, "scratch too small");
-    if (((uintptr_t)scratch & 255u) != 0) return fail(VLB_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
-    Grid g;
-    g.nx = p->n[0];
-    g.ny = p->n[1];
-    g.nz = p->n[2];
-    for (int a = 0; a < 3; ++a) g.wall[a] = p->wall[a];
-    g.ncell = (long long)g.nx * g.ny * g.nz;
-    g.tnx = g.tny = g.tnz = 1;
-    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    char* base = (char*)scratch;
-    int* counters = (int*)base;
-    base += up(sizeof(int) * CNT_COUNT);
-    int* prev = (int*)base;
-    base += up(sizeof(int) * (size_t)n);
-    float4* seg = (float4*)base;
-    base += up(sizeof(float4) * 3 * (size_t)n);
-    float* bsp = (float*)base;
-    base += up(sizeof(float) * 3 * (size_t)n * (size_t)bs_splits(n, BS_TPB));
-    int* tickets = (int*)base;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaMemsetAsync(tickets, 0, sizeof(int) * (size_t)((n + BS_TPB - 1) / BS_TPB), s);
-    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, s);
-    launch_biot_savart(g, p->kappa, seg, prev, counters, tickets, n, n, bsp, vel, s);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "Biot-Savart launch");
-    return VLB_OK;
+    return vlb::bs_standalone(p, pos, next, n, vel, scratch, scratch_bytes, stream);
 }
 
 }  // extern "C"

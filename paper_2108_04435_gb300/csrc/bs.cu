@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "vlb_internal.cuh"
 
 namespace vlb {
@@ -362,3 +364,60 @@ void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next
 }
 
 }  // namespace vlb
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the stand-alone Biot-Savart entry point, for
+// callers that may not allocate device memory while they run (for example a
+// host framework that only hands out pre-registered buffers, or code running
+// where cudaMalloc would synchronise the device).  Its scratch space is a
+// file-scope device array of fixed size that every GPU loading this library
+// holds until the process exits.
+
+namespace {
+
+constexpr int NOALLOC_MAX_POINTS = 65536;
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(6) << 20;  // >= vlb_biot_savart_scratch_bytes(65536)
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_bs_scratch[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_bs_scratch_mu;
+void* g_bs_scratch_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_bs_scratch on the current device.  In host code the
+// name g_bs_scratch is only a host-side stand-in, so the address is asked
+// from the runtime once per device (with that device current) and cached.
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return vlb::set_error(VLB_ERR_CUDA, "no usable current CUDA device");
+    }
+    std::lock_guard<std::mutex> lock(g_bs_scratch_mu);
+    if (!g_bs_scratch_addr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_bs_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return vlb::set_error(VLB_ERR_CUDA, "cudaGetSymbolAddress of the Biot-Savart scratch failed");
+        }
+        g_bs_scratch_addr[dev] = ptr;
+    }
+    *out = g_bs_scratch_addr[dev];
+    return VLB_OK;
+}
+
+}  // namespace
+
+extern "C" int vlb_biot_savart_noalloc(const vlb_params* p, const double* pos, const int32_t* next, int32_t n,
+                                       float* vel, void* stream) {
+    if (n > NOALLOC_MAX_POINTS)
+        return vlb::set_error(VLB_ERR_INVALID_ARG,
+                              "vlb_biot_savart_noalloc: n exceeds its 65536-point limit (use vlb_biot_savart)");
+    if (vlb_biot_savart_scratch_bytes(n) > NOALLOC_SCRATCH_BYTES)
+        return vlb::set_error(VLB_ERR_INVALID_ARG, "vlb_biot_savart_noalloc: scratch array too small");
+    void* scratch = nullptr;
+    const int rc = noalloc_scratch(&scratch);
+    if (rc != VLB_OK) return rc;
+    return vlb::bs_standalone(p, pos, next, n, vel, scratch, NOALLOC_SCRATCH_BYTES, stream);
+}

@@ -183,6 +183,11 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
                                int* counters, cudaStream_t s);
 
+// abi.cu
+int set_error(int code, const char* msg);
+int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel, void* scratch,
+                  size_t scratch_bytes, void* stream);
+
 // topo.cu
 void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s);
 void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, cudaStream_t s);

@@ -24,7 +24,8 @@ FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_FDEV = 6, 7, 8, 9
 
 EXPORTS = ["vlb_create_channel", "vlb_seed_vortices", "vlb_step", "vlb_run_phases", "vlb_read_fields",
            "vlb_write_fields", "vlb_line_length", "vlb_destroy", "vlb_last_error", "vlb_set_timing",
-           "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart", "vlb_set_graphs"]
+           "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart", "vlb_set_graphs",
+           "vlb_biot_savart_noalloc"]
 
 
 class Params(C.Structure):
@@ -82,6 +83,7 @@ def lib():
         L.vlb_biot_savart_scratch_bytes.argtypes = [C.c_int32]
         L.vlb_biot_savart_scratch_bytes.restype = C.c_size_t
         L.vlb_biot_savart.argtypes = [C.POINTER(Params), vp, vp, C.c_int32, vp, vp, C.c_size_t, vp]
+        L.vlb_biot_savart_noalloc.argtypes = [C.POINTER(Params), vp, vp, C.c_int32, vp, vp]
         _lib = L
     return _lib
 
@@ -230,3 +232,11 @@ def biot_savart(params: dict, pos_dev: int, next_dev: int, n: int, vel_dev: int,
 
 def biot_savart_scratch_bytes(n: int) -> int:
     return int(lib().vlb_biot_savart_scratch_bytes(n))
+
+
+def biot_savart_noalloc(params: dict, pos_dev: int, next_dev: int, n: int, vel_dev: int, stream: int):
+    """Allocation-free stand-alone Biot-Savart velocity (device pointers as
+    ints; at most 65536 points; calls on overlapping streams race)."""
+    p = make_params(params)
+    check(lib().vlb_biot_savart_noalloc(C.byref(p), C.c_void_p(pos_dev), C.c_void_p(next_dev), n,
+                                        C.c_void_p(vel_dev), C.c_void_p(stream)))
