@@ -219,9 +219,9 @@ def run_vlb(args, ws, rank, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded rings, lattice initialised at uniform equilibrium)",
-        "config": {"workload": f"{args.config}: closed channel {p['n'][0]}x{p['n'][1]}x{p['n'][2]} D3Q19, "
-                               f"walls on all sides, heater v_n={p['heater_vn']}, T=1.9 K, "
-                               f"{len(nxt)} seeded filament points in 20 rings",
+        "config": {"workload": f"{args.config}: D3Q19 {p['n'][0]}x{p['n'][1]}x{p['n'][2]}, walls "
+                               f"{tuple(p['wall'])} (1 = bounce-back), heater v_n={p['heater_vn']}, "
+                               f"alpha={p['alpha']}, {len(nxt)} seeded filament points on rings",
                    "cells": cells, "filament_points_start": int(len(nxt)),
                    "filament_points_timed": [int(n_before), int(n_after)],
                    "parallelism": f"replicas x{ws}",
