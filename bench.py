@@ -29,7 +29,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 DEFAULT_CONFIG = "channel64x64x256"
-BYTES_PER_CELL = 152  # 19 populations x 4 B read + 19 x 4 B written per cell and pass
+BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76}  # 19 populations read + 19 written per cell and pass
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 LAUNCHES_PER_STEP = 23  # kernels of one coupled step (1 RK4 sub-step), see the design doc
 
 
@@ -137,7 +138,9 @@ def run_vlb(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     p, xyz, nxt = configs.config(args.config, seed=rank)
+    p["storage"] = STORAGE[args.storage]
     cells = p["n"][0] * p["n"][1] * p["n"][2]
+    bpc = BYTES_PER_CELL[args.storage]
 
     # --- device-resident run: inputs in HBM before the timed region; each step
     # is replayed from the CUDA graph the library captures on first use
@@ -204,8 +207,8 @@ def run_vlb(args, ws, rank, local):
 
     pk, pk_kind = peaks()
     k1_avg_s = (k1_ms / 1e3) / max(k1_n, 1)
-    achieved = BYTES_PER_CELL * cells / k1_avg_s / 1e9 if k1_n else None
-    traffic = k1_traffic(args.config)
+    achieved = bpc * cells / k1_avg_s / 1e9 if k1_n else None
+    traffic = k1_traffic(args.config) if args.storage == "f32" else None
     line = {
         "metric": "coupled-step MLUPS",
         "value": round(mlups, 2),
@@ -218,6 +221,7 @@ def run_vlb(args, ws, rank, local):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
+        "storage": args.storage,
         "data": "synthetic (seeded rings, lattice initialised at uniform equilibrium)",
         "config": {"workload": f"{args.config}: D3Q19 {p['n'][0]}x{p['n'][1]}x{p['n'][2]}, walls "
                                f"{tuple(p['wall'])} (1 = bounce-back), heater v_n={p['heater_vn']}, "
@@ -236,7 +240,7 @@ def run_vlb(args, ws, rank, local):
                      "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
                      "peak_source": f"{pk_kind} hbm_gbs (copy bandwidth)",
-                     "traffic": traffic, "algorithmic_bytes_per_launch": BYTES_PER_CELL * cells,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bpc * cells,
                      "avg_launch_us": round(k1_avg_s * 1e6, 3), "launches": k1_n},
         "clocks": clk,
     }
@@ -300,6 +304,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--config", default=DEFAULT_CONFIG)
     ap.add_argument("--impl", default="vlb", choices=["vlb", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage (arithmetic is FP32 in all)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -67,7 +67,7 @@ typedef struct {
     int32_t couple;          /* 1: spread the mutual-friction reaction onto the lattice (Eqs. 10-11) */
     int32_t force_form;      /* 0: f of Eq. 10 as printed; 1: f = rho_s kappa (rhs of Eq. 10) x s' */
     int32_t max_points;      /* filament point capacity (device arrays are sized by it) */
-    int32_t reserved;        /* must be 0 */
+    int32_t storage;         /* population storage: VLB_STORE_F32 (0), VLB_STORE_F16 (1) or VLB_STORE_BF16 (2) */
     double  tau, rho0;       /* BGK relaxation time (> 1/2, Eq. 8) and reference density */
     double  body_force[3];   /* uniform body force added to the force grid (0 in the paper's runs) */
     double  heater_vn;       /* Sec. IV heater: normal velocity injected at the low z face and removed at the high one */
@@ -76,6 +76,11 @@ typedef struct {
     double  kappa, alpha, alpha_p, rho_s_over_rho_n, core_a; /* circulation, Eq. 4 friction, density ratio, core radius */
     double  dxi_min, dxi_max;                                /* remeshing interval (Sec. III: 0.70, 0.95) */
 } vlb_params;
+
+/* Population storage formats (vlb_params.storage).  All three store the
+ * deviation f_i - w_i rho0 and compute in FP32: F32 moves 152 B per cell and
+ * lattice pass, F16 (deviation scaled by 2^10) and BF16 move 76 B. */
+enum { VLB_STORE_F32 = 0, VLB_STORE_F16 = 1, VLB_STORE_BF16 = 2 };
 
 /* Optional device allocator (e.g. PyTorch's caching allocator).  alloc returns
  * a device pointer of at least `bytes` bytes (16-byte aligned) or NULL; free

@@ -197,8 +197,12 @@ bool valid_axis_params(const vlb_params* p, std::string* why) {
         *why = "rho_s_over_rho_n, core_a must be positive and kappa >= 0";
         return false;
     }
-    if (p->max_points < 0 || p->vfm_substeps < 1 || p->reserved != 0) {
-        *why = "max_points >= 0, vfm_substeps >= 1, reserved == 0 required";
+    if (p->max_points < 0 || p->vfm_substeps < 1) {
+        *why = "max_points >= 0 and vfm_substeps >= 1 required";
+        return false;
+    }
+    if (p->storage != VLB_STORE_F32 && p->storage != VLB_STORE_F16 && p->storage != VLB_STORE_BF16) {
+        *why = "storage must be VLB_STORE_F32, VLB_STORE_F16 or VLB_STORE_BF16";
         return false;
     }
     if (p->force_form != 0 && p->force_form != 1) { *why = "force_form must be 0 or 1"; return false; }
@@ -312,8 +316,9 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
             const int b = atoi(e);
             if (b == 128 || b == 256) blk = b;
         }
-        L.vec = vec;
+        L.vec = p->storage == VLB_STORE_F32 ? vec : 1;
         L.block = blk;
+        L.storage = p->storage;
     }
     {
         // float shift constants s_i = fl(fl(w_i) rho0) as the kernels form them
@@ -364,8 +369,9 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
         if (!q) ok = false;
         return q;
     };
-    d.f[0] = (float*)A(sizeof(float) * 19 * (size_t)C);
-    d.f[1] = (float*)A(sizeof(float) * 19 * (size_t)C);
+    const size_t esize = p->storage == VLB_STORE_F32 ? 4 : 2;
+    d.f[0] = A(esize * 19 * (size_t)C);
+    d.f[1] = A(esize * 19 * (size_t)C);
     d.F = (float*)A(sizeof(float) * 3 * (size_t)C);
     d.U = (float*)A(sizeof(float) * 3 * (size_t)C);
     d.fmask = (uint8_t*)A((size_t)ntiles);
@@ -597,14 +603,20 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
     if (bytes < need) return fail(VLB_ERR_INVALID_ARG, "destination buffer too small");
     Dev& d = ch->d;
     cudaStream_t s = ch->stream;
-    float* tmp = d.f[ch->cur_f ^ 1];  // scratch between steps
+    float* tmp = (float*)d.f[ch->cur_f ^ 1];  // scratch between steps
+    const int esize = ch->p.storage == VLB_STORE_F32 ? 4 : 2;
+    const int per_chunk = (int)((19 * (size_t)esize) / 4);  // populations per float chunk the spare buffer holds
     cudaError_t e = cudaSuccess;
     if (which == VLB_FIELD_RHO || which == VLB_FIELD_U) {
         launch_moments(ch->lp, d.f[ch->cur_f], d.F, d.fmask, tmp, tmp + C, s);
         e = cudaMemcpyAsync(dst, which == VLB_FIELD_RHO ? tmp : tmp + C, need, cudaMemcpyDeviceToHost, s);
     } else if (which == VLB_FIELD_FSTAR || which == VLB_FIELD_FDEV) {
-        launch_unshift(ch->lp, d.f[ch->cur_f], tmp, which == VLB_FIELD_FSTAR ? +1 : 0, s);
-        e = cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, s);
+        for (int i0 = 0; i0 < 19 && e == cudaSuccess; i0 += per_chunk) {
+            const int i1 = i0 + per_chunk < 19 ? i0 + per_chunk : 19;
+            launch_export(ch->lp, d.f[ch->cur_f], tmp, i0, i1, which == VLB_FIELD_FSTAR ? +1 : 0, s);
+            e = cudaMemcpyAsync((char*)dst + sizeof(float) * (size_t)i0 * C, tmp, sizeof(float) * (size_t)(i1 - i0) * C,
+                                cudaMemcpyDeviceToHost, s);
+        }
     } else if (which == VLB_FIELD_FORCE) {
         e = cudaMemcpyAsync(dst, d.F, need, cudaMemcpyDeviceToHost, s);
     } else if (which == VLB_FIELD_POS || which == VLB_FIELD_VEL) {
@@ -651,9 +663,16 @@ int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t byt
     cudaError_t e;
     if (which == VLB_FIELD_FSTAR) {
         if (bytes != sizeof(float) * 19 * (size_t)C) return fail(VLB_ERR_INVALID_ARG, "FSTAR size mismatch");
-        float* tmp = d.f[ch->cur_f ^ 1];
-        e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, s);
-        launch_unshift(ch->lp, tmp, d.f[ch->cur_f], -1, s);
+        float* tmp = (float*)d.f[ch->cur_f ^ 1];
+        const int esize = ch->p.storage == VLB_STORE_F32 ? 4 : 2;
+        const int per_chunk = (int)((19 * (size_t)esize) / 4);
+        e = cudaSuccess;
+        for (int i0 = 0; i0 < 19 && e == cudaSuccess; i0 += per_chunk) {
+            const int i1 = i0 + per_chunk < 19 ? i0 + per_chunk : 19;
+            e = cudaMemcpyAsync(tmp, (const char*)src + sizeof(float) * (size_t)i0 * C,
+                                sizeof(float) * (size_t)(i1 - i0) * C, cudaMemcpyHostToDevice, s);
+            launch_import(ch->lp, tmp, d.f[ch->cur_f], i0, i1, s);
+        }
     } else if (which == VLB_FIELD_FORCE) {
         if (bytes != sizeof(float) * 3 * (size_t)C) return fail(VLB_ERR_INVALID_ARG, "FORCE size mismatch");
         e = cudaMemcpyAsync(d.F, src, bytes, cudaMemcpyHostToDevice, s);

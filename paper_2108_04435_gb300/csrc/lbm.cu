@@ -7,6 +7,8 @@
 // Populations are stored as shifted deviations g_i = f_i - w_i rho0 in FP32;
 // the arithmetic below is the paper's with f_i = g_i + w_i rho0 substituted,
 // which keeps the O(u) signal of each population far above FP32 rounding.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -40,6 +42,33 @@ __host__ __device__ constexpr int wclass(int i) { return i == 0 ? 0 : (i < 7 ? 1
 // f_i = g_i + s_i exactly; the equilibrium below is shifted by s_i, not by the
 // (unrepresentable) w_i rho0, via the constants dr0 and dw.
 
+// Stored population formats: the deviation g_i = f_i - s_i in FP32, in FP16
+// scaled by 2^10 (deviations of 1e-4..1e-1 stay in the normal FP16 range; the
+// power-of-two scale is exact), or in BF16.  Arithmetic is FP32 in all three.
+template <int S>
+struct Pop;
+template <>
+struct Pop<STORE_F32> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ float raw(T v) { return v; }
+    static __device__ __forceinline__ T cv(float v) { return v; }
+};
+template <>
+struct Pop<STORE_F16> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)) * (1.f / 1024.f); }
+    static __device__ __forceinline__ float raw(T v) { return __half2float(v) * (1.f / 1024.f); }
+    static __device__ __forceinline__ T cv(float v) { return __float2half_rn(v * 1024.f); }
+};
+template <>
+struct Pop<STORE_BF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float raw(T v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ T cv(float v) { return __float2bfloat16_rn(v); }
+};
+
 __device__ __forceinline__ int tile_of(const Grid& g, int x, int y, int z) {
     return ((z >> TILE_SHIFT) * g.tny + (y >> TILE_SHIFT)) * g.tnx + (x >> TILE_SHIFT);
 }
@@ -48,9 +77,9 @@ __device__ __forceinline__ int tile_of(const Grid& g, int x, int y, int z) {
 // form).  A link whose source lies beyond a wall is bounced back half-way; on
 // the z faces the moving-wall term 2 w_i rho0 (c_i . u_w)/c_s^2 with
 // u_w = heater e_z injects (low face) or removes (high face) normal fluid.
-template <bool WX, bool WY, bool WZ>
-__device__ __forceinline__ void pull(const float* __restrict__ f, const LbmParams& P, int x, int y, int z,
-                                     long long cell, float g[19]) {
+template <bool WX, bool WY, bool WZ, int S>
+__device__ __forceinline__ void pull(const typename Pop<S>::T* __restrict__ f, const LbmParams& P, int x, int y,
+                                     int z, long long cell, float g[19]) {
     const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz;
     const long long C = P.g.ncell;
     int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
@@ -70,9 +99,9 @@ __device__ __forceinline__ void pull(const float* __restrict__ f, const LbmParam
         const bool oy = CY(i) == 1 ? oym : (CY(i) == -1 ? oyp : false);
         const bool oz = CZ(i) == 1 ? ozm : (CZ(i) == -1 ? ozp : false);
         if (!(ox || oy || oz)) {
-            g[i] = __ldg(&f[(long long)i * C + ((long long)sz * ny + sy) * nx + sx]);
+            g[i] = Pop<S>::ld(&f[(long long)i * C + ((long long)sz * ny + sy) * nx + sx]);
         } else {
-            float v = __ldg(&f[(long long)opp(i) * C + cell]);
+            float v = Pop<S>::ld(&f[(long long)opp(i) * C + cell]);
             if (oz) v += 6.f * wgt(i) * P.rho0 * (float)CZ(i) * P.heater;
             g[i] = v;
         }
@@ -118,9 +147,9 @@ __device__ __forceinline__ void pull_index(const LbmParams& P, int x, int y, int
     q.zo[0] = zp * nxy; q.zo[1] = z * nxy; q.zo[2] = zm * nxy;
 }
 
-template <bool WX, bool WY, bool WZ>
-__device__ __forceinline__ void pull_fast(const float* __restrict__ f, const LbmParams& P, const PullIdx& q, int cell,
-                                          float g[19]) {
+template <bool WX, bool WY, bool WZ, int S>
+__device__ __forceinline__ void pull_fast(const typename Pop<S>::T* __restrict__ f, const LbmParams& P,
+                                          const PullIdx& q, int cell, float g[19]) {
     const int C = (int)P.g.ncell;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
@@ -130,7 +159,7 @@ __device__ __forceinline__ void pull_fast(const float* __restrict__ f, const Lbm
         if (WY && CY(i) != 0) out = out || q.oy[CY(i) + 1];
         if (WZ && CZ(i) != 0) { outz = q.oz[CZ(i) + 1]; out = out || outz; }
         if (WX || WY || WZ) src = out ? opp(i) * C + cell : src;
-        float v = __ldg(&f[src]);
+        float v = Pop<S>::ld(&f[src]);
         if (WZ && CZ(i) != 0) v += outz ? 6.f * wgt(i) * P.rho0 * (float)CZ(i) * P.heater : 0.f;
         g[i] = v;
     }
@@ -142,8 +171,9 @@ __device__ __forceinline__ void pull_fast(const float* __restrict__ f, const Lbm
 // The collision works on opposite pairs (i, i'): with c_i' = -c_i the even
 // parts of f^eq (Eq. 7) and of F_i (Eq. 13) are shared and the odd parts
 // change sign.
-template <bool WX, bool WY, bool WZ>
-__global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict__ fin, float* __restrict__ fout,
+template <bool WX, bool WY, bool WZ, int S>
+__global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T* __restrict__ fin,
+                                                        typename Pop<S>::T* __restrict__ fout,
                                                         const float* __restrict__ F, float* __restrict__ U,
                                                         const uint8_t* __restrict__ fmask,
                                                         const uint8_t* __restrict__ umask, double* __restrict__ part,
@@ -160,7 +190,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
         {
             PullIdx q;
             pull_index<WX, WY, WZ>(P, x, y, z, q);
-            pull_fast<WX, WY, WZ>(fin, P, q, cell, g);
+            pull_fast<WX, WY, WZ, S>(fin, P, q, cell, g);
         }
         // Eqs. 5-6 with the half-force shift: rho = rho0 + sum g, j = sum c g
         float drho = P.dr0, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -200,7 +230,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
             float out = g[0] + om * (geq - g[0]);
             if (force) out += P.pref * wgt(0) * (-3.f * uF);
             if (pinned) out = wgt(0) * (drho - 1.5f * rho * P.pin * P.pin) + P.dw[0];
-            fout[cell] = out;
+            fout[cell] = Pop<S>::cv(out);
         }
 #pragma unroll
         for (int i = 1; i < 19; i += 2) {
@@ -225,8 +255,8 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const float* __restrict_
                 oi = ps + pa;
                 oj = ps - pa;
             }
-            fout[i * C + cell] = oi;
-            fout[j * C + cell] = oj;
+            fout[i * C + cell] = Pop<S>::cv(oi);
+            fout[j * C + cell] = Pop<S>::cv(oj);
         }
         s_drho = drho;
         s_uz = uz;
@@ -590,9 +620,10 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ 
 
 // Density and velocity of the streamed populations of the current state
 // (what the next pass will see), for read-out.
-template <bool WX, bool WY, bool WZ>
-__global__ void k_moments(const float* __restrict__ f, const float* __restrict__ F, const uint8_t* __restrict__ fmask,
-                          float* __restrict__ rho_out, float* __restrict__ U, LbmParams P) {
+template <bool WX, bool WY, bool WZ, int S>
+__global__ void k_moments(const typename Pop<S>::T* __restrict__ f, const float* __restrict__ F,
+                          const uint8_t* __restrict__ fmask, float* __restrict__ rho_out, float* __restrict__ U,
+                          LbmParams P) {
     const int nx = P.g.nx, ny = P.g.ny;
     const long long C = P.g.ncell;
     const int z = blockIdx.y;
@@ -601,7 +632,7 @@ __global__ void k_moments(const float* __restrict__ f, const float* __restrict__
     const int y = xy / nx, x = xy - y * nx;
     const long long cell = (long long)z * nx * ny + xy;
     float g[19];
-    pull<WX, WY, WZ>(f, P, x, y, z, cell, g);
+    pull<WX, WY, WZ, S>(f, P, x, y, z, cell, g);
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
@@ -624,7 +655,9 @@ __global__ void k_moments(const float* __restrict__ f, const float* __restrict__
     U[2 * C + cell] = (jz + 0.5f * Fz) / rho;
 }
 
-__global__ void k_lbm_init(float* __restrict__ f, float* __restrict__ U, LbmParams P, float ux, float uy, float uz) {
+template <int S>
+__global__ void k_lbm_init(typename Pop<S>::T* __restrict__ f, float* __restrict__ U, LbmParams P, float ux, float uy,
+                           float uz) {
     const long long C = P.g.ncell;
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
@@ -632,24 +665,39 @@ __global__ void k_lbm_init(float* __restrict__ f, float* __restrict__ U, LbmPara
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const float cu = (float)CX(i) * ux + (float)CY(i) * uy + (float)CZ(i) * uz;
-        f[(long long)i * C + c] = wgt(i) * (P.rho0 * (3.f * cu + 4.5f * cu * cu - 1.5f * usq)) + P.dw[wclass(i)];
+        f[(long long)i * C + c] =
+            Pop<S>::cv(wgt(i) * (P.rho0 * (3.f * cu + 4.5f * cu * cu - 1.5f * usq)) + P.dw[wclass(i)]);
     }
     U[c] = ux;
     U[C + c] = uy;
     U[2 * C + c] = uz;
 }
 
-// direction +1: out = g + s_i (populations f); -1: out = f - s_i (import);
-// 0: out = g - dw_i = f - w_i rho0 (deviation from the rest state)
-__global__ void k_unshift(const float* __restrict__ in, float* __restrict__ out, LbmParams P, int direction) {
+// Populations i0..i1-1 to float: mode +1 f = g + s_i, mode 0 f - w_i rho0 = g - dw_i.
+template <int S>
+__global__ void k_export(const typename Pop<S>::T* __restrict__ in, float* __restrict__ out, LbmParams P, int i0,
+                         int i1, int mode) {
     const long long C = P.g.ncell;
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const float s = wgt(i) * P.rho0;
-        const float v = in[(long long)i * C + c];
-        out[(long long)i * C + c] = direction > 0 ? v + s : (direction < 0 ? v - s : v - P.dw[wclass(i)]);
+    for (int i = i0; i < i1; ++i) {
+        const int k = i == 0 ? 0 : (i < 7 ? 1 : 2);
+        const float w = k == 0 ? 1.f / 3.f : (k == 1 ? 1.f / 18.f : 1.f / 36.f);
+        const float v = Pop<S>::raw(in[(long long)i * C + c]);
+        out[(long long)(i - i0) * C + c] = mode > 0 ? v + w * P.rho0 : v - P.dw[k];
+    }
+}
+
+// Float populations i0..i1-1 (f) into the stored deviations g = f - s_i.
+template <int S>
+__global__ void k_import(const float* __restrict__ in, typename Pop<S>::T* __restrict__ out, LbmParams P, int i0,
+                         int i1) {
+    const long long C = P.g.ncell;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    for (int i = i0; i < i1; ++i) {
+        const float w = i == 0 ? 1.f / 3.f : (i < 7 ? 1.f / 18.f : 1.f / 36.f);
+        out[(long long)i * C + c] = Pop<S>::cv(in[(long long)(i - i0) * C + c] - w * P.rho0);
     }
 }
 
@@ -697,28 +745,43 @@ __global__ void k_zero_force(Grid g, float* __restrict__ F, uint8_t* __restrict_
 }
 
 template <bool WX, bool WY, bool WZ>
-void lbm_dispatch(const LbmParams& P, const float* fin, float* fout, const float* F, float* U, const uint8_t* fmask,
+void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const float* F, float* U, const uint8_t* fmask,
                   const uint8_t* umask, double* part, cudaStream_t s) {
     const int nxy = P.g.nx * P.g.ny;
-    if (P.vec == 4 || P.vec == 2) {
+    if (P.storage == STORE_F32 && (P.vec == 4 || P.vec == 2)) {
         const int groups = nxy / P.vec;
         dim3 grid((groups + 127) / 128, P.g.nz);
         if (P.vec == 4)
-            k_lbm_step_vec<WX, WY, WZ, 4><<<grid, 128, 0, s>>>(fin, fout, F, U, fmask, umask, part, P);
+            k_lbm_step_vec<WX, WY, WZ, 4><<<grid, 128, 0, s>>>((const float*)fin, (float*)fout, F, U, fmask, umask,
+                                                                part, P);
         else
-            k_lbm_step_vec<WX, WY, WZ, 2><<<grid, 128, 0, s>>>(fin, fout, F, U, fmask, umask, part, P);
+            k_lbm_step_vec<WX, WY, WZ, 2><<<grid, 128, 0, s>>>((const float*)fin, (float*)fout, F, U, fmask, umask,
+                                                                part, P);
         return;
     }
     dim3 grid((nxy + P.block - 1) / P.block, P.g.nz);
-    k_lbm_step<WX, WY, WZ><<<grid, P.block, 0, s>>>(fin, fout, F, U, fmask, umask, part, P);
+    if (P.storage == STORE_F16)
+        k_lbm_step<WX, WY, WZ, STORE_F16><<<grid, P.block, 0, s>>>((const __half*)fin, (__half*)fout, F, U, fmask,
+                                                                    umask, part, P);
+    else if (P.storage == STORE_BF16)
+        k_lbm_step<WX, WY, WZ, STORE_BF16><<<grid, P.block, 0, s>>>(
+            (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, F, U, fmask, umask, part, P);
+    else
+        k_lbm_step<WX, WY, WZ, STORE_F32><<<grid, P.block, 0, s>>>((const float*)fin, (float*)fout, F, U, fmask,
+                                                                    umask, part, P);
 }
 
 template <bool WX, bool WY, bool WZ>
-void moments_dispatch(const LbmParams& P, const float* f, const float* F, const uint8_t* fmask, float* rho, float* U,
+void moments_dispatch(const LbmParams& P, const void* f, const float* F, const uint8_t* fmask, float* rho, float* U,
                       cudaStream_t s) {
     const int bpp = (P.g.nx * P.g.ny + LBM_BLOCK - 1) / LBM_BLOCK;
     dim3 grid(bpp, P.g.nz);
-    k_moments<WX, WY, WZ><<<grid, LBM_BLOCK, 0, s>>>(f, F, fmask, rho, U, P);
+    if (P.storage == STORE_F16)
+        k_moments<WX, WY, WZ, STORE_F16><<<grid, LBM_BLOCK, 0, s>>>((const __half*)f, F, fmask, rho, U, P);
+    else if (P.storage == STORE_BF16)
+        k_moments<WX, WY, WZ, STORE_BF16><<<grid, LBM_BLOCK, 0, s>>>((const __nv_bfloat16*)f, F, fmask, rho, U, P);
+    else
+        k_moments<WX, WY, WZ, STORE_F32><<<grid, LBM_BLOCK, 0, s>>>((const float*)f, F, fmask, rho, U, P);
 }
 
 }  // namespace
@@ -738,25 +801,46 @@ void moments_dispatch(const LbmParams& P, const float* f, const float* F, const 
         }                                                                            \
     } while (0)
 
-void launch_lbm_step(const LbmParams& P, const float* fin, float* fout, const float* F, float* U,
+void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const float* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s) {
     VLB_WALL_DISPATCH(lbm_dispatch, P, fin, fout, F, U, fmask, umask, part, s);
 }
 
-void launch_moments(const LbmParams& P, const float* f, const float* F, const uint8_t* fmask, float* rho, float* U,
+void launch_moments(const LbmParams& P, const void* f, const float* F, const uint8_t* fmask, float* rho, float* U,
                     cudaStream_t s) {
     VLB_WALL_DISPATCH(moments_dispatch, P, f, F, fmask, rho, U, s);
 }
 
-void launch_lbm_init(const LbmParams& P, float* f, float* U, const double init_u[3], cudaStream_t s) {
+void launch_lbm_init(const LbmParams& P, void* f, float* U, const double init_u[3], cudaStream_t s) {
     const long long C = P.g.ncell;
-    k_lbm_init<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(f, U, P, (float)init_u[0], (float)init_u[1],
-                                                           (float)init_u[2]);
+    const unsigned nb = (unsigned)((C + 255) / 256);
+    const float ux = (float)init_u[0], uy = (float)init_u[1], uz = (float)init_u[2];
+    if (P.storage == STORE_F16)
+        k_lbm_init<STORE_F16><<<nb, 256, 0, s>>>((__half*)f, U, P, ux, uy, uz);
+    else if (P.storage == STORE_BF16)
+        k_lbm_init<STORE_BF16><<<nb, 256, 0, s>>>((__nv_bfloat16*)f, U, P, ux, uy, uz);
+    else
+        k_lbm_init<STORE_F32><<<nb, 256, 0, s>>>((float*)f, U, P, ux, uy, uz);
 }
 
-void launch_unshift(const LbmParams& P, const float* in, float* out, int direction, cudaStream_t s) {
-    const long long C = P.g.ncell;
-    k_unshift<<<(unsigned)((C + 255) / 256), 256, 0, s>>>(in, out, P, direction);
+void launch_export(const LbmParams& P, const void* f, float* out, int i0, int i1, int mode, cudaStream_t s) {
+    const unsigned nb = (unsigned)((P.g.ncell + 255) / 256);
+    if (P.storage == STORE_F16)
+        k_export<STORE_F16><<<nb, 256, 0, s>>>((const __half*)f, out, P, i0, i1, mode);
+    else if (P.storage == STORE_BF16)
+        k_export<STORE_BF16><<<nb, 256, 0, s>>>((const __nv_bfloat16*)f, out, P, i0, i1, mode);
+    else
+        k_export<STORE_F32><<<nb, 256, 0, s>>>((const float*)f, out, P, i0, i1, mode);
+}
+
+void launch_import(const LbmParams& P, const float* in, void* f, int i0, int i1, cudaStream_t s) {
+    const unsigned nb = (unsigned)((P.g.ncell + 255) / 256);
+    if (P.storage == STORE_F16)
+        k_import<STORE_F16><<<nb, 256, 0, s>>>(in, (__half*)f, P, i0, i1);
+    else if (P.storage == STORE_BF16)
+        k_import<STORE_BF16><<<nb, 256, 0, s>>>(in, (__nv_bfloat16*)f, P, i0, i1);
+    else
+        k_import<STORE_F32><<<nb, 256, 0, s>>>(in, (float*)f, P, i0, i1);
 }
 
 int lbm_blocks_per_plane(const LbmParams& P) {

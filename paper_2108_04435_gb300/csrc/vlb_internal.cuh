@@ -43,6 +43,9 @@ enum : int {
     DS_COUNT = 8
 };
 
+// Stored population formats (vlb_params::storage).
+enum : int { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
+
 constexpr int TILE_SHIFT = 3;   // force / velocity activity tiles of 8^3 cells
 constexpr int LBM_BLOCK = 256;  // cells per stream-collide block (one z plane)
 constexpr int BS_TPB = 128;     // Biot-Savart targets per block
@@ -71,6 +74,7 @@ struct LbmParams {
     int pin_on;
     int vec;            // cells per thread of the stream-collide kernel (4, 2, or 1 = scalar kernel)
     int block;          // threads per block of the scalar kernel (128 or 256)
+    int storage;        // STORE_F32, STORE_F16 (deviation x 2^10) or STORE_BF16
     double inv_ratio;   // rho_n / rho_s
     // device buffers of the fused per-plane reduction (Eq. 18, mass, Mach)
     int* plane_ticket;  // [nz] blocks done per plane, back to 0 after the plane is reduced
@@ -108,7 +112,7 @@ __host__ __device__ inline int bs_splits(int N, int tile) {
 
 struct Dev {
     // lattice
-    float* f[2];        // shifted populations f_i - w_i rho0, [19][C]
+    void* f[2];         // stored deviations f_i - s_i, [19][C] in the storage format
     float* F;           // force grid [3][C]
     float* U;           // velocity of the last pass [3][C], valid in u-active tiles
     uint8_t* fmask;     // tiles where F may be non-zero
@@ -155,17 +159,18 @@ struct Dev {
 
 // ---------------------------------------------------------------- launchers
 // lbm.cu
-void launch_lbm_init(const LbmParams& P, float* f, float* U, const double init_u[3], cudaStream_t s);
-void launch_lbm_step(const LbmParams& P, const float* fin, float* fout, const float* F, float* U,
+void launch_lbm_init(const LbmParams& P, void* f, float* U, const double init_u[3], cudaStream_t s);
+void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const float* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
 void launch_plane_vs(const LbmParams& P, const double* part, cudaStream_t s);
 int lbm_blocks_per_plane(const LbmParams& P);
-void launch_moments(const LbmParams& P, const float* f, const float* F, const uint8_t* fmask, float* rho,
+void launch_moments(const LbmParams& P, const void* f, const float* F, const uint8_t* fmask, float* rho,
                     float* U, cudaStream_t s);
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,
                        cudaStream_t s);
 void launch_zero_force(const Grid& g, float* F, uint8_t* fmask, cudaStream_t s);
-void launch_unshift(const LbmParams& P, const float* fsh, float* out, int direction, cudaStream_t s);
+void launch_export(const LbmParams& P, const void* f, float* out, int i0, int i1, int mode, cudaStream_t s);
+void launch_import(const LbmParams& P, const float* in, void* f, int i0, int i1, cudaStream_t s);
 
 // vfm.cu
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,

@@ -1,0 +1,96 @@
+"""Reduced-precision population storage (FP16 scaled deviations, BF16
+deviations; FP32 arithmetic) against the FP64 oracle.
+
+The populations f_i ~ w_i dominate any error norm of f itself, so the error
+that matters is the one of the deviations f_i - w_i rho0 and of the flow
+they carry.  Measured errors are printed; the bounds below are the stated
+accuracy of each format (FP16 keeps 11 significant bits of the deviation,
+BF16 8):
+  one lattice pass      FP16: f 1e-5, deviation 1e-3, velocity 1e-3   BF16: 5e-5, 8e-3, 8e-3
+  40 lattice passes     FP16: deviation 3e-3, velocity 3e-3   BF16: 2e-2, 2e-2
+  one coupled step      FP16: filament velocity 1e-3           BF16: 5e-3
+"""
+import numpy as np
+import pytest
+
+from gpu_util import pair, rel_l2, same_lattice_state
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {1: dict(f=1e-5, one=1e-3, many=3e-3, vfm=1e-3), 2: dict(f=5e-5, one=8e-3, many=2e-2, vfm=5e-3)}
+NAMES = {1: "f16", 2: "bf16"}
+
+
+def params(n, wall, storage, **extra):
+    from paper_2108_04435_gb300 import configs
+    kw = dict(couple=0, max_points=4096, storage=storage)
+    kw.update(extra)
+    return configs.base_params(n, wall, 1.9, **kw)
+
+
+def lattice_errors(g, r):
+    import oracle
+    from paper_2108_04435_gb300 import vlb
+    c, w, _ = oracle.lattice()
+    rest = (w * r.params["rho0"])[:, None]
+    f_r = r.read(oracle.FIELD_FSTAR)
+    return dict(fstar=rel_l2(g.read(vlb.FIELD_FSTAR), f_r),
+                fdev=rel_l2(g.read(vlb.FIELD_FDEV), f_r - rest),
+                u=rel_l2(g.read(vlb.FIELD_U), r.read(oracle.FIELD_U)),
+                vs=rel_l2(g.read(vlb.FIELD_PLANE_VS), r.read(oracle.FIELD_PLANE_VS)))
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["f16", "bf16"])
+@pytest.mark.parametrize("geom", ["periodic", "walls"])
+def test_lattice_passes(storage, geom):
+    import oracle
+    from paper_2108_04435_gb300 import vlb
+    if geom == "periodic":
+        p = params((24, 20, 16), (0, 0, 0), storage, init_vn=[0.003, -0.002, 0.01])
+    else:
+        p = params((22, 18, 36), (1, 1, 1), storage, heater_vn=0.01, init_vn=[0.0, 0.0, 0.01])
+    g, r = pair(p)
+    same_lattice_state(g, r, seed=11, amp=1e-2, force_amp=2e-4)
+    g.run_phases(vlb.PHASE_LBM)
+    r.run_phases(oracle.PHASE_LBM)
+    e1 = lattice_errors(g, r)
+    for _ in range(39):
+        g.run_phases(vlb.PHASE_LBM)
+        r.run_phases(oracle.PHASE_LBM)
+    e40 = lattice_errors(g, r)
+    print(NAMES[storage], geom, "1 pass", e1, "40 passes", e40)
+    b = BOUNDS[storage]
+    assert e1["fstar"] < b["f"] and e1["fdev"] < b["one"] and e1["u"] < b["one"]
+    assert e40["fdev"] < b["many"] and e40["u"] < b["many"] and e40["vs"] < b["many"]
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["f16", "bf16"])
+def test_coupled_step(storage):
+    import oracle
+    from paper_2108_04435_gb300 import configs, vlb
+    p, xyz, nxt = configs.config("ring32")
+    p["storage"] = storage
+    g, r = pair(p, xyz, nxt)
+    g.step(2)
+    r.step(2)
+    e = rel_l2(g.read(vlb.FIELD_VEL), r.read(oracle.FIELD_VEL))
+    print(NAMES[storage], "coupled step velocity", e)
+    assert e < BOUNDS[storage]["vfm"]
+    assert np.array_equal(g.read(vlb.FIELD_NEXT), r.read(oracle.FIELD_NEXT))
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["f16", "bf16"])
+def test_mass_drift(storage):
+    """Rounding of the stored deviations breaks exact mass conservation; the
+    drift over 200 passes is reported and bounded."""
+    from paper_2108_04435_gb300 import vlb
+    p = params((20, 20, 40), (1, 1, 1), storage, heater_vn=0.01, init_vn=[0.0, 0.0, 0.01])
+    g, r = pair(p)
+    same_lattice_state(g, r, seed=3, amp=1e-2)
+    g.run_phases(vlb.PHASE_LBM)
+    m0 = g.stats()[2]
+    for _ in range(200):
+        g.run_phases(vlb.PHASE_LBM)
+    drift = abs(g.stats()[2] / m0 - 1)
+    print(NAMES[storage], "mass drift over 200 passes", drift)
+    assert drift < (1e-4 if storage == 1 else 1e-3)
