@@ -317,6 +317,24 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
             if (b == 128 || b == 256) blk = b;
         }
         L.vec = p->storage == VLB_STORE_F32 ? vec : 1;
+        // exact division by nx through a multiply-high (Granlund-Montgomery),
+        // checked here for every in-plane index the kernel can form
+        {
+            const unsigned d = (unsigned)g.nx;
+            int sh = 0;
+            while ((1ull << sh) < d) ++sh;
+            const int shift = 32 + sh;
+            const unsigned long long m = ((1ull << shift) + d - 1) / d;
+            bool exact = true;
+            const unsigned lim = (unsigned)g.nx * (unsigned)g.ny;
+            for (unsigned xy = 0; xy < lim && exact; ++xy) exact = ((xy * m) >> shift) == xy / d;
+            if (!exact) {
+                delete ch;
+                return fail(VLB_ERR_INVALID_ARG, "no exact multiply-high division for this nx");
+            }
+            L.nx_magic = m;
+            L.nx_shift = shift;
+        }
         L.block = blk;
         L.storage = p->storage;
     }

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
     const int xy = blockIdx.x * blockDim.x + threadIdx.x;
     float s_drho = 0.f, s_uz = 0.f, s_u2 = 0.f;
     if (xy < nx * ny) {
-        const int y = xy / nx, x = xy - y * nx;
+        const int y = (int)(((unsigned long long)(unsigned)xy * P.nx_magic) >> P.nx_shift), x = xy - y * nx;
         const int cell = z * nx * ny + xy;
         float g[19];
         {
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
         }
         const bool force = factive || P.body_on;
         const float rho = P.rho0 + drho;
-        const float inv = 1.f / rho;
+        const float inv = __fdividef(1.f, rho);  // ~1 ulp; rho is close to rho0
         const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
         const float usq = ux * ux + uy * uy + uz * uz;
         if (umask[tile]) {
