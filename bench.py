@@ -297,6 +297,47 @@ def run_reference(args, ws, rank):
     }
 
 
+def run_serving(args):
+    """Sweep of counterflow requests (grids 32^3..128^3, 1.6/1.9/2.1 K,
+    v_ns ~ U[0.005, 0.04], 100..20k points) in three forms: the plain FP32
+    single-run form (one request at a time, arrivals ignored), and the serving
+    form (Poisson arrivals, up to 16 runs admitted by memory budget, steps in
+    slices on separate streams) with FP32 and with FP16 population storage."""
+    import copy
+
+    import torch
+
+    from paper_2108_04435_gb300 import configs, serve
+    torch.cuda.set_device(0)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.8, 64 << 30))
+    out = {}
+    # sweep throughput: every request available at once
+    for form, storage, slots in (("fp32_single_run", 0, 1), ("fp32_serving", 0, 16), ("fp16_serving", 1, 16)):
+        reqs = configs.serving_requests(args.requests, args.rate, 0, args.req_steps, storage=storage)
+        res, summ = serve.serve_gpu(copy.deepcopy(reqs), budget_bytes=budget, max_slots=slots, slice_steps=50,
+                                    realtime=False)
+        out[form] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()}
+    # latency: Poisson arrivals, FP16 serving form
+    reqs = configs.serving_requests(args.requests, args.rate, 0, args.req_steps, storage=1)
+    res, lat = serve.serve_gpu(copy.deepcopy(reqs), budget_bytes=budget, max_slots=16, slice_steps=50, realtime=True)
+    lat = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in lat.items()}
+    base = out["fp32_single_run"]["throughput_req_per_s"]
+    line = {
+        "metric": "serving sweep throughput", "value": out["fp16_serving"]["throughput_req_per_s"],
+        "unit": "requests/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "storage": "f16",
+        "data": "synthetic",
+        "config": {"workload": f"{args.requests} counterflow requests, {args.req_steps} coupled steps each, "
+                               f"periodic grids 32^3..128^3, 1.6/1.9/2.1 K",
+                   "budget_bytes": budget},
+        "speedup_vs_fp32_single_run": round(out["fp16_serving"]["throughput_req_per_s"] / base, 3) if base else None,
+        "p50_latency_s": lat["p50_latency_s"], "p99_latency_s": lat["p99_latency_s"],
+        "latency_run": {"arrival_rate_per_s": args.rate, **lat},
+        "forms": out,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,6 +348,10 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage (arithmetic is FP32 in all)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--serve", action="store_true", help="serving sweep instead of the coupled-step benchmark")
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--rate", type=float, default=8.0)
+    ap.add_argument("--req-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -318,7 +363,10 @@ def main():
             import torch
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
-    if args.impl == "reference":
+    if args.serve:
+        if rank == 0:
+            run_serving(args)
+    elif args.impl == "reference":
         line = run_reference(args, ws, rank)
         if line is not None:
             print(json.dumps(line), flush=True)

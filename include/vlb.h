@@ -107,7 +107,7 @@ enum {
     VLB_FIELD_PLANE_VS = 6, /* float64 [n_z]: superfluid counterflow velocity per z plane (Eq. 18) */
     VLB_FIELD_STATS = 7,    /* float64 [16]: 0 points, 1 status bits, 2 mass, 3 line length, 4 max Mach,
                                5 splits, 6 merges, 7 reconnections, 8 points deleted in small loops,
-                               9 steps, 10..15 reserved */
+                               9 steps, 10 device bytes allocated, 11..15 reserved */
     VLB_FIELD_VEL = 8,      /* float64 [N][3]: ds/dt at the first RK stage of the last filament advance */
     VLB_FIELD_FDEV = 9      /* float32 [19][C]: f_i - w_i rho0 of the post-collision populations (read only;
                                the flow signal at full float precision) */
@@ -138,6 +138,20 @@ int vlb_step(vlb_channel* ch, int32_t nsteps);
 
 /* Enable (default) or disable the graph replay of vlb_step. */
 int vlb_set_graphs(vlb_channel* ch, int32_t enable);
+
+/* Non-blocking form of vlb_step for hosts that drive many channels at once
+ * (each on its own stream, so their work overlaps on the GPU): queues the
+ * steps and a read-back of the status, and returns without waiting.
+ * vlb_query then returns VLB_BUSY (1) while that work runs, VLB_OK once it
+ * has finished, or the first error the device reported (as vlb_step). */
+enum { VLB_BUSY = 1 };
+int vlb_step_async(vlb_channel* ch, int32_t nsteps);
+int vlb_query(vlb_channel* ch);
+
+/* Device bytes vlb_create_channel would allocate for these parameters (an
+ * upper bound used to admit channels against a memory budget); 0 if the
+ * parameters are invalid. */
+size_t vlb_channel_bytes(const vlb_params* p);
 
 /* Run only the selected phases once (bitwise OR of VLB_PHASE_*), in the
  * order of vlb_step; used to check each part of the step on its own. */

@@ -8,6 +8,8 @@ core radius a ~ 1 Angstrom (Sec. I) is expressed in cells of 2 mm / 64.
 """
 from __future__ import annotations
 
+import numpy as np
+
 from . import inputs
 
 DX_CM = 0.2 / 64.0          # Sec. III: L_x = 2 mm over 64 cells
@@ -17,6 +19,8 @@ TEMPS = {
     # T: alpha, alpha', rho_s/rho_n, kappa in lattice units (tau = 0.6)
     1.9: dict(alpha=0.206, alpha_p=0.0083, rho_s_over_rho_n=1.38, kappa=0.157),
     1.6: dict(alpha=0.098, alpha_p=0.016, rho_s_over_rho_n=5.2, kappa=0.057),
+    # 2.1 K: approximate values (not given by the paper or the workload definitions)
+    2.1: dict(alpha=0.5, alpha_p=0.02, rho_s_over_rho_n=0.35, kappa=0.22),
 }
 
 
@@ -66,3 +70,39 @@ def config(name: str, seed: int = 0):
 
 
 NAMES = ["ring32", "channel64x64x256", "box128", "channel128x128x1024"]
+
+
+MACH_SAFE_VN = 0.02  # imposed |u| with headroom under the Mach limit 0.05 c_s = 0.0289 (Sec. II.B)
+
+
+def serving_requests(count: int, rate: float, seed: int, steps: int,
+                     grids=((32, 32, 32), (64, 64, 64), (64, 64, 256), (128, 128, 128)),
+                     temps=(1.6, 1.9, 2.1), vns=(0.005, 0.04), points=(100, 20000), storage: int = 0):
+    """Seeded counterflow requests arriving as a Poisson process of `rate`/s.
+
+    Each request: a periodic grid from `grids`, a temperature from `temps`,
+    a counterflow v_ns ~ U[vns] (the normal velocity it implies is capped at
+    MACH_SAFE_VN), and rings seeded until about U[points] filament points,
+    capped at a line density of 0.02 per cell^2 of the grid.
+    Returns a list of dicts with arrival time, params, xyz, next and steps.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t, out = 0.0, []
+    for k in range(count):
+        t += rng.exponential(1.0 / rate)
+        n = grids[int(rng.integers(len(grids)))]
+        T = temps[int(rng.integers(len(temps)))]
+        v_ns = rng.uniform(*vns)
+        target = int(rng.uniform(*points))
+        target = min(target, int(0.02 * n[0] * n[1] * n[2] / 0.8))
+        r_max = min(n) / 4.0 - 3.0
+        r_min = min(4.0, r_max)
+        mean_pts = 2 * np.pi * 0.5 * (r_min + r_max) / 0.8
+        count_rings = max(1, int(round(target / mean_pts)))
+        xyz, nxt = inputs.random_rings(n, (0, 0, 0), count_rings, r_min, r_max, seed * 100003 + k, min_sep=2.0,
+                                       max_tries=20, skip_crowded=True)
+        vn = min(counterflow_vn(v_ns, T), MACH_SAFE_VN)
+        p = base_params(n, (0, 0, 0), T, init_vn=[0.0, 0.0, vn], storage=storage,
+                        max_points=max(4096, int(4 * len(nxt))))
+        out.append(dict(id=k, arrival=t, params=p, xyz=xyz, next=nxt, steps=steps, grid=n, T=T, v_ns=v_ns))
+    return out

@@ -46,14 +46,18 @@ struct vlb_channel {
     int n_hint = 0;
     long long steps = 0;
     std::vector<void*> blocks;
+    size_t bytes = 0;  // device bytes allocated at create
     int* h_counters = nullptr;   // pinned
     double* h_dstats = nullptr;  // pinned
     bool timing = false;
     bool graphs = true;                      // replay captured steps when the stream allows capture
-    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [cur_f][cur_p]
-    int gclass[2][2] = {{-1, -1}, {-1, -1}};  // filament size class each graph was captured for
+    // [steps per graph: 1 or GRAPH_MULTI][cur_f][cur_p]
+    cudaGraphExec_t gexec[2][2][2] = {{{nullptr, nullptr}, {nullptr, nullptr}}, {{nullptr, nullptr}, {nullptr, nullptr}}};
+    int gclass[2][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};  // filament size class at capture
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
+    cudaEvent_t done = nullptr;  // completion of the work queued by vlb_step_async
+    bool pending = false;
     double timing_ms = 0.0;
     long long timing_launches = 0;
 
@@ -66,7 +70,10 @@ struct vlb_channel {
         } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
             ptr = nullptr;
         }
-        if (ptr) blocks.push_back(ptr);
+        if (ptr) {
+            blocks.push_back(ptr);
+            this->bytes += bytes;
+        }
         return ptr;
     }
 };
@@ -82,12 +89,15 @@ void release(vlb_channel* ch) {
     ch->blocks.clear();
     for (cudaEvent_t e : ch->ev) cudaEventDestroy(e);
     ch->ev.clear();
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            if (ch->gexec[a][b]) {
-                cudaGraphExecDestroy(ch->gexec[a][b]);
-                ch->gexec[a][b] = nullptr;
-            }
+    if (ch->done) cudaEventDestroy(ch->done);
+    ch->done = nullptr;
+    for (int m = 0; m < 2; ++m)
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                if (ch->gexec[m][a][b]) {
+                    cudaGraphExecDestroy(ch->gexec[m][a][b]);
+                    ch->gexec[m][a][b] = nullptr;
+                }
     if (ch->h_counters) cudaFreeHost(ch->h_counters);
     if (ch->h_dstats) cudaFreeHost(ch->h_dstats);
     ch->h_counters = nullptr;
@@ -268,6 +278,27 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
 extern "C" {
 
 const char* vlb_last_error(void) { return g_last_error.c_str(); }
+
+size_t vlb_channel_bytes(const vlb_params* p) {
+    std::string why;
+    if (!p || !valid_axis_params(p, &why)) return 0;
+    auto up = [](size_t b) { return ((b ? b : 16) + 255) & ~size_t(255); };
+    const size_t C = (size_t)p->n[0] * p->n[1] * p->n[2];
+    const size_t cap = p->max_points > 0 ? (size_t)p->max_points : 1;
+    const size_t nt = (size_t)((p->n[0] + 7) >> 3) * ((p->n[1] + 7) >> 3) * ((p->n[2] + 7) >> 3);
+    size_t h = 1;
+    while (h < 2 * cap) h <<= 1;
+    const size_t esize = p->storage == VLB_STORE_F32 ? 4 : 2;
+    const size_t bpp = (size_t)((p->n[0] * p->n[1] + 127) / 128) + 1;
+    size_t b = 2 * up(esize * 19 * C) + 2 * up(4 * 3 * C) + 2 * up(nt) + up(8 * 3 * bpp * p->n[2]);
+    b += 3 * up(8 * (size_t)p->n[2]) + up(4 * (size_t)p->n[2]) + up(8 * DS_COUNT) + up(4 * CNT_COUNT);
+    b += 2 * (up(24 * cap) + 2 * up(4 * cap)) + 6 * up(24 * cap) + up(8 * cap) + up(32 * cap) + up(48 * cap);
+    b += up(12 * cap * (size_t)bs_max_splits((int)cap)) + up(12 * cap) + up(4 * ((cap + 127) / 128));
+    b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(8 * cap);
+    const size_t nc = cap / 2 + 1;
+    b += 4 * up(4 * nc) + up(8 * nc) + up(4 * cap) + up(8 * ((cap + 255) / 256));
+    return b;
+}
 
 int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* stream, vlb_channel** out) {
     if (!p || !out) return fail(VLB_ERR_INVALID_ARG, "null argument");
@@ -542,51 +573,99 @@ int size_class(int n) {
     return c;
 }
 
-bool step_graph(vlb_channel* ch) {
+// Steps per multi-step graph (even, so both buffer parities are restored).
+constexpr int GRAPH_MULTI = 8;
+
+// Replay `multi ? GRAPH_MULTI : 1` coupled steps from a graph captured on
+// first use for the current buffer parities and filament size class.
+bool step_graph(vlb_channel* ch, bool multi) {
+    const int m = multi ? 1 : 0, nst = multi ? GRAPH_MULTI : 1;
     const int f = ch->cur_f, q = ch->cur_p;
     const int cls = size_class(ch->n_hint);
-    if (ch->gexec[f][q] && ch->gclass[f][q] != cls) {
+    cudaGraphExec_t& ge = ch->gexec[m][f][q];
+    if (ge && ch->gclass[m][f][q] != cls) {
         // the Biot-Savart grid was sized for another filament count: capture again
-        cudaGraphExecDestroy(ch->gexec[f][q]);
-        ch->gexec[f][q] = nullptr;
+        cudaGraphExecDestroy(ge);
+        ge = nullptr;
     }
-    if (!ch->gexec[f][q]) {
+    if (!ge) {
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(ch->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
-        run_phases(ch, VLB_PHASE_ALL);
+        for (int k = 0; k < nst; ++k) run_phases(ch, VLB_PHASE_ALL);
         cudaError_t e = cudaStreamEndCapture(ch->stream, &graph);
-        ch->cur_f = f;  // the captured step has not run yet
+        ch->cur_f = f;  // the captured steps have not run yet
         ch->cur_p = q;
         if (e != cudaSuccess || !graph) {
             cudaGetLastError();
             return false;
         }
-        e = cudaGraphInstantiate(&ch->gexec[f][q], graph, 0);
+        e = cudaGraphInstantiate(&ge, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            ch->gexec[f][q] = nullptr;
+            ge = nullptr;
             return false;
         }
-        ch->gclass[f][q] = cls;
+        ch->gclass[m][f][q] = cls;
     }
-    if (cudaGraphLaunch(ch->gexec[f][q], ch->stream) != cudaSuccess) return false;
-    ch->cur_f ^= 1;  // the point buffers are back to q after remesh and reconnect
+    if (cudaGraphLaunch(ge, ch->stream) != cudaSuccess) return false;
+    if (nst & 1) ch->cur_f ^= 1;  // the point buffers are back to q after remesh and reconnect
     return true;
+}
+
+// Queue nsteps coupled steps: multi-step graphs while enough steps remain,
+// then single-step graphs; direct launches when graphs are off or unavailable.
+void queue_steps(vlb_channel* ch, int nsteps) {
+    const bool use_graph = ch->graphs && !ch->timing && ch->stream != nullptr;
+    int k = 0;
+    while (k < nsteps) {
+        if (use_graph && nsteps - k >= GRAPH_MULTI && step_graph(ch, true)) {
+            k += GRAPH_MULTI;
+            ch->steps += GRAPH_MULTI;
+            continue;
+        }
+        if (!(use_graph && step_graph(ch, false))) run_phases(ch, VLB_PHASE_ALL);
+        ++k;
+        ch->steps++;
+    }
 }
 }  // namespace
 
 int vlb_step(vlb_channel* ch, int32_t nsteps) {
     if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
-    const bool use_graph = ch->graphs && !ch->timing && ch->stream != nullptr;
-    for (int k = 0; k < nsteps; ++k) {
-        if (!(use_graph && step_graph(ch))) run_phases(ch, VLB_PHASE_ALL);
-        ch->steps++;
-    }
+    queue_steps(ch, nsteps);
     return finish(ch);
+}
+
+int vlb_step_async(vlb_channel* ch, int32_t nsteps) {
+    if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
+    if (!ch->done && cudaEventCreateWithFlags(&ch->done, cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "event create");
+    queue_steps(ch, nsteps);
+    cudaMemcpyAsync(ch->h_counters, ch->d.counters, sizeof(int) * CNT_COUNT, cudaMemcpyDeviceToHost, ch->stream);
+    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, sizeof(double) * DS_COUNT, cudaMemcpyDeviceToHost, ch->stream);
+    cudaEventRecord(ch->done, ch->stream);
+    ch->pending = true;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+    return VLB_OK;
+}
+
+int vlb_query(vlb_channel* ch) {
+    if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
+    if (!ch->pending) return VLB_OK;
+    const cudaError_t e = cudaEventQuery(ch->done);
+    if (e == cudaErrorNotReady) return VLB_BUSY;
+    ch->pending = false;
+    if (e != cudaSuccess) return cuda_fail(e, "step completion");
+    ch->n_hint = ch->h_counters[CNT_N];
+    std::string msg;
+    const int rc = status_to_code(ch->h_counters[CNT_STATUS], &msg);
+    if (rc) return fail(rc, msg);
+    return VLB_OK;
 }
 
 int vlb_set_graphs(vlb_channel* ch, int32_t enable) {
@@ -666,6 +745,7 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
         o[7] = ch->h_dstats[DS_RECON];
         o[8] = ch->h_dstats[DS_SMALL];
         o[9] = (double)ch->steps;
+        o[10] = (double)ch->bytes;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "read field");

@@ -46,21 +46,23 @@ def concat(parts):
 
 
 def random_rings(n_box, wall, count: int, r_min: float, r_max: float, seed: int,
-                 spacing: float = 0.8, min_sep: float = 2.0, max_tries: int = 200):
+                 spacing: float = 0.8, min_sep: float = 2.0, max_tries: int = 200, skip_crowded: bool = False):
     """``count`` rings with radius ~ U[r_min, r_max], random centres and normals.
 
     Centres are uniform in the box; on wall axes they are kept R + 2 cells
     inside the walls (walls sit half a cell outside the first/last node).  A
     candidate ring that would pass within ``min_sep`` cells of an earlier
     ring is redrawn (intersecting seeds would start from near-singular
-    velocities); min_sep = 0 disables the check.
+    velocities); min_sep = 0 disables the check.  After max_tries the last
+    draw is placed anyway, or dropped when skip_crowded is set.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     box = np.asarray(n_box, np.float64)
     periodic = np.array([not w for w in wall])
-    grid = _PointGrid(box, periodic, max(min_sep, 1e-9))
+    grid = _Occupancy(box, periodic, min_sep) if min_sep > 0 else None
     parts = []
     for _ in range(count):
+        placed = False
         for _try in range(max_tries):
             R = rng.uniform(r_min, r_max)
             c = np.empty(3)
@@ -76,10 +78,14 @@ def random_rings(n_box, wall, count: int, r_min: float, r_max: float, seed: int,
             nrm /= np.linalg.norm(nrm)
             phase = rng.uniform(0.0, 2.0 * np.pi)
             xyz, nxt = ring(c, nrm, R, spacing=spacing, phase=phase)
-            if min_sep <= 0 or grid.clearance(xyz, min_sep) >= min_sep:
+            if grid is None or grid.free(xyz):
+                placed = True
                 break
+        if not placed and skip_crowded:
+            continue
         parts.append((xyz, nxt))
-        grid.add(xyz)
+        if grid is not None:
+            grid.add(xyz)
     xyz, nxt = concat(parts)
     for a in range(3):
         if not wall[a]:
@@ -87,42 +93,38 @@ def random_rings(n_box, wall, count: int, r_min: float, r_max: float, seed: int,
     return xyz, nxt
 
 
-class _PointGrid:
-    """Uniform grid of cell size h over placed points, for clearance queries."""
+class _Occupancy:
+    """Cells of size min_sep/2 within two cells of a placed point.
 
-    def __init__(self, box, periodic, h):
-        self.box, self.periodic, self.h = box, periodic, h
-        self.ncell = np.maximum(np.floor(box / h).astype(int), 1)
-        self.cells = {}
+    A candidate point in a free cell is at least min_sep from every placed
+    point (the test is conservative: some farther candidates are refused too).
+    """
 
-    def _key(self, c):
-        c = np.where(self.periodic, np.mod(c, self.ncell), c)
-        return tuple(int(v) for v in c)
+    def __init__(self, box, periodic, min_sep):
+        self.box, self.periodic = box, periodic
+        self.h = 0.5 * min_sep
+        self.n = np.maximum(np.ceil(box / self.h).astype(int) + 4, 1)
+        self.occ = np.zeros(tuple(self.n), dtype=bool)
+        self.off = np.array([(i, j, k) for i in range(-2, 3) for j in range(-2, 3) for k in range(-2, 3)])
 
-    def _cells_of(self, pts):
-        return np.floor(np.where(self.periodic, np.mod(pts, self.box), pts) / self.h).astype(int)
+    def _cells(self, pts):
+        q = np.where(self.periodic, np.mod(pts, self.box), pts)
+        c = np.floor(q / self.h).astype(int) + 2
+        return c
+
+    def _wrap(self, c):
+        nper = np.ceil(self.box / self.h).astype(int)
+        w = np.where(self.periodic, np.mod(c - 2, nper) + 2, c)
+        return np.clip(w, 0, self.n - 1)
 
     def add(self, pts):
-        for q, c in zip(pts, self._cells_of(pts)):
-            self.cells.setdefault(self._key(c), []).append(q)
+        c = self._cells(pts)
+        allc = self._wrap((c[:, None, :] + self.off[None, :, :]).reshape(-1, 3))
+        self.occ[allc[:, 0], allc[:, 1], allc[:, 2]] = True
 
-    def clearance(self, pts, stop_below=0.0):
-        """Smallest distance from pts to the placed points (stops early below stop_below)."""
-        best = np.inf
-        if not self.cells:
-            return best
-        offs = [(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]
-        for q, c in zip(pts, self._cells_of(pts)):
-            for o in offs:
-                lst = self.cells.get(self._key(c + np.array(o)))
-                if not lst:
-                    continue
-                d = np.asarray(lst) - q
-                d = np.where(self.periodic, d - self.box * np.round(d / self.box), d)
-                best = min(best, float(np.sqrt((d * d).sum(-1)).min()))
-                if best < stop_below:
-                    return best
-        return best
+    def free(self, pts):
+        c = self._wrap(self._cells(pts))
+        return not self.occ[c[:, 0], c[:, 1], c[:, 2]].any()
 
 
 def perturbed_equilibrium(ncell: int, seed: int, amp: float = 1e-3):

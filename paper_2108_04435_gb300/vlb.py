@@ -25,7 +25,8 @@ FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_FDEV = 6, 7, 8, 9
 EXPORTS = ["vlb_create_channel", "vlb_seed_vortices", "vlb_step", "vlb_run_phases", "vlb_read_fields",
            "vlb_write_fields", "vlb_line_length", "vlb_destroy", "vlb_last_error", "vlb_set_timing",
            "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart", "vlb_set_graphs",
-           "vlb_biot_savart_noalloc"]
+           "vlb_biot_savart_noalloc", "vlb_step_async", "vlb_query", "vlb_channel_bytes"]
+BUSY = 1
 
 
 class Params(C.Structure):
@@ -84,6 +85,10 @@ def lib():
         L.vlb_biot_savart_scratch_bytes.restype = C.c_size_t
         L.vlb_biot_savart.argtypes = [C.POINTER(Params), vp, vp, C.c_int32, vp, vp, C.c_size_t, vp]
         L.vlb_biot_savart_noalloc.argtypes = [C.POINTER(Params), vp, vp, C.c_int32, vp, vp]
+        L.vlb_step_async.argtypes = [vp, C.c_int32]
+        L.vlb_query.argtypes = [vp]
+        L.vlb_channel_bytes.argtypes = [C.POINTER(Params)]
+        L.vlb_channel_bytes.restype = C.c_size_t
         _lib = L
     return _lib
 
@@ -170,6 +175,18 @@ class Channel:
             check(rc)
         return rc
 
+    def step_async(self, nsteps: int):
+        """Queue nsteps coupled steps on the channel's stream and return."""
+        check(lib().vlb_step_async(self.h, nsteps))
+
+    def query(self) -> bool:
+        """True once the queued steps have finished (raises on a device error)."""
+        rc = lib().vlb_query(self.h)
+        if rc == BUSY:
+            return False
+        check(rc)
+        return True
+
     def run_phases(self, mask: int, raise_on_error: bool = True) -> int:
         rc = lib().vlb_run_phases(self.h, mask)
         if raise_on_error:
@@ -240,3 +257,8 @@ def biot_savart_noalloc(params: dict, pos_dev: int, next_dev: int, n: int, vel_d
     p = make_params(params)
     check(lib().vlb_biot_savart_noalloc(C.byref(p), C.c_void_p(pos_dev), C.c_void_p(next_dev), n,
                                         C.c_void_p(vel_dev), C.c_void_p(stream)))
+
+
+def channel_bytes(params: dict) -> int:
+    """Device bytes a channel with these parameters allocates (0 if invalid)."""
+    return int(lib().vlb_channel_bytes(C.byref(make_params(params))))

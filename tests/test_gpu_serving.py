@@ -1,0 +1,60 @@
+"""Serving on the GPU: runs admitted together overlap on separate streams and
+each gives the same result as when it is served alone, within 1e-5 relative
+(the per-step tolerance of the method; the difference is the FP32 round-off
+of the order in which the force spreading's atomic additions land)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def small_requests():
+    from paper_2108_04435_gb300 import configs
+    reqs = configs.serving_requests(5, 50.0, 7, 60, grids=((32, 32, 32), (48, 48, 48), (64, 64, 64)),
+                                    points=(100, 800))
+    for r in reqs:
+        n = r["params"]["n"]
+        r["cells"] = n[0] * n[1] * n[2]
+    return reqs
+
+
+def test_same_alone_and_in_the_mix():
+    import copy
+    from paper_2108_04435_gb300 import serve, vlb
+    reqs = small_requests()
+    budget = sum(vlb.channel_bytes(r["params"]) for r in reqs)
+    mix, summary = serve.serve_gpu(copy.deepcopy(reqs), budget_bytes=budget, max_slots=5, slice_steps=20,
+                                   realtime=False)
+    assert summary["failed"] == 0 and summary["peak_slots"] >= 2
+    for r in reqs:
+        alone, _ = serve.serve_gpu([copy.deepcopy(r)], budget_bytes=budget, max_slots=1, slice_steps=20,
+                                   realtime=False)
+        a, m = alone[0], mix[r["id"]]
+        assert a.steps == m.steps == 60
+        assert a.n_points == m.n_points
+        assert abs(a.line_length / m.line_length - 1) < 1e-5
+
+
+def test_budget_limits_concurrency():
+    import copy
+    from paper_2108_04435_gb300 import serve, vlb
+    reqs = small_requests()
+    biggest = max(vlb.channel_bytes(r["params"]) for r in reqs)
+    res, summary = serve.serve_gpu(copy.deepcopy(reqs), budget_bytes=biggest, max_slots=5, slice_steps=20,
+                                   realtime=False)
+    assert summary["failed"] == 0
+    assert summary["peak_bytes"] <= biggest
+    full, s2 = serve.serve_gpu(copy.deepcopy(reqs), budget_bytes=10 * biggest, max_slots=5, slice_steps=20,
+                               realtime=False)
+    assert s2["peak_slots"] > summary["peak_slots"]
+
+
+def test_channel_bytes_covers_allocation():
+    from paper_2108_04435_gb300 import configs, vlb
+    for name in ("ring32", "channel64x64x256"):
+        p, xyz, nxt = configs.config(name)
+        for st in (0, 1):
+            p["storage"] = st
+            ch = vlb.Channel(p)
+            assert vlb.channel_bytes(p) >= ch.stats()[10] > 0
+            ch.close()
