@@ -109,8 +109,10 @@ enum {
                                5 splits, 6 merges, 7 reconnections, 8 points deleted in small loops,
                                9 steps, 10 device bytes allocated, 11..15 reserved */
     VLB_FIELD_VEL = 8,      /* float64 [N][3]: ds/dt at the first RK stage of the last filament advance */
-    VLB_FIELD_FDEV = 9      /* float32 [19][C]: f_i - w_i rho0 of the post-collision populations (read only;
+    VLB_FIELD_FDEV = 9,     /* float32 [19][C]: f_i - w_i rho0 of the post-collision populations (read only;
                                the flow signal at full float precision) */
+    VLB_FIELD_LINE_PROFILE = 10 /* float64 [n_z]: line length per z plane, each segment counted in the plane
+                                   nearest its midpoint (line density L(z) = profile / (n_x n_y), Sec. IV) */
 };
 
 /* Create a channel (Sec. II set-up): validates p (tau > 1/2, stream_axis 2,

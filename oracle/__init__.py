@@ -26,7 +26,7 @@ _lib = None
 
 PHASE_LBM, PHASE_VFM, PHASE_REMESH, PHASE_RECONNECT, PHASE_ALL = 1, 2, 4, 8, 15
 FIELD_RHO, FIELD_U, FIELD_FSTAR, FIELD_FORCE, FIELD_POS, FIELD_NEXT = 0, 1, 2, 3, 4, 5
-FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_ULAST = 6, 7, 8, 9
+FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_ULAST, FIELD_LINE_PROFILE = 6, 7, 8, 9, 10
 
 
 def build(force: bool = False) -> str:
@@ -203,6 +203,7 @@ class Channel:
             FIELD_FORCE: (3, self.ncell), FIELD_ULAST: (3, self.ncell),
             FIELD_POS: (N, 3), FIELD_VEL: (N, 3), FIELD_NEXT: (N,),
             FIELD_PLANE_VS: (self.n[self.params.get("stream_axis", 2)],), FIELD_STATS: (16,),
+            FIELD_LINE_PROFILE: (self.n[self.params.get("stream_axis", 2)],),
         }
         dtype = np.int32 if which == FIELD_NEXT else np.float64
         out = np.zeros(shapes[which], dtype)

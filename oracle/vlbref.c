@@ -797,6 +797,23 @@ static double line_length(const vlbref_channel* ch) {
     return L;
 }
 
+/* Line length per stream plane (the profile behind the line density L(x) of
+ * Sec. IV, Fig. 8b): each segment's length goes to the plane nearest its
+ * midpoint (periodic axes wrap, walls clamp). */
+static void line_profile(const vlbref_channel* ch, double* prof) {
+    const int sa = ch->p.stream_axis, ns = ch->p.n[sa];
+    for (int k = 0; k < ns; ++k) prof[k] = 0.0;
+    for (int i = 0; i < ch->N; ++i) {
+        double b[3];
+        diff3(ch, &ch->pos[3 * ch->next[i]], &ch->pos[3 * i], b);
+        double mid = ch->pos[3 * i + sa] + 0.5 * b[sa];
+        int k = (int)floor(mid + 0.5);
+        if (!ch->p.wall[sa]) k = ((k % ns) + ns) % ns;
+        else k = k < 0 ? 0 : (k > ns - 1 ? ns - 1 : k);
+        prof[k] += norm3(b);
+    }
+}
+
 int vlbref_line_length(vlbref_channel* ch, double* out) {
     if (!ch || !out) return VLBREF_ERR_INVALID_ARG;
     *out = line_length(ch);
@@ -813,7 +830,9 @@ int vlbref_read_fields(vlbref_channel* ch, int32_t which, void* dst, size_t byte
     case VLBREF_FIELD_FSTAR: need = sizeof(double) * Q * (size_t)C; break;
     case VLBREF_FIELD_POS: case VLBREF_FIELD_VEL: need = sizeof(double) * 3 * (size_t)ch->N; break;
     case VLBREF_FIELD_NEXT: need = sizeof(int32_t) * (size_t)ch->N; break;
-    case VLBREF_FIELD_PLANE_VS: need = sizeof(double) * (size_t)ch->p.n[ch->p.stream_axis]; break;
+    case VLBREF_FIELD_PLANE_VS: case VLBREF_FIELD_LINE_PROFILE:
+        need = sizeof(double) * (size_t)ch->p.n[ch->p.stream_axis];
+        break;
     case VLBREF_FIELD_STATS: need = sizeof(double) * 16; break;
     default: return VLBREF_ERR_INVALID_ARG;
     }
@@ -844,6 +863,8 @@ int vlbref_read_fields(vlbref_channel* ch, int32_t which, void* dst, size_t byte
         memcpy(dst, ch->next, need);
     } else if (which == VLBREF_FIELD_PLANE_VS) {
         memcpy(d, ch->Vs, need);
+    } else if (which == VLBREF_FIELD_LINE_PROFILE) {
+        line_profile(ch, d);
     } else {
         for (int k = 0; k < 16; ++k) d[k] = 0.0;
         d[0] = ch->N; d[1] = ch->status; d[2] = ch->mass; d[3] = line_length(ch);

@@ -71,7 +71,8 @@ enum {
     VLBREF_FIELD_PLANE_VS = 6, /* [n_s]    superfluid velocity per stream plane (Eq. 18) */
     VLBREF_FIELD_STATS = 7,    /* [16]     see vlbref.c */
     VLBREF_FIELD_VEL = 8,      /* [N][3]   stage-1 ds/dt of the last filament advance */
-    VLBREF_FIELD_ULAST = 9     /* [3][C]   velocity u^n seen by the last filament advance */
+    VLBREF_FIELD_ULAST = 9,    /* [3][C]   velocity u^n seen by the last filament advance */
+    VLBREF_FIELD_LINE_PROFILE = 10 /* [n_s] line length per stream plane */
 };
 
 int  vlbref_create(const vlbref_params* p, vlbref_channel** out);

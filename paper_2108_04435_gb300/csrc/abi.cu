@@ -693,7 +693,7 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
         case VLB_FIELD_FSTAR: case VLB_FIELD_FDEV: need = sizeof(float) * 19 * (size_t)C; break;
         case VLB_FIELD_POS: case VLB_FIELD_VEL: need = sizeof(double) * 3 * (size_t)N; break;
         case VLB_FIELD_NEXT: need = sizeof(int) * (size_t)N; break;
-        case VLB_FIELD_PLANE_VS: need = sizeof(double) * (size_t)ch->lp.g.nz; break;
+        case VLB_FIELD_PLANE_VS: case VLB_FIELD_LINE_PROFILE: need = sizeof(double) * (size_t)ch->lp.g.nz; break;
         case VLB_FIELD_STATS: need = sizeof(double) * 16; break;
         default: return fail(VLB_ERR_INVALID_ARG, "unknown field");
     }
@@ -729,6 +729,10 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
         if (N > 0) e = cudaMemcpyAsync(dst, d.next[ch->cur_p], need, cudaMemcpyDeviceToHost, s);
     } else if (which == VLB_FIELD_PLANE_VS) {
         e = cudaMemcpyAsync(dst, d.Vs, need, cudaMemcpyDeviceToHost, s);
+    } else if (which == VLB_FIELD_LINE_PROFILE) {
+        double* prof = (double*)tmp;  // spare population buffer
+        launch_line_profile(ch->lp.g, d.pos[ch->cur_p], d.next[ch->cur_p], d.counters, ch->cap, prof, s);
+        e = cudaMemcpyAsync(dst, prof, need, cudaMemcpyDeviceToHost, s);
     } else {
         launch_line_length(ch->lp.g, d.pos[ch->cur_p], d.next[ch->cur_p], d.counters, ch->cap, d.line_part, d.dstats, s);
         rc = sync_counters(ch);

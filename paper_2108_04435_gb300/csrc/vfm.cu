@@ -279,8 +279,24 @@ __global__ void __launch_bounds__(256) k_line_length(Grid g, const double* __res
     }
 }
 
-}  // namespace
+// Line length per z plane: each segment's length goes to the plane nearest
+// its midpoint (periodic z wraps, walls clamp); FP64 atomics.
+__global__ void k_line_profile(Grid g, const double* __restrict__ pos, const int* __restrict__ next,
+                               const int* __restrict__ counters, int cap, double* __restrict__ prof) {
+    const int N = counters[CNT_N];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int q = next[i];
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = min_image(g, k, pos[(long long)k * cap + q] - pos[(long long)k * cap + i]);
+    const double mid = pos[2LL * cap + i] + 0.5 * d[2];
+    int k = (int)floor(mid + 0.5);
+    if (!g.wall[2]) k = ((k % g.nz) + g.nz) % g.nz;
+    else k = k < 0 ? 0 : (k > g.nz - 1 ? g.nz - 1 : k);
+    atomicAdd(&prof[k], sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+}
 
+}  // namespace
 
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
                            int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st) {
@@ -299,6 +315,12 @@ void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, dou
 void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,
                         double* dstats, cudaStream_t s) {
     k_line_length<<<(cap + 255) / 256, 256, 0, s>>>(g, pos, next, counters, cap, part, dstats);
+}
+
+void launch_line_profile(const Grid& g, const double* pos, const int* next, const int* counters, int cap,
+                         double* prof, cudaStream_t s) {
+    cudaMemsetAsync(prof, 0, sizeof(double) * (size_t)g.nz, s);
+    if (cap > 0) k_line_profile<<<(cap + 255) / 256, 256, 0, s>>>(g, pos, next, counters, cap, prof);
 }
 
 }  // namespace vlb

@@ -180,6 +180,8 @@ void launch_geometry_stage(const VfmParams& P, const double* s, const int* next,
 void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, double* st, double* pos_out,
                 double* acc, double* vel1, const float4* geo, const float* vbs, const float* U, const double* Vs,
                 float* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s);
+void launch_line_profile(const Grid& g, const double* pos, const int* next, const int* counters, int cap,
+                         double* prof, cudaStream_t s);
 void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,
                         double* dstats, cudaStream_t s);
 

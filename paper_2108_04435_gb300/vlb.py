@@ -20,7 +20,7 @@ ERR = {-1: "INVALID_ARG", -2: "OOM", -3: "CAPACITY", -4: "TOPOLOGY", -5: "MACH",
        -7: "TIMEOUT", -8: "CUDA", -9: "CFL"}
 PHASE_LBM, PHASE_VFM, PHASE_REMESH, PHASE_RECONNECT, PHASE_ALL = 1, 2, 4, 8, 15
 FIELD_RHO, FIELD_U, FIELD_FSTAR, FIELD_FORCE, FIELD_POS, FIELD_NEXT = 0, 1, 2, 3, 4, 5
-FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_FDEV = 6, 7, 8, 9
+FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_FDEV, FIELD_LINE_PROFILE = 6, 7, 8, 9, 10
 
 EXPORTS = ["vlb_create_channel", "vlb_seed_vortices", "vlb_step", "vlb_run_phases", "vlb_read_fields",
            "vlb_write_fields", "vlb_line_length", "vlb_destroy", "vlb_last_error", "vlb_set_timing",
@@ -211,6 +211,7 @@ class Channel:
             FIELD_FORCE: ((3, self.ncell), np.float32),
             FIELD_POS: ((N, 3), np.float64), FIELD_VEL: ((N, 3), np.float64), FIELD_NEXT: ((N,), np.int32),
             FIELD_PLANE_VS: ((self.n[2],), np.float64), FIELD_STATS: ((16,), np.float64),
+            FIELD_LINE_PROFILE: ((self.n[2],), np.float64),
         }
         shape, dt = shapes[which]
         out = np.zeros(shape, dt)

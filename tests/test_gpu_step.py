@@ -23,6 +23,8 @@ def compare_step(g, r, xyz, n, wall, tol=1e-5, line_tol=1e-9):
     pg, pr = g.read(vlb.FIELD_POS), r.read(oracle.FIELD_POS)
     assert rel_l2(g.read(vlb.FIELD_VEL), r.read(oracle.FIELD_VEL)) < tol
     assert abs(g.line_length() / r.line_length() - 1) < line_tol
+    prof_g, prof_r = g.read(vlb.FIELD_LINE_PROFILE), r.read(oracle.FIELD_LINE_PROFILE)
+    assert np.abs(prof_g - prof_r).sum() < max(line_tol, 1e-9) * prof_r.sum()
     return pg, pr
 
 

@@ -109,3 +109,13 @@ def test_biot_savart_entry_point(case):
     _, vbs = r.point_velocity()
     got = _bs_gpu(p, r.read(oracle.FIELD_POS), r.read(oracle.FIELD_NEXT))
     assert rel_l2(got, vbs) < 1e-5
+
+
+def test_line_profile_parity():
+    import oracle
+    from paper_2108_04435_gb300 import vlb
+    for n, wall in (((32, 32, 40), (0, 0, 0)), ((36, 32, 48), (1, 1, 1))):
+        xyz, nxt = filaments("tangle", n, wall, seed=3)
+        g, r = pair(vparams(n, wall), xyz, nxt)
+        pg, pr = g.read(vlb.FIELD_LINE_PROFILE), r.read(oracle.FIELD_LINE_PROFILE)
+        assert np.abs(pg - pr).max() < 1e-10 * pr.sum()

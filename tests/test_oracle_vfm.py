@@ -180,3 +180,22 @@ def test_friction_reaction_total(oracle_mod):
     ch.run_phases(oracle_mod.PHASE_VFM)
     F = ch.read(oracle_mod.FIELD_FORCE)
     assert np.abs(F.sum(axis=1) - expect).max() < 1e-15
+
+
+def test_line_profile_of_tilted_ring(oracle_mod):
+    """The profile sums to the line length; a ring in a z = const plane puts
+    all its length in that plane, and a ring tilted about x spreads it over
+    the planes it crosses symmetrically about its centre."""
+    p = vparams(n=(32, 32, 32))
+    ch = oracle_mod.Channel(p)
+    xyz, nxt = inputs.ring((16, 16, 16.2), (0, 0, 1), 6.0, npts=48)
+    ch.seed(xyz, nxt)
+    prof = ch.read(oracle_mod.FIELD_LINE_PROFILE)
+    assert abs(prof.sum() - ch.line_length()) < 1e-12
+    assert abs(prof[16] - ch.line_length()) < 1e-12
+    xyz, nxt = inputs.ring((16, 16, 16.0), (0, 1, 0), 6.0, npts=48)
+    ch.seed(xyz, nxt)
+    prof = ch.read(oracle_mod.FIELD_LINE_PROFILE)
+    assert abs(prof.sum() - ch.line_length()) < 1e-12
+    assert np.abs(prof[10:16][::-1] - prof[17:23]).max() < 0.2
+    assert prof[:9].sum() == 0 and prof[24:].sum() == 0
