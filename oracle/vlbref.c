@@ -33,7 +33,7 @@
  * Stats array (VLBREF_FIELD_STATS, 16 doubles):
  *   0 points  1 status bits  2 mass  3 line length  4 max Mach  5 splits
  *   6 merges  7 reconnections  8 points deleted in small loops  9 steps
- *   10..12 momentum sum(rho u)  13..15 reserved
+ *   10..12 momentum sum(rho u)  13 wall-contact cuts  14..15 reserved
  * Status bits: 1 Mach >= 0.05, 2 NaN, 4 capacity, 16 stage displacement >= 1.
  */
 #include "vlbref.h"
@@ -80,7 +80,7 @@ struct vlbref_channel {
     int* next;
     int* prev;
     double* vel1;  /* [cap][3] stage-1 ds/dt of the last advance */
-    long n_split, n_merge, n_reconnect, n_small;
+    long n_split, n_merge, n_reconnect, n_small, n_wallcut;
     char err[256];
 };
 
@@ -115,6 +115,24 @@ static void cross3(const double* a, const double* b, double* out) {
 
 static void set_err(vlbref_channel* ch, const char* msg) {
     if (ch) snprintf(ch->err, sizeof ch->err, "%s", msg);
+}
+
+/* Walls sit halfway between the last fluid node and the outside, at -1/2
+ * and n - 1/2; filament points are kept dxi_min/2 inside them.  These are the
+ * two clamp bounds of a wall axis. */
+static double wall_lo(const vlbref_channel* ch) { return -0.5 + 0.5 * ch->p.dxi_min; }
+static double wall_hi(const vlbref_channel* ch, int a) { return (double)ch->p.n[a] - 0.5 - 0.5 * ch->p.dxi_min; }
+
+/* The first clamp bound that position s touches, in the order x-, x+, y-, y+,
+ * z-, z+, as 2*axis + side (side 1 = high wall); -1 when none.  An open end of
+ * a line is pinned to this wall. */
+static int touching_wall(const vlbref_channel* ch, const double* s) {
+    for (int a = 0; a < 3; ++a) {
+        if (!ch->p.wall[a]) continue;
+        if (s[a] <= wall_lo(ch)) return 2 * a;
+        if (s[a] >= wall_hi(ch, a)) return 2 * a + 1;
+    }
+    return -1;
 }
 
 /* --------------------------------------------------------- LBM pieces (II.B) */
@@ -327,19 +345,37 @@ static void segment_add(const double* R1, const double* d, double kappa, double*
 /* Per-point geometry of the discretised filament: three-point derivatives on
  * the non-uniform arc-length grid, the segment-length weight and the local
  * (LIA) velocity beta s' x s'' of the divergent part of Eq. 3. */
+/* An open end pinned on a wall takes as its missing neighbour the mirror image
+ * of its present neighbour across that wall (the line continued by its image);
+ * an end touching no wall (not produced by the rules below) is continued
+ * straight.  The end represents half of its one real segment. */
 static void point_geometry(const vlbref_channel* ch, const double* s, int i, double* sp, double* spp,
                            double* dxi, double* lia, double* lplus) {
     int p = ch->prev[i], q = ch->next[i];
     double a[3], b[3];
-    diff3(ch, &s[3 * i], &s[3 * p], a); /* s_i - s_p */
-    diff3(ch, &s[3 * q], &s[3 * i], b); /* s_q - s_i */
+    if (p >= 0) diff3(ch, &s[3 * i], &s[3 * p], a); /* s_i - s_p */
+    if (q >= 0) diff3(ch, &s[3 * q], &s[3 * i], b); /* s_q - s_i */
+    if (p < 0 || q < 0) {
+        int nb = p < 0 ? q : p, code = touching_wall(ch, &s[3 * i]);
+        double g[3], *ghost_diff = p < 0 ? a : b;
+        for (int k = 0; k < 3; ++k) g[k] = s[3 * nb + k];
+        if (code >= 0) {
+            int ax = code >> 1;
+            double w = (code & 1) ? (double)ch->p.n[ax] - 0.5 : -0.5;
+            g[ax] = 2.0 * w - s[3 * nb + ax];
+            if (p < 0) diff3(ch, &s[3 * i], g, ghost_diff); /* s_i - ghost */
+            else diff3(ch, g, &s[3 * i], ghost_diff);       /* ghost - s_i */
+        } else {
+            for (int k = 0; k < 3; ++k) ghost_diff[k] = p < 0 ? b[k] : a[k];
+        }
+    }
     double lm = norm3(a), lp = norm3(b);
     double den = lp * lm * (lp + lm);
     for (int k = 0; k < 3; ++k) {
         sp[k] = (lm * lm * b[k] + lp * lp * a[k]) / den;
         spp[k] = 2.0 * (lm * b[k] - lp * a[k]) / den;
     }
-    *dxi = 0.5 * (lp + lm);
+    *dxi = p < 0 ? 0.5 * lp : (q < 0 ? 0.5 * lm : 0.5 * (lp + lm));
     double beta = ch->p.kappa / (4.0 * PI) * log(2.0 * sqrt(lp * lm) / (exp(0.25) * ch->p.core_a));
     double c[3];
     cross3(sp, spp, c);
@@ -360,13 +396,13 @@ static void filament_velocity(vlbref_channel* ch, const double* s, double* k, do
     double* fr = (double*)malloc(sizeof(double) * 3 * (size_t)N);
     for (int i = 0; i < N; ++i) {
         point_geometry(ch, s, i, &sp[3 * i], &spp[3 * i], &dxi[i], &lia[3 * i], NULL);
-        diff3(ch, &s[3 * ch->next[i]], &s[3 * i], &seg[3 * i]); /* segment i -> next(i) */
+        if (ch->next[i] >= 0) diff3(ch, &s[3 * ch->next[i]], &s[3 * i], &seg[3 * i]); /* segment i -> next(i) */
     }
 #pragma omp parallel for schedule(dynamic, 16)
     for (int i = 0; i < N; ++i) {
         double vbs[3] = {0.0, 0.0, 0.0};
         for (int j = 0; j < N; ++j) {
-            if (j == i || ch->next[j] == i) continue; /* adjacent segments: local term */
+            if (j == i || ch->next[j] == i || ch->next[j] < 0) continue; /* adjacent: local term; open end: none */
             double R1[3];
             diff3(ch, &s[3 * j], &s[3 * i], R1);
             segment_add(R1, &seg[3 * j], ch->p.kappa, vbs);
@@ -381,6 +417,10 @@ static void filament_velocity(vlbref_channel* ch, const double* s, double* k, do
         for (int a = 0; a < 3; ++a) {
             fr[3 * i + a] = ch->p.alpha * t[a] - ch->p.alpha_p * tt[a];
             k[3 * i + a] = vs[a] + fr[3 * i + a]; /* Eq. 4 */
+        }
+        if (ch->prev[i] < 0 || ch->next[i] < 0) { /* a pinned end slides along its wall */
+            int code = touching_wall(ch, &s[3 * i]);
+            if (code >= 0) k[3 * i + (code >> 1)] = 0.0;
         }
         if (vbs_out)
             for (int a = 0; a < 3; ++a) vbs_out[3 * i + a] = vbs[a];
@@ -472,14 +512,22 @@ static int outranks(int a, int b) {
     return ha > hb || (ha == hb && a < b);
 }
 
-/* Mark points of loops with fewer than five points (next^k(i) == i, k <= 4). */
-static int in_small_loop(const int* next, int i) {
-    int j = i;
-    for (int k = 1; k <= 4; ++k) {
-        j = next[j];
-        if (j == i) return 1;
-    }
-    return 0;
+/* Is point i on a loop or an open line of fewer than five points?  prev must
+ * be the predecessor array of next (-1 at a line's first point). */
+static int in_small_component(const int* next, const int* prev, int i) {
+    int j = i, size = 1;
+    while (next[j] >= 0 && next[j] != i && size < 5) { j = next[j]; ++size; }
+    if (size >= 5) return 0;
+    if (next[j] == i) return 1; /* a loop of fewer than five points */
+    j = i;
+    while (prev[j] >= 0 && size < 5) { j = prev[j]; ++size; }
+    return size < 5;
+}
+
+static void predecessors(const int* next, const int* alive, int total, int* prev) {
+    for (int k = 0; k < total; ++k) prev[k] = -1;
+    for (int k = 0; k < total; ++k)
+        if (alive[k] && next[k] >= 0) prev[next[k]] = k;
 }
 
 /* Keep the alive points in ascending index order and renumber next/prev. */
@@ -491,10 +539,12 @@ static void compact(vlbref_channel* ch, int total, const double* pos, const int*
         if (!alive[k]) continue;
         int nk = idx[k];
         for (int a = 0; a < 3; ++a) ch->pos[3 * nk + a] = pos[3 * k + a];
-        ch->next[nk] = idx[next[k]];
+        ch->next[nk] = next[k] >= 0 ? idx[next[k]] : -1;
     }
     ch->N = m;
-    for (int k = 0; k < m; ++k) ch->prev[ch->next[k]] = k;
+    for (int k = 0; k < m; ++k) ch->prev[k] = -1;
+    for (int k = 0; k < m; ++k)
+        if (ch->next[k] >= 0) ch->prev[ch->next[k]] = k;
     free(idx);
 }
 
@@ -502,10 +552,11 @@ static void compact(vlbref_channel* ch, int total, const double* pos, const int*
  * all decisions are taken on the state before the pass.
  *  split: segment i->q with l > dxi_max gets the arc midpoint
  *         m = s_i + b/2 - (l^2/16)(s''_i + s''_q), appended in ascending i;
- *  merge: point i is a candidate if min(l-, l+) < dxi_min, |s_q - s_p| <= dxi_max
- *         and neither adjacent segment splits; a candidate is removed unless a
- *         neighbouring candidate outranks it (fmix32 priority, see outranks());
- *  loops left with fewer than five points are deleted. */
+ *  merge: point i with both neighbours is a candidate if min(l-, l+) < dxi_min,
+ *         |s_q - s_p| <= dxi_max and neither adjacent segment splits; a
+ *         candidate is removed unless a neighbouring candidate outranks it
+ *         (fmix32 priority, see outranks()); open ends are never removed;
+ *  loops and open lines left with fewer than five points are deleted. */
 static void remesh(vlbref_channel* ch) {
     const int N = ch->N;
     if (N == 0) return;
@@ -519,14 +570,16 @@ static void remesh(vlbref_channel* ch) {
     for (int i = 0; i < N; ++i) {
         double sp[3], dxi, lia[3];
         point_geometry(ch, ch->pos, i, sp, &spp[3 * i], &dxi, lia, &l[i]);
+        if (ch->next[i] < 0) l[i] = 0.0; /* no segment leaves an end */
     }
     int S = 0;
     for (int i = 0; i < N; ++i) {
-        split[i] = l[i] > dmax;
+        split[i] = ch->next[i] >= 0 && l[i] > dmax;
         rank[i] = split[i] ? S++ : -1;
     }
     for (int i = 0; i < N; ++i) {
         int p = ch->prev[i], q = ch->next[i];
+        if (p < 0 || q < 0) continue;
         double pq[3];
         diff3(ch, &ch->pos[3 * q], &ch->pos[3 * p], pq);
         double lmin = l[p] < l[i] ? l[p] : l[i];
@@ -547,7 +600,9 @@ static void remesh(vlbref_channel* ch) {
         alive[i] = !rem[i];
         if (rem[i]) { ++merges; continue; }
         int q = ch->next[i];
-        if (split[i] && S > 0) {
+        if (q < 0) {
+            nnext[i] = -1;
+        } else if (split[i] && S > 0) {
             int m = N + rank[i];
             double b[3];
             diff3(ch, &ch->pos[3 * q], &ch->pos[3 * i], b);
@@ -565,10 +620,13 @@ static void remesh(vlbref_channel* ch) {
     }
     long small = 0;
     int* alive2 = (int*)malloc(sizeof(int) * (size_t)total);
+    int* nprev = (int*)malloc(sizeof(int) * (size_t)total);
+    predecessors(nnext, alive, total, nprev);
     for (int k = 0; k < total; ++k) {
-        alive2[k] = alive[k] && !in_small_loop(nnext, k);
+        alive2[k] = alive[k] && !in_small_component(nnext, nprev, k);
         if (alive[k] && !alive2[k]) ++small;
     }
+    free(nprev);
     ch->n_split += S;
     ch->n_merge += merges;
     ch->n_small += small;
@@ -586,9 +644,14 @@ static void remesh(vlbref_channel* ch) {
  *     {(i, j), (i, p(j)), (p(i), j), (p(i), p(j))} are tried in that order and
  *     the first one with the largest length decrease
  *     l_a + l_b - |s_qb - s_a| - |s_qa - s_b| is kept if that decrease is > 0;
+ *     (a pair whose a or b is missing or is a line's last point is not tried);
  *  3. exchanges are applied in ascending (d_ij^2, i); one that touches a point
  *     already used by an applied exchange (a, qa, b, qb) is skipped;
- *  4. loops left with fewer than five points are deleted. */
+ *  4. wall contact: a point with both neighbours that touches a wall's clamp
+ *     bound, taken in ascending index and skipped if it or a neighbour is
+ *     already used, cuts its line there: it is deleted, its neighbours become
+ *     the ends of the cut line and are moved onto the same bound (pinned);
+ *  5. loops and open lines left with fewer than five points are deleted. */
 static double seg_len(const vlbref_channel* ch, int a, int b) {
     double d[3];
     diff3(ch, &ch->pos[3 * b], &ch->pos[3 * a], d);
@@ -604,7 +667,7 @@ static void reconnect(vlbref_channel* ch) {
 #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < N; ++i) {
         int p = ch->prev[i], q = ch->next[i];
-        int pp = ch->prev[p], qq = ch->next[q];
+        int pp = p >= 0 ? ch->prev[p] : -1, qq = q >= 0 ? ch->next[q] : -1;
         int best = -1;
         double bd = 0.0;
         for (int j = 0; j < N; ++j) {
@@ -631,7 +694,9 @@ static void reconnect(vlbref_channel* ch) {
         double best = 0.0;
         int pick = -1;
         for (int k = 0; k < 4; ++k) {
-            int a = as[k], b = bs[k], qa = ch->next[a], qb = ch->next[b];
+            int a = as[k], b = bs[k];
+            if (a < 0 || b < 0 || ch->next[a] < 0 || ch->next[b] < 0) continue;
+            int qa = ch->next[a], qb = ch->next[b];
             double gain = (seg_len(ch, a, qa) + seg_len(ch, b, qb)) - (seg_len(ch, a, qb) + seg_len(ch, b, qa));
             if (gain > 0.0 && (pick < 0 || gain > best)) { best = gain; pick = k; }
         }
@@ -662,13 +727,32 @@ static void reconnect(vlbref_channel* ch) {
     }
     ch->n_reconnect += applied;
     int* alive = (int*)malloc(sizeof(int) * (size_t)N);
+    for (int k = 0; k < N; ++k) alive[k] = 1;
+    long cuts = 0;
+    for (int i = 0; i < N; ++i) {
+        int p = ch->prev[i], q = ch->next[i];
+        if (p < 0 || q < 0 || claimed[i] || claimed[p] || claimed[q]) continue;
+        int code = touching_wall(ch, &ch->pos[3 * i]);
+        if (code < 0) continue;
+        int ax = code >> 1;
+        double bound = (code & 1) ? wall_hi(ch, ax) : wall_lo(ch);
+        claimed[i] = claimed[p] = claimed[q] = 1;
+        alive[i] = 0;
+        ch->next[p] = -1;
+        ch->prev[q] = -1;
+        ch->pos[3 * p + ax] = bound;
+        ch->pos[3 * q + ax] = bound;
+        ++cuts;
+    }
+    ch->n_wallcut += cuts;
     long small = 0;
     for (int k = 0; k < N; ++k) {
-        alive[k] = !in_small_loop(ch->next, k);
+        if (!alive[k]) continue;
+        alive[k] = !in_small_component(ch->next, ch->prev, k);
         if (!alive[k]) ++small;
     }
     ch->n_small += small;
-    if (small > 0) {
+    if (small > 0 || cuts > 0) {
         double* cpos = (double*)malloc(sizeof(double) * 3 * (size_t)N);
         int* cnext = (int*)malloc(sizeof(int) * (size_t)N);
         memcpy(cpos, ch->pos, sizeof(double) * 3 * (size_t)N);
@@ -738,12 +822,12 @@ int vlbref_seed_vortices(vlbref_channel* ch, const double* xyz, const int32_t* n
     if (n > ch->cap) { set_err(ch, "more points than max_points"); return VLBREF_ERR_CAPACITY; }
     int* seen = (int*)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
     for (int i = 0; i < n; ++i) {
-        if (next[i] < 0 || next[i] >= n || seen[next[i]]) {
+        if (next[i] < -1 || next[i] >= n || (next[i] >= 0 && seen[next[i]])) {
             free(seen);
-            set_err(ch, "next[] must be a permutation made of closed loops");
+            set_err(ch, "next[] must describe closed loops and open lines");
             return VLBREF_ERR_TOPOLOGY;
         }
-        seen[next[i]] = 1;
+        if (next[i] >= 0) seen[next[i]] = 1;
         for (int a = 0; a < 3; ++a) {
             double v = xyz[3 * i + a];
             if (v != v) { free(seen); set_err(ch, "NaN position"); return VLBREF_ERR_INVALID_ARG; }
@@ -754,14 +838,48 @@ int vlbref_seed_vortices(vlbref_channel* ch, const double* xyz, const int32_t* n
             }
         }
     }
+    for (int i = 0; i < n; ++i)
+        if (next[i] < 0 && !seen[i]) {
+            free(seen);
+            set_err(ch, "isolated point");
+            return VLBREF_ERR_TOPOLOGY;
+        }
     free(seen);
+    /* open ends go onto the nearest wall bound (within dxi_max of it) */
+    double* tmp = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    int* tprev = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) tmp[3 * i + a] = xyz[3 * i + a];
+        wrap_or_clamp(ch, &tmp[3 * i]);
+        tprev[i] = -1;
+    }
+    for (int i = 0; i < n; ++i)
+        if (next[i] >= 0) tprev[next[i]] = i;
+    for (int i = 0; i < n; ++i) {
+        if (next[i] >= 0 && tprev[i] >= 0) continue;
+        int best_a = -1;
+        double best_d = 0.0, best_b = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            if (!ch->p.wall[a]) continue;
+            double lo = wall_lo(ch), hi = wall_hi(ch, a);
+            double dl = tmp[3 * i + a] - lo, dh = hi - tmp[3 * i + a];
+            if (best_a < 0 || dl < best_d) { best_a = a; best_d = dl; best_b = lo; }
+            if (dh < best_d) { best_a = a; best_d = dh; best_b = hi; }
+        }
+        if (best_a < 0 || best_d > ch->p.dxi_max) {
+            free(tmp); free(tprev);
+            set_err(ch, "open end farther than dxi_max from every wall");
+            return VLBREF_ERR_TOPOLOGY;
+        }
+        tmp[3 * i + best_a] = best_b;
+    }
     ch->N = n;
     for (int i = 0; i < n; ++i) {
-        for (int a = 0; a < 3; ++a) ch->pos[3 * i + a] = xyz[3 * i + a];
-        wrap_or_clamp(ch, &ch->pos[3 * i]);
+        for (int a = 0; a < 3; ++a) ch->pos[3 * i + a] = tmp[3 * i + a];
         ch->next[i] = next[i];
+        ch->prev[i] = tprev[i];
     }
-    for (int i = 0; i < n; ++i) ch->prev[ch->next[i]] = i;
+    free(tmp); free(tprev);
     return VLBREF_OK;
 }
 
@@ -790,6 +908,7 @@ int vlbref_step(vlbref_channel* ch, int32_t nsteps) {
 static double line_length(const vlbref_channel* ch) {
     double L = 0.0;
     for (int i = 0; i < ch->N; ++i) {
+        if (ch->next[i] < 0) continue;
         double b[3];
         diff3(ch, &ch->pos[3 * ch->next[i]], &ch->pos[3 * i], b);
         L += norm3(b);
@@ -804,6 +923,7 @@ static void line_profile(const vlbref_channel* ch, double* prof) {
     const int sa = ch->p.stream_axis, ns = ch->p.n[sa];
     for (int k = 0; k < ns; ++k) prof[k] = 0.0;
     for (int i = 0; i < ch->N; ++i) {
+        if (ch->next[i] < 0) continue;
         double b[3];
         diff3(ch, &ch->pos[3 * ch->next[i]], &ch->pos[3 * i], b);
         double mid = ch->pos[3 * i + sa] + 0.5 * b[sa];
@@ -871,6 +991,7 @@ int vlbref_read_fields(vlbref_channel* ch, int32_t which, void* dst, size_t byte
         d[4] = ch->max_mach; d[5] = (double)ch->n_split; d[6] = (double)ch->n_merge;
         d[7] = (double)ch->n_reconnect; d[8] = (double)ch->n_small; d[9] = (double)ch->steps;
         d[10] = ch->mom[0]; d[11] = ch->mom[1]; d[12] = ch->mom[2];
+        d[13] = (double)ch->n_wallcut;
     }
     if (written) *written = need;
     return VLBREF_OK;

@@ -67,7 +67,7 @@ enum {
     VLBREF_FIELD_FSTAR = 2,    /* [19][C]  post-collision populations */
     VLBREF_FIELD_FORCE = 3,    /* [3][C]   force grid */
     VLBREF_FIELD_POS = 4,      /* [N][3]   filament points */
-    VLBREF_FIELD_NEXT = 5,     /* [N]      int32 successor index */
+    VLBREF_FIELD_NEXT = 5,     /* [N]      int32 successor index, -1 at the last point of an open line */
     VLBREF_FIELD_PLANE_VS = 6, /* [n_s]    superfluid velocity per stream plane (Eq. 18) */
     VLBREF_FIELD_STATS = 7,    /* [16]     see vlbref.c */
     VLBREF_FIELD_VEL = 8,      /* [N][3]   stage-1 ds/dt of the last filament advance */
@@ -78,6 +78,10 @@ enum {
 int  vlbref_create(const vlbref_params* p, vlbref_channel** out);
 void vlbref_destroy(vlbref_channel* ch);
 const char* vlbref_last_error(const vlbref_channel* ch);
+/* next[i] = successor of point i, or -1 where an open line ends.  Closed loops
+ * and open lines only (no point has two predecessors; no isolated point).  An
+ * open end must lie within dxi_max of a wall's clamp bound and is moved onto
+ * the nearest one: it is pinned to that wall. */
 int  vlbref_seed_vortices(vlbref_channel* ch, const double* xyz, const int32_t* next, int32_t n);
 int  vlbref_step(vlbref_channel* ch, int32_t nsteps);
 int  vlbref_run_phases(vlbref_channel* ch, int32_t phase_mask);

@@ -3,8 +3,9 @@
 This module holds no arithmetic of the method; it only lays out filament
 points on circles (numpy ``Generator(PCG64(seed))``) so that the CUDA path and
 the FP64 oracle start from the same arrays.  The shapes follow the paper's
-workloads: single rings (Sec. III.A), ring collisions (Sec. III.B) and a
-random tangle seeded from rings (Sec. III.C, Sec. IV).
+workloads: single rings (Sec. III.A), ring collisions (Sec. III.B), a
+random tangle seeded from rings (Sec. III.C, Sec. IV) and lines bound to the
+walls of the closed channel (Sec. IV).
 """
 from __future__ import annotations
 
@@ -33,12 +34,52 @@ def ring(center, normal, radius: float, npts: int | None = None, spacing: float 
     return xyz, nxt
 
 
+def open_line(points):
+    """An open line through the given points in order (next = -1 at the last)."""
+    xyz = np.asarray(points, np.float64).reshape(-1, 3)
+    nxt = np.arange(1, len(xyz) + 1, dtype=np.int32)
+    nxt[-1] = -1
+    return xyz, nxt
+
+
+def wall_line(start, end, spacing: float = 0.8):
+    """A straight open line from ``start`` to ``end`` (both near walls), with
+    equal segments no longer than ``spacing``."""
+    a = np.asarray(start, np.float64)
+    b = np.asarray(end, np.float64)
+    m = max(1, int(np.ceil(np.linalg.norm(b - a) / spacing)))
+    t = np.arange(m + 1) / m
+    return open_line(a[None, :] + t[:, None] * (b - a)[None, :])
+
+
+def wall_lines(n_box, count: int, seed: int, amp: float = 0.0, spacing: float = 0.8):
+    """``count`` lines along z from the low to the high z wall at random (x, y),
+    as in the wall-bound seeds of the closed channel (Sec. IV).  ``amp`` > 0
+    adds a helical displacement of that amplitude (one turn along the line),
+    vanishing at both walls."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nx, ny, nz = (float(v) for v in n_box)
+    parts = []
+    for _ in range(count):
+        x0 = rng.uniform(2.0 + amp, nx - 3.0 - amp)
+        y0 = rng.uniform(2.0 + amp, ny - 3.0 - amp)
+        xyz, nxt = wall_line((x0, y0, 0.0), (x0, y0, nz - 1.0), spacing)
+        if amp > 0.0:
+            t = (xyz[:, 2] - xyz[0, 2]) / (xyz[-1, 2] - xyz[0, 2])
+            env = np.sin(np.pi * t)
+            xyz[:, 0] += amp * env * np.cos(2.0 * np.pi * t)
+            xyz[:, 1] += amp * env * np.sin(2.0 * np.pi * t)
+        parts.append((xyz, nxt))
+    return concat(parts)
+
+
 def concat(parts):
-    """Join several (xyz, next) loops into one point set."""
+    """Join several (xyz, next) loops or open lines into one point set."""
     xs, ns, off = [], [], 0
     for xyz, nxt in parts:
+        nxt = np.asarray(nxt)
         xs.append(xyz)
-        ns.append(nxt + off)
+        ns.append(np.where(nxt >= 0, nxt + off, -1))
         off += len(nxt)
     if not xs:
         return np.zeros((0, 3)), np.zeros(0, np.int32)
