@@ -103,11 +103,12 @@ enum {
     VLB_FIELD_FSTAR = 2,    /* float32 [19][C]: post-collision populations (read and write) */
     VLB_FIELD_FORCE = 3,    /* float32 [3][C]: force grid of the next lattice pass (read and write) */
     VLB_FIELD_POS = 4,      /* float64 [N][3]: filament points */
-    VLB_FIELD_NEXT = 5,     /* int32 [N]: successor of each point */
+    VLB_FIELD_NEXT = 5,     /* int32 [N]: successor of each point, -1 at the last point of an open line */
     VLB_FIELD_PLANE_VS = 6, /* float64 [n_z]: superfluid counterflow velocity per z plane (Eq. 18) */
     VLB_FIELD_STATS = 7,    /* float64 [16]: 0 points, 1 status bits, 2 mass, 3 line length, 4 max Mach,
                                5 splits, 6 merges, 7 reconnections, 8 points deleted in small loops,
-                               9 steps, 10 device bytes allocated, 11..15 reserved */
+                               9 steps, 10 device bytes allocated, 11..12 reserved, 13 wall-contact cuts,
+                               14..15 reserved */
     VLB_FIELD_VEL = 8,      /* float64 [N][3]: ds/dt at the first RK stage of the last filament advance */
     VLB_FIELD_FDEV = 9,     /* float32 [19][C]: f_i - w_i rho0 of the post-collision populations (read only;
                                the flow signal at full float precision) */
@@ -124,9 +125,17 @@ enum {
 int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* stream, vlb_channel** out);
 
 /* Replace the filament set (Sec. II.A): xyz is host float64 [n][3], next host
- * int32 [n] (a permutation made of closed loops).  Points on periodic axes are
- * wrapped into [0, n); points outside the walls are rejected.  Errors:
- * CAPACITY (n > max_points), TOPOLOGY, INVALID_ARG (NaN, outside walls). */
+ * int32 [n] with the successor of each point or -1 where an open line ends.
+ * The set must be made of closed loops and open lines (no point with two
+ * predecessors, no isolated point).  Open lines are bound to the solid walls
+ * (Sec. IV): each end must lie within dxi_max of a wall's clamp bound (walls at
+ * -1/2 and n - 1/2, bounds dxi_min/2 inside them) and is moved onto the
+ * nearest one; it then stays on that wall, taking the mirror image of its
+ * neighbour across the wall as its missing neighbour.  Points on periodic axes
+ * are wrapped into [0, n); points outside the walls are rejected; points
+ * closer than dxi_min/2 to a wall are moved onto the bound.  Errors: CAPACITY
+ * (n > max_points), TOPOLOGY (structure, or an open end away from the walls),
+ * INVALID_ARG (NaN, outside walls). */
 int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, int32_t n);
 
 /* Advance `nsteps` coupled steps (all phases, in order LBM, VFM, remesh,
@@ -188,7 +197,8 @@ int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches);
  * next[j] except the two touching the target, minimum image on periodic axes)
  * at every point of a device-resident filament set.
  *   pos      device float64 SoA [3][n] (x block, then y, then z)
- *   next     device int32 [n] successor indices (closed loops)
+ *   next     device int32 [n] successor indices, -1 at the last point of an
+ *            open line (that point starts no segment)
  *   vel      device float32 SoA [3][n], written
  *   scratch  device buffer of at least vlb_biot_savart_scratch_bytes(n) bytes
  * Uses only p->n, p->wall and p->kappa.  Runs on `stream`; does not wait. */

@@ -66,10 +66,23 @@ def config(name: str, seed: int = 0):
                         max_points=262144)
         xyz, nxt = inputs.random_rings((128, 128, 1024), (1, 1, 1), 1000, 6.0, 20.0, seed)
         return p, xyz, nxt
+    if name == "channel64x64x256_lines":
+        # the closed channel of Sec. IV seeded as there: four lines bound to the heater and the far
+        # wall, with a helical kink, and two smaller rings to kick them; heater v_n = 0.01 along z
+        p = base_params((64, 64, 256), (1, 1, 1), 1.9, heater_vn=0.01, init_vn=[0.0, 0.0, 0.01],
+                        max_points=8192)
+        lines = inputs.wall_lines((64, 64, 256), 4, seed, amp=2.0)
+        for k in range(1, 64):  # rings redrawn until they pass 3 cells clear of the lines
+            rings = inputs.random_rings((64, 64, 256), (1, 1, 1), 2, 5.0, 7.0, seed + k)
+            gap = np.sqrt(((rings[0][:, None, :] - lines[0][None, :, :]) ** 2).sum(-1)).min()
+            if gap >= 3.0:
+                break
+        xyz, nxt = inputs.concat([lines, rings])
+        return p, xyz, nxt
     raise KeyError(name)
 
 
-NAMES = ["ring32", "channel64x64x256", "box128", "channel128x128x1024"]
+NAMES = ["ring32", "channel64x64x256", "box128", "channel128x128x1024", "channel64x64x256_lines"]
 
 
 MACH_SAFE_VN = 0.02  # imposed |u| with headroom under the Mach limit 0.05 c_s = 0.0289 (Sec. II.B)

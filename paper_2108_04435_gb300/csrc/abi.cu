@@ -521,12 +521,15 @@ int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, i
     if (n > ch->cap || (n > 0 && ch->p.max_points == 0)) return fail(VLB_ERR_CAPACITY, "more points than max_points");
     std::vector<char> seen((size_t)n, 0);
     std::vector<double> soa(3 * (size_t)ch->cap, 0.0);
-    std::vector<int> prv((size_t)(n > 0 ? n : 1), 0);
+    std::vector<int> prv((size_t)(n > 0 ? n : 1), -1);
     for (int i = 0; i < n; ++i) {
         const int q = next[i];
-        if (q < 0 || q >= n || seen[(size_t)q]) return fail(VLB_ERR_TOPOLOGY, "next[] must be a permutation of closed loops");
-        seen[(size_t)q] = 1;
-        prv[(size_t)q] = i;
+        if (q < -1 || q >= n || (q >= 0 && seen[(size_t)q]))
+            return fail(VLB_ERR_TOPOLOGY, "next[] must describe closed loops and open lines");
+        if (q >= 0) {
+            seen[(size_t)q] = 1;
+            prv[(size_t)q] = i;
+        }
         for (int a = 0; a < 3; ++a) {
             double v = xyz[3 * (size_t)i + a];
             if (v != v || isinf(v)) return fail(VLB_ERR_INVALID_ARG, "non-finite position");
@@ -543,6 +546,25 @@ int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, i
             }
             soa[(size_t)a * ch->cap + i] = v;
         }
+    }
+    // Open ends go onto the nearest wall clamp bound within dxi_max (order x-,
+    // x+, y-, y+, z-, z+ on ties).
+    for (int i = 0; i < n; ++i) {
+        if (next[i] < 0 && prv[(size_t)i] < 0) return fail(VLB_ERR_TOPOLOGY, "isolated point");
+        if (next[i] >= 0 && prv[(size_t)i] >= 0) continue;
+        int best_a = -1;
+        double best_d = 0.0, best_b = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            if (!ch->p.wall[a]) continue;
+            const double lo = -0.5 + 0.5 * ch->p.dxi_min, hi = (double)ch->p.n[a] - 0.5 - 0.5 * ch->p.dxi_min;
+            const double x = soa[(size_t)a * ch->cap + i];
+            const double dl = x - lo, dh = hi - x;
+            if (best_a < 0 || dl < best_d) { best_a = a; best_d = dl; best_b = lo; }
+            if (dh < best_d) { best_a = a; best_d = dh; best_b = hi; }
+        }
+        if (best_a < 0 || best_d > ch->p.dxi_max)
+            return fail(VLB_ERR_TOPOLOGY, "open end farther than dxi_max from every wall");
+        soa[(size_t)best_a * ch->cap + i] = best_b;
     }
     Dev& d = ch->d;
     cudaStream_t s = ch->stream;
@@ -750,6 +772,7 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
         o[8] = ch->h_dstats[DS_SMALL];
         o[9] = (double)ch->steps;
         o[10] = (double)ch->bytes;
+        o[13] = ch->h_dstats[DS_WALLCUT];
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "read field");

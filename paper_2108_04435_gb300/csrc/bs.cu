@@ -286,13 +286,17 @@ __global__ void k_bs_prep(Grid g, const double* __restrict__ pos, const int* __r
         counters[CNT_BSWORK] = 0;
     }
     if (i >= n) return;
-    const int q = next[i];
-    prev[q] = i;
+    int q = next[i];
+    if (q < -1 || q >= n) {  // not a point index: no segment
+        atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
+        q = -1;
+    }
+    if (q >= 0) prev[q] = i;
     const int nn[3] = {g.nx, g.ny, g.nz};
     float hi[3], lo[3], d[3];
     for (int k = 0; k < 3; ++k) {
         const double si = pos[(long long)k * n + i];
-        double dd = pos[(long long)k * n + q] - si;
+        double dd = q >= 0 ? pos[(long long)k * n + q] - si : 0.0;
         if (!g.wall[k]) {
             const double L = (double)nn[k];
             if (dd > 0.5 * L) dd -= L;
@@ -360,6 +364,7 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
 
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
                                int* counters, cudaStream_t s) {
+    cudaMemsetAsync(prev, 0xff, sizeof(int) * (size_t)n, s);  // first points of open lines keep -1
     k_bs_prep<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(g, pos, next, n, prev, seg, counters);
 }
 

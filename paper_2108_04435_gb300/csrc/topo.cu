@@ -16,7 +16,15 @@
 //            of the segment pairs (i,j), (i,p(j)), (p(i),j), (p(i),p(j)) with
 //            the largest positive length decrease is exchanged; exchanges are
 //            applied in ascending (d^2, i), skipping any that touches a point
-//            already used.
+//            already used; a pair whose segment is missing (a line's last
+//            point) is not tried.
+//  walls     open lines end on walls: an end keeps the mirror image of its
+//            neighbour across its wall as the missing neighbour and is never
+//            removed; after the exchanges a point with both neighbours that
+//            touches a wall's clamp bound cuts its line there (ascending
+//            index, skipping points already used): it is deleted and its
+//            neighbours become ends moved onto that bound.  Loops and lines
+//            of fewer than five points are deleted.
 // All decisions are FP64 predicates evaluated in the same order as a plain
 // IEEE implementation (this file is compiled with -fmad=false), so they are
 // bit-identical to it on identical inputs.
@@ -42,6 +50,24 @@ __device__ __forceinline__ double dist(const Grid& g, const double* pos, int cap
     double d[3];
     for (int k = 0; k < 3; ++k) d[k] = min_image(g, k, pos[(long long)k * cap + to] - pos[(long long)k * cap + from]);
     return sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+}
+
+__device__ __forceinline__ double wall_bound(const Grid& g, double dmin, int code) {
+    const int a = code >> 1;
+    const double L = (double)(a == 0 ? g.nx : (a == 1 ? g.ny : g.nz));
+    return (code & 1) ? L - 0.5 - 0.5 * dmin : -0.5 + 0.5 * dmin;
+}
+
+// First wall clamp bound touched by point i (order x-, x+, y-, y+, z-, z+) as
+// 2*axis + side, or -1.
+__device__ __forceinline__ int touching_wall(const Grid& g, double dmin, const double* pos, int cap, int i) {
+    for (int a = 0; a < 3; ++a) {
+        if (!g.wall[a]) continue;
+        const double x = pos[(long long)a * cap + i];
+        if (x <= wall_bound(g, dmin, 2 * a)) return 2 * a;
+        if (x >= wall_bound(g, dmin, 2 * a + 1)) return 2 * a + 1;
+    }
+    return -1;
 }
 
 // MurmurHash3 32-bit finaliser (fmix32), used as the merge priority.
@@ -90,7 +116,9 @@ __device__ int block_exclusive_scan(int v, int* total) {
 
 // FP64 geometry for the remeshing decisions: segment length l+ = |s_q - s_i|
 // and the three-point curvature s'' = 2 (l- b - l+ a) / (l+ l- (l+ + l-)) on
-// the non-uniform arc-length grid (a = s_i - s_p, b = s_q - s_i).
+// the non-uniform arc-length grid (a = s_i - s_p, b = s_q - s_i); an open
+// end on a wall uses the mirror image of its neighbour across the wall, and a
+// line's last point has seglen 0.
 __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double* __restrict__ s,
                                                        const int* __restrict__ next, const int* __restrict__ prev,
                                                        const int* __restrict__ counters, int cap,
@@ -102,14 +130,37 @@ __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double
     double a[3], b[3];
     for (int k = 0; k < 3; ++k) {
         const double si = s[(long long)k * cap + i];
-        a[k] = min_image(P.g, k, si - s[(long long)k * cap + p]);
-        b[k] = min_image(P.g, k, s[(long long)k * cap + q] - si);
+        if (p >= 0) a[k] = min_image(P.g, k, si - s[(long long)k * cap + p]);
+        if (q >= 0) b[k] = min_image(P.g, k, s[(long long)k * cap + q] - si);
+    }
+    if (p < 0 || q < 0) {
+        const int nb = p < 0 ? q : p;
+        const int code = touching_wall(P.g, P.dmin, s, cap, i);
+        double g[3];
+        for (int k = 0; k < 3; ++k) g[k] = s[(long long)k * cap + nb];
+        if (code >= 0) {
+            const int ax = code >> 1;
+            const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
+            const double w = (code & 1) ? L - 0.5 : -0.5;
+            g[ax] = 2.0 * w - g[ax];
+        }
+        for (int k = 0; k < 3; ++k) {
+            const double si = s[(long long)k * cap + i];
+            if (code < 0) {
+                if (p < 0) a[k] = b[k];
+                else b[k] = a[k];
+            } else if (p < 0) {
+                a[k] = min_image(P.g, k, si - g[k]);
+            } else {
+                b[k] = min_image(P.g, k, g[k] - si);
+            }
+        }
     }
     const double lm = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     const double lp = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
     const double den = lp * lm * (lp + lm);
     for (int k = 0; k < 3; ++k) spp[(long long)k * cap + i] = 2.0 * (lm * b[k] - lp * a[k]) / den;
-    seglen[i] = lp;
+    seglen[i] = q >= 0 ? lp : 0.0;
 }
 
 // ------------------------------------------------------------------ remesh
@@ -121,25 +172,54 @@ __global__ void k_remesh_flags(VfmParams P, const double* __restrict__ pos, cons
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int p = prev[i], q = next[i];
-    const double li = seglen[i], lp = seglen[p];
-    const bool split = li > P.dmax;
-    const bool split_p = lp > P.dmax;
-    const double lmin = lp < li ? lp : li;
-    const bool cand = (lmin < P.dmin) && (dist(P.g, pos, cap, p, q) <= P.dmax) && !split_p && !split;
+    const double li = seglen[i];
+    const bool split = q >= 0 && li > P.dmax;
+    bool cand = false;
+    if (p >= 0 && q >= 0) {  // open ends are never removed
+        const double lp = seglen[p];
+        const bool split_p = lp > P.dmax;
+        const double lmin = lp < li ? lp : li;
+        cand = (lmin < P.dmin) && (dist(P.g, pos, cap, p, q) <= P.dmax) && !split_p && !split;
+    }
     flags[i] = (uint8_t)((split ? 1 : 0) | (cand ? 2 : 0));
 }
 
-// Points of loops with fewer than five points (succ^k(i) == i for k <= 4)
-// die; one block, strided over [0, T).  Returns this thread's count.
-__device__ int block_small_loops(const int* __restrict__ succ, uint8_t* __restrict__ alive, int T,
-                                 int* __restrict__ counters) {
+// Points of loops and open lines with fewer than five points die; one block,
+// strided over [0, T).  A loop point finds its own loop (succ^k(i) == i,
+// k <= 4); a line is measured and deleted by the thread of its first point
+// (start(k) says which points have no predecessor).  Returns this thread's
+// count.
+template <typename StartFn>
+__device__ int block_small_components(const int* __restrict__ succ, uint8_t* __restrict__ alive, int T,
+                                      StartFn start, int* __restrict__ counters) {
     int dead = 0;
     for (int k = threadIdx.x; k < T; k += blockDim.x) {
         if (!alive[k]) continue;
+        if (start(k)) {
+            int j = k, size = 1;
+            while (size < 5) {
+                const int n = succ[j];
+                if (n < 0) break;
+                if (n >= T) {
+                    atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
+                    size = 5;
+                    break;
+                }
+                j = n;
+                ++size;
+            }
+            if (size < 5)
+                for (j = k; j >= 0; j = succ[j]) {
+                    alive[j] = 0;
+                    ++dead;
+                }
+            continue;
+        }
         int j = k;
         for (int s = 1; s <= 4; ++s) {
             j = succ[j];
-            if ((unsigned)j >= (unsigned)T) {
+            if (j < 0) break;  // a line, handled from its first point
+            if (j >= T) {
                 atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
                 break;
             }
@@ -166,14 +246,21 @@ __device__ void block_compact(const double* __restrict__ pin, const int* __restr
     for (int k = b0; k < b1; ++k) mine += alive[k] ? 1 : 0;
     int M = 0;
     int base = block_exclusive_scan(mine, &M);
-    for (int k = b0; k < b1; ++k) newidx[k] = alive[k] ? base++ : -1;
+    for (int k = b0; k < b1; ++k) {
+        newidx[k] = alive[k] ? base : -1;
+        if (alive[k]) pvout[base++] = -1;  // first points of lines keep -1
+    }
     __syncthreads();
     for (int k = b0; k < b1; ++k) {
         if (!alive[k]) continue;
         const int n = newidx[k];
         for (int c = 0; c < 3; ++c) pout[(long long)c * cap + n] = pin[(long long)c * cap + k];
         const int sk = succ[k];
-        const int sn = (unsigned)sk < (unsigned)T ? newidx[sk] : -1;
+        if (sk < 0) {  // last point of an open line
+            nout[n] = -1;
+            continue;
+        }
+        const int sn = sk < T ? newidx[sk] : -1;
         if (sn < 0) {
             atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
             continue;
@@ -233,7 +320,9 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
             ++removed;
             continue;
         }
-        if ((fi & 1) && S > 0) {
+        if (q < 0) {
+            nnext[i] = -1;
+        } else if ((fi & 1) && S > 0) {
             const int m = N + running;
             const double l = seglen[i];
             double ms[3];
@@ -268,7 +357,8 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
     }
     const int T = N + S;
     __syncthreads();
-    const int dead = block_small_loops(nnext, alive, T, counters);
+    const int dead = block_small_components(
+        nnext, alive, T, [&](int k) { return k < N && prev[k] < 0; }, counters);
     const int removed_all = block_sum(removed);
     const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) {
@@ -314,7 +404,7 @@ __global__ void __launch_bounds__(128) k_nearest(VfmParams P, double dmax2, cons
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= N) return;  // whole warp
-    const int p = prev[i], q = next[i], pp = prev[p], qq = next[q];
+    const int p = prev[i], q = next[i], pp = p >= 0 ? prev[p] : -1, qq = q >= 0 ? next[q] : -1;
     double xi[3];
     int c[3];
     for (int k = 0; k < 3; ++k) {
@@ -371,7 +461,9 @@ __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* 
     double best = 0.0;
     int pick = -1;
     for (int k = 0; k < 4; ++k) {
-        const int a = as[k], b = bs[k], qa = next[a], qb = next[b];
+        const int a = as[k], b = bs[k];
+        if (a < 0 || b < 0 || next[a] < 0 || next[b] < 0) continue;
+        const int qa = next[a], qb = next[b];
         const double gain = (dist(P.g, pos, cap, a, qa) + dist(P.g, pos, cap, b, qb)) -
                             (dist(P.g, pos, cap, a, qb) + dist(P.g, pos, cap, b, qa));
         if (gain > 0.0 && (pick < 0 || gain > best)) {
@@ -389,10 +481,11 @@ __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* 
 
 // One block finishes the reconnection: candidates in ascending (d^2, i)
 // order (keys are unique), the greedy pass in that order (an exchange that
-// touches a point already used is skipped), emptying the hash buckets,
-// small-loop deletion and the compaction into the other point buffer.
+// touches a point already used is skipped), emptying the hash buckets, the
+// wall-contact cuts, small-component deletion and the compaction into the
+// other point buffer.
 __global__ void __launch_bounds__(1024) k_reconnect_finish(
-    double* __restrict__ pos, int* __restrict__ next, int* __restrict__ prev, const int* __restrict__ cand_i,
+    VfmParams P, int* __restrict__ clist, double* __restrict__ pos, int* __restrict__ next, int* __restrict__ prev, const int* __restrict__ cand_i,
     const int* __restrict__ cand_a, const int* __restrict__ cand_b, const double* __restrict__ cand_d2,
     int* __restrict__ order, int* __restrict__ stamp, const int* __restrict__ hkey, int* __restrict__ hhead,
     uint8_t* __restrict__ alive, int* __restrict__ newidx, double* __restrict__ pout, int* __restrict__ nout,
@@ -436,7 +529,44 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
         dstats[DS_RECON] += (double)applied;
     }
     __syncthreads();
-    const int dead = block_small_loops(next, alive, N, counters);
+    // Wall contact: the points with both neighbours on a wall bound, listed in
+    // ascending index, then cut in that order by one thread.
+    {
+        const int per = (N + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int b0 = min(N, (int)threadIdx.x * per);
+        const int b1 = min(N, b0 + per);
+        int mine = 0;
+        for (int i = b0; i < b1; ++i)
+            mine += (prev[i] >= 0 && next[i] >= 0 && touching_wall(P.g, P.dmin, pos, cap, i) >= 0) ? 1 : 0;
+        int ncand = 0;
+        int at = block_exclusive_scan(mine, &ncand);
+        for (int i = b0; i < b1; ++i)
+            if (prev[i] >= 0 && next[i] >= 0 && touching_wall(P.g, P.dmin, pos, cap, i) >= 0) clist[at++] = i;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int st = counters[CNT_STAMP];
+            int cuts = 0;
+            for (int r = 0; r < ncand; ++r) {
+                const int i = clist[r], p = prev[i], q = next[i];
+                if (stamp[i] == st || stamp[p] == st || stamp[q] == st) continue;
+                const int code = touching_wall(P.g, P.dmin, pos, cap, i);
+                stamp[i] = st;
+                stamp[p] = st;
+                stamp[q] = st;
+                alive[i] = 0;
+                next[p] = -1;
+                prev[q] = -1;
+                const double bnd = wall_bound(P.g, P.dmin, code);
+                pos[(long long)(code >> 1) * cap + p] = bnd;
+                pos[(long long)(code >> 1) * cap + q] = bnd;
+                ++cuts;
+            }
+            counters[CNT_NCONTACT] = ncand;
+            dstats[DS_WALLCUT] += (double)cuts;
+        }
+        __syncthreads();
+    }
+    const int dead = block_small_components(next, alive, N, [&](int k) { return prev[k] < 0; }, counters);
     const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) dstats[DS_SMALL] += (double)dead_all;
     __syncthreads();
@@ -468,7 +598,7 @@ void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, c
                                             d.hhead, d.hlink, d.nn, d.nd2);
     k_pairs<<<nb, 256, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap, d.cand_i,
                                d.cand_a, d.cand_b, d.cand_d2);
-    k_reconnect_finish<<<1, 1024, 0, s>>>(d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
+    k_reconnect_finish<<<1, 1024, 0, s>>>(P, d.nn, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
                                           d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
                                           cap);

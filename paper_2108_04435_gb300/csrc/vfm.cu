@@ -37,6 +37,19 @@ __device__ __forceinline__ void wrap_or_clamp(const Grid& g, double dmin, double
     }
 }
 
+// The first wall clamp bound that position s touches, in the order x-, x+,
+// y-, y+, z-, z+, as 2*axis + side (side 1 = high wall), or -1.  An open end
+// of a line is pinned to this wall.
+__device__ __forceinline__ int touching_wall(const Grid& g, double dmin, const double s[3]) {
+    for (int a = 0; a < 3; ++a) {
+        if (!g.wall[a]) continue;
+        const double L = (double)(a == 0 ? g.nx : (a == 1 ? g.ny : g.nz));
+        if (s[a] <= -0.5 + 0.5 * dmin) return 2 * a;
+        if (s[a] >= L - 0.5 - 0.5 * dmin) return 2 * a + 1;
+    }
+    return -1;
+}
+
 // Nodes and weights of the 2-point delta function (Eq. 11) along one axis:
 // periodic axes wrap, wall axes move an outside node's weight to the nearest
 // fluid node.
@@ -64,7 +77,10 @@ __device__ __forceinline__ void delta_axis(const Grid& g, int axis, double s, in
 // k_geometry, with the neighbour differences formed in FP64 (positions are up
 // to ~1e3 cells) and everything after them in FP32, which is accurate to
 // ~1e-7 relative for segments of O(1) cells.  The remeshing decisions use the
-// FP64 k_geometry instead.
+// FP64 k_geometry instead.  An open end pinned on a wall takes the mirror image
+// of its neighbour across that wall as its missing neighbour, represents half
+// of its segment, and carries its wall code (+1) to the equation of motion; a
+// line's last point has a zero-length source record.
 __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double* __restrict__ s,
                                                        const int* __restrict__ next, const int* __restrict__ prev,
                                                        int* __restrict__ counters, int cap,
@@ -80,8 +96,30 @@ __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double
     for (int k = 0; k < 3; ++k) {
         si[k] = s[(long long)k * cap + i];
         if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
-        a[k] = (float)min_image(P.g, k, si[k] - s[(long long)k * cap + p]);
-        b[k] = (float)min_image(P.g, k, s[(long long)k * cap + q] - si[k]);
+        if (p >= 0) a[k] = (float)min_image(P.g, k, si[k] - s[(long long)k * cap + p]);
+        if (q >= 0) b[k] = (float)min_image(P.g, k, s[(long long)k * cap + q] - si[k]);
+    }
+    int code = -1;
+    if (p < 0 || q < 0) {
+        code = touching_wall(P.g, P.dmin, si);
+        const int nb = p < 0 ? q : p;
+        double gpos[3];
+        for (int k = 0; k < 3; ++k) gpos[k] = s[(long long)k * cap + nb];
+        if (code >= 0) {
+            const int ax = code >> 1;
+            const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
+            gpos[ax] = 2.0 * ((code & 1) ? L - 0.5 : -0.5) - gpos[ax];
+        }
+        for (int k = 0; k < 3; ++k) {
+            if (code < 0) {  // not on a wall: continued straight
+                if (p < 0) a[k] = b[k];
+                else b[k] = a[k];
+            } else if (p < 0) {
+                a[k] = (float)min_image(P.g, k, si[k] - gpos[k]);
+            } else {
+                b[k] = (float)min_image(P.g, k, gpos[k] - si[k]);
+            }
+        }
     }
     const float lm = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     const float lp = sqrtf(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
@@ -92,10 +130,12 @@ __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double
         t2[k] = 2.f * (lm * b[k] - lp * a[k]) * inv;
     }
     const float beta = P.kq_f * logf(2.f * sqrtf(lp * lm) * P.inv_ea_f);
-    // geo[2i] = (s'.xyz, dxi), geo[2i+1] = (local velocity beta s' x s'', 0)
-    geo[2LL * i] = make_float4(t1[0], t1[1], t1[2], 0.5f * (lp + lm));
+    // geo[2i] = (s'.xyz, dxi), geo[2i+1] = (local velocity beta s' x s'', wall code + 1 of a pinned end)
+    const float dxi = p < 0 ? 0.5f * lp : (q < 0 ? 0.5f * lm : 0.5f * (lp + lm));
+    geo[2LL * i] = make_float4(t1[0], t1[1], t1[2], dxi);
     geo[2LL * i + 1] = make_float4(beta * (t1[1] * t2[2] - t1[2] * t2[1]), beta * (t1[2] * t2[0] - t1[0] * t2[2]),
-                                   beta * (t1[0] * t2[1] - t1[1] * t2[0]), 0.f);
+                                   beta * (t1[0] * t2[1] - t1[1] * t2[0]), (float)(code + 1));
+    if (q < 0) b[0] = b[1] = b[2] = 0.f;  // no segment leaves a line's last point
     float hi[3], lo[3];
     for (int k = 0; k < 3; ++k) {
         hi[k] = __double2float_rn(si[k]);
@@ -132,6 +172,7 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
         float vs[3];
         const float4 g0 = geo[2LL * i], g1 = geo[2LL * i + 1];
         s1[0] = g0.x; s1[1] = g0.y; s1[2] = g0.z; dxi = g0.w;
+        const int pin = (int)g1.w - 1;  // wall code of a pinned end, else -1
         const float lia[3] = {g1.x, g1.y, g1.z};
         for (int k = 0; k < 3; ++k) {
             x[k] = xs[(long long)k * cap + i];
@@ -160,8 +201,10 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
         for (int k = 0; k < 3; ++k) {
             fr[k] = P.alpha_f * t[k] - P.alpha_p_f * tt[k];
             kv[k] = (double)(vs[k] + fr[k]);
-            if (!(fabs(P.dt * kv[k]) < 1.0)) bad |= (kv[k] == kv[k]) ? ST_CFL : ST_NAN;
         }
+        if (pin >= 0) kv[pin >> 1] = 0.0;  // a pinned end slides along its wall
+        for (int k = 0; k < 3; ++k)
+            if (!(fabs(P.dt * kv[k]) < 1.0)) bad |= (kv[k] == kv[k]) ? ST_CFL : ST_NAN;
         if (bad) atomicOr(&counters[CNT_STATUS], bad);
         const double cst_next = stage == 0 ? 0.5 : (stage == 1 ? 0.5 : 1.0);
         const double wst = (stage == 0 || stage == 3) ? 1.0 : 2.0;
@@ -245,7 +288,7 @@ __global__ void __launch_bounds__(256) k_line_length(Grid g, const double* __res
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
-    if (i < N) {
+    if (i < N && next[i] >= 0) {
         const int q = next[i];
         double d[3];
         for (int k = 0; k < 3; ++k) d[k] = min_image(g, k, pos[(long long)k * cap + q] - pos[(long long)k * cap + i]);
@@ -287,6 +330,7 @@ __global__ void k_line_profile(Grid g, const double* __restrict__ pos, const int
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int q = next[i];
+    if (q < 0) return;
     double d[3];
     for (int k = 0; k < 3; ++k) d[k] = min_image(g, k, pos[(long long)k * cap + q] - pos[(long long)k * cap + i]);
     const double mid = pos[2LL * cap + i] + 0.5 * d[2];

@@ -28,6 +28,7 @@ enum : int {
     CNT_BSWORK = 6,     // Biot-Savart work-item counter (reset before each launch)
     CNT_PLANES = 7,     // z planes reduced in the current lattice pass
     CNT_LINEDONE = 8,   // blocks done in the line-length reduction
+    CNT_NCONTACT = 9,   // wall-contact candidates of the current reconnection pass
     CNT_COUNT = 12
 };
 
@@ -40,6 +41,7 @@ enum : int {
     DS_MERGES = 4,
     DS_RECON = 5,
     DS_SMALL = 6,
+    DS_WALLCUT = 7,
     DS_COUNT = 8
 };
 
