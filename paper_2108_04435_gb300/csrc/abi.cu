@@ -290,7 +290,7 @@ size_t vlb_channel_bytes(const vlb_params* p) {
     while (h < 2 * cap) h <<= 1;
     const size_t esize = p->storage == VLB_STORE_F32 ? 4 : 2;
     const size_t bpp = (size_t)((p->n[0] * p->n[1] + 127) / 128) + 1;
-    size_t b = 2 * up(esize * 19 * C) + 2 * up(4 * 3 * C) + 2 * up(nt) + up(8 * 3 * bpp * p->n[2]);
+    size_t b = 2 * up(esize * 19 * C) + up(8 * 3 * C) + up(4 * 3 * C) + 2 * up(nt) + up(8 * 3 * bpp * p->n[2]);
     b += 3 * up(8 * (size_t)p->n[2]) + up(4 * (size_t)p->n[2]) + up(8 * DS_COUNT) + up(4 * CNT_COUNT);
     b += 2 * (up(24 * cap) + 2 * up(4 * cap)) + 6 * up(24 * cap) + up(8 * cap) + up(32 * cap) + up(48 * cap);
     b += up(12 * cap * (size_t)bs_max_splits((int)cap)) + up(12 * cap) + up(4 * ((cap + 127) / 128));
@@ -421,7 +421,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     const size_t esize = p->storage == VLB_STORE_F32 ? 4 : 2;
     d.f[0] = A(esize * 19 * (size_t)C);
     d.f[1] = A(esize * 19 * (size_t)C);
-    d.F = (float*)A(sizeof(float) * 3 * (size_t)C);
+    d.F = (long long*)A(sizeof(long long) * 3 * (size_t)C);
     d.U = (float*)A(sizeof(float) * 3 * (size_t)C);
     d.fmask = (uint8_t*)A((size_t)ntiles);
     d.umask = (uint8_t*)A((size_t)ntiles);
@@ -477,7 +477,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
         return fail(VLB_ERR_OOM, "pinned host allocation failed");
     }
     cudaStream_t s = ch->stream;
-    cudaMemsetAsync(d.F, 0, sizeof(float) * 3 * (size_t)C, s);
+    cudaMemsetAsync(d.F, 0, sizeof(long long) * 3 * (size_t)C, s);
     cudaMemsetAsync(d.fmask, 0, (size_t)ntiles, s);
     cudaMemsetAsync(d.umask, 0, (size_t)ntiles, s);
     cudaMemsetAsync(d.counters, 0, sizeof(int) * CNT_COUNT, s);
@@ -737,7 +737,8 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
                                 cudaMemcpyDeviceToHost, s);
         }
     } else if (which == VLB_FIELD_FORCE) {
-        e = cudaMemcpyAsync(dst, d.F, need, cudaMemcpyDeviceToHost, s);
+        launch_force_export(ch->lp.g, d.F, tmp, s);  // spare population buffer holds 12 B per cell
+        e = cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, s);
     } else if (which == VLB_FIELD_POS || which == VLB_FIELD_VEL) {
         std::vector<double> soa(3 * (size_t)ch->cap);
         const double* src = which == VLB_FIELD_POS ? d.pos[ch->cur_p] : d.vel1;
@@ -800,7 +801,9 @@ int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t byt
         }
     } else if (which == VLB_FIELD_FORCE) {
         if (bytes != sizeof(float) * 3 * (size_t)C) return fail(VLB_ERR_INVALID_ARG, "FORCE size mismatch");
-        e = cudaMemcpyAsync(d.F, src, bytes, cudaMemcpyHostToDevice, s);
+        float* tmp = (float*)d.f[ch->cur_f ^ 1];  // spare population buffer
+        e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, s);
+        launch_force_import(ch->lp.g, tmp, d.F, s);
         const int nt = ch->lp.g.tnx * ch->lp.g.tny * ch->lp.g.tnz;
         cudaMemsetAsync(d.fmask, 1, (size_t)nt, s);
     } else {

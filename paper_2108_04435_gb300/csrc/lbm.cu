@@ -174,7 +174,7 @@ __device__ __forceinline__ void pull_fast(const typename Pop<S>::T* __restrict__
 template <bool WX, bool WY, bool WZ, int S>
 __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T* __restrict__ fin,
                                                         typename Pop<S>::T* __restrict__ fout,
-                                                        const float* __restrict__ F, float* __restrict__ U,
+                                                        const long long* __restrict__ F, float* __restrict__ U,
                                                         const uint8_t* __restrict__ fmask,
                                                         const uint8_t* __restrict__ umask, double* __restrict__ part,
                                                         LbmParams P) {
@@ -205,9 +205,9 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
         const bool factive = fmask[tile] != 0;
         float Fx = P.body[0], Fy = P.body[1], Fz = P.body[2];
         if (factive) {
-            Fx += __ldg(&F[cell]);
-            Fy += __ldg(&F[C + cell]);
-            Fz += __ldg(&F[2 * C + cell]);
+            Fx += force_value(__ldg(&F[cell]));
+            Fy += force_value(__ldg(&F[C + cell]));
+            Fz += force_value(__ldg(&F[2 * C + cell]));
         }
         const bool force = factive || P.body_on;
         const float rho = P.rho0 + drho;
@@ -401,7 +401,7 @@ __device__ __forceinline__ void vstore(float* p, const float (&v)[VEC]) {
 
 template <bool WX, bool WY, bool WZ, int VEC>
 __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ fin, float* __restrict__ fout,
-                                                      const float* __restrict__ F, float* __restrict__ U,
+                                                      const long long* __restrict__ F, float* __restrict__ U,
                                                       const uint8_t* __restrict__ fmask,
                                                       const uint8_t* __restrict__ umask, double* __restrict__ part,
                                                       LbmParams P) {
@@ -498,16 +498,12 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ 
             Fz[c] = P.body[2];
         }
         if (factive) {
-            float a[VEC];
-            vload<VEC>(F + cell0, a);
 #pragma unroll
-            for (int c = 0; c < VEC; ++c) Fx[c] += a[c];
-            vload<VEC>(F + C + cell0, a);
-#pragma unroll
-            for (int c = 0; c < VEC; ++c) Fy[c] += a[c];
-            vload<VEC>(F + 2 * C + cell0, a);
-#pragma unroll
-            for (int c = 0; c < VEC; ++c) Fz[c] += a[c];
+            for (int c = 0; c < VEC; ++c) {
+                Fx[c] += force_value(F[cell0 + c]);
+                Fy[c] += force_value(F[C + cell0 + c]);
+                Fz[c] += force_value(F[2 * C + cell0 + c]);
+            }
         }
         float drho[VEC], ux[VEC], uy[VEC], uz[VEC];
 #pragma unroll
@@ -621,7 +617,7 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ 
 // Density and velocity of the streamed populations of the current state
 // (what the next pass will see), for read-out.
 template <bool WX, bool WY, bool WZ, int S>
-__global__ void k_moments(const typename Pop<S>::T* __restrict__ f, const float* __restrict__ F,
+__global__ void k_moments(const typename Pop<S>::T* __restrict__ f, const long long* __restrict__ F,
                           const uint8_t* __restrict__ fmask, float* __restrict__ rho_out, float* __restrict__ U,
                           LbmParams P) {
     const int nx = P.g.nx, ny = P.g.ny;
@@ -644,9 +640,9 @@ __global__ void k_moments(const typename Pop<S>::T* __restrict__ f, const float*
     drho += P.dr0;
     float Fx = P.body[0], Fy = P.body[1], Fz = P.body[2];
     if (fmask[tile_of(P.g, x, y, z)]) {
-        Fx += F[cell];
-        Fy += F[C + cell];
-        Fz += F[2 * C + cell];
+        Fx += force_value(F[cell]);
+        Fy += force_value(F[C + cell]);
+        Fz += force_value(F[2 * C + cell]);
     }
     const float rho = P.rho0 + drho;
     rho_out[cell] = rho;
@@ -726,7 +722,7 @@ __global__ void k_mark_umask(Grid g, const double* __restrict__ pos, const int* 
 }
 
 // Zero the force grid in every tile the last spreading touched, then clear the tile flag.
-__global__ void k_zero_force(Grid g, float* __restrict__ F, uint8_t* __restrict__ fmask) {
+__global__ void k_zero_force(Grid g, long long* __restrict__ F, uint8_t* __restrict__ fmask) {
     const int t = blockIdx.x;
     if (!fmask[t]) return;
     const int tx = t % g.tnx, ty = (t / g.tnx) % g.tny, tz = t / (g.tnx * g.tny);
@@ -735,17 +731,28 @@ __global__ void k_zero_force(Grid g, float* __restrict__ F, uint8_t* __restrict_
                   z = (tz << TILE_SHIFT) + (k >> 6);
         if (x < g.nx && y < g.ny && z < g.nz) {
             const long long c = ((long long)z * g.ny + y) * g.nx + x;
-            F[c] = 0.f;
-            F[g.ncell + c] = 0.f;
-            F[2 * g.ncell + c] = 0.f;
+            F[c] = 0;
+            F[g.ncell + c] = 0;
+            F[2 * g.ncell + c] = 0;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) fmask[t] = 0;
 }
 
+// Force grid to and from float [3][C] (field export and import).
+__global__ void k_force_export(const long long* __restrict__ F, float* __restrict__ out, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        out[k] = force_value(F[k]);
+}
+
+__global__ void k_force_import(const float* __restrict__ in, long long* __restrict__ F, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        F[k] = force_fixed(in[k]);
+}
+
 template <bool WX, bool WY, bool WZ>
-void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const float* F, float* U, const uint8_t* fmask,
+void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U, const uint8_t* fmask,
                   const uint8_t* umask, double* part, cudaStream_t s) {
     const int nxy = P.g.nx * P.g.ny;
     if (P.storage == STORE_F32 && (P.vec == 4 || P.vec == 2)) {
@@ -772,7 +779,7 @@ void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const float* 
 }
 
 template <bool WX, bool WY, bool WZ>
-void moments_dispatch(const LbmParams& P, const void* f, const float* F, const uint8_t* fmask, float* rho, float* U,
+void moments_dispatch(const LbmParams& P, const void* f, const long long* F, const uint8_t* fmask, float* rho, float* U,
                       cudaStream_t s) {
     const int bpp = (P.g.nx * P.g.ny + LBM_BLOCK - 1) / LBM_BLOCK;
     dim3 grid(bpp, P.g.nz);
@@ -801,12 +808,12 @@ void moments_dispatch(const LbmParams& P, const void* f, const float* F, const u
         }                                                                            \
     } while (0)
 
-void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const float* F, float* U,
+void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s) {
     VLB_WALL_DISPATCH(lbm_dispatch, P, fin, fout, F, U, fmask, umask, part, s);
 }
 
-void launch_moments(const LbmParams& P, const void* f, const float* F, const uint8_t* fmask, float* rho, float* U,
+void launch_moments(const LbmParams& P, const void* f, const long long* F, const uint8_t* fmask, float* rho, float* U,
                     cudaStream_t s) {
     VLB_WALL_DISPATCH(moments_dispatch, P, f, F, fmask, rho, U, s);
 }
@@ -860,7 +867,15 @@ void launch_mark_umask(const Grid& g, const double* pos, const int* counters, in
     k_mark_umask<<<(cap + 127) / 128, 128, 0, s>>>(g, pos, counters, cap, umask);
 }
 
-void launch_zero_force(const Grid& g, float* F, uint8_t* fmask, cudaStream_t s) {
+void launch_force_export(const Grid& g, const long long* F, float* out, cudaStream_t s) {
+    k_force_export<<<1216, 256, 0, s>>>(F, out, 3 * g.ncell);
+}
+
+void launch_force_import(const Grid& g, const float* in, long long* F, cudaStream_t s) {
+    k_force_import<<<1216, 256, 0, s>>>(in, F, 3 * g.ncell);
+}
+
+void launch_zero_force(const Grid& g, long long* F, uint8_t* fmask, cudaStream_t s) {
     const int ntiles = g.tnx * g.tny * g.tnz;
     k_zero_force<<<ntiles, 256, 0, s>>>(g, F, fmask);
 }

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
                                             double* __restrict__ acc, double* __restrict__ vel1,
                                             const float4* __restrict__ geo, const float* __restrict__ vbs,
                                             const float* __restrict__ U, const double* __restrict__ Vs,
-                                            float* __restrict__ F, uint8_t* __restrict__ fmask,
+                                            long long* __restrict__ F, uint8_t* __restrict__ fmask,
                                             int* __restrict__ counters, int cap) {
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -271,9 +271,10 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
             for (int cx = 0; cx < 2; ++cx) {
                 const int k = (cz * 2 + cy) * 2 + cx;
                 const long long c = ((long long)iz[cz] * g.ny + iy[cy]) * g.nx + ix[cx];
-                atomicAdd(&F[c], val[3 * k]);
-                atomicAdd(&F[C + c], val[3 * k + 1]);
-                atomicAdd(&F[2 * C + c], val[3 * k + 2]);
+                // fixed point: exact, order-independent sums
+                atomicAdd((unsigned long long*)&F[c], (unsigned long long)force_fixed(val[3 * k]));
+                atomicAdd((unsigned long long*)&F[C + c], (unsigned long long)force_fixed(val[3 * k + 1]));
+                atomicAdd((unsigned long long*)&F[2 * C + c], (unsigned long long)force_fixed(val[3 * k + 2]));
                 fmask[((iz[cz] >> TILE_SHIFT) * g.tny + (iy[cy] >> TILE_SHIFT)) * g.tnx + (ix[cx] >> TILE_SHIFT)] = 1;
             }
 }
@@ -350,7 +351,7 @@ void launch_geometry_stage(const VfmParams& P, const double* s, const int* next,
 
 void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, double* st, double* pos_out,
                 double* acc, double* vel1, const float4* geo, const float* vbs, const float* U, const double* Vs,
-                float* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s) {
+                long long* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s) {
     if (cap <= 0) return;
     k_eom<<<(cap + 63) / 64, 64, 0, s>>>(P, stage, spread, s0, st, pos_out, acc, vel1, geo, vbs, U, Vs, F, fmask,
                                          counters, cap);

@@ -49,6 +49,14 @@ enum : int {
 enum : int { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
 
 constexpr int TILE_SHIFT = 3;   // force / velocity activity tiles of 8^3 cells
+
+// The force grid accumulates the spreading of Eqs. 10-11 in fixed point:
+// int64 with FORCE_FRAC fractional bits (resolution 5.7e-14, range 5e5), so
+// the atomic additions are exact and their order does not matter; every run
+// is bitwise reproducible.  A contribution is rounded to the grid once.
+constexpr int FORCE_FRAC = 44;
+__device__ __forceinline__ long long force_fixed(float v) { return __float2ll_rn(v * 0x1p44f); }
+__device__ __forceinline__ float force_value(long long a) { return __ll2float_rn(a) * 0x1p-44f; }
 constexpr int LBM_BLOCK = 256;  // cells per stream-collide block (one z plane)
 constexpr int BS_TPB = 128;     // Biot-Savart targets per block
 constexpr int BS_TILE = 256;    // source segments per shared-memory tile
@@ -117,7 +125,7 @@ __host__ __device__ inline int bs_splits(int N, int tile) {
 struct Dev {
     // lattice
     void* f[2];         // stored deviations f_i - s_i, [19][C] in the storage format
-    float* F;           // force grid [3][C]
+    long long* F;       // force grid [3][C], fixed point (FORCE_FRAC fractional bits)
     float* U;           // velocity of the last pass [3][C], valid in u-active tiles
     uint8_t* fmask;     // tiles where F may be non-zero
     uint8_t* umask;     // tiles where U must be written
@@ -164,15 +172,17 @@ struct Dev {
 // ---------------------------------------------------------------- launchers
 // lbm.cu
 void launch_lbm_init(const LbmParams& P, void* f, float* U, const double init_u[3], cudaStream_t s);
-void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const float* F, float* U,
+void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
 void launch_plane_vs(const LbmParams& P, const double* part, cudaStream_t s);
 int lbm_blocks_per_plane(const LbmParams& P);
-void launch_moments(const LbmParams& P, const void* f, const float* F, const uint8_t* fmask, float* rho,
+void launch_moments(const LbmParams& P, const void* f, const long long* F, const uint8_t* fmask, float* rho,
                     float* U, cudaStream_t s);
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,
                        cudaStream_t s);
-void launch_zero_force(const Grid& g, float* F, uint8_t* fmask, cudaStream_t s);
+void launch_zero_force(const Grid& g, long long* F, uint8_t* fmask, cudaStream_t s);
+void launch_force_export(const Grid& g, const long long* F, float* out, cudaStream_t s);
+void launch_force_import(const Grid& g, const float* in, long long* F, cudaStream_t s);
 void launch_export(const LbmParams& P, const void* f, float* out, int i0, int i1, int mode, cudaStream_t s);
 void launch_import(const LbmParams& P, const float* in, void* f, int i0, int i1, cudaStream_t s);
 
@@ -181,7 +191,7 @@ void launch_geometry_stage(const VfmParams& P, const double* s, const int* next,
                            int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st);
 void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, double* st, double* pos_out,
                 double* acc, double* vel1, const float4* geo, const float* vbs, const float* U, const double* Vs,
-                float* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s);
+                long long* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s);
 void launch_line_profile(const Grid& g, const double* pos, const int* next, const int* counters, int cap,
                          double* prof, cudaStream_t s);
 void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,
