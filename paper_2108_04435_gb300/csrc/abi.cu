@@ -135,14 +135,13 @@ void record_event(vlb_channel* ch) {
 
 void phase_lbm(vlb_channel* ch) {
     Dev& d = ch->d;
-    const int nt = ch->lp.g.tnx * ch->lp.g.tny * ch->lp.g.tnz;
-    cudaMemsetAsync(d.umask, 0, (size_t)nt, ch->stream);
+    // the velocity-tile flags were cleared by the previous pass's plane reduction (or at creation)
     launch_mark_umask(ch->lp.g, d.pos[ch->cur_p], d.counters, ch->cap, d.umask, ch->stream);
     if (ch->timing) record_event(ch);
     launch_lbm_step(ch->lp, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
     if (ch->timing) record_event(ch);
     ch->cur_f ^= 1;
-    launch_plane_vs(ch->lp, d.part, ch->stream);
+    launch_plane_vs(ch->lp, d.part, d.umask, ch->stream);
 }
 
 void phase_vfm(vlb_channel* ch) {

@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
                                                         int* __restrict__ counters, int* __restrict__ tile_ticket,
                                                         int cap, BoxF box, float kq, float* __restrict__ part,
                                                         float* __restrict__ vel) {
+    pdl_wait_trigger();
     __shared__ __align__(128) float4 tile[2][BS_TILE * 3];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_item, s_last;
@@ -343,9 +344,9 @@ void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int*
     const int grid = items < 8 * 152 ? items : 8 * 152;
     const BoxF box = make_box(g);
     if (g.wall[0] && g.wall[1] && g.wall[2])
-        k_biot_savart<false, TGT><<<grid, BS_TPB, 0, s>>>(seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
+        launch_pdl(k_biot_savart<false, TGT>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
     else
-        k_biot_savart<true, TGT><<<grid, BS_TPB, 0, s>>>(seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
+        launch_pdl(k_biot_savart<true, TGT>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
 }
 
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,

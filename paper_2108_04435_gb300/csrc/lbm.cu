@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
                                                         const uint8_t* __restrict__ fmask,
                                                         const uint8_t* __restrict__ umask, double* __restrict__ part,
                                                         LbmParams P) {
+    pdl_wait_trigger();
     const int nx = P.g.nx, ny = P.g.ny;
     const int C = (int)P.g.ncell;
     const int z = blockIdx.y;
@@ -292,8 +293,12 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
 // and the Mach limit of Sec. II.B (|u|/c_s < 0.05).  One warp per plane
 // (lane-strided loads, fixed shuffle tree); the last block to finish reduces
 // the planes in a fixed order.  FP64 work is spread over many SMs because
-// its per-SM rate is low on this GPU.
-__global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ part, int bpp, LbmParams P) {
+// its per-SM rate is low on this GPU.  It also clears the velocity-tile
+// flags the stream-collide pass has just used.
+__global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ part, int bpp, LbmParams P,
+                                                  uint8_t* __restrict__ umask, int ntiles) {
+    pdl_wait_trigger();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) umask[t] = 0;
     __shared__ double s_tot[256], s_mass[256], s_max[256];
     __shared__ int s_last;
     const int nz = P.g.nz;
@@ -405,6 +410,7 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ 
                                                       const uint8_t* __restrict__ fmask,
                                                       const uint8_t* __restrict__ umask, double* __restrict__ part,
                                                       LbmParams P) {
+    pdl_wait_trigger();
     const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz, nxy = nx * ny;
     const int C = (int)P.g.ncell;
     const int nq = nx / VEC;  // cell groups per row
@@ -702,6 +708,7 @@ __global__ void k_import(const float* __restrict__ in, typename Pop<S>::T* __res
 // by less than one cell, which the advance checks).
 __global__ void k_mark_umask(Grid g, const double* __restrict__ pos, const int* __restrict__ counters, int cap,
                              uint8_t* __restrict__ umask) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -723,6 +730,7 @@ __global__ void k_mark_umask(Grid g, const double* __restrict__ pos, const int* 
 
 // Zero the force grid in every tile the last spreading touched, then clear the tile flag.
 __global__ void k_zero_force(Grid g, long long* __restrict__ F, uint8_t* __restrict__ fmask) {
+    pdl_wait_trigger();
     const int t = blockIdx.x;
     if (!fmask[t]) return;
     const int tx = t % g.tnx, ty = (t / g.tnx) % g.tny, tz = t / (g.tnx * g.tny);
@@ -759,22 +767,22 @@ void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const long lo
         const int groups = nxy / P.vec;
         dim3 grid((groups + 127) / 128, P.g.nz);
         if (P.vec == 4)
-            k_lbm_step_vec<WX, WY, WZ, 4><<<grid, 128, 0, s>>>((const float*)fin, (float*)fout, F, U, fmask, umask,
+            launch_pdl(k_lbm_step_vec<WX, WY, WZ, 4>, grid, 128, 0, s, (const float*)fin, (float*)fout, F, U, fmask, umask,
                                                                 part, P);
         else
-            k_lbm_step_vec<WX, WY, WZ, 2><<<grid, 128, 0, s>>>((const float*)fin, (float*)fout, F, U, fmask, umask,
+            launch_pdl(k_lbm_step_vec<WX, WY, WZ, 2>, grid, 128, 0, s, (const float*)fin, (float*)fout, F, U, fmask, umask,
                                                                 part, P);
         return;
     }
     dim3 grid((nxy + P.block - 1) / P.block, P.g.nz);
     if (P.storage == STORE_F16)
-        k_lbm_step<WX, WY, WZ, STORE_F16><<<grid, P.block, 0, s>>>((const __half*)fin, (__half*)fout, F, U, fmask,
+        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_F16>, grid, P.block, 0, s, (const __half*)fin, (__half*)fout, F, U, fmask,
                                                                     umask, part, P);
     else if (P.storage == STORE_BF16)
-        k_lbm_step<WX, WY, WZ, STORE_BF16><<<grid, P.block, 0, s>>>(
+        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_BF16>, grid, P.block, 0, s, 
             (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, F, U, fmask, umask, part, P);
     else
-        k_lbm_step<WX, WY, WZ, STORE_F32><<<grid, P.block, 0, s>>>((const float*)fin, (float*)fout, F, U, fmask,
+        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_F32>, grid, P.block, 0, s, (const float*)fin, (float*)fout, F, U, fmask,
                                                                     umask, part, P);
 }
 
@@ -856,15 +864,15 @@ int lbm_blocks_per_plane(const LbmParams& P) {
     return (nxy + P.block - 1) / P.block;
 }
 
-void launch_plane_vs(const LbmParams& P, const double* part, cudaStream_t s) {
+void launch_plane_vs(const LbmParams& P, const double* part, uint8_t* umask, cudaStream_t s) {
     const int bpp = lbm_blocks_per_plane(P);
-    k_plane_vs<<<(P.g.nz + 7) / 8, 256, 0, s>>>(part, bpp, P);
+    launch_pdl(k_plane_vs, (P.g.nz + 7) / 8, 256, 0, s, part, bpp, P, umask, P.g.tnx * P.g.tny * P.g.tnz);
 }
 
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,
                        cudaStream_t s) {
     if (cap <= 0) return;
-    k_mark_umask<<<(cap + 127) / 128, 128, 0, s>>>(g, pos, counters, cap, umask);
+    launch_pdl(k_mark_umask, (cap + 127) / 128, 128, 0, s, g, pos, counters, cap, umask);
 }
 
 void launch_force_export(const Grid& g, const long long* F, float* out, cudaStream_t s) {
@@ -877,7 +885,7 @@ void launch_force_import(const Grid& g, const float* in, long long* F, cudaStrea
 
 void launch_zero_force(const Grid& g, long long* F, uint8_t* fmask, cudaStream_t s) {
     const int ntiles = g.tnx * g.tny * g.tnz;
-    k_zero_force<<<ntiles, 256, 0, s>>>(g, F, fmask);
+    launch_pdl(k_zero_force, ntiles, 256, 0, s, g, F, fmask);
 }
 
 }  // namespace vlb

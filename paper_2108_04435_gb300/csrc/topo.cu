@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double
                                                        const int* __restrict__ next, const int* __restrict__ prev,
                                                        const int* __restrict__ counters, int cap,
                                                        double* __restrict__ spp, double* __restrict__ seglen) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double
 __global__ void k_remesh_flags(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
                                const int* __restrict__ prev, const double* __restrict__ seglen,
                                const int* __restrict__ counters, int cap, uint8_t* __restrict__ flags) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
                                                          double* __restrict__ pout, int* __restrict__ nout,
                                                          int* __restrict__ pvout, int* __restrict__ counters,
                                                          double* __restrict__ dstats, int cap) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int per = (N + (int)blockDim.x - 1) / (int)blockDim.x;
     const int b0 = min(N, (int)threadIdx.x * per);
@@ -381,6 +384,7 @@ __device__ __forceinline__ uint32_t cell_hash(int cx, int cy, int cz) {
 __global__ void k_hash_insert(const double* __restrict__ pos, int* __restrict__ counters, int cap,
                               uint32_t hmask, int* __restrict__ hkey, int* __restrict__ hhead,
                               int* __restrict__ hlink) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) counters[CNT_NPAIRS] = 0;
@@ -400,6 +404,7 @@ __global__ void __launch_bounds__(128) k_nearest(VfmParams P, double dmax2, cons
                                                  const int* __restrict__ counters, int cap, uint32_t hmask,
                                                  const int* __restrict__ hhead, const int* __restrict__ hlink,
                                                  int* __restrict__ nn, double* __restrict__ nd2) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -451,6 +456,7 @@ __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* 
                         const int* __restrict__ prev, const int* __restrict__ nn, const double* __restrict__ nd2,
                         int* __restrict__ counters, int cap, int* __restrict__ cand_i, int* __restrict__ cand_a,
                         int* __restrict__ cand_b, double* __restrict__ cand_d2) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -490,6 +496,7 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     int* __restrict__ order, int* __restrict__ stamp, const int* __restrict__ hkey, int* __restrict__ hhead,
     uint8_t* __restrict__ alive, int* __restrict__ newidx, double* __restrict__ pout, int* __restrict__ nout,
     int* __restrict__ pvout, int* __restrict__ counters, double* __restrict__ dstats, int cap) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int K = counters[CNT_NPAIRS];
     for (int c = threadIdx.x; c < K; c += blockDim.x) {
@@ -578,10 +585,10 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
 void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s) {
     if (cap <= 0) return;
     const int nb = (cap + 255) / 256;
-    k_geometry_exact<<<(cap + 63) / 64, 64, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, d.spp,
+    launch_pdl(k_geometry_exact, (cap + 63) / 64, 64, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, d.spp,
                                                      d.seglen);
-    k_remesh_flags<<<nb, 256, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.seglen, d.counters, cap, d.flags);
-    k_remesh_finish<<<1, 1024, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
+    launch_pdl(k_remesh_flags, nb, 256, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.seglen, d.counters, cap, d.flags);
+    launch_pdl(k_remesh_finish, 1, 1024, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
                                        d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1],
                                        d.counters, d.dstats, cap);
 }
@@ -593,12 +600,12 @@ void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, c
     const int nb = (cap + 255) / 256;
     const uint32_t hmask = (uint32_t)hsize - 1u;
     const double dmax2 = P.dmax * P.dmax;
-    k_hash_insert<<<nb, 256, 0, s>>>(d.pos[cur], d.counters, cap, hmask, d.hkey, d.hhead, d.hlink);
-    k_nearest<<<(cap + 3) / 4, 128, 0, s>>>(P, dmax2, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, hmask,
+    launch_pdl(k_hash_insert, nb, 256, 0, s, d.pos[cur], d.counters, cap, hmask, d.hkey, d.hhead, d.hlink);
+    launch_pdl(k_nearest, (cap + 3) / 4, 128, 0, s, P, dmax2, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, hmask,
                                             d.hhead, d.hlink, d.nn, d.nd2);
-    k_pairs<<<nb, 256, 0, s>>>(P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap, d.cand_i,
+    launch_pdl(k_pairs, nb, 256, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap, d.cand_i,
                                d.cand_a, d.cand_b, d.cand_d2);
-    k_reconnect_finish<<<1, 1024, 0, s>>>(P, d.nn, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
+    launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.nn, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
                                           d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
                                           cap);

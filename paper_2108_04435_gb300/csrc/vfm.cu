@@ -52,12 +52,13 @@ __device__ __forceinline__ int touching_wall(const Grid& g, double dmin, const d
 
 // Nodes and weights of the 2-point delta function (Eq. 11) along one axis:
 // periodic axes wrap, wall axes move an outside node's weight to the nearest
-// fluid node.
+// fluid node.  b = floor(s) before wrapping or clamping: points with equal b
+// on every axis have the same eight nodes.
 __device__ __forceinline__ void delta_axis(const Grid& g, int axis, double s, int& i0, int& i1, double& w0,
-                                           double& w1) {
+                                           double& w1, int& b) {
     const int n = axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz);
     const double fl = floor(s);
-    const int b = (int)fl;
+    b = (int)fl;
     const double fr = s - fl;
     w0 = 1.0 - fr;
     w1 = fr;
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double
                                                        int* __restrict__ counters, int cap,
                                                        float4* __restrict__ geo, float4* __restrict__ seg,
                                                        double* __restrict__ s0_copy) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch that follows takes items from 0
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
                                             const float* __restrict__ U, const double* __restrict__ Vs,
                                             long long* __restrict__ F, uint8_t* __restrict__ fmask,
                                             int* __restrict__ counters, int cap) {
+    pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < N;
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
     const long long C = g.ncell;
     const double* xs = stage == 0 ? s0 : st;
     float s1[3] = {0.f, 0.f, 0.f}, fr[3] = {0.f, 0.f, 0.f}, dxi = 0.f;
-    int ix[2] = {0, 0}, iy[2] = {0, 0}, iz[2] = {0, 0};
+    int ix[2] = {0, 0}, iy[2] = {0, 0}, iz[2] = {0, 0}, base[3] = {0, 0, 0};
     float wx[2] = {0.f, 0.f}, wy[2] = {0.f, 0.f}, wz[2] = {0.f, 0.f};
     if (valid) {
         double x[3];
@@ -179,9 +182,9 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
             vs[k] = vbs[(long long)k * cap + i] + lia[k];
         }
         double w0, w1;
-        delta_axis(g, 0, x[0], ix[0], ix[1], w0, w1); wx[0] = (float)w0; wx[1] = (float)w1;
-        delta_axis(g, 1, x[1], iy[0], iy[1], w0, w1); wy[0] = (float)w0; wy[1] = (float)w1;
-        delta_axis(g, 2, x[2], iz[0], iz[1], w0, w1); wz[0] = (float)w0; wz[1] = (float)w1;
+        delta_axis(g, 0, x[0], ix[0], ix[1], w0, w1, base[0]); wx[0] = (float)w0; wx[1] = (float)w1;
+        delta_axis(g, 1, x[1], iy[0], iy[1], w0, w1, base[1]); wy[0] = (float)w0; wy[1] = (float)w1;
+        delta_axis(g, 2, x[2], iz[0], iz[1], w0, w1, base[2]); wz[0] = (float)w0; wz[1] = (float)w1;
         vs[2] += wz[0] * (float)Vs[iz[0]] + wz[1] * (float)Vs[iz[1]];  // v_s,a (Eq. 18)
         float vn[3] = {0.f, 0.f, 0.f};
         for (int cz = 0; cz < 2; ++cz)
@@ -248,10 +251,13 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
                 val[3 * k + 1] = w * gv[1];
                 val[3 * k + 2] = w * gv[2];
             }
-    // Lanes whose points share a base cell share all eight corners: sum their
-    // contributions in the lowest such lane, which alone issues the atomics.
+    // Lanes whose points share the unclamped base cell share all eight corners
+    // (a clamped base cell would not: next to a wall, floor -1 and floor 0 both
+    // clamp to node 0): sum their contributions in the lowest such lane, which
+    // alone issues the atomics.
     const int lane = threadIdx.x & 31;
-    const long long key = valid ? ((long long)iz[0] * g.ny + iy[0]) * g.nx + ix[0] : -1 - (long long)lane;
+    const long long key = valid ? ((long long)(base[2] + 1) * (g.ny + 2) + (base[1] + 1)) * (g.nx + 2) + (base[0] + 1)
+                                : -1 - (long long)lane;
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int leader = __ffs(peers) - 1;
     const int steps = __reduce_max_sync(0xffffffffu, (unsigned)__popc(peers)) - 1;
@@ -284,6 +290,7 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
 __global__ void __launch_bounds__(256) k_line_length(Grid g, const double* __restrict__ pos,
                                                       const int* __restrict__ next, int* __restrict__ counters,
                                                       int cap, double* __restrict__ part, double* __restrict__ dstats) {
+    pdl_wait_trigger();
     __shared__ double sm[256];
     __shared__ int s_last;
     const int N = counters[CNT_N];
@@ -346,20 +353,20 @@ __global__ void k_line_profile(Grid g, const double* __restrict__ pos, const int
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
                            int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st) {
     if (cap <= 0) return;
-    k_geometry_stage<<<(cap + 63) / 64, 64, 0, st>>>(P, s, next, prev, counters, cap, geo, seg, s0_copy);
+    launch_pdl(k_geometry_stage, (cap + 63) / 64, 64, 0, st, P, s, next, prev, counters, cap, geo, seg, s0_copy);
 }
 
 void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, double* st, double* pos_out,
                 double* acc, double* vel1, const float4* geo, const float* vbs, const float* U, const double* Vs,
                 long long* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s) {
     if (cap <= 0) return;
-    k_eom<<<(cap + 63) / 64, 64, 0, s>>>(P, stage, spread, s0, st, pos_out, acc, vel1, geo, vbs, U, Vs, F, fmask,
+    launch_pdl(k_eom, (cap + 63) / 64, 64, 0, s, P, stage, spread, s0, st, pos_out, acc, vel1, geo, vbs, U, Vs, F, fmask,
                                          counters, cap);
 }
 
 void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,
                         double* dstats, cudaStream_t s) {
-    k_line_length<<<(cap + 255) / 256, 256, 0, s>>>(g, pos, next, counters, cap, part, dstats);
+    launch_pdl(k_line_length, (cap + 255) / 256, 256, 0, s, g, pos, next, counters, cap, part, dstats);
 }
 
 void launch_line_profile(const Grid& g, const double* pos, const int* next, const int* counters, int cap,

@@ -1,6 +1,8 @@
 // Internal declarations shared by the CUDA translation units of libvlb.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <utility>
 #include <stdint.h>
 
 #include "../../include/vlb.h"
@@ -57,6 +59,32 @@ constexpr int TILE_SHIFT = 3;   // force / velocity activity tiles of 8^3 cells
 constexpr int FORCE_FRAC = 44;
 __device__ __forceinline__ long long force_fixed(float v) { return __float2ll_rn(v * 0x1p44f); }
 __device__ __forceinline__ float force_value(long long a) { return __ll2float_rn(a) * 0x1p-44f; }
+
+// Programmatic dependent launch: the kernels of a step are launched with
+// programmatic stream serialisation, so each one is scheduled while its
+// predecessor drains.  Every such kernel first waits for its predecessor's
+// completion and memory flush (griddepcontrol.wait, a no-op without a
+// programmatic predecessor), then lets its own successor be scheduled.
+__device__ __forceinline__ void pdl_wait_trigger() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 constexpr int LBM_BLOCK = 256;  // cells per stream-collide block (one z plane)
 constexpr int BS_TPB = 128;     // Biot-Savart targets per block
 constexpr int BS_TILE = 256;    // source segments per shared-memory tile
@@ -174,7 +202,7 @@ struct Dev {
 void launch_lbm_init(const LbmParams& P, void* f, float* U, const double init_u[3], cudaStream_t s);
 void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
-void launch_plane_vs(const LbmParams& P, const double* part, cudaStream_t s);
+void launch_plane_vs(const LbmParams& P, const double* part, uint8_t* umask, cudaStream_t s);
 int lbm_blocks_per_plane(const LbmParams& P);
 void launch_moments(const LbmParams& P, const void* f, const long long* F, const uint8_t* fmask, float* rho,
                     float* U, cudaStream_t s);
