@@ -233,6 +233,16 @@ namespace vlb {
 
 int set_error(int code, const char* msg) { return fail(code, msg); }
 
+thread_local bool tl_capturing = false;
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("VLB_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 // Stand-alone Biot-Savart velocity on caller-provided device buffers; the
 // scratch layout is counters | prev | source records | split partials |
 // per-tile tickets, each 256-byte aligned.  Allocates nothing.
@@ -615,7 +625,9 @@ bool step_graph(vlb_channel* ch, bool multi) {
             cudaGetLastError();
             return false;
         }
+        tl_capturing = true;
         for (int k = 0; k < nst; ++k) run_phases(ch, VLB_PHASE_ALL);
+        tl_capturing = false;
         cudaError_t e = cudaStreamEndCapture(ch->stream, &graph);
         ch->cur_f = f;  // the captured steps have not run yet
         ch->cur_p = q;

@@ -128,33 +128,36 @@ __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int p = prev[i], q = next[i];
-    double a[3], b[3];
+    const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
+    double si[3], sp[3], sq[3], a[3], b[3];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double si = s[(long long)k * cap + i];
-        if (p >= 0) a[k] = min_image(P.g, k, si - s[(long long)k * cap + p]);
-        if (q >= 0) b[k] = min_image(P.g, k, s[(long long)k * cap + q] - si);
+        si[k] = s[(long long)k * cap + i];
+        sp[k] = s[(long long)k * cap + pl];
+        sq[k] = s[(long long)k * cap + ql];
     }
+    int code = -1;
     if (p < 0 || q < 0) {
-        const int nb = p < 0 ? q : p;
-        const int code = touching_wall(P.g, P.dmin, s, cap, i);
-        double g[3];
-        for (int k = 0; k < 3; ++k) g[k] = s[(long long)k * cap + nb];
-        if (code >= 0) {
-            const int ax = code >> 1;
-            const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
-            const double w = (code & 1) ? L - 0.5 : -0.5;
-            g[ax] = 2.0 * w - g[ax];
+        code = touching_wall(P.g, P.dmin, s, cap, i);
+        const int ax = code >> 1;
+        const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
+        const double w = (code & 1) ? L - 0.5 : -0.5;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {  // the mirror image of the present neighbour across the wall
+            if (p < 0) sp[k] = k == ax ? 2.0 * w - sq[k] : sq[k];
+            else sq[k] = k == ax ? 2.0 * w - sp[k] : sp[k];
         }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a[k] = min_image(P.g, k, si[k] - sp[k]);
+        b[k] = min_image(P.g, k, sq[k] - si[k]);
+    }
+    if (code < 0 && (p < 0 || q < 0)) {  // an end on no wall is continued straight
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double si = s[(long long)k * cap + i];
-            if (code < 0) {
-                if (p < 0) a[k] = b[k];
-                else b[k] = a[k];
-            } else if (p < 0) {
-                a[k] = min_image(P.g, k, si - g[k]);
-            } else {
-                b[k] = min_image(P.g, k, g[k] - si);
-            }
+            if (p < 0) a[k] = b[k];
+            else b[k] = a[k];
         }
     }
     const double lm = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
@@ -387,7 +390,10 @@ __global__ void k_hash_insert(const double* __restrict__ pos, int* __restrict__ 
     pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) counters[CNT_NPAIRS] = 0;
+    if (i == 0) {
+        counters[CNT_NPAIRS] = 0;
+        counters[CNT_NCONTACT] = 0;
+    }
     if (i >= N) return;
     const int cx = (int)floor(pos[i]), cy = (int)floor(pos[(long long)cap + i]), cz = (int)floor(pos[2LL * cap + i]);
     const int h = (int)(cell_hash(cx, cy, cz) & hmask);
@@ -452,36 +458,46 @@ __global__ void __launch_bounds__(128) k_nearest(VfmParams P, double dmax2, cons
     }
 }
 
+// Candidate exchanges of the mutual nearest pairs, and the wall-contact
+// candidates (points with both neighbours on a wall's clamp bound; exchanges
+// change neither property), each appended to its list.
 __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
                         const int* __restrict__ prev, const int* __restrict__ nn, const double* __restrict__ nd2,
                         int* __restrict__ counters, int cap, int* __restrict__ cand_i, int* __restrict__ cand_a,
-                        int* __restrict__ cand_b, double* __restrict__ cand_d2) {
+                        int* __restrict__ cand_b, double* __restrict__ cand_d2, int* __restrict__ clist) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const int pi = prev[i];
+    if (P.g.wall[0] | P.g.wall[1] | P.g.wall[2]) {
+        if (pi >= 0 && next[i] >= 0 && touching_wall(P.g, P.dmin, pos, cap, i) >= 0)
+            clist[atomicAdd(&counters[CNT_NCONTACT], 1)] = i;
+    }
     const int j = nn[i];
     if (j <= i || nn[j] != i) return;
-    const int as[4] = {i, i, prev[i], prev[i]};
-    const int bs[4] = {j, prev[j], j, prev[j]};
+    const int pj = prev[j];
     double best = 0.0;
-    int pick = -1;
-    for (int k = 0; k < 4; ++k) {
-        const int a = as[k], b = bs[k];
-        if (a < 0 || b < 0 || next[a] < 0 || next[b] < 0) continue;
+    int pa = -1, pb = -1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // (i,j), (i,p(j)), (p(i),j), (p(i),p(j))
+        const int a = k < 2 ? i : pi, b = (k & 1) ? pj : j;
+        if (a < 0 || b < 0) continue;
         const int qa = next[a], qb = next[b];
+        if (qa < 0 || qb < 0) continue;
         const double gain = (dist(P.g, pos, cap, a, qa) + dist(P.g, pos, cap, b, qb)) -
                             (dist(P.g, pos, cap, a, qb) + dist(P.g, pos, cap, b, qa));
-        if (gain > 0.0 && (pick < 0 || gain > best)) {
+        if (gain > 0.0 && (pa < 0 || gain > best)) {
             best = gain;
-            pick = k;
+            pa = a;
+            pb = b;
         }
     }
-    if (pick < 0) return;
+    if (pa < 0) return;
     const int slot = atomicAdd(&counters[CNT_NPAIRS], 1);
     cand_i[slot] = i;
-    cand_a[slot] = as[pick];
-    cand_b[slot] = bs[pick];
+    cand_a[slot] = pa;
+    cand_b[slot] = pb;
     cand_d2[slot] = nd2[i];
 }
 
@@ -491,7 +507,8 @@ __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* 
 // wall-contact cuts, small-component deletion and the compaction into the
 // other point buffer.
 __global__ void __launch_bounds__(1024) k_reconnect_finish(
-    VfmParams P, int* __restrict__ clist, double* __restrict__ pos, int* __restrict__ next, int* __restrict__ prev, const int* __restrict__ cand_i,
+    VfmParams P, const int* __restrict__ clist, double* __restrict__ pos, int* __restrict__ next,
+    int* __restrict__ prev, const int* __restrict__ cand_i,
     const int* __restrict__ cand_a, const int* __restrict__ cand_b, const double* __restrict__ cand_d2,
     int* __restrict__ order, int* __restrict__ stamp, const int* __restrict__ hkey, int* __restrict__ hhead,
     uint8_t* __restrict__ alive, int* __restrict__ newidx, double* __restrict__ pout, int* __restrict__ nout,
@@ -536,43 +553,39 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
         dstats[DS_RECON] += (double)applied;
     }
     __syncthreads();
-    // Wall contact: the points with both neighbours on a wall bound, listed in
-    // ascending index, then cut in that order by one thread.
-    {
-        const int per = (N + (int)blockDim.x - 1) / (int)blockDim.x;
-        const int b0 = min(N, (int)threadIdx.x * per);
-        const int b1 = min(N, b0 + per);
-        int mine = 0;
-        for (int i = b0; i < b1; ++i)
-            mine += (prev[i] >= 0 && next[i] >= 0 && touching_wall(P.g, P.dmin, pos, cap, i) >= 0) ? 1 : 0;
-        int ncand = 0;
-        int at = block_exclusive_scan(mine, &ncand);
-        for (int i = b0; i < b1; ++i)
-            if (prev[i] >= 0 && next[i] >= 0 && touching_wall(P.g, P.dmin, pos, cap, i) >= 0) clist[at++] = i;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int st = counters[CNT_STAMP];
-            int cuts = 0;
-            for (int r = 0; r < ncand; ++r) {
-                const int i = clist[r], p = prev[i], q = next[i];
-                if (stamp[i] == st || stamp[p] == st || stamp[q] == st) continue;
-                const int code = touching_wall(P.g, P.dmin, pos, cap, i);
-                stamp[i] = st;
-                stamp[p] = st;
-                stamp[q] = st;
-                alive[i] = 0;
-                next[p] = -1;
-                prev[q] = -1;
-                const double bnd = wall_bound(P.g, P.dmin, code);
-                pos[(long long)(code >> 1) * cap + p] = bnd;
-                pos[(long long)(code >> 1) * cap + q] = bnd;
-                ++cuts;
-            }
-            counters[CNT_NCONTACT] = ncand;
-            dstats[DS_WALLCUT] += (double)cuts;
-        }
-        __syncthreads();
+    // Wall contact: the candidates listed by k_pairs, put in ascending index
+    // order (indices are unique; newidx holds the order until the compaction),
+    // then cut in that order by one thread.
+    int* corder = newidx;
+    const int ncand = counters[CNT_NCONTACT];
+    for (int c = threadIdx.x; c < ncand; c += blockDim.x) {
+        const int ic = clist[c];
+        int r = 0;
+        for (int o = 0; o < ncand; ++o) r += clist[o] < ic ? 1 : 0;
+        corder[r] = ic;
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && ncand > 0) {
+        const int st = counters[CNT_STAMP];
+        int cuts = 0;
+        for (int r = 0; r < ncand; ++r) {
+            const int i = corder[r], p = prev[i], q = next[i];
+            if (stamp[i] == st || stamp[p] == st || stamp[q] == st) continue;
+            const int code = touching_wall(P.g, P.dmin, pos, cap, i);
+            stamp[i] = st;
+            stamp[p] = st;
+            stamp[q] = st;
+            alive[i] = 0;
+            next[p] = -1;
+            prev[q] = -1;
+            const double bnd = wall_bound(P.g, P.dmin, code);
+            pos[(long long)(code >> 1) * cap + p] = bnd;
+            pos[(long long)(code >> 1) * cap + q] = bnd;
+            ++cuts;
+        }
+        dstats[DS_WALLCUT] += (double)cuts;
+    }
+    __syncthreads();
     const int dead = block_small_components(next, alive, N, [&](int k) { return prev[k] < 0; }, counters);
     const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) dstats[DS_SMALL] += (double)dead_all;
@@ -604,8 +617,8 @@ void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, c
     launch_pdl(k_nearest, (cap + 3) / 4, 128, 0, s, P, dmax2, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, hmask,
                                             d.hhead, d.hlink, d.nn, d.nd2);
     launch_pdl(k_pairs, nb, 256, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap, d.cand_i,
-                               d.cand_a, d.cand_b, d.cand_d2);
-    launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.nn, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
+                               d.cand_a, d.cand_b, d.cand_d2, d.hlink);
+    launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.hlink, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
                                           d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
                                           cap);

@@ -93,35 +93,35 @@ __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double
     if (i == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch that follows takes items from 0
     if (i >= N) return;
     const int p = prev[i], q = next[i];
-    double si[3];
+    const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
+    double si[3], sp[3], sq[3];
     float a[3], b[3];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
         si[k] = s[(long long)k * cap + i];
-        if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
-        if (p >= 0) a[k] = (float)min_image(P.g, k, si[k] - s[(long long)k * cap + p]);
-        if (q >= 0) b[k] = (float)min_image(P.g, k, s[(long long)k * cap + q] - si[k]);
+        sp[k] = s[(long long)k * cap + pl];
+        sq[k] = s[(long long)k * cap + ql];
     }
     int code = -1;
     if (p < 0 || q < 0) {
         code = touching_wall(P.g, P.dmin, si);
-        const int nb = p < 0 ? q : p;
-        double gpos[3];
-        for (int k = 0; k < 3; ++k) gpos[k] = s[(long long)k * cap + nb];
-        if (code >= 0) {
-            const int ax = code >> 1;
-            const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
-            gpos[ax] = 2.0 * ((code & 1) ? L - 0.5 : -0.5) - gpos[ax];
-        }
+        const int ax = code >> 1;
+        const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
+        const double w2 = 2.0 * ((code & 1) ? L - 0.5 : -0.5);
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            if (code < 0) {  // not on a wall: continued straight
-                if (p < 0) a[k] = b[k];
-                else b[k] = a[k];
-            } else if (p < 0) {
-                a[k] = (float)min_image(P.g, k, si[k] - gpos[k]);
-            } else {
-                b[k] = (float)min_image(P.g, k, gpos[k] - si[k]);
-            }
+            const double nb = p < 0 ? sq[k] : sp[k];
+            // mirror image across the wall; an end on no wall is continued straight
+            const double g = code < 0 ? 2.0 * si[k] - nb : (k == ax ? w2 - nb : nb);
+            if (p < 0) sp[k] = g;
+            else sq[k] = g;
         }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
+        a[k] = (float)min_image(P.g, k, si[k] - sp[k]);
+        b[k] = (float)min_image(P.g, k, sq[k] - si[k]);
     }
     const float lm = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     const float lp = sqrtf(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
@@ -205,7 +205,12 @@ __global__ void __launch_bounds__(64) k_eom(VfmParams P, int stage, int spread, 
             fr[k] = P.alpha_f * t[k] - P.alpha_p_f * tt[k];
             kv[k] = (double)(vs[k] + fr[k]);
         }
-        if (pin >= 0) kv[pin >> 1] = 0.0;  // a pinned end slides along its wall
+        if (pin >= 0) {  // a pinned end slides along its wall
+            const int ax = pin >> 1;
+            kv[0] = ax == 0 ? 0.0 : kv[0];
+            kv[1] = ax == 1 ? 0.0 : kv[1];
+            kv[2] = ax == 2 ? 0.0 : kv[2];
+        }
         for (int k = 0; k < 3; ++k)
             if (!(fabs(P.dt * kv[k]) < 1.0)) bad |= (kv[k] == kv[k]) ? ST_CFL : ST_NAN;
         if (bad) atomicOr(&counters[CNT_STATUS], bad);

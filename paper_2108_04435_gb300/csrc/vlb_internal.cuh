@@ -70,12 +70,19 @@ __device__ __forceinline__ void pdl_wait_trigger() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// VLB_PDL=0 in the environment turns programmatic launch off (default on).  It
+// is not used while a CUDA graph is captured on this thread: the graph
+// schedules its kernel nodes back to back by itself, and measured slower with
+// programmatic edges.
+bool pdl_enabled();
+extern thread_local bool tl_capturing;
+
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                        Args&&... args) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[0].val.programmaticStreamSerializationAllowed = (pdl_enabled() && !tl_capturing) ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
