@@ -144,6 +144,14 @@ void phase_lbm(vlb_channel* ch) {
     launch_plane_vs(ch->lp, d.part, d.umask, ch->stream);
 }
 
+bool fused_eom() {  // VLB_FUSED_EOM=0 in the environment keeps the equation of motion a kernel of its own
+    static const bool on = [] {
+        const char* v = getenv("VLB_FUSED_EOM");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 void phase_vfm(vlb_channel* ch) {
     Dev& d = ch->d;
     const int cap = ch->cap;
@@ -151,17 +159,37 @@ void phase_vfm(vlb_channel* ch) {
     double* pos = d.pos[ch->cur_p];
     const int* next = d.next[ch->cur_p];
     const int* prev = d.prev[ch->cur_p];
+    EomArgs ea = {};
+    ea.P = ch->vp;
+    ea.cap = cap;
+    ea.s0 = d.s0;
+    ea.st = d.st;
+    ea.pos_out = pos;
+    ea.acc = d.acc;
+    ea.vel1 = d.vel1;
+    ea.geo = d.geo;
+    ea.U = d.U;
+    ea.Vs = d.Vs;
+    ea.F = d.F;
+    ea.fmask = d.fmask;
+    ea.counters = d.counters;
     for (int sub = 0; sub < nsub; ++sub) {
         const int spread = (sub == 0 && ch->p.couple) ? 1 : 0;
         if (spread) launch_zero_force(ch->lp.g, d.F, d.fmask, ch->stream);
         for (int stage = 0; stage < 4; ++stage) {
             const double* xs = stage == 0 ? pos : d.st;
+            ea.stage = stage;
+            ea.spread = spread;
             launch_geometry_stage(ch->vp, xs, next, prev, d.counters, cap, d.geo, d.seg, stage == 0 ? d.s0 : nullptr,
                                   ch->stream);
-            launch_biot_savart(ch->vp.g, ch->vp.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint,
-                               d.bsp, d.vbs, ch->stream);
-            launch_eom(ch->vp, stage, spread, d.s0, d.st, pos, d.acc, d.vel1, d.geo, d.vbs, d.U, d.Vs, d.F, d.fmask,
-                       d.counters, cap, ch->stream);
+            if (fused_eom()) {
+                launch_biot_savart(ch->vp.g, ch->vp.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint,
+                                   d.bsp, d.vbs, ch->stream, &ea);
+            } else {
+                launch_biot_savart(ch->vp.g, ch->vp.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint,
+                                   d.bsp, d.vbs, ch->stream);
+                launch_eom(ea, d.vbs, ch->stream);
+            }
         }
     }
 }

@@ -20,6 +20,7 @@
 
 #include <mutex>
 
+#include "eom.cuh"
 #include "vlb_internal.cuh"
 
 namespace vlb {
@@ -154,11 +155,11 @@ __device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, i
 // host-side estimate of N.  With several splits, each item stores its partial
 // sums and the last item of a target tile adds them in split order (fixed,
 // hence deterministic) into vel; with one split the item writes vel directly.
-template <bool PERIODIC, int TGT>
+template <bool PERIODIC, int TGT, bool EOM>
 __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev,
                                                         int* __restrict__ counters, int* __restrict__ tile_ticket,
                                                         int cap, BoxF box, float kq, float* __restrict__ part,
-                                                        float* __restrict__ vel) {
+                                                        float* __restrict__ vel, EomArgs ea) {
     pdl_wait_trigger();
     __shared__ __align__(128) float4 tile[2][BS_TILE * 3];
     __shared__ __align__(8) uint64_t bar[2];
@@ -231,7 +232,9 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
 #pragma unroll
             for (int v = 0; v < TGT; ++v) {
                 const int i = t[v].self;
-                if (i >= 0) {
+                if (EOM) {
+                    eom_point(ea, i, i >= 0, t[v].vx, t[v].vy, t[v].vz);
+                } else if (i >= 0) {
                     vel[i] = t[v].vx;
                     vel[(long long)cap + i] = t[v].vy;
                     vel[2LL * cap + i] = t[v].vz;
@@ -256,11 +259,15 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
 #pragma unroll
                 for (int v = 0; v < TGT; ++v) {
                     const int i = t[v].self;
+                    float a[3] = {0.f, 0.f, 0.f};
                     if (i >= 0) {
-                        float a[3] = {0.f, 0.f, 0.f};
                         for (int m = 0; m < ns; ++m)
 #pragma unroll
                             for (int k = 0; k < 3; ++k) a[k] += __ldcg(&part[((long long)m * 3 + k) * cap + i]);
+                    }
+                    if (EOM) {
+                        eom_point(ea, i, i >= 0, a[0], a[1], a[2]);
+                    } else if (i >= 0) {
                         vel[i] = a[0];
                         vel[(long long)cap + i] = a[1];
                         vel[2LL * cap + i] = a[2];
@@ -334,9 +341,9 @@ int bs_max_splits(int cap) {
     return m;
 }
 
-template <int TGT>
+template <int TGT, bool EOM>
 void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int* cnt, int* tile_ticket, int cap, int n,
-               float* part, float* vel, cudaStream_t s) {
+               float* part, float* vel, const EomArgs& ea, cudaStream_t s) {
     // enough blocks for every item of about n points (at most 8 per SM); more
     // points than that are still covered by the blocks' item loop
     constexpr int TT = BS_TPB * TGT;
@@ -344,23 +351,31 @@ void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int*
     const int grid = items < 8 * 152 ? items : 8 * 152;
     const BoxF box = make_box(g);
     if (g.wall[0] && g.wall[1] && g.wall[2])
-        launch_pdl(k_biot_savart<false, TGT>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
+        launch_pdl(k_biot_savart<false, TGT, EOM>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part,
+                   vel, ea);
     else
-        launch_pdl(k_biot_savart<true, TGT>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part, vel);
+        launch_pdl(k_biot_savart<true, TGT, EOM>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part,
+                   vel, ea);
 }
 
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
-                        int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s) {
+                        int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
+                        const EomArgs* eom) {
     if (cap <= 0) return;
     const int n = n_hint > 0 ? (n_hint < cap ? n_hint : cap) : 1;
     const float kq = (float)(kappa / (4.0 * 3.14159265358979323846));
     int* cnt = const_cast<int*>(counters);
     // two targets per thread once there are enough points to fill the GPU with
     // them (each shared-memory record is then read once for both)
-    if (n >= 2 * BS_TPB * 152 * 2)
-        bs_launch<2>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, s);
-    else
-        bs_launch<1>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, s);
+    const EomArgs none = {};
+    const EomArgs& ea = eom ? *eom : none;
+    if (n >= 2 * BS_TPB * 152 * 2) {
+        if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, s);
+        else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, s);
+    } else {
+        if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, s);
+        else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, s);
+    }
 }
 
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,

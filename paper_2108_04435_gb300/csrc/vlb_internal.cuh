@@ -142,6 +142,23 @@ struct VfmParams {
     int couple, force_form;
 };
 
+// Arguments of the equation of motion at one RK4 stage (eom.cuh).
+struct EomArgs {
+    VfmParams P;
+    int stage, spread, cap;
+    const double* s0;   // RK4 base positions
+    double* st;         // stage positions (written for the next stage)
+    double* pos_out;    // new positions (last stage)
+    double* acc;        // RK4 sum
+    double* vel1;       // stage-1 velocity (exported)
+    const float4* geo;  // stage geometry
+    const float* U;     // v_n grid
+    const double* Vs;   // V_s per plane
+    long long* F;       // force grid (spreading at stage 0)
+    uint8_t* fmask;
+    int* counters;
+};
+
 // Biot-Savart source splits for N points and target tiles of `tile` points:
 // enough (target tile, split) work items to fill the GPU (~4 per SM on 152
 // SMs), at least 64 segments per split.  The kernel derives it from the
@@ -224,9 +241,7 @@ void launch_import(const LbmParams& P, const float* in, void* f, int i0, int i1,
 // vfm.cu
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
                            int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st);
-void launch_eom(const VfmParams& P, int stage, int spread, const double* s0, double* st, double* pos_out,
-                double* acc, double* vel1, const float4* geo, const float* vbs, const float* U, const double* Vs,
-                long long* F, uint8_t* fmask, int* counters, int cap, cudaStream_t s);
+void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s);
 void launch_line_profile(const Grid& g, const double* pos, const int* next, const int* counters, int cap,
                          double* prof, cudaStream_t s);
 void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,
@@ -234,8 +249,11 @@ void launch_line_length(const Grid& g, const double* pos, const int* next, int* 
 
 // bs.cu
 int bs_max_splits(int cap);
+// With eom != nullptr the kernel applies the equation of motion to each target
+// tile as soon as its sum is complete, and does not write vel.
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
-                        int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s);
+                        int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
+                        const EomArgs* eom = nullptr);
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
                                int* counters, cudaStream_t s);
 

@@ -76,10 +76,14 @@ def run(vn_mm_s: float, seconds: float, seed: int = 0, sample_s: float = 0.05, u
     every = max(1, int(round(sample_s / u["dt_s"])))
     t, L, vns = [], [], []
     t0 = time.perf_counter()
-    done = 0
+    done, error = 0, ""
     while done < steps:
         n = min(every, steps - done)
-        ch.step(n)
+        try:
+            ch.step(n)
+        except vlb.VlbError as e:  # keep what was measured up to the failing step
+            error = str(e)
+            break
         done += n
         t.append(done * u["dt_s"])
         L.append(line_density_cm2(ch.line_length(), u))
@@ -91,12 +95,12 @@ def run(vn_mm_s: float, seconds: float, seed: int = 0, sample_s: float = 0.05, u
     st = ch.stats()
     ch.close()
     t, L = np.asarray(t), np.asarray(L)
-    tail = t >= 0.6 * t[-1]
-    L_sat = float(L[tail].mean())
-    V_ns = float(np.mean(vns))
-    return dict(vn_mm_s=vn_mm_s, seconds=seconds, steps=steps, seed=seed, dt_s=u["dt_s"], tau=u["tau"],
+    tail = t >= 0.6 * seconds
+    L_sat = float(L[tail].mean()) if tail.any() else float("nan")
+    V_ns = float(np.mean(vns)) if vns else float("nan")
+    return dict(vn_mm_s=vn_mm_s, seconds=seconds, steps=done, error=error, seed=seed, dt_s=u["dt_s"], tau=u["tau"],
                 kappa_lb=u["kappa_lb"], L_sat_cm2=L_sat, L_sat_std=float(L[tail].std()), V_ns_cm_s=V_ns,
-                gamma=math.sqrt(L_sat) / V_ns if V_ns > 0 else None, points=int(st[0]), status=int(st[1]),
+                gamma=math.sqrt(L_sat) / V_ns if V_ns > 0 and L_sat > 0 else None, points=int(st[0]), status=int(st[1]),
                 reconnections=int(st[7]), gpu_wall_s=wall, t=t.tolist(), L=L.tolist())
 
 
