@@ -31,7 +31,25 @@ if ROOT not in sys.path:
 DEFAULT_CONFIG = "channel64x64x256"
 BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76}  # 19 populations read + 19 written per cell and pass
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
-LAUNCHES_PER_STEP = 23  # kernels of one coupled step (1 RK4 sub-step), see the design doc
+
+
+def l2_note(cells: int, esize: int) -> str:
+    pops = 2 * 19 * esize * cells / 1e6
+    fu = (24 + 12) * cells / 1e6  # force grid int64 x 3, velocity float x 3
+    rel = "larger" if (pops + fu) > 129.0 else "not larger"
+    return (f"working set (2 population buffers {pops:.0f} MB + force/velocity {fu:.0f} MB) {rel} than the "
+            f"129 MB L2")
+
+
+def launches_per_step(n_points: int) -> int:
+    """Kernels of one coupled step (1 RK4 sub-step): lattice 3 (velocity-tile
+    marks, stream-collide, plane reduction), filaments 1 + 4 x 3 (force reset;
+    per RK stage geometry, Biot-Savart, equation of motion), remesh 3,
+    reconnection 4.  The Biot-Savart kernel applies the equation of motion
+    itself from 8192 points on (or as VLB_FUSED_EOM forces), 4 launches fewer."""
+    mode = os.environ.get("VLB_FUSED_EOM")
+    fused = n_points >= 8192 if mode is None else mode != "0"
+    return 19 if fused else 23
 
 
 def dist_env():
@@ -229,12 +247,12 @@ def run_vlb(args, ws, rank, local):
                    "cells": cells, "filament_points_start": int(len(nxt)),
                    "filament_points_timed": [int(n_before), int(n_after)],
                    "parallelism": f"replicas x{ws}",
-                   "l2": "working set (2 population buffers 160 MB + force/velocity 25 MB) larger than the 129 MB L2"},
+                   "l2": l2_note(cells, 4 if args.storage == "f32" else 2)},
         "filament_pts_per_s": round(pts_all / secs, 1),
         "ms_per_step_without_graphs": round(nograph_s * 1e3 / args.steps, 4),
         "e2e": {"value": round(e2e_units / e2e_secs / 1e6, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1)},
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": launches_per_step(int(n_before)) * args.steps,
         "roofline": {"kernel": "k_lbm_step", "bound": "hbm",
                      "achieved": round(achieved, 1) if achieved else None,
                      "peak": pk["hbm_gbs"], "unit": "GB/s",
