@@ -39,6 +39,9 @@ struct vlb_channel {
     VfmParams vp;
     int cur_f = 0;     // population buffer holding the current state
     int cur_p = 0;     // point buffer holding the current filaments
+    // Host record of the device state that lets a full step skip two launches:
+    bool f_clean = true;       // force grid zero everywhere (each lattice pass consumes it)
+    bool umask_fresh = false;  // velocity-tile flags match the current points (set by reconnection)
     int cap = 0;
     int hsize = 0;
     int bpp = 0;
@@ -133,15 +136,25 @@ void record_event(vlb_channel* ch) {
     cudaEventRecord(ch->ev[ch->ev_used++], ch->stream);
 }
 
+// Flag the velocity tiles of the current points unless the last reconnection
+// pass already did.  Flags left over from older points only cost extra writes.
+void mark_points(vlb_channel* ch) {
+    if (ch->umask_fresh) return;
+    launch_mark_umask(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.counters, ch->cap, ch->d.umask, ch->stream);
+    ch->umask_fresh = true;
+}
+
 void phase_lbm(vlb_channel* ch) {
     Dev& d = ch->d;
-    // the velocity-tile flags were cleared by the previous pass's plane reduction (or at creation)
-    launch_mark_umask(ch->lp.g, d.pos[ch->cur_p], d.counters, ch->cap, d.umask, ch->stream);
+    mark_points(ch);
     if (ch->timing) record_event(ch);
     launch_lbm_step(ch->lp, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
     if (ch->timing) record_event(ch);
     ch->cur_f ^= 1;
-    launch_plane_vs(ch->lp, d.part, d.umask, ch->stream);
+    // the pass reset the force grid in the flagged tiles; the plane reduction clears both tile flags
+    launch_plane_vs(ch->lp, d.part, d.umask, d.fmask, ch->stream);
+    ch->f_clean = true;
+    ch->umask_fresh = false;
 }
 
 // Whether the Biot-Savart kernel applies the equation of motion itself.  It
@@ -180,7 +193,8 @@ void phase_vfm(vlb_channel* ch) {
     ea.counters = d.counters;
     for (int sub = 0; sub < nsub; ++sub) {
         const int spread = (sub == 0 && ch->p.couple) ? 1 : 0;
-        if (spread) launch_zero_force(ch->lp.g, d.F, d.fmask, ch->stream);
+        if (spread && !ch->f_clean) launch_zero_force(ch->lp.g, d.F, d.fmask, ch->stream);
+        if (spread) ch->f_clean = false;
         for (int stage = 0; stage < 4; ++stage) {
             const double* xs = stage == 0 ? pos : d.st;
             ea.stage = stage;
@@ -201,14 +215,19 @@ void phase_vfm(vlb_channel* ch) {
 
 void run_phases(vlb_channel* ch, int mask) {
     if (mask & VLB_PHASE_LBM) phase_lbm(ch);
-    if (mask & VLB_PHASE_VFM) phase_vfm(ch);
+    if (mask & VLB_PHASE_VFM) {
+        phase_vfm(ch);
+        ch->umask_fresh = false;
+    }
     if (mask & VLB_PHASE_REMESH) {
         launch_remesh(ch->vp, ch->d, ch->cur_p, ch->cap, ch->stream);
         ch->cur_p ^= 1;
+        ch->umask_fresh = false;
     }
     if (mask & VLB_PHASE_RECONNECT) {
-        launch_reconnect(ch->vp, ch->d, ch->cur_p, ch->cap, ch->hsize, ch->stream);
+        launch_reconnect(ch->vp, ch->d, ch->cur_p, ch->cap, ch->hsize, ch->stream);  // flags the new points' tiles
         ch->cur_p ^= 1;
+        ch->umask_fresh = true;
     }
 }
 
@@ -620,6 +639,7 @@ int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, i
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "seed copy");
     ch->n_hint = n;
+    ch->umask_fresh = false;
     return VLB_OK;
 }
 
@@ -647,6 +667,15 @@ bool step_graph(vlb_channel* ch, bool multi) {
     const int f = ch->cur_f, q = ch->cur_p;
     const int cls = size_class(ch->n_hint);
     cudaGraphExec_t& ge = ch->gexec[m][f][q];
+    mark_points(ch);  // the captured steps start from flagged velocity tiles
+    const bool f_clean0 = ch->f_clean, umask_fresh0 = ch->umask_fresh;
+    auto undo = [&] {  // nothing ran: back to the state before the attempt
+        ch->cur_f = f;
+        ch->cur_p = q;
+        ch->f_clean = f_clean0;
+        ch->umask_fresh = umask_fresh0;
+        return false;
+    };
     if (ge && ch->gclass[m][f][q] != cls) {
         // the Biot-Savart grid was sized for another filament count: capture again
         cudaGraphExecDestroy(ge);
@@ -656,7 +685,7 @@ bool step_graph(vlb_channel* ch, bool multi) {
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(ch->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
-            return false;
+            return undo();
         }
         tl_capturing = true;
         for (int k = 0; k < nst; ++k) run_phases(ch, VLB_PHASE_ALL);
@@ -666,19 +695,21 @@ bool step_graph(vlb_channel* ch, bool multi) {
         ch->cur_p = q;
         if (e != cudaSuccess || !graph) {
             cudaGetLastError();
-            return false;
+            return undo();
         }
         e = cudaGraphInstantiate(&ge, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             cudaGetLastError();
             ge = nullptr;
-            return false;
+            return undo();
         }
         ch->gclass[m][f][q] = cls;
     }
-    if (cudaGraphLaunch(ge, ch->stream) != cudaSuccess) return false;
+    if (cudaGraphLaunch(ge, ch->stream) != cudaSuccess) return undo();
     if (nst & 1) ch->cur_f ^= 1;  // the point buffers are back to q after remesh and reconnect
+    ch->f_clean = !ch->p.couple;  // state after full steps: the last one spread its reaction
+    ch->umask_fresh = true;       // and flagged its points' velocity tiles
     return true;
 }
 
@@ -848,6 +879,7 @@ int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t byt
         float* tmp = (float*)d.f[ch->cur_f ^ 1];  // spare population buffer
         e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, s);
         launch_force_import(ch->lp.g, tmp, d.F, s);
+        ch->f_clean = false;
         const int nt = ch->lp.g.tnx * ch->lp.g.tny * ch->lp.g.tnz;
         cudaMemsetAsync(d.fmask, 1, (size_t)nt, s);
     } else {

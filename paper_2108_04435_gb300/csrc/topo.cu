@@ -122,7 +122,8 @@ __device__ int block_exclusive_scan(int v, int* total) {
 __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double* __restrict__ s,
                                                        const int* __restrict__ next, const int* __restrict__ prev,
                                                        const int* __restrict__ counters, int cap,
-                                                       double* __restrict__ spp, double* __restrict__ seglen) {
+                                                       double* __restrict__ spp, double* __restrict__ seglen,
+                                                       uint8_t* __restrict__ flags) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,29 +166,23 @@ __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double
     const double den = lp * lm * (lp + lm);
     for (int k = 0; k < 3; ++k) spp[(long long)k * cap + i] = 2.0 * (lm * b[k] - lp * a[k]) / den;
     seglen[i] = q >= 0 ? lp : 0.0;
-}
-
-// ------------------------------------------------------------------ remesh
-
-__global__ void k_remesh_flags(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
-                               const int* __restrict__ prev, const double* __restrict__ seglen,
-                               const int* __restrict__ counters, int cap, uint8_t* __restrict__ flags) {
-    pdl_wait_trigger();
-    const int N = counters[CNT_N];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int p = prev[i], q = next[i];
-    const double li = seglen[i];
-    const bool split = q >= 0 && li > P.dmax;
+    // Remesh flags (bit 1 split, bit 2 removal candidate).  The predecessor's
+    // segment length is lm: the same expression its own thread evaluates.
+    const bool split = q >= 0 && lp > P.dmax;
     bool cand = false;
     if (p >= 0 && q >= 0) {  // open ends are never removed
-        const double lp = seglen[p];
-        const bool split_p = lp > P.dmax;
-        const double lmin = lp < li ? lp : li;
-        cand = (lmin < P.dmin) && (dist(P.g, pos, cap, p, q) <= P.dmax) && !split_p && !split;
+        const bool split_p = lm > P.dmax;
+        const double lmin = lm < lp ? lm : lp;
+        double d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = min_image(P.g, k, sq[k] - sp[k]);
+        const double lpq = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        cand = (lmin < P.dmin) && (lpq <= P.dmax) && !split_p && !split;
     }
     flags[i] = (uint8_t)((split ? 1 : 0) | (cand ? 2 : 0));
 }
+
+// ------------------------------------------------------------------ remesh
 
 // Points of loops and open lines with fewer than five points die; one block,
 // strided over [0, T).  A loop point finds its own loop (succ^k(i) == i,
@@ -239,11 +234,12 @@ __device__ int block_small_components(const int* __restrict__ succ, uint8_t* __r
 }
 
 // One block: stable compaction of the alive points of [0, T) into the other
-// point buffer, successor indices renumbered, predecessors rebuilt.
+// point buffer, successor indices renumbered, predecessors rebuilt; with umask
+// set, the velocity tiles of the next lattice pass are flagged at the same time.
 __device__ void block_compact(const double* __restrict__ pin, const int* __restrict__ succ,
                               const uint8_t* __restrict__ alive, int T, int* __restrict__ newidx,
                               double* __restrict__ pout, int* __restrict__ nout, int* __restrict__ pvout,
-                              int* __restrict__ counters, int cap) {
+                              int* __restrict__ counters, int cap, const Grid& g, uint8_t* __restrict__ umask) {
     const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
     const int b0 = min(T, (int)threadIdx.x * per);
     const int b1 = min(T, b0 + per);
@@ -260,6 +256,7 @@ __device__ void block_compact(const double* __restrict__ pin, const int* __restr
         if (!alive[k]) continue;
         const int n = newidx[k];
         for (int c = 0; c < 3; ++c) pout[(long long)c * cap + n] = pin[(long long)c * cap + k];
+        if (umask) mark_velocity_tiles(g, pin[k], pin[(long long)cap + k], pin[2LL * cap + k], umask);
         const int sk = succ[k];
         if (sk < 0) {  // last point of an open line
             nout[n] = -1;
@@ -373,7 +370,7 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
         dstats[DS_SMALL] += (double)dead_all;
     }
     __syncthreads();
-    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap);
+    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap, P.g, nullptr);
 }
 
 // -------------------------------------------------------------- reconnect
@@ -512,7 +509,8 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     const int* __restrict__ cand_a, const int* __restrict__ cand_b, const double* __restrict__ cand_d2,
     int* __restrict__ order, int* __restrict__ stamp, const int* __restrict__ hkey, int* __restrict__ hhead,
     uint8_t* __restrict__ alive, int* __restrict__ newidx, double* __restrict__ pout, int* __restrict__ nout,
-    int* __restrict__ pvout, int* __restrict__ counters, double* __restrict__ dstats, int cap) {
+    int* __restrict__ pvout, int* __restrict__ counters, double* __restrict__ dstats, int cap,
+    uint8_t* __restrict__ umask) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int K = counters[CNT_NPAIRS];
@@ -590,17 +588,15 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) dstats[DS_SMALL] += (double)dead_all;
     __syncthreads();
-    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap);
+    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, P.g, umask);
 }
 
 }  // namespace
 
 void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s) {
     if (cap <= 0) return;
-    const int nb = (cap + 255) / 256;
-    launch_pdl(k_geometry_exact, (cap + 63) / 64, 64, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, d.spp,
-                                                     d.seglen);
-    launch_pdl(k_remesh_flags, nb, 256, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.seglen, d.counters, cap, d.flags);
+    launch_pdl(k_geometry_exact, (cap + 63) / 64, 64, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap,
+               d.spp, d.seglen, d.flags);
     launch_pdl(k_remesh_finish, 1, 1024, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
                                        d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1],
                                        d.counters, d.dstats, cap);
@@ -621,7 +617,7 @@ void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, c
     launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.hlink, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
                                           d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
-                                          cap);
+                                          cap, d.umask);
 }
 
 }  // namespace vlb

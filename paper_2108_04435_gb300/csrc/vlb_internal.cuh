@@ -105,6 +105,34 @@ struct Grid {
     int tnx, tny, tnz;  // activity tiles per axis
 };
 
+// Flag the velocity tiles within one cell of point x (the nodes the 2-point
+// delta function of Eq. 11 can reach, with a cell of margin): the
+// stream-collide pass writes u only in flagged tiles.
+__device__ __forceinline__ void mark_velocity_tiles(const Grid& g, double x, double y, double z,
+                                                    uint8_t* __restrict__ umask) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const double xs[3] = {x, y, z};
+    int t[3][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int b = (int)floor(xs[a]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int c = b - 1 + k;
+            if (g.wall[a]) c = c < 0 ? 0 : (c > n[a] - 1 ? n[a] - 1 : c);
+            else c = ((c % n[a]) + n[a]) % n[a];
+            t[a][k] = c >> TILE_SHIFT;
+        }
+    }
+#pragma unroll
+    for (int kz = 0; kz < 4; ++kz)
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 4; ++kx) umask[(t[2][kz] * g.tny + t[1][ky]) * g.tnx + t[0][kx]] = 1;
+}
+
+
 struct LbmParams {
     Grid g;
     float omega;        // 1/tau
@@ -224,9 +252,9 @@ struct Dev {
 // ---------------------------------------------------------------- launchers
 // lbm.cu
 void launch_lbm_init(const LbmParams& P, void* f, float* U, const double init_u[3], cudaStream_t s);
-void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U,
+void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, long long* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
-void launch_plane_vs(const LbmParams& P, const double* part, uint8_t* umask, cudaStream_t s);
+void launch_plane_vs(const LbmParams& P, const double* part, uint8_t* umask, uint8_t* fmask, cudaStream_t s);
 int lbm_blocks_per_plane(const LbmParams& P);
 void launch_moments(const LbmParams& P, const void* f, const long long* F, const uint8_t* fmask, float* rho,
                     float* U, cudaStream_t s);
