@@ -25,7 +25,8 @@
  *    beta = kappa/(4 pi) ln(2 sqrt(l+ l-)/(e^{1/4} a)).
  *  - Time integration: classic RK4 over one lattice step (or vfm_substeps
  *    sub-steps) with u, V_s frozen; the reaction of Eq. 10 is taken from the
- *    first stage and spread with the 2-point delta function of Eq. 11.
+ *    first stage and spread with the 2-point delta function of Eq. 11.  The
+ *    force grid is the force of the next lattice pass only, which consumes it.
  *  - Remeshing and reconnection rules (Sec. II.A only fixes the resolution
  *    [dxi_min, dxi_max] and "exchange legs within the resolution"): see
  *    remesh() and reconnect() below.
@@ -259,6 +260,10 @@ static void lbm_pass(vlbref_channel* ch) {
     ch->max_mach = sqrt(3.0 * maxu2);
     if (ch->max_mach >= 0.05) ch->status |= ST_MACH; /* Sec. II.B: |u|/c_s < 0.05 */
     if (nan) ch->status |= ST_NAN;
+    /* The force grid holds the friction reaction for this one lattice pass
+     * (the reaction spread in step n acts in the next lattice step only): the
+     * pass consumes it. */
+    memset(ch->F, 0, sizeof(double) * 3 * (size_t)C);
 }
 
 /* -------------------------------------------- coupling: Eq. 11 (2-point delta) */
