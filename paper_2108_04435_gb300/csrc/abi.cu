@@ -151,8 +151,8 @@ void phase_lbm(vlb_channel* ch) {
     launch_lbm_step(ch->lp, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
     if (ch->timing) record_event(ch);
     ch->cur_f ^= 1;
-    // the pass reset the force grid in the flagged tiles; the plane reduction clears both tile flags
-    launch_plane_vs(ch->lp, d.part, d.umask, d.fmask, ch->stream);
+    // the pass consumed the force grid: the plane reduction resets it and clears both tile flags
+    launch_plane_vs(ch->lp, d.part, d.F, d.umask, d.fmask, ch->stream);
     ch->f_clean = true;
     ch->umask_fresh = false;
 }
@@ -213,7 +213,7 @@ void phase_vfm(vlb_channel* ch) {
     }
 }
 
-void run_phases(vlb_channel* ch, int mask) {
+void run_phases_body(vlb_channel* ch, int mask) {
     if (mask & VLB_PHASE_LBM) phase_lbm(ch);
     if (mask & VLB_PHASE_VFM) {
         phase_vfm(ch);
@@ -231,6 +231,12 @@ void run_phases(vlb_channel* ch, int mask) {
     }
 }
 
+void run_phases(vlb_channel* ch, int mask) {
+    const bool was = tl_no_pdl;
+    if (ch->timing) tl_no_pdl = true;
+    run_phases_body(ch, mask);
+    tl_no_pdl = was;
+}
 int finish(vlb_channel* ch) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -285,7 +291,7 @@ namespace vlb {
 
 int set_error(int code, const char* msg) { return fail(code, msg); }
 
-thread_local bool tl_capturing = false;
+thread_local bool tl_no_pdl = false;
 
 bool pdl_enabled() {
     static const bool on = [] {
@@ -687,9 +693,9 @@ bool step_graph(vlb_channel* ch, bool multi) {
             cudaGetLastError();
             return undo();
         }
-        tl_capturing = true;
+        tl_no_pdl = true;
         for (int k = 0; k < nst; ++k) run_phases(ch, VLB_PHASE_ALL);
-        tl_capturing = false;
+        tl_no_pdl = false;
         cudaError_t e = cudaStreamEndCapture(ch->stream, &graph);
         ch->cur_f = f;  // the captured steps have not run yet
         ch->cur_p = q;

@@ -174,7 +174,7 @@ __device__ __forceinline__ void pull_fast(const typename Pop<S>::T* __restrict__
 template <bool WX, bool WY, bool WZ, int S>
 __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T* __restrict__ fin,
                                                         typename Pop<S>::T* __restrict__ fout,
-                                                        long long* __restrict__ F, float* __restrict__ U,
+                                                        const long long* __restrict__ F, float* __restrict__ U,
                                                         const uint8_t* __restrict__ fmask,
                                                         const uint8_t* __restrict__ umask, double* __restrict__ part,
                                                         LbmParams P) {
@@ -205,13 +205,10 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
         const int tile = tile_of(P.g, x, y, z);
         const bool factive = fmask[tile] != 0;
         float Fx = P.body[0], Fy = P.body[1], Fz = P.body[2];
-        if (factive) {  // consumed: the cell's force is read once and reset for the next spreading
-            Fx += force_value(F[cell]);
-            Fy += force_value(F[C + cell]);
-            Fz += force_value(F[2 * C + cell]);
-            F[cell] = 0;
-            F[C + cell] = 0;
-            F[2 * C + cell] = 0;
+        if (factive) {
+            Fx += force_value(__ldg(&F[cell]));
+            Fy += force_value(__ldg(&F[C + cell]));
+            Fz += force_value(__ldg(&F[2 * C + cell]));
         }
         const bool force = factive || P.body_on;
         const float rho = P.rho0 + drho;
@@ -296,16 +293,35 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
 // and the Mach limit of Sec. II.B (|u|/c_s < 0.05).  One warp per plane
 // (lane-strided loads, fixed shuffle tree); the last block to finish reduces
 // the planes in a fixed order.  FP64 work is spread over many SMs because
-// its per-SM rate is low on this GPU.  It also clears the force- and
-// velocity-tile flags the stream-collide pass has just used (that pass reset
-// the force grid in the flagged tiles).
+// its per-SM rate is low on this GPU.  The stream-collide pass has consumed
+// the force grid: one warp per tile resets it in the flagged tiles, then
+// both tile flags are cleared for the next step.
 __global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ part, int bpp, LbmParams P,
-                                                  uint8_t* __restrict__ umask, uint8_t* __restrict__ fmask,
-                                                  int ntiles) {
+                                                  long long* __restrict__ F, uint8_t* __restrict__ umask,
+                                                  uint8_t* __restrict__ fmask, int ntiles) {
     pdl_wait_trigger();
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
-        umask[t] = 0;
-        fmask[t] = 0;
+    {
+        const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+        const int ln = threadIdx.x & 31;
+        const Grid& g = P.g;
+        for (int t = warp; t < ntiles; t += nwarps) {
+            if (fmask[t]) {
+                const int tx = t % g.tnx, ty = (t / g.tnx) % g.tny, tz = t / (g.tnx * g.tny);
+                for (int k = ln; k < 512; k += 32) {
+                    const int x = (tx << TILE_SHIFT) + (k & 7), y = (ty << TILE_SHIFT) + ((k >> 3) & 7),
+                              z = (tz << TILE_SHIFT) + (k >> 6);
+                    if (x < g.nx && y < g.ny && z < g.nz) {
+                        const long long c = ((long long)z * g.ny + y) * g.nx + x;
+                        F[c] = 0;
+                        F[g.ncell + c] = 0;
+                        F[2 * g.ncell + c] = 0;
+                    }
+                }
+                __syncwarp();
+                if (ln == 0) fmask[t] = 0;
+            }
+            if (ln == 0) umask[t] = 0;
+        }
     }
     __shared__ double s_tot[256], s_mass[256], s_max[256];
     __shared__ int s_last;
@@ -414,7 +430,7 @@ __device__ __forceinline__ void vstore(float* p, const float (&v)[VEC]) {
 
 template <bool WX, bool WY, bool WZ, int VEC>
 __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ fin, float* __restrict__ fout,
-                                                      long long* __restrict__ F, float* __restrict__ U,
+                                                      const long long* __restrict__ F, float* __restrict__ U,
                                                       const uint8_t* __restrict__ fmask,
                                                       const uint8_t* __restrict__ umask, double* __restrict__ part,
                                                       LbmParams P) {
@@ -517,9 +533,6 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ 
                 Fx[c] += force_value(F[cell0 + c]);
                 Fy[c] += force_value(F[C + cell0 + c]);
                 Fz[c] += force_value(F[2 * C + cell0 + c]);
-                F[cell0 + c] = 0;
-                F[C + cell0 + c] = 0;
-                F[2 * C + cell0 + c] = 0;
             }
         }
         float drho[VEC], ux[VEC], uy[VEC], uz[VEC];
@@ -758,7 +771,7 @@ __global__ void k_force_import(const float* __restrict__ in, long long* __restri
 }
 
 template <bool WX, bool WY, bool WZ>
-void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, long long* F, float* U, const uint8_t* fmask,
+void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U, const uint8_t* fmask,
                   const uint8_t* umask, double* part, cudaStream_t s) {
     const int nxy = P.g.nx * P.g.ny;
     if (P.storage == STORE_F32 && (P.vec == 4 || P.vec == 2)) {
@@ -814,7 +827,7 @@ void moments_dispatch(const LbmParams& P, const void* f, const long long* F, con
         }                                                                            \
     } while (0)
 
-void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, long long* F, float* U,
+void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s) {
     VLB_WALL_DISPATCH(lbm_dispatch, P, fin, fout, F, U, fmask, umask, part, s);
 }
@@ -862,9 +875,10 @@ int lbm_blocks_per_plane(const LbmParams& P) {
     return (nxy + P.block - 1) / P.block;
 }
 
-void launch_plane_vs(const LbmParams& P, const double* part, uint8_t* umask, uint8_t* fmask, cudaStream_t s) {
+void launch_plane_vs(const LbmParams& P, const double* part, long long* F, uint8_t* umask, uint8_t* fmask,
+                     cudaStream_t s) {
     const int bpp = lbm_blocks_per_plane(P);
-    launch_pdl(k_plane_vs, (P.g.nz + 7) / 8, 256, 0, s, part, bpp, P, umask, fmask, P.g.tnx * P.g.tny * P.g.tnz);
+    launch_pdl(k_plane_vs, (P.g.nz + 7) / 8, 256, 0, s, part, bpp, P, F, umask, fmask, P.g.tnx * P.g.tny * P.g.tnz);
 }
 
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,

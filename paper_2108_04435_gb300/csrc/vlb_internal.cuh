@@ -71,18 +71,19 @@ __device__ __forceinline__ void pdl_wait_trigger() {
 }
 
 // VLB_PDL=0 in the environment turns programmatic launch off (default on).  It
-// is not used while a CUDA graph is captured on this thread: the graph
-// schedules its kernel nodes back to back by itself, and measured slower with
-// programmatic edges.
+// is not used while tl_no_pdl is set on this thread: during graph capture (the
+// graph schedules its kernel nodes back to back by itself, and measured slower
+// with programmatic edges) and in the event-timed mode (an event between two
+// kernels must see the first one finished).
 bool pdl_enabled();
-extern thread_local bool tl_capturing;
+extern thread_local bool tl_no_pdl;
 
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                        Args&&... args) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = (pdl_enabled() && !tl_capturing) ? 1 : 0;
+    attr[0].val.programmaticStreamSerializationAllowed = (pdl_enabled() && !tl_no_pdl) ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -252,9 +253,10 @@ struct Dev {
 // ---------------------------------------------------------------- launchers
 // lbm.cu
 void launch_lbm_init(const LbmParams& P, void* f, float* U, const double init_u[3], cudaStream_t s);
-void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, long long* F, float* U,
+void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U,
                      const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
-void launch_plane_vs(const LbmParams& P, const double* part, uint8_t* umask, uint8_t* fmask, cudaStream_t s);
+void launch_plane_vs(const LbmParams& P, const double* part, long long* F, uint8_t* umask, uint8_t* fmask,
+                     cudaStream_t s);
 int lbm_blocks_per_plane(const LbmParams& P);
 void launch_moments(const LbmParams& P, const void* f, const long long* F, const uint8_t* fmask, float* rho,
                     float* U, cudaStream_t s);
