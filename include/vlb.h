@@ -68,6 +68,9 @@ typedef struct {
     int32_t force_form;      /* 0: f of Eq. 10 as printed; 1: f = rho_s kappa (rhs of Eq. 10) x s' */
     int32_t max_points;      /* filament point capacity (device arrays are sized by it) */
     int32_t storage;         /* population storage: VLB_STORE_F32 (0), VLB_STORE_F16 (1) or VLB_STORE_BF16 (2) */
+    int32_t wall_images;     /* 1: the boundary-induced velocity v_s,b of Sec. II.A from first-order mirror images
+                                of every segment across each solid wall face (orientation reversed); 0: v_s,b = 0 */
+    int32_t reserved;        /* 0 */
     double  tau, rho0;       /* BGK relaxation time (> 1/2, Eq. 8) and reference density */
     double  body_force[3];   /* uniform body force added to the force grid (0 in the paper's runs) */
     double  heater_vn;       /* Sec. IV heater: normal velocity injected at the low z face and removed at the high one */

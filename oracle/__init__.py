@@ -46,7 +46,7 @@ class Params(C.Structure):
     _fields_ = [
         ("n", C.c_int32 * 3), ("wall", C.c_int32 * 3), ("stream_axis", C.c_int32),
         ("vfm_substeps", C.c_int32), ("couple", C.c_int32), ("force_form", C.c_int32),
-        ("max_points", C.c_int32), ("reserved", C.c_int32),
+        ("max_points", C.c_int32), ("reserved", C.c_int32), ("wall_images", C.c_int32), ("reserved2", C.c_int32),
         ("tau", C.c_double), ("rho0", C.c_double), ("body_force", C.c_double * 3),
         ("heater_vn", C.c_double), ("pin_vn", C.c_double), ("init_vn", C.c_double * 3),
         ("kappa", C.c_double), ("alpha", C.c_double), ("alpha_p", C.c_double),

@@ -23,6 +23,9 @@
  *    image on periodic axes, the two segments touching the target excluded and
  *    replaced by the local term beta s' x s'' with Schwarz's cutoff
  *    beta = kappa/(4 pi) ln(2 sqrt(l+ l-)/(e^{1/4} a)).
+ *  - Wall images (wall_images = 1): v_s,b from first-order mirror images of
+ *    every segment across each solid wall face, orientation reversed; a pinned
+ *    end skips the image of its own segment across its own wall (image_velocity()).
  *  - Time integration: classic RK4 over one lattice step (or vfm_substeps
  *    sub-steps) with u, V_s frozen; the reaction of Eq. 10 is taken from the
  *    first stage and spread with the 2-point delta function of Eq. 11.  The
@@ -388,6 +391,41 @@ static void point_geometry(const vlbref_channel* ch, const double* s, int i, dou
     if (lplus) *lplus = lp;
 }
 
+/* Boundary-induced velocity v_s,b (Sec. II.A) from images: each segment
+ * j -> q is mirrored across each solid wall face (x_a -> 2w - x_a, walls at
+ * w = -1/2 and n_a - 1/2) with its orientation reversed, i.e. the image
+ * segment runs from M(s_q) to M(s_j); first-order images only.  A pinned end
+ * does not see the image, across its own wall, of its one segment: that
+ * image continues the line through the wall and belongs to its local term. */
+static void image_velocity(const vlbref_channel* ch, const double* s, const double* seg, int i, double* out) {
+    const int N = ch->N;
+    int own_face = -1, own_seg = -1;
+    if (ch->prev[i] < 0 || ch->next[i] < 0) {
+        own_face = touching_wall(ch, &s[3 * i]);
+        own_seg = ch->prev[i] < 0 ? i : ch->prev[i];
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (!ch->p.wall[a]) continue;
+        for (int side = 0; side < 2; ++side) {
+            const double w = side ? (double)ch->p.n[a] - 0.5 : -0.5;
+            for (int j = 0; j < N; ++j) {
+                const int q = ch->next[j];
+                if (q < 0) continue;
+                if (2 * a + side == own_face && j == own_seg) continue;
+                double start[3], d[3], R1[3];
+                for (int k = 0; k < 3; ++k) {
+                    start[k] = s[3 * q + k];
+                    d[k] = -seg[3 * j + k]; /* M(s_j) - M(s_q) off the normal axis */
+                }
+                start[a] = 2.0 * w - s[3 * q + a];
+                d[a] = seg[3 * j + a];
+                diff3(ch, start, &s[3 * i], R1);
+                segment_add(R1, d, ch->p.kappa, out);
+            }
+        }
+    }
+}
+
 /* Velocity ds/dt of every point at positions s (Eq. 3 + Eq. 4).  When
  * spread != 0, the reaction of Eq. 10 on the normal fluid is spread into F. */
 static void filament_velocity(vlbref_channel* ch, const double* s, double* k, double* vbs_out, int spread) {
@@ -412,6 +450,7 @@ static void filament_velocity(vlbref_channel* ch, const double* s, double* k, do
             diff3(ch, &s[3 * j], &s[3 * i], R1);
             segment_add(R1, &seg[3 * j], ch->p.kappa, vbs);
         }
+        if (ch->p.wall_images) image_velocity(ch, s, seg, i, vbs);
         double vs[3], vn[3], w[3], t[3], tt[3];
         for (int a = 0; a < 3; ++a) vs[a] = vbs[a] + lia[3 * i + a];
         vs[sa] += vs_at(ch, &s[3 * i]); /* v_s,a: counterflow superfluid velocity (Eq. 18) */

@@ -37,6 +37,8 @@ typedef struct {
     int32_t force_form;      /* 0: f of Eq. 10 as printed; 1: f = rho_s kappa (Eq. 10 rhs) x s' (Magnus drag) */
     int32_t max_points;      /* filament point capacity */
     int32_t reserved;
+    int32_t wall_images;     /* 1: v_s,b from first-order mirror images across each solid wall face (Sec. II.A) */
+    int32_t reserved2;
     double tau, rho0;        /* BGK relaxation time (> 1/2), reference density */
     double body_force[3];    /* uniform body force added to the force grid */
     double heater_vn;        /* normal velocity injected at the low stream face, removed at the high face */

@@ -26,7 +26,7 @@ TEMPS = {
 
 def base_params(n, wall, T=1.9, **kw):
     p = dict(n=list(n), wall=list(wall), stream_axis=2, vfm_substeps=1, couple=1, force_form=0,
-             max_points=4096, storage=0, tau=0.6, rho0=1.0, body_force=[0.0, 0.0, 0.0],
+             max_points=4096, storage=0, wall_images=0, tau=0.6, rho0=1.0, body_force=[0.0, 0.0, 0.0],
              heater_vn=0.0, pin_vn=0.0, init_vn=[0.0, 0.0, 0.0], core_a=CORE_A,
              dxi_min=0.70, dxi_max=0.95)
     p.update(TEMPS[T])

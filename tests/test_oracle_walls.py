@@ -18,7 +18,11 @@ become pinned ends on that bound).  The cases:
   segment at an end is split at its midpoint; two antiparallel wall-bound lines
   reconnect into two U-shaped lines;
 - a ring driven into a wall by its own motion ends up as a line pinned on that
-  wall, and all ends stay on wall bounds throughout.
+  wall, and all ends stay on wall bounds throughout;
+- wall images (the boundary-induced velocity v_s,b): a line parallel to the
+  walls moves at the closed-form velocity of its two image lines; a half
+  circle standing on a wall plus its images is the full circle, ends included;
+  a line perpendicular to the walls gets nothing from its collinear images.
 """
 import numpy as np
 import pytest
@@ -267,3 +271,69 @@ def test_ring_driven_into_wall_becomes_pinned_line(oracle_mod):
     assert st[13] >= 1
     ends = [k for k in range(len(nx)) if nx[k] < 0]
     assert len(ends) >= 1 and all(pos[k, 2] == lo for k in ends)
+
+
+def test_images_of_a_line_parallel_to_the_walls(oracle_mod):
+    """A straight line along the periodic z axis between two x walls sees its
+    two images (antiparallel lines at twice its distance to each wall): it
+    moves along y at g(D_hi) - g(D_lo), with g the velocity of the finite image
+    line the minimum image leaves (m segments of L/m, odd m: from (m+1)L/(2m)
+    below the target to (m-1)L/(2m) above)."""
+    nx, L, m = 16, 32, 41
+    x0, y0 = 4.3, 7.0
+    p = wparams(n=(nx, 16, L), wall=(1, 0, 0), wall_images=1)
+    z = L * np.arange(m) / m
+    xyz = np.c_[np.full(m, x0), np.full(m, y0), z]
+    nxt = ((np.arange(m) + 1) % m).astype(np.int32)
+    ch = oracle_mod.Channel(p)
+    ch.seed(xyz, nxt)
+    _, vbs = ch.point_velocity()
+    a, b = (m + 1) * L / (2 * m), (m - 1) * L / (2 * m)
+
+    def g(D):
+        return p["kappa"] / (4 * np.pi * D) * (a / np.hypot(a, D) + b / np.hypot(b, D))
+
+    D_lo, D_hi = 2 * (x0 + 0.5), 2 * (nx - 0.5 - x0)
+    vy = g(D_hi) - g(D_lo)
+    assert vy < 0  # nearer to the low wall: pulled along -y
+    assert np.abs(vbs[:, 1] - vy).max() < 1e-12 * abs(vy)
+    assert np.abs(vbs[:, [0, 2]]).max() < 1e-15
+    # without images the straight line has no velocity at all
+    ch0 = oracle_mod.Channel(wparams(n=(nx, 16, L), wall=(1, 0, 0)))
+    ch0.seed(xyz, nxt)
+    assert np.abs(ch0.point_velocity()[1]).max() < 1e-15
+
+
+@pytest.mark.parametrize("m", [9, 13])
+def test_half_circle_and_its_image_are_the_full_circle(oracle_mod, m):
+    """A half circle standing on a wall plus its images is the full circle:
+    every point, the pinned ends included, gets the full circle's Biot-Savart
+    velocity.  At an end this needs the exclusion rule: the image of the end's
+    own segment is the full circle's other adjacent segment."""
+    R = 2.5
+    # the far z wall sits 1024 cells away: its image of the open arc adds
+    # ~ kappa l / d^2 ~ 1.5e-8 (1e-6 relative); a wrong exclusion at the ends
+    # would be off by the adjacent segment's ~1e-2
+    p = wparams(n=(16, 16, 1024), dxi_min=1e-9, dxi_max=1.2, wall_images=1)
+    th = np.pi * np.arange(m) / (m - 1)
+    half = np.c_[8.0 + R * np.cos(th), np.full(m, 8.0), -0.5 + R * np.sin(th)]
+    half[[0, -1], 2] = -0.5 + 1e-10
+    ch = oracle_mod.Channel(p)
+    ch.seed(*inputs.open_line(half))
+    _, v_half = ch.point_velocity()
+    M = 2 * (m - 1)
+    thf = 2 * np.pi * np.arange(M) / M
+    full = np.c_[32.0 + R * np.cos(thf), np.full(M, 32.0), 32.0 + R * np.sin(thf)]
+    cf = oracle_mod.Channel(wparams(n=(64, 64, 64), wall=(0, 0, 0)))
+    cf.seed(full, ((np.arange(M) + 1) % M).astype(np.int32))
+    _, v_full = cf.point_velocity()
+    assert np.abs(v_half - v_full[:m]).max() < 1e-5 * np.abs(v_full).max()
+
+
+def test_images_leave_a_spanning_line_still(oracle_mod):
+    """The images of a line perpendicular to the walls are collinear with it."""
+    p = wparams(n=(12, 12, 16), wall_images=1)
+    ch = oracle_mod.Channel(p)
+    ch.seed(*inputs.wall_line((5.3, 6.1, 0.0), (5.3, 6.1, 15.0), spacing=0.9))
+    _, vbs = ch.point_velocity()
+    assert np.abs(vbs).max() < 1e-15
