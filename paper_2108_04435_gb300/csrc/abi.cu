@@ -201,12 +201,13 @@ void phase_vfm(vlb_channel* ch) {
             ea.spread = spread;
             launch_geometry_stage(ch->vp, xs, next, prev, d.counters, cap, d.geo, d.seg, stage == 0 ? d.s0 : nullptr,
                                   ch->stream);
+            const VfmParams& V = ch->vp;
             if (fused_eom(ch->n_hint)) {
-                launch_biot_savart(ch->vp.g, ch->vp.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint,
-                                   d.bsp, d.vbs, ch->stream, &ea);
+                launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint, d.bsp, d.vbs,
+                                   ch->stream, &ea, V.nfaces, V.face_code, d.geo);
             } else {
-                launch_biot_savart(ch->vp.g, ch->vp.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint,
-                                   d.bsp, d.vbs, ch->stream);
+                launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint, d.bsp, d.vbs,
+                                   ch->stream, nullptr, V.nfaces, V.face_code, d.geo);
                 launch_eom(ea, d.vbs, ch->stream);
             }
         }
@@ -254,6 +255,7 @@ bool valid_axis_params(const vlb_params* p, std::string* why) {
         if (p->wall[a] != 0 && p->wall[a] != 1) { *why = "wall must be 0 or 1"; return false; }
     }
     if (p->stream_axis != 2) { *why = "stream_axis must be 2 (z) in this library"; return false; }
+    if (p->wall_images != 0 && p->wall_images != 1) { *why = "wall_images must be 0 or 1"; return false; }
     if (!(p->tau > 0.5)) { *why = "tau must exceed 1/2"; return false; }
     if (!(p->rho0 > 0.0)) { *why = "rho0 must be positive"; return false; }
     if (!(p->dxi_min > 0.0) || !(p->dxi_max > p->dxi_min) || !(p->dxi_max < 1.0)) {
@@ -359,7 +361,11 @@ size_t vlb_channel_bytes(const vlb_params* p) {
     const size_t bpp = (size_t)((p->n[0] * p->n[1] + 127) / 128) + 1;
     size_t b = 2 * up(esize * 19 * C) + up(8 * 3 * C) + up(4 * 3 * C) + 2 * up(nt) + up(8 * 3 * bpp * p->n[2]);
     b += 3 * up(8 * (size_t)p->n[2]) + up(4 * (size_t)p->n[2]) + up(8 * DS_COUNT) + up(4 * CNT_COUNT);
-    b += 2 * (up(24 * cap) + 2 * up(4 * cap)) + 6 * up(24 * cap) + up(8 * cap) + up(32 * cap) + up(48 * cap);
+    size_t nfaces = 0;
+    if (p->wall_images)
+        for (int a = 0; a < 3; ++a) nfaces += p->wall[a] ? 2 : 0;
+    b += 2 * (up(24 * cap) + 2 * up(4 * cap)) + 6 * up(24 * cap) + up(8 * cap) + up(32 * cap) +
+         up(48 * cap * (1 + nfaces));
     b += up(12 * cap * (size_t)bs_max_splits((int)cap)) + up(12 * cap) + up(4 * ((cap + 127) / 128));
     b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(8 * cap);
     const size_t nc = cap / 2 + 1;
@@ -467,6 +473,11 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     V.alpha_f = (float)p->alpha;
     V.alpha_p_f = (float)p->alpha_p;
     V.gscale_f = (float)(-p->rho_s_over_rho_n * p->rho0 * p->kappa);
+    V.nfaces = 0;
+    if (p->wall_images)
+        for (int a = 0; a < 3; ++a)
+            if (p->wall[a])
+                for (int side = 0; side < 2; ++side) V.face_code[V.nfaces++] = 2 * a + side;
 
     const long long C = g.ncell;
     const int cap = p->max_points > 0 ? p->max_points : 1;
@@ -511,7 +522,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.spp = (double*)A(P3);
     d.seglen = (double*)A(sizeof(double) * (size_t)cap);
     d.geo = (float4*)A(sizeof(float4) * 2 * (size_t)cap);
-    d.seg = (float4*)A(sizeof(float4) * 3 * (size_t)cap);
+    d.seg = (float4*)A(sizeof(float4) * 3 * (size_t)cap * (size_t)(1 + V.nfaces));  // segments, then wall images
     d.bsp = (float*)A(sizeof(float) * 3 * (size_t)cap * (size_t)nsm);
     d.vbs = (float*)A(sizeof(float) * 3 * (size_t)cap);
     d.tile_ticket = (int*)A(sizeof(int) * (size_t)((cap + BS_TPB - 1) / BS_TPB));

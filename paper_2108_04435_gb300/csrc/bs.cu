@@ -102,6 +102,7 @@ struct BsTarget {
     float hx, hy, hz, lx, ly, lz;  // position, float hi + lo parts
     float vx, vy, vz;              // accumulated velocity
     int self, prev;                // its own segment and its predecessor's (local term)
+    int excl;                      // a pinned end: the image of its own segment across its wall (local term)
 };
 
 // Sum over the segments of one shared-memory tile for TGT targets per thread.
@@ -139,7 +140,7 @@ __device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, i
             bool use = s > 1e-6f * ab;
             if (MASKED) {
                 const int j = jb + k;
-                use = use & (j != t[u].self) & (j != t[u].prev);
+                use = use & (j != t[u].self) & (j != t[u].prev) & (j != t[u].excl);
             }
             const float c = use ? fac : 0.f;
             t[u].vx += c * (r1y * dz - r1z * dy);
@@ -155,11 +156,17 @@ __device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, i
 // host-side estimate of N.  With several splits, each item stores its partial
 // sums and the last item of a target tile adds them in split order (fixed,
 // hence deterministic) into vel; with one split the item writes vel directly.
+struct BsImages {
+    int nfaces;
+    int face_code[6];
+    const float4* geo;  // pinned-end wall codes (+1) in geo[2i + 1].w
+};
+
 template <bool PERIODIC, int TGT, bool EOM>
 __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev,
                                                         int* __restrict__ counters, int* __restrict__ tile_ticket,
                                                         int cap, BoxF box, float kq, float* __restrict__ part,
-                                                        float* __restrict__ vel, EomArgs ea) {
+                                                        float* __restrict__ vel, EomArgs ea, BsImages im) {
     pdl_wait_trigger();
     __shared__ __align__(128) float4 tile[2][BS_TILE * 3];
     __shared__ __align__(8) uint64_t bar[2];
@@ -170,7 +177,8 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
     const int ns = bs_splits(N, TT);
     const int ntb = (N + TT - 1) / TT;
     const int nitems = ntb * ns;
-    const int chunk = (N + ns - 1) / ns;
+    const int nsrc = N * (1 + im.nfaces);  // segments, then their wall images
+    const int chunk = (nsrc + ns - 1) / ns;
     if ((int)blockIdx.x >= nitems) return;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -183,18 +191,25 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
         __syncthreads();
         const int tb = item % ntb, split = item / ntb;
         const int j0 = split * chunk;
-        const int j1 = min(N, j0 + chunk);
+        const int j1 = min(nsrc, j0 + chunk);
         BsTarget t[TGT];
         bool own_any = false;
 #pragma unroll
         for (int u = 0; u < TGT; ++u) {
             const int i = tb * TT + u * BS_TPB + threadIdx.x;
-            t[u] = BsTarget{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1};
+            t[u] = BsTarget{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1};
             if (i < N) {
                 const float4 a = seg[3LL * i], b = seg[3LL * i + 1];
                 t[u].hx = a.x; t[u].hy = a.y; t[u].hz = a.z; t[u].lx = a.w; t[u].ly = b.x; t[u].lz = b.y;
                 t[u].self = i;
                 t[u].prev = prev[i];
+                if (im.nfaces > 0) {
+                    const int pin = (int)im.geo[2LL * i + 1].w - 1;
+#pragma unroll
+                    for (int f = 0; f < 6; ++f)
+                        if (f < im.nfaces && im.face_code[f] == pin)
+                            t[u].excl = (1 + f) * N + (t[u].prev < 0 ? i : t[u].prev);
+                }
             }
         }
         const int ntiles = j1 > j0 ? (j1 - j0 + BS_TILE - 1) / BS_TILE : 0;
@@ -220,7 +235,8 @@ __global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict
             own_any = false;
 #pragma unroll
             for (int v = 0; v < TGT; ++v)
-                own_any |= (unsigned)(t[v].self - jb) < (unsigned)cnt || (unsigned)(t[v].prev - jb) < (unsigned)cnt;
+                own_any |= (unsigned)(t[v].self - jb) < (unsigned)cnt || (unsigned)(t[v].prev - jb) < (unsigned)cnt ||
+                           (unsigned)(t[v].excl - jb) < (unsigned)cnt;
             if (__any_sync(0xffffffffu, own_any))
                 bs_tile<PERIODIC, true, TGT>(tile[b], cnt, jb, t, box, kq);
             else
@@ -343,7 +359,7 @@ int bs_max_splits(int cap) {
 
 template <int TGT, bool EOM>
 void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int* cnt, int* tile_ticket, int cap, int n,
-               float* part, float* vel, const EomArgs& ea, cudaStream_t s) {
+               float* part, float* vel, const EomArgs& ea, const BsImages& im, cudaStream_t s) {
     // enough blocks for every item of about n points (at most 8 per SM); more
     // points than that are still covered by the blocks' item loop
     constexpr int TT = BS_TPB * TGT;
@@ -352,15 +368,15 @@ void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int*
     const BoxF box = make_box(g);
     if (g.wall[0] && g.wall[1] && g.wall[2])
         launch_pdl(k_biot_savart<false, TGT, EOM>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part,
-                   vel, ea);
+                   vel, ea, im);
     else
         launch_pdl(k_biot_savart<true, TGT, EOM>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part,
-                   vel, ea);
+                   vel, ea, im);
 }
 
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
                         int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
-                        const EomArgs* eom) {
+                        const EomArgs* eom, int nfaces, const int* face_code, const float4* geo) {
     if (cap <= 0) return;
     const int n = n_hint > 0 ? (n_hint < cap ? n_hint : cap) : 1;
     const float kq = (float)(kappa / (4.0 * 3.14159265358979323846));
@@ -369,12 +385,16 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
     // them (each shared-memory record is then read once for both)
     const EomArgs none = {};
     const EomArgs& ea = eom ? *eom : none;
+    BsImages im = {};
+    im.nfaces = geo ? nfaces : 0;
+    for (int f = 0; f < im.nfaces; ++f) im.face_code[f] = face_code[f];
+    im.geo = geo;
     if (n >= 2 * BS_TPB * 152 * 2) {
-        if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, s);
-        else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, s);
+        if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
+        else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
     } else {
-        if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, s);
-        else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, s);
+        if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
+        else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
     }
 }
 

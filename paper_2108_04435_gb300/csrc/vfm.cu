@@ -88,6 +88,29 @@ __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double
     seg[3LL * i] = make_float4(hi[0], hi[1], hi[2], lo[0]);
     seg[3LL * i + 1] = make_float4(lo[1], lo[2], b[0], b[1]);
     seg[3LL * i + 2] = make_float4(b[2], b[0] * b[0] + b[1] * b[1] + b[2] * b[2], 0.f, 0.f);
+    // Image of segment i -> q across each solid face: from M(s_q) to M(s_i),
+    // M mirroring the normal coordinate x_a -> 2w - x_a (record (1 + f) N + i).
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        if (f >= P.nfaces) break;
+        const int code = P.face_code[f], ax = code >> 1;
+        const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
+        const double w2 = 2.0 * ((code & 1) ? L - 0.5 : -0.5);
+        float ihi[3], ilo[3], d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // a line's last point starts no segment: a zero-length record at its own image
+            const double st = q >= 0 ? sq[k] : si[k];
+            const double m = k == ax ? w2 - st : st;
+            ihi[k] = __double2float_rn(m);
+            ilo[k] = __double2float_rn(m - (double)ihi[k]);
+            d[k] = k == ax ? b[k] : -b[k];
+        }
+        const long long r = 3LL * ((long long)(1 + f) * N + i);
+        seg[r] = make_float4(ihi[0], ihi[1], ihi[2], ilo[0]);
+        seg[r + 1] = make_float4(ilo[1], ilo[2], d[0], d[1]);
+        seg[r + 2] = make_float4(d[2], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], 0.f, 0.f);
+    }
 }
 
 // The equation of motion of each point as a kernel of its own (used when the

@@ -169,6 +169,10 @@ struct VfmParams {
     float alpha_f, alpha_p_f;
     float gscale_f;  // -(rho_s/rho_n) rho0 kappa
     int couple, force_form;
+    // wall images (v_s,b): the solid faces, as wall codes 2*axis + side, whose
+    // mirror images of the segments are Biot-Savart sources; 0 faces = v_s,b off
+    int nfaces;
+    int face_code[6];
 };
 
 // Arguments of the equation of motion at one RK4 stage (eom.cuh).
@@ -281,9 +285,14 @@ void launch_line_length(const Grid& g, const double* pos, const int* next, int* 
 int bs_max_splits(int cap);
 // With eom != nullptr the kernel applies the equation of motion to each target
 // tile as soon as its sum is complete, and does not write vel.
+// Sources are the N segments, then with nfaces > 0 their images across each
+// face (records (1 + f) N .. (2 + f) N - 1, written by the stage geometry);
+// geo then gives each pinned end's wall, whose image of its own segment is
+// left out.
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
                         int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
-                        const EomArgs* eom = nullptr);
+                        const EomArgs* eom = nullptr, int nfaces = 0, const int* face_code = nullptr,
+                        const float4* geo = nullptr);
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
                                int* counters, cudaStream_t s);
 

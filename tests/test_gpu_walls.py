@@ -170,3 +170,41 @@ def test_channel_lines_one_step():
     pg, pr = compare_step(g, r, xyz, p["n"], p["wall"])
     if len(pr) == len(x0):
         assert rel_l2(pg - x0, pr - x0) < 1e-5
+
+
+@pytest.mark.parametrize("wall", [(1, 1, 1), (1, 0, 1)], ids=["walls-all", "walls-xz"])
+def test_advance_with_wall_images(wall):
+    """The boundary-induced velocity from wall images (wall_images = 1): the
+    Biot-Savart sources then include the mirror image of every segment across
+    each solid face, and a pinned end skips its own segment's image."""
+    import oracle
+    from paper_2108_04435_gb300 import vlb
+    n = (24, 20, 32)
+    xyz, nxt = wall_tangle(n, wall, 6, jitter=0.05)
+    p = wparams(n, wall, couple=1, wall_images=1, heater_vn=0.01, init_vn=[0.0, 0.0, 0.01])
+    g, r = pair(p, xyz, nxt)
+    p0 = r.read(oracle.FIELD_POS)
+    g.run_phases(vlb.PHASE_LBM | vlb.PHASE_VFM)
+    r.run_phases(oracle.PHASE_LBM | oracle.PHASE_VFM)
+    assert rel_l2(g.read(vlb.FIELD_VEL), r.read(oracle.FIELD_VEL)) < 1e-5
+    assert rel_l2(g.read(vlb.FIELD_POS) - p0, r.read(oracle.FIELD_POS) - p0) < 1e-5
+    assert rel_l2(g.read(vlb.FIELD_FORCE), r.read(oracle.FIELD_FORCE)) < 1e-5
+    # the images change the motion: the same state without them moves differently
+    q = dict(p, wall_images=0)
+    r0 = oracle.Channel(q)
+    r0.seed(xyz, nxt)
+    r0.run_phases(oracle.PHASE_LBM | oracle.PHASE_VFM)
+    assert rel_l2(r0.read(oracle.FIELD_VEL), r.read(oracle.FIELD_VEL)) > 1e-3
+
+
+def test_channel_lines_with_images_steps():
+    """Ten whole steps of the Sec. IV seed with wall images, GPU vs oracle."""
+    import oracle
+    from paper_2108_04435_gb300 import configs, vlb
+    from test_gpu_step import compare_step
+    p, xyz, nxt = configs.config("channel64x64x256_lines")
+    p = dict(p, wall_images=1)
+    g, r = pair(p, xyz, nxt)
+    g.step(10)
+    r.step(10)
+    compare_step(g, r, xyz, p["n"], p["wall"], tol=2e-5, line_tol=1e-7)
