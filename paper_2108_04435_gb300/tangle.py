@@ -1,4 +1,5 @@
-"""The counterflow tangle of Sec. III.C (T-1 regime) in physical units.
+"""The counterflow tangle of Sec. III.C (T-1 regime) in physical units, and
+the closed channel of Sec. IV.
 
 The paper's box is 64 x 32 x 32 cells with L = 2 mm along the counterflow,
 all faces periodic, at T = 1.9 K; the normal velocity V_n (2.0 - 2.5 mm/s)
@@ -104,6 +105,81 @@ def run(vn_mm_s: float, seconds: float, seed: int = 0, sample_s: float = 0.05, u
                 reconnections=int(st[7]), gpu_wall_s=wall, t=t.tolist(), L=L.tolist())
 
 
+SIGMA_19K = 0.757e7  # entropy of He II at 1.9 K in erg/(g K), approximate tabulated value (not printed by the paper)
+
+
+def channel_params(vn_mm_s: float = 2.5, u=None, wall_images: int = 1, max_points: int = 65536):
+    """The closed channel of Sec. IV: the box of Sec. III.C with solid walls at
+    the two ends of the counterflow axis (heater at z = 0, cooled wall at the
+    far end) and periodic side faces; V_n injected by the heater."""
+    u = u or units()
+    vn_lb = 0.1 * vn_mm_s * u["dt_s"] / u["dx_cm"]
+    return configs.base_params(BOX, (0, 0, 1), 1.9, tau=u["tau"], kappa=u["kappa_lb"],
+                               rho_s_over_rho_n=u["rho_s_over_rho_n"], heater_vn=vn_lb,
+                               init_vn=[0.0, 0.0, vn_lb], wall_images=wall_images, max_points=max_points)
+
+
+def channel_seeds(seed: int):
+    """Four lines bound to the two end walls and two smaller rings to kick
+    them (Sec. IV)."""
+    lines = inputs.wall_lines(BOX, 4, seed, amp=0.0)
+    for k in range(1, 64):  # rings redrawn until they pass 2.5 cells clear of the lines
+        rings = inputs.random_rings(BOX, (0, 0, 1), 2, 3.0, 5.0, seed + k)
+        gap = np.sqrt(((rings[0][:, None, :] - lines[0][None, :, :]) ** 2).sum(-1)).min()
+        if gap >= 2.5:
+            break
+    return inputs.concat([lines, rings])
+
+
+def channel_run(vn_mm_s: float = 2.5, seconds: float = 7.2, t_avg: float = 1.0, seed: int = 0,
+                sample_s: float = 0.05, wall_images: int = 1, u=None):
+    """Sec. IV on the GPU: total line length L(t), the line density profile
+    L(z) averaged over t >= t_avg, its linear fit L(z) = L0 (1 - z/z0), and the
+    temperature difference of Eq. 20, dT = (alpha / sigma) kappa L0 V_ns."""
+    from . import vlb
+    u = u or units()
+    p = channel_params(vn_mm_s, u, wall_images)
+    xyz, nxt = channel_seeds(seed)
+    ch = vlb.Channel(p)
+    ch.seed(xyz, nxt)
+    steps = int(round(seconds / u["dt_s"]))
+    every = max(1, int(round(sample_s / u["dt_s"])))
+    nz = BOX[2]
+    plane = BOX[0] * BOX[1] * u["dx_cm"] ** 2  # cm^2 of line per cell of length, per plane
+    t, Ltot, prof, vns = [], [], np.zeros(nz), []
+    nprof, done, error = 0, 0, ""
+    t0 = time.perf_counter()
+    while done < steps:
+        n = min(every, steps - done)
+        try:
+            ch.step(n)
+        except vlb.VlbError as e:
+            error = str(e)
+            break
+        done += n
+        t.append(done * u["dt_s"])
+        Ltot.append(line_density_cm2(ch.line_length(), u))
+        if t[-1] >= t_avg:
+            prof += ch.read(vlb.FIELD_LINE_PROFILE) / plane
+            nprof += 1
+            uz = ch.read(vlb.FIELD_U)[2].mean()
+            vs = ch.read(vlb.FIELD_PLANE_VS).mean()
+            vns.append(abs(uz - vs) * u["dx_cm"] / u["dt_s"])
+    wall = time.perf_counter() - t0
+    st = ch.stats()
+    ch.close()
+    prof = prof / max(nprof, 1)
+    z_mm = (np.arange(nz) + 0.5) * u["dx_cm"] * 10.0  # plane centres from the heater wall at -1/2
+    B, A = np.polyfit(z_mm, prof, 1)
+    V_ns = float(np.mean(vns)) if vns else float("nan")
+    L0, z0 = float(A), float(-A / B) if B != 0 else float("inf")
+    dT_K_per_cm = p["alpha"] / SIGMA_19K * KAPPA_CM2_S * L0 * V_ns
+    return dict(vn_mm_s=vn_mm_s, seconds=seconds, steps=done, error=error, wall_images=wall_images,
+                L_mean_cm2=float(np.mean(prof)), L0_cm2=L0, z0_mm=z0, V_ns_cm_s=V_ns,
+                dT_mK_per_m=dT_K_per_cm * 1e5, points=int(st[0]), wall_cuts=int(st[13]), status=int(st[1]),
+                gpu_wall_s=wall, t=t, L_total=Ltot, z_mm=z_mm.tolist(), L_profile=prof.tolist())
+
+
 def main():
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
@@ -111,7 +187,15 @@ def main():
     ap.add_argument("--seconds", type=float, default=6.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None, help="write the runs (with L(t)) as JSON here")
+    ap.add_argument("--channel", action="store_true", help="the closed channel of Sec. IV instead")
     a = ap.parse_args()
+    if a.channel:
+        r = channel_run(seconds=a.seconds, seed=a.seed)
+        print(json.dumps({k: v for k, v in r.items() if k not in ("t", "L_total", "z_mm", "L_profile")}))
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(r, f)
+        return
     u = units(max(a.vn))
     runs = [run(v, a.seconds, a.seed, u=u) for v in a.vn]
     for r in runs:
