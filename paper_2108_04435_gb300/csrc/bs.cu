@@ -162,8 +162,11 @@ struct BsImages {
     const float4* geo;  // pinned-end wall codes (+1) in geo[2i + 1].w
 };
 
+// At least 8 resident blocks of 128 threads per SM (the grid is sized for 8):
+// the pair loop is issue-bound and needs the warps, and the equation of motion
+// applied after it (EOM) would otherwise raise the count to 72 registers.
 template <bool PERIODIC, int TGT, bool EOM>
-__global__ void __launch_bounds__(BS_TPB) k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev,
+__global__ void __launch_bounds__(BS_TPB, EOM ? 8 : 9) k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev,
                                                         int* __restrict__ counters, int* __restrict__ tile_ticket,
                                                         int cap, BoxF box, float kq, float* __restrict__ part,
                                                         float* __restrict__ vel, EomArgs ea, BsImages im) {
