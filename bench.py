@@ -42,16 +42,15 @@ def l2_note(cells: int, esize: int) -> str:
 
 
 def launches_per_step(n_points: int) -> int:
-    """Kernels of one coupled step (1 RK4 sub-step) in steady state: lattice 2
-    (stream-collide, which also resets the force grid it consumes; plane
-    reduction), filaments 4 x 3 (per RK stage geometry, Biot-Savart, equation
-    of motion), remesh 2, reconnection 4 (its compaction also flags the next
-    pass's velocity tiles).  The Biot-Savart kernel applies the equation of
-    motion itself from 8192 points on (or as VLB_FUSED_EOM forces), 4 launches
-    fewer."""
+    """Kernels of one coupled step (1 RK4 sub-step) in steady state: lattice 3
+    (velocity-tile flags, stream-collide, plane reduction with the force-grid
+    reset), filaments 4 x 3 (per RK stage geometry, Biot-Savart, equation of
+    motion), remesh 2, reconnection 4.  The Biot-Savart kernel applies the
+    equation of motion itself from 8192 points on (or as VLB_FUSED_EOM
+    forces), 4 launches fewer."""
     mode = os.environ.get("VLB_FUSED_EOM")
     fused = n_points >= 8192 if mode is None else mode != "0"
-    return 16 if fused else 20
+    return 17 if fused else 21
 
 
 def dist_env():

@@ -39,9 +39,8 @@ struct vlb_channel {
     VfmParams vp;
     int cur_f = 0;     // population buffer holding the current state
     int cur_p = 0;     // point buffer holding the current filaments
-    // Host record of the device state that lets a full step skip two launches:
-    bool f_clean = true;       // force grid zero everywhere (each lattice pass consumes it)
-    bool umask_fresh = false;  // velocity-tile flags match the current points (set by reconnection)
+    // Host record of the device state that lets a full step skip the force reset:
+    bool f_clean = true;  // force grid zero everywhere (each lattice pass consumes it)
     int cap = 0;
     int hsize = 0;
     int bpp = 0;
@@ -136,17 +135,10 @@ void record_event(vlb_channel* ch) {
     cudaEventRecord(ch->ev[ch->ev_used++], ch->stream);
 }
 
-// Flag the velocity tiles of the current points unless the last reconnection
-// pass already did.  Flags left over from older points only cost extra writes.
-void mark_points(vlb_channel* ch) {
-    if (ch->umask_fresh) return;
-    launch_mark_umask(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.counters, ch->cap, ch->d.umask, ch->stream);
-    ch->umask_fresh = true;
-}
-
 void phase_lbm(vlb_channel* ch) {
     Dev& d = ch->d;
-    mark_points(ch);
+    // flag the velocity tiles around the current points (the previous plane reduction cleared them)
+    launch_mark_umask(ch->lp.g, d.pos[ch->cur_p], d.counters, ch->cap, d.umask, ch->stream);
     if (ch->timing) record_event(ch);
     launch_lbm_step(ch->lp, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
     if (ch->timing) record_event(ch);
@@ -154,7 +146,6 @@ void phase_lbm(vlb_channel* ch) {
     // the pass consumed the force grid: the plane reduction resets it and clears both tile flags
     launch_plane_vs(ch->lp, d.part, d.F, d.umask, d.fmask, ch->stream);
     ch->f_clean = true;
-    ch->umask_fresh = false;
 }
 
 // Whether the Biot-Savart kernel applies the equation of motion itself.  It
@@ -216,19 +207,14 @@ void phase_vfm(vlb_channel* ch) {
 
 void run_phases_body(vlb_channel* ch, int mask) {
     if (mask & VLB_PHASE_LBM) phase_lbm(ch);
-    if (mask & VLB_PHASE_VFM) {
-        phase_vfm(ch);
-        ch->umask_fresh = false;
-    }
+    if (mask & VLB_PHASE_VFM) phase_vfm(ch);
     if (mask & VLB_PHASE_REMESH) {
         launch_remesh(ch->vp, ch->d, ch->cur_p, ch->cap, ch->stream);
         ch->cur_p ^= 1;
-        ch->umask_fresh = false;
     }
     if (mask & VLB_PHASE_RECONNECT) {
-        launch_reconnect(ch->vp, ch->d, ch->cur_p, ch->cap, ch->hsize, ch->stream);  // flags the new points' tiles
+        launch_reconnect(ch->vp, ch->d, ch->cur_p, ch->cap, ch->hsize, ch->stream);
         ch->cur_p ^= 1;
-        ch->umask_fresh = true;
     }
 }
 
@@ -656,7 +642,6 @@ int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, i
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "seed copy");
     ch->n_hint = n;
-    ch->umask_fresh = false;
     return VLB_OK;
 }
 
@@ -684,13 +669,11 @@ bool step_graph(vlb_channel* ch, bool multi) {
     const int f = ch->cur_f, q = ch->cur_p;
     const int cls = size_class(ch->n_hint);
     cudaGraphExec_t& ge = ch->gexec[m][f][q];
-    mark_points(ch);  // the captured steps start from flagged velocity tiles
-    const bool f_clean0 = ch->f_clean, umask_fresh0 = ch->umask_fresh;
+    const bool f_clean0 = ch->f_clean;
     auto undo = [&] {  // nothing ran: back to the state before the attempt
         ch->cur_f = f;
         ch->cur_p = q;
         ch->f_clean = f_clean0;
-        ch->umask_fresh = umask_fresh0;
         return false;
     };
     if (ge && ch->gclass[m][f][q] != cls) {
@@ -726,7 +709,6 @@ bool step_graph(vlb_channel* ch, bool multi) {
     if (cudaGraphLaunch(ge, ch->stream) != cudaSuccess) return undo();
     if (nst & 1) ch->cur_f ^= 1;  // the point buffers are back to q after remesh and reconnect
     ch->f_clean = !ch->p.couple;  // state after full steps: the last one spread its reaction
-    ch->umask_fresh = true;       // and flagged its points' velocity tiles
     return true;
 }
 

@@ -234,12 +234,11 @@ __device__ int block_small_components(const int* __restrict__ succ, uint8_t* __r
 }
 
 // One block: stable compaction of the alive points of [0, T) into the other
-// point buffer, successor indices renumbered, predecessors rebuilt; with umask
-// set, the velocity tiles of the next lattice pass are flagged at the same time.
+// point buffer, successor indices renumbered, predecessors rebuilt.
 __device__ void block_compact(const double* __restrict__ pin, const int* __restrict__ succ,
                               const uint8_t* __restrict__ alive, int T, int* __restrict__ newidx,
                               double* __restrict__ pout, int* __restrict__ nout, int* __restrict__ pvout,
-                              int* __restrict__ counters, int cap, const Grid& g, uint8_t* __restrict__ umask) {
+                              int* __restrict__ counters, int cap) {
     const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
     const int b0 = min(T, (int)threadIdx.x * per);
     const int b1 = min(T, b0 + per);
@@ -256,7 +255,6 @@ __device__ void block_compact(const double* __restrict__ pin, const int* __restr
         if (!alive[k]) continue;
         const int n = newidx[k];
         for (int c = 0; c < 3; ++c) pout[(long long)c * cap + n] = pin[(long long)c * cap + k];
-        if (umask) mark_velocity_tiles(g, pin[k], pin[(long long)cap + k], pin[2LL * cap + k], umask);
         const int sk = succ[k];
         if (sk < 0) {  // last point of an open line
             nout[n] = -1;
@@ -370,7 +368,7 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
         dstats[DS_SMALL] += (double)dead_all;
     }
     __syncthreads();
-    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap, P.g, nullptr);
+    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap);
 }
 
 // -------------------------------------------------------------- reconnect
@@ -509,8 +507,7 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     const int* __restrict__ cand_a, const int* __restrict__ cand_b, const double* __restrict__ cand_d2,
     int* __restrict__ order, int* __restrict__ stamp, const int* __restrict__ hkey, int* __restrict__ hhead,
     uint8_t* __restrict__ alive, int* __restrict__ newidx, double* __restrict__ pout, int* __restrict__ nout,
-    int* __restrict__ pvout, int* __restrict__ counters, double* __restrict__ dstats, int cap,
-    uint8_t* __restrict__ umask) {
+    int* __restrict__ pvout, int* __restrict__ counters, double* __restrict__ dstats, int cap) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int K = counters[CNT_NPAIRS];
@@ -588,7 +585,7 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) dstats[DS_SMALL] += (double)dead_all;
     __syncthreads();
-    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, P.g, umask);
+    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap);
 }
 
 }  // namespace
@@ -617,7 +614,7 @@ void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, c
     launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.hlink, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
                                           d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
-                                          cap, d.umask);
+                                          cap);
 }
 
 }  // namespace vlb
