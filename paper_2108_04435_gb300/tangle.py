@@ -108,13 +108,14 @@ def run(vn_mm_s: float, seconds: float, seed: int = 0, sample_s: float = 0.05, u
 SIGMA_19K = 0.757e7  # entropy of He II at 1.9 K in erg/(g K), approximate tabulated value (not printed by the paper)
 
 
-def channel_params(vn_mm_s: float = 2.5, u=None, wall_images: int = 1, max_points: int = 65536):
+def channel_params(vn_mm_s: float = 2.5, u=None, wall_images: int = 1, max_points: int = 65536, tau=None):
     """The closed channel of Sec. IV: the box of Sec. III.C with solid walls at
     the two ends of the counterflow axis (heater at z = 0, cooled wall at the
-    far end) and periodic side faces; V_n injected by the heater."""
+    far end) and periodic side faces; V_n injected by the heater.  tau, when
+    given, replaces the viscosity-matched value (a more viscous normal fluid)."""
     u = u or units()
     vn_lb = 0.1 * vn_mm_s * u["dt_s"] / u["dx_cm"]
-    return configs.base_params(BOX, (0, 0, 1), 1.9, tau=u["tau"], kappa=u["kappa_lb"],
+    return configs.base_params(BOX, (0, 0, 1), 1.9, tau=tau if tau else u["tau"], kappa=u["kappa_lb"],
                                rho_s_over_rho_n=u["rho_s_over_rho_n"], heater_vn=vn_lb,
                                init_vn=[0.0, 0.0, vn_lb], wall_images=wall_images, max_points=max_points)
 
@@ -132,13 +133,13 @@ def channel_seeds(seed: int):
 
 
 def channel_run(vn_mm_s: float = 2.5, seconds: float = 7.2, t_avg: float = 1.0, seed: int = 0,
-                sample_s: float = 0.05, wall_images: int = 1, u=None):
+                sample_s: float = 0.05, wall_images: int = 1, u=None, tau=None):
     """Sec. IV on the GPU: total line length L(t), the line density profile
     L(z) averaged over t >= t_avg, its linear fit L(z) = L0 (1 - z/z0), and the
     temperature difference of Eq. 20, dT = (alpha / sigma) kappa L0 V_ns."""
     from . import vlb
     u = u or units()
-    p = channel_params(vn_mm_s, u, wall_images)
+    p = channel_params(vn_mm_s, u, wall_images, tau=tau)
     xyz, nxt = channel_seeds(seed)
     ch = vlb.Channel(p)
     ch.seed(xyz, nxt)
@@ -174,7 +175,7 @@ def channel_run(vn_mm_s: float = 2.5, seconds: float = 7.2, t_avg: float = 1.0, 
     V_ns = float(np.mean(vns)) if vns else float("nan")
     L0, z0 = float(A), float(-A / B) if B != 0 else float("inf")
     dT_K_per_cm = p["alpha"] / SIGMA_19K * KAPPA_CM2_S * L0 * V_ns
-    return dict(vn_mm_s=vn_mm_s, seconds=seconds, steps=done, error=error, wall_images=wall_images,
+    return dict(vn_mm_s=vn_mm_s, seconds=seconds, steps=done, error=error, wall_images=wall_images, tau=p["tau"],
                 L_mean_cm2=float(np.mean(prof)), L0_cm2=L0, z0_mm=z0, V_ns_cm_s=V_ns,
                 dT_mK_per_m=dT_K_per_cm * 1e5, points=int(st[0]), wall_cuts=int(st[13]), status=int(st[1]),
                 gpu_wall_s=wall, t=t, L_total=Ltot, z_mm=z_mm.tolist(), L_profile=prof.tolist())
@@ -188,11 +189,14 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None, help="write the runs (with L(t)) as JSON here")
     ap.add_argument("--channel", action="store_true", help="the closed channel of Sec. IV instead")
-    ap.add_argument("--u-max", type=float, default=0.012, help="lattice velocity of 2.5 mm/s in the channel run")
+    ap.add_argument("--u-max", type=float, default=0.02, help="lattice velocity of 2.5 mm/s in the channel run")
+    ap.add_argument("--tau", type=float, default=None,
+                    help="channel run: BGK relaxation time instead of the viscosity-matched 0.516, which "
+                         "goes unstable at the outflow wall once the tangle perturbs the flow")
     a = ap.parse_args()
     if a.channel:
         # the closed channel concentrates the flow around the dense tangle: more Mach headroom
-        r = channel_run(seconds=a.seconds, seed=a.seed, u=units(2.5, u_max=a.u_max))
+        r = channel_run(seconds=a.seconds, seed=a.seed, u=units(2.5, u_max=a.u_max), tau=a.tau)
         print(json.dumps({k: v for k, v in r.items() if k not in ("t", "L_total", "z_mm", "L_profile")}))
         if a.out:
             with open(a.out, "w") as f:
