@@ -16,14 +16,8 @@ namespace vlb {
 namespace {
 
 
-// Stage geometry for the equation of motion: the same quantities as
-// k_geometry, with the neighbour differences formed in FP64 (positions are up
-// to ~1e3 cells) and everything after them in FP32, which is accurate to
-// ~1e-7 relative for segments of O(1) cells.  The remeshing decisions use the
-// FP64 k_geometry instead.  An open end pinned on a wall takes the mirror image
-// of its neighbour across that wall as its missing neighbour, represents half
-// of its segment, and carries its wall code (+1) to the equation of motion; a
-// line's last point has a zero-length source record.
+// One thread per point; thread 0 also resets the work counter of the
+// Biot-Savart launch that follows.
 __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double* __restrict__ s,
                                                        const int* __restrict__ next, const int* __restrict__ prev,
                                                        int* __restrict__ counters, int cap,
@@ -34,83 +28,7 @@ __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch that follows takes items from 0
     if (i >= N) return;
-    const int p = prev[i], q = next[i];
-    const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
-    double si[3], sp[3], sq[3];
-    float a[3], b[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        si[k] = s[(long long)k * cap + i];
-        sp[k] = s[(long long)k * cap + pl];
-        sq[k] = s[(long long)k * cap + ql];
-    }
-    int code = -1;
-    if (p < 0 || q < 0) {
-        code = touching_wall(P.g, P.dmin, si);
-        const int ax = code >> 1;
-        const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
-        const double w2 = 2.0 * ((code & 1) ? L - 0.5 : -0.5);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const double nb = p < 0 ? sq[k] : sp[k];
-            // mirror image across the wall; an end on no wall is continued straight
-            const double g = code < 0 ? 2.0 * si[k] - nb : (k == ax ? w2 - nb : nb);
-            if (p < 0) sp[k] = g;
-            else sq[k] = g;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
-        a[k] = (float)min_image(P.g, k, si[k] - sp[k]);
-        b[k] = (float)min_image(P.g, k, sq[k] - si[k]);
-    }
-    const float lm = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-    const float lp = sqrtf(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-    const float inv = 1.f / (lp * lm * (lp + lm));
-    float t1[3], t2[3];
-    for (int k = 0; k < 3; ++k) {
-        t1[k] = (lm * lm * b[k] + lp * lp * a[k]) * inv;
-        t2[k] = 2.f * (lm * b[k] - lp * a[k]) * inv;
-    }
-    const float beta = P.kq_f * logf(2.f * sqrtf(lp * lm) * P.inv_ea_f);
-    // geo[2i] = (s'.xyz, dxi), geo[2i+1] = (local velocity beta s' x s'', wall code + 1 of a pinned end)
-    const float dxi = p < 0 ? 0.5f * lp : (q < 0 ? 0.5f * lm : 0.5f * (lp + lm));
-    geo[2LL * i] = make_float4(t1[0], t1[1], t1[2], dxi);
-    geo[2LL * i + 1] = make_float4(beta * (t1[1] * t2[2] - t1[2] * t2[1]), beta * (t1[2] * t2[0] - t1[0] * t2[2]),
-                                   beta * (t1[0] * t2[1] - t1[1] * t2[0]), (float)(code + 1));
-    if (q < 0) b[0] = b[1] = b[2] = 0.f;  // no segment leaves a line's last point
-    float hi[3], lo[3];
-    for (int k = 0; k < 3; ++k) {
-        hi[k] = __double2float_rn(si[k]);
-        lo[k] = __double2float_rn(si[k] - (double)hi[k]);
-    }
-    seg[3LL * i] = make_float4(hi[0], hi[1], hi[2], lo[0]);
-    seg[3LL * i + 1] = make_float4(lo[1], lo[2], b[0], b[1]);
-    seg[3LL * i + 2] = make_float4(b[2], b[0] * b[0] + b[1] * b[1] + b[2] * b[2], 0.f, 0.f);
-    // Image of segment i -> q across each solid face: from M(s_q) to M(s_i),
-    // M mirroring the normal coordinate x_a -> 2w - x_a (record (1 + f) N + i).
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        if (f >= P.nfaces) break;
-        const int code = P.face_code[f], ax = code >> 1;
-        const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
-        const double w2 = 2.0 * ((code & 1) ? L - 0.5 : -0.5);
-        float ihi[3], ilo[3], d[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            // a line's last point starts no segment: a zero-length record at its own image
-            const double st = q >= 0 ? sq[k] : si[k];
-            const double m = k == ax ? w2 - st : st;
-            ihi[k] = __double2float_rn(m);
-            ilo[k] = __double2float_rn(m - (double)ihi[k]);
-            d[k] = k == ax ? b[k] : -b[k];
-        }
-        const long long r = 3LL * ((long long)(1 + f) * N + i);
-        seg[r] = make_float4(ihi[0], ihi[1], ihi[2], ilo[0]);
-        seg[r + 1] = make_float4(ilo[1], ilo[2], d[0], d[1]);
-        seg[r + 2] = make_float4(d[2], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], 0.f, 0.f);
-    }
+    geometry_point(P, s, next, prev, N, cap, i, geo, seg, s0_copy);
 }
 
 // The equation of motion of each point as a kernel of its own (used when the
