@@ -46,10 +46,6 @@ struct vlb_channel {
     int bpp = 0;
     int nsplit_max = 1;
     int n_hint = 0;
-    // persistent filament kernel (one cooperative launch per RK4 sub-step) for small point sets
-    int coop_blocks = 0;             // its grid (2 blocks per SM), 0 = not available
-    bool coop_used = false;          // the last captured steps used it
-    bool coop_graph_failed = false;  // a capture containing it failed: graphs use separate launches
     long long steps = 0;
     std::vector<void*> blocks;
     size_t bytes = 0;  // device bytes allocated at create
@@ -152,21 +148,6 @@ void phase_lbm(vlb_channel* ch) {
     ch->f_clean = true;
 }
 
-thread_local bool tl_capture = false;  // a step graph is being captured on this thread
-
-// The persistent filament kernel replaces the 12 launches of a sub-step up to
-// this many points; beyond it the Biot-Savart pass needs the whole GPU.
-// VLB_COOP=0 in the environment turns it off.
-constexpr int COOP_MAX_POINTS = 4096;
-
-bool coop_enabled() {
-    static const bool on = [] {
-        const char* v = getenv("VLB_COOP");
-        return !(v && v[0] == '0');
-    }();
-    return on;
-}
-
 // Whether the Biot-Savart kernel applies the equation of motion itself.  It
 // pays once there are many points (measured: 1.8% faster per step at 17k
 // points, 3% slower at 1.1k, where the separate kernel overlaps better), so by
@@ -201,21 +182,10 @@ void phase_vfm(vlb_channel* ch) {
     ea.F = d.F;
     ea.fmask = d.fmask;
     ea.counters = d.counters;
-    const bool coop = ch->coop_blocks > 0 && ch->n_hint <= COOP_MAX_POINTS && !(tl_capture && ch->coop_graph_failed);
     for (int sub = 0; sub < nsub; ++sub) {
         const int spread = (sub == 0 && ch->p.couple) ? 1 : 0;
         if (spread && !ch->f_clean) launch_zero_force(ch->lp.g, d.F, d.fmask, ch->stream);
         if (spread) ch->f_clean = false;
-        if (coop) {
-            ea.spread = spread;
-            const cudaError_t e = launch_vfm_coop(ea, pos, next, prev, d.seg, d.tile_ticket, d.bsp, d.vbs,
-                                                  ch->coop_blocks, ch->stream);
-            if (e == cudaSuccess) {
-                ch->coop_used = true;
-                continue;
-            }
-            cudaGetLastError();  // not launched: separate kernels for this sub-step
-        }
         for (int stage = 0; stage < 4; ++stage) {
             const double* xs = stage == 0 ? pos : d.st;
             ea.stage = stage;
@@ -504,15 +474,6 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     ch->bpp = lbm_blocks_per_plane(L);
     const int nsm = bs_max_splits(cap);
     ch->nsplit_max = nsm;
-    if (coop_enabled()) {  // two co-resident blocks per SM for the persistent filament kernel
-        int dev = 0, nsm_dev = 0, coop_ok = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm_dev, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev);
-        const bool periodic = !(g.wall[0] && g.wall[1] && g.wall[2]);
-        if (coop_ok && nsm_dev > 0 && vfm_coop_max_blocks_per_sm(periodic) >= 2) ch->coop_blocks = 2 * nsm_dev;
-        cudaGetLastError();
-    }
     const int ntiles = g.tnx * g.tny * g.tnz;
     Dev& d = ch->d;
     bool ok = true;
@@ -727,17 +688,13 @@ bool step_graph(vlb_channel* ch, bool multi) {
             return undo();
         }
         tl_no_pdl = true;
-        tl_capture = true;
-        ch->coop_used = false;
         for (int k = 0; k < nst; ++k) run_phases(ch, VLB_PHASE_ALL);
-        tl_capture = false;
         tl_no_pdl = false;
         cudaError_t e = cudaStreamEndCapture(ch->stream, &graph);
         ch->cur_f = f;  // the captured steps have not run yet
         ch->cur_p = q;
         if (e != cudaSuccess || !graph) {
             cudaGetLastError();
-            if (ch->coop_used) ch->coop_graph_failed = true;  // capture again without the cooperative launch
             return undo();
         }
         e = cudaGraphInstantiate(&ge, graph, 0);
@@ -745,7 +702,6 @@ bool step_graph(vlb_channel* ch, bool multi) {
         if (e != cudaSuccess) {
             cudaGetLastError();
             ge = nullptr;
-            if (ch->coop_used) ch->coop_graph_failed = true;
             return undo();
         }
         ch->gclass[m][f][q] = cls;

@@ -335,86 +335,6 @@ __global__ void __launch_bounds__(BS_TPB, EOM ? 8 : 9)
     bs_work<PERIODIC, TGT, EOM>(seg, prev, counters, tile_ticket, cap, box, kq, part, vel, ea, im, sm, used);
 }
 
-// Grid-wide barrier of the persistent filament kernel (all its blocks are
-// co-resident: cooperative launch).  One arrival per block on CNT_GBAR; the
-// last one resets it and advances CNT_GGEN, which the others poll.  The wait
-// gives up after ~1 s of clock (status TIMEOUT) and the kernel then returns.
-__device__ __forceinline__ bool grid_barrier(int* __restrict__ counters) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile int* gen = &counters[CNT_GGEN];
-        const int g0 = *gen;  // read before arriving: only the last arrival can advance it
-        __threadfence();
-        int ok = 1;
-        if (atomicAdd(&counters[CNT_GBAR], 1) == (int)gridDim.x - 1) {
-            atomicExch(&counters[CNT_GBAR], 0);
-            __threadfence();
-            atomicAdd(&counters[CNT_GGEN], 1);
-        } else {
-            const long long t0 = clock64();
-            while (*gen == g0) {
-                if (clock64() - t0 > 2000000000LL) {
-                    atomicOr(&counters[CNT_STATUS], ST_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// One RK4 sub-step of the filaments in one launch: for each stage the stage
-// geometry (grid-stride over points), the Biot-Savart pass (the same work
-// items as k_biot_savart) and the equation of motion, separated by grid
-// barriers.  ea.stage is set here.
-template <bool PERIODIC>
-__global__ void __launch_bounds__(BS_TPB)
-    k_vfm_coop(EomArgs ea, BsImages im, const double* __restrict__ pos, const int* __restrict__ next,
-               const int* __restrict__ prev, float4* __restrict__ seg, int* __restrict__ tile_ticket, BoxF box,
-               float kq, float* __restrict__ part, float* __restrict__ vbs) {
-    // wait for a programmatic predecessor, but let no successor in early: its
-    // blocks would sit on the SMs for the whole sub-step
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    __shared__ __align__(128) float4 tile[2][BS_TILE * 3];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_item, s_last;
-    const BsSmem sm = {tile, bar, &s_item, &s_last};
-    bs_smem_init(sm);
-    uint32_t used = 0;
-    int* counters = ea.counters;
-    const int N = counters[CNT_N];
-    const int cap = ea.cap;
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsize = gridDim.x * blockDim.x;
-    for (int stage = 0; stage < 4; ++stage) {
-        const double* xs = stage == 0 ? pos : ea.st;
-        for (int i = gtid; i < N; i += gsize)
-            geometry_point(ea.P, xs, next, prev, N, cap, i, const_cast<float4*>(ea.geo), seg,
-                           stage == 0 ? const_cast<double*>(ea.s0) : nullptr);
-        if (gtid == 0) counters[CNT_BSWORK] = 0;
-        if (!grid_barrier(counters)) return;
-        bs_work<PERIODIC, 1, false>(seg, prev, counters, tile_ticket, cap, box, kq, part, vbs, ea, im, sm, used);
-        if (!grid_barrier(counters)) return;
-        EomArgs es = ea;
-        es.stage = stage;
-        // whole warps take points together (the spreading aggregates over a warp)
-        for (int base = gtid & ~31; base < N; base += gsize) {
-            const int i = base + (threadIdx.x & 31);
-            const bool valid = i < N;
-            float v[3] = {0.f, 0.f, 0.f};
-            if (valid)
-                for (int k = 0; k < 3; ++k) v[k] = vbs[(long long)k * cap + i];
-            eom_point(es, i, valid, v[0], v[1], v[2]);
-        }
-        if (stage < 3 && !grid_barrier(counters)) return;
-    }
-}
-
 // Stand-alone entry: prev[] and the source records from a caller's point set.
 __global__ void k_bs_prep(Grid g, const double* __restrict__ pos, const int* __restrict__ next, int n,
                           int* __restrict__ prev, float4* __restrict__ seg, int* __restrict__ counters) {
@@ -511,37 +431,6 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
         if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
         else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
     }
-}
-
-cudaError_t launch_vfm_coop(const EomArgs& ea, const double* pos, const int* next, const int* prev, float4* seg,
-                            int* tile_ticket, float* part, float* vbs, int blocks, cudaStream_t s) {
-    const Grid& g = ea.P.g;
-    BsImages im = {};
-    im.nfaces = ea.P.nfaces;
-    for (int f = 0; f < im.nfaces; ++f) im.face_code[f] = ea.P.face_code[f];
-    im.geo = ea.geo;
-    const BoxF box = make_box(g);
-    const float kq = (float)(ea.P.kappa / (4.0 * 3.14159265358979323846));
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)blocks);
-    cfg.blockDim = dim3(BS_TPB);
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (g.wall[0] && g.wall[1] && g.wall[2])
-        return cudaLaunchKernelEx(&cfg, k_vfm_coop<false>, ea, im, pos, next, prev, seg, tile_ticket, box, kq, part,
-                                  vbs);
-    return cudaLaunchKernelEx(&cfg, k_vfm_coop<true>, ea, im, pos, next, prev, seg, tile_ticket, box, kq, part, vbs);
-}
-
-int vfm_coop_max_blocks_per_sm(bool periodic) {
-    int nb = 0;
-    if (periodic) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vfm_coop<true>, BS_TPB, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_vfm_coop<false>, BS_TPB, 0);
-    return nb;
 }
 
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,

@@ -31,8 +31,6 @@ enum : int {
     CNT_PLANES = 7,     // z planes reduced in the current lattice pass
     CNT_LINEDONE = 8,   // blocks done in the line-length reduction
     CNT_NCONTACT = 9,   // wall-contact candidates of the current reconnection pass
-    CNT_GBAR = 10,      // blocks arrived at the persistent filament kernel's current grid barrier
-    CNT_GGEN = 11,      // grid barriers completed (generation)
     CNT_COUNT = 12
 };
 
@@ -285,15 +283,6 @@ void launch_line_length(const Grid& g, const double* pos, const int* next, int* 
 
 // bs.cu
 int bs_max_splits(int cap);
-// One RK4 sub-step of the filaments (four stages of stage geometry,
-// Biot-Savart and equation of motion) as a single cooperative launch of
-// `blocks` blocks, stages separated by grid barriers; for small point sets,
-// where separate launches are latency-bound.  The force grid must be clean
-// when ea.spread is set.  Returns the launch status.
-cudaError_t launch_vfm_coop(const EomArgs& ea, const double* pos, const int* next, const int* prev, float4* seg,
-                            int* tile_ticket, float* part, float* vbs, int blocks, cudaStream_t s);
-int vfm_coop_max_blocks_per_sm(bool periodic);
-
 // With eom != nullptr the kernel applies the equation of motion to each target
 // tile as soon as its sum is complete, and does not write vel.
 // Sources are the N segments, then with nfaces > 0 their images across each
