@@ -84,11 +84,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// Nearest integer of |x| < 2^22 on the FMA pipe: adding and removing
-// 1.5 * 2^23 rounds to nearest even in FP32.
-__device__ __forceinline__ float round_fma(float x) {
+// Nearest integer of x * inv (|x * inv| < 2^22) on the FMA pipe, in two
+// instructions: adding 1.5 * 2^23 to the exact product rounds it to the
+// nearest integer in FP32, and removing it again is exact.
+__device__ __forceinline__ float round_mul_fma(float x, float inv) {
     const float M = 12582912.0f;
-    return __fsub_rn(__fadd_rn(x, M), M);
+    return __fsub_rn(__fmaf_rn(x, inv, M), M);
 }
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
@@ -123,9 +124,9 @@ __device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, i
             float r1y = (A.y - t[u].hy) + (B.x - t[u].ly);
             float r1z = (A.z - t[u].hz) + (B.y - t[u].lz);
             if (PERIODIC) {
-                r1x -= box.Lx * round_fma(r1x * box.iLx);
-                r1y -= box.Ly * round_fma(r1y * box.iLy);
-                r1z -= box.Lz * round_fma(r1z * box.iLz);
+                r1x = fmaf(-box.Lx, round_mul_fma(r1x, box.iLx), r1x);
+                r1y = fmaf(-box.Ly, round_mul_fma(r1y, box.iLy), r1y);
+                r1z = fmaf(-box.Lz, round_mul_fma(r1z, box.iLz), r1z);
             }
             const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
             const float rd = r1x * dx + r1y * dy + r1z * dz;
@@ -416,15 +417,15 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
     const int n = n_hint > 0 ? (n_hint < cap ? n_hint : cap) : 1;
     const float kq = (float)(kappa / (4.0 * 3.14159265358979323846));
     int* cnt = const_cast<int*>(counters);
-    // two targets per thread once there are enough points to fill the GPU with
-    // them (each shared-memory record is then read once for both)
+    // two targets per thread from 8192 points on (each shared-memory record is
+    // then read once for both; 1% faster at 17k points, the same at 86k)
     const EomArgs none = {};
     const EomArgs& ea = eom ? *eom : none;
     BsImages im = {};
     im.nfaces = geo ? nfaces : 0;
     for (int f = 0; f < im.nfaces; ++f) im.face_code[f] = face_code[f];
     im.geo = geo;
-    if (n >= 2 * BS_TPB * 152 * 2) {
+    if (n >= 8192) {
         if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
         else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
     } else {
