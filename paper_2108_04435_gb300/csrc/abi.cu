@@ -406,7 +406,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
             const int b = atoi(e);
             if (b == 128 || b == 256) blk = b;
         }
-        L.vec = vec;
+        L.vec = p->storage == VLB_STORE_F32 ? vec : 1;
         // exact division by nx through a multiply-high (Granlund-Montgomery),
         // checked here for every in-plane index the kernel can form
         {

@@ -10,8 +10,6 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
-
-#include <type_traits>
 #include <math.h>
 
 #include "vlb_internal.cuh"
@@ -430,38 +428,8 @@ __device__ __forceinline__ void vstore(float* p, const float (&v)[VEC]) {
     *reinterpret_cast<typename VecT<VEC>::T*>(p) = t;
 }
 
-// VEC consecutive stored populations as one 2VEC- or 4VEC-byte access,
-// converted to / from FP32 (the 16-bit formats pack two values per word).
-template <int VEC, int S>
-__device__ __forceinline__ void pload(const typename Pop<S>::T* __restrict__ p, float (&v)[VEC]) {
-    if (S == STORE_F32) {
-        vload<VEC>(reinterpret_cast<const float*>(p), v);
-    } else {
-        using W = typename std::conditional<VEC == 2, unsigned, uint2>::type;
-        const W w = __ldg(reinterpret_cast<const W*>(p));
-        const typename Pop<S>::T* h = reinterpret_cast<const typename Pop<S>::T*>(&w);
-#pragma unroll
-        for (int c = 0; c < VEC; ++c) v[c] = Pop<S>::raw(h[c]);
-    }
-}
-
-template <int VEC, int S>
-__device__ __forceinline__ void pstore(typename Pop<S>::T* p, const float (&v)[VEC]) {
-    if (S == STORE_F32) {
-        vstore<VEC>(reinterpret_cast<float*>(p), v);
-    } else {
-        using W = typename std::conditional<VEC == 2, unsigned, uint2>::type;
-        W w;
-        typename Pop<S>::T* h = reinterpret_cast<typename Pop<S>::T*>(&w);
-#pragma unroll
-        for (int c = 0; c < VEC; ++c) h[c] = Pop<S>::cv(v[c]);
-        *reinterpret_cast<W*>(p) = w;
-    }
-}
-
-template <bool WX, bool WY, bool WZ, int VEC, int S>
-__global__ void __launch_bounds__(128) k_lbm_step_vec(const typename Pop<S>::T* __restrict__ fin,
-                                                      typename Pop<S>::T* __restrict__ fout,
+template <bool WX, bool WY, bool WZ, int VEC>
+__global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ fin, float* __restrict__ fout,
                                                       const long long* __restrict__ F, float* __restrict__ U,
                                                       const uint8_t* __restrict__ fmask,
                                                       const uint8_t* __restrict__ umask, double* __restrict__ part,
@@ -500,7 +468,7 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const typename Pop<S>::T* 
         const int row = i * C + zo[CZ(i) + 1] + yo[CY(i) + 1];
         const bool rowout = (WY && oy[CY(i) + 1]) || (WZ && oz[CZ(i) + 1]);
         if (live) {
-            pload<VEC, S>(rowout ? fin + opp(i) * C + cell0 : fin + row + x0, g[i]);
+            vload<VEC>(rowout ? fin + opp(i) * C + cell0 : fin + row + x0, g[i]);
         } else {
 #pragma unroll
             for (int c = 0; c < VEC; ++c) g[i][c] = 0.f;
@@ -509,11 +477,11 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const typename Pop<S>::T* 
         if (CX(i) == 1) {
             const bool need = live && !rowout && (lane == 0 || row_first);
             const int a = !row_first ? row + x0 - 1 : (WX ? opp(i) * C + cell0 : row + nx - 1);
-            if (need) edge[i] = Pop<S>::ld(&fin[a]);
+            if (need) edge[i] = __ldg(&fin[a]);
         } else if (CX(i) == -1) {
             const bool need = live && !rowout && (lane == 31 || row_last);
             const int a = !row_last ? row + x0 + VEC : (WX ? opp(i) * C + cell0 + VEC - 1 : row);
-            if (need) edge[i] = Pop<S>::ld(&fin[a]);
+            if (need) edge[i] = __ldg(&fin[a]);
         }
     }
     // Phase 2: moving-wall terms, then the +-x shifts through the neighbouring lanes.
@@ -613,7 +581,7 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const typename Pop<S>::T* 
             if (pinned) out = wgt(0) * (drho[c] - 1.5f * (P.rho0 + drho[c]) * P.pin * P.pin) + P.dw[0];
             g[0][c] = out;
         }
-        pstore<VEC, S>(fout + cell0, g[0]);
+        vstore<VEC>(fout + cell0, g[0]);
         // opposite pairs (i, i+1): even parts of Eqs. 7 and 13 shared, odd parts change sign
 #pragma unroll
         for (int i = 1; i < 19; i += 2) {
@@ -645,8 +613,8 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const typename Pop<S>::T* 
                 g[i][c] = oi;
                 g[j][c] = oj;
             }
-            pstore<VEC, S>(fout + i * C + cell0, g[i]);
-            pstore<VEC, S>(fout + j * C + cell0, g[j]);
+            vstore<VEC>(fout + i * C + cell0, g[i]);
+            vstore<VEC>(fout + j * C + cell0, g[j]);
         }
     }
     // per-block partials for Eq. 18 and the mass / Mach checks
@@ -806,33 +774,15 @@ template <bool WX, bool WY, bool WZ>
 void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U, const uint8_t* fmask,
                   const uint8_t* umask, double* part, cudaStream_t s) {
     const int nxy = P.g.nx * P.g.ny;
-    if (P.vec == 4 || P.vec == 2) {
+    if (P.storage == STORE_F32 && (P.vec == 4 || P.vec == 2)) {
         const int groups = nxy / P.vec;
         dim3 grid((groups + 127) / 128, P.g.nz);
-        using H = __half;
-        using B = __nv_bfloat16;
-        if (P.storage == STORE_F16) {
-            if (P.vec == 4)
-                launch_pdl(k_lbm_step_vec<WX, WY, WZ, 4, STORE_F16>, grid, 128, 0, s, (const H*)fin, (H*)fout, F, U,
-                           fmask, umask, part, P);
-            else
-                launch_pdl(k_lbm_step_vec<WX, WY, WZ, 2, STORE_F16>, grid, 128, 0, s, (const H*)fin, (H*)fout, F, U,
-                           fmask, umask, part, P);
-        } else if (P.storage == STORE_BF16) {
-            if (P.vec == 4)
-                launch_pdl(k_lbm_step_vec<WX, WY, WZ, 4, STORE_BF16>, grid, 128, 0, s, (const B*)fin, (B*)fout, F, U,
-                           fmask, umask, part, P);
-            else
-                launch_pdl(k_lbm_step_vec<WX, WY, WZ, 2, STORE_BF16>, grid, 128, 0, s, (const B*)fin, (B*)fout, F, U,
-                           fmask, umask, part, P);
-        } else {
-            if (P.vec == 4)
-                launch_pdl(k_lbm_step_vec<WX, WY, WZ, 4, STORE_F32>, grid, 128, 0, s, (const float*)fin, (float*)fout, F,
-                           U, fmask, umask, part, P);
-            else
-                launch_pdl(k_lbm_step_vec<WX, WY, WZ, 2, STORE_F32>, grid, 128, 0, s, (const float*)fin, (float*)fout, F,
-                           U, fmask, umask, part, P);
-        }
+        if (P.vec == 4)
+            launch_pdl(k_lbm_step_vec<WX, WY, WZ, 4>, grid, 128, 0, s, (const float*)fin, (float*)fout, F, U, fmask, umask,
+                                                                part, P);
+        else
+            launch_pdl(k_lbm_step_vec<WX, WY, WZ, 2>, grid, 128, 0, s, (const float*)fin, (float*)fout, F, U, fmask, umask,
+                                                                part, P);
         return;
     }
     dim3 grid((nxy + P.block - 1) / P.block, P.g.nz);

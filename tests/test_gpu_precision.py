@@ -97,34 +97,3 @@ def test_mass_drift(storage):
     drift = abs(g.stats()[2] / m0 - 1)
     print(NAMES[storage], "mass drift over 200 passes", drift)
     assert drift < (1e-4 if storage == 1 else 1e-3)
-
-
-@pytest.mark.parametrize("vec", [2, 4])
-@pytest.mark.parametrize("storage", [0, 1, 2], ids=["f32", "f16", "bf16"])
-@pytest.mark.parametrize("geom", ["periodic", "walls"])
-def test_vectorised_lattice_passes(storage, vec, geom, monkeypatch):
-    """The stream-collide variant with VEC cells per thread (VLB_LBM_VEC,
-    read when a channel is created) against the oracle over 40 forced passes,
-    for every storage format, within the bounds of the one-cell kernel."""
-    import oracle
-    from paper_2108_04435_gb300 import vlb
-    monkeypatch.setenv("VLB_LBM_VEC", str(vec))
-    if geom == "periodic":
-        p = params((24, 20, 16), (0, 0, 0), storage, init_vn=[0.003, -0.002, 0.01])
-    else:
-        p = params((24, 18, 36), (1, 1, 1), storage, heater_vn=0.01, init_vn=[0.0, 0.0, 0.01])
-    g, r = pair(p)
-    same_lattice_state(g, r, seed=11, amp=1e-2, force_amp=2e-4)
-    F = g.read(vlb.FIELD_FORCE)
-    for k in range(40):
-        if k:
-            g.write(vlb.FIELD_FORCE, F)
-            r.write(oracle.FIELD_FORCE, F.astype(np.float64))
-        g.run_phases(vlb.PHASE_LBM)
-        r.run_phases(oracle.PHASE_LBM)
-    e = lattice_errors(g, r)
-    if storage == 0:
-        assert e["fstar"] < 1e-6 and e["fdev"] < 1e-5 and e["u"] < 1e-5 and e["vs"] < 1e-5, e
-    else:
-        b = BOUNDS[storage]
-        assert e["fdev"] < b["many"] and e["u"] < b["many"] and e["vs"] < b["many"], e
