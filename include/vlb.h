@@ -153,6 +153,18 @@ int vlb_step(vlb_channel* ch, int32_t nsteps);
 /* Enable (default) or disable the graph replay of vlb_step. */
 int vlb_set_graphs(vlb_channel* ch, int32_t enable);
 
+/* Enable (default) or disable the overlap inside the 8-step graphs that
+ * vlb_step replays while 8 or more steps remain (created stream only): the
+ * lattice pass of each step runs on the channel's stream alongside the remesh
+ * and reconnection of the step before and the first Biot-Savart sum of its
+ * own step, which run on a second stream of the highest priority.  Results
+ * are the same, bit for bit, either way.  The overlap pays for a channel that
+ * has the GPU to itself; where many channels share the GPU, their work
+ * overlaps already and the extra streams compete for the device's hardware
+ * queues, so turn it off there.  Errors: INVALID_ARG (null channel, or steps
+ * of vlb_step_async still queued). */
+int vlb_set_overlap(vlb_channel* ch, int32_t enable);
+
 /* Non-blocking form of vlb_step for hosts that drive many channels at once
  * (each on its own stream, so their work overlaps on the GPU): queues the
  * steps and a read-back of the status, and returns without waiting.

@@ -59,6 +59,10 @@ struct vlb_channel {
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
     cudaEvent_t done = nullptr;  // completion of the work queued by vlb_step_async
+    // second stream (highest priority) and fork/join events of the multi-step graphs
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool overlap = true;  // multi-step graphs use the second stream (vlb_set_overlap)
     bool pending = false;
     double timing_ms = 0.0;
     long long timing_launches = 0;
@@ -93,6 +97,11 @@ void release(vlb_channel* ch) {
     ch->ev.clear();
     if (ch->done) cudaEventDestroy(ch->done);
     ch->done = nullptr;
+    if (ch->side) cudaStreamDestroy(ch->side);
+    if (ch->ev_fork) cudaEventDestroy(ch->ev_fork);
+    if (ch->ev_join) cudaEventDestroy(ch->ev_join);
+    ch->side = nullptr;
+    ch->ev_fork = ch->ev_join = nullptr;
     for (int m = 0; m < 2; ++m)
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
@@ -135,10 +144,15 @@ void record_event(vlb_channel* ch) {
     cudaEventRecord(ch->ev[ch->ev_used++], ch->stream);
 }
 
-void phase_lbm(vlb_channel* ch) {
+// Flag the velocity tiles around the current points for the next lattice
+// pass (the previous plane reduction cleared them).
+void mark_points(vlb_channel* ch) {
+    launch_mark_umask(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.counters, ch->cap, ch->d.umask, ch->stream);
+}
+
+// The lattice pass: stream-collide and plane reduction (tiles already flagged).
+void lattice_pass(vlb_channel* ch) {
     Dev& d = ch->d;
-    // flag the velocity tiles around the current points (the previous plane reduction cleared them)
-    launch_mark_umask(ch->lp.g, d.pos[ch->cur_p], d.counters, ch->cap, d.umask, ch->stream);
     if (ch->timing) record_event(ch);
     launch_lbm_step(ch->lp, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
     if (ch->timing) record_event(ch);
@@ -146,6 +160,11 @@ void phase_lbm(vlb_channel* ch) {
     // the pass consumed the force grid: the plane reduction resets it and clears both tile flags
     launch_plane_vs(ch->lp, d.part, d.F, d.umask, d.fmask, ch->stream);
     ch->f_clean = true;
+}
+
+void phase_lbm(vlb_channel* ch) {
+    mark_points(ch);
+    lattice_pass(ch);
 }
 
 // Whether the Biot-Savart kernel applies the equation of motion itself.  It
@@ -161,19 +180,26 @@ bool fused_eom(int n) {
     return mode < 0 ? n >= 8192 : mode == 1;
 }
 
-void phase_vfm(vlb_channel* ch) {
+// Stage-0 geometry and Biot-Savart sum of the first sub-step: they read only
+// the points, so they may run before the lattice pass is done.
+void vfm_pre(vlb_channel* ch, cudaStream_t s) {
     Dev& d = ch->d;
-    const int cap = ch->cap;
-    const int nsub = ch->p.vfm_substeps > 0 ? ch->p.vfm_substeps : 1;
-    double* pos = d.pos[ch->cur_p];
-    const int* next = d.next[ch->cur_p];
+    const VfmParams& V = ch->vp;
     const int* prev = d.prev[ch->cur_p];
+    launch_geometry_stage(V, d.pos[ch->cur_p], d.next[ch->cur_p], prev, d.counters, ch->cap, d.geo, d.seg, d.s0, s);
+    launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp, d.vbs, s,
+                       nullptr, V.nfaces, V.face_code, d.geo);
+}
+
+// Arguments of one filament step on the current points, v_n and V_s.
+EomArgs eom_args(vlb_channel* ch) {
+    Dev& d = ch->d;
     EomArgs ea = {};
     ea.P = ch->vp;
-    ea.cap = cap;
+    ea.cap = ch->cap;
     ea.s0 = d.s0;
     ea.st = d.st;
-    ea.pos_out = pos;
+    ea.pos_out = d.pos[ch->cur_p];
     ea.acc = d.acc;
     ea.vel1 = d.vel1;
     ea.geo = d.geo;
@@ -182,28 +208,45 @@ void phase_vfm(vlb_channel* ch) {
     ea.F = d.F;
     ea.fmask = d.fmask;
     ea.counters = d.counters;
+    return ea;
+}
+
+// One filament step: the RK4 stages of every sub-step (Eqs. 3-4, 10-11) on
+// the current points; the first stage's geometry and Biot-Savart sum are
+// skipped when vfm_pre queued them.
+void vfm_step(vlb_channel* ch, bool pre_done, cudaStream_t s) {
+    Dev& d = ch->d;
+    const VfmParams& V = ch->vp;
+    const int* next = d.next[ch->cur_p];
+    const int* prev = d.prev[ch->cur_p];
+    const int nsub = ch->p.vfm_substeps > 0 ? ch->p.vfm_substeps : 1;
+    EomArgs ea = eom_args(ch);
     for (int sub = 0; sub < nsub; ++sub) {
         const int spread = (sub == 0 && ch->p.couple) ? 1 : 0;
-        if (spread && !ch->f_clean) launch_zero_force(ch->lp.g, d.F, d.fmask, ch->stream);
+        if (spread && !ch->f_clean) launch_zero_force(ch->lp.g, d.F, d.fmask, s);
         if (spread) ch->f_clean = false;
         for (int stage = 0; stage < 4; ++stage) {
-            const double* xs = stage == 0 ? pos : d.st;
             ea.stage = stage;
             ea.spread = spread;
-            launch_geometry_stage(ch->vp, xs, next, prev, d.counters, cap, d.geo, d.seg, stage == 0 ? d.s0 : nullptr,
-                                  ch->stream);
-            const VfmParams& V = ch->vp;
+            if (pre_done && sub == 0 && stage == 0) {
+                launch_eom(ea, d.vbs, s);
+                continue;
+            }
+            launch_geometry_stage(V, stage == 0 ? ea.pos_out : d.st, next, prev, d.counters, ch->cap, d.geo, d.seg,
+                                  stage == 0 ? d.s0 : nullptr, s);
             if (fused_eom(ch->n_hint)) {
-                launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint, d.bsp, d.vbs,
-                                   ch->stream, &ea, V.nfaces, V.face_code, d.geo);
+                launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp,
+                                   d.vbs, s, &ea, V.nfaces, V.face_code, d.geo);
             } else {
-                launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, cap, ch->n_hint, d.bsp, d.vbs,
-                                   ch->stream, nullptr, V.nfaces, V.face_code, d.geo);
-                launch_eom(ea, d.vbs, ch->stream);
+                launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp,
+                                   d.vbs, s, nullptr, V.nfaces, V.face_code, d.geo);
+                launch_eom(ea, d.vbs, s);
             }
         }
     }
 }
+
+void phase_vfm(vlb_channel* ch) { vfm_step(ch, false, ch->stream); }
 
 void run_phases_body(vlb_channel* ch, int mask) {
     if (mask & VLB_PHASE_LBM) phase_lbm(ch);
@@ -372,6 +415,18 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
         ch->has_alloc = true;
     }
     ch->stream = (cudaStream_t)stream;
+    if (ch->stream) {
+        // the multi-step graphs fork the filament chain onto it, at the highest priority
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&ch->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ch->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ch->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (ch->side) cudaStreamDestroy(ch->side);
+            ch->side = nullptr;
+        }
+    }
     Grid g;
     g.nx = p->n[0];
     g.ny = p->n[1];
@@ -487,10 +542,10 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.f[1] = A(esize * 19 * (size_t)C);
     d.F = (long long*)A(sizeof(long long) * 3 * (size_t)C);
     d.U = (float*)A(sizeof(float) * 3 * (size_t)C);
+    d.Vs = (double*)A(sizeof(double) * (size_t)g.nz);
     d.fmask = (uint8_t*)A((size_t)ntiles);
     d.umask = (uint8_t*)A((size_t)ntiles);
     d.part = (double*)A(sizeof(double) * 3 * (size_t)ch->bpp * g.nz);
-    d.Vs = (double*)A(sizeof(double) * (size_t)g.nz);
     d.plane = (double*)A(sizeof(double) * 3 * (size_t)g.nz);
     d.plane_ticket = (int*)A(sizeof(int) * (size_t)g.nz);
     d.dstats = (double*)A(sizeof(double) * DS_COUNT);
@@ -662,6 +717,49 @@ int size_class(int n) {
 // Steps per multi-step graph (even, so both buffer parities are restored).
 constexpr int GRAPH_MULTI = 8;
 
+// nst full steps for a multi-step graph, on two streams.  The lattice pass
+// of step s + 1 reads and writes nothing that the remesh and reconnection of
+// step s touch (populations, force and velocity grids against the point
+// arrays and topology scratch; counters and stats in separate slots or by
+// atomics), nor what the stage-0 geometry and Biot-Savart sum of step s + 1
+// read (the points only).  So that filament chain runs on the second stream
+// alongside the lattice pass, forked and joined inside the graph.  The chain
+// is a row of small, latency-bound launches; its stream has the highest
+// priority, so its blocks go ahead of waiting stream-collide blocks.  (Run
+// alongside the RK stages instead, the lattice pass slowed the Biot-Savart
+// launches more than it gained.)  The points of a lattice pass are not known
+// when it starts, so it writes v_n in every tile instead of the tiles around
+// the points: the same values where the filaments read them.  The result is
+// the same, bit for bit, as in sequence.
+void run_steps_forked(vlb_channel* ch, int nst) {
+    Dev& d = ch->d;
+    const size_t ntiles = (size_t)ch->lp.g.tnx * ch->lp.g.tny * ch->lp.g.tnz;
+    const bool pre = !fused_eom(ch->n_hint);
+    phase_lbm(ch);  // pass 0, tiles flagged around the points
+    cudaEventRecord(ch->ev_fork, ch->stream);
+    cudaStreamWaitEvent(ch->side, ch->ev_fork, 0);
+    for (int s = 0; s < nst; ++s) {
+        vfm_step(ch, s > 0 && pre, ch->side);
+        if (s + 1 < nst) {
+            cudaEventRecord(ch->ev_fork, ch->side);
+            cudaStreamWaitEvent(ch->stream, ch->ev_fork, 0);
+            cudaMemsetAsync(d.umask, 1, ntiles, ch->stream);
+            lattice_pass(ch);
+            cudaEventRecord(ch->ev_join, ch->stream);
+        }
+        launch_remesh(ch->vp, d, ch->cur_p, ch->cap, ch->side);
+        ch->cur_p ^= 1;
+        launch_reconnect(ch->vp, d, ch->cur_p, ch->cap, ch->hsize, ch->side);
+        ch->cur_p ^= 1;
+        if (s + 1 < nst) {
+            if (pre) vfm_pre(ch, ch->side);
+            cudaStreamWaitEvent(ch->side, ch->ev_join, 0);
+        }
+    }
+    cudaEventRecord(ch->ev_join, ch->side);
+    cudaStreamWaitEvent(ch->stream, ch->ev_join, 0);
+}
+
 // Replay `multi ? GRAPH_MULTI : 1` coupled steps from a graph captured on
 // first use for the current buffer parities and filament size class.
 bool step_graph(vlb_channel* ch, bool multi) {
@@ -688,7 +786,9 @@ bool step_graph(vlb_channel* ch, bool multi) {
             return undo();
         }
         tl_no_pdl = true;
-        for (int k = 0; k < nst; ++k) run_phases(ch, VLB_PHASE_ALL);
+        if (nst > 1 && ch->side && ch->overlap) run_steps_forked(ch, nst);
+        else
+            for (int k = 0; k < nst; ++k) run_phases(ch, VLB_PHASE_ALL);
         tl_no_pdl = false;
         cudaError_t e = cudaStreamEndCapture(ch->stream, &graph);
         ch->cur_f = f;  // the captured steps have not run yet
@@ -697,7 +797,7 @@ bool step_graph(vlb_channel* ch, bool multi) {
             cudaGetLastError();
             return undo();
         }
-        e = cudaGraphInstantiate(&ge, graph, 0);
+        e = cudaGraphInstantiate(&ge, graph, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -767,6 +867,24 @@ int vlb_query(vlb_channel* ch) {
 int vlb_set_graphs(vlb_channel* ch, int32_t enable) {
     if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
     ch->graphs = enable != 0;
+    return VLB_OK;
+}
+
+int vlb_set_overlap(vlb_channel* ch, int32_t enable) {
+    if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
+    if (ch->pending) return fail(VLB_ERR_INVALID_ARG, "steps still queued");
+    if (ch->overlap != (enable != 0)) {
+        // the multi-step graphs were captured in the other form
+        cudaStreamSynchronize(ch->stream);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                if (ch->gexec[1][a][b]) {
+                    cudaGraphExecDestroy(ch->gexec[1][a][b]);
+                    ch->gexec[1][a][b] = nullptr;
+                    ch->gclass[1][a][b] = -1;
+                }
+    }
+    ch->overlap = enable != 0;
     return VLB_OK;
 }
 

@@ -145,14 +145,22 @@ def summarize(results, wall_s: float):
     }
 
 
-class GpuRun:
-    """One request as a libvlb channel on its own stream."""
+# Hardware work queues for a serving process (CUDA_DEVICE_MAX_CONNECTIONS).
+MAX_CONNECTIONS = 32
 
-    def __init__(self, req, device: int = 0):
+
+class GpuRun:
+    """One request as a libvlb channel on its own stream.  With other runs
+    sharing the GPU (overlap=False) the channel keeps its steps in sequence:
+    the runs overlap one another already, and a second stream per channel
+    would compete for the device's hardware queues."""
+
+    def __init__(self, req, device: int = 0, overlap: bool = True):
         import torch
 
         from . import vlb
         self.ch = vlb.Channel(req["params"], stream=torch.cuda.Stream(device), device=device)
+        self.ch.set_overlap(overlap)
         self.ch.seed(req["xyz"], req["next"])
         self._n = len(req["next"])
 
@@ -173,12 +181,17 @@ class GpuRun:
 
 
 def serve_gpu(requests, budget_bytes: int, max_slots: int = 16, slice_steps: int = 50, realtime: bool = True):
-    """Serve requests on the current GPU; returns (results, summary)."""
+    """Serve requests on the current GPU; returns (results, summary).  Many
+    channels on their own streams share the device's hardware work queues
+    (8 unless CUDA_DEVICE_MAX_CONNECTIONS, read when the process creates its
+    CUDA context, says otherwise); MAX_CONNECTIONS is the value to set before
+    that for 16 slots."""
     from . import vlb
     for r in requests:
         n = r["params"]["n"]
         r.setdefault("cells", n[0] * n[1] * n[2])
-    sched = Scheduler(make_run=GpuRun, bytes_of=lambda r: vlb.channel_bytes(r["params"]), budget_bytes=budget_bytes,
+    make = GpuRun if max_slots == 1 else (lambda req: GpuRun(req, overlap=False))
+    sched = Scheduler(make_run=make, bytes_of=lambda r: vlb.channel_bytes(r["params"]), budget_bytes=budget_bytes,
                       max_slots=max_slots, slice_steps=slice_steps)
     t0 = time.perf_counter()
     res = sched.serve(requests, realtime=realtime)

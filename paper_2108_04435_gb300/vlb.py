@@ -24,7 +24,7 @@ FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_FDEV, FIELD_LINE_PROFILE = 6, 7, 8
 
 EXPORTS = ["vlb_create_channel", "vlb_seed_vortices", "vlb_step", "vlb_run_phases", "vlb_read_fields",
            "vlb_write_fields", "vlb_line_length", "vlb_destroy", "vlb_last_error", "vlb_set_timing",
-           "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart", "vlb_set_graphs",
+           "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart", "vlb_set_graphs", "vlb_set_overlap",
            "vlb_biot_savart_noalloc", "vlb_step_async", "vlb_query", "vlb_channel_bytes"]
 BUSY = 1
 
@@ -80,6 +80,7 @@ def lib():
         L.vlb_last_error.restype = C.c_char_p
         L.vlb_set_timing.argtypes = [vp, C.c_int32]
         L.vlb_set_graphs.argtypes = [vp, C.c_int32]
+        L.vlb_set_overlap.argtypes = [vp, C.c_int32]
         L.vlb_lbm_timing.argtypes = [vp, dp, C.POINTER(C.c_int64)]
         L.vlb_biot_savart_scratch_bytes.argtypes = [C.c_int32]
         L.vlb_biot_savart_scratch_bytes.restype = C.c_size_t
@@ -230,6 +231,9 @@ class Channel:
 
     def set_graphs(self, enable: bool):
         check(lib().vlb_set_graphs(self.h, 1 if enable else 0))
+
+    def set_overlap(self, enable: bool):
+        check(lib().vlb_set_overlap(self.h, 1 if enable else 0))
 
     def set_timing(self, enable: bool):
         check(lib().vlb_set_timing(self.h, 1 if enable else 0))
