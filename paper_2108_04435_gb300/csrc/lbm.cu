@@ -51,6 +51,7 @@ template <>
 struct Pop<STORE_F32> {
     using T = float;
     static __device__ __forceinline__ float ld(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_cs(const T* p) { return __ldcs(p); }
     static __device__ __forceinline__ float raw(T v) { return v; }
     static __device__ __forceinline__ T cv(float v) { return v; }
 };
@@ -58,6 +59,7 @@ template <>
 struct Pop<STORE_F16> {
     using T = __half;
     static __device__ __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)) * (1.f / 1024.f); }
+    static __device__ __forceinline__ float ld_cs(const T* p) { return __half2float(__ldcs(p)) * (1.f / 1024.f); }
     static __device__ __forceinline__ float raw(T v) { return __half2float(v) * (1.f / 1024.f); }
     static __device__ __forceinline__ T cv(float v) { return __float2half_rn(v * 1024.f); }
 };
@@ -65,9 +67,23 @@ template <>
 struct Pop<STORE_BF16> {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_cs(const T* p) { return __bfloat162float(__ldcs(p)); }
     static __device__ __forceinline__ float raw(T v) { return __bfloat162float(v); }
     static __device__ __forceinline__ T cv(float v) { return __float2bfloat16_rn(v); }
 };
+
+// Population loads and stores of the stream-collide pass.  CS: evict-first
+// (cache-streaming) hints on both, so that a lattice whose population buffer
+// fits in L2 leaves the filament data there (LbmParams::stream_hint).
+template <int S, bool CS>
+__device__ __forceinline__ float pop_ld(const typename Pop<S>::T* p) {
+    return CS ? Pop<S>::ld_cs(p) : Pop<S>::ld(p);
+}
+template <int S, bool CS>
+__device__ __forceinline__ void pop_st(typename Pop<S>::T* p, float v) {
+    if (CS) __stcs(p, Pop<S>::cv(v));
+    else *p = Pop<S>::cv(v);
+}
 
 __device__ __forceinline__ int tile_of(const Grid& g, int x, int y, int z) {
     return ((z >> TILE_SHIFT) * g.tny + (y >> TILE_SHIFT)) * g.tnx + (x >> TILE_SHIFT);
@@ -147,7 +163,7 @@ __device__ __forceinline__ void pull_index(const LbmParams& P, int x, int y, int
     q.zo[0] = zp * nxy; q.zo[1] = z * nxy; q.zo[2] = zm * nxy;
 }
 
-template <bool WX, bool WY, bool WZ, int S>
+template <bool WX, bool WY, bool WZ, int S, bool CS>
 __device__ __forceinline__ void pull_fast(const typename Pop<S>::T* __restrict__ f, const LbmParams& P,
                                           const PullIdx& q, int cell, float g[19]) {
     const int C = (int)P.g.ncell;
@@ -159,7 +175,7 @@ __device__ __forceinline__ void pull_fast(const typename Pop<S>::T* __restrict__
         if (WY && CY(i) != 0) out = out || q.oy[CY(i) + 1];
         if (WZ && CZ(i) != 0) { outz = q.oz[CZ(i) + 1]; out = out || outz; }
         if (WX || WY || WZ) src = out ? opp(i) * C + cell : src;
-        float v = Pop<S>::ld(&f[src]);
+        float v = pop_ld<S, CS>(&f[src]);
         if (WZ && CZ(i) != 0) v += outz ? 6.f * wgt(i) * P.rho0 * (float)CZ(i) * P.heater : 0.f;
         g[i] = v;
     }
@@ -171,7 +187,7 @@ __device__ __forceinline__ void pull_fast(const typename Pop<S>::T* __restrict__
 // The collision works on opposite pairs (i, i'): with c_i' = -c_i the even
 // parts of f^eq (Eq. 7) and of F_i (Eq. 13) are shared and the odd parts
 // change sign.
-template <bool WX, bool WY, bool WZ, int S>
+template <bool WX, bool WY, bool WZ, int S, bool CS>
 __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T* __restrict__ fin,
                                                         typename Pop<S>::T* __restrict__ fout,
                                                         const long long* __restrict__ F, float* __restrict__ U,
@@ -191,7 +207,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
         {
             PullIdx q;
             pull_index<WX, WY, WZ>(P, x, y, z, q);
-            pull_fast<WX, WY, WZ, S>(fin, P, q, cell, g);
+            pull_fast<WX, WY, WZ, S, CS>(fin, P, q, cell, g);
         }
         // Eqs. 5-6 with the half-force shift: rho = rho0 + sum g, j = sum c g
         float drho = P.dr0, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -231,7 +247,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
             float out = g[0] + om * (geq - g[0]);
             if (force) out += P.pref * wgt(0) * (-3.f * uF);
             if (pinned) out = wgt(0) * (drho - 1.5f * rho * P.pin * P.pin) + P.dw[0];
-            fout[cell] = Pop<S>::cv(out);
+            pop_st<S, CS>(&fout[cell], out);
         }
 #pragma unroll
         for (int i = 1; i < 19; i += 2) {
@@ -256,8 +272,8 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
                 oi = ps + pa;
                 oj = ps - pa;
             }
-            fout[i * C + cell] = Pop<S>::cv(oi);
-            fout[j * C + cell] = Pop<S>::cv(oj);
+            pop_st<S, CS>(&fout[i * C + cell], oi);
+            pop_st<S, CS>(&fout[j * C + cell], oj);
         }
         s_drho = drho;
         s_uz = uz;
@@ -770,6 +786,20 @@ __global__ void k_force_import(const float* __restrict__ in, long long* __restri
         F[k] = force_fixed(in[k]);
 }
 
+template <bool WX, bool WY, bool WZ, bool CS>
+void lbm_launch(const LbmParams& P, dim3 grid, const void* fin, void* fout, const long long* F, float* U,
+                const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s) {
+    if (P.storage == STORE_F16)
+        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_F16, CS>, grid, P.block, 0, s, (const __half*)fin, (__half*)fout, F, U,
+                   fmask, umask, part, P);
+    else if (P.storage == STORE_BF16)
+        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_BF16, CS>, grid, P.block, 0, s, (const __nv_bfloat16*)fin,
+                   (__nv_bfloat16*)fout, F, U, fmask, umask, part, P);
+    else
+        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_F32, CS>, grid, P.block, 0, s, (const float*)fin, (float*)fout, F, U,
+                   fmask, umask, part, P);
+}
+
 template <bool WX, bool WY, bool WZ>
 void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U, const uint8_t* fmask,
                   const uint8_t* umask, double* part, cudaStream_t s) {
@@ -786,15 +816,10 @@ void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const long lo
         return;
     }
     dim3 grid((nxy + P.block - 1) / P.block, P.g.nz);
-    if (P.storage == STORE_F16)
-        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_F16>, grid, P.block, 0, s, (const __half*)fin, (__half*)fout, F, U, fmask,
-                                                                    umask, part, P);
-    else if (P.storage == STORE_BF16)
-        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_BF16>, grid, P.block, 0, s, 
-            (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, F, U, fmask, umask, part, P);
+    if (P.stream_hint)
+        lbm_launch<WX, WY, WZ, true>(P, grid, fin, fout, F, U, fmask, umask, part, s);
     else
-        launch_pdl(k_lbm_step<WX, WY, WZ, STORE_F32>, grid, P.block, 0, s, (const float*)fin, (float*)fout, F, U, fmask,
-                                                                    umask, part, P);
+        lbm_launch<WX, WY, WZ, false>(P, grid, fin, fout, F, U, fmask, umask, part, s);
 }
 
 template <bool WX, bool WY, bool WZ>

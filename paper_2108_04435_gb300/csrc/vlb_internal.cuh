@@ -149,6 +149,7 @@ struct LbmParams {
     int vec;            // cells per thread of the stream-collide kernel (4, 2, or 1 = scalar kernel)
     int block;          // threads per block of the scalar kernel (128 or 256)
     int storage;        // STORE_F32, STORE_F16 (deviation x 2^10) or STORE_BF16
+    int stream_hint;    // evict-first loads and stores of the populations (one population buffer fits in L2)
     unsigned long long nx_magic;  // y = (xy * nx_magic) >> nx_shift equals xy / nx for 0 <= xy < nx * ny
     int nx_shift;
     double inv_ratio;   // rho_n / rho_s
