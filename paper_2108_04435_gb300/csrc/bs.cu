@@ -106,48 +106,49 @@ struct BsTarget {
     int excl;                      // a pinned end: the image of its own segment across its wall (local term)
 };
 
+// One (target, segment) pair of Eq. 3.  With R1 = s_j - r and d the segment
+// vector: R1 x R2 = R1 x d, R1.R2 = |R1|^2 + R1.d and |R2|^2 = |R1|^2 +
+// 2 R1.d + |d|^2 (|d|^2 stored in the record).  MASKED: j may be the target's
+// own segment or its predecessor's, which belong to the local term.
+template <bool PERIODIC, bool MASKED>
+__device__ __forceinline__ void bs_pair(const float4& A, const float4& B, const float4& D, int j, BsTarget& t,
+                                        const BoxF& box, float kq) {
+    const float dx = B.z, dy = B.w, dz = D.x, dd = D.y;
+    float r1x = (A.x - t.hx) + (A.w - t.lx);
+    float r1y = (A.y - t.hy) + (B.x - t.ly);
+    float r1z = (A.z - t.hz) + (B.y - t.lz);
+    if (PERIODIC) {
+        r1x = fmaf(-box.Lx, round_mul_fma(r1x, box.iLx), r1x);
+        r1y = fmaf(-box.Ly, round_mul_fma(r1y, box.iLy), r1y);
+        r1z = fmaf(-box.Lz, round_mul_fma(r1z, box.iLz), r1z);
+    }
+    const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
+    const float rd = r1x * dx + r1y * dy + r1z * dz;
+    const float b2 = fmaf(2.f, rd, a2) + dd;
+    const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
+    const float la = a2 * ia, lb = b2 * ib;
+    const float ab = la * lb;
+    const float s = ab + (a2 + rd);
+    const float fac = kq * (la + lb) * rcp_approx(ab * s);
+    // s <= 1e-6 ab: the target lies on the segment (or coincides with an
+    // end point), where the integral is not defined; NaN fails the test too
+    bool use = s > 1e-6f * ab;
+    if (MASKED) use = use & (j != t.self) & (j != t.prev) & (j != t.excl);
+    const float c = use ? fac : 0.f;
+    t.vx += c * (r1y * dz - r1z * dy);
+    t.vy += c * (r1z * dx - r1x * dz);
+    t.vz += c * (r1x * dy - r1y * dx);
+}
+
 // Sum over the segments of one shared-memory tile for TGT targets per thread.
-// With R1 = s_j - r and d the segment vector: R1 x R2 = R1 x d,
-// R1.R2 = |R1|^2 + R1.d and |R2|^2 = |R1|^2 + 2 R1.d + |d|^2 (|d|^2 stored in
-// the record).  MASKED: the tile may hold a target's own segment or its
-// predecessor's, which belong to the local term.
 template <bool PERIODIC, bool MASKED, int TGT>
 __device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, int jb, BsTarget (&t)[TGT],
                                         const BoxF& box, float kq) {
 #pragma unroll 2
     for (int k = 0; k < cnt; ++k) {
         const float4 A = T[3 * k], B = T[3 * k + 1], D = T[3 * k + 2];
-        const float dx = B.z, dy = B.w, dz = D.x, dd = D.y;
 #pragma unroll
-        for (int u = 0; u < TGT; ++u) {
-            float r1x = (A.x - t[u].hx) + (A.w - t[u].lx);
-            float r1y = (A.y - t[u].hy) + (B.x - t[u].ly);
-            float r1z = (A.z - t[u].hz) + (B.y - t[u].lz);
-            if (PERIODIC) {
-                r1x = fmaf(-box.Lx, round_mul_fma(r1x, box.iLx), r1x);
-                r1y = fmaf(-box.Ly, round_mul_fma(r1y, box.iLy), r1y);
-                r1z = fmaf(-box.Lz, round_mul_fma(r1z, box.iLz), r1z);
-            }
-            const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
-            const float rd = r1x * dx + r1y * dy + r1z * dz;
-            const float b2 = fmaf(2.f, rd, a2) + dd;
-            const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
-            const float la = a2 * ia, lb = b2 * ib;
-            const float ab = la * lb;
-            const float s = ab + (a2 + rd);
-            const float fac = kq * (la + lb) * rcp_approx(ab * s);
-            // s <= 1e-6 ab: the target lies on the segment (or coincides with an
-            // end point), where the integral is not defined; NaN fails the test too
-            bool use = s > 1e-6f * ab;
-            if (MASKED) {
-                const int j = jb + k;
-                use = use & (j != t[u].self) & (j != t[u].prev) & (j != t[u].excl);
-            }
-            const float c = use ? fac : 0.f;
-            t[u].vx += c * (r1y * dz - r1z * dy);
-            t[u].vy += c * (r1z * dx - r1x * dz);
-            t[u].vz += c * (r1x * dy - r1y * dx);
-        }
+        for (int u = 0; u < TGT; ++u) bs_pair<PERIODIC, MASKED>(A, B, D, jb + k, t[u], box, kq);
     }
 }
 
@@ -162,6 +163,26 @@ struct BsImages {
     int face_code[6];
     const float4* geo;  // pinned-end wall codes (+1) in geo[2i + 1].w
 };
+
+// Target i of N (none when i >= N): its position from its own segment record,
+// and the segments that belong to its local term.
+__device__ __forceinline__ BsTarget bs_target(const float4* __restrict__ seg, const int* __restrict__ prev,
+                                              const BsImages& im, int N, int i) {
+    BsTarget t{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1};
+    if (i < N) {
+        const float4 a = seg[3LL * i], b = seg[3LL * i + 1];
+        t.hx = a.x; t.hy = a.y; t.hz = a.z; t.lx = a.w; t.ly = b.x; t.lz = b.y;
+        t.self = i;
+        t.prev = prev[i];
+        if (im.nfaces > 0) {
+            const int pin = (int)im.geo[2LL * i + 1].w - 1;
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+                if (f < im.nfaces && im.face_code[f] == pin) t.excl = (1 + f) * N + (t.prev < 0 ? i : t.prev);
+        }
+    }
+    return t;
+}
 
 // Shared memory of one block's Biot-Savart work: two source tiles, their
 // mbarriers and two broadcast slots.  `used` counts the tiles the block has
@@ -212,23 +233,7 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
         BsTarget t[TGT];
         bool own_any = false;
 #pragma unroll
-        for (int u = 0; u < TGT; ++u) {
-            const int i = tb * TT + u * BS_TPB + threadIdx.x;
-            t[u] = BsTarget{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1};
-            if (i < N) {
-                const float4 a = seg[3LL * i], b = seg[3LL * i + 1];
-                t[u].hx = a.x; t[u].hy = a.y; t[u].hz = a.z; t[u].lx = a.w; t[u].ly = b.x; t[u].lz = b.y;
-                t[u].self = i;
-                t[u].prev = prev[i];
-                if (im.nfaces > 0) {
-                    const int pin = (int)im.geo[2LL * i + 1].w - 1;
-#pragma unroll
-                    for (int f = 0; f < 6; ++f)
-                        if (f < im.nfaces && im.face_code[f] == pin)
-                            t[u].excl = (1 + f) * N + (t[u].prev < 0 ? i : t[u].prev);
-                }
-            }
-        }
+        for (int u = 0; u < TGT; ++u) t[u] = bs_target(seg, prev, im, N, tb * TT + u * BS_TPB + threadIdx.x);
         const int ntiles = j1 > j0 ? (j1 - j0 + BS_TILE - 1) / BS_TILE : 0;
         if (threadIdx.x == 0 && ntiles > 0) issue_tile(tile[used & 1], seg, j0, min(BS_TILE, j1 - j0), &bar[used & 1]);
         for (int tt = 0; tt < ntiles; ++tt) {
