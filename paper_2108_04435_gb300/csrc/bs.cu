@@ -141,10 +141,14 @@ __device__ __forceinline__ void bs_pair(const float4& A, const float4& B, const 
 }
 
 // Sum over the segments of one shared-memory tile for TGT targets per thread.
+// Four segments per unrolled pass: with few points a block's four warps are
+// alone on their SM, and the pair arithmetic is a chain of dependent
+// instructions (measured: 1.2% faster coupled step at 1.1k points, 0.6% at
+// 17k, than two per pass).
 template <bool PERIODIC, bool MASKED, int TGT>
 __device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, int jb, BsTarget (&t)[TGT],
                                         const BoxF& box, float kq) {
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < cnt; ++k) {
         const float4 A = T[3 * k], B = T[3 * k + 1], D = T[3 * k + 2];
 #pragma unroll
