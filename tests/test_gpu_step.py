@@ -124,3 +124,23 @@ def test_overlap_switch_mid_run():
         g.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("storage", [0, 1], ids=["f32", "f16"])
+def test_cache_hints_change_nothing(storage, monkeypatch):
+    """The evict-first hints on the population traffic (on by default when a
+    population buffer fits in L2) change where lines live, not a single
+    value: 16 coupled steps agree bit for bit with the hints forced off."""
+    from paper_2108_04435_gb300 import configs, vlb
+    p, xyz, nxt = configs.config("channel64x64x256")
+    p["storage"] = storage
+    out = []
+    for hint in ("1", "0"):
+        monkeypatch.setenv("VLB_LBM_STREAM_HINT", hint)
+        g = vlb.Channel(p)
+        g.seed(xyz, nxt)
+        g.step(16)
+        out.append([g.read(w) for w in (vlb.FIELD_FSTAR, vlb.FIELD_FORCE, vlb.FIELD_POS, vlb.FIELD_NEXT)])
+        g.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
