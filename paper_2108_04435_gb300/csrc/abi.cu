@@ -150,11 +150,14 @@ void mark_points(vlb_channel* ch) {
     launch_mark_umask(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.counters, ch->cap, ch->d.umask, ch->stream);
 }
 
-// The lattice pass: stream-collide and plane reduction (tiles already flagged).
-void lattice_pass(vlb_channel* ch) {
+// The lattice pass: stream-collide and plane reduction (tiles already
+// flagged, or every tile with all_u).
+void lattice_pass(vlb_channel* ch, bool all_u = false) {
     Dev& d = ch->d;
     if (ch->timing) record_event(ch);
-    launch_lbm_step(ch->lp, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
+    LbmParams L = ch->lp;
+    L.all_u = all_u ? 1 : 0;
+    launch_lbm_step(L, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
     if (ch->timing) record_event(ch);
     ch->cur_f ^= 1;
     // the pass consumed the force grid: the plane reduction resets it and clears both tile flags
@@ -188,7 +191,7 @@ void vfm_pre(vlb_channel* ch, cudaStream_t s) {
     const int* prev = d.prev[ch->cur_p];
     launch_geometry_stage(V, d.pos[ch->cur_p], d.next[ch->cur_p], prev, d.counters, ch->cap, d.geo, d.seg, d.s0, s);
     launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp, d.vbs, s,
-                       nullptr, V.nfaces, V.face_code, d.geo);
+                       nullptr, V.nfaces, V.face_code, d.geo, d.vacc);
 }
 
 // Arguments of one filament step on the current points, v_n and V_s.
@@ -228,8 +231,10 @@ void vfm_step(vlb_channel* ch, bool pre_done, cudaStream_t s) {
         for (int stage = 0; stage < 4; ++stage) {
             ea.stage = stage;
             ea.spread = spread;
+            // below the fused size the Biot-Savart sums arrive in d.vacc
+            long long* vacc = bs_uses_vacc(ch->n_hint) ? d.vacc : nullptr;
             if (pre_done && sub == 0 && stage == 0) {
-                launch_eom(ea, d.vbs, s);
+                launch_eom(ea, d.vbs, s, vacc);
                 continue;
             }
             launch_geometry_stage(V, stage == 0 ? ea.pos_out : d.st, next, prev, d.counters, ch->cap, d.geo, d.seg,
@@ -239,8 +244,8 @@ void vfm_step(vlb_channel* ch, bool pre_done, cudaStream_t s) {
                                    d.vbs, s, &ea, V.nfaces, V.face_code, d.geo);
             } else {
                 launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp,
-                                   d.vbs, s, nullptr, V.nfaces, V.face_code, d.geo);
-                launch_eom(ea, d.vbs, s);
+                                   d.vbs, s, nullptr, V.nfaces, V.face_code, d.geo, vacc);
+                launch_eom(ea, d.vbs, s, vacc);
             }
         }
     }
@@ -395,7 +400,7 @@ size_t vlb_channel_bytes(const vlb_params* p) {
         for (int a = 0; a < 3; ++a) nfaces += p->wall[a] ? 2 : 0;
     b += 2 * (up(24 * cap) + 2 * up(4 * cap)) + 6 * up(24 * cap) + up(8 * cap) + up(32 * cap) +
          up(48 * cap * (1 + nfaces));
-    b += up(12 * cap * (size_t)bs_max_splits((int)cap)) + up(12 * cap) + up(4 * ((cap + 127) / 128));
+    b += up(12 * cap * (size_t)bs_max_splits((int)cap)) + up(12 * cap) + up(24 * cap) + up(4 * ((cap + 127) / 128));
     b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(8 * cap);
     const size_t nc = cap / 2 + 1;
     b += 4 * up(4 * nc) + up(8 * nc) + up(4 * cap) + up(8 * ((cap + 255) / 256));
@@ -578,6 +583,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.seg = (float4*)A(sizeof(float4) * 3 * (size_t)cap * (size_t)(1 + V.nfaces));  // segments, then wall images
     d.bsp = (float*)A(sizeof(float) * 3 * (size_t)cap * (size_t)nsm);
     d.vbs = (float*)A(sizeof(float) * 3 * (size_t)cap);
+    d.vacc = (long long*)A(sizeof(long long) * 3 * (size_t)cap);
     d.tile_ticket = (int*)A(sizeof(int) * (size_t)((cap + BS_TPB - 1) / BS_TPB));
     d.flags = (uint8_t*)A((size_t)cap);
     d.alive = (uint8_t*)A((size_t)cap);
@@ -621,6 +627,10 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     L.inv_ratio = 1.0 / p->rho_s_over_rho_n;
     cudaMemsetAsync(d.dstats, 0, sizeof(double) * DS_COUNT, s);
     cudaMemsetAsync(d.stamp, 0, sizeof(int) * (size_t)cap, s);
+    cudaMemsetAsync(d.vacc, 0, sizeof(long long) * 3 * (size_t)cap, s);
+    // the stage-1 velocity export starts at zero, as in the oracle (rows past
+    // the current count keep what an earlier, larger advance left)
+    cudaMemsetAsync(d.vel1, 0, sizeof(double) * 3 * (size_t)cap, s);
     cudaMemsetAsync(d.bsp, 0, sizeof(float) * 3 * (size_t)cap * (size_t)nsm, s);
     cudaMemsetAsync(d.tile_ticket, 0, sizeof(int) * (size_t)((cap + BS_TPB - 1) / BS_TPB), s);
     init_hash(d, h, s);
@@ -745,7 +755,6 @@ constexpr int GRAPH_MULTI = 8;
 // the same, bit for bit, as in sequence.
 void run_steps_forked(vlb_channel* ch, int nst) {
     Dev& d = ch->d;
-    const size_t ntiles = (size_t)ch->lp.g.tnx * ch->lp.g.tny * ch->lp.g.tnz;
     const bool pre = !fused_eom(ch->n_hint);
     phase_lbm(ch);  // pass 0, tiles flagged around the points
     cudaEventRecord(ch->ev_fork, ch->stream);
@@ -755,8 +764,7 @@ void run_steps_forked(vlb_channel* ch, int nst) {
         if (s + 1 < nst) {
             cudaEventRecord(ch->ev_fork, ch->side);
             cudaStreamWaitEvent(ch->stream, ch->ev_fork, 0);
-            cudaMemsetAsync(d.umask, 1, ntiles, ch->stream);
-            lattice_pass(ch);
+            lattice_pass(ch, true);
             cudaEventRecord(ch->ev_join, ch->stream);
         }
         launch_remesh(ch->vp, d, ch->cur_p, ch->cap, ch->side);

@@ -210,11 +210,11 @@ __device__ __forceinline__ void bs_smem_init(const BsSmem& sm) {
 // blockIdx.x, then items from the device counter CNT_BSWORK (reset to 0
 // before the pass).  Returns false after a timed-out tile copy (status
 // TIMEOUT set).
-template <bool PERIODIC, int TGT, bool EOM>
+template <bool PERIODIC, int TGT, bool EOM, bool ACC>
 __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ prev, int* __restrict__ counters,
                         int* __restrict__ tile_ticket, int cap, const BoxF& box, float kq, float* __restrict__ part,
                         float* __restrict__ vel, const EomArgs& ea, const BsImages& im, const BsSmem& sm,
-                        uint32_t& used) {
+                        uint32_t& used, long long* __restrict__ vacc) {
     float4 (*tile)[BS_TILE * 3] = sm.tile;
     uint64_t* bar = sm.bar;
     int& s_item = *sm.s_item;
@@ -270,7 +270,19 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
             __syncthreads();
         }
         used += (uint32_t)ntiles;
-        if (ns == 1) {
+        if (ACC) {
+            // ACC: each split adds its sums in fixed point (exact, in any
+            // order); the equation-of-motion kernel that follows reads them
+#pragma unroll
+            for (int v = 0; v < TGT; ++v) {
+                const int i = t[v].self;
+                if (i >= 0) {
+                    atomicAdd((unsigned long long*)&vacc[i], (unsigned long long)bs_fixed(t[v].vx));
+                    atomicAdd((unsigned long long*)&vacc[(long long)cap + i], (unsigned long long)bs_fixed(t[v].vy));
+                    atomicAdd((unsigned long long*)&vacc[2LL * cap + i], (unsigned long long)bs_fixed(t[v].vz));
+                }
+            }
+        } else if (ns == 1) {
 #pragma unroll
             for (int v = 0; v < TGT; ++v) {
                 const int i = t[v].self;
@@ -330,11 +342,11 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
 // At least 8 resident blocks of 128 threads per SM (the grid is sized for 8):
 // the pair loop is issue-bound and needs the warps, and the equation of motion
 // applied after it (EOM) would otherwise raise the count to 72 registers.
-template <bool PERIODIC, int TGT, bool EOM>
+template <bool PERIODIC, int TGT, bool EOM, bool ACC>
 __global__ void __launch_bounds__(BS_TPB, EOM ? 8 : 9)
     k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev, int* __restrict__ counters,
                   int* __restrict__ tile_ticket, int cap, BoxF box, float kq, float* __restrict__ part,
-                  float* __restrict__ vel, EomArgs ea, BsImages im) {
+                  float* __restrict__ vel, EomArgs ea, BsImages im, long long* __restrict__ vacc) {
     pdl_wait_trigger();
     __shared__ __align__(128) float4 tile[2][BS_TILE * 3];
     __shared__ __align__(8) uint64_t bar[2];
@@ -342,7 +354,8 @@ __global__ void __launch_bounds__(BS_TPB, EOM ? 8 : 9)
     const BsSmem sm = {tile, bar, &s_item, &s_last};
     bs_smem_init(sm);
     uint32_t used = 0;
-    bs_work<PERIODIC, TGT, EOM>(seg, prev, counters, tile_ticket, cap, box, kq, part, vel, ea, im, sm, used);
+    bs_work<PERIODIC, TGT, EOM, ACC>(seg, prev, counters, tile_ticket, cap, box, kq, part, vel, ea, im, sm, used,
+                                     vacc);
 }
 
 // Stand-alone entry: prev[] and the source records from a caller's point set.
@@ -393,6 +406,12 @@ BoxF make_box(const Grid& g) {
 
 }  // namespace
 
+// Few points: the split sums go to the fixed-point accumulator, so no block
+// waits for a ticket and no last block re-reads the partial sums.  From 8192
+// points on (two targets per thread, usually the fused equation of motion)
+// the partial-sum path stays.
+bool bs_uses_vacc(int n_hint) { return n_hint < 8192; }
+
 int bs_max_splits(int cap) {
     int m = 1;
     for (int n = 1; n <= cap; n += (n < 8192 ? 1 : 128)) {
@@ -402,9 +421,10 @@ int bs_max_splits(int cap) {
     return m;
 }
 
-template <int TGT, bool EOM>
+template <int TGT, bool EOM, bool ACC = false>
 void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int* cnt, int* tile_ticket, int cap, int n,
-               float* part, float* vel, const EomArgs& ea, const BsImages& im, cudaStream_t s) {
+               float* part, float* vel, const EomArgs& ea, const BsImages& im, cudaStream_t s,
+               long long* vacc = nullptr) {
     // enough blocks for every item of about n points (at most 8 per SM); more
     // points than that are still covered by the blocks' item loop
     constexpr int TT = BS_TPB * TGT;
@@ -412,16 +432,17 @@ void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int*
     const int grid = items < 8 * 152 ? items : 8 * 152;
     const BoxF box = make_box(g);
     if (g.wall[0] && g.wall[1] && g.wall[2])
-        launch_pdl(k_biot_savart<false, TGT, EOM>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part,
-                   vel, ea, im);
+        launch_pdl(k_biot_savart<false, TGT, EOM, ACC>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq,
+                   part, vel, ea, im, vacc);
     else
-        launch_pdl(k_biot_savart<true, TGT, EOM>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part,
-                   vel, ea, im);
+        launch_pdl(k_biot_savart<true, TGT, EOM, ACC>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq,
+                   part, vel, ea, im, vacc);
 }
 
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
                         int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
-                        const EomArgs* eom, int nfaces, const int* face_code, const float4* geo) {
+                        const EomArgs* eom, int nfaces, const int* face_code, const float4* geo,
+                        long long* vacc) {
     if (cap <= 0) return;
     const int n = n_hint > 0 ? (n_hint < cap ? n_hint : cap) : 1;
     const float kq = (float)(kappa / (4.0 * 3.14159265358979323846));
@@ -434,6 +455,10 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
     im.nfaces = geo ? nfaces : 0;
     for (int f = 0; f < im.nfaces; ++f) im.face_code[f] = face_code[f];
     im.geo = geo;
+    if (vacc && !eom && bs_uses_vacc(n)) {
+        bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s, vacc);
+        return;
+    }
     if (n >= 8192) {
         if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
         else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);

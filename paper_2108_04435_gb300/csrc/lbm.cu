@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
         const float inv = __fdividef(1.f, rho);  // ~1 ulp; rho is close to rho0
         const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
         const float usq = ux * ux + uy * uy + uz * uz;
-        if (umask[tile]) {
+        if (P.all_u || umask[tile]) {
             U[cell] = ux;
             U[C + cell] = uy;
             U[2 * C + cell] = uz;
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ 
         const int tile = tile_of(P.g, x0, y, z);  // VEC <= 8 cells share a tile
         const bool factive = fmask[tile] != 0;
         const bool force = factive || P.body_on;
-        const bool uact = umask[tile] != 0;
+        const bool uact = P.all_u || umask[tile] != 0;
         float Fx[VEC], Fy[VEC], Fz[VEC];
 #pragma unroll
         for (int c = 0; c < VEC; ++c) {

@@ -33,14 +33,22 @@ __global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double
 
 // The equation of motion of each point as a kernel of its own (used when the
 // Biot-Savart pass does not apply it).
-__global__ void __launch_bounds__(64) k_eom(EomArgs A, const float* __restrict__ vbs) {
+__global__ void __launch_bounds__(64) k_eom(EomArgs A, const float* __restrict__ vbs, long long* __restrict__ vacc) {
     pdl_wait_trigger();
     const int N = A.counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = i < N;
     float v[3] = {0.f, 0.f, 0.f};
-    if (valid)
-        for (int k = 0; k < 3; ++k) v[k] = vbs[(long long)k * A.cap + i];
+    if (valid) {
+        if (vacc) {
+            for (int k = 0; k < 3; ++k) {
+                v[k] = bs_value(vacc[(long long)k * A.cap + i]);
+                vacc[(long long)k * A.cap + i] = 0;  // cleared for the next Biot-Savart pass
+            }
+        } else {
+            for (int k = 0; k < 3; ++k) v[k] = vbs[(long long)k * A.cap + i];
+        }
+    }
     eom_point(A, i, valid, v[0], v[1], v[2]);
 }
 
@@ -115,9 +123,9 @@ void launch_geometry_stage(const VfmParams& P, const double* s, const int* next,
     launch_pdl(k_geometry_stage, (cap + 63) / 64, 64, 0, st, P, s, next, prev, counters, cap, geo, seg, s0_copy);
 }
 
-void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s) {
+void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s, long long* vacc) {
     if (A.cap <= 0) return;
-    launch_pdl(k_eom, (A.cap + 63) / 64, 64, 0, s, A, vbs);
+    launch_pdl(k_eom, (A.cap + 63) / 64, 64, 0, s, A, vbs, vacc);
 }
 
 void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,

@@ -60,6 +60,12 @@ constexpr int FORCE_FRAC = 44;
 __device__ __forceinline__ long long force_fixed(float v) { return __float2ll_rn(v * 0x1p44f); }
 __device__ __forceinline__ float force_value(long long a) { return __ll2float_rn(a) * 0x1p-44f; }
 
+// Biot-Savart split sums below the fused size, accumulated the same way: int64
+// with 40 fractional bits (resolution 9.1e-13, range 8.4e6 in lattice units),
+// so the sum over splits is exact and independent of their order.
+__device__ __forceinline__ long long bs_fixed(float v) { return __float2ll_rn(v * 0x1p40f); }
+__device__ __forceinline__ float bs_value(long long a) { return __ll2float_rn(a) * 0x1p-40f; }
+
 // Programmatic dependent launch: the kernels of a step are launched with
 // programmatic stream serialisation, so each one is scheduled while its
 // predecessor drains.  Every such kernel first waits for its predecessor's
@@ -150,6 +156,7 @@ struct LbmParams {
     int block;          // threads per block of the scalar kernel (128 or 256)
     int storage;        // STORE_F32, STORE_F16 (deviation x 2^10) or STORE_BF16
     int stream_hint;    // evict-first loads and stores of the populations (one population buffer fits in L2)
+    int all_u;          // write v_n in every tile, flagged or not (a pass queued before its points exist)
     unsigned long long nx_magic;  // y = (xy * nx_magic) >> nx_shift equals xy / nx for 0 <= xy < nx * ny
     int nx_shift;
     double inv_ratio;   // rho_n / rho_s
@@ -236,6 +243,7 @@ struct Dev {
     float4* seg;        // Biot-Savart source records, 3 float4 per point
     float* bsp;         // Biot-Savart partial sums [splits][3][cap]
     float* vbs;         // Biot-Savart velocity [3][cap]
+    long long* vacc;    // Biot-Savart velocity [3][cap], fixed point (bs_fixed), zero between uses
     int* tile_ticket;   // per target tile: splits done
     float4* geo;        // stage geometry: (s', dxi), (local velocity, 0) per point
     // topology scratch
@@ -278,7 +286,9 @@ void launch_import(const LbmParams& P, const float* in, void* f, int i0, int i1,
 // vfm.cu
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
                            int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st);
-void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s);
+// vacc != nullptr: the Biot-Savart velocity is read from the fixed-point sums,
+// which the kernel clears again for the next pass.
+void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s, long long* vacc = nullptr);
 void launch_line_profile(const Grid& g, const double* pos, const int* next, const int* counters, int cap,
                          double* prof, cudaStream_t s);
 void launch_line_length(const Grid& g, const double* pos, const int* next, int* counters, int cap, double* part,
@@ -295,7 +305,10 @@ int bs_max_splits(int cap);
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
                         int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
                         const EomArgs* eom = nullptr, int nfaces = 0, const int* face_code = nullptr,
-                        const float4* geo = nullptr);
+                        const float4* geo = nullptr, long long* vacc = nullptr);
+// Whether launch_biot_savart, given vacc and no equation of motion, adds the
+// split sums of about n_hint points into vacc (else it writes vel).
+bool bs_uses_vacc(int n_hint);
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
                                int* counters, cudaStream_t s);
 
