@@ -45,10 +45,10 @@ def launches_per_step(n_points: int) -> int:
     """Kernels of one coupled step (1 RK4 sub-step): lattice 3 (velocity-tile
     flags, stream-collide, plane reduction with the force-grid reset),
     filaments 4 x 3 (per RK stage geometry, Biot-Savart, equation of motion),
-    remesh 2, reconnection 4 = 21.  From 8192 points on the Biot-Savart kernel
+    remesh 2, reconnection 4 = 21.  From 24576 points on the Biot-Savart kernel
     applies the equation of motion itself (17; or as VLB_FUSED_EOM forces)."""
     mode = os.environ.get("VLB_FUSED_EOM")
-    fused = n_points >= 8192 if mode is None else mode != "0"
+    fused = n_points >= 24576 if mode is None else mode != "0"
     return 17 if fused else 21
 
 

@@ -170,17 +170,13 @@ void phase_lbm(vlb_channel* ch) {
     lattice_pass(ch);
 }
 
-// Whether the Biot-Savart kernel applies the equation of motion itself.  It
-// pays once there are many points (measured: 1.8% faster per step at 17k
-// points, 3% slower at 1.1k, where the separate kernel overlaps better), so by
-// default from 8192 points on; VLB_FUSED_EOM=1 / 0 in the environment forces
-// it on / off.
+// Whether the Biot-Savart kernel applies the equation of motion itself: by
+// default from BS_ACC_MAX points on, where it sums partial sums per target
+// tile (below, the fixed-point accumulator and a separate kernel are faster);
+// VLB_FUSED_EOM=1 / 0 in the environment forces it on / off.
 bool fused_eom(int n) {
-    static const int mode = [] {
-        const char* v = getenv("VLB_FUSED_EOM");
-        return v ? (v[0] == '0' ? 0 : 1) : -1;
-    }();
-    return mode < 0 ? n >= 8192 : mode == 1;
+    const char* v = getenv("VLB_FUSED_EOM");
+    return v ? v[0] != '0' : n >= BS_ACC_MAX;
 }
 
 // Stage-0 geometry and Biot-Savart sum of the first sub-step: they read only

@@ -406,11 +406,9 @@ BoxF make_box(const Grid& g) {
 
 }  // namespace
 
-// Few points: the split sums go to the fixed-point accumulator, so no block
-// waits for a ticket and no last block re-reads the partial sums.  From 8192
-// points on (two targets per thread, usually the fused equation of motion)
-// the partial-sum path stays.
-bool bs_uses_vacc(int n_hint) { return n_hint < 8192; }
+// Up to BS_ACC_MAX points the split sums go to the fixed-point accumulator,
+// so no block waits for a ticket and no last block re-reads partial sums.
+bool bs_uses_vacc(int n_hint) { return n_hint < BS_ACC_MAX; }
 
 int bs_max_splits(int cap) {
     int m = 1;
@@ -456,7 +454,8 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
     for (int f = 0; f < im.nfaces; ++f) im.face_code[f] = face_code[f];
     im.geo = geo;
     if (vacc && !eom && bs_uses_vacc(n)) {
-        bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s, vacc);
+        if (n >= 8192) bs_launch<2, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s, vacc);
+        else bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s, vacc);
         return;
     }
     if (n >= 8192) {

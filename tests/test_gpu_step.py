@@ -81,15 +81,18 @@ def test_smoke_entry():
     __graft_entry__.smoke()
 
 
-@pytest.mark.parametrize("name,steps", [("channel64x64x256", 20), ("channel64x64x256_lines", 20), ("box128", 12)])
-def test_overlapped_graph_steps_match_sequential(name, steps):
+@pytest.mark.parametrize("name,steps,fused", [("channel64x64x256", 20, "0"), ("channel64x64x256_lines", 20, "0"),
+                                              ("box128", 12, "0"), ("box128", 12, "1")])
+def test_overlapped_graph_steps_match_sequential(name, steps, fused, monkeypatch):
     """The 8-step graphs run the lattice pass of each step alongside the
     remesh and reconnection of the step before, on a second stream; with the
     overlap off the same graphs keep every step in sequence.  Populations,
     force grid, points, links and statistics agree bit for bit (walls with
-    open lines; the periodic box from 8192 points, where the Biot-Savart
-    kernel applies the equation of motion)."""
+    open lines; the periodic box at 16.9k points, with fixed-point split sums
+    and, forced by VLB_FUSED_EOM=1, with the Biot-Savart kernel applying the
+    equation of motion)."""
     from paper_2108_04435_gb300 import configs, vlb
+    monkeypatch.setenv("VLB_FUSED_EOM", fused)
     p, xyz, nxt = configs.config(name)
     out = []
     for overlap in (True, False):

@@ -1,8 +1,11 @@
 """GPU filament advance (Eqs. 3-4, 10-11, local term, RK4) vs the oracle.
 
 Stage-1 velocities, the one-step displacement and the spread force grid must
-agree to relative L2 1e-5 (below 8192 points with the equation of motion as a
-kernel of its own, above with the Biot-Savart kernel applying it); the
+agree to relative L2 1e-5: with the Biot-Savart split sums accumulated in
+fixed point and the equation of motion as a kernel of its own (one and, from
+8192 points, two targets per thread), and with the partial-sum kernel applying
+the equation of motion itself (the default from 24576 points; forced here by
+VLB_FUSED_EOM=1 on 8.7k points).  The
 stand-alone Biot-Savart entry point is checked against the oracle's nonlocal
 sum on rings, a periodic tangle (minimum image) and at a size spanning many
 shared-memory tiles and source splits."""
@@ -27,7 +30,7 @@ def filaments(kind, n, wall, seed=0):
         return inputs.ring(c, (0, 0, 1), 8.0, npts=64)
     if kind == "tangle":
         return inputs.random_rings(n, wall, 12, 3.0, 7.0, seed)
-    if kind == "large":  # ~8.7k points: the Biot-Savart kernel applies the equation of motion itself
+    if kind == "large":  # ~8.7k points: two targets per thread in the Biot-Savart kernel
         return inputs.random_rings(n, wall, 170, 6.0, 12.0, 11, skip_crowded=True)
     raise KeyError(kind)
 
@@ -37,14 +40,17 @@ CASES = [
     ("tangle-periodic", (32, 32, 32), (0, 0, 0), "tangle", dict(init_vn=[0.0, 0.0, 0.0116])),
     ("tangle-walls-heater", (40, 36, 48), (1, 1, 1), "tangle", dict(heater_vn=0.01, init_vn=[0.0, 0.0, 0.01])),
     ("drag-form", (32, 32, 32), (0, 0, 0), "tangle", dict(init_vn=[0.0, 0.0, 0.0116], force_form=1)),
+    ("large-accumulated", (80, 80, 80), (0, 0, 0), "large", dict(init_vn=[0.0, 0.0, 0.0116], max_points=32768)),
     ("large-fused", (80, 80, 80), (0, 0, 0), "large", dict(init_vn=[0.0, 0.0, 0.0116], max_points=32768)),
 ]
 
 
 @pytest.mark.parametrize("name,n,wall,kind,extra", CASES, ids=[c[0] for c in CASES])
-def test_advance_parity(name, n, wall, kind, extra):
+def test_advance_parity(name, n, wall, kind, extra, monkeypatch):
     import oracle
     from paper_2108_04435_gb300 import vlb
+    if name == "large-fused":
+        monkeypatch.setenv("VLB_FUSED_EOM", "1")
     xyz, nxt = filaments(kind, n, wall)
     assert kind != "large" or len(nxt) >= 8192
     p = vparams(n, wall, **extra)
