@@ -234,24 +234,45 @@ __device__ int block_small_components(const int* __restrict__ succ, uint8_t* __r
 }
 
 // One block: stable compaction of the alive points of [0, T) into the other
-// point buffer, successor indices renumbered, predecessors rebuilt.
+// point buffer, successor indices renumbered, predecessors rebuilt.  The
+// points go in chunks of blockDim.x consecutive indices, one per thread: a
+// ballot per warp and a scan over the warps rank the alive points of a chunk,
+// so every load and store of a chunk is coalesced (per-thread ranges of
+// consecutive points made each warp access touch 32 lines).
 __device__ void block_compact(const double* __restrict__ pin, const int* __restrict__ succ,
                               const uint8_t* __restrict__ alive, int T, int* __restrict__ newidx,
                               double* __restrict__ pout, int* __restrict__ nout, int* __restrict__ pvout,
                               int* __restrict__ counters, int cap) {
-    const int per = (T + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int b0 = min(T, (int)threadIdx.x * per);
-    const int b1 = min(T, b0 + per);
-    int mine = 0;
-    for (int k = b0; k < b1; ++k) mine += alive[k] ? 1 : 0;
+    __shared__ int s_off[33];  // per-warp exclusive offsets of a chunk; [32] = the chunk's count
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
     int M = 0;
-    int base = block_exclusive_scan(mine, &M);
-    for (int k = b0; k < b1; ++k) {
-        newidx[k] = alive[k] ? base : -1;
-        if (alive[k]) pvout[base++] = -1;  // first points of lines keep -1
+    for (int c0 = 0; c0 < T; c0 += blockDim.x) {
+        const int k = c0 + (int)threadIdx.x;
+        const bool a = k < T && alive[k] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, a);
+        if (lane == 0) s_off[wid] = __popc(m);
+        __syncthreads();
+        if (wid == 0) {
+            const int v = lane < nw ? s_off[lane] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < nw) s_off[lane] = x - v;
+            if (lane == 31) s_off[32] = x;
+        }
+        __syncthreads();
+        if (k < T) {
+            const int n = a ? M + s_off[wid] + __popc(m & ((1u << lane) - 1u)) : -1;
+            newidx[k] = n;
+            if (a) pvout[n] = -1;  // first points of lines keep -1
+        }
+        M += s_off[32];
+        __syncthreads();  // s_off is reused by the next chunk
     }
-    __syncthreads();
-    for (int k = b0; k < b1; ++k) {
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
         if (!alive[k]) continue;
         const int n = newidx[k];
         for (int c = 0; c < 3; ++c) pout[(long long)c * cap + n] = pin[(long long)c * cap + k];
