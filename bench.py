@@ -265,7 +265,8 @@ def run_vlb(args, ws, rank, local):
         "ms_per_step_without_graphs": round(nograph_s * 1e3 / args.steps, 4),
         "e2e": {"value": round(e2e_units / e2e_secs / 1e6, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1)},
-        "gpu_launches": launches(int(n_before), args.steps, not args.no_overlap),
+        # + 1: the line-length kernel that ends each vlb_step call
+        "gpu_launches": launches(int(n_before), args.steps, not args.no_overlap) + 1,
         "roofline": {"kernel": "k_lbm_step", "bound": "hbm",
                      "achieved": round(achieved, 1) if achieved else None,
                      "peak": pk["hbm_gbs"], "unit": "GB/s",

@@ -147,7 +147,9 @@ int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, i
  * CAPACITY, CFL, TIMEOUT).  On a created (non-default) stream each step is
  * replayed from a CUDA graph captured on first use; every kernel reads the
  * live filament count from device memory, so no host round trip is needed
- * between steps. */
+ * between steps.  When nsteps > 0 the total line length of the new points is
+ * computed at the end and read back with the status, so vlb_line_length
+ * returns it without a launch or a wait until the state changes again. */
 int vlb_step(vlb_channel* ch, int32_t nsteps);
 
 /* Enable (default) or disable the graph replay of vlb_step. */

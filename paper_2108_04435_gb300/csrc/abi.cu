@@ -63,6 +63,7 @@ struct vlb_channel {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool overlap = true;  // multi-step graphs use the second stream (vlb_set_overlap)
+    bool line_fresh = false;  // h_dstats[DS_LINE] holds the line length of the current points
     bool pending = false;
     double timing_ms = 0.0;
     long long timing_launches = 0;
@@ -655,6 +656,7 @@ void vlb_destroy(vlb_channel* ch) {
 
 int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, int32_t n) {
     if (!ch || n < 0 || (n > 0 && (!xyz || !next))) return fail(VLB_ERR_INVALID_ARG, "bad seed arguments");
+    ch->line_fresh = false;
     if (n > ch->cap || (n > 0 && ch->p.max_points == 0)) return fail(VLB_ERR_CAPACITY, "more points than max_points");
     std::vector<char> seen((size_t)n, 0);
     std::vector<double> soa(3 * (size_t)ch->cap, 0.0);
@@ -848,12 +850,21 @@ void queue_steps(vlb_channel* ch, int nsteps) {
 
 int vlb_step(vlb_channel* ch, int32_t nsteps) {
     if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
+    ch->line_fresh = false;
     queue_steps(ch, nsteps);
-    return finish(ch);
+    // the total line length of the new points rides along with the status read,
+    // so a vlb_line_length right after the steps needs no launch or wait of its own
+    if (nsteps > 0)
+        launch_line_length(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.next[ch->cur_p], ch->d.counters, ch->cap,
+                           ch->d.line_part, ch->d.dstats, ch->stream);
+    const int rc = finish(ch);
+    ch->line_fresh = rc == VLB_OK && nsteps > 0;
+    return rc;
 }
 
 int vlb_step_async(vlb_channel* ch, int32_t nsteps) {
     if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
+    ch->line_fresh = false;
     if (!ch->done && cudaEventCreateWithFlags(&ch->done, cudaEventDisableTiming) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "event create");
     queue_steps(ch, nsteps);
@@ -906,6 +917,7 @@ int vlb_set_overlap(vlb_channel* ch, int32_t enable) {
 
 int vlb_run_phases(vlb_channel* ch, int32_t mask) {
     if (!ch || mask < 0 || mask > VLB_PHASE_ALL) return fail(VLB_ERR_INVALID_ARG, "bad phase mask");
+    ch->line_fresh = false;
     run_phases(ch, mask);
     return finish(ch);
 }
@@ -991,6 +1003,7 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
 
 int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t bytes) {
     if (!ch || !src) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    ch->line_fresh = false;
     const long long C = ch->lp.g.ncell;
     Dev& d = ch->d;
     cudaStream_t s = ch->stream;
@@ -1026,6 +1039,10 @@ int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t byt
 
 int vlb_line_length(vlb_channel* ch, double* out) {
     if (!ch || !out) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    if (ch->line_fresh) {  // computed at the end of the last vlb_step
+        *out = ch->h_dstats[DS_LINE];
+        return VLB_OK;
+    }
     launch_line_length(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.next[ch->cur_p], ch->d.counters, ch->cap,
                        ch->d.line_part, ch->d.dstats, ch->stream);
     cudaMemcpyAsync(ch->h_dstats + DS_LINE, ch->d.dstats + DS_LINE, sizeof(double), cudaMemcpyDeviceToHost,

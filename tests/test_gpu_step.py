@@ -147,3 +147,20 @@ def test_cache_hints_change_nothing(storage, monkeypatch):
         g.close()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+def test_line_length_after_step_is_current():
+    """vlb_step leaves the line length of the new points with the status; it
+    equals a fresh computation after the same steps, and a call that changes
+    nothing (an empty phase mask) makes the next read compute it again."""
+    from paper_2108_04435_gb300 import configs, vlb
+    p, xyz, nxt = configs.config("channel64x64x256")
+    g = vlb.Channel(p)
+    g.seed(xyz, nxt)
+    l0 = g.line_length()
+    g.step(5)
+    cached = g.line_length()
+    g.run_phases(0)
+    fresh = g.line_length()
+    g.close()
+    assert cached == fresh and cached != l0
