@@ -234,7 +234,9 @@ def run_vlb(args, ws, rank, local):
     ch2.close()
     e2e_units, e2e_secs = aggregate(cells * args.steps, e2e_s, ws)
     h2d = (xyz.size * 8 + nxt.size * 4) / args.steps
-    d2h = 8 + 4 * 8 + 8 * 8 + final.nbytes / args.steps
+    # per vlb_step: the status block (8 doubles of statistics, the line length
+    # among them, and 12 int counters); at the end, the filaments
+    d2h = 8 * 8 + 12 * 4 + final.nbytes / args.steps
 
     pk, pk_kind = peaks()
     k1_avg_s = (k1_ms / 1e3) / max(k1_n, 1)

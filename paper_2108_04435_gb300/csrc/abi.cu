@@ -110,8 +110,7 @@ void release(vlb_channel* ch) {
                     cudaGraphExecDestroy(ch->gexec[m][a][b]);
                     ch->gexec[m][a][b] = nullptr;
                 }
-    if (ch->h_counters) cudaFreeHost(ch->h_counters);
-    if (ch->h_dstats) cudaFreeHost(ch->h_dstats);
+    if (ch->h_dstats) cudaFreeHost(ch->h_dstats);  // one pinned block: dstats, then counters
     ch->h_counters = nullptr;
     ch->h_dstats = nullptr;
 }
@@ -128,8 +127,8 @@ int status_to_code(int st, std::string* msg) {
 
 // Copy the device counters and statistics to the pinned mirrors and wait.
 int sync_counters(vlb_channel* ch) {
-    cudaMemcpyAsync(ch->h_counters, ch->d.counters, sizeof(int) * CNT_COUNT, cudaMemcpyDeviceToHost, ch->stream);
-    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, sizeof(double) * DS_COUNT, cudaMemcpyDeviceToHost, ch->stream);
+    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT,
+                    cudaMemcpyDeviceToHost, ch->stream);
     cudaError_t e = cudaStreamSynchronize(ch->stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     ch->n_hint = ch->h_counters[CNT_N];
@@ -562,8 +561,9 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.part = (double*)A(sizeof(double) * 3 * (size_t)ch->bpp * g.nz);
     d.plane = (double*)A(sizeof(double) * 3 * (size_t)g.nz);
     d.plane_ticket = (int*)A(sizeof(int) * (size_t)g.nz);
-    d.dstats = (double*)A(sizeof(double) * DS_COUNT);
-    d.counters = (int*)A(sizeof(int) * CNT_COUNT);
+    // statistics and counters in one block, read back with one copy
+    d.dstats = (double*)A(sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT);
+    d.counters = d.dstats ? (int*)(d.dstats + DS_COUNT) : nullptr;
     const size_t P3 = sizeof(double) * 3 * (size_t)cap;
     for (int b = 0; b < 2; ++b) {
         d.pos[b] = (double*)A(P3);
@@ -604,8 +604,9 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
         delete ch;
         return fail(VLB_ERR_OOM, "device allocation failed");
     }
-    if (cudaMallocHost((void**)&ch->h_counters, sizeof(int) * CNT_COUNT) != cudaSuccess ||
-        cudaMallocHost((void**)&ch->h_dstats, sizeof(double) * DS_COUNT) != cudaSuccess) {
+    if (cudaMallocHost((void**)&ch->h_dstats, sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT) == cudaSuccess)
+        ch->h_counters = (int*)(ch->h_dstats + DS_COUNT);
+    if (!ch->h_dstats) {
         release(ch);
         delete ch;
         return fail(VLB_ERR_OOM, "pinned host allocation failed");
@@ -868,8 +869,8 @@ int vlb_step_async(vlb_channel* ch, int32_t nsteps) {
     if (!ch->done && cudaEventCreateWithFlags(&ch->done, cudaEventDisableTiming) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "event create");
     queue_steps(ch, nsteps);
-    cudaMemcpyAsync(ch->h_counters, ch->d.counters, sizeof(int) * CNT_COUNT, cudaMemcpyDeviceToHost, ch->stream);
-    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, sizeof(double) * DS_COUNT, cudaMemcpyDeviceToHost, ch->stream);
+    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT,
+                    cudaMemcpyDeviceToHost, ch->stream);
     cudaEventRecord(ch->done, ch->stream);
     ch->pending = true;
     const cudaError_t e = cudaGetLastError();
