@@ -64,6 +64,7 @@ struct vlb_channel {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool overlap = true;  // multi-step graphs use the second stream (vlb_set_overlap)
     bool line_fresh = false;  // h_dstats[DS_LINE] holds the line length of the current points
+    bool side_failed = false;  // the second stream could not be created
     bool pending = false;
     double timing_ms = 0.0;
     long long timing_launches = 0;
@@ -416,18 +417,6 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
         ch->has_alloc = true;
     }
     ch->stream = (cudaStream_t)stream;
-    if (ch->stream) {
-        // the multi-step graphs fork the filament chain onto it, at the highest priority
-        int lo = 0, hi = 0;
-        cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        if (cudaStreamCreateWithPriority(&ch->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ch->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ch->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            if (ch->side) cudaStreamDestroy(ch->side);
-            ch->side = nullptr;
-        }
-    }
     Grid g;
     g.nx = p->n[0];
     g.ny = p->n[1];
@@ -735,6 +724,26 @@ int size_class(int n) {
     return c;
 }
 
+// The second stream (highest priority) and the fork/join events of the
+// overlapped graphs, created when first needed.  False if they cannot be made:
+// the graphs then keep their steps in sequence.
+bool ensure_side(vlb_channel* ch) {
+    if (ch->side) return true;
+    if (ch->side_failed) return false;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&ch->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        (!ch->ev_fork && cudaEventCreateWithFlags(&ch->ev_fork, cudaEventDisableTiming) != cudaSuccess) ||
+        (!ch->ev_join && cudaEventCreateWithFlags(&ch->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        if (ch->side) cudaStreamDestroy(ch->side);
+        ch->side = nullptr;
+        ch->side_failed = true;
+        return false;
+    }
+    return true;
+}
+
 // Steps per multi-step graph (even, so both buffer parities are restored).
 constexpr int GRAPH_MULTI = 8;
 
@@ -800,12 +809,13 @@ bool step_graph(vlb_channel* ch, bool multi) {
     }
     if (!ge) {
         cudaGraph_t graph = nullptr;
+        const bool forked = nst > 1 && ch->overlap && ensure_side(ch);  // before the capture begins
         if (cudaStreamBeginCapture(ch->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
             return undo();
         }
         tl_no_pdl = true;
-        if (nst > 1 && ch->side && ch->overlap) run_steps_forked(ch, nst);
+        if (forked) run_steps_forked(ch, nst);
         else
             for (int k = 0; k < nst; ++k) run_phases(ch, VLB_PHASE_ALL);
         tl_no_pdl = false;
