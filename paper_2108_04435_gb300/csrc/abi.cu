@@ -228,6 +228,7 @@ void vfm_step(vlb_channel* ch, bool pre_done, cudaStream_t s) {
         for (int stage = 0; stage < 4; ++stage) {
             ea.stage = stage;
             ea.spread = spread;
+            ea.first = sub == 0 ? 1 : 0;
             // below the fused size the Biot-Savart sums arrive in d.vacc
             long long* vacc = bs_uses_vacc(ch->n_hint) ? d.vacc : nullptr;
             if (pre_done && sub == 0 && stage == 0) {

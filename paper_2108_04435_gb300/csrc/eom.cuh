@@ -238,7 +238,7 @@ __device__ __forceinline__ void eom_point(const EomArgs& A, int i, bool valid, f
             const long long o = (long long)k * cap + i;
             a3[k] = stage == 0 ? kv[k] : acc[o] + wst * kv[k];
             acc[o] = a3[k];
-            if (stage == 0) A.vel1[o] = kv[k];
+            if (stage == 0 && A.first) A.vel1[o] = kv[k];
         }
         if (stage < 3) {
             for (int k = 0; k < 3; ++k) {

@@ -187,6 +187,7 @@ struct VfmParams {
 struct EomArgs {
     VfmParams P;
     int stage, spread, cap;
+    int first;          // the first sub-step of the lattice step (its stage-1 velocity is exported)
     const double* s0;   // RK4 base positions
     double* st;         // stage positions (written for the next stage)
     double* pos_out;    // new positions (last stage)
