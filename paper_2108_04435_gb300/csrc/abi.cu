@@ -705,6 +705,8 @@ int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, i
         cudaMemcpyAsync(d.prev[b], prv.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s);
     }
     cudaMemcpyAsync(d.counters + CNT_N, &n, sizeof(int), cudaMemcpyHostToDevice, s);
+    const int dirty = 1;  // the seeded loops and lines are checked for size by the next remesh
+    cudaMemcpyAsync(d.counters + CNT_DIRTY, &dirty, sizeof(int), cudaMemcpyHostToDevice, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "seed copy");
     ch->n_hint = n;

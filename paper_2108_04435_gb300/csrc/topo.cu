@@ -379,9 +379,19 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
     }
     const int T = N + S;
     __syncthreads();
-    const int dead = block_small_components(
-        nnext, alive, T, [&](int k) { return k < N && prev[k] < 0; }, counters);
+    // Splits only add points, so without removals no loop or line shrinks
+    // below five points here (every one had five or more after the last
+    // reconnection pass), unless the points were just seeded.
+    __shared__ int s_check;
     const int removed_all = block_sum(removed);
+    if (threadIdx.x == 0) {
+        s_check = removed_all > 0 || counters[CNT_DIRTY] != 0;
+        counters[CNT_DIRTY] = 0;
+    }
+    __syncthreads();
+    const int dead = s_check ? block_small_components(
+                                   nnext, alive, T, [&](int k) { return k < N && prev[k] < 0; }, counters)
+                             : 0;
     const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) {
         dstats[DS_SPLITS] += (double)S;
@@ -546,6 +556,7 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
         alive[k] = 1;
         hhead[hkey[k]] = -1;
     }
+    __shared__ int s_changed;  // an exchange or a cut happened: small components may have formed
     __syncthreads();
     if (threadIdx.x == 0) {
         const int st = counters[CNT_STAMP] + 1;
@@ -567,6 +578,8 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
             ++applied;
         }
         dstats[DS_RECON] += (double)applied;
+        s_changed = applied > 0 || counters[CNT_DIRTY] != 0;  // (seeded points not yet remeshed: check them)
+        counters[CNT_DIRTY] = 0;
     }
     __syncthreads();
     // Wall contact: the candidates listed by k_pairs, put in ascending index
@@ -600,9 +613,11 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
             ++cuts;
         }
         dstats[DS_WALLCUT] += (double)cuts;
+        if (cuts > 0) s_changed = 1;
     }
     __syncthreads();
-    const int dead = block_small_components(next, alive, N, [&](int k) { return prev[k] < 0; }, counters);
+    const int dead =
+        s_changed ? block_small_components(next, alive, N, [&](int k) { return prev[k] < 0; }, counters) : 0;
     const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) dstats[DS_SMALL] += (double)dead_all;
     __syncthreads();

@@ -31,6 +31,7 @@ enum : int {
     CNT_PLANES = 7,     // z planes reduced in the current lattice pass
     CNT_LINEDONE = 8,   // blocks done in the line-length reduction
     CNT_NCONTACT = 9,   // wall-contact candidates of the current reconnection pass
+    CNT_DIRTY = 10,     // 1 after seeding: the next remesh checks for small components even without removals
     CNT_COUNT = 12
 };
 
