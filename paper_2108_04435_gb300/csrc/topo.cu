@@ -239,10 +239,23 @@ __device__ int block_small_components(const int* __restrict__ succ, uint8_t* __r
 // ballot per warp and a scan over the warps rank the alive points of a chunk,
 // so every load and store of a chunk is coalesced (per-thread ranges of
 // consecutive points made each warp access touch 32 lines).
+// identity_prev != nullptr (uniform): every point of [0, T) survives in place
+// and the links are unchanged, so the arrays are copied as they are.
 __device__ void block_compact(const double* __restrict__ pin, const int* __restrict__ succ,
                               const uint8_t* __restrict__ alive, int T, int* __restrict__ newidx,
                               double* __restrict__ pout, int* __restrict__ nout, int* __restrict__ pvout,
-                              int* __restrict__ counters, int cap) {
+                              int* __restrict__ counters, int cap, const int* __restrict__ identity_prev = nullptr) {
+    if (identity_prev) {
+        for (int k = threadIdx.x; k < T; k += blockDim.x) {
+            for (int c = 0; c < 3; ++c) pout[(long long)c * cap + k] = pin[(long long)c * cap + k];
+            nout[k] = succ[k];
+            pvout[k] = identity_prev[k];
+            newidx[k] = k;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) counters[CNT_N] = T;
+        return;
+    }
     __shared__ int s_off[33];  // per-warp exclusive offsets of a chunk; [32] = the chunk's count
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
     int M = 0;
@@ -393,13 +406,15 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
                                    nnext, alive, T, [&](int k) { return k < N && prev[k] < 0; }, counters)
                              : 0;
     const int dead_all = block_sum(dead);
+    __shared__ int s_same;  // no split, removal or deletion: points and links pass through unchanged
     if (threadIdx.x == 0) {
         dstats[DS_SPLITS] += (double)S;
         dstats[DS_MERGES] += (double)removed_all;
         dstats[DS_SMALL] += (double)dead_all;
+        s_same = S == 0 && removed_all == 0 && dead_all == 0;
     }
     __syncthreads();
-    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap);
+    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap, s_same ? prev : nullptr);
 }
 
 // -------------------------------------------------------------- reconnect
@@ -621,7 +636,8 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     const int dead_all = block_sum(dead);
     if (threadIdx.x == 0) dstats[DS_SMALL] += (double)dead_all;
     __syncthreads();
-    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap);
+    // no exchange and no cut: the points and links pass through unchanged
+    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, s_changed ? nullptr : prev);
 }
 
 }  // namespace
