@@ -118,3 +118,35 @@ def test_empty_and_capacity():
     rc = g2.run_phases(vlb.PHASE_REMESH, raise_on_error=False)
     assert rc == -3
     assert g2.n_points() == 40
+
+
+@pytest.mark.parametrize("phase", ["remesh", "reconnect", "step"])
+def test_seeded_small_loop_deleted(phase):
+    """A seeded loop of four points dies in the first remesh or reconnection
+    pass that follows the seeding, even when that pass removes, exchanges and
+    cuts nothing: the finishers skip the small-component check only when
+    nothing could have shortened a loop, and seeding asks for one check."""
+    import oracle
+    from paper_2108_04435_gb300 import inputs, vlb
+    n, wall = (32, 32, 32), (0, 0, 0)
+    big, nbig = inputs.ring((16.0, 16.0, 8.0), (0.0, 0.0, 1.0), 6.0, npts=48)
+    small, nsmall = inputs.ring((16.0, 16.0, 24.0), (0.0, 0.0, 1.0), 0.45, npts=4)
+    xyz, nxt = inputs.concat([(big, nbig), (small, nsmall)])
+    p = tparams(n, wall, dxi_min=0.2, dxi_max=0.95)
+    g, r = pair(p, xyz, nxt)
+    if phase == "remesh":
+        g.run_phases(vlb.PHASE_REMESH)
+        r.run_phases(oracle.PHASE_REMESH)
+    elif phase == "reconnect":
+        g.run_phases(vlb.PHASE_RECONNECT)
+        r.run_phases(oracle.PHASE_RECONNECT)
+    else:  # a whole step: the advance is FP32 against FP64, the topology still exact
+        g.step(1)
+        r.step(1)
+        assert g.n_points() == r.n_points() == len(nbig)
+        assert np.array_equal(g.read(vlb.FIELD_NEXT), r.read(oracle.FIELD_NEXT))
+        pg, pr = g.read(vlb.FIELD_POS), r.read(oracle.FIELD_POS)
+        assert np.linalg.norm(pg - pr) < 1e-5 * np.linalg.norm(pr)
+        return
+    assert_same_points(g, r)
+    assert g.n_points() == len(nbig)
