@@ -255,11 +255,11 @@ void run_phases_body(vlb_channel* ch, int mask) {
     if (mask & VLB_PHASE_LBM) phase_lbm(ch);
     if (mask & VLB_PHASE_VFM) phase_vfm(ch);
     if (mask & VLB_PHASE_REMESH) {
-        launch_remesh(ch->vp, ch->d, ch->cur_p, ch->cap, ch->stream);
+        launch_remesh(ch->vp, ch->d, ch->cur_p, ch->cap, point_span(ch->n_hint, ch->cap), ch->stream);
         ch->cur_p ^= 1;
     }
     if (mask & VLB_PHASE_RECONNECT) {
-        launch_reconnect(ch->vp, ch->d, ch->cur_p, ch->cap, ch->hsize, ch->stream);
+        launch_reconnect(ch->vp, ch->d, ch->cur_p, ch->cap, point_span(ch->n_hint, ch->cap), ch->hsize, ch->stream);
         ch->cur_p ^= 1;
     }
 }
@@ -399,7 +399,7 @@ size_t vlb_channel_bytes(const vlb_params* p) {
     b += 2 * (up(24 * cap) + 2 * up(4 * cap)) + 6 * up(24 * cap) + up(8 * cap) + up(32 * cap) +
          up(48 * cap * (1 + nfaces));
     b += up(12 * cap * (size_t)bs_max_splits((int)cap)) + up(12 * cap) + up(24 * cap) + up(4 * ((cap + 127) / 128));
-    b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(8 * cap);
+    b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(16 * cap) + up(8 * cap);
     const size_t nc = cap / 2 + 1;
     b += 4 * up(4 * nc) + up(8 * nc) + up(4 * cap) + up(8 * ((cap + 255) / 256));
     return b;
@@ -579,6 +579,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.hkey = (int*)A(sizeof(int) * (size_t)cap);
     d.hhead = (int*)A(sizeof(int) * (size_t)h);
     d.hlink = (int*)A(sizeof(int) * (size_t)cap);
+    d.hpos = (float4*)A(sizeof(float4) * (size_t)cap);
     d.nn = (int*)A(sizeof(int) * (size_t)cap);
     d.nd2 = (double*)A(sizeof(double) * (size_t)cap);
     const size_t nc = (size_t)cap / 2 + 1;
@@ -778,9 +779,9 @@ void run_steps_forked(vlb_channel* ch, int nst) {
             lattice_pass(ch, true);
             cudaEventRecord(ch->ev_join, ch->stream);
         }
-        launch_remesh(ch->vp, d, ch->cur_p, ch->cap, ch->side);
+        launch_remesh(ch->vp, d, ch->cur_p, ch->cap, point_span(ch->n_hint, ch->cap), ch->side);
         ch->cur_p ^= 1;
-        launch_reconnect(ch->vp, d, ch->cur_p, ch->cap, ch->hsize, ch->side);
+        launch_reconnect(ch->vp, d, ch->cur_p, ch->cap, point_span(ch->n_hint, ch->cap), ch->hsize, ch->side);
         ch->cur_p ^= 1;
         if (s + 1 < nst) {
             if (pre) vfm_pre(ch, ch->side);

@@ -119,15 +119,10 @@ __device__ int block_exclusive_scan(int v, int* total) {
 // the non-uniform arc-length grid (a = s_i - s_p, b = s_q - s_i); an open
 // end on a wall uses the mirror image of its neighbour across the wall, and a
 // line's last point has seglen 0.
-__global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double* __restrict__ s,
-                                                       const int* __restrict__ next, const int* __restrict__ prev,
-                                                       const int* __restrict__ counters, int cap,
-                                                       double* __restrict__ spp, double* __restrict__ seglen,
-                                                       uint8_t* __restrict__ flags) {
-    pdl_wait_trigger();
-    const int N = counters[CNT_N];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+__device__ __forceinline__ void geometry_exact_point(const VfmParams& P, const double* __restrict__ s,
+                                                     const int* __restrict__ next, const int* __restrict__ prev,
+                                                     int cap, int i, double* __restrict__ spp,
+                                                     double* __restrict__ seglen, uint8_t* __restrict__ flags) {
     const int p = prev[i], q = next[i];
     const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
     double si[3], sp[3], sq[3], a[3], b[3];
@@ -180,6 +175,17 @@ __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double
         cand = (lmin < P.dmin) && (lpq <= P.dmax) && !split_p && !split;
     }
     flags[i] = (uint8_t)((split ? 1 : 0) | (cand ? 2 : 0));
+}
+
+__global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double* __restrict__ s,
+                                                       const int* __restrict__ next, const int* __restrict__ prev,
+                                                       const int* __restrict__ counters, int cap,
+                                                       double* __restrict__ spp, double* __restrict__ seglen,
+                                                       uint8_t* __restrict__ flags) {
+    pdl_wait_trigger();
+    const int N = counters[CNT_N];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        geometry_exact_point(P, s, next, prev, cap, i, spp, seglen, flags);
 }
 
 // ------------------------------------------------------------------ remesh
@@ -424,92 +430,115 @@ __device__ __forceinline__ uint32_t cell_hash(int cx, int cy, int cz) {
 }
 
 // Unit-cell hash of the points: bucket heads (kept at -1 between passes) and a
-// link per point, filled with atomicExch; bucket order does not matter.
+// link per point, filled with atomicExch; bucket order does not matter.  The
+// link is also stored beside the point's FP32 position in hpos, the record
+// the nearest-point search walks.
 __global__ void k_hash_insert(const double* __restrict__ pos, int* __restrict__ counters, int cap,
                               uint32_t hmask, int* __restrict__ hkey, int* __restrict__ hhead,
-                              int* __restrict__ hlink) {
+                              int* __restrict__ hlink, float4* __restrict__ hpos) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
         counters[CNT_NPAIRS] = 0;
         counters[CNT_NCONTACT] = 0;
     }
-    if (i >= N) return;
-    const int cx = (int)floor(pos[i]), cy = (int)floor(pos[(long long)cap + i]), cz = (int)floor(pos[2LL * cap + i]);
-    const int h = (int)(cell_hash(cx, cy, cz) & hmask);
-    hkey[i] = h;
-    hlink[i] = atomicExch(&hhead[h], i);
+    for (int i = t; i < N; i += gridDim.x * blockDim.x) {
+        const double x = pos[i], y = pos[(long long)cap + i], z = pos[2LL * cap + i];
+        const int h = (int)(cell_hash((int)floor(x), (int)floor(y), (int)floor(z)) & hmask);
+        hkey[i] = h;
+        const int link = atomicExch(&hhead[h], i);
+        hlink[i] = link;
+        hpos[i] = make_float4(__double2float_rn(x), __double2float_rn(y), __double2float_rn(z), __int_as_float(link));
+    }
+}
+
+__device__ __forceinline__ float min_image_f(const Grid& g, int axis, float d) {
+    if (!g.wall[axis]) {
+        const float L = (float)(axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz));
+        if (d > 0.5f * L) d -= L;
+        else if (d < -0.5f * L) d += L;
+    }
+    return d;
 }
 
 // Nearest point within dxi_max outside the two-link neighbourhood.  Every
 // point closer than dxi_max < 1 lies in one of the 27 unit cells around; one
 // warp per point, lane l < 27 walks the bucket of cell l, then the warp takes
-// the minimum of (d^2, j).
-__global__ void __launch_bounds__(128) k_nearest(VfmParams P, double dmax2, const double* __restrict__ pos,
+// the minimum of (d^2, j).  The walk reads the FP32 records of hpos and skips
+// a point whose FP32 distance squared exceeds r2f, a bound above which the
+// FP64 distance is certainly not below dxi_max (nearest_filter_r2); the
+// others are decided in FP64 exactly as without the filter.
+__global__ void __launch_bounds__(128) k_nearest(VfmParams P, double dmax2, float r2f, const double* __restrict__ pos,
                                                  const int* __restrict__ next, const int* __restrict__ prev,
                                                  const int* __restrict__ counters, int cap, uint32_t hmask,
-                                                 const int* __restrict__ hhead, const int* __restrict__ hlink,
+                                                 const int* __restrict__ hhead, const float4* __restrict__ hpos,
                                                  int* __restrict__ nn, double* __restrict__ nd2) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
-    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= N) return;  // whole warp
-    const int p = prev[i], q = next[i], pp = p >= 0 ? prev[p] : -1, qq = q >= 0 ? next[q] : -1;
-    double xi[3];
-    int c[3];
-    for (int k = 0; k < 3; ++k) {
-        xi[k] = pos[(long long)k * cap + i];
-        c[k] = (int)floor(xi[k]);
-    }
-    int best = -1;
-    double bd = 0.0;
-    if (lane < 27) {
-        const int n[3] = {P.g.nx, P.g.ny, P.g.nz};
-        int cc[3] = {c[0] + lane % 3 - 1, c[1] + (lane / 3) % 3 - 1, c[2] + lane / 9 - 1};
-        for (int a = 0; a < 3; ++a)
-            if (!P.g.wall[a]) cc[a] = ((cc[a] % n[a]) + n[a]) % n[a];
-        const int h = (int)(cell_hash(cc[0], cc[1], cc[2]) & hmask);
-        int j = hhead[h];
-        for (int guard = 0; j >= 0 && guard < N; ++guard, j = hlink[j]) {
-            if (j == i || j == p || j == q || j == pp || j == qq) continue;
-            double d[3];
-            for (int k = 0; k < 3; ++k) d[k] = min_image(P.g, k, pos[(long long)k * cap + j] - xi[k]);
-            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (!(d2 < dmax2)) continue;
-            if (best < 0 || d2 < bd || (d2 == bd && j < best)) {
-                best = j;
-                bd = d2;
+    const int lane = threadIdx.x & 31, wpb = (int)(blockDim.x >> 5);
+    // one point per warp at a time: i is uniform over the warp
+    for (int i = (int)blockIdx.x * wpb + (int)(threadIdx.x >> 5); i < N; i += (int)gridDim.x * wpb) {
+        const int p = prev[i], q = next[i], pp = p >= 0 ? prev[p] : -1, qq = q >= 0 ? next[q] : -1;
+        const float4 fi = hpos[i];
+        int best = -1;
+        double bd = 0.0;
+        if (lane < 27) {
+            double xi[3];
+            int c[3];
+            for (int k = 0; k < 3; ++k) {
+                xi[k] = pos[(long long)k * cap + i];
+                c[k] = (int)floor(xi[k]);
+            }
+            const int n[3] = {P.g.nx, P.g.ny, P.g.nz};
+            int cc[3] = {c[0] + lane % 3 - 1, c[1] + (lane / 3) % 3 - 1, c[2] + lane / 9 - 1};
+            for (int a = 0; a < 3; ++a)
+                if (!P.g.wall[a]) cc[a] = ((cc[a] % n[a]) + n[a]) % n[a];
+            const int h = (int)(cell_hash(cc[0], cc[1], cc[2]) & hmask);
+            int j = hhead[h];
+            for (int guard = 0; j >= 0 && guard < N; ++guard) {
+                const float4 fj = hpos[j];
+                const int jn = __float_as_int(fj.w);
+                const float e0 = min_image_f(P.g, 0, fj.x - fi.x), e1 = min_image_f(P.g, 1, fj.y - fi.y),
+                            e2 = min_image_f(P.g, 2, fj.z - fi.z);
+                const bool skip = j == i || j == p || j == q || j == pp || j == qq || e0 * e0 + e1 * e1 + e2 * e2 > r2f;
+                if (!skip) {
+                    double d[3];
+                    for (int k = 0; k < 3; ++k) d[k] = min_image(P.g, k, pos[(long long)k * cap + j] - xi[k]);
+                    const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (d2 < dmax2 && (best < 0 || d2 < bd || (d2 == bd && j < best))) {
+                        best = j;
+                        bd = d2;
+                    }
+                }
+                j = jn;
             }
         }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const int ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
-        if (ob >= 0 && (best < 0 || od < bd || (od == bd && ob < best))) {
-            best = ob;
-            bd = od;
+        for (int o = 16; o > 0; o >>= 1) {
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+            if (ob >= 0 && (best < 0 || od < bd || (od == bd && ob < best))) {
+                best = ob;
+                bd = od;
+            }
         }
-    }
-    if (lane == 0) {
-        nn[i] = best;
-        nd2[i] = bd;
+        if (lane == 0) {
+            nn[i] = best;
+            nd2[i] = bd;
+        }
     }
 }
 
 // Candidate exchanges of the mutual nearest pairs, and the wall-contact
 // candidates (points with both neighbours on a wall's clamp bound; exchanges
 // change neither property), each appended to its list.
-__global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
-                        const int* __restrict__ prev, const int* __restrict__ nn, const double* __restrict__ nd2,
-                        int* __restrict__ counters, int cap, int* __restrict__ cand_i, int* __restrict__ cand_a,
-                        int* __restrict__ cand_b, double* __restrict__ cand_d2, int* __restrict__ clist) {
-    pdl_wait_trigger();
-    const int N = counters[CNT_N];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+__device__ __forceinline__ void pair_candidates(const VfmParams& P, const double* __restrict__ pos,
+                                                const int* __restrict__ next, const int* __restrict__ prev,
+                                                const int* __restrict__ nn, const double* __restrict__ nd2,
+                                                int* __restrict__ counters, int cap, int i, int* __restrict__ cand_i,
+                                                int* __restrict__ cand_a, int* __restrict__ cand_b,
+                                                double* __restrict__ cand_d2, int* __restrict__ clist) {
     const int pi = prev[i];
     if (P.g.wall[0] | P.g.wall[1] | P.g.wall[2]) {
         if (pi >= 0 && next[i] >= 0 && touching_wall(P.g, P.dmin, pos, cap, i) >= 0)
@@ -540,6 +569,17 @@ __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* 
     cand_a[slot] = pa;
     cand_b[slot] = pb;
     cand_d2[slot] = nd2[i];
+}
+
+// The candidates of every point, one thread per point.
+__global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
+                        const int* __restrict__ prev, const int* __restrict__ nn, const double* __restrict__ nd2,
+                        int* __restrict__ counters, int cap, int* __restrict__ cand_i, int* __restrict__ cand_a,
+                        int* __restrict__ cand_b, double* __restrict__ cand_d2, int* __restrict__ clist) {
+    pdl_wait_trigger();
+    const int N = counters[CNT_N];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        pair_candidates(P, pos, next, prev, nn, nd2, counters, cap, i, cand_i, cand_a, cand_b, cand_d2, clist);
 }
 
 // One block finishes the reconnection: candidates in ascending (d^2, i)
@@ -642,9 +682,9 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
 
 }  // namespace
 
-void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s) {
+void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, int span, cudaStream_t s) {
     if (cap <= 0) return;
-    launch_pdl(k_geometry_exact, (cap + 63) / 64, 64, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap,
+    launch_pdl(k_geometry_exact, (span + 63) / 64, 64, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap,
                d.spp, d.seglen, d.flags);
     launch_pdl(k_remesh_finish, 1, 1024, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
                                        d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1],
@@ -653,16 +693,39 @@ void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s)
 
 void init_hash(Dev& d, int hsize, cudaStream_t s) { cudaMemsetAsync(d.hhead, 0xff, sizeof(int) * (size_t)hsize, s); }
 
-void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, cudaStream_t s) {
+// The FP32 bound of the nearest-point search.  Positions lie within
+// [-0.5, L] on every axis (L the largest extent), so the FP32 roundings of
+// the two coordinates, of their difference and of the periodic shift err by
+// at most 5 L 2^-24 on an axis together: an FP32 distance vector is within
+// 5 sqrt(3) L 2^-24 < 9 L 2^-24 of the FP64 one, wherever both take the same
+// periodic image.  Where they
+// take different images (a difference within that error of L/2), both
+// distances are near L/2 > dxi_max + the margin, which holds when every
+// periodic extent is 4 or more; otherwise the filter is off.  The bound
+// (dxi_max + 16 L 2^-24)^2 (1 + 2^-20), rounded up to FP32, also covers the
+// roundings of the squared sum.
+float nearest_filter_r2(const VfmParams& P) {
+    const int n[3] = {P.g.nx, P.g.ny, P.g.nz};
+    double L = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (!P.g.wall[a] && n[a] < 4) return INFINITY;
+        L = fmax(L, (double)n[a]);
+    }
+    const double r = P.dmax + 16.0 * L * ldexp(1.0, -24);
+    const float r2 = (float)(r * r * (1.0 + ldexp(1.0, -20)));
+    return nextafterf(r2, INFINITY);
+}
+
+void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int span, int hsize, cudaStream_t s) {
     if (cap <= 0) return;
-    const int nb = (cap + 255) / 256;
     const uint32_t hmask = (uint32_t)hsize - 1u;
     const double dmax2 = P.dmax * P.dmax;
-    launch_pdl(k_hash_insert, nb, 256, 0, s, d.pos[cur], d.counters, cap, hmask, d.hkey, d.hhead, d.hlink);
-    launch_pdl(k_nearest, (cap + 3) / 4, 128, 0, s, P, dmax2, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap, hmask,
-                                            d.hhead, d.hlink, d.nn, d.nd2);
-    launch_pdl(k_pairs, nb, 256, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap, d.cand_i,
-                               d.cand_a, d.cand_b, d.cand_d2, d.hlink);
+    launch_pdl(k_hash_insert, (span + 255) / 256, 256, 0, s, d.pos[cur], d.counters, cap, hmask, d.hkey, d.hhead, d.hlink,
+               d.hpos);
+    launch_pdl(k_nearest, (span + 3) / 4, 128, 0, s, P, dmax2, nearest_filter_r2(P), d.pos[cur], d.next[cur], d.prev[cur],
+               d.counters, cap, hmask, d.hhead, d.hpos, d.nn, d.nd2);
+    launch_pdl(k_pairs, (span + 63) / 64, 64, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap,
+               d.cand_i, d.cand_a, d.cand_b, d.cand_d2, d.hlink);
     launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.hlink, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
                                           d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,

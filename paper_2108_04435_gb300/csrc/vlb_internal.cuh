@@ -256,6 +256,7 @@ struct Dev {
     int* hkey;
     int* hhead;         // first point of each hash bucket (-1 empty), kept all -1 between passes
     int* hlink;         // next point in the same bucket
+    float4* hpos;       // per point: FP32 position and (as int bits) hlink, read by the nearest-point search
     int* nn;
     double* nd2;
     int* cand_i;
@@ -328,8 +329,16 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
                   size_t scratch_bytes, void* stream);
 
 // topo.cu
-void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s);
-void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int hsize, cudaStream_t s);
+// Points one pass of a per-point grid covers: the top of the power-of-two
+// class of the last known count n (graphs are captured again when the count
+// leaves its class), at most cap.  The kernels stride over any points beyond.
+inline int point_span(int n, int cap) {
+    long long t = 2;
+    while (t <= n) t <<= 1;
+    return (int)(t < cap ? t : cap);
+}
+void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, int span, cudaStream_t s);
+void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int span, int hsize, cudaStream_t s);
 void init_hash(Dev& d, int hsize, cudaStream_t s);
 
 }  // namespace vlb

@@ -95,6 +95,44 @@ def test_reconnect_dense_tangle_bit_exact(seed, wall):
     assert r.stats()[7] > 0
 
 
+@pytest.mark.parametrize("rel", [-1e-12, 1e-12])
+def test_reconnect_at_the_threshold_far_from_origin(rel):
+    """Two squares whose facing sides are dxi_max (1 + rel) apart, 250 cells
+    along a 256-cell axis: the pairs just inside dxi_max reconnect and those
+    just outside do not, exactly as the FP64 oracle decides (the FP32 bound
+    that prunes the nearest-point search drops no point inside dxi_max)."""
+    import oracle
+    from paper_2108_04435_gb300 import vlb
+    p = tparams((256, 8, 8), (0, 0, 0))
+    d = p["dxi_max"] * (1.0 + rel)
+    sq = 1.2 * np.array([(0, 0), (1, 0), (2, 0), (2, 1), (2, 2), (1, 2), (0, 2), (0, 1)])
+    A = np.c_[sq + [250.0, 2.0], np.full(8, 4.0)]
+    B = np.c_[sq + [252.4 + d, 2.0], np.full(8, 4.0)]
+    xyz = np.r_[A, B]
+    nxt = np.r_[(np.arange(8) + 1) % 8, 8 + (np.arange(8) + 1) % 8].astype(np.int32)
+    g, r = pair(p, xyz, nxt)
+    g.run_phases(vlb.PHASE_RECONNECT)
+    r.run_phases(oracle.PHASE_RECONNECT)
+    assert_same_points(g, r)
+    assert r.stats()[7] == (1 if rel < 0 else 0)
+
+
+def test_remesh_then_reconnect_past_the_grid_span():
+    """Remeshing doubles the points within one launch sequence, so the
+    reconnection kernels, whose grids cover the count known before it (rounded
+    up to a power of two), stride over the points beyond their grid."""
+    import oracle
+    from paper_2108_04435_gb300 import vlb
+    n, wall = (24, 24, 24), (0, 0, 0)
+    xyz, nxt = jittered_tangle(n, wall, 20, 5, 0.02, 1.02)
+    assert 512 < len(xyz) < 1024
+    g, r = pair(tparams(n, wall), xyz, nxt)
+    g.run_phases(vlb.PHASE_REMESH | vlb.PHASE_RECONNECT)
+    r.run_phases(oracle.PHASE_REMESH | oracle.PHASE_RECONNECT)
+    assert_same_points(g, r)
+    assert r.n_points() > 1024 and r.stats()[7] > 0
+
+
 def test_empty_and_capacity():
     from paper_2108_04435_gb300 import inputs, vlb
     p = tparams((16, 16, 16), (0, 0, 0), max_points=100)
