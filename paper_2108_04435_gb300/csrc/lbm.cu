@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "vlb_internal.cuh"
 
 namespace vlb {
@@ -311,10 +313,13 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
 // the planes in a fixed order.  FP64 work is spread over many SMs because
 // its per-SM rate is low on this GPU.  The stream-collide pass has consumed
 // the force grid: one warp per tile resets it in the flagged tiles, then
-// both tile flags are cleared for the next step.
+// both tile flags are cleared for the next step.  The first nplane blocks
+// hold the plane warps; the grid has enough blocks beyond them for about
+// one tile per warp, since a warp that resets tile after tile is a long
+// chain of dependent address arithmetic and stores.
 __global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ part, int bpp, LbmParams P,
                                                   long long* __restrict__ F, uint8_t* __restrict__ umask,
-                                                  uint8_t* __restrict__ fmask, int ntiles) {
+                                                  uint8_t* __restrict__ fmask, int ntiles, int nplane) {
     pdl_wait_trigger();
     {
         const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -323,6 +328,7 @@ __global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ par
         for (int t = warp; t < ntiles; t += nwarps) {
             if (fmask[t]) {
                 const int tx = t % g.tnx, ty = (t / g.tnx) % g.tny, tz = t / (g.tnx * g.tny);
+#pragma unroll 4
                 for (int k = ln; k < 512; k += 32) {
                     const int x = (tx << TILE_SHIFT) + (k & 7), y = (ty << TILE_SHIFT) + ((k >> 3) & 7),
                               z = (tz << TILE_SHIFT) + (k >> 6);
@@ -339,6 +345,7 @@ __global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ par
             if (ln == 0) umask[t] = 0;
         }
     }
+    if ((int)blockIdx.x >= nplane) return;  // a tile-only block (uniform)
     __shared__ double s_tot[256], s_mass[256], s_max[256];
     __shared__ int s_last;
     const int nz = P.g.nz;
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ par
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(&P.counters[CNT_PLANES], 1) == (int)gridDim.x - 1;
+        s_last = atomicAdd(&P.counters[CNT_PLANES], 1) == nplane - 1;
     }
     __syncthreads();
     if (!s_last) return;
@@ -903,7 +910,9 @@ int lbm_blocks_per_plane(const LbmParams& P) {
 void launch_plane_vs(const LbmParams& P, const double* part, long long* F, uint8_t* umask, uint8_t* fmask,
                      cudaStream_t s) {
     const int bpp = lbm_blocks_per_plane(P);
-    launch_pdl(k_plane_vs, (P.g.nz + 7) / 8, 256, 0, s, part, bpp, P, F, umask, fmask, P.g.tnx * P.g.tny * P.g.tnz);
+    const int ntiles = P.g.tnx * P.g.tny * P.g.tnz, nplane = (P.g.nz + 7) / 8;
+    const int nblk = std::max(nplane, std::min((ntiles + 7) / 8, 1216));  // at most 8 blocks per SM of 152
+    launch_pdl(k_plane_vs, nblk, 256, 0, s, part, bpp, P, F, umask, fmask, ntiles, nplane);
 }
 
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,
