@@ -682,13 +682,22 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
 
 }  // namespace
 
-void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, int span, cudaStream_t s) {
+void launch_remesh_geometry(const VfmParams& P, Dev& d, int cur, int cap, int span, cudaStream_t s) {
     if (cap <= 0) return;
     launch_pdl(k_geometry_exact, (span + 63) / 64, 64, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.counters, cap,
                d.spp, d.seglen, d.flags);
+}
+
+void launch_remesh_finish(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s) {
+    if (cap <= 0) return;
     launch_pdl(k_remesh_finish, 1, 1024, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
                                        d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1],
                                        d.counters, d.dstats, cap);
+}
+
+void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, int span, cudaStream_t s) {
+    launch_remesh_geometry(P, d, cur, cap, span, s);
+    launch_remesh_finish(P, d, cur, cap, s);
 }
 
 void init_hash(Dev& d, int hsize, cudaStream_t s) { cudaMemsetAsync(d.hhead, 0xff, sizeof(int) * (size_t)hsize, s); }

@@ -337,6 +337,10 @@ inline int point_span(int n, int cap) {
     while (t <= n) t <<= 1;
     return (int)(t < cap ? t : cap);
 }
+// remesh = geometry (FP64 lengths, curvature, flags; reads the points only)
+// then the single-block finish, which writes the other point buffer
+void launch_remesh_geometry(const VfmParams& P, Dev& d, int cur, int cap, int span, cudaStream_t s);
+void launch_remesh_finish(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s);
 void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, int span, cudaStream_t s);
 void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int span, int hsize, cudaStream_t s);
 void init_hash(Dev& d, int hsize, cudaStream_t s);
