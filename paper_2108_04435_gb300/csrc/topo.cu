@@ -119,7 +119,7 @@ __device__ int block_exclusive_scan(int v, int* total) {
 // the non-uniform arc-length grid (a = s_i - s_p, b = s_q - s_i); an open
 // end on a wall uses the mirror image of its neighbour across the wall, and a
 // line's last point has seglen 0.
-__device__ __forceinline__ void geometry_exact_point(const VfmParams& P, const double* __restrict__ s,
+__device__ __forceinline__ bool geometry_exact_point(const VfmParams& P, const double* __restrict__ s,
                                                      const int* __restrict__ next, const int* __restrict__ prev,
                                                      int cap, int i, double* __restrict__ spp,
                                                      double* __restrict__ seglen, uint8_t* __restrict__ flags) {
@@ -175,17 +175,20 @@ __device__ __forceinline__ void geometry_exact_point(const VfmParams& P, const d
         cand = (lmin < P.dmin) && (lpq <= P.dmax) && !split_p && !split;
     }
     flags[i] = (uint8_t)((split ? 1 : 0) | (cand ? 2 : 0));
+    return split || cand;
 }
 
 __global__ void __launch_bounds__(64) k_geometry_exact(VfmParams P, const double* __restrict__ s,
                                                        const int* __restrict__ next, const int* __restrict__ prev,
-                                                       const int* __restrict__ counters, int cap,
+                                                       int* __restrict__ counters, int cap,
                                                        double* __restrict__ spp, double* __restrict__ seglen,
                                                        uint8_t* __restrict__ flags) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
+    bool any = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        geometry_exact_point(P, s, next, prev, cap, i, spp, seglen, flags);
+        any |= geometry_exact_point(P, s, next, prev, cap, i, spp, seglen, flags);
+    if (__ballot_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(&counters[CNT_RFLAGS], 1);
 }
 
 // ------------------------------------------------------------------ remesh
@@ -340,6 +343,18 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
                                                          double* __restrict__ dstats, int cap) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
+    __shared__ int s_any;
+    if (threadIdx.x == 0) {
+        s_any = counters[CNT_RFLAGS] | counters[CNT_DIRTY];
+        counters[CNT_RFLAGS] = 0;
+    }
+    __syncthreads();
+    if (!s_any) {
+        // no split, no removal candidate and nothing newly seeded: the points
+        // and links pass through unchanged (what the full pass concludes too)
+        block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, prev);
+        return;
+    }
     const int per = (N + (int)blockDim.x - 1) / (int)blockDim.x;
     const int b0 = min(N, (int)threadIdx.x * per);
     const int b1 = min(N, b0 + per);
@@ -597,6 +612,17 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int K = counters[CNT_NPAIRS];
+    __shared__ int s_quiet;
+    if (threadIdx.x == 0) s_quiet = K == 0 && counters[CNT_NCONTACT] == 0 && counters[CNT_DIRTY] == 0;
+    __syncthreads();
+    if (s_quiet) {
+        // no candidate exchange, no wall contact and nothing newly seeded:
+        // empty the hash buckets and pass the points and links through
+        for (int k = threadIdx.x; k < N; k += blockDim.x) hhead[hkey[k]] = -1;
+        if (threadIdx.x == 0) counters[CNT_STAMP] += 1;
+        block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, prev);
+        return;
+    }
     for (int c = threadIdx.x; c < K; c += blockDim.x) {
         const double d = cand_d2[c];
         const int ic = cand_i[c];

@@ -32,6 +32,7 @@ enum : int {
     CNT_LINEDONE = 8,   // blocks done in the line-length reduction
     CNT_NCONTACT = 9,   // wall-contact candidates of the current reconnection pass
     CNT_DIRTY = 10,     // 1 after seeding: the next remesh checks for small components even without removals
+    CNT_RFLAGS = 11,    // nonzero when the remesh geometry flagged a split or removal candidate (cleared by the finish)
     CNT_COUNT = 12
 };
 
