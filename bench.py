@@ -214,27 +214,49 @@ def run_vlb(args, ws, rank, local):
     pts_all, _ = aggregate(pts, dev_s, ws)
     mlups = units / secs / 1e6
 
-    # --- end to end through the public API: seed from host, step, read the
-    # line length after every step, read the filaments back at the end
-    ch2 = vlb.Channel(p, stream=stream)
-    ch2.set_overlap(not args.no_overlap)
-    ch2.step(0)
-    barrier(ws)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ch2.seed(xyz, nxt)
-    lengths = []
-    for _ in range(args.steps):
-        ch2.step(1)
-        lengths.append(ch2.line_length())
-    final = ch2.read(vlb.FIELD_POS)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    barrier(ws)
-    ch2.close()
+    # --- end to end through the public API: seed from host, step one step
+    # per call, read every step's status (its line length among it), read
+    # the filaments back at the end.  Pipelined: each step is queued with
+    # vlb_step_async while the step before still runs, and its status is
+    # read once vlb_query has completed it, so the host's launch and read
+    # of one step overlap the device's next step.  The blocking loop (one
+    # vlb_step per step) is timed as well.
+    def e2e_run(pipelined):
+        ch2 = vlb.Channel(p, stream=stream)
+        ch2.set_overlap(not args.no_overlap)
+        ch2.step(0)
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ch2.seed(xyz, nxt)
+        lengths = []
+        if pipelined:
+            depth = 2
+            for k in range(args.steps + depth - 1):
+                if k < args.steps:
+                    ch2.step_async(1)
+                if k >= depth - 1:
+                    while not ch2.query():
+                        pass
+                    lengths.append(ch2.query_stats()[3])
+        else:
+            for _ in range(args.steps):
+                ch2.step(1)
+                lengths.append(ch2.line_length())
+        final = ch2.read(vlb.FIELD_POS)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        barrier(ws)
+        ch2.close()
+        assert len(lengths) == args.steps
+        return final, e2e_s
+
+    final, e2e_s = e2e_run(True)
+    _, e2e_block_s = e2e_run(False)
     e2e_units, e2e_secs = aggregate(cells * args.steps, e2e_s, ws)
+    e2e_block_units, e2e_block_secs = aggregate(cells * args.steps, e2e_block_s, ws)
     h2d = (xyz.size * 8 + nxt.size * 4) / args.steps
-    # per vlb_step: the status block (8 doubles of statistics, the line length
+    # per step call: the status block (8 doubles of statistics, the line length
     # among them, and 12 int counters); at the end, the filaments
     d2h = 8 * 8 + 12 * 4 + final.nbytes / args.steps
 
@@ -266,7 +288,9 @@ def run_vlb(args, ws, rank, local):
         "filament_pts_per_s": round(pts_all / secs, 1),
         "ms_per_step_without_graphs": round(nograph_s * 1e3 / args.steps, 4),
         "e2e": {"value": round(e2e_units / e2e_secs / 1e6, 2), "unit": "MLUPS",
-                "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1)},
+                "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
+                "loop": "vlb_step_async(1) per step, two in flight, vlb_query + vlb_query_stats per step",
+                "blocking_value": round(e2e_block_units / e2e_block_secs / 1e6, 2)},
         # + 1: the line-length kernel that ends each vlb_step call
         "gpu_launches": launches(int(n_before), args.steps, not args.no_overlap) + 1,
         "roofline": {"kernel": "k_lbm_step", "bound": "hbm",

@@ -167,14 +167,28 @@ int vlb_set_graphs(vlb_channel* ch, int32_t enable);
  * of vlb_step_async still queued). */
 int vlb_set_overlap(vlb_channel* ch, int32_t enable);
 
-/* Non-blocking form of vlb_step for hosts that drive many channels at once
- * (each on its own stream, so their work overlaps on the GPU): queues the
- * steps and a read-back of the status, and returns without waiting.
- * vlb_query then returns VLB_BUSY (1) while that work runs, VLB_OK once it
- * has finished, or the first error the device reported (as vlb_step). */
-enum { VLB_BUSY = 1 };
+/* Non-blocking form of vlb_step, for hosts that drive many channels at once
+ * (each on its own stream, so their work overlaps on the GPU) or that read
+ * each step's result while the next steps already run: queues the steps, the
+ * line length of the new points (nsteps > 0) and a read-back of the status
+ * block into a pinned slot of this call's own, and returns without waiting.
+ * A channel holds up to VLB_ASYNC_DEPTH such calls in flight (INVALID_ARG
+ * beyond), completed in order by vlb_query: it returns VLB_BUSY (1) while
+ * the oldest queued call runs, VLB_OK once it has finished (vlb_query_stats
+ * then reads that call's status, and vlb_line_length returns its line length
+ * without a wait if no later call is queued), or the first error the device
+ * reported (as vlb_step).  vlb_step and vlb_set_overlap return INVALID_ARG
+ * while calls are queued. */
+enum { VLB_BUSY = 1, VLB_ASYNC_DEPTH = 4 };
 int vlb_step_async(vlb_channel* ch, int32_t nsteps);
 int vlb_query(vlb_channel* ch);
+
+/* The VLB_FIELD_STATS record (16 float64, same layout) of the vlb_step_async
+ * call that vlb_query completed last: the state right after that call's
+ * steps, whatever calls are queued after it; out[9] counts the steps up to
+ * it.  No device work and no wait.  INVALID_ARG (null argument, or no call
+ * completed yet). */
+int vlb_query_stats(vlb_channel* ch, double* out);
 
 /* Device bytes vlb_create_channel would allocate for these parameters (an
  * upper bound used to admit channels against a memory budget); 0 if the

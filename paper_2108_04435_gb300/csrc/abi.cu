@@ -14,6 +14,11 @@
 
 using namespace vlb;
 
+// The status block on the device and in its pinned host copies: the f64
+// statistics, then the int32 counters.
+static constexpr size_t STATUS_BYTES = sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT;
+static constexpr size_t STATUS_SLOT = (STATUS_BYTES + 255) & ~size_t(255);  // stride of the async slots
+
 namespace {
 
 thread_local std::string g_last_error = "no error";
@@ -58,14 +63,22 @@ struct vlb_channel {
     int gclass[2][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};  // filament size class at capture
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
-    cudaEvent_t done = nullptr;  // completion of the work queued by vlb_step_async
+    // vlb_step_async calls in flight: each copies the status block into its
+    // own pinned slot and records its own event; vlb_query completes the
+    // oldest (slots q_tail .. q_head - 1, modulo VLB_ASYNC_DEPTH)
+    unsigned char* h_ring = nullptr;  // pinned, VLB_ASYNC_DEPTH status blocks
+    cudaEvent_t q_ev[VLB_ASYNC_DEPTH] = {};
+    bool q_line[VLB_ASYNC_DEPTH] = {};  // the call stepped (its status carries the line length)
+    long long q_steps[VLB_ASYNC_DEPTH] = {};  // steps queued on the channel up to the end of the call
+    int q_head = 0, q_tail = 0;
+    unsigned char done_block[STATUS_BYTES] = {};  // status block of the call vlb_query last completed
+    long long done_steps = -1;                   // its step count; -1: no call completed yet
     // second stream (highest priority) and fork/join events of the multi-step graphs
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool overlap = true;  // multi-step graphs use the second stream (vlb_set_overlap)
     bool line_fresh = false;  // h_dstats[DS_LINE] holds the line length of the current points
     bool side_failed = false;  // the second stream could not be created
-    bool pending = false;
     double timing_ms = 0.0;
     long long timing_launches = 0;
 
@@ -97,8 +110,13 @@ void release(vlb_channel* ch) {
     ch->blocks.clear();
     for (cudaEvent_t e : ch->ev) cudaEventDestroy(e);
     ch->ev.clear();
-    if (ch->done) cudaEventDestroy(ch->done);
-    ch->done = nullptr;
+    for (cudaEvent_t& e : ch->q_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    if (ch->h_ring) cudaFreeHost(ch->h_ring);
+    ch->h_ring = nullptr;
+    ch->q_head = ch->q_tail = 0;
     if (ch->side) cudaStreamDestroy(ch->side);
     if (ch->ev_fork) cudaEventDestroy(ch->ev_fork);
     if (ch->ev_join) cudaEventDestroy(ch->ev_join);
@@ -128,7 +146,7 @@ int status_to_code(int st, std::string* msg) {
 
 // Copy the device counters and statistics to the pinned mirrors and wait.
 int sync_counters(vlb_channel* ch) {
-    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT,
+    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, STATUS_BYTES,
                     cudaMemcpyDeviceToHost, ch->stream);
     cudaError_t e = cudaStreamSynchronize(ch->stream);
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
@@ -552,7 +570,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.plane = (double*)A(sizeof(double) * 3 * (size_t)g.nz);
     d.plane_ticket = (int*)A(sizeof(int) * (size_t)g.nz);
     // statistics and counters in one block, read back with one copy
-    d.dstats = (double*)A(sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT);
+    d.dstats = (double*)A(STATUS_BYTES);
     d.counters = d.dstats ? (int*)(d.dstats + DS_COUNT) : nullptr;
     const size_t P3 = sizeof(double) * 3 * (size_t)cap;
     for (int b = 0; b < 2; ++b) {
@@ -595,7 +613,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
         delete ch;
         return fail(VLB_ERR_OOM, "device allocation failed");
     }
-    if (cudaMallocHost((void**)&ch->h_dstats, sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT) == cudaSuccess)
+    if (cudaMallocHost((void**)&ch->h_dstats, STATUS_BYTES) == cudaSuccess)
         ch->h_counters = (int*)(ch->h_dstats + DS_COUNT);
     if (!ch->h_dstats) {
         release(ch);
@@ -867,8 +885,28 @@ void queue_steps(vlb_channel* ch, int nsteps) {
 }
 }  // namespace
 
+namespace {
+// The STATS record (VLB_FIELD_STATS) from a status block.
+void fill_stats(const vlb_channel* ch, const double* ds, const int* cnt, long long steps, double* o) {
+    for (int k = 0; k < 16; ++k) o[k] = 0.0;
+    o[0] = cnt[CNT_N];
+    o[1] = cnt[CNT_STATUS];
+    o[2] = ds[DS_MASS];
+    o[3] = ds[DS_LINE];
+    o[4] = ds[DS_MAXMACH];
+    o[5] = ds[DS_SPLITS];
+    o[6] = ds[DS_MERGES];
+    o[7] = ds[DS_RECON];
+    o[8] = ds[DS_SMALL];
+    o[9] = (double)steps;
+    o[10] = (double)ch->bytes;
+    o[13] = ds[DS_WALLCUT];
+}
+}  // namespace
+
 int vlb_step(vlb_channel* ch, int32_t nsteps) {
     if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
+    if (ch->q_head != ch->q_tail) return fail(VLB_ERR_INVALID_ARG, "vlb_step_async calls still queued");
     ch->line_fresh = false;
     queue_steps(ch, nsteps);
     // the total line length of the new points rides along with the status read,
@@ -883,14 +921,26 @@ int vlb_step(vlb_channel* ch, int32_t nsteps) {
 
 int vlb_step_async(vlb_channel* ch, int32_t nsteps) {
     if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
-    ch->line_fresh = false;
-    if (!ch->done && cudaEventCreateWithFlags(&ch->done, cudaEventDisableTiming) != cudaSuccess)
+    if (ch->q_head - ch->q_tail >= VLB_ASYNC_DEPTH)
+        return fail(VLB_ERR_INVALID_ARG, "VLB_ASYNC_DEPTH calls already queued: complete one with vlb_query");
+    const int slot = ch->q_head % VLB_ASYNC_DEPTH;
+    if (!ch->q_ev[slot] && cudaEventCreateWithFlags(&ch->q_ev[slot], cudaEventDisableTiming) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "event create");
+    if (!ch->h_ring && cudaMallocHost((void**)&ch->h_ring, STATUS_SLOT * VLB_ASYNC_DEPTH) != cudaSuccess) {
+        ch->h_ring = nullptr;
+        return fail(VLB_ERR_OOM, "pinned status slots");
+    }
+    ch->line_fresh = false;
     queue_steps(ch, nsteps);
-    cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, sizeof(double) * DS_COUNT + sizeof(int) * CNT_COUNT,
-                    cudaMemcpyDeviceToHost, ch->stream);
-    cudaEventRecord(ch->done, ch->stream);
-    ch->pending = true;
+    if (nsteps > 0)  // as in vlb_step: the line length of the new points rides along with the status
+        launch_line_length(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.next[ch->cur_p], ch->d.counters, ch->cap,
+                           ch->d.line_part, ch->d.dstats, ch->stream);
+    cudaMemcpyAsync(ch->h_ring + (size_t)slot * STATUS_SLOT, ch->d.dstats, STATUS_BYTES, cudaMemcpyDeviceToHost,
+                    ch->stream);
+    cudaEventRecord(ch->q_ev[slot], ch->stream);
+    ch->q_line[slot] = nsteps > 0;
+    ch->q_steps[slot] = ch->steps;
+    ++ch->q_head;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "step launch");
     return VLB_OK;
@@ -898,15 +948,33 @@ int vlb_step_async(vlb_channel* ch, int32_t nsteps) {
 
 int vlb_query(vlb_channel* ch) {
     if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
-    if (!ch->pending) return VLB_OK;
-    const cudaError_t e = cudaEventQuery(ch->done);
+    if (ch->q_head == ch->q_tail) return VLB_OK;
+    const int slot = ch->q_tail % VLB_ASYNC_DEPTH;
+    const cudaError_t e = cudaEventQuery(ch->q_ev[slot]);
     if (e == cudaErrorNotReady) return VLB_BUSY;
-    ch->pending = false;
+    ++ch->q_tail;
     if (e != cudaSuccess) return cuda_fail(e, "step completion");
+    // this call's status block: kept for vlb_query_stats, and the channel's
+    // host copy of the status until the state is read again
+    memcpy(ch->done_block, ch->h_ring + (size_t)slot * STATUS_SLOT, STATUS_BYTES);
+    ch->done_steps = ch->q_steps[slot];
+    memcpy(ch->h_dstats, ch->done_block, STATUS_BYTES);
     ch->n_hint = ch->h_counters[CNT_N];
+    ch->line_fresh = ch->q_line[slot] && ch->q_head == ch->q_tail;
     std::string msg;
     const int rc = status_to_code(ch->h_counters[CNT_STATUS], &msg);
-    if (rc) return fail(rc, msg);
+    if (rc) {
+        ch->line_fresh = false;
+        return fail(rc, msg);
+    }
+    return VLB_OK;
+}
+
+int vlb_query_stats(vlb_channel* ch, double* out) {
+    if (!ch || !out) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    if (ch->done_steps < 0) return fail(VLB_ERR_INVALID_ARG, "no vlb_step_async call has completed");
+    fill_stats(ch, (const double*)ch->done_block, (const int*)(ch->done_block + sizeof(double) * DS_COUNT),
+               ch->done_steps, out);
     return VLB_OK;
 }
 
@@ -918,7 +986,7 @@ int vlb_set_graphs(vlb_channel* ch, int32_t enable) {
 
 int vlb_set_overlap(vlb_channel* ch, int32_t enable) {
     if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
-    if (ch->pending) return fail(VLB_ERR_INVALID_ARG, "steps still queued");
+    if (ch->q_head != ch->q_tail) return fail(VLB_ERR_INVALID_ARG, "steps still queued");
     if (ch->overlap != (enable != 0)) {
         // the multi-step graphs were captured in the other form
         cudaStreamSynchronize(ch->stream);
@@ -999,20 +1067,7 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
         launch_line_length(ch->lp.g, d.pos[ch->cur_p], d.next[ch->cur_p], d.counters, ch->cap, d.line_part, d.dstats, s);
         rc = sync_counters(ch);
         if (rc) return rc;
-        double* o = (double*)dst;
-        for (int k = 0; k < 16; ++k) o[k] = 0.0;
-        o[0] = ch->h_counters[CNT_N];
-        o[1] = ch->h_counters[CNT_STATUS];
-        o[2] = ch->h_dstats[DS_MASS];
-        o[3] = ch->h_dstats[DS_LINE];
-        o[4] = ch->h_dstats[DS_MAXMACH];
-        o[5] = ch->h_dstats[DS_SPLITS];
-        o[6] = ch->h_dstats[DS_MERGES];
-        o[7] = ch->h_dstats[DS_RECON];
-        o[8] = ch->h_dstats[DS_SMALL];
-        o[9] = (double)ch->steps;
-        o[10] = (double)ch->bytes;
-        o[13] = ch->h_dstats[DS_WALLCUT];
+        fill_stats(ch, ch->h_dstats, ch->h_counters, ch->steps, (double*)dst);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "read field");

@@ -25,8 +25,9 @@ FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_FDEV, FIELD_LINE_PROFILE = 6, 7, 8
 EXPORTS = ["vlb_create_channel", "vlb_seed_vortices", "vlb_step", "vlb_run_phases", "vlb_read_fields",
            "vlb_write_fields", "vlb_line_length", "vlb_destroy", "vlb_last_error", "vlb_set_timing",
            "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart", "vlb_set_graphs", "vlb_set_overlap",
-           "vlb_biot_savart_noalloc", "vlb_step_async", "vlb_query", "vlb_channel_bytes"]
+           "vlb_biot_savart_noalloc", "vlb_step_async", "vlb_query", "vlb_query_stats", "vlb_channel_bytes"]
 BUSY = 1
+ASYNC_DEPTH = 4  # vlb_step_async calls a channel holds in flight
 
 
 class Params(C.Structure):
@@ -88,6 +89,7 @@ def lib():
         L.vlb_biot_savart_noalloc.argtypes = [C.POINTER(Params), vp, vp, C.c_int32, vp, vp]
         L.vlb_step_async.argtypes = [vp, C.c_int32]
         L.vlb_query.argtypes = [vp]
+        L.vlb_query_stats.argtypes = [vp, C.POINTER(C.c_double)]
         L.vlb_channel_bytes.argtypes = [C.POINTER(Params)]
         L.vlb_channel_bytes.restype = C.c_size_t
         _lib = L
@@ -181,12 +183,18 @@ class Channel:
         check(lib().vlb_step_async(self.h, nsteps))
 
     def query(self) -> bool:
-        """True once the queued steps have finished (raises on a device error)."""
+        """True once the oldest queued call has finished (raises on a device error)."""
         rc = lib().vlb_query(self.h)
         if rc == BUSY:
             return False
         check(rc)
         return True
+
+    def query_stats(self) -> np.ndarray:
+        """STATS record of the queued call that query() completed last."""
+        out = np.zeros(16)
+        check(lib().vlb_query_stats(self.h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
 
     def run_phases(self, mask: int, raise_on_error: bool = True) -> int:
         rc = lib().vlb_run_phases(self.h, mask)

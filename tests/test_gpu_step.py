@@ -164,3 +164,49 @@ def test_line_length_after_step_is_current():
     fresh = g.line_length()
     g.close()
     assert cached == fresh and cached != l0
+
+
+def test_async_calls_in_flight_match_blocking_steps():
+    """Several vlb_step_async calls in flight, each completed in order by
+    vlb_query: every call's own status (points, line length, step count)
+    equals that of a blocking vlb_step(1) channel after the same steps, and
+    the final points are identical.  The queue holds VLB_ASYNC_DEPTH calls;
+    vlb_step waits for none of them and refuses while they are queued."""
+    import torch
+    from paper_2108_04435_gb300 import configs, vlb
+    p, xyz, nxt = configs.config("channel64x64x256")
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    a = vlb.Channel(p, stream=sa)
+    b = vlb.Channel(p, stream=sb)
+    a.seed(xyz, nxt)
+    b.seed(xyz, nxt)
+    ref = []
+    for _ in range(6):
+        b.step(1)
+        ref.append(b.stats())
+    got = []
+    for k in range(6):
+        a.step_async(1)
+        if k >= 2:  # three calls in flight, then one completed per call
+            while not a.query():
+                pass
+            got.append(a.query_stats())
+    while len(got) < 6:
+        while not a.query():
+            pass
+        got.append(a.query_stats())
+    for r, g in zip(ref, got):
+        assert g[0] == r[0] and g[3] == r[3] and g[9] == r[9], (g[:10], r[:10])
+    assert np.array_equal(a.read(vlb.FIELD_POS), b.read(vlb.FIELD_POS))
+    for _ in range(vlb.ASYNC_DEPTH):
+        a.step_async(1)
+    with pytest.raises(vlb.VlbError):
+        a.step_async(1)
+    with pytest.raises(vlb.VlbError):
+        a.step(1)
+    for _ in range(vlb.ASYNC_DEPTH):
+        while not a.query():
+            pass
+    a.step(1)
+    a.close()
+    b.close()
