@@ -256,9 +256,9 @@ def run_vlb(args, ws, rank, local):
     e2e_units, e2e_secs = aggregate(cells * args.steps, e2e_s, ws)
     e2e_block_units, e2e_block_secs = aggregate(cells * args.steps, e2e_block_s, ws)
     h2d = (xyz.size * 8 + nxt.size * 4) / args.steps
-    # per step call: the status block (8 doubles of statistics, the line length
-    # among them, and 12 int counters); at the end, the filaments
-    d2h = 8 * 8 + 12 * 4 + final.nbytes / args.steps
+    # per step call: the status block (12 doubles of statistics, the line
+    # length among them, and 12 int counters); at the end, the filaments
+    d2h = 12 * 8 + 12 * 4 + final.nbytes / args.steps
 
     pk, pk_kind = peaks()
     k1_avg_s = (k1_ms / 1e3) / max(k1_n, 1)

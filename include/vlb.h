@@ -178,7 +178,12 @@ int vlb_set_overlap(vlb_channel* ch, int32_t enable);
  * then reads that call's status, and vlb_line_length returns its line length
  * without a wait if no later call is queued), or the first error the device
  * reported (as vlb_step).  vlb_step and vlb_set_overlap return INVALID_ARG
- * while calls are queued. */
+ * while calls are queued.  A one-step call on a created stream, with graphs
+ * and the overlap on, runs split over the channel's stream and the second
+ * stream: its remesh, reconnection, line length and status copy run beside
+ * the lattice pass of the next queued call, with the same results bit for
+ * bit.  A device error may then show in the status of the call queued
+ * before the step that raised it (status bits are sticky). */
 enum { VLB_BUSY = 1, VLB_ASYNC_DEPTH = 4 };
 int vlb_step_async(vlb_channel* ch, int32_t nsteps);
 int vlb_query(vlb_channel* ch);

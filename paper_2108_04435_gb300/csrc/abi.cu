@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -70,6 +71,18 @@ struct vlb_channel {
     cudaEvent_t q_ev[VLB_ASYNC_DEPTH] = {};
     bool q_line[VLB_ASYNC_DEPTH] = {};  // the call stepped (its status carries the line length)
     long long q_steps[VLB_ASYNC_DEPTH] = {};  // steps queued on the channel up to the end of the call
+    int q_lat[VLB_ASYNC_DEPTH] = {};          // split step: parity slot of its lattice statistics, else -1
+    int done_lat = -1;
+    // Split async steps (vlb_step_async of one step, overlap on): lattice pass
+    // and RK stages on the channel's stream, remesh, reconnection, line length
+    // and status read on the second stream, so the second-stream work of one
+    // call runs beside the lattice pass of the next.  [lattice, stages,
+    // topology][population parity, point parity, point parity]
+    cudaGraphExec_t sgexec[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    int sgclass[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    bool b_tail = false;  // second-stream work of a split step not yet joined into the channel's stream
+    int last_lat = 0;     // parity slot of the last split lattice pass
     int q_head = 0, q_tail = 0;
     unsigned char done_block[STATUS_BYTES] = {};  // status block of the call vlb_query last completed
     long long done_steps = -1;                   // its step count; -1: no call completed yet
@@ -103,6 +116,7 @@ namespace {
 
 void release(vlb_channel* ch) {
     cudaStreamSynchronize(ch->stream);
+    if (ch->side) cudaStreamSynchronize(ch->side);
     for (void* b : ch->blocks) {
         if (ch->has_alloc) ch->alloc.free(ch->alloc.ctx, b, (void*)ch->stream);
         else cudaFree(b);
@@ -114,6 +128,15 @@ void release(vlb_channel* ch) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
     }
+    for (auto& row : ch->sgexec)
+        for (cudaGraphExec_t& g : row) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    if (ch->ev_a) cudaEventDestroy(ch->ev_a);
+    if (ch->ev_b) cudaEventDestroy(ch->ev_b);
+    ch->ev_a = ch->ev_b = nullptr;
+    ch->b_tail = false;
     if (ch->h_ring) cudaFreeHost(ch->h_ring);
     ch->h_ring = nullptr;
     ch->q_head = ch->q_tail = 0;
@@ -144,8 +167,21 @@ int status_to_code(int st, std::string* msg) {
     return VLB_OK;
 }
 
+// Make the channel's stream wait for the second-stream work of the last
+// split async step, and give the status block's own mass and Mach slots the
+// values of its lattice pass.  Every call that reads or changes the state
+// on the channel's stream comes through here first.
+void join_side(vlb_channel* ch) {
+    if (!ch->b_tail) return;
+    cudaStreamWaitEvent(ch->stream, ch->ev_b, 0);
+    cudaMemcpyAsync(ch->d.dstats + DS_MASS, ch->d.dstats + DS_LAT + 2 * ch->last_lat, 2 * sizeof(double),
+                    cudaMemcpyDeviceToDevice, ch->stream);
+    ch->b_tail = false;
+}
+
 // Copy the device counters and statistics to the pinned mirrors and wait.
 int sync_counters(vlb_channel* ch) {
+    join_side(ch);
     cudaMemcpyAsync(ch->h_dstats, ch->d.dstats, STATUS_BYTES,
                     cudaMemcpyDeviceToHost, ch->stream);
     cudaError_t e = cudaStreamSynchronize(ch->stream);
@@ -171,7 +207,9 @@ void mark_points(vlb_channel* ch) {
 
 // The lattice pass: stream-collide and plane reduction (tiles already
 // flagged, or every tile with all_u).
-void lattice_pass(vlb_channel* ch, bool all_u = false) {
+// stats != nullptr: the plane reduction writes the mass and max Mach there
+// (as [0], [1]) instead of into the status block's own slots.
+void lattice_pass(vlb_channel* ch, bool all_u = false, double* stats = nullptr) {
     Dev& d = ch->d;
     if (ch->timing) record_event(ch);
     LbmParams L = ch->lp;
@@ -180,7 +218,9 @@ void lattice_pass(vlb_channel* ch, bool all_u = false) {
     if (ch->timing) record_event(ch);
     ch->cur_f ^= 1;
     // the pass consumed the force grid: the plane reduction resets it and clears both tile flags
-    launch_plane_vs(ch->lp, d.part, d.F, d.umask, d.fmask, ch->stream);
+    LbmParams R = ch->lp;
+    if (stats) R.dstats = stats - DS_MASS;
+    launch_plane_vs(R, d.part, d.F, d.umask, d.fmask, ch->stream);
     ch->f_clean = true;
 }
 
@@ -666,6 +706,7 @@ void vlb_destroy(vlb_channel* ch) {
 
 int vlb_seed_vortices(vlb_channel* ch, const double* xyz, const int32_t* next, int32_t n) {
     if (!ch || n < 0 || (n > 0 && (!xyz || !next))) return fail(VLB_ERR_INVALID_ARG, "bad seed arguments");
+    join_side(ch);
     ch->line_fresh = false;
     if (n > ch->cap || (n > 0 && ch->p.max_points == 0)) return fail(VLB_ERR_CAPACITY, "more points than max_points");
     std::vector<char> seen((size_t)n, 0);
@@ -867,6 +908,97 @@ bool step_graph(vlb_channel* ch, bool multi) {
     return true;
 }
 
+// Capture body() on stream s as split graph kind/par if it is missing or
+// was sized for another filament count; nothing is launched.  body() runs on
+// the channel's state as it will be at launch and leaves it as it found it.
+bool capture_split(vlb_channel* ch, int kind, int par, cudaStream_t s, const std::function<void()>& body) {
+    const int cls = size_class(ch->n_hint);
+    cudaGraphExec_t& ge = ch->sgexec[kind][par];
+    if (ge && ch->sgclass[kind][par] == cls) return true;
+    if (ge) cudaGraphExecDestroy(ge);
+    ge = nullptr;
+    const int f = ch->cur_f, q = ch->cur_p;
+    const bool fc = ch->f_clean;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    tl_no_pdl = true;
+    body();
+    tl_no_pdl = false;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    ch->cur_f = f;
+    ch->cur_p = q;
+    ch->f_clean = fc;
+    if (e != cudaSuccess || !graph) {
+        cudaGetLastError();
+        return false;
+    }
+    e = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ge = nullptr;
+        return false;
+    }
+    ch->sgclass[kind][par] = cls;
+    return true;
+}
+
+// One coupled step of vlb_step_async, split over the two streams:
+//   channel stream: lattice pass (v_n in every tile, its mass and Mach into
+//     the parity slot DS_LAT + 2 f), then, once the second stream's work of
+//     the previous split step is done, the RK stages;
+//   second stream: after the stages, remesh, reconnection, the line length
+//     and the status copy into the call's pinned slot.
+// The lattice pass of the next call then runs beside this call's remesh and
+// reconnection, as in the overlapped multi-step graphs, with the same result
+// bit for bit.  False, with nothing queued, if it cannot be set up; the call
+// then queues the step in sequence.
+bool queue_split_step(vlb_channel* ch, int slot) {
+    if (!(ch->graphs && !ch->timing && ch->stream && ch->overlap && ensure_side(ch))) return false;
+    if ((!ch->ev_a && cudaEventCreateWithFlags(&ch->ev_a, cudaEventDisableTiming) != cudaSuccess) ||
+        (!ch->ev_b && cudaEventCreateWithFlags(&ch->ev_b, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    Dev& d = ch->d;
+    cudaStream_t A = ch->stream, B = ch->side;
+    const int f = ch->cur_f, q = ch->cur_p;
+    auto lat = [&] { lattice_pass(ch, true, d.dstats + DS_LAT + 2 * f); };
+    auto stages = [&] {
+        ch->f_clean = true;  // the lattice pass before consumed the force grid
+        vfm_step(ch, false, A);
+    };
+    auto topo = [&] {
+        const int span = point_span(ch->n_hint, ch->cap);
+        launch_remesh(ch->vp, d, ch->cur_p, ch->cap, span, B);
+        ch->cur_p ^= 1;
+        launch_reconnect(ch->vp, d, ch->cur_p, ch->cap, span, ch->hsize, B);
+        ch->cur_p ^= 1;
+        launch_line_length(ch->lp.g, d.pos[ch->cur_p], d.next[ch->cur_p], d.counters, ch->cap, d.line_part,
+                           d.dstats, B);
+    };
+    if (!capture_split(ch, 0, f, A, lat) || !capture_split(ch, 1, q, A, stages) || !capture_split(ch, 2, q, B, topo))
+        return false;
+    if (cudaGraphLaunch(ch->sgexec[0][f], A) != cudaSuccess) return false;
+    if (ch->b_tail) cudaStreamWaitEvent(A, ch->ev_b, 0);
+    cudaGraphLaunch(ch->sgexec[1][q], A);
+    cudaEventRecord(ch->ev_a, A);
+    cudaStreamWaitEvent(B, ch->ev_a, 0);
+    cudaGraphLaunch(ch->sgexec[2][q], B);
+    cudaMemcpyAsync(ch->h_ring + (size_t)slot * STATUS_SLOT, d.dstats, STATUS_BYTES, cudaMemcpyDeviceToHost, B);
+    cudaEventRecord(ch->ev_b, B);
+    cudaEventRecord(ch->q_ev[slot], B);
+    ch->b_tail = true;
+    ch->last_lat = f;
+    ch->cur_f ^= 1;
+    ch->f_clean = !ch->p.couple;
+    ch->steps++;
+    return true;
+}
+
 // Queue nsteps coupled steps: multi-step graphs while enough steps remain,
 // then single-step graphs; direct launches when graphs are off or unavailable.
 void queue_steps(vlb_channel* ch, int nsteps) {
@@ -887,13 +1019,15 @@ void queue_steps(vlb_channel* ch, int nsteps) {
 
 namespace {
 // The STATS record (VLB_FIELD_STATS) from a status block.
-void fill_stats(const vlb_channel* ch, const double* ds, const int* cnt, long long steps, double* o) {
+// lat >= 0: the mass and Mach come from that parity slot of a split step.
+void fill_stats(const vlb_channel* ch, const double* ds, const int* cnt, long long steps, double* o, int lat = -1) {
+    const double* m = lat >= 0 ? ds + DS_LAT + 2 * lat : ds + DS_MASS;
     for (int k = 0; k < 16; ++k) o[k] = 0.0;
     o[0] = cnt[CNT_N];
     o[1] = cnt[CNT_STATUS];
-    o[2] = ds[DS_MASS];
+    o[2] = m[0];
     o[3] = ds[DS_LINE];
-    o[4] = ds[DS_MAXMACH];
+    o[4] = m[1];
     o[5] = ds[DS_SPLITS];
     o[6] = ds[DS_MERGES];
     o[7] = ds[DS_RECON];
@@ -907,6 +1041,7 @@ void fill_stats(const vlb_channel* ch, const double* ds, const int* cnt, long lo
 int vlb_step(vlb_channel* ch, int32_t nsteps) {
     if (!ch || nsteps < 0) return fail(VLB_ERR_INVALID_ARG, "bad step arguments");
     if (ch->q_head != ch->q_tail) return fail(VLB_ERR_INVALID_ARG, "vlb_step_async calls still queued");
+    join_side(ch);
     ch->line_fresh = false;
     queue_steps(ch, nsteps);
     // the total line length of the new points rides along with the status read,
@@ -931,13 +1066,19 @@ int vlb_step_async(vlb_channel* ch, int32_t nsteps) {
         return fail(VLB_ERR_OOM, "pinned status slots");
     }
     ch->line_fresh = false;
-    queue_steps(ch, nsteps);
-    if (nsteps > 0)  // as in vlb_step: the line length of the new points rides along with the status
-        launch_line_length(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.next[ch->cur_p], ch->d.counters, ch->cap,
-                           ch->d.line_part, ch->d.dstats, ch->stream);
-    cudaMemcpyAsync(ch->h_ring + (size_t)slot * STATUS_SLOT, ch->d.dstats, STATUS_BYTES, cudaMemcpyDeviceToHost,
-                    ch->stream);
-    cudaEventRecord(ch->q_ev[slot], ch->stream);
+    ch->q_lat[slot] = -1;
+    if (nsteps == 1 && queue_split_step(ch, slot)) {
+        ch->q_lat[slot] = ch->last_lat;
+    } else {
+        join_side(ch);
+        queue_steps(ch, nsteps);
+        if (nsteps > 0)  // as in vlb_step: the line length of the new points rides along with the status
+            launch_line_length(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.next[ch->cur_p], ch->d.counters, ch->cap,
+                               ch->d.line_part, ch->d.dstats, ch->stream);
+        cudaMemcpyAsync(ch->h_ring + (size_t)slot * STATUS_SLOT, ch->d.dstats, STATUS_BYTES, cudaMemcpyDeviceToHost,
+                        ch->stream);
+        cudaEventRecord(ch->q_ev[slot], ch->stream);
+    }
     ch->q_line[slot] = nsteps > 0;
     ch->q_steps[slot] = ch->steps;
     ++ch->q_head;
@@ -958,6 +1099,7 @@ int vlb_query(vlb_channel* ch) {
     // host copy of the status until the state is read again
     memcpy(ch->done_block, ch->h_ring + (size_t)slot * STATUS_SLOT, STATUS_BYTES);
     ch->done_steps = ch->q_steps[slot];
+    ch->done_lat = ch->q_lat[slot];
     memcpy(ch->h_dstats, ch->done_block, STATUS_BYTES);
     ch->n_hint = ch->h_counters[CNT_N];
     ch->line_fresh = ch->q_line[slot] && ch->q_head == ch->q_tail;
@@ -974,7 +1116,7 @@ int vlb_query_stats(vlb_channel* ch, double* out) {
     if (!ch || !out) return fail(VLB_ERR_INVALID_ARG, "null argument");
     if (ch->done_steps < 0) return fail(VLB_ERR_INVALID_ARG, "no vlb_step_async call has completed");
     fill_stats(ch, (const double*)ch->done_block, (const int*)(ch->done_block + sizeof(double) * DS_COUNT),
-               ch->done_steps, out);
+               ch->done_steps, out, ch->done_lat);
     return VLB_OK;
 }
 
@@ -987,6 +1129,7 @@ int vlb_set_graphs(vlb_channel* ch, int32_t enable) {
 int vlb_set_overlap(vlb_channel* ch, int32_t enable) {
     if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
     if (ch->q_head != ch->q_tail) return fail(VLB_ERR_INVALID_ARG, "steps still queued");
+    join_side(ch);
     if (ch->overlap != (enable != 0)) {
         // the multi-step graphs were captured in the other form
         cudaStreamSynchronize(ch->stream);
@@ -1004,6 +1147,7 @@ int vlb_set_overlap(vlb_channel* ch, int32_t enable) {
 
 int vlb_run_phases(vlb_channel* ch, int32_t mask) {
     if (!ch || mask < 0 || mask > VLB_PHASE_ALL) return fail(VLB_ERR_INVALID_ARG, "bad phase mask");
+    join_side(ch);
     ch->line_fresh = false;
     run_phases(ch, mask);
     return finish(ch);
@@ -1077,6 +1221,7 @@ int vlb_read_fields(vlb_channel* ch, int32_t which, void* dst, size_t bytes, siz
 
 int vlb_write_fields(vlb_channel* ch, int32_t which, const void* src, size_t bytes) {
     if (!ch || !src) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    join_side(ch);
     ch->line_fresh = false;
     const long long C = ch->lp.g.ncell;
     Dev& d = ch->d;
@@ -1117,6 +1262,7 @@ int vlb_line_length(vlb_channel* ch, double* out) {
         *out = ch->h_dstats[DS_LINE];
         return VLB_OK;
     }
+    join_side(ch);
     launch_line_length(ch->lp.g, ch->d.pos[ch->cur_p], ch->d.next[ch->cur_p], ch->d.counters, ch->cap,
                        ch->d.line_part, ch->d.dstats, ch->stream);
     cudaMemcpyAsync(ch->h_dstats + DS_LINE, ch->d.dstats + DS_LINE, sizeof(double), cudaMemcpyDeviceToHost,
@@ -1129,6 +1275,7 @@ int vlb_line_length(vlb_channel* ch, double* out) {
 
 int vlb_set_timing(vlb_channel* ch, int32_t enable) {
     if (!ch) return fail(VLB_ERR_INVALID_ARG, "null channel");
+    join_side(ch);
     cudaStreamSynchronize(ch->stream);
     ch->timing = enable != 0;
     ch->ev_used = 0;

@@ -46,7 +46,8 @@ enum : int {
     DS_RECON = 5,
     DS_SMALL = 6,
     DS_WALLCUT = 7,
-    DS_COUNT = 8
+    DS_LAT = 8,  // mass and max Mach of the lattice passes of split async steps, one pair per population parity
+    DS_COUNT = 12
 };
 
 // Stored population formats (vlb_params::storage).

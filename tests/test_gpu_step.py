@@ -168,10 +168,12 @@ def test_line_length_after_step_is_current():
 
 def test_async_calls_in_flight_match_blocking_steps():
     """Several vlb_step_async calls in flight, each completed in order by
-    vlb_query: every call's own status (points, line length, step count)
+    vlb_query.  One-step calls run split over two streams (the remesh and
+    reconnection of one call beside the lattice pass of the next); every
+    call's own status (points, mass, line length, max Mach, step count)
     equals that of a blocking vlb_step(1) channel after the same steps, and
-    the final points are identical.  The queue holds VLB_ASYNC_DEPTH calls;
-    vlb_step waits for none of them and refuses while they are queued."""
+    the final points, populations and status are identical.  The queue holds
+    VLB_ASYNC_DEPTH calls; vlb_step refuses while calls are queued."""
     import torch
     from paper_2108_04435_gb300 import configs, vlb
     p, xyz, nxt = configs.config("channel64x64x256")
@@ -195,9 +197,11 @@ def test_async_calls_in_flight_match_blocking_steps():
         while not a.query():
             pass
         got.append(a.query_stats())
-    for r, g in zip(ref, got):
-        assert g[0] == r[0] and g[3] == r[3] and g[9] == r[9], (g[:10], r[:10])
+    for r, g in zip(ref, got):  # points, mass, line length, max Mach, steps
+        assert all(g[k] == r[k] for k in (0, 2, 3, 4, 9)), (g[:10], r[:10])
     assert np.array_equal(a.read(vlb.FIELD_POS), b.read(vlb.FIELD_POS))
+    assert np.array_equal(a.read(vlb.FIELD_FSTAR), b.read(vlb.FIELD_FSTAR))
+    assert np.array_equal(a.stats()[:5], b.stats()[:5])
     for _ in range(vlb.ASYNC_DEPTH):
         a.step_async(1)
     with pytest.raises(vlb.VlbError):
