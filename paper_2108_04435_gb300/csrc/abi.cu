@@ -82,6 +82,7 @@ struct vlb_channel {
     int sgclass[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     bool b_tail = false;  // second-stream work of a split step not yet joined into the channel's stream
+    int b_slot = 0;       // its slot (the slot's event follows all of that work, the status copy included)
     int last_lat = 0;     // parity slot of the last split lattice pass
     int q_head = 0, q_tail = 0;
     unsigned char done_block[STATUS_BYTES] = {};  // status block of the call vlb_query last completed
@@ -173,7 +174,7 @@ int status_to_code(int st, std::string* msg) {
 // on the channel's stream comes through here first.
 void join_side(vlb_channel* ch) {
     if (!ch->b_tail) return;
-    cudaStreamWaitEvent(ch->stream, ch->ev_b, 0);
+    cudaStreamWaitEvent(ch->stream, ch->q_ev[ch->b_slot], 0);
     cudaMemcpyAsync(ch->d.dstats + DS_MASS, ch->d.dstats + DS_LAT + 2 * ch->last_lat, 2 * sizeof(double),
                     cudaMemcpyDeviceToDevice, ch->stream);
     ch->b_tail = false;
@@ -982,16 +983,19 @@ bool queue_split_step(vlb_channel* ch, int slot) {
     };
     if (!capture_split(ch, 0, f, A, lat) || !capture_split(ch, 1, q, A, stages) || !capture_split(ch, 2, q, B, topo))
         return false;
+    // this lattice pass writes the parity slot of the call two back: its status copy must be done
+    if (ch->q_head >= 2) cudaStreamWaitEvent(A, ch->q_ev[(ch->q_head - 2) % VLB_ASYNC_DEPTH], 0);
     if (cudaGraphLaunch(ch->sgexec[0][f], A) != cudaSuccess) return false;
     if (ch->b_tail) cudaStreamWaitEvent(A, ch->ev_b, 0);
     cudaGraphLaunch(ch->sgexec[1][q], A);
     cudaEventRecord(ch->ev_a, A);
     cudaStreamWaitEvent(B, ch->ev_a, 0);
     cudaGraphLaunch(ch->sgexec[2][q], B);
+    cudaEventRecord(ch->ev_b, B);  // the points are final: the next call's stages may start
     cudaMemcpyAsync(ch->h_ring + (size_t)slot * STATUS_SLOT, d.dstats, STATUS_BYTES, cudaMemcpyDeviceToHost, B);
-    cudaEventRecord(ch->ev_b, B);
     cudaEventRecord(ch->q_ev[slot], B);
     ch->b_tail = true;
+    ch->b_slot = slot;
     ch->last_lat = f;
     ch->cur_f ^= 1;
     ch->f_clean = !ch->p.couple;
