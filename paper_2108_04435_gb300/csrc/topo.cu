@@ -547,54 +547,58 @@ __global__ void __launch_bounds__(128) k_nearest(VfmParams P, double dmax2, floa
 
 // Candidate exchanges of the mutual nearest pairs, and the wall-contact
 // candidates (points with both neighbours on a wall's clamp bound; exchanges
-// change neither property), each appended to its list.
-__device__ __forceinline__ void pair_candidates(const VfmParams& P, const double* __restrict__ pos,
-                                                const int* __restrict__ next, const int* __restrict__ prev,
-                                                const int* __restrict__ nn, const double* __restrict__ nd2,
-                                                int* __restrict__ counters, int cap, int i, int* __restrict__ cand_i,
-                                                int* __restrict__ cand_a, int* __restrict__ cand_b,
-                                                double* __restrict__ cand_d2, int* __restrict__ clist) {
-    const int pi = prev[i];
-    if (P.g.wall[0] | P.g.wall[1] | P.g.wall[2]) {
-        if (pi >= 0 && next[i] >= 0 && touching_wall(P.g, P.dmin, pos, cap, i) >= 0)
-            clist[atomicAdd(&counters[CNT_NCONTACT], 1)] = i;
-    }
-    const int j = nn[i];
-    if (j <= i || nn[j] != i) return;
-    const int pj = prev[j];
-    double best = 0.0;
-    int pa = -1, pb = -1;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {  // (i,j), (i,p(j)), (p(i),j), (p(i),p(j))
-        const int a = k < 2 ? i : pi, b = (k & 1) ? pj : j;
-        if (a < 0 || b < 0) continue;
-        const int qa = next[a], qb = next[b];
-        if (qa < 0 || qb < 0) continue;
-        const double gain = (dist(P.g, pos, cap, a, qa) + dist(P.g, pos, cap, b, qb)) -
-                            (dist(P.g, pos, cap, a, qb) + dist(P.g, pos, cap, b, qa));
-        if (gain > 0.0 && (pa < 0 || gain > best)) {
-            best = gain;
-            pa = a;
-            pb = b;
-        }
-    }
-    if (pa < 0) return;
-    const int slot = atomicAdd(&counters[CNT_NPAIRS], 1);
-    cand_i[slot] = i;
-    cand_a[slot] = pa;
-    cand_b[slot] = pb;
-    cand_d2[slot] = nd2[i];
-}
-
-// The candidates of every point, one thread per point.
+// change neither property), each appended to its list.  Four threads per
+// point: thread k of the quad evaluates the k-th exchange (i,j), (i,p(j)),
+// (p(i),j), (p(i),p(j)) (its four FP64 distances); the quad keeps the largest
+// positive gain, the lowest k among equal gains, which is what evaluating the
+// four in order and keeping a strictly larger gain selects.
 __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
                         const int* __restrict__ prev, const int* __restrict__ nn, const double* __restrict__ nd2,
                         int* __restrict__ counters, int cap, int* __restrict__ cand_i, int* __restrict__ cand_a,
                         int* __restrict__ cand_b, double* __restrict__ cand_d2, int* __restrict__ clist) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        pair_candidates(P, pos, next, prev, nn, nd2, counters, cap, i, cand_i, cand_a, cand_b, cand_d2, clist);
+    const int k = threadIdx.x & 3;
+    const unsigned quad = 0xfu << (threadIdx.x & 28);
+    const int nq = (int)((gridDim.x * blockDim.x) >> 2);
+    // i is uniform over a quad, so each quad runs the loop and its shuffles together
+    for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2); i < N; i += nq) {
+        const int pi = prev[i];
+        if (k == 0 && (P.g.wall[0] | P.g.wall[1] | P.g.wall[2])) {
+            if (pi >= 0 && next[i] >= 0 && touching_wall(P.g, P.dmin, pos, cap, i) >= 0)
+                clist[atomicAdd(&counters[CNT_NCONTACT], 1)] = i;
+        }
+        const int j = nn[i];
+        if (j <= i || nn[j] != i) continue;
+        const int pj = prev[j];
+        const int a = k < 2 ? i : pi, b = (k & 1) ? pj : j;
+        bool ok = false;
+        double gain = 0.0;
+        if (a >= 0 && b >= 0) {
+            const int qa = next[a], qb = next[b];
+            if (qa >= 0 && qb >= 0) {
+                gain = (dist(P.g, pos, cap, a, qa) + dist(P.g, pos, cap, b, qb)) -
+                       (dist(P.g, pos, cap, a, qb) + dist(P.g, pos, cap, b, qa));
+                ok = gain > 0.0;
+            }
+        }
+        int kb = ok ? k : 4;  // 4: no exchange
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            const double og = __shfl_xor_sync(quad, gain, o);
+            const int ok_ = __shfl_xor_sync(quad, kb, o);
+            if (ok_ < 4 && (kb == 4 || og > gain || (og == gain && ok_ < kb))) {
+                gain = og;
+                kb = ok_;
+            }
+        }
+        if (k != 0 || kb == 4) continue;
+        const int slot = atomicAdd(&counters[CNT_NPAIRS], 1);
+        cand_i[slot] = i;
+        cand_a[slot] = kb < 2 ? i : pi;
+        cand_b[slot] = (kb & 1) ? pj : j;
+        cand_d2[slot] = nd2[i];
+    }
 }
 
 // One block finishes the reconnection: candidates in ascending (d^2, i)
@@ -759,8 +763,8 @@ void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int span, in
                d.hpos);
     launch_pdl(k_nearest, (span + 3) / 4, 128, 0, s, P, dmax2, nearest_filter_r2(P), d.pos[cur], d.next[cur], d.prev[cur],
                d.counters, cap, hmask, d.hhead, d.hpos, d.nn, d.nd2);
-    launch_pdl(k_pairs, (span + 63) / 64, 64, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2, d.counters, cap,
-               d.cand_i, d.cand_a, d.cand_b, d.cand_d2, d.hlink);
+    launch_pdl(k_pairs, (4 * span + 127) / 128, 128, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2,
+               d.counters, cap, d.cand_i, d.cand_a, d.cand_b, d.cand_d2, d.hlink);
     launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.hlink, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
                                           d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
