@@ -231,7 +231,7 @@ def run_vlb(args, ws, rank, local):
         ch2.seed(xyz, nxt)
         lengths = []
         if pipelined:
-            depth = 2
+            depth = max(1, min(args.e2e_depth, vlb.ASYNC_DEPTH))
             for k in range(args.steps + depth - 1):
                 if k < args.steps:
                     ch2.step_async(1)
@@ -289,7 +289,8 @@ def run_vlb(args, ws, rank, local):
         "ms_per_step_without_graphs": round(nograph_s * 1e3 / args.steps, 4),
         "e2e": {"value": round(e2e_units / e2e_secs / 1e6, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(h2d, 1), "d2h_bytes_per_step": round(d2h, 1),
-                "loop": "vlb_step_async(1) per step, two in flight, vlb_query + vlb_query_stats per step",
+                "loop": f"vlb_step_async(1) per step, {max(1, min(args.e2e_depth, vlb.ASYNC_DEPTH))} in flight, "
+                        "vlb_query + vlb_query_stats per step",
                 "blocking_value": round(e2e_block_units / e2e_block_secs / 1e6, 2)},
         # + 1: the line-length kernel that ends each vlb_step call
         "gpu_launches": launches(int(n_before), args.steps, not args.no_overlap) + 1,
@@ -414,6 +415,8 @@ def main():
     ap.add_argument("--rate", type=float, default=8.0)
     ap.add_argument("--req-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-depth", type=int, default=2,
+                    help="one-step calls in flight in the end-to-end loop (1 to 4)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="keep the steps of the 8-step graphs in sequence (vlb_set_overlap off)")
     args = ap.parse_args()
