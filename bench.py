@@ -1,16 +1,22 @@
 """Benchmark of the coupled vortex-filament / lattice-Boltzmann step.
 
 Metric: coupled-step MLUPS (lattice cells x steps / s of the whole coupled
-step) on the closed-channel workload 64x64x256 (walls on all sides, heater
-v_n = 0.01, 20 seeded rings, ~1.2k filament points), with filament-point
-updates/s beside it.  One process per GPU; with N > 1 every rank runs an
+step) on the largest single-GPU workload, the closed channel 128x128x1024
+(~16.8M cells, walls on all sides, heater v_n = 0.01, 1.6 K, 1000 seeded
+rings of ~86k filament points, FP16 shifted population storage with FP32
+arithmetic), with filament-point updates/s beside it.  The line carries the
+roofline of the dominant kernel (the Biot-Savart sum, FP32-bound) and of the
+stream-collide pass, an end-to-end figure through the C ABI with host
+buffers, a short serving sweep with p50/p99 latency, and the FP64 oracle
+timed on the host cores.  One process per GPU; with N > 1 every rank runs an
 independent replica (the method has no exchange step at one-GPU scale), the
 timing is the max over ranks and the value the sum of all ranks' work.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl vlb|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--storage f32|f16|bf16]
+                  [--impl vlb|reference] [--serve]
 
 --impl reference times the FP64 CPU oracle on this machine's host cores on
-the same workload (the reference arm of this benchmark).
+bounded samples of the same workload (the reference arm of this benchmark).
 """
 from __future__ import annotations
 
@@ -28,9 +34,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-DEFAULT_CONFIG = "channel64x64x256"
+DEFAULT_CONFIG = "channel128x128x1024"
+DEFAULT_STORAGE = "f16"
 BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76}  # 19 populations read + 19 written per cell and pass
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+# FP32 operations of one (target, segment) pair of the straight-segment
+# Biot-Savart formula (Eq. 3): two differences, two norms, the cross and dot
+# products, the denominator and three accumulations, with FMA = 2, besides
+# 2 reciprocal square roots and 1 reciprocal
+BS_FLOP_PER_PAIR = 45
+FP32_LANES_PER_SM = 128
 
 
 def l2_note(cells: int, esize: int) -> str:
@@ -56,8 +69,7 @@ def launches(n_points: int, steps: int, overlap: bool = True) -> int:
     """Kernels of `steps` coupled steps as the library queues them: graphs of
     8 steps while 8 remain, then single steps.  In an 8-step graph the lattice
     passes after the first run alongside the filament chain and write v_n in
-    every tile (a memset node sets the tile flags), so 7 tile-flag kernels
-    drop out (unless the overlap is off)."""
+    every tile, so 7 tile-flag kernels drop out (unless the overlap is off)."""
     per = launches_per_step(n_points)
     multi, rest = divmod(steps, 8)
     return multi * (8 * per - (7 if overlap else 0)) + rest * per
@@ -139,24 +151,39 @@ def peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def k1_traffic(config_name: str):
-    """DRAM bytes per stream-collide launch from the committed ncu summary, if
-    the kernel source has not changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", f"k_lbm_step_{config_name}.md")
-    src = os.path.join(ROOT, "paper_2108_04435_gb300", "csrc", "lbm.cu")
+def profile_traffic(kernel: str, config_name: str, sources):
+    """DRAM bytes per launch of `kernel` on `config_name` from the committed ncu
+    summary profiles/<kernel>_<config>.md, if none of the kernel's source files
+    has changed since it was captured (their hash is recorded there)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{config_name}.md")
+    h = hashlib.sha256()
     try:
+        for src in sources:
+            h.update(open(os.path.join(ROOT, "paper_2108_04435_gb300", "csrc", src), "rb").read())
+        digest = h.hexdigest()[:16]
         txt = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        m = re.search(r"lbm\.cu sha256\[:16\]:\s*([0-9a-f]+)", txt)
+        m = re.search(r"sources sha256\[:16\]:\s*([0-9a-f]+)", txt)
         t = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", txt)
         if m and t and m.group(1) == digest:
             return float(t.group(1))
     except Exception:
         pass
     return None
+
+
+def workload_config(name: str, p: dict, nxt, storage: str, ws: int) -> dict:
+    """The `config` object of the JSON line, the same in both arms."""
+    cells = p["n"][0] * p["n"][1] * p["n"][2]
+    return {"workload": name,
+            "description": f"D3Q19 {p['n'][0]}x{p['n'][1]}x{p['n'][2]}, walls {tuple(p['wall'])} "
+                           f"(1 = bounce-back), heater v_n={p['heater_vn']}, alpha={p['alpha']}, "
+                           f"alpha'={p['alpha_p']}, {len(nxt)} seeded filament points on rings",
+            "cells": cells, "filament_points_start": int(len(nxt)), "storage": storage,
+            "parallelism": f"replicas x{ws}",
+            "l2": l2_note(cells, 4 if storage == "f32" else 2)}
 
 
 def run_vlb(args, ws, rank, local):
@@ -166,18 +193,29 @@ def run_vlb(args, ws, rank, local):
     from paper_2108_04435_gb300 import configs, vlb
 
     torch.cuda.set_device(local)
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
     p, xyz, nxt = configs.config(args.config, seed=rank)
     p["storage"] = STORAGE[args.storage]
     cells = p["n"][0] * p["n"][1] * p["n"][2]
     bpc = BYTES_PER_CELL[args.storage]
 
-    # --- device-resident run: inputs in HBM before the timed region; each step
-    # is replayed from the CUDA graph the library captures on first use
+    # --- device-resident run: inputs in HBM before the timed region; the steps
+    # are replayed from the CUDA graphs the library captures on first use.  The
+    # warm-up runs W steps and then the timed call's own step count (twice when
+    # it is odd), so that every graph the timed call replays -- the 8-step
+    # graphs and the single-step graphs of each buffer parity -- is captured
+    # and instantiated before the timer starts.
     stream = torch.cuda.Stream()
     ch = vlb.Channel(p, stream=stream)
     ch.set_overlap(not args.no_overlap)
     ch.seed(xyz, nxt)
     ch.step(args.warmup)
+    warm_steps = args.warmup + args.steps
+    ch.step(args.steps)
+    if args.steps % 2:
+        ch.step(args.steps)
+        warm_steps += args.steps
     n_before = ch.n_points()
     clocks = ClockSampler(local).start()
     barrier(ws)
@@ -192,21 +230,21 @@ def run_vlb(args, ws, rank, local):
     dev_s = e0.elapsed_time(e1) / 1e3
     n_after = ch.n_points()
     pts = 0.5 * (n_before + n_after) * args.steps  # filament-point updates (mean count x steps)
-    ch.close()
 
-    # --- the same K steps launched kernel by kernel with CUDA events around
-    # every stream-collide launch (graphs off): the roofline of that kernel
-    ch = vlb.Channel(p, stream=stream)
-    ch.seed(xyz, nxt)
-    ch.step(args.warmup)
+    # --- the same channel, K more steps launched kernel by kernel with CUDA
+    # events on its stream around every stream-collide and Biot-Savart launch
+    # (graphs off): the rooflines of the two kernels
     ch.set_timing(True)
+    nt0 = ch.n_points()
     torch.cuda.synchronize()
     e0.record(stream)
     ch.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     nograph_s = e0.elapsed_time(e1) / 1e3
-    k1_ms, k1_n = ch.lbm_timing()
+    nt1 = ch.n_points()
+    k1_ms, k1_n = ch.kernel_timing(vlb.TIMED_LBM)
+    bs_ms, bs_n = ch.kernel_timing(vlb.TIMED_BIOT_SAVART)
     ch.set_timing(False)
     ch.close()
 
@@ -220,18 +258,30 @@ def run_vlb(args, ws, rank, local):
     # vlb_step_async while the step before still runs, and its status is
     # read once vlb_query has completed it, so the host's launch and read
     # of one step overlap the device's next step.  The blocking loop (one
-    # vlb_step per step) is timed as well.
+    # vlb_step per step) is timed as well.  Before the timer, two untimed
+    # calls of the same kind capture the graphs the loop replays (both
+    # population parities); the filaments are then seeded again inside the
+    # timed region.
     def e2e_run(pipelined):
         ch2 = vlb.Channel(p, stream=stream)
         ch2.set_overlap(not args.no_overlap)
-        ch2.step(0)
+        ch2.seed(xyz, nxt)
+        depth = max(1, min(args.e2e_depth, vlb.ASYNC_DEPTH))
+        if pipelined:
+            for _ in range(2):
+                ch2.step_async(1)
+            for _ in range(2):
+                while not ch2.query():
+                    pass
+        else:
+            ch2.step(1)
+            ch2.step(1)
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ch2.seed(xyz, nxt)
         lengths = []
         if pipelined:
-            depth = max(1, min(args.e2e_depth, vlb.ASYNC_DEPTH))
             for k in range(args.steps + depth - 1):
                 if k < args.steps:
                     ch2.step_async(1)
@@ -261,9 +311,25 @@ def run_vlb(args, ws, rank, local):
     d2h = 12 * 8 + 12 * 4 + final.nbytes / args.steps
 
     pk, pk_kind = peaks()
+    # stream-collide: algorithmic bytes / mean event-timed launch
     k1_avg_s = (k1_ms / 1e3) / max(k1_n, 1)
-    achieved = bpc * cells / k1_avg_s / 1e9 if k1_n else None
-    traffic = k1_traffic(args.config) if args.storage == "f32" else None
+    k1_achieved = bpc * cells / k1_avg_s / 1e9 if k1_n else None
+    k1_traffic = profile_traffic("k_lbm_step", args.config, ["lbm.cu", "vlb_internal.cuh"])
+    # Biot-Savart: N (N - 2) pairs per launch at the mean live count of the
+    # event-timed steps, 45 FP32 flop each, against the FP32 peak of this
+    # GPU (SMs x 128 lanes x 2 flop x clock) at the maximum clock and at the
+    # median clock sampled during the timed region
+    n_bs = 0.5 * (nt0 + nt1)
+    pairs = n_bs * (n_bs - 2)
+    bs_avg_s = (bs_ms / 1e3) / max(bs_n, 1)
+    bs_tflops = pairs * BS_FLOP_PER_PAIR / bs_avg_s / 1e12 if bs_n else None
+    f_max = float(clk.get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0)
+    f_med = float(clk.get("sm_mhz") or f_max)
+    fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * f_max * 1e6 / 1e12
+    fp32_peak_med = n_sm * FP32_LANES_PER_SM * 2 * f_med * 1e6 / 1e12
+    bs_traffic = profile_traffic("k_biot_savart", args.config, ["bs.cu", "eom.cuh", "vlb_internal.cuh"])
+    bs_share = bs_ms / (nograph_s * 1e3) if nograph_s > 0 else None
+    config = workload_config(args.config, p, nxt, args.storage, ws)
     line = {
         "metric": "coupled-step MLUPS",
         "value": round(mlups, 2),
@@ -271,20 +337,15 @@ def run_vlb(args, ws, rank, local):
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
+        "warmup_steps_run": warm_steps,
         "ms_per_step": round(secs * 1e3 / args.steps, 4),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "storage": args.storage,
         "data": "synthetic (seeded rings, lattice initialised at uniform equilibrium)",
-        "config": {"workload": f"{args.config}: D3Q19 {p['n'][0]}x{p['n'][1]}x{p['n'][2]}, walls "
-                               f"{tuple(p['wall'])} (1 = bounce-back), heater v_n={p['heater_vn']}, "
-                               f"alpha={p['alpha']}, {len(nxt)} seeded filament points on rings",
-                   "cells": cells, "filament_points_start": int(len(nxt)),
-                   "filament_points_timed": [int(n_before), int(n_after)],
-                   "parallelism": f"replicas x{ws}",
-                   "l2": l2_note(cells, 4 if args.storage == "f32" else 2)},
+        "config": config,
+        "filament_points_timed": [int(n_before), int(n_after)],
         "filament_pts_per_s": round(pts_all / secs, 1),
         "ms_per_step_without_graphs": round(nograph_s * 1e3 / args.steps, 4),
         "e2e": {"value": round(e2e_units / e2e_secs / 1e6, 2), "unit": "MLUPS",
@@ -294,34 +355,110 @@ def run_vlb(args, ws, rank, local):
                 "blocking_value": round(e2e_block_units / e2e_block_secs / 1e6, 2)},
         # + 1: the line-length kernel that ends each vlb_step call
         "gpu_launches": launches(int(n_before), args.steps, not args.no_overlap) + 1,
-        "roofline": {"kernel": "k_lbm_step", "bound": "hbm",
-                     "achieved": round(achieved, 1) if achieved else None,
-                     "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
-                     "peak_source": f"{pk_kind} hbm_gbs (copy bandwidth)",
-                     "traffic": traffic, "algorithmic_bytes_per_launch": bpc * cells,
-                     "avg_launch_us": round(k1_avg_s * 1e6, 3), "launches": k1_n},
+        "roofline": {"kernel": "k_biot_savart", "bound": "alu",
+                     "achieved": round(bs_tflops, 3) if bs_tflops else None,
+                     "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(bs_tflops / fp32_peak, 4) if bs_tflops else None,
+                     "peak_source": f"derived FP32 peak: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                                    f"{f_max:.0f} MHz (maximum SM clock)",
+                     "frac_at_median_clock": round(bs_tflops / fp32_peak_med, 4) if bs_tflops else None,
+                     "median_clock_mhz": f_med,
+                     "traffic": bs_traffic,
+                     "flop_per_pair": BS_FLOP_PER_PAIR, "pairs_per_launch": round(pairs),
+                     "pairs_per_s": round(pairs / bs_avg_s, 1) if bs_n else None,
+                     "avg_launch_us": round(bs_avg_s * 1e6, 3), "launches": bs_n,
+                     "share_of_event_timed_step": round(bs_share, 4) if bs_share else None},
+        "roofline_lbm": {"kernel": "k_lbm_step", "bound": "hbm",
+                         "achieved": round(k1_achieved, 1) if k1_achieved else None,
+                         "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(k1_achieved / pk["hbm_gbs"], 4) if k1_achieved else None,
+                         "peak_source": f"{pk_kind} hbm_gbs (copy bandwidth)",
+                         "traffic": k1_traffic, "algorithmic_bytes_per_launch": bpc * cells,
+                         "bytes_per_cell": bpc,
+                         "avg_launch_us": round(k1_avg_s * 1e6, 3), "launches": k1_n},
         "clocks": clk,
     }
     return line, p, xyz, nxt
 
 
-def oracle_sample(p, xyz, nxt, budget_s: float, min_steps: int = 2, max_steps: int = 1000):
-    """Time the FP64 oracle on host cores for about budget_s seconds."""
-    import oracle
-    oracle.build()
-    ch = oracle.Channel(p)
-    ch.seed(xyz, nxt)
-    ch.step(1)  # first-touch of the arrays outside the timed part
-    steps, t0 = 0, time.perf_counter()
+class OracleSampler:
+    """The FP64 oracle on host cores, one bounded sample of the workload per
+    step, timed; `step_s` is the estimated time of one full oracle coupled step.
+
+    Workloads of up to 8192 filament points run whole oracle coupled steps.
+    On larger ones a full oracle step takes minutes (its Biot-Savart sums and
+    its brute-force nearest-point search both visit N (N - 2) pairs), so each
+    sample step is the oracle's lattice pass over the whole lattice, timed,
+    plus its filament phases (RK4 Biot-Savart advance, remesh, reconnection)
+    on the first rings of the seed holding about `fil_fraction` of the
+    points, timed and scaled by the ratio of the pair counts N (N - 2)."""
+
+    def __init__(self, p, xyz, nxt, fil_fraction: float = 0.125):
+        import numpy as np
+
+        import oracle
+        oracle.build()
+        self.oracle = oracle
+        self.cells = p["n"][0] * p["n"][1] * p["n"][2]
+        self.n = n = len(nxt)
+        self.full = n <= 8192
+        nxt = np.asarray(nxt)
+        if self.full:
+            self.ch = oracle.Channel(p)
+            self.ch.seed(xyz, nxt)
+            self.ch.step(1)  # first touch of the arrays outside the timed part
+            self.m = n
+            return
+        # the first closed rings (each closes back onto its first point) up to fil_fraction of the points
+        ends = [i for i in range(n) if nxt[i] < i]
+        self.m = next((e + 1 for e in ends if e + 1 >= fil_fraction * n), n)
+        self.lat = oracle.Channel(p)
+        self.lat.seed(xyz[:0], nxt[:0])
+        self.fil = oracle.Channel(p)
+        self.fil.seed(xyz[:self.m], nxt[:self.m])
+        self.lat.run_phases(oracle.PHASE_LBM)  # first touch
+        self.scale = (n * (n - 2.0)) / (self.m * (self.m - 2.0))
+
+    def step(self):
+        """One timed sample step: returns (estimated full-step seconds, lattice s, filament s)."""
+        if self.full:
+            a = time.perf_counter()
+            self.ch.step(1)
+            t = time.perf_counter() - a
+            return t, t, 0.0
+        o = self.oracle
+        a = time.perf_counter()
+        self.lat.run_phases(o.PHASE_LBM)
+        b = time.perf_counter()
+        self.fil.run_phases(o.PHASE_VFM | o.PHASE_REMESH | o.PHASE_RECONNECT)
+        c = time.perf_counter()
+        return (b - a) + (c - b) * self.scale, b - a, c - b
+
+    def describe(self, steps, t_step, t_lat, t_fil):
+        if self.full:
+            return f"{steps} full FP64 oracle coupled steps ({t_step:.2f} s each)"
+        return (f"{steps} sample steps, each the oracle lattice pass over all {self.cells} cells "
+                f"({t_lat:.2f} s) + the oracle filament phases on the first {self.m} of {self.n} seeded points "
+                f"({t_fil:.2f} s, x{self.scale:.1f} = ratio of N(N-2)); estimated full coupled step {t_step:.1f} s")
+
+    def close(self):
+        for name in ("ch", "lat", "fil"):
+            if hasattr(self, name):
+                getattr(self, name).close()
+
+
+def oracle_sample(p, xyz, nxt, budget_s: float, min_steps: int = 1, max_steps: int = 1000):
+    """Coupled-step MLUPS of the oracle from about budget_s seconds of sample
+    steps (OracleSampler), with the description of the sample."""
+    smp = OracleSampler(p, xyz, nxt)
+    steps, tot, lat, fil, t0 = 0, 0.0, 0.0, 0.0, time.perf_counter()
     while steps < max_steps and (steps < min_steps or time.perf_counter() - t0 < budget_s):
-        ch.step(1)
+        a, b, c = smp.step()
+        tot, lat, fil = tot + a, lat + b, fil + c
         steps += 1
-    secs = time.perf_counter() - t0
-    n = ch.n_points()
-    ch.close()
-    cells = p["n"][0] * p["n"][1] * p["n"][2]
-    return cells * steps / secs / 1e6, steps, secs, n
+    smp.close()
+    step_s = tot / steps
+    return smp.cells / step_s / 1e6, smp.describe(steps, step_s, lat / steps, fil / steps), step_s
 
 
 def omp_threads():
@@ -330,84 +467,96 @@ def omp_threads():
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the FP64 CPU oracle on this machine's host cores.
+    Each of the W + K steps is one bounded sample step of the workload
+    (OracleSampler), sized so that the whole run ends within a few minutes;
+    the value is the coupled-step MLUPS of the K timed samples."""
     from paper_2108_04435_gb300 import configs
     if rank != 0:
         return None
     p, xyz, nxt = configs.config(args.config, seed=0)
-    import oracle
-    oracle.build()
-    ch = oracle.Channel(p)
-    ch.seed(xyz, nxt)
-    ch.step(max(args.warmup, 0))
-    t0 = time.perf_counter()
-    ch.step(args.steps)
-    secs = time.perf_counter() - t0
+    p["storage"] = STORAGE[args.storage]
     cells = p["n"][0] * p["n"][1] * p["n"][2]
-    v = cells * args.steps / secs / 1e6
+    smp = OracleSampler(p, xyz, nxt)
+    for _ in range(max(args.warmup, 0)):
+        smp.step()
+    total_s, lat, fil = 0.0, 0.0, 0.0
+    for _ in range(args.steps):
+        a, b, c = smp.step()
+        total_s, lat, fil = total_s + a, lat + b, fil + c
+    smp.close()
+    desc = smp.describe(args.steps, total_s / args.steps, lat / args.steps, fil / args.steps)
+    v = cells * args.steps / total_s / 1e6
     cores = omp_threads()
-    sample = f"{args.steps} full oracle coupled steps of {args.config} after {args.warmup} warm-up steps"
+    sample = f"{args.config}, after {args.warmup} warm-up sample steps: {desc}"
     return {
         "impl": "reference", "metric": "coupled-step MLUPS", "value": round(v, 4), "unit": "MLUPS",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 3),
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_s * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.config, "cells": cells},
+        "config": workload_config(args.config, p, nxt, args.storage, ws),
         "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
-def run_serving(args):
+def serving_sweep(requests: int, rate: float, req_steps: int):
     """Sweep of counterflow requests (grids 32^3..128^3, 1.6/1.9/2.1 K,
     v_ns ~ U[0.005, 0.04], 100..20k points) in three forms: the plain FP32
     single-run form (one request at a time, arrivals ignored), and the serving
-    form (Poisson arrivals, up to 16 runs admitted by memory budget, steps in
-    slices on separate streams) with FP32 and with FP16 population storage."""
+    form (up to 16 runs admitted by memory budget, steps in slices on separate
+    streams) with FP32 and with FP16 population storage; then the latency of
+    the FP16 serving form under Poisson arrivals at `rate`/s.  Failed requests
+    are counted in each form with their error messages (CFL: a point moved a
+    cell within one step; MACH: |u|/c_s reached 0.05)."""
     import copy
+
+    import torch
 
     from paper_2108_04435_gb300 import configs, serve
 
-    # 16 runs on their own streams: more hardware queues than the default 8
-    # (read when the CUDA context is created, so before the first CUDA call)
-    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", str(serve.MAX_CONNECTIONS))
-    import torch
     torch.cuda.set_device(0)
+    torch.cuda.empty_cache()
     free, total = torch.cuda.mem_get_info()
     budget = int(min(free * 0.8, 64 << 30))
     out = {}
     # sweep throughput: every request available at once
     for form, storage, slots in (("fp32_single_run", 0, 1), ("fp32_serving", 0, 16), ("fp16_serving", 1, 16)):
-        reqs = configs.serving_requests(args.requests, args.rate, 0, args.req_steps, storage=storage)
+        reqs = configs.serving_requests(requests, rate, 0, req_steps, storage=storage)
         res, summ = serve.serve_gpu(copy.deepcopy(reqs), budget_bytes=budget, max_slots=slots, slice_steps=50,
                                     realtime=False)
         out[form] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()}
     # latency: Poisson arrivals, FP16 serving form
-    reqs = configs.serving_requests(args.requests, args.rate, 0, args.req_steps, storage=1)
+    reqs = configs.serving_requests(requests, rate, 0, req_steps, storage=1)
     res, lat = serve.serve_gpu(copy.deepcopy(reqs), budget_bytes=budget, max_slots=16, slice_steps=50, realtime=True)
     lat = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in lat.items()}
     base = out["fp32_single_run"]["throughput_req_per_s"]
-    line = {
+    return {
         "metric": "serving sweep throughput", "value": out["fp16_serving"]["throughput_req_per_s"],
         "unit": "requests/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "storage": "f16",
         "data": "synthetic",
-        "config": {"workload": f"{args.requests} counterflow requests, {args.req_steps} coupled steps each, "
-                               f"periodic grids 32^3..128^3, 1.6/1.9/2.1 K",
+        "config": {"workload": f"{requests} counterflow requests, {req_steps} coupled steps each, "
+                               f"periodic grids 32^3..128^3, 1.6/1.9/2.1 K, Poisson arrivals at {rate}/s",
                    "budget_bytes": budget},
         "speedup_vs_fp32_single_run": round(out["fp16_serving"]["throughput_req_per_s"] / base, 3) if base else None,
         "p50_latency_s": lat["p50_latency_s"], "p99_latency_s": lat["p99_latency_s"],
-        "latency_run": {"arrival_rate_per_s": args.rate, **lat},
+        "failed": {form: out[form]["failed"] for form in out} | {"fp16_serving_poisson": lat["failed"]},
+        "latency_run": {"arrival_rate_per_s": rate, **lat},
         "forms": out,
     }
-    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    print(json.dumps(serving_sweep(args.requests, args.rate, args.req_steps)), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--config", default=DEFAULT_CONFIG)
     ap.add_argument("--impl", default="vlb", choices=["vlb", "reference"])
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+    ap.add_argument("--storage", default=DEFAULT_STORAGE, choices=["f32", "f16", "bf16"],
                     help="population storage (arithmetic is FP32 in all)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--serve", action="store_true", help="serving sweep instead of the coupled-step benchmark")
@@ -415,6 +564,8 @@ def main():
     ap.add_argument("--rate", type=float, default=8.0)
     ap.add_argument("--req-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving-sample", action="store_true",
+                    help="leave out the short serving sweep added to the coupled-step line")
     ap.add_argument("--e2e-depth", type=int, default=2,
                     help="one-step calls in flight in the end-to-end loop (1 to 4)")
     ap.add_argument("--no-overlap", action="store_true",
@@ -422,6 +573,11 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
+    if args.serve or (args.impl == "vlb" and ws == 1 and not args.no_serving_sample):
+        # many runs on their own streams: more hardware queues than the default
+        # 8 (read when the CUDA context is created, so before the first CUDA call)
+        from paper_2108_04435_gb300 import serve
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", str(serve.MAX_CONNECTIONS))
     if ws > 1:
         import torch.distributed as dist
         backend = "gloo" if args.impl == "reference" else "nccl"
@@ -438,13 +594,19 @@ def main():
             print(json.dumps(line), flush=True)
     else:
         line, p, xyz, nxt = run_vlb(args, ws, rank, local)
-        if rank == 0:
-            if ws == 1 and not args.no_cpu_baseline:
-                v, steps, secs, n = oracle_sample(p, xyz, nxt, args.cpu_budget)
+        if rank == 0 and ws == 1:
+            if not args.no_serving_sample:
+                sv = serving_sweep(args.requests, args.rate, args.req_steps)
+                line["serving"] = {k: sv[k] for k in ("value", "unit", "speedup_vs_fp32_single_run", "p50_latency_s",
+                                                      "p99_latency_s", "failed", "config")}
+                line["serving"]["forms"] = {f: {k: v[k] for k in ("throughput_req_per_s", "mlups", "failed",
+                                                                  "errors", "wall_s")}
+                                            for f, v in sv["forms"].items()}
+            if not args.no_cpu_baseline:
+                v, desc, _ = oracle_sample(p, xyz, nxt, args.cpu_budget)
                 line["cpu_baseline"] = {"value": round(v, 4), "unit": "MLUPS", "cores": omp_threads(),
-                                        "kind": "oracle",
-                                        "sample": f"{steps} full FP64 oracle coupled steps of {args.config} from the "
-                                                  f"seeded state ({secs:.1f} s)"}
+                                        "kind": "oracle", "sample": f"{args.config}: {desc}"}
+        if rank == 0:
             print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

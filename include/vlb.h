@@ -222,11 +222,19 @@ void vlb_destroy(vlb_channel* ch);
 /* Message of the last error on this thread (never NULL). */
 const char* vlb_last_error(void);
 
-/* Device time of the lattice pass (Eqs. 9, 14) accumulated while `enable` is
- * set: CUDA events recorded on the channel stream around every launch of the
- * stream-collide kernel.  vlb_lbm_timing returns the total milliseconds and
- * launch count since the last reset (after a stream sync). */
+/* Event-timed mode.  While `enable` is set, vlb_step launches the kernels of
+ * each step one by one (no graph replay, no programmatic launch) and records
+ * CUDA events on the channel's stream around every launch of two kernels:
+ *   VLB_TIMED_LBM          the stream-collide pass (Eqs. 9, 14)
+ *   VLB_TIMED_BIOT_SAVART  the Biot-Savart sum of each RK stage (Eq. 3; from
+ *                          24576 points on it also applies Eq. 4 to its targets)
+ * vlb_set_timing resets the totals.  vlb_kernel_timing returns the total
+ * milliseconds and launch count of one kind since the last reset (after a
+ * stream sync); vlb_lbm_timing is vlb_kernel_timing of VLB_TIMED_LBM.
+ * Errors: INVALID_ARG (null argument, unknown kind), CUDA. */
+enum { VLB_TIMED_LBM = 0, VLB_TIMED_BIOT_SAVART = 1, VLB_TIMED_KINDS = 2 };
 int vlb_set_timing(vlb_channel* ch, int32_t enable);
+int vlb_kernel_timing(vlb_channel* ch, int32_t kind, double* total_ms, int64_t* launches);
 int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches);
 
 /* Stand-alone Biot-Savart velocity (Eq. 3, nonlocal part: every segment j ->

@@ -29,7 +29,10 @@ def _stale(target: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "vlb_internal.cuh"), os.path.join(HERE, "..", "include", "vlb.h"), __file__]
+    # every header a translation unit may include: an edit to any of them
+    # rebuilds every object
+    headers = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+    headers += [os.path.join(HERE, "..", "include", "vlb.h"), __file__]
     objs, jobs = [], []
     for src, extra in SOURCES.items():
         s = os.path.join(CSRC, src)

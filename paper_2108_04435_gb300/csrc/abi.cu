@@ -62,8 +62,10 @@ struct vlb_channel {
     // [steps per graph: 1 or GRAPH_MULTI][cur_f][cur_p]
     cudaGraphExec_t gexec[2][2][2] = {{{nullptr, nullptr}, {nullptr, nullptr}}, {{nullptr, nullptr}, {nullptr, nullptr}}};
     int gclass[2][2][2] = {{{-1, -1}, {-1, -1}}, {{-1, -1}, {-1, -1}}};  // filament size class at capture
-    std::vector<cudaEvent_t> ev;
-    size_t ev_used = 0;
+    // event-timed mode: CUDA events around every launch of one kernel kind
+    // (VLB_TIMED_*), in pairs, on the channel's stream
+    std::vector<cudaEvent_t> ev[VLB_TIMED_KINDS];
+    size_t ev_used[VLB_TIMED_KINDS] = {};
     // vlb_step_async calls in flight: each copies the status block into its
     // own pinned slot and records its own event; vlb_query completes the
     // oldest (slots q_tail .. q_head - 1, modulo VLB_ASYNC_DEPTH)
@@ -93,8 +95,8 @@ struct vlb_channel {
     bool overlap = true;  // multi-step graphs use the second stream (vlb_set_overlap)
     bool line_fresh = false;  // h_dstats[DS_LINE] holds the line length of the current points
     bool side_failed = false;  // the second stream could not be created
-    double timing_ms = 0.0;
-    long long timing_launches = 0;
+    double timing_ms[VLB_TIMED_KINDS] = {};
+    long long timing_launches[VLB_TIMED_KINDS] = {};
 
     void* dalloc(size_t bytes) {
         if (bytes == 0) bytes = 16;
@@ -123,8 +125,10 @@ void release(vlb_channel* ch) {
         else cudaFree(b);
     }
     ch->blocks.clear();
-    for (cudaEvent_t e : ch->ev) cudaEventDestroy(e);
-    ch->ev.clear();
+    for (auto& list : ch->ev) {
+        for (cudaEvent_t e : list) cudaEventDestroy(e);
+        list.clear();
+    }
     for (cudaEvent_t& e : ch->q_ev) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
@@ -191,13 +195,14 @@ int sync_counters(vlb_channel* ch) {
     return VLB_OK;
 }
 
-void record_event(vlb_channel* ch) {
-    if (ch->ev_used == ch->ev.size()) {
+void record_event(vlb_channel* ch, int kind) {
+    std::vector<cudaEvent_t>& list = ch->ev[kind];
+    if (ch->ev_used[kind] == list.size()) {
         cudaEvent_t e;
         cudaEventCreate(&e);
-        ch->ev.push_back(e);
+        list.push_back(e);
     }
-    cudaEventRecord(ch->ev[ch->ev_used++], ch->stream);
+    cudaEventRecord(list[ch->ev_used[kind]++], ch->stream);
 }
 
 // Flag the velocity tiles around the current points for the next lattice
@@ -212,11 +217,11 @@ void mark_points(vlb_channel* ch) {
 // (as [0], [1]) instead of into the status block's own slots.
 void lattice_pass(vlb_channel* ch, bool all_u = false, double* stats = nullptr) {
     Dev& d = ch->d;
-    if (ch->timing) record_event(ch);
+    if (ch->timing) record_event(ch, VLB_TIMED_LBM);
     LbmParams L = ch->lp;
     L.all_u = all_u ? 1 : 0;
     launch_lbm_step(L, d.f[ch->cur_f], d.f[ch->cur_f ^ 1], d.F, d.U, d.fmask, d.umask, d.part, ch->stream);
-    if (ch->timing) record_event(ch);
+    if (ch->timing) record_event(ch, VLB_TIMED_LBM);
     ch->cur_f ^= 1;
     // the pass consumed the force grid: the plane reduction resets it and clears both tile flags
     LbmParams R = ch->lp;
@@ -296,12 +301,16 @@ void vfm_step(vlb_channel* ch, bool pre_done, cudaStream_t s) {
             }
             launch_geometry_stage(V, stage == 0 ? ea.pos_out : d.st, next, prev, d.counters, ch->cap, d.geo, d.seg,
                                   stage == 0 ? d.s0 : nullptr, s);
+            const bool timed = ch->timing && s == ch->stream;
+            if (timed) record_event(ch, VLB_TIMED_BIOT_SAVART);
             if (fused_eom(ch->n_hint)) {
                 launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp,
                                    d.vbs, s, &ea, V.nfaces, V.face_code, d.geo);
+                if (timed) record_event(ch, VLB_TIMED_BIOT_SAVART);
             } else {
                 launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp,
                                    d.vbs, s, nullptr, V.nfaces, V.face_code, d.geo, vacc);
+                if (timed) record_event(ch, VLB_TIMED_BIOT_SAVART);
                 launch_eom(ea, d.vbs, s, vacc);
             }
         }
@@ -1282,26 +1291,34 @@ int vlb_set_timing(vlb_channel* ch, int32_t enable) {
     join_side(ch);
     cudaStreamSynchronize(ch->stream);
     ch->timing = enable != 0;
-    ch->ev_used = 0;
-    ch->timing_ms = 0.0;
-    ch->timing_launches = 0;
+    for (int k = 0; k < VLB_TIMED_KINDS; ++k) {
+        ch->ev_used[k] = 0;
+        ch->timing_ms[k] = 0.0;
+        ch->timing_launches[k] = 0;
+    }
+    return VLB_OK;
+}
+
+int vlb_kernel_timing(vlb_channel* ch, int32_t kind, double* total_ms, int64_t* launches) {
+    if (!ch || !total_ms || !launches) return fail(VLB_ERR_INVALID_ARG, "null argument");
+    if (kind < 0 || kind >= VLB_TIMED_KINDS) return fail(VLB_ERR_INVALID_ARG, "unknown timed kernel kind");
+    cudaError_t e = cudaStreamSynchronize(ch->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "timing sync");
+    std::vector<cudaEvent_t>& list = ch->ev[kind];
+    for (size_t k = 0; k + 1 < ch->ev_used[kind]; k += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, list[k], list[k + 1]);
+        ch->timing_ms[kind] += ms;
+        ch->timing_launches[kind]++;
+    }
+    ch->ev_used[kind] = 0;
+    *total_ms = ch->timing_ms[kind];
+    *launches = ch->timing_launches[kind];
     return VLB_OK;
 }
 
 int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches) {
-    if (!ch || !total_ms || !launches) return fail(VLB_ERR_INVALID_ARG, "null argument");
-    cudaError_t e = cudaStreamSynchronize(ch->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "timing sync");
-    for (size_t k = 0; k + 1 < ch->ev_used; k += 2) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ch->ev[k], ch->ev[k + 1]);
-        ch->timing_ms += ms;
-        ch->timing_launches++;
-    }
-    ch->ev_used = 0;
-    *total_ms = ch->timing_ms;
-    *launches = ch->timing_launches;
-    return VLB_OK;
+    return vlb_kernel_timing(ch, VLB_TIMED_LBM, total_ms, launches);
 }
 
 size_t vlb_biot_savart_scratch_bytes(int32_t n) {

@@ -25,9 +25,11 @@ FIELD_PLANE_VS, FIELD_STATS, FIELD_VEL, FIELD_FDEV, FIELD_LINE_PROFILE = 6, 7, 8
 EXPORTS = ["vlb_create_channel", "vlb_seed_vortices", "vlb_step", "vlb_run_phases", "vlb_read_fields",
            "vlb_write_fields", "vlb_line_length", "vlb_destroy", "vlb_last_error", "vlb_set_timing",
            "vlb_lbm_timing", "vlb_biot_savart_scratch_bytes", "vlb_biot_savart", "vlb_set_graphs", "vlb_set_overlap",
-           "vlb_biot_savart_noalloc", "vlb_step_async", "vlb_query", "vlb_query_stats", "vlb_channel_bytes"]
+           "vlb_biot_savart_noalloc", "vlb_step_async", "vlb_query", "vlb_query_stats", "vlb_channel_bytes",
+           "vlb_kernel_timing"]
 BUSY = 1
 ASYNC_DEPTH = 4  # vlb_step_async calls a channel holds in flight
+TIMED_LBM, TIMED_BIOT_SAVART = 0, 1  # kernel kinds of the event-timed mode
 
 
 class Params(C.Structure):
@@ -83,6 +85,7 @@ def lib():
         L.vlb_set_graphs.argtypes = [vp, C.c_int32]
         L.vlb_set_overlap.argtypes = [vp, C.c_int32]
         L.vlb_lbm_timing.argtypes = [vp, dp, C.POINTER(C.c_int64)]
+        L.vlb_kernel_timing.argtypes = [vp, C.c_int32, dp, C.POINTER(C.c_int64)]
         L.vlb_biot_savart_scratch_bytes.argtypes = [C.c_int32]
         L.vlb_biot_savart_scratch_bytes.restype = C.c_size_t
         L.vlb_biot_savart.argtypes = [C.POINTER(Params), vp, vp, C.c_int32, vp, vp, C.c_size_t, vp]
@@ -247,8 +250,12 @@ class Channel:
         check(lib().vlb_set_timing(self.h, 1 if enable else 0))
 
     def lbm_timing(self):
+        return self.kernel_timing(TIMED_LBM)
+
+    def kernel_timing(self, kind: int):
+        """(total ms, launches) of one kernel kind since set_timing(True)."""
         ms, n = C.c_double(), C.c_int64()
-        check(lib().vlb_lbm_timing(self.h, C.byref(ms), C.byref(n)))
+        check(lib().vlb_kernel_timing(self.h, kind, C.byref(ms), C.byref(n)))
         return ms.value, n.value
 
 
