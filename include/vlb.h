@@ -244,8 +244,13 @@ int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches);
  *   next     device int32 [n] successor indices, -1 at the last point of an
  *            open line (that point starts no segment)
  *   vel      device float32 SoA [3][n], written
- *   scratch  device buffer of at least vlb_biot_savart_scratch_bytes(n) bytes
- * Uses only p->n, p->wall and p->kappa.  Runs on `stream`; does not wait. */
+ *   scratch  device buffer of at least vlb_biot_savart_scratch_bytes(n) bytes,
+ *            256-byte aligned; its contents need not be initialised
+ * Uses only p->n, p->wall and p->kappa.  Runs on `stream` and does not wait,
+ * so it returns only the errors it can see on the host (INVALID_ARG for bad
+ * arguments or a small scratch, CUDA for a failed launch): device-side
+ * findings (a next[] entry outside [-1, n), a timed-out tile copy) are not
+ * reported, and vel is then not meaningful. */
 size_t vlb_biot_savart_scratch_bytes(int32_t n);
 int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next, int32_t n,
                     float* vel, void* scratch, size_t scratch_bytes, void* stream);
@@ -255,15 +260,18 @@ int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next,
  * while they run, e.g. hosts that only hand out pre-registered buffers or
  * code that must not trigger the device synchronisation cudaMalloc implies).
  * Same arguments and result as vlb_biot_savart, without the scratch buffer:
- * the scratch lives in a fixed 6 MiB file-scope device array that every GPU
+ * the scratch lives in a fixed 8 MiB file-scope device array that every GPU
  * loading this library holds until the process exits, and no cudaMalloc,
- * cudaFree or allocating library routine is called.
+ * cudaFree or allocating library routine is called.  A compile-time check
+ * keeps the array at least as large as the scratch of a 65536-point call.
  *   n        at most 65536 points; larger n returns VLB_ERR_INVALID_ARG
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.  All calls share the one array, so
- * calls whose work overlaps on the GPU (other streams, other threads) race:
- * serialise them.  Runs on `stream`; does not wait. */
+ * (cudaGetSymbolAddress, with that device current) and caches it for the
+ * life of the process; make that first call before any stream capture, and
+ * make no call after a cudaDeviceReset of that device.  All calls share the
+ * one array, so calls whose work overlaps on the GPU (other streams, other
+ * threads) race: serialise them.  Runs on `stream`; does not wait; reports
+ * no device-side findings (as vlb_biot_savart). */
 int vlb_biot_savart_noalloc(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel,
                             void* stream);
 

@@ -246,12 +246,36 @@ bool fused_eom(int n) {
 
 // Stage-0 geometry and Biot-Savart sum of the first sub-step: they read only
 // the points, so they may run before the lattice pass is done.
+// Order of the Biot-Savart sources for the current filament size: spatial
+// from BS_SORT_MIN points on (the pair sums are compute-bound there and
+// compact groups of sources take the cheap pair path), point order below.
+BsOrder bs_order(vlb_channel* ch) {
+    BsOrder o;
+    o.sorted = ch->n_hint >= BS_SORT_MIN ? 1 : 0;
+    o.ord = ch->d.bs_ord;
+    o.rank = ch->d.bs_rank;
+    o.org = ch->d.bs_org;
+    return o;
+}
+
+// The spatial order of the current points (before the first stage geometry
+// of a step; the order then serves every RK stage of the step).
+void bs_sort(vlb_channel* ch, const BsOrder& o, cudaStream_t s) {
+    if (!o.sorted) return;
+    Dev& d = ch->d;
+    launch_bs_sort(ch->vp.g, d.pos[ch->cur_p], ch->cap, point_span(ch->n_hint, ch->cap), d.counters, d.bs_key,
+                   d.bs_tmp, d.bs_ord, d.bs_rank, d.bs_org, d.bs_cnt, d.bs_start, s);
+}
+
 void vfm_pre(vlb_channel* ch, cudaStream_t s) {
     Dev& d = ch->d;
     const VfmParams& V = ch->vp;
     const int* prev = d.prev[ch->cur_p];
-    launch_geometry_stage(V, d.pos[ch->cur_p], d.next[ch->cur_p], prev, d.counters, ch->cap, d.geo, d.seg, d.s0, s);
-    launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp, d.vbs, s,
+    const BsOrder o = bs_order(ch);
+    bs_sort(ch, o, s);
+    launch_geometry_stage(V, d.pos[ch->cur_p], d.next[ch->cur_p], prev, d.counters, ch->cap, d.geo, d.seg, d.s0, o,
+                          s);
+    launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp, d.vbs, s, o,
                        nullptr, V.nfaces, V.face_code, d.geo, d.vacc);
 }
 
@@ -285,6 +309,7 @@ void vfm_step(vlb_channel* ch, bool pre_done, cudaStream_t s) {
     const int* prev = d.prev[ch->cur_p];
     const int nsub = ch->p.vfm_substeps > 0 ? ch->p.vfm_substeps : 1;
     EomArgs ea = eom_args(ch);
+    const BsOrder o = bs_order(ch);
     for (int sub = 0; sub < nsub; ++sub) {
         const int spread = (sub == 0 && ch->p.couple) ? 1 : 0;
         if (spread && !ch->f_clean) launch_zero_force(ch->lp.g, d.F, d.fmask, s);
@@ -299,17 +324,18 @@ void vfm_step(vlb_channel* ch, bool pre_done, cudaStream_t s) {
                 launch_eom(ea, d.vbs, s, vacc);
                 continue;
             }
+            if (sub == 0 && stage == 0) bs_sort(ch, o, s);
             launch_geometry_stage(V, stage == 0 ? ea.pos_out : d.st, next, prev, d.counters, ch->cap, d.geo, d.seg,
-                                  stage == 0 ? d.s0 : nullptr, s);
+                                  stage == 0 ? d.s0 : nullptr, o, s);
             const bool timed = ch->timing && s == ch->stream;
             if (timed) record_event(ch, VLB_TIMED_BIOT_SAVART);
             if (fused_eom(ch->n_hint)) {
                 launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp,
-                                   d.vbs, s, &ea, V.nfaces, V.face_code, d.geo);
+                                   d.vbs, s, o, &ea, V.nfaces, V.face_code, d.geo);
                 if (timed) record_event(ch, VLB_TIMED_BIOT_SAVART);
             } else {
                 launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp,
-                                   d.vbs, s, nullptr, V.nfaces, V.face_code, d.geo, vacc);
+                                   d.vbs, s, o, nullptr, V.nfaces, V.face_code, d.geo, vacc);
                 if (timed) record_event(ch, VLB_TIMED_BIOT_SAVART);
                 launch_eom(ea, d.vbs, s, vacc);
             }
@@ -404,8 +430,9 @@ bool pdl_enabled() {
 }
 
 // Stand-alone Biot-Savart velocity on caller-provided device buffers; the
-// scratch layout is counters | prev | source records | split partials |
-// per-tile tickets, each 256-byte aligned.  Allocates nothing.
+// scratch layout is the one bs_scratch_bytes sizes, each part 256-byte
+// aligned.  The split sums are added in fixed point (exact, in any order) and
+// converted to float at the end.  Allocates nothing.
 int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel, void* scratch,
                   size_t scratch_bytes, void* stream) {
     if (!p || n < 0 || (n > 0 && (!pos || !next || !vel || !scratch)))
@@ -413,7 +440,7 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
     if (n == 0) return VLB_OK;
     for (int a = 0; a < 3; ++a)
         if (p->n[a] < 1 || (p->wall[a] != 0 && p->wall[a] != 1)) return fail(VLB_ERR_INVALID_ARG, "bad box");
-    if (scratch_bytes < vlb_biot_savart_scratch_bytes(n)) return fail(VLB_ERR_INVALID_ARG, "scratch too small");
+    if (scratch_bytes < bs_scratch_bytes(n)) return fail(VLB_ERR_INVALID_ARG, "scratch too small");
     if (((uintptr_t)scratch & 255u) != 0) return fail(VLB_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
     Grid g;
     g.nx = p->n[0];
@@ -422,21 +449,36 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
     for (int a = 0; a < 3; ++a) g.wall[a] = p->wall[a];
     g.ncell = (long long)g.nx * g.ny * g.nz;
     g.tnx = g.tny = g.tnz = 1;
-    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t groups = (size_t)((n + BS_GROUP - 1) / BS_GROUP);
     char* base = (char*)scratch;
-    int* counters = (int*)base;
-    base += up(sizeof(int) * CNT_COUNT);
-    int* prev = (int*)base;
-    base += up(sizeof(int) * (size_t)n);
-    float4* seg = (float4*)base;
-    base += up(sizeof(float4) * 3 * (size_t)n);
-    float* bsp = (float*)base;
-    base += up(sizeof(float) * 3 * (size_t)n * (size_t)bs_splits(n, BS_TPB));
-    int* tickets = (int*)base;
+    auto take = [&](size_t bytes) {
+        char* q = base;
+        base += bs_up256(bytes);
+        return (void*)q;
+    };
+    int* counters = (int*)take(sizeof(int) * 16);
+    int* prev = (int*)take(sizeof(int) * (size_t)n);
+    float4* seg = (float4*)take(sizeof(float4) * BS_REC * groups * BS_GROUP);
+    int* key = (int*)take(sizeof(int) * (size_t)n);
+    int* tmp = (int*)take(sizeof(int) * (size_t)n);
+    int* ord = (int*)take(sizeof(int) * (size_t)n);
+    int* rank = (int*)take(sizeof(int) * (size_t)n);
+    int4* org = (int4*)take(sizeof(int4) * groups);
+    int* cnt = (int*)take(sizeof(int) * BS_SORT_MAX_BINS);
+    int* start = (int*)take(sizeof(int) * BS_SORT_MAX_BINS);
+    long long* vacc = (long long*)take(sizeof(long long) * 3 * (size_t)n);
     cudaStream_t s = (cudaStream_t)stream;
-    cudaMemsetAsync(tickets, 0, sizeof(int) * (size_t)((n + BS_TPB - 1) / BS_TPB), s);
-    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, s);
-    launch_biot_savart(g, p->kappa, seg, prev, counters, tickets, n, n, bsp, vel, s);
+    BsOrder o;
+    o.sorted = n >= BS_SORT_MIN ? 1 : 0;
+    o.ord = ord;
+    o.rank = rank;
+    o.org = org;
+    if (o.sorted) cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)bs_bins(g.nx, g.ny, g.nz).K, s);
+    cudaMemsetAsync(vacc, 0, sizeof(long long) * 3 * (size_t)n, s);
+    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, o, key, tmp, cnt, start, s);
+    launch_biot_savart(g, p->kappa, seg, prev, counters, nullptr, n, n, nullptr, vel, s, o, nullptr, 0, nullptr,
+                       nullptr, vacc);
+    launch_bs_unfix(vacc, n, vel, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "Biot-Savart launch");
     return VLB_OK;
@@ -464,9 +506,12 @@ size_t vlb_channel_bytes(const vlb_params* p) {
     size_t nfaces = 0;
     if (p->wall_images)
         for (int a = 0; a < 3; ++a) nfaces += p->wall[a] ? 2 : 0;
+    const size_t capg = (size_t)bs_block((int)cap, 1);
     b += 2 * (up(24 * cap) + 2 * up(4 * cap)) + 6 * up(24 * cap) + up(8 * cap) + up(32 * cap) +
-         up(48 * cap * (1 + nfaces));
-    b += up(12 * cap * (size_t)bs_max_splits((int)cap)) + up(12 * cap) + up(24 * cap) + up(4 * ((cap + 127) / 128));
+         up(sizeof(float4) * BS_REC * capg * (1 + nfaces));
+    b += up(12 * cap * (size_t)bs_max_splits((int)cap, sm_count())) + up(12 * cap) + up(24 * cap) +
+         up(4 * ((cap + 127) / 128));
+    b += 4 * up(4 * cap) + up(16 * (capg / BS_GROUP)) + 2 * up(4 * (size_t)bs_bins(p->n[0], p->n[1], p->n[2]).K);
     b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(16 * cap) + up(8 * cap);
     const size_t nc = cap / 2 + 1;
     b += 4 * up(4 * nc) + up(8 * nc) + up(4 * cap) + up(8 * ((cap + 255) / 256));
@@ -580,8 +625,8 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     V.dt = 1.0 / (double)p->vfm_substeps;
     V.couple = p->couple;
     V.force_form = p->force_form;
-    V.kq_f = (float)(p->kappa / (4.0 * 3.14159265358979323846));
-    V.inv_ea_f = (float)(1.0 / (exp(0.25) * p->core_a));
+    V.kq = p->kappa / (4.0 * 3.14159265358979323846);
+    V.inv_ea = 1.0 / (exp(0.25) * p->core_a);
     V.alpha_f = (float)p->alpha;
     V.alpha_p_f = (float)p->alpha_p;
     V.gscale_f = (float)(-p->rho_s_over_rho_n * p->rho0 * p->kappa);
@@ -598,8 +643,10 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     while (h < 2 * cap) h <<= 1;
     ch->hsize = h;
     ch->bpp = lbm_blocks_per_plane(L);
-    const int nsm = bs_max_splits(cap);
+    const int nsm = bs_max_splits(cap, sm_count());
     ch->nsplit_max = nsm;
+    const BsBins bins = bs_bins(g.nx, g.ny, g.nz);
+    const size_t capg = (size_t)bs_block(cap, 1);  // capacity rounded up to whole record groups
     const int ntiles = g.tnx * g.tny * g.tnz;
     Dev& d = ch->d;
     bool ok = true;
@@ -635,7 +682,14 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.spp = (double*)A(P3);
     d.seglen = (double*)A(sizeof(double) * (size_t)cap);
     d.geo = (float4*)A(sizeof(float4) * 2 * (size_t)cap);
-    d.seg = (float4*)A(sizeof(float4) * 3 * (size_t)cap * (size_t)(1 + V.nfaces));  // segments, then wall images
+    d.seg = (float4*)A(sizeof(float4) * BS_REC * capg * (size_t)(1 + V.nfaces));  // segments, then wall images
+    d.bs_key = (int*)A(sizeof(int) * (size_t)cap);
+    d.bs_tmp = (int*)A(sizeof(int) * (size_t)cap);
+    d.bs_ord = (int*)A(sizeof(int) * (size_t)cap);
+    d.bs_rank = (int*)A(sizeof(int) * (size_t)cap);
+    d.bs_org = (int4*)A(sizeof(int4) * (capg / BS_GROUP));
+    d.bs_cnt = (int*)A(sizeof(int) * (size_t)bins.K);
+    d.bs_start = (int*)A(sizeof(int) * (size_t)bins.K);
     d.bsp = (float*)A(sizeof(float) * 3 * (size_t)cap * (size_t)nsm);
     d.vbs = (float*)A(sizeof(float) * 3 * (size_t)cap);
     d.vacc = (long long*)A(sizeof(long long) * 3 * (size_t)cap);
@@ -690,6 +744,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     cudaMemsetAsync(d.vel1, 0, sizeof(double) * 3 * (size_t)cap, s);
     cudaMemsetAsync(d.bsp, 0, sizeof(float) * 3 * (size_t)cap * (size_t)nsm, s);
     cudaMemsetAsync(d.tile_ticket, 0, sizeof(int) * (size_t)((cap + BS_TPB - 1) / BS_TPB), s);
+    cudaMemsetAsync(d.bs_cnt, 0, sizeof(int) * (size_t)bins.K, s);  // the sort clears what it counts
     init_hash(d, h, s);
     launch_lbm_init(L, d.f[0], d.U, p->init_vn, s);
     std::vector<double> vs((size_t)g.nz, -(1.0 / p->rho_s_over_rho_n) * p->init_vn[2]);
@@ -1321,13 +1376,7 @@ int vlb_lbm_timing(vlb_channel* ch, double* total_ms, int64_t* launches) {
     return vlb_kernel_timing(ch, VLB_TIMED_LBM, total_ms, launches);
 }
 
-size_t vlb_biot_savart_scratch_bytes(int32_t n) {
-    if (n < 1) n = 1;
-    const int ns = bs_splits(n, BS_TPB);
-    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return up(sizeof(int) * CNT_COUNT) + up(sizeof(int) * (size_t)n) + up(sizeof(float4) * 3 * (size_t)n) +
-           up(sizeof(float) * 3 * (size_t)n * (size_t)ns) + up(sizeof(int) * (size_t)((n + BS_TPB - 1) / BS_TPB));
-}
+size_t vlb_biot_savart_scratch_bytes(int32_t n) { return bs_scratch_bytes(n < 1 ? 1 : n); }
 
 int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel, void* scratch,
                     size_t scratch_bytes, void* stream) {

@@ -7,14 +7,28 @@
 //     v = kappa/(4 pi) (R1 x R2) (|R1| + |R2|) / (|R1||R2| (|R1||R2| + R1.R2)).
 // The two segments touching the target are left to the local term.
 //
-// GB300 mapping: one target per thread (position in registers as float hi+lo
-// parts, so that R1 keeps ~1e-7 relative accuracy in boxes up to 1024 cells),
-// source segments streamed through shared memory in tiles that a single
-// thread fetches with TMA bulk copies (cp.async.bulk + mbarrier, double
-// buffered), every lane reading each record as a broadcast.  This is FP32 +
-// MUFU work (2 rsqrt + 1 reciprocal per pair), not a contraction, so no tensor
-// cores.  Small filament sets are split over source chunks (grid.y); the
-// partial sums are reduced later in a fixed order.
+// GB300 mapping.  This is FP32 + MUFU work (2 rsqrt + 1 reciprocal per pair),
+// not a contraction, so no tensor cores.  Targets sit in registers (one or
+// two per thread); source records stream through shared memory in tiles that
+// one thread fetches with bulk copies (cp.async.bulk + mbarrier, double
+// buffered), every lane reading each record as a broadcast.
+//
+// From BS_SORT_MIN points on, the points are put in a spatial (Morton) order
+// once per step, and each group of BS_GROUP consecutive records stores its
+// positions relative to an integer origin.  A target then meets a group
+// through one offset t = (O - O_t) - h_t - l_t formed exactly once per group;
+// the group's box decides, for the whole warp, between three pair paths:
+//  - near (some source within BS_NEAR cells of the target in any periodic
+//    image): full precision (h + l + t, the offset split in two floats), the
+//    minimum image (decided in FP64 within 1e-3 of half the box, as the FP64
+//    difference of the positions decides it), on-segment guard and the
+//    target's own segments masked;
+//  - wrap (a source may lie half a periodic box away): the same precision and
+//    minimum image, no guard;
+//  - far (everything else): h + t only, and the cross product R1 x d split
+//    into the stored h x d and one t x (sum fac d) per group.
+// Splits of the source range are summed in a fixed order (or exactly, in
+// fixed point), so every result is bitwise reproducible.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -73,9 +87,9 @@ struct BoxF {
 };
 
 __device__ __forceinline__ void issue_tile(float4* dst, const float4* seg, int jb, int cnt, uint64_t* bar) {
-    const uint32_t bytes = (uint32_t)cnt * 48u;
+    const uint32_t bytes = (uint32_t)cnt * (uint32_t)(BS_REC * sizeof(float4));
     mbar_expect_tx(bar, bytes);
-    bulk_copy_g2s(dst, seg + 3LL * jb, bytes, bar);
+    bulk_copy_g2s(dst, seg + (long long)BS_REC * jb, bytes, bar);
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -98,102 +112,213 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return r;
 }
 
-// One target of a Biot-Savart tile pass (registers of one thread).
+// Minimum image of r on one periodic axis (L = 0 on wall axes: unchanged).
+__device__ __forceinline__ float mi_axis(float r, float L, float iL) { return fmaf(-L, round_mul_fma(r, iL), r); }
+
+// A group whose records all lie at least BS_NEAR cells (Chebyshev) from every
+// target of a warp takes the cheap pair path: the low parts are left out (an
+// error of about one float ulp of the group extent and of the offset, i.e.
+// ~1e-7 (1 + extent / distance) of the pair), no target can lie on a segment,
+// and none of the target's own segments is in the group.
+constexpr float BS_NEAR = 12.f;
+
+// One target of a Biot-Savart pass (registers of one thread): its own
+// record (origin O, parts h + l, so that the point is O + h + l) and the
+// record positions of the segments that belong to its local term.
 struct BsTarget {
-    float hx, hy, hz, lx, ly, lz;  // position, float hi + lo parts
-    float vx, vy, vz;              // accumulated velocity
-    int self, prev;                // its own segment and its predecessor's (local term)
-    int excl;                      // a pinned end: the image of its own segment across its wall (local term)
+    float h[3], l[3], O[3];
+    float v[3];      // sum over the sources, without the factor kappa / 4 pi
+    int self, prev;  // record positions of its own segment and of its predecessor's
+    int excl;        // a pinned end: the image of its own segment across its wall
+    int i;           // point index, -1 for an idle lane
 };
 
-// One (target, segment) pair of Eq. 3.  With R1 = s_j - r and d the segment
-// vector: R1 x R2 = R1 x d, R1.R2 = |R1|^2 + R1.d and |R2|^2 = |R1|^2 +
-// 2 R1.d + |d|^2 (|d|^2 stored in the record).  MASKED: j may be the target's
-// own segment or its predecessor's, which belong to the local term.
-template <bool PERIODIC, bool MASKED>
-__device__ __forceinline__ void bs_pair(const float4& A, const float4& B, const float4& D, int j, BsTarget& t,
-                                        const BoxF& box, float kq) {
-    const float dx = B.z, dy = B.w, dz = D.x, dd = D.y;
-    float r1x = (A.x - t.hx) + (A.w - t.lx);
-    float r1y = (A.y - t.hy) + (B.x - t.ly);
-    float r1z = (A.z - t.hz) + (B.y - t.lz);
-    if (PERIODIC) {
-        r1x = fmaf(-box.Lx, round_mul_fma(r1x, box.iLx), r1x);
-        r1y = fmaf(-box.Ly, round_mul_fma(r1y, box.iLy), r1y);
-        r1z = fmaf(-box.Lz, round_mul_fma(r1z, box.iLz), r1z);
-    }
-    const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
-    const float rd = r1x * dx + r1y * dy + r1z * dz;
-    const float b2 = fmaf(2.f, rd, a2) + dd;
-    const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
-    const float la = a2 * ia, lb = b2 * ib;
-    const float ab = la * lb;
-    const float s = ab + (a2 + rd);
-    const float fac = kq * (la + lb) * rcp_approx(ab * s);
-    // s <= 1e-6 ab: the target lies on the segment (or coincides with an
-    // end point), where the integral is not defined; NaN fails the test too
-    bool use = s > 1e-6f * ab;
-    if (MASKED) use = use & (j != t.self) & (j != t.prev) & (j != t.excl);
-    const float c = use ? fac : 0.f;
-    t.vx += c * (r1y * dz - r1z * dy);
-    t.vy += c * (r1z * dx - r1x * dz);
-    t.vz += c * (r1x * dy - r1y * dx);
-}
+// Bounding box and origin of one group of records in shared memory.
+struct BsGroup {
+    float lo[3], hi[3];  // of the records' h, relative to the origin
+    float O[3];          // integer origin (exact in float)
+};
 
-// Sum over the segments of one shared-memory tile for TGT targets per thread.
-// Four segments per unrolled pass: with few points a block's four warps are
-// alone on their SM, and the pair arithmetic is a chain of dependent
-// instructions (measured: 1.2% faster coupled step at 1.1k points, 0.6% at
-// 17k, than two per pass).
-template <bool PERIODIC, bool MASKED, int TGT>
-__device__ __forceinline__ void bs_tile(const float4* __restrict__ T, int cnt, int jb, BsTarget (&t)[TGT],
-                                        const BoxF& box, float kq) {
-#pragma unroll 4
-    for (int k = 0; k < cnt; ++k) {
-        const float4 A = T[3 * k], B = T[3 * k + 1], D = T[3 * k + 2];
-#pragma unroll
-        for (int u = 0; u < TGT; ++u) bs_pair<PERIODIC, MASKED>(A, B, D, jb + k, t[u], box, kq);
-    }
-}
-
-// Work items are (target tile of BS_TPB points, source split).  Block b
-// starts with item b and takes further items from a device counter (reset by
-// the stage-geometry kernel), so the grid is fixed and no item depends on a
-// host-side estimate of N.  With several splits, each item stores its partial
-// sums and the last item of a target tile adds them in split order (fixed,
-// hence deterministic) into vel; with one split the item writes vel directly.
+// Integer origin of the group of record position j, mirrored onto the image
+// side for an image block: x_a -> w2 - x_a on the face axis a.
 struct BsImages {
     int nfaces;
     int face_code[6];
-    const float4* geo;  // pinned-end wall codes (+1) in geo[2i + 1].w
+    float w2[6];         // twice the coordinate of the face
+    const float4* geo;   // pinned-end wall codes (+1) in geo[2i + 1].w
 };
 
-// Target i of N (none when i >= N): its position from its own segment record,
-// and the segments that belong to its local term.
+__device__ __forceinline__ void group_origin(const BsOrder& o, const BsImages& im, long long Np, int j, float O[3]) {
+    const int f = (int)(j / Np);
+    const int kk = (int)(j - (long long)f * Np);
+    const int4 g = o.org[kk / BS_GROUP];
+    O[0] = (float)g.x;
+    O[1] = (float)g.y;
+    O[2] = (float)g.z;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        if (q + 1 != f) continue;
+        const int ax = im.face_code[q] >> 1;
+        const float w2 = im.w2[q];
+        if (ax == 0) O[0] = w2 - O[0];
+        else if (ax == 1) O[1] = w2 - O[1];
+        else O[2] = w2 - O[2];
+    }
+}
+
+// Target at sorted position k of N (none when k >= N).
 __device__ __forceinline__ BsTarget bs_target(const float4* __restrict__ seg, const int* __restrict__ prev,
-                                              const BsImages& im, int N, int i) {
-    BsTarget t{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, -1, -1};
-    if (i < N) {
-        const float4 a = seg[3LL * i], b = seg[3LL * i + 1];
-        t.hx = a.x; t.hy = a.y; t.hz = a.z; t.lx = a.w; t.ly = b.x; t.lz = b.y;
-        t.self = i;
-        t.prev = prev[i];
+                                              const BsOrder& o, const BsImages& im, long long Np, int N, int k) {
+    BsTarget t;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t.h[a] = t.l[a] = t.O[a] = t.v[a] = 0.f;
+    t.self = t.prev = t.excl = -1;
+    t.i = -1;
+    if (k < N) {
+        const float4 a = seg[(long long)BS_REC * k], c = seg[(long long)BS_REC * k + 3];
+        t.h[0] = a.x; t.h[1] = a.y; t.h[2] = a.z;
+        t.l[0] = c.x; t.l[1] = c.y; t.l[2] = c.z;
+        group_origin(o, im, Np, k, t.O);
+        const int i = o.sorted ? o.ord[k] : k;
+        t.i = i;
+        t.self = k;
+        const int p = prev[i];
+        t.prev = p >= 0 ? (o.sorted ? o.rank[p] : p) : -1;
         if (im.nfaces > 0) {
             const int pin = (int)im.geo[2LL * i + 1].w - 1;
 #pragma unroll
             for (int f = 0; f < 6; ++f)
-                if (f < im.nfaces && im.face_code[f] == pin) t.excl = (1 + f) * N + (t.prev < 0 ? i : t.prev);
+                if (f < im.nfaces && im.face_code[f] == pin) t.excl = (int)((1 + f) * Np) + (p < 0 ? k : t.prev);
         }
     }
     return t;
 }
 
+// The cheap pair path: R1 = h + t (no low parts), no guard, no minimum image;
+// the cross product R1 x d = h x d + t x d is split into the record's c = h x d
+// and t x (sum of fac d), added once per group.  With ia = 1/|R1|, ib = 1/|R2|
+// and P = ia ib, the segment factor (|R1| + |R2|)/(|R1||R2| (|R1||R2| + R1.R2))
+// of Eq. 3 is (ia + ib) P / (1 + P R1.R2), with R1.R2 = |R1|^2 + R1.d.
+__device__ __forceinline__ void pair_far(const float4& A, const float4& B, const float4& C, const float t[3],
+                                         float av[3], float aw[3]) {
+    const float r1x = A.x + t[0], r1y = A.y + t[1], r1z = A.z + t[2];
+    const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
+    const float rd = r1x * B.x + r1y * B.y + r1z * B.z;
+    const float b2 = fmaf(2.f, rd, a2) + A.w;
+    const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
+    const float P = ia * ib;
+    const float den = fmaf(P, a2 + rd, 1.f);
+    const float fac = (ia + ib) * P * rcp_approx(den);
+    av[0] = fmaf(fac, B.w, av[0]);
+    av[1] = fmaf(fac, C.x, av[1]);
+    av[2] = fmaf(fac, C.y, av[2]);
+    aw[0] = fmaf(fac, B.x, aw[0]);
+    aw[1] = fmaf(fac, B.y, aw[1]);
+    aw[2] = fmaf(fac, B.z, aw[2]);
+}
+
+// Minimum image of one component of R1 on a periodic axis (L = 0 on wall
+// axes: unchanged).  r = (h + t_hi) + (l + t_lo) carries FP32 rounding, so
+// within 1e-3 of half the box it cannot tell which image is nearer.  There
+// the image is chosen from the exact sum x = s + c, s = fl(h + t_hi) and c
+// its TwoSum error plus l + t_lo (exact to ~1e-13 cells): y0 = s - kL is
+// exact (Sterbenz), and so is y0 -/+ L/2, so the sign of (y0 -/+ L/2) + c,
+// which decides the image, is the sign an FP64 evaluation of s_j - r gives.
+__device__ __forceinline__ float mi_exact(float r, float h, float th, float l, float tl, float L, float iL) {
+    const float rm = mi_axis(r, L, iL);
+    if (fabsf(rm) > 0.5f * L - 1e-3f && L > 0.f) {
+        const float s = __fadd_rn(h, th), bb = __fsub_rn(s, h);
+        const float c = __fadd_rn(__fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(th, bb)), __fadd_rn(l, tl));
+        const float y0 = __fsub_rn(s, __fmul_rn(L, rintf(__fmul_rn(s, iL))));
+        const float hl = 0.5f * L;
+        float y = __fadd_rn(y0, c);
+        if (__fadd_rn(__fsub_rn(y0, hl), c) > 0.f) y = __fsub_rn(y, L);
+        else if (__fadd_rn(__fadd_rn(y0, hl), c) < 0.f) y = __fadd_rn(y, L);
+        return y;
+    }
+    return rm;
+}
+
+// Pair paths with R1 in full precision: R1 = (h + t_hi) + (l + t_lo), the
+// minimum image on periodic axes.  GUARD (near groups): the on-segment guard
+// and the target's own segments (left to the local term) masked out by
+// record position j.  Without GUARD (groups some target sees across half a
+// periodic box, none near): neither can occur.
+template <bool PERIODIC, bool GUARD>
+__device__ __forceinline__ void pair_precise(const float4& A, const float4& B, const float4& D, int j,
+                                             const float th[3], const float tl[3], const BsTarget& t, float v[3],
+                                             const BoxF& box) {
+    float r1x = (A.x + th[0]) + (D.x + tl[0]);
+    float r1y = (A.y + th[1]) + (D.y + tl[1]);
+    float r1z = (A.z + th[2]) + (D.z + tl[2]);
+    if (PERIODIC) {
+        r1x = mi_exact(r1x, A.x, th[0], D.x, tl[0], box.Lx, box.iLx);
+        r1y = mi_exact(r1y, A.y, th[1], D.y, tl[1], box.Ly, box.iLy);
+        r1z = mi_exact(r1z, A.z, th[2], D.z, tl[2], box.Lz, box.iLz);
+    }
+    const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
+    const float rd = r1x * B.x + r1y * B.y + r1z * B.z;
+    const float b2 = fmaf(2.f, rd, a2) + A.w;
+    const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
+    const float P = ia * ib;
+    const float den = fmaf(P, a2 + rd, 1.f);
+    const float fac = (ia + ib) * P * rcp_approx(den);
+    float c = fac;
+    if (GUARD) {
+        // den <= 1e-6: the target lies on the segment (or coincides with an
+        // end point), where the integral is not defined; NaN and infinity fail too
+        const bool use = (den > 1e-6f) & (den < 3.0e38f) & (j != t.self) & (j != t.prev) & (j != t.excl);
+        c = use ? fac : 0.f;
+    }
+    v[0] = fmaf(c, r1y * B.z - r1z * B.y, v[0]);
+    v[1] = fmaf(c, r1z * B.x - r1x * B.z, v[1]);
+    v[2] = fmaf(c, r1x * B.y - r1y * B.x, v[2]);
+}
+
+// Offset of a group (origin O, record box [lo, hi]) from a target: the
+// integer part D = O - O_t is exact, and on periodic axes D is moved by a
+// whole box so that the group's centre is the nearest image.  Returns
+// t_hi = fl(D - h_t) and flags whether the group may hold a source within
+// BS_NEAR of the target (near) and whether some source may lie more than half
+// a box away on a periodic axis in that image (wrap).
+template <bool PERIODIC>
+__device__ __forceinline__ void group_offset(const BsGroup& G, const BsTarget& t, const BoxF& box, float D[3],
+                                             float th[3], bool& near, bool& wrap) {
+    const float L[3] = {box.Lx, box.Ly, box.Lz}, iL[3] = {box.iLx, box.iLy, box.iLz};
+    float dist = 0.f;
+    wrap = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        D[a] = G.O[a] - t.O[a];
+        if (PERIODIC) D[a] -= L[a] * rintf((D[a] + 0.5f * (G.lo[a] + G.hi[a]) - t.h[a]) * iL[a]);
+        th[a] = D[a] - t.h[a];
+        const float lo = th[a] + G.lo[a], hi = th[a] + G.hi[a];
+        float da = fmaxf(fmaxf(lo, -hi), 0.f);
+        if (PERIODIC) {
+            // the box's neighbouring images may come closer (L = 0 on wall axes: the same box)
+            da = fminf(da, fmaxf(fmaxf(lo - L[a], L[a] - hi), 0.f));
+            da = fminf(da, fmaxf(fmaxf(lo + L[a], -(hi + L[a])), 0.f));
+            wrap |= (hi > 0.5f * L[a] - 0.01f) | (lo < 0.01f - 0.5f * L[a]);
+        }
+        dist = fmaxf(dist, da);
+    }
+    near = dist < BS_NEAR;
+}
+
+// Work items are (target tile of BS_TPB * TGT points, source split).  Block b
+// starts with item b and takes further items from a device counter (reset by
+// the stage-geometry kernel), so the grid is fixed and no item depends on a
+// host-side estimate of N.  With several splits, each item stores its partial
+// sums and the last item of a target tile adds them in split order (fixed,
+// hence deterministic) into vel; with one split the item writes vel directly.
 // Shared memory of one block's Biot-Savart work: two source tiles, their
-// mbarriers and two broadcast slots.  `used` counts the tiles the block has
-// consumed (buffer = used & 1, phase = (used >> 1) & 1) across calls.
+// mbarriers, the groups of the current tile and two broadcast slots.  `used`
+// counts the tiles the block has consumed (buffer = used & 1, phase =
+// (used >> 1) & 1) across calls.
 struct BsSmem {
-    float4 (*tile)[BS_TILE * 3];
+    float4 (*tile)[BS_TILE * BS_REC];
     uint64_t* bar;
+    BsGroup* grp;
     int* s_item;
     int* s_last;
 };
@@ -206,38 +331,140 @@ __device__ __forceinline__ void bs_smem_init(const BsSmem& sm) {
     }
 }
 
+// Warp w < (groups in the tile) finds the box of group w's records and its origin.
+__device__ __forceinline__ void tile_groups(const float4* __restrict__ T, int jb, int cnt, const BsOrder& o,
+                                            const BsImages& im, long long Np, BsGroup* grp) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w * BS_GROUP >= cnt) return;
+    const int gcnt = min(BS_GROUP, cnt - w * BS_GROUP);
+    float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+    for (int r = lane; r < gcnt; r += 32) {
+        const float4 A = T[BS_REC * (w * BS_GROUP + r)];
+        lo[0] = fminf(lo[0], A.x); hi[0] = fmaxf(hi[0], A.x);
+        lo[1] = fminf(lo[1], A.y); hi[1] = fmaxf(hi[1], A.y);
+        lo[2] = fminf(lo[2], A.z); hi[2] = fmaxf(hi[2], A.z);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+    if (lane == 0) {
+        BsGroup& G = grp[w];
+        group_origin(o, im, Np, jb + w * BS_GROUP, G.O);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            G.lo[a] = lo[a];
+            G.hi[a] = hi[a];
+        }
+    }
+}
+
+// The sums of one group of records for TGT targets per thread, on the path
+// the warp's targets need.
+template <bool PERIODIC, int TGT>
+__device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gcnt, int gbase, const BsGroup& G,
+                                         BsTarget (&t)[TGT], const BoxF& box) {
+    float D[TGT][3], th[TGT][3];
+    bool nearL = false, wrapL = false;
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        bool nu, wu;
+        group_offset<PERIODIC>(G, t[u], box, D[u], th[u], nu, wu);
+        const bool own = (unsigned)(t[u].self - gbase) < (unsigned)gcnt ||
+                         (unsigned)(t[u].prev - gbase) < (unsigned)gcnt ||
+                         (unsigned)(t[u].excl - gbase) < (unsigned)gcnt;
+        if (t[u].i >= 0) {
+            nearL |= nu | own;
+            wrapL |= wu;
+        }
+    }
+    const bool nearW = __any_sync(0xffffffffu, nearL);
+    if (nearW || (PERIODIC && __any_sync(0xffffffffu, wrapL))) {
+        // low part of the offset: t = D - h_t - l_t with D - h_t split exactly (TwoSum)
+        float tl[TGT][3];
+#pragma unroll
+        for (int u = 0; u < TGT; ++u)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float s = th[u][a], x = D[u][a], y = -t[u].h[a];
+                const float bb = s - x;
+                tl[u][a] = ((x - (s - bb)) + (y - bb)) - t[u].l[a];
+            }
+        if (nearW) {
+#pragma unroll 2
+            for (int r = 0; r < gcnt; ++r) {
+                const float4 A = T[BS_REC * r], B = T[BS_REC * r + 1], Lo = T[BS_REC * r + 3];
+#pragma unroll
+                for (int u = 0; u < TGT; ++u)
+                    pair_precise<PERIODIC, true>(A, B, Lo, gbase + r, th[u], tl[u], t[u], t[u].v, box);
+            }
+        } else {
+#pragma unroll 2
+            for (int r = 0; r < gcnt; ++r) {
+                const float4 A = T[BS_REC * r], B = T[BS_REC * r + 1], Lo = T[BS_REC * r + 3];
+#pragma unroll
+                for (int u = 0; u < TGT; ++u)
+                    pair_precise<PERIODIC, false>(A, B, Lo, gbase + r, th[u], tl[u], t[u], t[u].v, box);
+            }
+        }
+    } else {
+        float av[TGT][3], aw[TGT][3];
+#pragma unroll
+        for (int u = 0; u < TGT; ++u)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) av[u][a] = aw[u][a] = 0.f;
+#pragma unroll 4
+        for (int r = 0; r < gcnt; ++r) {
+            const float4 A = T[BS_REC * r], B = T[BS_REC * r + 1], C = T[BS_REC * r + 2];
+#pragma unroll
+            for (int u = 0; u < TGT; ++u) pair_far(A, B, C, th[u], av[u], aw[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < TGT; ++u) {
+            t[u].v[0] += av[u][0] + (th[u][1] * aw[u][2] - th[u][2] * aw[u][1]);
+            t[u].v[1] += av[u][1] + (th[u][2] * aw[u][0] - th[u][0] * aw[u][2]);
+            t[u].v[2] += av[u][2] + (th[u][0] * aw[u][1] - th[u][1] * aw[u][0]);
+        }
+    }
+}
+
 // The work items of one Biot-Savart pass taken by this block: the item
 // blockIdx.x, then items from the device counter CNT_BSWORK (reset to 0
 // before the pass).  Returns false after a timed-out tile copy (status
-// TIMEOUT set).
+// TIMEOUT set).  A thread's TGT targets are consecutive record positions, so
+// that a warp's targets are as compact as the order makes them.
 template <bool PERIODIC, int TGT, bool EOM, bool ACC>
 __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ prev, int* __restrict__ counters,
                         int* __restrict__ tile_ticket, int cap, const BoxF& box, float kq, float* __restrict__ part,
-                        float* __restrict__ vel, const EomArgs& ea, const BsImages& im, const BsSmem& sm,
-                        uint32_t& used, long long* __restrict__ vacc) {
-    float4 (*tile)[BS_TILE * 3] = sm.tile;
+                        float* __restrict__ vel, const EomArgs& ea, const BsImages& im, const BsOrder& o, int nsm,
+                        const BsSmem& sm, uint32_t& used, long long* __restrict__ vacc) {
+    float4 (*tile)[BS_TILE * BS_REC] = sm.tile;
     uint64_t* bar = sm.bar;
     int& s_item = *sm.s_item;
     int& s_last = *sm.s_last;
     constexpr int TT = BS_TPB * TGT;  // targets per item
     const int N = counters[CNT_N];
     if (N <= 0) return true;
-    const int ns = bs_splits(N, TT);
+    const int ns = bs_splits(N, TT, nsm);
     const int ntb = (N + TT - 1) / TT;
     const int nitems = ntb * ns;
-    const int nsrc = N * (1 + im.nfaces);  // segments, then their wall images
-    const int chunk = (nsrc + ns - 1) / ns;
+    const long long Np = bs_block(N, im.nfaces);
+    const int nsrc = (int)(Np * (1 + im.nfaces));  // segments, then their wall images
+    // splits start on group boundaries, so that every tile starts on one
+    const int chunk = ((nsrc + ns - 1) / ns + BS_GROUP - 1) / BS_GROUP * BS_GROUP;
     if ((int)blockIdx.x >= nitems) return true;
     int item = blockIdx.x;
     while (true) {
         __syncthreads();
         const int tb = item % ntb, split = item / ntb;
-        const int j0 = split * chunk;
+        const int j0 = min(nsrc, split * chunk);
         const int j1 = min(nsrc, j0 + chunk);
         BsTarget t[TGT];
-        bool own_any = false;
 #pragma unroll
-        for (int u = 0; u < TGT; ++u) t[u] = bs_target(seg, prev, im, N, tb * TT + u * BS_TPB + threadIdx.x);
+        for (int u = 0; u < TGT; ++u) t[u] = bs_target(seg, prev, o, im, Np, N, tb * TT + threadIdx.x * TGT + u);
         const int ntiles = j1 > j0 ? (j1 - j0 + BS_TILE - 1) / BS_TILE : 0;
         if (threadIdx.x == 0 && ntiles > 0) issue_tile(tile[used & 1], seg, j0, min(BS_TILE, j1 - j0), &bar[used & 1]);
         for (int tt = 0; tt < ntiles; ++tt) {
@@ -248,6 +475,9 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
                 issue_tile(tile[b ^ 1], seg, jn, min(BS_TILE, j1 - jn), &bar[b ^ 1]);
             }
             const bool ok = mbar_wait_bounded(&bar[b], (u >> 1) & 1u);
+            const int jb = j0 + tt * BS_TILE;
+            const int cnt = min(BS_TILE, j1 - jb);
+            if (ok) tile_groups(tile[b], jb, cnt, o, im, Np, sm.grp);
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) {
                     atomicOr(&counters[CNT_STATUS], ST_TIMEOUT);
@@ -256,52 +486,51 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
                 }
                 return false;
             }
-            const int jb = j0 + tt * BS_TILE;
-            const int cnt = min(BS_TILE, j1 - jb);
-            own_any = false;
-#pragma unroll
-            for (int v = 0; v < TGT; ++v)
-                own_any |= (unsigned)(t[v].self - jb) < (unsigned)cnt || (unsigned)(t[v].prev - jb) < (unsigned)cnt ||
-                           (unsigned)(t[v].excl - jb) < (unsigned)cnt;
-            if (__any_sync(0xffffffffu, own_any))
-                bs_tile<PERIODIC, true, TGT>(tile[b], cnt, jb, t, box, kq);
-            else
-                bs_tile<PERIODIC, false, TGT>(tile[b], cnt, jb, t, box, kq);
+#pragma unroll 1
+            for (int gi = 0; gi * BS_GROUP < cnt; ++gi)
+                bs_group<PERIODIC, TGT>(tile[b] + BS_REC * BS_GROUP * gi, min(BS_GROUP, cnt - gi * BS_GROUP),
+                                        jb + gi * BS_GROUP, sm.grp[gi], t, box);
             __syncthreads();
         }
         used += (uint32_t)ntiles;
+#pragma unroll
+        for (int v = 0; v < TGT; ++v)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) t[v].v[a] *= kq;
         if (ACC) {
             // ACC: each split adds its sums in fixed point (exact, in any
             // order); the equation-of-motion kernel that follows reads them
 #pragma unroll
             for (int v = 0; v < TGT; ++v) {
-                const int i = t[v].self;
+                const int i = t[v].i;
                 if (i >= 0) {
-                    atomicAdd((unsigned long long*)&vacc[i], (unsigned long long)bs_fixed(t[v].vx));
-                    atomicAdd((unsigned long long*)&vacc[(long long)cap + i], (unsigned long long)bs_fixed(t[v].vy));
-                    atomicAdd((unsigned long long*)&vacc[2LL * cap + i], (unsigned long long)bs_fixed(t[v].vz));
+                    atomicAdd((unsigned long long*)&vacc[i], (unsigned long long)bs_fixed(t[v].v[0]));
+                    atomicAdd((unsigned long long*)&vacc[(long long)cap + i], (unsigned long long)bs_fixed(t[v].v[1]));
+                    atomicAdd((unsigned long long*)&vacc[2LL * cap + i], (unsigned long long)bs_fixed(t[v].v[2]));
                 }
             }
         } else if (ns == 1) {
 #pragma unroll
             for (int v = 0; v < TGT; ++v) {
-                const int i = t[v].self;
+                const int i = t[v].i;
                 if (EOM) {
-                    eom_point(ea, i, i >= 0, t[v].vx, t[v].vy, t[v].vz);
+                    eom_point(ea, i, i >= 0, t[v].v[0], t[v].v[1], t[v].v[2]);
                 } else if (i >= 0) {
-                    vel[i] = t[v].vx;
-                    vel[(long long)cap + i] = t[v].vy;
-                    vel[2LL * cap + i] = t[v].vz;
+                    vel[i] = t[v].v[0];
+                    vel[(long long)cap + i] = t[v].v[1];
+                    vel[2LL * cap + i] = t[v].v[2];
                 }
             }
         } else {
+            // partial sums by record position, summed in split order by the
+            // last split of the target tile
 #pragma unroll
             for (int v = 0; v < TGT; ++v) {
-                const int i = t[v].self;
-                if (i >= 0) {
-                    part[((long long)split * 3 + 0) * cap + i] = t[v].vx;
-                    part[((long long)split * 3 + 1) * cap + i] = t[v].vy;
-                    part[((long long)split * 3 + 2) * cap + i] = t[v].vz;
+                const int k = t[v].self;
+                if (k >= 0) {
+                    part[((long long)split * 3 + 0) * cap + k] = t[v].v[0];
+                    part[((long long)split * 3 + 1) * cap + k] = t[v].v[1];
+                    part[((long long)split * 3 + 2) * cap + k] = t[v].v[2];
                 }
             }
             __threadfence();
@@ -312,12 +541,12 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
                 __threadfence();
 #pragma unroll
                 for (int v = 0; v < TGT; ++v) {
-                    const int i = t[v].self;
+                    const int k = t[v].self, i = t[v].i;
                     float a[3] = {0.f, 0.f, 0.f};
-                    if (i >= 0) {
+                    if (k >= 0) {
                         for (int m = 0; m < ns; ++m)
 #pragma unroll
-                            for (int k = 0; k < 3; ++k) a[k] += __ldcg(&part[((long long)m * 3 + k) * cap + i]);
+                            for (int c = 0; c < 3; ++c) a[c] += __ldcg(&part[((long long)m * 3 + c) * cap + k]);
                     }
                     if (EOM) {
                         eom_point(ea, i, i >= 0, a[0], a[1], a[2]);
@@ -339,34 +568,146 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
     return true;
 }
 
-// At least 8 resident blocks of 128 threads per SM (the grid is sized for 8):
-// the pair loop is issue-bound and needs the warps, and the equation of motion
-// applied after it (EOM) would otherwise raise the count to 72 registers.
+// Resident blocks: the pair loop is issue-bound and needs the warps; the
+// equation of motion applied after it (EOM) needs more registers.
 template <bool PERIODIC, int TGT, bool EOM, bool ACC>
-__global__ void __launch_bounds__(BS_TPB, EOM ? 8 : 9)
+__global__ void __launch_bounds__(BS_TPB, TGT == 1 ? 8 : 6)
     k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev, int* __restrict__ counters,
                   int* __restrict__ tile_ticket, int cap, BoxF box, float kq, float* __restrict__ part,
-                  float* __restrict__ vel, EomArgs ea, BsImages im, long long* __restrict__ vacc) {
+                  float* __restrict__ vel, EomArgs ea, BsImages im, BsOrder o, int nsm,
+                  long long* __restrict__ vacc) {
     pdl_wait_trigger();
-    __shared__ __align__(128) float4 tile[2][BS_TILE * 3];
+    __shared__ __align__(128) float4 tile[2][BS_TILE * BS_REC];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ BsGroup grp[BS_TILE / BS_GROUP];
     __shared__ int s_item, s_last;
-    const BsSmem sm = {tile, bar, &s_item, &s_last};
+    const BsSmem sm = {tile, bar, grp, &s_item, &s_last};
     bs_smem_init(sm);
     uint32_t used = 0;
-    bs_work<PERIODIC, TGT, EOM, ACC>(seg, prev, counters, tile_ticket, cap, box, kq, part, vel, ea, im, sm, used,
-                                     vacc);
+    bs_work<PERIODIC, TGT, EOM, ACC>(seg, prev, counters, tile_ticket, cap, box, kq, part, vel, ea, im, o, nsm, sm,
+                                     used, vacc);
 }
 
-// Stand-alone entry: prev[] and the source records from a caller's point set.
-__global__ void k_bs_prep(Grid g, const double* __restrict__ pos, const int* __restrict__ next, int n,
-                          int* __restrict__ prev, float4* __restrict__ seg, int* __restrict__ counters) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
-        counters[CNT_N] = n;
-        counters[CNT_STATUS] = 0;
-        counters[CNT_BSWORK] = 0;
+// ----------------------------------------------------------- spatial order
+
+__device__ __forceinline__ int bs_key_of(const Grid& g, const BsBins& bb, double x, double y, double z) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const double s[3] = {x, y, z};
+    int b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)floor(s[a]);
+        c = c < 0 ? 0 : (c > n[a] - 1 ? n[a] - 1 : c);
+        b[a] = c >> bb.shift;
     }
+    int key = 0, pos = 0;
+    for (int l = 0; l < 16; ++l)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (l < bb.bits[a]) key |= ((b[a] >> l) & 1) << pos++;
+    return key;
+}
+
+// Key and bin count of every point (grid-stride beyond the grid).
+__global__ void k_sort_keys(Grid g, BsBins bb, const double* __restrict__ pos, int cap,
+                            const int* __restrict__ counters, int* __restrict__ key, int* __restrict__ cnt) {
+    pdl_wait_trigger();
+    const int N = counters[CNT_N];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const int k = bs_key_of(g, bb, pos[i], pos[(long long)cap + i], pos[2LL * cap + i]);
+        key[i] = k;
+        atomicAdd(&cnt[k], 1);
+    }
+}
+
+// Exclusive scan of the bin counts (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_sort_scan(int K, const int* __restrict__ cnt, int* __restrict__ start) {
+    pdl_wait_trigger();
+    __shared__ int warp_sum[32];
+    const int per = (K + 1023) / 1024;
+    const int b0 = threadIdx.x * per;
+    int sum = 0;
+    for (int k = b0; k < min(K, b0 + per); ++k) sum += cnt[k];
+    // inclusive scan of the thread sums across the block
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int z = warp_sum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, off);
+            if (lane >= off) z += y;
+        }
+        warp_sum[lane] = z;
+    }
+    __syncthreads();
+    int run = x - sum + (w > 0 ? warp_sum[w - 1] : 0);
+    for (int k = b0; k < min(K, b0 + per); ++k) {
+        start[k] = run;
+        run += cnt[k];
+    }
+}
+
+// Every point into its bin (arbitrary order inside the bin; start[k] ends as
+// the bin's end).
+__global__ void k_sort_scatter(const int* __restrict__ counters, const int* __restrict__ key, int* __restrict__ start,
+                               int* __restrict__ tmp) {
+    pdl_wait_trigger();
+    const int N = counters[CNT_N];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        tmp[atomicAdd(&start[key[i]], 1)] = i;
+}
+
+// One warp per bin: the bin's points in ascending index (so the order is
+// deterministic), their ranks, the origin of every group that starts in the
+// bin, and the bin count cleared for the next sort.
+__global__ void k_sort_bins(int K, const double* __restrict__ pos, int cap, int* __restrict__ cnt,
+                            const int* __restrict__ start, const int* __restrict__ tmp, int* __restrict__ ord,
+                            int* __restrict__ rank, int4* __restrict__ org) {
+    pdl_wait_trigger();
+    const int lane = threadIdx.x & 31;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= K) return;
+    const int n = cnt[k];
+    if (n == 0) return;
+    const int e = start[k], s0 = e - n;
+    for (int c = 0; c < n; c += 32) {
+        const int my = c + lane < n ? tmp[s0 + c + lane] : 0x7fffffff;
+        int r = 0;
+        for (int m = 0; m < n; m += 32) {
+            const int other = m + lane < n ? tmp[s0 + m + lane] : 0x7fffffff;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) r += __shfl_sync(0xffffffffu, other, q) < my;
+        }
+        if (c + lane < n) {
+            const int p = s0 + r;
+            ord[p] = my;
+            rank[my] = p;
+            if (p % BS_GROUP == 0)
+                org[p / BS_GROUP] = make_int4((int)floor(pos[my]), (int)floor(pos[(long long)cap + my]),
+                                              (int)floor(pos[2LL * cap + my]), 0);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) cnt[k] = 0;
+}
+
+// Stand-alone entry: prev[] and the source records of a caller's point set
+// (one block per group of BS_GROUP records in point order).
+__global__ void __launch_bounds__(BS_GROUP) k_bs_prep(Grid g, const double* __restrict__ pos,
+                                                      const int* __restrict__ next, int n, int* __restrict__ prev,
+                                                      float4* __restrict__ seg, int* __restrict__ counters,
+                                                      BsOrder o) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bs_point_order_origin(o, pos, n, n);
+    __syncthreads();
     if (i >= n) return;
     int q = next[i];
     if (q < -1 || q >= n) {  // not a point index: no segment
@@ -375,22 +716,36 @@ __global__ void k_bs_prep(Grid g, const double* __restrict__ pos, const int* __r
     }
     if (q >= 0) prev[q] = i;
     const int nn[3] = {g.nx, g.ny, g.nz};
-    float hi[3], lo[3], d[3];
-    for (int k = 0; k < 3; ++k) {
-        const double si = pos[(long long)k * n + i];
-        double dd = q >= 0 ? pos[(long long)k * n + q] - si : 0.0;
-        if (!g.wall[k]) {
-            const double L = (double)nn[k];
+    double O[3], rel[3];
+    const long long k = bs_position(o, i, O);
+    float d[3];
+    for (int a = 0; a < 3; ++a) {
+        const double si = pos[(long long)a * n + i];
+        double dd = q >= 0 ? pos[(long long)a * n + q] - si : 0.0;
+        double r = si - O[a];
+        if (!g.wall[a]) {
+            const double L = (double)nn[a];
             if (dd > 0.5 * L) dd -= L;
             else if (dd < -0.5 * L) dd += L;
+            if (r > 0.5 * L) r -= L;
+            else if (r < -0.5 * L) r += L;
         }
-        hi[k] = __double2float_rn(si);
-        lo[k] = __double2float_rn(si - (double)hi[k]);
-        d[k] = __double2float_rn(dd);
+        rel[a] = r;
+        d[a] = __double2float_rn(dd);
     }
-    seg[3LL * i] = make_float4(hi[0], hi[1], hi[2], lo[0]);
-    seg[3LL * i + 1] = make_float4(lo[1], lo[2], d[0], d[1]);
-    seg[3LL * i + 2] = make_float4(d[2], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], 0.f, 0.f);
+    bs_write_record(seg, k, rel, d);
+}
+
+__global__ void k_bs_counters(int* __restrict__ counters, int n) {
+    counters[CNT_N] = n;
+    counters[CNT_STATUS] = 0;
+    counters[CNT_BSWORK] = 0;
+}
+
+__global__ void k_bs_unfix(const long long* __restrict__ vacc, int n, float* __restrict__ vel) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    vel[i] = bs_value(vacc[i]);
 }
 
 BoxF make_box(const Grid& g) {
@@ -406,71 +761,118 @@ BoxF make_box(const Grid& g) {
 
 }  // namespace
 
+int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
 // Up to BS_ACC_MAX points the split sums go to the fixed-point accumulator,
 // so no block waits for a ticket and no last block re-reads partial sums.
 bool bs_uses_vacc(int n_hint) { return n_hint < BS_ACC_MAX; }
 
-int bs_max_splits(int cap) {
+int bs_max_splits(int cap, int nsm) {
     int m = 1;
     for (int n = 1; n <= cap; n += (n < 8192 ? 1 : 128)) {
-        const int k = bs_splits(n, BS_TPB);
+        const int k = bs_splits(n, BS_TPB, nsm);
         if (k > m) m = k;
     }
     return m;
 }
 
+void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
+                    int* ord, int* rank, int4* org, int* cnt, int* start, cudaStream_t s) {
+    const BsBins bb = bs_bins(g.nx, g.ny, g.nz);
+    const int blocks = (span + 255) / 256 > 0 ? (span + 255) / 256 : 1;
+    launch_pdl(k_sort_keys, blocks, 256, 0, s, g, bb, pos, cap, counters, key, cnt);
+    launch_pdl(k_sort_scan, 1, 1024, 0, s, bb.K, (const int*)cnt, start);
+    launch_pdl(k_sort_scatter, blocks, 256, 0, s, counters, (const int*)key, start, tmp);
+    launch_pdl(k_sort_bins, (bb.K * 32 + 255) / 256, 256, 0, s, bb.K, pos, cap, cnt, (const int*)start,
+               (const int*)tmp, ord, rank, org);
+}
+
 template <int TGT, bool EOM, bool ACC = false>
 void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int* cnt, int* tile_ticket, int cap, int n,
-               float* part, float* vel, const EomArgs& ea, const BsImages& im, cudaStream_t s,
+               float* part, float* vel, const EomArgs& ea, const BsImages& im, const BsOrder& o, cudaStream_t s,
                long long* vacc = nullptr) {
     // enough blocks for every item of about n points (at most 8 per SM); more
     // points than that are still covered by the blocks' item loop
     constexpr int TT = BS_TPB * TGT;
-    const int items = ((n + TT - 1) / TT) * bs_splits(n, TT);
-    const int grid = items < 8 * 152 ? items : 8 * 152;
+    const int nsm = sm_count();
+    const int items = ((n + TT - 1) / TT) * bs_splits(n, TT, nsm);
+    const int grid = items < 8 * nsm ? items : 8 * nsm;
     const BoxF box = make_box(g);
     if (g.wall[0] && g.wall[1] && g.wall[2])
         launch_pdl(k_biot_savart<false, TGT, EOM, ACC>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq,
-                   part, vel, ea, im, vacc);
+                   part, vel, ea, im, o, nsm, vacc);
     else
         launch_pdl(k_biot_savart<true, TGT, EOM, ACC>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq,
-                   part, vel, ea, im, vacc);
+                   part, vel, ea, im, o, nsm, vacc);
 }
 
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
                         int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
-                        const EomArgs* eom, int nfaces, const int* face_code, const float4* geo,
+                        const BsOrder& o, const EomArgs* eom, int nfaces, const int* face_code, const float4* geo,
                         long long* vacc) {
     if (cap <= 0) return;
     const int n = n_hint > 0 ? (n_hint < cap ? n_hint : cap) : 1;
     const float kq = (float)(kappa / (4.0 * 3.14159265358979323846));
     int* cnt = const_cast<int*>(counters);
     // two targets per thread from 8192 points on (each shared-memory record is
-    // then read once for both; 1% faster at 17k points, the same at 86k)
+    // then read once for both)
     const EomArgs none = {};
     const EomArgs& ea = eom ? *eom : none;
     BsImages im = {};
     im.nfaces = geo ? nfaces : 0;
-    for (int f = 0; f < im.nfaces; ++f) im.face_code[f] = face_code[f];
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    for (int f = 0; f < im.nfaces; ++f) {
+        im.face_code[f] = face_code[f];
+        const int ax = face_code[f] >> 1;
+        im.w2[f] = (face_code[f] & 1) ? 2.f * (float)nn[ax] - 1.f : -1.f;
+    }
     im.geo = geo;
-    if (vacc && !eom && bs_uses_vacc(n)) {
-        if (n >= 8192) bs_launch<2, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s, vacc);
-        else bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s, vacc);
+    // without a partial-sum buffer the split sums always go to vacc
+    if (vacc && !eom && (bs_uses_vacc(n) || !part)) {
+        if (n >= 8192) bs_launch<2, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
+        else bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
         return;
     }
     if (n >= 8192) {
-        if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
-        else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
+        if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
+        else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
     } else {
-        if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
-        else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, s);
+        if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
+        else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
     }
 }
 
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
-                               int* counters, cudaStream_t s) {
+                               int* counters, const BsOrder& o, int* key, int* tmp, int* cnt, int* start,
+                               cudaStream_t s) {
+    k_bs_counters<<<1, 1, 0, s>>>(counters, n);
     cudaMemsetAsync(prev, 0xff, sizeof(int) * (size_t)n, s);  // first points of open lines keep -1
-    k_bs_prep<<<(n + 255) / 256 > 0 ? (n + 255) / 256 : 1, 256, 0, s>>>(g, pos, next, n, prev, seg, counters);
+    if (o.sorted) {
+        // the caller's positions are SoA [3][n]
+        launch_bs_sort(g, pos, n, n, counters, key, tmp, const_cast<int*>(o.ord), const_cast<int*>(o.rank), o.org,
+                       cnt, start, s);
+    }
+    k_bs_prep<<<(n + BS_GROUP - 1) / BS_GROUP, BS_GROUP, 0, s>>>(g, pos, next, n, prev, seg, counters, o);
+}
+
+void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s) {
+    if (n > 0) k_bs_unfix<<<(3 * n + 255) / 256, 256, 0, s>>>(vacc, n, vel);
 }
 
 }  // namespace vlb
@@ -486,7 +888,11 @@ void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next
 namespace {
 
 constexpr int NOALLOC_MAX_POINTS = 65536;
-constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(6) << 20;  // >= vlb_biot_savart_scratch_bytes(65536)
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;
+// the scratch of the stand-alone entry grows linearly with the point count,
+// so the array holds every call up to the point limit
+static_assert(vlb::bs_scratch_bytes(NOALLOC_MAX_POINTS) <= NOALLOC_SCRATCH_BYTES,
+              "the allocation-free scratch array is smaller than the scratch of its largest call");
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_bs_scratch[NOALLOC_SCRATCH_BYTES];

@@ -73,18 +73,69 @@ __device__ __forceinline__ void delta_axis(const Grid& g, int axis, double s, in
     i1 = a1;
 }
 
+// One Biot-Savart source record (layout in vlb_internal.cuh): rel = the
+// segment's start relative to its group origin (FP64), d = the segment.
+__device__ __forceinline__ void bs_write_record(float4* __restrict__ seg, long long k, const double rel[3],
+                                                const float d[3]) {
+    float h[3], l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        h[a] = __double2float_rn(rel[a]);
+        l[a] = __double2float_rn(rel[a] - (double)h[a]);
+    }
+    const float dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const float cx = h[1] * d[2] - h[2] * d[1], cy = h[2] * d[0] - h[0] * d[2], cz = h[0] * d[1] - h[1] * d[0];
+    float4* r = seg + BS_REC * k;
+    r[0] = make_float4(h[0], h[1], h[2], dd);
+    r[1] = make_float4(d[0], d[1], d[2], cx);
+    r[2] = make_float4(cy, cz, 0.f, 0.f);
+    r[3] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// Group origins in point order: a block of BS_GROUP threads covers group
+// blockIdx.x, whose origin is the cell of its first point (all threads of the
+// block must call this; N = live points).
+__device__ __forceinline__ void bs_point_order_origin(const BsOrder& o, const double* __restrict__ s, int cap,
+                                                      int N) {
+    if (o.sorted || threadIdx.x != 0) return;
+    const int i0 = blockIdx.x * BS_GROUP;
+    if (i0 >= N) return;
+    o.org[blockIdx.x] = make_int4((int)floor(s[i0]), (int)floor(s[(long long)cap + i0]),
+                                  (int)floor(s[2LL * cap + i0]), 0);
+}
+
+// Record position and group origin of point i in the order o.
+__device__ __forceinline__ long long bs_position(const BsOrder& o, int i, double O[3]) {
+    const int k = o.sorted ? o.rank[i] : i;
+    const int4 g = o.org[k / BS_GROUP];
+    O[0] = (double)g.x;
+    O[1] = (double)g.y;
+    O[2] = (double)g.z;
+    return k;
+}
+
+// Zero-length records at the padding positions [N, Np) of every record block
+// (wall images on): thread i covers position i.
+__device__ __forceinline__ void bs_pad_records(int N, int nfaces, int i, float4* __restrict__ seg) {
+    const long long Np = bs_block(N, nfaces);
+    if (nfaces == 0 || i < N || i >= Np) return;
+    const double z[3] = {0.0, 0.0, 0.0};
+    const float d[3] = {0.f, 0.f, 0.f};
+    for (int f = 0; f <= nfaces; ++f) bs_write_record(seg, (long long)f * Np + i, z, d);
+}
+
 // Stage geometry of point i for the equation of motion: the same quantities as
-// k_geometry, with the neighbour differences formed in FP64 (positions are up
-// to ~1e3 cells) and everything after them in FP32, which is accurate to
-// ~1e-7 relative for segments of O(1) cells.  The remeshing decisions use the
-// FP64 k_geometry instead.  An open end pinned on a wall takes the mirror image
+// k_geometry, in FP64 (positions are up to ~1e3 cells), stored as float for
+// the FP32 equation of motion and Biot-Savart sum.  The remeshing decisions
+// use the FP64 k_geometry instead.  An open end pinned on a wall takes the mirror image
 // of its neighbour across that wall as its missing neighbour, represents half
 // of its segment, and carries its wall code (+1) to the equation of motion; a
-// line's last point has a zero-length source record.
+// line's last point has a zero-length source record.  The source records go
+// to the positions of the order o.
 __device__ __forceinline__ void geometry_point(const VfmParams& P, const double* __restrict__ s,
                                                const int* __restrict__ next, const int* __restrict__ prev, int N,
                                                int cap, int i, float4* __restrict__ geo, float4* __restrict__ seg,
-                                               double* __restrict__ s0_copy) {
+                                               double* __restrict__ s0_copy, const BsOrder& o) {
     const int p = prev[i], q = next[i];
     const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
     double si[3], sp[3], sq[3];
@@ -110,57 +161,59 @@ __device__ __forceinline__ void geometry_point(const VfmParams& P, const double*
             else sq[k] = g;
         }
     }
+    // The local self-induced term is near-singular (its coefficient carries
+    // ln(l / a) with a ~ 1e-5 cells, and s'' comes from nearly cancelling
+    // differences on gently curved lines): it is formed in FP64 from the FP64
+    // neighbour differences, and only the result is rounded to float.
+    double da[3], db[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
-        a[k] = (float)min_image(P.g, k, si[k] - sp[k]);
-        b[k] = (float)min_image(P.g, k, sq[k] - si[k]);
+        da[k] = min_image(P.g, k, si[k] - sp[k]);
+        db[k] = min_image(P.g, k, sq[k] - si[k]);
+        a[k] = (float)da[k];
+        b[k] = (float)db[k];
     }
-    const float lm = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-    const float lp = sqrtf(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
-    const float inv = 1.f / (lp * lm * (lp + lm));
-    float t1[3], t2[3];
+    const double lm = sqrt(da[0] * da[0] + da[1] * da[1] + da[2] * da[2]);
+    const double lp = sqrt(db[0] * db[0] + db[1] * db[1] + db[2] * db[2]);
+    const double inv = 1.0 / (lp * lm * (lp + lm));
+    double t1[3], t2[3];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-        t1[k] = (lm * lm * b[k] + lp * lp * a[k]) * inv;
-        t2[k] = 2.f * (lm * b[k] - lp * a[k]) * inv;
+        t1[k] = (lm * lm * db[k] + lp * lp * da[k]) * inv;
+        t2[k] = 2.0 * (lm * db[k] - lp * da[k]) * inv;
     }
-    const float beta = P.kq_f * logf(2.f * sqrtf(lp * lm) * P.inv_ea_f);
+    const double beta = P.kq * log(2.0 * sqrt(lp * lm) * P.inv_ea);
     // geo[2i] = (s'.xyz, dxi), geo[2i+1] = (local velocity beta s' x s'', wall code + 1 of a pinned end)
-    const float dxi = p < 0 ? 0.5f * lp : (q < 0 ? 0.5f * lm : 0.5f * (lp + lm));
-    geo[2LL * i] = make_float4(t1[0], t1[1], t1[2], dxi);
-    geo[2LL * i + 1] = make_float4(beta * (t1[1] * t2[2] - t1[2] * t2[1]), beta * (t1[2] * t2[0] - t1[0] * t2[2]),
-                                   beta * (t1[0] * t2[1] - t1[1] * t2[0]), (float)(code + 1));
+    const double dxi = p < 0 ? 0.5 * lp : (q < 0 ? 0.5 * lm : 0.5 * (lp + lm));
+    geo[2LL * i] = make_float4((float)t1[0], (float)t1[1], (float)t1[2], (float)dxi);
+    geo[2LL * i + 1] = make_float4((float)(beta * (t1[1] * t2[2] - t1[2] * t2[1])),
+                                   (float)(beta * (t1[2] * t2[0] - t1[0] * t2[2])),
+                                   (float)(beta * (t1[0] * t2[1] - t1[1] * t2[0])), (float)(code + 1));
     if (q < 0) b[0] = b[1] = b[2] = 0.f;  // no segment leaves a line's last point
-    float hi[3], lo[3];
-    for (int k = 0; k < 3; ++k) {
-        hi[k] = __double2float_rn(si[k]);
-        lo[k] = __double2float_rn(si[k] - (double)hi[k]);
-    }
-    seg[3LL * i] = make_float4(hi[0], hi[1], hi[2], lo[0]);
-    seg[3LL * i + 1] = make_float4(lo[1], lo[2], b[0], b[1]);
-    seg[3LL * i + 2] = make_float4(b[2], b[0] * b[0] + b[1] * b[1] + b[2] * b[2], 0.f, 0.f);
+    double O[3], rel[3];
+    const long long k = bs_position(o, i, O);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rel[a] = min_image(P.g, a, si[a] - O[a]);
+    bs_write_record(seg, k, rel, b);
     // Image of segment i -> q across each solid face: from M(s_q) to M(s_i),
-    // M mirroring the normal coordinate x_a -> 2w - x_a (record (1 + f) N + i).
+    // M mirroring the normal coordinate x_a -> w2 - x_a (record (1 + f) Np + k,
+    // relative to the mirrored origin w2 - O_a, an integer as w2 is).
+    const long long Np = bs_block(N, P.nfaces);
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
         if (f >= P.nfaces) break;
         const int code = P.face_code[f], ax = code >> 1;
-        const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
-        const double w2 = 2.0 * ((code & 1) ? L - 0.5 : -0.5);
-        float ihi[3], ilo[3], d[3];
+        float d[3];
+        double irel[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+        for (int a = 0; a < 3; ++a) {
             // a line's last point starts no segment: a zero-length record at its own image
-            const double st = q >= 0 ? sq[k] : si[k];
-            const double m = k == ax ? w2 - st : st;
-            ihi[k] = __double2float_rn(m);
-            ilo[k] = __double2float_rn(m - (double)ihi[k]);
-            d[k] = k == ax ? b[k] : -b[k];
+            const double st = q >= 0 ? sq[a] : si[a];
+            irel[a] = a == ax ? O[a] - st : min_image(P.g, a, st - O[a]);
+            d[a] = a == ax ? b[a] : -b[a];
         }
-        const long long r = 3LL * ((long long)(1 + f) * N + i);
-        seg[r] = make_float4(ihi[0], ihi[1], ihi[2], ilo[0]);
-        seg[r + 1] = make_float4(ilo[1], ilo[2], d[0], d[1]);
-        seg[r + 2] = make_float4(d[2], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], 0.f, 0.f);
+        bs_write_record(seg, (long long)(1 + f) * Np + k, irel, d);
     }
 }
 

@@ -16,19 +16,26 @@ namespace vlb {
 namespace {
 
 
-// One thread per point; thread 0 also resets the work counter of the
-// Biot-Savart launch that follows.
-__global__ void __launch_bounds__(64) k_geometry_stage(VfmParams P, const double* __restrict__ s,
-                                                       const int* __restrict__ next, const int* __restrict__ prev,
-                                                       int* __restrict__ counters, int cap,
-                                                       float4* __restrict__ geo, float4* __restrict__ seg,
-                                                       double* __restrict__ s0_copy) {
+// One thread per point (and per padding record position), one block per
+// group of BS_GROUP records in point order; thread 0 also resets the work
+// counter of the Biot-Savart launch that follows.
+__global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const double* __restrict__ s,
+                                                             const int* __restrict__ next,
+                                                             const int* __restrict__ prev,
+                                                             int* __restrict__ counters, int cap,
+                                                             float4* __restrict__ geo, float4* __restrict__ seg,
+                                                             double* __restrict__ s0_copy, BsOrder o) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch that follows takes items from 0
-    if (i >= N) return;
-    geometry_point(P, s, next, prev, N, cap, i, geo, seg, s0_copy);
+    bs_point_order_origin(o, s, cap, N);
+    __syncthreads();
+    if (i >= N) {
+        bs_pad_records(N, P.nfaces, i, seg);
+        return;
+    }
+    geometry_point(P, s, next, prev, N, cap, i, geo, seg, s0_copy, o);
 }
 
 // The equation of motion of each point as a kernel of its own (used when the
@@ -118,9 +125,12 @@ __global__ void k_line_profile(Grid g, const double* __restrict__ pos, const int
 }  // namespace
 
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
-                           int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st) {
+                           int cap, float4* geo, float4* seg, double* s0_copy, const BsOrder& o, cudaStream_t st) {
     if (cap <= 0) return;
-    launch_pdl(k_geometry_stage, (cap + 63) / 64, 64, 0, st, P, s, next, prev, counters, cap, geo, seg, s0_copy);
+    // padding positions reach the capacity rounded up to a whole group
+    const int span = (int)bs_block(cap, 1);
+    launch_pdl(k_geometry_stage, span / BS_GROUP, BS_GROUP, 0, st, P, s, next, prev, counters, cap, geo, seg,
+               s0_copy, o);
 }
 
 void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s, long long* vacc) {

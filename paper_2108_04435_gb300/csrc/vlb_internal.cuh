@@ -103,9 +103,74 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 constexpr int LBM_BLOCK = 256;  // cells per stream-collide block (one z plane)
-constexpr int BS_TPB = 128;     // Biot-Savart targets per block
-constexpr int BS_TILE = 256;    // source segments per shared-memory tile
+constexpr int BS_TPB = 128;     // threads per Biot-Savart block
+constexpr int BS_TILE = 128;    // source records per shared-memory tile
+constexpr int BS_GROUP = 64;    // source records that share one integer origin
+constexpr int BS_REC = 4;       // float4 per source record (64 bytes)
 constexpr int MAX_SPLIT = 64;   // Biot-Savart source splits
+// From this many points on the Biot-Savart sources are put in a spatial order
+// once per step, so that a group of BS_GROUP records spans a small box
+constexpr int BS_SORT_MIN = 8192;
+constexpr int BS_SORT_MAX_BINS = 1 << 16;  // bins of the spatial order (bin edge 8 cells or more)
+
+// Biot-Savart source record of segment s_j -> s_j + d, stored relative to
+// the integer origin O of its group of BS_GROUP records (the cell of the
+// group's first point):
+//   [0] (h.x, h.y, h.z, |d|^2)   h = fl(s_j - O), minimum image on periodic axes
+//   [1] (d.x, d.y, d.z, c.x)     c = h x d (FP32)
+//   [2] (c.y, c.z, 0, 0)
+//   [3] (l.x, l.y, l.z, 0)       l = fl(s_j - O - h): h + l carries s_j - O to ~1e-14 cells
+// A target r (its own record k: origin O_t, parts h_t, l_t) sees the group
+// at offset t = (O - O_t) - h_t - l_t, so R1 = s_j - r = h + l + t.
+
+// Order of the Biot-Savart sources.  sorted = 0: record k is point k;
+// sorted = 1: record k is point ord[k] (rank is the inverse), a spatial order.
+// Either way group g of BS_GROUP records has the integer origin org[g] (the
+// cell of its first point), written by the sort or, in point order, by the
+// stage geometry.
+struct BsOrder {
+    int sorted;
+    const int* ord;
+    const int* rank;
+    int4* org;
+};
+
+// Bins of the spatial order: the cell floor(x) >> shift per axis, clamped to
+// the lattice, interleaved bit by bit (x, y, z) into a Morton key < K.
+struct BsBins {
+    int shift;
+    int bits[3];
+    int K;
+};
+
+__host__ __device__ inline int bs_ceil_log2(int v) {
+    int b = 0;
+    while ((1 << b) < v) ++b;
+    return b;
+}
+
+__host__ __device__ inline BsBins bs_bins(int nx, int ny, int nz) {
+    BsBins b;
+    b.shift = 3;
+    while (true) {
+        const int e = 1 << b.shift;
+        b.bits[0] = bs_ceil_log2((nx + e - 1) / e);
+        b.bits[1] = bs_ceil_log2((ny + e - 1) / e);
+        b.bits[2] = bs_ceil_log2((nz + e - 1) / e);
+        const int tot = b.bits[0] + b.bits[1] + b.bits[2];
+        if (tot <= 16) {
+            b.K = 1 << tot;
+            return b;
+        }
+        ++b.shift;
+    }
+}
+
+// Records of a point set of n points with nfaces wall-image blocks: each
+// block is padded to a multiple of BS_GROUP records when images are on.
+__host__ __device__ inline long long bs_block(int n, int nfaces) {
+    return nfaces > 0 ? (long long)((n + BS_GROUP - 1) / BS_GROUP) * BS_GROUP : (long long)n;
+}
 
 // Geometry of the lattice, passed by value to kernels.
 struct Grid {
@@ -175,8 +240,8 @@ struct VfmParams {
     Grid g;
     double kappa, alpha, alpha_p, ratio, rho0, core_a, dmin, dmax;
     double dt;
-    float kq_f;      // kappa / (4 pi)
-    float inv_ea_f;  // 1 / (e^{1/4} a)
+    double kq;       // kappa / (4 pi)
+    double inv_ea;   // 1 / (e^{1/4} a)
     float alpha_f, alpha_p_f;
     float gscale_f;  // -(rho_s/rho_n) rho0 kappa
     int couple, force_form;
@@ -204,16 +269,16 @@ struct EomArgs {
     int* counters;
 };
 
-// Biot-Savart source splits for N points and target tiles of `tile` points:
-// about 3 (target tile, split) work items per resident block (8 blocks on
-// each of 152 SMs), taken from a device counter, so that the SMs finish
-// together (one item per block left a fifth of the SMs idle at the end:
-// 12% slower at 17k and 86k points), at least 64 segments per split.  The
-// kernel derives it from the device-side N, so it needs no host estimate.
-__host__ __device__ inline int bs_splits(int N, int tile) {
+// Biot-Savart source splits for N points and target tiles of `tile` points
+// on a GPU of nsm SMs: about 3 (target tile, split) work items per resident
+// block (8 blocks on each SM), taken from a device counter, so that the SMs
+// finish together (one item per block left a fifth of the SMs idle at the
+// end: 12% slower at 17k and 86k points), at least 64 segments per split.
+// The kernel derives it from the device-side N, so it needs no host estimate.
+__host__ __device__ inline int bs_splits(int N, int tile, int nsm) {
     const int n = N > 0 ? N : 1;
     const int tb = (n + tile - 1) / tile;
-    int ns = (3 * 8 * 152 + tb - 1) / tb;
+    int ns = (3 * 8 * nsm + tb - 1) / tb;
     const int by_chunk = (n + 63) / 64;
     if (ns > by_chunk) ns = by_chunk;
     if (ns < 1) ns = 1;
@@ -244,7 +309,14 @@ struct Dev {
     double* vel1;
     double* spp;        // FP64 curvature for remeshing
     double* seglen;     // FP64 segment lengths for remeshing
-    float4* seg;        // Biot-Savart source records, 3 float4 per point
+    float4* seg;        // Biot-Savart source records, BS_REC float4 each (segments, then wall images)
+    int* bs_key;        // spatial order: Morton key of each point
+    int* bs_tmp;        // spatial order: points scattered by key, before the in-bin sort
+    int* bs_ord;        // sorted position -> point
+    int* bs_rank;       // point -> sorted position
+    int4* bs_org;       // integer origin of each group of BS_GROUP records
+    int* bs_cnt;        // points per bin (zero between sorts)
+    int* bs_start;      // bin starts
     float* bsp;         // Biot-Savart partial sums [splits][3][cap]
     float* vbs;         // Biot-Savart velocity [3][cap]
     long long* vacc;    // Biot-Savart velocity [3][cap], fixed point (bs_fixed), zero between uses
@@ -289,8 +361,9 @@ void launch_export(const LbmParams& P, const void* f, float* out, int i0, int i1
 void launch_import(const LbmParams& P, const float* in, void* f, int i0, int i1, cudaStream_t s);
 
 // vfm.cu
+// The stage geometry writes the Biot-Savart source records in the order `o`.
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
-                           int cap, float4* geo, float4* seg, double* s0_copy, cudaStream_t st);
+                           int cap, float4* geo, float4* seg, double* s0_copy, const BsOrder& o, cudaStream_t st);
 // vacc != nullptr: the Biot-Savart velocity is read from the fixed-point sums,
 // which the kernel clears again for the next pass.
 void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s, long long* vacc = nullptr);
@@ -300,7 +373,14 @@ void launch_line_length(const Grid& g, const double* pos, const int* next, int* 
                         double* dstats, cudaStream_t s);
 
 // bs.cu
-int bs_max_splits(int cap);
+// SMs of the current device (queried once per device).
+int sm_count();
+int bs_max_splits(int cap, int nsm);
+// Spatial order of the points pos[3][cap] (count from the device counters):
+// bs_ord, bs_rank and the group origins bs_org.  span: points one pass of the
+// per-point grids covers (they stride over any beyond).
+void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
+                    int* ord, int* rank, int4* org, int* cnt, int* start, cudaStream_t s);
 // With eom != nullptr the kernel applies the equation of motion to each target
 // tile as soon as its sum is complete, and does not write vel.
 // Sources are the N segments, then with nfaces > 0 their images across each
@@ -309,8 +389,8 @@ int bs_max_splits(int cap);
 // left out.
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
                         int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
-                        const EomArgs* eom = nullptr, int nfaces = 0, const int* face_code = nullptr,
-                        const float4* geo = nullptr, long long* vacc = nullptr);
+                        const BsOrder& o, const EomArgs* eom = nullptr, int nfaces = 0,
+                        const int* face_code = nullptr, const float4* geo = nullptr, long long* vacc = nullptr);
 // Below BS_ACC_MAX points the Biot-Savart split sums go to the fixed-point
 // accumulator and a separate kernel applies the equation of motion; from it on,
 // the splits write partial sums, the last split of a target tile adds them,
@@ -322,8 +402,25 @@ constexpr int BS_ACC_MAX = 24576;
 // Whether launch_biot_savart, given vacc and no equation of motion, adds the
 // split sums of about n_hint points into vacc (else it writes vel).
 bool bs_uses_vacc(int n_hint);
+// Stand-alone entry: prev[], the spatial order (from BS_SORT_MIN points on)
+// and the source records of a caller's point set, into the scratch buffers.
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
-                               int* counters, cudaStream_t s);
+                               int* counters, const BsOrder& o, int* key, int* tmp, int* cnt, int* start,
+                               cudaStream_t s);
+// vel[3][n] = the fixed-point sums vacc[3][n] (stand-alone entry)
+void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s);
+
+// Scratch of the stand-alone entry points for n points, each part 256-byte
+// aligned: counters | prev | source records | sort keys | scattered points |
+// ord | rank | group origins | bin counts | bin starts | fixed-point sums.
+// Linear in n, so its maximum over n <= m is its value at m.
+__host__ __device__ constexpr size_t bs_up256(size_t b) { return (b + 255) & ~size_t(255); }
+__host__ __device__ constexpr size_t bs_scratch_bytes(long long n) {
+    return bs_up256(sizeof(int) * 16) + bs_up256(sizeof(int) * (size_t)n) +
+           bs_up256(sizeof(float4) * BS_REC * (size_t)((n + BS_GROUP - 1) / BS_GROUP) * BS_GROUP) +
+           4 * bs_up256(sizeof(int) * (size_t)n) + bs_up256(sizeof(int4) * (size_t)((n + BS_GROUP - 1) / BS_GROUP)) +
+           2 * bs_up256(sizeof(int) * (size_t)BS_SORT_MAX_BINS) + bs_up256(sizeof(long long) * 3 * (size_t)n);
+}
 
 // abi.cu
 int set_error(int code, const char* msg);

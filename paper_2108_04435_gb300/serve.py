@@ -33,6 +33,7 @@ class Result:
     line_length: float = 0.0
     n_points: int = 0
     error: str = ""
+    state: dict = field(default_factory=dict)  # fields read at completion (serve_gpu's snapshot)
 
     @property
     def latency(self) -> float:
@@ -121,6 +122,8 @@ class Scheduler:
                 if not a.res.error:
                     a.res.n_points = a.run.n_points()
                     a.res.line_length = a.run.line_length()
+                    if hasattr(a.run, "final_state"):
+                        a.res.state = a.run.final_state()
                 a.res.points_mean = a.pts_sum / max(1, a.slices)
                 a.run.close()
                 used -= a.bytes
@@ -155,7 +158,7 @@ class GpuRun:
     the runs overlap one another already, and a second stream per channel
     would compete for the device's hardware queues."""
 
-    def __init__(self, req, device: int = 0, overlap: bool = True):
+    def __init__(self, req, device: int = 0, overlap: bool = True, snapshot=()):
         import torch
 
         from . import vlb
@@ -163,6 +166,11 @@ class GpuRun:
         self.ch.set_overlap(overlap)
         self.ch.seed(req["xyz"], req["next"])
         self._n = len(req["next"])
+        self.snapshot = tuple(snapshot)
+
+    def final_state(self):
+        """The fields named in `snapshot` (vlb.FIELD_*), read at completion."""
+        return {w: self.ch.read(w) for w in self.snapshot}
 
     def step_async(self, n):
         self.ch.step_async(n)
@@ -180,17 +188,19 @@ class GpuRun:
         self.ch.close()
 
 
-def serve_gpu(requests, budget_bytes: int, max_slots: int = 16, slice_steps: int = 50, realtime: bool = True):
+def serve_gpu(requests, budget_bytes: int, max_slots: int = 16, slice_steps: int = 50, realtime: bool = True,
+              snapshot=()):
     """Serve requests on the current GPU; returns (results, summary).  Many
     channels on their own streams share the device's hardware work queues
     (8 unless CUDA_DEVICE_MAX_CONNECTIONS, read when the process creates its
     CUDA context, says otherwise); MAX_CONNECTIONS is the value to set before
-    that for 16 slots."""
+    that for 16 slots.  `snapshot` names fields (vlb.FIELD_*) to read from
+    each run when it completes, into its Result.state."""
     from . import vlb
     for r in requests:
         n = r["params"]["n"]
         r.setdefault("cells", n[0] * n[1] * n[2])
-    make = GpuRun if max_slots == 1 else (lambda req: GpuRun(req, overlap=False))
+    make = lambda req: GpuRun(req, overlap=max_slots == 1, snapshot=snapshot)  # noqa: E731
     sched = Scheduler(make_run=make, bytes_of=lambda r: vlb.channel_bytes(r["params"]), budget_bytes=budget_bytes,
                       max_slots=max_slots, slice_steps=slice_steps)
     t0 = time.perf_counter()

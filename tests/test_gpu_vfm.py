@@ -7,8 +7,11 @@ fixed point and the equation of motion as a kernel of its own (one and, from
 the equation of motion itself (the default from 24576 points; forced here by
 VLB_FUSED_EOM=1 on 8.7k points).  The
 stand-alone Biot-Savart entry point is checked against the oracle's nonlocal
-sum on rings, a periodic tangle (minimum image) and at a size spanning many
-shared-memory tiles and source splits."""
+sum on rings, a periodic tangle (minimum image), at a size spanning many
+shared-memory tiles and source splits, and from 8192 points on in the
+spatial order (a periodic box, where groups are met across half the box, and
+a 512-cell walled channel); pairs that sit 2.5e-7 beyond half a periodic box
+must take the image the FP64 oracle takes."""
 import numpy as np
 import pytest
 
@@ -99,7 +102,8 @@ def _bs_gpu(p, xyz, nxt):
     return vel.cpu().numpy().T.astype(np.float64)
 
 
-@pytest.mark.parametrize("case", ["ring", "periodic-tangle", "walls-tangle", "large"])
+@pytest.mark.parametrize("case", ["ring", "periodic-tangle", "walls-tangle", "large", "sorted-periodic",
+                                  "sorted-walls", "half-box", "half-box-sorted"])
 def test_biot_savart_entry_point(case):
     import oracle
     from paper_2108_04435_gb300 import inputs
@@ -112,9 +116,27 @@ def test_biot_savart_entry_point(case):
     elif case == "walls-tangle":
         n, wall = (48, 40, 64), (1, 1, 1)
         xyz, nxt = inputs.random_rings(n, wall, 20, 3.0, 9.0, 5)
-    else:
+    elif case == "large":
         n, wall = (128, 128, 128), (0, 0, 0)
         xyz, nxt = inputs.random_rings(n, wall, 60, 6.0, 20.0, 6)
+    elif case == "sorted-periodic":  # spatial order, groups seen across half the box
+        n, wall = (128, 128, 128), (0, 0, 0)
+        xyz, nxt = inputs.random_rings(n, wall, 200, 6.0, 20.0, 7)
+    elif case == "sorted-walls":  # spatial order in a long walled channel: far groups, hi/lo coordinates up to 512
+        n, wall = (128, 128, 512), (1, 1, 1)
+        xyz, nxt = inputs.random_rings(n, wall, 400, 6.0, 20.0, 8)
+    else:
+        # a ring and its copy shifted by half the box plus 2.5e-7 along x: every
+        # point meets its twin's segment at |R1_x| = L/2 + 2.5e-7, where FP32
+        # cannot tell the two images apart and the FP64 decision must be kept
+        n, wall = (128, 128, 128), (0, 0, 0)
+        a, na = inputs.ring((20.0, 30.0, 40.0), (0.3, 0.5, 0.8), 10.0)
+        b, nb = a + [64.00000025, 0.0, 0.0], na
+        parts = [(a, na), (b, nb)]
+        if case == "half-box-sorted":  # with enough further rings for the spatial order
+            parts.append(inputs.random_rings(n, wall, 90, 6.0, 20.0, 9))
+        xyz, nxt = inputs.concat(parts)
+    assert "sorted" not in case or len(nxt) >= 8192
     p = vparams(n, wall, max_points=max(8192, 2 * len(nxt)))
     r = oracle.Channel(p)
     r.seed(xyz, nxt)

@@ -5,8 +5,10 @@ while they run: it keeps its scratch in a fixed device array inside the
 library instead of a caller-provided buffer.  Called through the C ABI twice
 in a row (the second call reuses the array the first one left behind), it
 must give the same velocities as vlb_biot_savart within the tolerance of the
-other Biot-Savart tests.  This file is collected last so that a run stopping
-at the first failure has already run every other test."""
+other Biot-Savart tests, from a few hundred points up to its 65536-point
+limit (the sizes cover the point-order and the spatially ordered sums).  This
+file is collected last so that a run stopping at the first failure has
+already run every other test."""
 import numpy as np
 import pytest
 
@@ -18,18 +20,32 @@ def _inputs(case):
     if case == "periodic":
         n, wall = (48, 48, 48), (0, 0, 0)
         xyz, nxt = inputs.random_rings(n, wall, 25, 3.0, 10.0, 11)
-    else:
+    elif case == "walls":
         n, wall = (40, 36, 64), (1, 1, 1)
         xyz, nxt = inputs.random_rings(n, wall, 15, 3.0, 9.0, 12)
+    elif case == "sorted-16k":
+        n, wall = (128, 128, 128), (0, 0, 0)
+        xyz, nxt = inputs.random_rings(n, wall, 170, 6.0, 20.0, 13)
+    else:  # "limit": exactly 65536 points in a walled channel
+        n, wall = (128, 128, 768), (1, 1, 1)
+        xyz, nxt = inputs.random_rings(n, wall, 760, 6.0, 20.0, 14)
+        assert len(nxt) >= 65536
+        xyz, nxt = xyz[:65536].copy(), np.asarray(nxt[:65536]).copy()
+        first = 65535  # the ring cut at the last point closes back onto its own first point
+        while first > 0 and nxt[first - 1] == first:
+            first -= 1
+        nxt[65535] = first
     return configs.base_params(n, wall, 1.9, max_points=8192), xyz, nxt
 
 
-@pytest.mark.parametrize("case", ["periodic", "walls"])
+@pytest.mark.parametrize("case", ["periodic", "walls", "sorted-16k", "limit"])
 def test_noalloc_matches_allocating_entry_point(case):
     import torch
     from paper_2108_04435_gb300 import vlb
     p, xyz, nxt = _inputs(case)
     n = len(nxt)
+    if case == "limit":
+        assert n == 65536
     pos = torch.tensor(np.ascontiguousarray(np.asarray(xyz).T), dtype=torch.float64, device="cuda")
     nx = torch.tensor(np.asarray(nxt, np.int32), device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
