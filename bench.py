@@ -58,11 +58,13 @@ def launches_per_step(n_points: int) -> int:
     """Kernels of one coupled step (1 RK4 sub-step): lattice 3 (velocity-tile
     flags, stream-collide, plane reduction with the force-grid reset),
     filaments 4 x 3 (per RK stage geometry, Biot-Savart, equation of motion),
-    remesh 2, reconnection 4 = 21.  From 24576 points on the Biot-Savart kernel
-    applies the equation of motion itself (17; or as VLB_FUSED_EOM forces)."""
+    remesh 2, reconnection 4 = 21.  From 8192 points on, 4 more build the
+    spatial order of the Biot-Savart sources once per step; from 24576 points
+    on the Biot-Savart kernel applies the equation of motion itself (4 fewer;
+    or as VLB_FUSED_EOM forces)."""
     mode = os.environ.get("VLB_FUSED_EOM")
     fused = n_points >= 24576 if mode is None else mode != "0"
-    return 17 if fused else 21
+    return (17 if fused else 21) + (4 if n_points >= 8192 else 0)
 
 
 def launches(n_points: int, steps: int, overlap: bool = True) -> int:

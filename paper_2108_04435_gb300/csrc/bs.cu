@@ -33,6 +33,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <stdlib.h>
 
 #include "eom.cuh"
 #include "vlb_internal.cuh"
@@ -175,9 +176,12 @@ __device__ __forceinline__ BsTarget bs_target(const float4* __restrict__ seg, co
     t.self = t.prev = t.excl = -1;
     t.i = -1;
     if (k < N) {
-        const float4 a = seg[(long long)BS_REC * k], c = seg[(long long)BS_REC * k + 3];
-        t.h[0] = a.x; t.h[1] = a.y; t.h[2] = a.z;
-        t.l[0] = c.x; t.l[1] = c.y; t.l[2] = c.z;
+        const float* r = reinterpret_cast<const float*>(seg);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t.h[a] = r[bs_value_index(k, a)];
+            t.l[a] = r[bs_value_index(k, 10 + a)];
+        }
         group_origin(o, im, Np, k, t.O);
         const int i = o.sorted ? o.ord[k] : k;
         t.i = i;
@@ -194,27 +198,39 @@ __device__ __forceinline__ BsTarget bs_target(const float4* __restrict__ seg, co
     return t;
 }
 
-// The cheap pair path: R1 = h + t (no low parts), no guard, no minimum image;
-// the cross product R1 x d = h x d + t x d is split into the record's c = h x d
-// and t x (sum of fac d), added once per group.  With ia = 1/|R1|, ib = 1/|R2|
-// and P = ia ib, the segment factor (|R1| + |R2|)/(|R1||R2| (|R1||R2| + R1.R2))
-// of Eq. 3 is (ia + ib) P / (1 + P R1.R2), with R1.R2 = |R1|^2 + R1.d.
-__device__ __forceinline__ void pair_far(const float4& A, const float4& B, const float4& C, const float t[3],
-                                         float av[3], float aw[3]) {
-    const float r1x = A.x + t[0], r1y = A.y + t[1], r1z = A.z + t[2];
-    const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
-    const float rd = r1x * B.x + r1y * B.y + r1z * B.z;
-    const float b2 = fmaf(2.f, rd, a2) + A.w;
-    const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
-    const float P = ia * ib;
-    const float den = fmaf(P, a2 + rd, 1.f);
-    const float fac = (ia + ib) * P * rcp_approx(den);
-    av[0] = fmaf(fac, B.w, av[0]);
-    av[1] = fmaf(fac, C.x, av[1]);
-    av[2] = fmaf(fac, C.y, av[2]);
-    aw[0] = fmaf(fac, B.x, aw[0]);
-    aw[1] = fmaf(fac, B.y, aw[1]);
-    aw[2] = fmaf(fac, B.z, aw[2]);
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// The cheap pair path for the two records of a pair at once (packed FP32x2:
+// one instruction does the arithmetic of both): R1 = h + t (no low parts),
+// no guard, no minimum image; the cross product R1 x d = h x d + t x d is
+// split into the record's c = h x d and t x (sum of fac d), added once per
+// group.  With ia = 1/|R1|, ib = 1/|R2| and P = ia ib, the segment factor
+// (|R1| + |R2|)/(|R1||R2| (|R1||R2| + R1.R2)) of Eq. 3 is
+// (ia + ib) P / (1 + P R1.R2), with R1.R2 = |R1|^2 + R1.d.  q0..q4 are the
+// first five float4 of the pair (values 0-9 of both records).
+__device__ __forceinline__ void pair2_far(const float4& q0, const float4& q1, const float4& q2, const float4& q3,
+                                          const float4& q4, const float2 (&t)[3], float2 (&av)[3],
+                                          float2 (&aw)[3]) {
+    const float2 hx = make_float2(q0.x, q0.y), hy = make_float2(q0.z, q0.w), hz = make_float2(q1.x, q1.y);
+    const float2 dd = make_float2(q1.z, q1.w), dx = make_float2(q2.x, q2.y), dy = make_float2(q2.z, q2.w);
+    const float2 dz = make_float2(q3.x, q3.y), cx = make_float2(q3.z, q3.w), cy = make_float2(q4.x, q4.y);
+    const float2 cz = make_float2(q4.z, q4.w);
+    const float2 rx = __fadd2_rn(hx, t[0]), ry = __fadd2_rn(hy, t[1]), rz = __fadd2_rn(hz, t[2]);
+    const float2 a2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+    const float2 rd = __ffma2_rn(rz, dz, __ffma2_rn(ry, dy, __fmul2_rn(rx, dx)));
+    const float2 b2 = __fadd2_rn(__ffma2_rn(f2(2.f), rd, a2), dd);
+    const float2 ia = make_float2(rsqrt_approx(a2.x), rsqrt_approx(a2.y));
+    const float2 ib = make_float2(rsqrt_approx(b2.x), rsqrt_approx(b2.y));
+    const float2 P = __fmul2_rn(ia, ib);
+    const float2 den = __ffma2_rn(P, __fadd2_rn(a2, rd), f2(1.f));
+    const float2 rc = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+    const float2 fac = __fmul2_rn(__fmul2_rn(__fadd2_rn(ia, ib), P), rc);
+    av[0] = __ffma2_rn(fac, cx, av[0]);
+    av[1] = __ffma2_rn(fac, cy, av[1]);
+    av[2] = __ffma2_rn(fac, cz, av[2]);
+    aw[0] = __ffma2_rn(fac, dx, aw[0]);
+    aw[1] = __ffma2_rn(fac, dy, aw[1]);
+    aw[2] = __ffma2_rn(fac, dz, aw[2]);
 }
 
 // Minimum image of one component of R1 on a periodic axis (L = 0 on wall
@@ -245,20 +261,20 @@ __device__ __forceinline__ float mi_exact(float r, float h, float th, float l, f
 // record position j.  Without GUARD (groups some target sees across half a
 // periodic box, none near): neither can occur.
 template <bool PERIODIC, bool GUARD>
-__device__ __forceinline__ void pair_precise(const float4& A, const float4& B, const float4& D, int j,
-                                             const float th[3], const float tl[3], const BsTarget& t, float v[3],
-                                             const BoxF& box) {
-    float r1x = (A.x + th[0]) + (D.x + tl[0]);
-    float r1y = (A.y + th[1]) + (D.y + tl[1]);
-    float r1z = (A.z + th[2]) + (D.z + tl[2]);
+__device__ __forceinline__ void pair_precise(float hx, float hy, float hz, float dd, float dx, float dy, float dz,
+                                             float lx, float ly, float lz, int j, const float th[3],
+                                             const float tl[3], const BsTarget& t, float v[3], const BoxF& box) {
+    float r1x = (hx + th[0]) + (lx + tl[0]);
+    float r1y = (hy + th[1]) + (ly + tl[1]);
+    float r1z = (hz + th[2]) + (lz + tl[2]);
     if (PERIODIC) {
-        r1x = mi_exact(r1x, A.x, th[0], D.x, tl[0], box.Lx, box.iLx);
-        r1y = mi_exact(r1y, A.y, th[1], D.y, tl[1], box.Ly, box.iLy);
-        r1z = mi_exact(r1z, A.z, th[2], D.z, tl[2], box.Lz, box.iLz);
+        r1x = mi_exact(r1x, hx, th[0], lx, tl[0], box.Lx, box.iLx);
+        r1y = mi_exact(r1y, hy, th[1], ly, tl[1], box.Ly, box.iLy);
+        r1z = mi_exact(r1z, hz, th[2], lz, tl[2], box.Lz, box.iLz);
     }
     const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
-    const float rd = r1x * B.x + r1y * B.y + r1z * B.z;
-    const float b2 = fmaf(2.f, rd, a2) + A.w;
+    const float rd = r1x * dx + r1y * dy + r1z * dz;
+    const float b2 = fmaf(2.f, rd, a2) + dd;
     const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
     const float P = ia * ib;
     const float den = fmaf(P, a2 + rd, 1.f);
@@ -270,9 +286,23 @@ __device__ __forceinline__ void pair_precise(const float4& A, const float4& B, c
         const bool use = (den > 1e-6f) & (den < 3.0e38f) & (j != t.self) & (j != t.prev) & (j != t.excl);
         c = use ? fac : 0.f;
     }
-    v[0] = fmaf(c, r1y * B.z - r1z * B.y, v[0]);
-    v[1] = fmaf(c, r1z * B.x - r1x * B.z, v[1]);
-    v[2] = fmaf(c, r1x * B.y - r1y * B.x, v[2]);
+    v[0] = fmaf(c, r1y * dz - r1z * dy, v[0]);
+    v[1] = fmaf(c, r1z * dx - r1x * dz, v[1]);
+    v[2] = fmaf(c, r1x * dy - r1y * dx, v[2]);
+}
+
+// Both records of a pair on the precise path (q0..q6: values 0-13 of both).
+template <bool PERIODIC, bool GUARD, int TGT>
+__device__ __forceinline__ void pair2_precise(const float4* __restrict__ Q, int j, const float (&th)[TGT][3],
+                                              const float (&tl)[TGT][3], BsTarget (&t)[TGT], const BoxF& box) {
+    const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q5 = Q[5], q6 = Q[6];
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        pair_precise<PERIODIC, GUARD>(q0.x, q0.z, q1.x, q1.z, q2.x, q2.z, q3.x, q5.x, q5.z, q6.x, j, th[u], tl[u], t[u],
+                                      t[u].v, box);
+        pair_precise<PERIODIC, GUARD>(q0.y, q0.w, q1.y, q1.w, q2.y, q2.w, q3.y, q5.y, q5.w, q6.y, j + 1, th[u], tl[u],
+                                      t[u], t[u].v, box);
+    }
 }
 
 // Offset of a group (origin O, record box [lo, hi]) from a target: the
@@ -305,44 +335,62 @@ __device__ __forceinline__ void group_offset(const BsGroup& G, const BsTarget& t
     near = dist < BS_NEAR;
 }
 
-// Work items are (target tile of BS_TPB * TGT points, source split).  Block b
-// starts with item b and takes further items from a device counter (reset by
-// the stage-geometry kernel), so the grid is fixed and no item depends on a
-// host-side estimate of N.  With several splits, each item stores its partial
-// sums and the last item of a target tile adds them in split order (fixed,
-// hence deterministic) into vel; with one split the item writes vel directly.
-// Shared memory of one block's Biot-Savart work: two source tiles, their
-// mbarriers, the groups of the current tile and two broadcast slots.  `used`
-// counts the tiles the block has consumed (buffer = used & 1, phase =
-// (used >> 1) & 1) across calls.
+// Shared-memory stages of the source pipeline.  Every tile of BS_TILE
+// records lands by one bulk copy that completes full[b]; the warps consume
+// it independently (a warp's groups may take another pair path than its
+// neighbours' and so take longer), and the warp that releases the buffer
+// last (a counter per stage) issues the copy of the tile BS_STAGES further
+// on.  No block-wide barrier is needed per tile, so warps can drift up to
+// that many tiles apart.  One target per thread: three stages, so that eight
+// blocks fit on an SM; two targets: four.
+template <int TGT>
+__host__ __device__ constexpr int bs_stages() { return TGT == 1 ? 3 : 4; }
+
 struct BsSmem {
+    int nst;          // stages in use
     float4 (*tile)[BS_TILE * BS_REC];
-    uint64_t* bar;
-    BsGroup* grp;
+    uint64_t* full;   // [nst] completed by the copy's byte count
+    int* release;     // [nst] warps done with the stage's current tile
+    int* fills;       // [nst] copies issued into the stage so far
     int* s_item;
     int* s_last;
+    int* s_abort;     // a wait timed out: every warp leaves the pass
 };
 
 __device__ __forceinline__ void bs_smem_init(const BsSmem& sm) {
+    if (threadIdx.x < sm.nst) {
+        sm.release[threadIdx.x] = 0;
+        sm.fills[threadIdx.x] = 0;
+    }
     if (threadIdx.x == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
+        for (int b = 0; b < sm.nst; ++b) mbar_init(&sm.full[b], 1);
+        *sm.s_abort = 0;
         fence_mbar_init();
     }
+    __syncthreads();
 }
 
-// Warp w < (groups in the tile) finds the box of group w's records and its origin.
-__device__ __forceinline__ void tile_groups(const float4* __restrict__ T, int jb, int cnt, const BsOrder& o,
-                                            const BsImages& im, long long Np, BsGroup* grp) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w * BS_GROUP >= cnt) return;
-    const int gcnt = min(BS_GROUP, cnt - w * BS_GROUP);
+// Copy tile number `tile` of the range [j0, j1) into the stage of the
+// block's tile sequence number q.
+__device__ __forceinline__ void bs_fill(const BsSmem& sm, const float4* seg, uint32_t q, int j0, int j1, int tile) {
+    const int b = (int)(q % (uint32_t)sm.nst);
+    const int jb = j0 + tile * BS_TILE;
+    sm.fills[b] += 1;
+    issue_tile(sm.tile[b], seg, jb, min(BS_TILE, j1 - jb), &sm.full[b]);
+}
+
+// Box and origin of one group of records (computed by every warp for
+// itself): lane l takes pair l (gcnt is even and at most 64).
+__device__ __forceinline__ BsGroup group_box(const float4* __restrict__ T, int gcnt, int j, const BsOrder& o,
+                                             const BsImages& im, long long Np) {
+    const int lane = threadIdx.x & 31;
+    BsGroup G;
     float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-    for (int r = lane; r < gcnt; r += 32) {
-        const float4 A = T[BS_REC * (w * BS_GROUP + r)];
-        lo[0] = fminf(lo[0], A.x); hi[0] = fmaxf(hi[0], A.x);
-        lo[1] = fminf(lo[1], A.y); hi[1] = fmaxf(hi[1], A.y);
-        lo[2] = fminf(lo[2], A.z); hi[2] = fmaxf(hi[2], A.z);
+    if (2 * lane < gcnt) {
+        const float4 q0 = T[8 * lane], q1 = T[8 * lane + 1];
+        lo[0] = fminf(q0.x, q0.y); hi[0] = fmaxf(q0.x, q0.y);
+        lo[1] = fminf(q0.z, q0.w); hi[1] = fmaxf(q0.z, q0.w);
+        lo[2] = fminf(q1.x, q1.y); hi[2] = fmaxf(q1.x, q1.y);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
@@ -351,15 +399,13 @@ __device__ __forceinline__ void tile_groups(const float4* __restrict__ T, int jb
             lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
             hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
         }
-    if (lane == 0) {
-        BsGroup& G = grp[w];
-        group_origin(o, im, Np, jb + w * BS_GROUP, G.O);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            G.lo[a] = lo[a];
-            G.hi[a] = hi[a];
-        }
+    for (int a = 0; a < 3; ++a) {
+        G.lo[a] = lo[a];
+        G.hi[a] = hi[a];
     }
+    group_origin(o, im, Np, j, G.O);
+    return G;
 }
 
 // The sums of one group of records for TGT targets per thread, on the path
@@ -393,59 +439,64 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gcnt,
                 const float bb = s - x;
                 tl[u][a] = ((x - (s - bb)) + (y - bb)) - t[u].l[a];
             }
+        // two pairs per pass with one target per thread: with few points the
+        // kernel is latency-bound, and the pairs are independent chains
         if (nearW) {
-#pragma unroll 2
-            for (int r = 0; r < gcnt; ++r) {
-                const float4 A = T[BS_REC * r], B = T[BS_REC * r + 1], Lo = T[BS_REC * r + 3];
-#pragma unroll
-                for (int u = 0; u < TGT; ++u)
-                    pair_precise<PERIODIC, true>(A, B, Lo, gbase + r, th[u], tl[u], t[u], t[u].v, box);
-            }
+#pragma unroll(TGT == 1 ? 2 : 1)
+            for (int p = 0; 2 * p < gcnt; ++p) pair2_precise<PERIODIC, true, TGT>(T + 8 * p, gbase + 2 * p, th, tl, t, box);
         } else {
-#pragma unroll 2
-            for (int r = 0; r < gcnt; ++r) {
-                const float4 A = T[BS_REC * r], B = T[BS_REC * r + 1], Lo = T[BS_REC * r + 3];
-#pragma unroll
-                for (int u = 0; u < TGT; ++u)
-                    pair_precise<PERIODIC, false>(A, B, Lo, gbase + r, th[u], tl[u], t[u], t[u].v, box);
-            }
+#pragma unroll(TGT == 1 ? 2 : 1)
+            for (int p = 0; 2 * p < gcnt; ++p) pair2_precise<PERIODIC, false, TGT>(T + 8 * p, gbase + 2 * p, th, tl, t, box);
         }
     } else {
-        float av[TGT][3], aw[TGT][3];
+        float2 t2[TGT][3], av[TGT][3], aw[TGT][3];
 #pragma unroll
         for (int u = 0; u < TGT; ++u)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) av[u][a] = aw[u][a] = 0.f;
-#pragma unroll 4
-        for (int r = 0; r < gcnt; ++r) {
-            const float4 A = T[BS_REC * r], B = T[BS_REC * r + 1], C = T[BS_REC * r + 2];
+            for (int a = 0; a < 3; ++a) {
+                t2[u][a] = f2(th[u][a]);
+                av[u][a] = aw[u][a] = make_float2(0.f, 0.f);
+            }
+#pragma unroll 2
+        for (int p = 0; 2 * p < gcnt; ++p) {
+            const float4* Q = T + 8 * p;
+            const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
 #pragma unroll
-            for (int u = 0; u < TGT; ++u) pair_far(A, B, C, th[u], av[u], aw[u]);
+            for (int u = 0; u < TGT; ++u) pair2_far(q0, q1, q2, q3, q4, t2[u], av[u], aw[u]);
         }
 #pragma unroll
         for (int u = 0; u < TGT; ++u) {
-            t[u].v[0] += av[u][0] + (th[u][1] * aw[u][2] - th[u][2] * aw[u][1]);
-            t[u].v[1] += av[u][1] + (th[u][2] * aw[u][0] - th[u][0] * aw[u][2]);
-            t[u].v[2] += av[u][2] + (th[u][0] * aw[u][1] - th[u][1] * aw[u][0]);
+            const float wx = aw[u][0].x + aw[u][0].y, wy = aw[u][1].x + aw[u][1].y, wz = aw[u][2].x + aw[u][2].y;
+            t[u].v[0] += (av[u][0].x + av[u][0].y) + (th[u][1] * wz - th[u][2] * wy);
+            t[u].v[1] += (av[u][1].x + av[u][1].y) + (th[u][2] * wx - th[u][0] * wz);
+            t[u].v[2] += (av[u][2].x + av[u][2].y) + (th[u][0] * wy - th[u][1] * wx);
         }
     }
 }
 
-// The work items of one Biot-Savart pass taken by this block: the item
-// blockIdx.x, then items from the device counter CNT_BSWORK (reset to 0
-// before the pass).  Returns false after a timed-out tile copy (status
-// TIMEOUT set).  A thread's TGT targets are consecutive record positions, so
-// that a warp's targets are as compact as the order makes them.
+// Work items are (target tile of BS_TPB * TGT points, source split).  Block b
+// starts with item b and takes further items from a device counter (reset by
+// the stage-geometry kernel), so the grid is fixed and no item depends on a
+// host-side estimate of N.  With several splits, each item stores its partial
+// sums and the last item of a target tile adds them in split order (fixed,
+// hence deterministic) into vel; with one split the item writes vel directly.
+// `q` counts the tiles the block has consumed across items (stage q %
+// stages, fill phase (q / stages) & 1).  A thread's TGT targets are
+// consecutive record positions, so that a warp's targets are as compact as
+// the order makes them.  Returns false after a timed-out tile copy (status
+// TIMEOUT set).
 template <bool PERIODIC, int TGT, bool EOM, bool ACC>
 __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ prev, int* __restrict__ counters,
                         int* __restrict__ tile_ticket, int cap, const BoxF& box, float kq, float* __restrict__ part,
                         float* __restrict__ vel, const EomArgs& ea, const BsImages& im, const BsOrder& o, int nsm,
-                        const BsSmem& sm, uint32_t& used, long long* __restrict__ vacc) {
-    float4 (*tile)[BS_TILE * BS_REC] = sm.tile;
-    uint64_t* bar = sm.bar;
+                        const BsSmem& sm, uint32_t& q, long long* __restrict__ vacc) {
     int& s_item = *sm.s_item;
     int& s_last = *sm.s_last;
+    volatile int* s_abort = sm.s_abort;
     constexpr int TT = BS_TPB * TGT;  // targets per item
+    constexpr int NW = BS_TPB / 32;   // warps per block
+    constexpr uint32_t NST = bs_stages<TGT>();
+    const int lane = threadIdx.x & 31;
     const int N = counters[CNT_N];
     if (N <= 0) return true;
     const int ns = bs_splits(N, TT, nsm);
@@ -458,41 +509,45 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
     if ((int)blockIdx.x >= nitems) return true;
     int item = blockIdx.x;
     while (true) {
-        __syncthreads();
         const int tb = item % ntb, split = item / ntb;
         const int j0 = min(nsrc, split * chunk);
         const int j1 = min(nsrc, j0 + chunk);
+        const int ntiles = j1 > j0 ? (j1 - j0 + BS_TILE - 1) / BS_TILE : 0;
+        // every stage is free here (the item before ended with a block barrier)
+        if (threadIdx.x == 0)
+            for (int k = 0; k < min(NST, ntiles); ++k) bs_fill(sm, seg, q + (uint32_t)k, j0, j1, k);
         BsTarget t[TGT];
 #pragma unroll
         for (int u = 0; u < TGT; ++u) t[u] = bs_target(seg, prev, o, im, Np, N, tb * TT + threadIdx.x * TGT + u);
-        const int ntiles = j1 > j0 ? (j1 - j0 + BS_TILE - 1) / BS_TILE : 0;
-        if (threadIdx.x == 0 && ntiles > 0) issue_tile(tile[used & 1], seg, j0, min(BS_TILE, j1 - j0), &bar[used & 1]);
         for (int tt = 0; tt < ntiles; ++tt) {
-            const uint32_t u = used + (uint32_t)tt;
-            const int b = (int)(u & 1u);
-            if (threadIdx.x == 0 && tt + 1 < ntiles) {
-                const int jn = j0 + (tt + 1) * BS_TILE;
-                issue_tile(tile[b ^ 1], seg, jn, min(BS_TILE, j1 - jn), &bar[b ^ 1]);
+            const uint32_t qt = q + (uint32_t)tt;
+            const int b = (int)(qt % NST);
+            if (*s_abort) break;
+            if (!mbar_wait_bounded(&sm.full[b], (qt / NST) & 1u)) {
+                if (lane == 0) {
+                    *s_abort = 1;
+                    atomicOr(&counters[CNT_STATUS], ST_TIMEOUT);
+                }
+                break;
             }
-            const bool ok = mbar_wait_bounded(&bar[b], (u >> 1) & 1u);
             const int jb = j0 + tt * BS_TILE;
             const int cnt = min(BS_TILE, j1 - jb);
-            if (ok) tile_groups(tile[b], jb, cnt, o, im, Np, sm.grp);
-            if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) {
-                    atomicOr(&counters[CNT_STATUS], ST_TIMEOUT);
-                    // let a copy still in flight land before the block's shared memory goes away
-                    if (tt + 1 < ntiles) mbar_wait_bounded(&bar[b ^ 1], ((u + 1u) >> 1) & 1u);
-                }
-                return false;
-            }
+            const float4* T = sm.tile[b];
 #pragma unroll 1
-            for (int gi = 0; gi * BS_GROUP < cnt; ++gi)
-                bs_group<PERIODIC, TGT>(tile[b] + BS_REC * BS_GROUP * gi, min(BS_GROUP, cnt - gi * BS_GROUP),
-                                        jb + gi * BS_GROUP, sm.grp[gi], t, box);
-            __syncthreads();
+            for (int gi = 0; gi * BS_GROUP < cnt; ++gi) {
+                const int gcnt = min(BS_GROUP, cnt - gi * BS_GROUP);
+                const BsGroup G = group_box(T + BS_REC * BS_GROUP * gi, gcnt, jb + gi * BS_GROUP, o, im, Np);
+                bs_group<PERIODIC, TGT>(T + BS_REC * BS_GROUP * gi, gcnt, jb + gi * BS_GROUP, G, t, box);
+            }
+            // release the stage; the last warp out refills it with the tile NST on
+            __syncwarp();
+            if (lane == 0 && atomicAdd(&sm.release[b], 1) == NW - 1) {
+                sm.release[b] = 0;
+                if (tt + NST < ntiles) bs_fill(sm, seg, qt + NST, j0, j1, tt + NST);
+            }
         }
-        used += (uint32_t)ntiles;
+        q += (uint32_t)ntiles;
+        if (__syncthreads_or(*s_abort)) return false;
 #pragma unroll
         for (int v = 0; v < TGT; ++v)
 #pragma unroll
@@ -568,24 +623,31 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
     return true;
 }
 
-// Resident blocks: the pair loop is issue-bound and needs the warps; the
-// equation of motion applied after it (EOM) needs more registers.
+// Resident blocks: the pair loop is issue-bound and needs the warps; more
+// targets per thread need more registers.
 template <bool PERIODIC, int TGT, bool EOM, bool ACC>
-__global__ void __launch_bounds__(BS_TPB, TGT == 1 ? 8 : 6)
+__global__ void __launch_bounds__(BS_TPB, TGT == 1 ? (ACC ? 7 : 8) : 5)
     k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev, int* __restrict__ counters,
                   int* __restrict__ tile_ticket, int cap, BoxF box, float kq, float* __restrict__ part,
                   float* __restrict__ vel, EomArgs ea, BsImages im, BsOrder o, int nsm,
                   long long* __restrict__ vacc) {
     pdl_wait_trigger();
-    __shared__ __align__(128) float4 tile[2][BS_TILE * BS_REC];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ BsGroup grp[BS_TILE / BS_GROUP];
-    __shared__ int s_item, s_last;
-    const BsSmem sm = {tile, bar, grp, &s_item, &s_last};
+    constexpr int NST = bs_stages<TGT>();
+    __shared__ __align__(128) float4 tile[NST][BS_TILE * BS_REC];
+    __shared__ __align__(8) uint64_t full[NST];
+    __shared__ int release[NST], fills[NST];
+    __shared__ int s_item, s_last, s_abort;
+    const BsSmem sm = {NST, tile, full, release, fills, &s_item, &s_last, &s_abort};
     bs_smem_init(sm);
-    uint32_t used = 0;
-    bs_work<PERIODIC, TGT, EOM, ACC>(seg, prev, counters, tile_ticket, cap, box, kq, part, vel, ea, im, o, nsm, sm,
-                                     used, vacc);
+    uint32_t q = 0;
+    const bool ok = bs_work<PERIODIC, TGT, EOM, ACC>(seg, prev, counters, tile_ticket, cap, box, kq, part, vel, ea,
+                                                    im, o, nsm, sm, q, vacc);
+    if (!ok && threadIdx.x == 0) {
+        // a wait gave up: let every copy still in flight land before the
+        // block's shared memory goes away (bounded as well)
+        for (int b = 0; b < NST; ++b)
+            if (fills[b] > 0) mbar_wait_bounded(&full[b], (uint32_t)(fills[b] - 1) & 1u);
+    }
 }
 
 // ----------------------------------------------------------- spatial order
@@ -708,6 +770,7 @@ __global__ void __launch_bounds__(BS_GROUP) k_bs_prep(Grid g, const double* __re
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     bs_point_order_origin(o, pos, n, n);
     __syncthreads();
+    bs_pad_records(n, 0, i, seg);
     if (i >= n) return;
     int q = next[i];
     if (q < -1 || q >= n) {  // not a point index: no segment
@@ -803,23 +866,51 @@ void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const i
                (const int*)tmp, ord, rank, org);
 }
 
+// Resident blocks per SM of one instantiation (queried once).
+template <typename K>
+int bs_resident(K kernel) {
+    static int cached = 0;
+    if (!cached) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, BS_TPB, 0) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 1;
+        }
+        cached = v;
+    }
+    return cached;
+}
+
 template <int TGT, bool EOM, bool ACC = false>
 void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int* cnt, int* tile_ticket, int cap, int n,
                float* part, float* vel, const EomArgs& ea, const BsImages& im, const BsOrder& o, cudaStream_t s,
                long long* vacc = nullptr) {
-    // enough blocks for every item of about n points (at most 8 per SM); more
-    // points than that are still covered by the blocks' item loop
+    // enough blocks for every item of about n points (at most the resident
+    // blocks); more points than that are still covered by the blocks' item loop
     constexpr int TT = BS_TPB * TGT;
     const int nsm = sm_count();
     const int items = ((n + TT - 1) / TT) * bs_splits(n, TT, nsm);
-    const int grid = items < 8 * nsm ? items : 8 * nsm;
     const BoxF box = make_box(g);
-    if (g.wall[0] && g.wall[1] && g.wall[2])
-        launch_pdl(k_biot_savart<false, TGT, EOM, ACC>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq,
-                   part, vel, ea, im, o, nsm, vacc);
-    else
-        launch_pdl(k_biot_savart<true, TGT, EOM, ACC>, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq,
-                   part, vel, ea, im, o, nsm, vacc);
+    const bool periodic = !(g.wall[0] && g.wall[1] && g.wall[2]);
+    auto kern = periodic ? k_biot_savart<true, TGT, EOM, ACC> : k_biot_savart<false, TGT, EOM, ACC>;
+    const int slots = bs_resident(kern) * nsm;
+    const int grid = items < slots ? items : slots;
+    launch_pdl(kern, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part, vel, ea, im, o, nsm, vacc);
+}
+
+// Targets per thread from 8192 points on: 2 in a box with walls on every
+// axis (each shared-memory pair is then read once for both: 6.49 against
+// 6.69 ms per launch at 86k points in the 128x128x1024 channel), 1 with a
+// periodic axis (a warp's 32 targets then meet fewer groups across half the
+// box: 594 against 673 us at 18.5k points in the 128^3 box).
+// VLB_BS_TARGETS=1 or 2 overrides.  Below 8192 points: 1.
+int bs_targets(const Grid& g) {
+    static const int forced = [] {
+        const char* e = getenv("VLB_BS_TARGETS");
+        return e ? (e[0] == '2' ? 2 : (e[0] == '1' ? 1 : 0)) : 0;
+    }();
+    if (forced) return forced;
+    return (g.wall[0] && g.wall[1] && g.wall[2]) ? 2 : 1;
 }
 
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
@@ -830,8 +921,6 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
     const int n = n_hint > 0 ? (n_hint < cap ? n_hint : cap) : 1;
     const float kq = (float)(kappa / (4.0 * 3.14159265358979323846));
     int* cnt = const_cast<int*>(counters);
-    // two targets per thread from 8192 points on (each shared-memory record is
-    // then read once for both)
     const EomArgs none = {};
     const EomArgs& ea = eom ? *eom : none;
     BsImages im = {};
@@ -844,12 +933,13 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
     }
     im.geo = geo;
     // without a partial-sum buffer the split sums always go to vacc
+    const int tgt = n >= 8192 ? bs_targets(g) : 1;
     if (vacc && !eom && (bs_uses_vacc(n) || !part)) {
-        if (n >= 8192) bs_launch<2, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
+        if (tgt == 2) bs_launch<2, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
         else bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
         return;
     }
-    if (n >= 8192) {
+    if (tgt == 2) {
         if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
         else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
     } else {

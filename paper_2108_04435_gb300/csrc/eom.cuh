@@ -83,13 +83,12 @@ __device__ __forceinline__ void bs_write_record(float4* __restrict__ seg, long l
         h[a] = __double2float_rn(rel[a]);
         l[a] = __double2float_rn(rel[a] - (double)h[a]);
     }
-    const float dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    const float cx = h[1] * d[2] - h[2] * d[1], cy = h[2] * d[0] - h[0] * d[2], cz = h[0] * d[1] - h[1] * d[0];
-    float4* r = seg + BS_REC * k;
-    r[0] = make_float4(h[0], h[1], h[2], dd);
-    r[1] = make_float4(d[0], d[1], d[2], cx);
-    r[2] = make_float4(cy, cz, 0.f, 0.f);
-    r[3] = make_float4(l[0], l[1], l[2], 0.f);
+    const float val[16] = {h[0], h[1], h[2], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], d[0], d[1], d[2],
+                           h[1] * d[2] - h[2] * d[1], h[2] * d[0] - h[0] * d[2], h[0] * d[1] - h[1] * d[0],
+                           l[0], l[1], l[2], 0.f, 0.f, 0.f};
+    float* r = reinterpret_cast<float*>(seg);
+#pragma unroll
+    for (int v = 0; v < 16; ++v) r[bs_value_index(k, v)] = val[v];
 }
 
 // Group origins in point order: a block of BS_GROUP threads covers group
@@ -114,11 +113,11 @@ __device__ __forceinline__ long long bs_position(const BsOrder& o, int i, double
     return k;
 }
 
-// Zero-length records at the padding positions [N, Np) of every record block
-// (wall images on): thread i covers position i.
+// Zero-length records at the padding positions [N, Np) of every record block:
+// thread i covers position i.
 __device__ __forceinline__ void bs_pad_records(int N, int nfaces, int i, float4* __restrict__ seg) {
     const long long Np = bs_block(N, nfaces);
-    if (nfaces == 0 || i < N || i >= Np) return;
+    if (i < N || i >= Np) return;
     const double z[3] = {0.0, 0.0, 0.0};
     const float d[3] = {0.f, 0.f, 0.f};
     for (int f = 0; f <= nfaces; ++f) bs_write_record(seg, (long long)f * Np + i, z, d);
@@ -139,7 +138,7 @@ __device__ __forceinline__ void geometry_point(const VfmParams& P, const double*
     const int p = prev[i], q = next[i];
     const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
     double si[3], sp[3], sq[3];
-    float a[3], b[3];
+    float b[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         si[k] = s[(long long)k * cap + i];
@@ -171,7 +170,6 @@ __device__ __forceinline__ void geometry_point(const VfmParams& P, const double*
         if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
         da[k] = min_image(P.g, k, si[k] - sp[k]);
         db[k] = min_image(P.g, k, sq[k] - si[k]);
-        a[k] = (float)da[k];
         b[k] = (float)db[k];
     }
     const double lm = sqrt(da[0] * da[0] + da[1] * da[1] + da[2] * da[2]);
@@ -183,7 +181,10 @@ __device__ __forceinline__ void geometry_point(const VfmParams& P, const double*
         t1[k] = (lm * lm * db[k] + lp * lp * da[k]) * inv;
         t2[k] = 2.0 * (lm * db[k] - lp * da[k]) * inv;
     }
-    const double beta = P.kq * log(2.0 * sqrt(lp * lm) * P.inv_ea);
+    // beta = kappa/4pi ln(2 sqrt(l+ l-) / (e^{1/4} a)) = kappa/4pi (C + ln(l+ l-) / 2) with
+    // C = ln(2 / (e^{1/4} a)) (~12 for a ~ 1e-5 cells) formed in FP64 on the host;
+    // the small ln(l+ l-) (|.| < 1 for remeshed segments) from logf changes beta by ~3e-9
+    const double beta = P.kq * (P.beta_c + 0.5 * (double)logf((float)(lp * lm)));
     // geo[2i] = (s'.xyz, dxi), geo[2i+1] = (local velocity beta s' x s'', wall code + 1 of a pinned end)
     const double dxi = p < 0 ? 0.5 * lp : (q < 0 ? 0.5 * lm : 0.5 * (lp + lm));
     geo[2LL * i] = make_float4((float)t1[0], (float)t1[1], (float)t1[2], (float)dxi);

@@ -106,7 +106,7 @@ constexpr int LBM_BLOCK = 256;  // cells per stream-collide block (one z plane)
 constexpr int BS_TPB = 128;     // threads per Biot-Savart block
 constexpr int BS_TILE = 128;    // source records per shared-memory tile
 constexpr int BS_GROUP = 64;    // source records that share one integer origin
-constexpr int BS_REC = 4;       // float4 per source record (64 bytes)
+constexpr int BS_REC = 4;       // float4 per source record (64 bytes; records are stored in interleaved pairs)
 constexpr int MAX_SPLIT = 64;   // Biot-Savart source splits
 // From this many points on the Biot-Savart sources are put in a spatial order
 // once per step, so that a group of BS_GROUP records spans a small box
@@ -115,13 +115,16 @@ constexpr int BS_SORT_MAX_BINS = 1 << 16;  // bins of the spatial order (bin edg
 
 // Biot-Savart source record of segment s_j -> s_j + d, stored relative to
 // the integer origin O of its group of BS_GROUP records (the cell of the
-// group's first point):
-//   [0] (h.x, h.y, h.z, |d|^2)   h = fl(s_j - O), minimum image on periodic axes
-//   [1] (d.x, d.y, d.z, c.x)     c = h x d (FP32)
-//   [2] (c.y, c.z, 0, 0)
-//   [3] (l.x, l.y, l.z, 0)       l = fl(s_j - O - h): h + l carries s_j - O to ~1e-14 cells
+// group's first point).  Its 16 values:
+//   0-2 h = fl(s_j - O) (minimum image on periodic axes), 3 |d|^2,
+//   4-6 d, 7-9 c = h x d (FP32), 10-12 l = fl(s_j - O - h), 13-15 zero;
+// h + l carries s_j - O to ~1e-14 cells.  Records come in pairs (2p, 2p + 1)
+// stored interleaved in 128 bytes: value v of record k is float
+// (k / 2) * 32 + 2 v + (k % 2), so that one float4 holds two values of both
+// records and one float2 the same value of both (the packed FP32 pair path).
 // A target r (its own record k: origin O_t, parts h_t, l_t) sees the group
 // at offset t = (O - O_t) - h_t - l_t, so R1 = s_j - r = h + l + t.
+__host__ __device__ inline long long bs_value_index(long long k, int v) { return (k >> 1) * 32 + 2 * v + (k & 1); }
 
 // Order of the Biot-Savart sources.  sorted = 0: record k is point k;
 // sorted = 1: record k is point ord[k] (rank is the inverse), a spatial order.
@@ -167,9 +170,10 @@ __host__ __device__ inline BsBins bs_bins(int nx, int ny, int nz) {
 }
 
 // Records of a point set of n points with nfaces wall-image blocks: each
-// block is padded to a multiple of BS_GROUP records when images are on.
+// block is padded to a multiple of BS_GROUP records when images are on, and
+// to an even count (whole pairs) without them; padding records are zero.
 __host__ __device__ inline long long bs_block(int n, int nfaces) {
-    return nfaces > 0 ? (long long)((n + BS_GROUP - 1) / BS_GROUP) * BS_GROUP : (long long)n;
+    return nfaces > 0 ? (long long)((n + BS_GROUP - 1) / BS_GROUP) * BS_GROUP : (long long)(n + (n & 1));
 }
 
 // Geometry of the lattice, passed by value to kernels.
@@ -241,7 +245,7 @@ struct VfmParams {
     double kappa, alpha, alpha_p, ratio, rho0, core_a, dmin, dmax;
     double dt;
     double kq;       // kappa / (4 pi)
-    double inv_ea;   // 1 / (e^{1/4} a)
+    double beta_c;   // ln(2 / (e^{1/4} a)), the constant part of the local coefficient
     float alpha_f, alpha_p_f;
     float gscale_f;  // -(rho_s/rho_n) rho0 kappa
     int couple, force_form;
