@@ -316,7 +316,7 @@ def run_vlb(args, ws, rank, local):
     # stream-collide: algorithmic bytes / mean event-timed launch
     k1_avg_s = (k1_ms / 1e3) / max(k1_n, 1)
     k1_achieved = bpc * cells / k1_avg_s / 1e9 if k1_n else None
-    k1_traffic = profile_traffic("k_lbm_step", args.config, ["lbm.cu", "vlb_internal.cuh"])
+    k1_traffic = profile_traffic("k_lbm_step", args.config, ["lbm.cu"])
     # Biot-Savart: N (N - 2) pairs per launch at the mean live count of the
     # event-timed steps, 45 FP32 flop each, against the FP32 peak of this
     # GPU (SMs x 128 lanes x 2 flop x clock) at the maximum clock and at the

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = {"abi.cu": [], "lbm.cu": [], "bs.cu": [], "vfm.cu": [], "topo.cu": ["-fmad=false"]}
+SOURCES = {"abi.cu": [], "lbm.cu": [], "bs.cu": [], "order.cu": [], "vfm.cu": [], "topo.cu": ["-fmad=false"]}
 NVCC = os.environ.get("NVCC", "nvcc")
 
 

@@ -625,8 +625,8 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     V.dt = 1.0 / (double)p->vfm_substeps;
     V.couple = p->couple;
     V.force_form = p->force_form;
-    V.kq = p->kappa / (4.0 * 3.14159265358979323846);
-    V.beta_c = log(2.0 / (exp(0.25) * p->core_a));
+    V.kq_f = (float)(p->kappa / (4.0 * 3.14159265358979323846));
+    V.beta_c_f = (float)log(2.0 / (exp(0.25) * p->core_a));
     V.alpha_f = (float)p->alpha;
     V.alpha_p_f = (float)p->alpha_p;
     V.gscale_f = (float)(-p->rho_s_over_rho_n * p->rho0 * p->kappa);

@@ -36,6 +36,7 @@
 #include <stdlib.h>
 
 #include "eom.cuh"
+#include "records.cuh"
 #include "vlb_internal.cuh"
 
 namespace vlb {
@@ -121,7 +122,7 @@ __device__ __forceinline__ float mi_axis(float r, float L, float iL) { return fm
 // error of about one float ulp of the group extent and of the offset, i.e.
 // ~1e-7 (1 + extent / distance) of the pair), no target can lie on a segment,
 // and none of the target's own segments is in the group.
-constexpr float BS_NEAR = 12.f;
+constexpr float BS_NEAR = 8.f;
 
 // One target of a Biot-Savart pass (registers of one thread): its own
 // record (origin O, parts h + l, so that the point is O + h + l) and the
@@ -650,126 +651,12 @@ __global__ void __launch_bounds__(BS_TPB, TGT == 1 ? (ACC ? 7 : 8) : 5)
     }
 }
 
-// ----------------------------------------------------------- spatial order
-
-__device__ __forceinline__ int bs_key_of(const Grid& g, const BsBins& bb, double x, double y, double z) {
-    const int n[3] = {g.nx, g.ny, g.nz};
-    const double s[3] = {x, y, z};
-    int b[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        int c = (int)floor(s[a]);
-        c = c < 0 ? 0 : (c > n[a] - 1 ? n[a] - 1 : c);
-        b[a] = c >> bb.shift;
-    }
-    int key = 0, pos = 0;
-    for (int l = 0; l < 16; ++l)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (l < bb.bits[a]) key |= ((b[a] >> l) & 1) << pos++;
-    return key;
-}
-
-// Key and bin count of every point (grid-stride beyond the grid).
-__global__ void k_sort_keys(Grid g, BsBins bb, const double* __restrict__ pos, int cap,
-                            const int* __restrict__ counters, int* __restrict__ key, int* __restrict__ cnt) {
-    pdl_wait_trigger();
-    const int N = counters[CNT_N];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const int k = bs_key_of(g, bb, pos[i], pos[(long long)cap + i], pos[2LL * cap + i]);
-        key[i] = k;
-        atomicAdd(&cnt[k], 1);
-    }
-}
-
-// Exclusive scan of the bin counts (one block of 1024 threads).
-__global__ void __launch_bounds__(1024) k_sort_scan(int K, const int* __restrict__ cnt, int* __restrict__ start) {
-    pdl_wait_trigger();
-    __shared__ int warp_sum[32];
-    const int per = (K + 1023) / 1024;
-    const int b0 = threadIdx.x * per;
-    int sum = 0;
-    for (int k = b0; k < min(K, b0 + per); ++k) sum += cnt[k];
-    // inclusive scan of the thread sums across the block
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int x = sum;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) warp_sum[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int z = warp_sum[lane];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, z, off);
-            if (lane >= off) z += y;
-        }
-        warp_sum[lane] = z;
-    }
-    __syncthreads();
-    int run = x - sum + (w > 0 ? warp_sum[w - 1] : 0);
-    for (int k = b0; k < min(K, b0 + per); ++k) {
-        start[k] = run;
-        run += cnt[k];
-    }
-}
-
-// Every point into its bin (arbitrary order inside the bin; start[k] ends as
-// the bin's end).
-__global__ void k_sort_scatter(const int* __restrict__ counters, const int* __restrict__ key, int* __restrict__ start,
-                               int* __restrict__ tmp) {
-    pdl_wait_trigger();
-    const int N = counters[CNT_N];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        tmp[atomicAdd(&start[key[i]], 1)] = i;
-}
-
-// One warp per bin: the bin's points in ascending index (so the order is
-// deterministic), their ranks, the origin of every group that starts in the
-// bin, and the bin count cleared for the next sort.
-__global__ void k_sort_bins(int K, const double* __restrict__ pos, int cap, int* __restrict__ cnt,
-                            const int* __restrict__ start, const int* __restrict__ tmp, int* __restrict__ ord,
-                            int* __restrict__ rank, int4* __restrict__ org) {
-    pdl_wait_trigger();
-    const int lane = threadIdx.x & 31;
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (k >= K) return;
-    const int n = cnt[k];
-    if (n == 0) return;
-    const int e = start[k], s0 = e - n;
-    for (int c = 0; c < n; c += 32) {
-        const int my = c + lane < n ? tmp[s0 + c + lane] : 0x7fffffff;
-        int r = 0;
-        for (int m = 0; m < n; m += 32) {
-            const int other = m + lane < n ? tmp[s0 + m + lane] : 0x7fffffff;
-#pragma unroll 8
-            for (int q = 0; q < 32; ++q) r += __shfl_sync(0xffffffffu, other, q) < my;
-        }
-        if (c + lane < n) {
-            const int p = s0 + r;
-            ord[p] = my;
-            rank[my] = p;
-            if (p % BS_GROUP == 0)
-                org[p / BS_GROUP] = make_int4((int)floor(pos[my]), (int)floor(pos[(long long)cap + my]),
-                                              (int)floor(pos[2LL * cap + my]), 0);
-        }
-    }
-    __syncwarp();
-    if (lane == 0) cnt[k] = 0;
-}
-
-// Stand-alone entry: prev[] and the source records of a caller's point set
-// (one block per group of BS_GROUP records in point order).
+// Stand-alone entry: prev[] and the source records of a caller's point set.
 __global__ void __launch_bounds__(BS_GROUP) k_bs_prep(Grid g, const double* __restrict__ pos,
                                                       const int* __restrict__ next, int n, int* __restrict__ prev,
                                                       float4* __restrict__ seg, int* __restrict__ counters,
                                                       BsOrder o) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bs_point_order_origin(o, pos, n, n);
-    __syncthreads();
     bs_pad_records(n, 0, i, seg);
     if (i >= n) return;
     int q = next[i];
@@ -780,7 +667,7 @@ __global__ void __launch_bounds__(BS_GROUP) k_bs_prep(Grid g, const double* __re
     if (q >= 0) prev[q] = i;
     const int nn[3] = {g.nx, g.ny, g.nz};
     double O[3], rel[3];
-    const long long k = bs_position(o, i, O);
+    const long long k = bs_position(o, pos, n, i, O);
     float d[3];
     for (int a = 0; a < 3; ++a) {
         const double si = pos[(long long)a * n + i];
@@ -853,17 +740,6 @@ int bs_max_splits(int cap, int nsm) {
         if (k > m) m = k;
     }
     return m;
-}
-
-void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
-                    int* ord, int* rank, int4* org, int* cnt, int* start, cudaStream_t s) {
-    const BsBins bb = bs_bins(g.nx, g.ny, g.nz);
-    const int blocks = (span + 255) / 256 > 0 ? (span + 255) / 256 : 1;
-    launch_pdl(k_sort_keys, blocks, 256, 0, s, g, bb, pos, cap, counters, key, cnt);
-    launch_pdl(k_sort_scan, 1, 1024, 0, s, bb.K, (const int*)cnt, start);
-    launch_pdl(k_sort_scatter, blocks, 256, 0, s, counters, (const int*)key, start, tmp);
-    launch_pdl(k_sort_bins, (bb.K * 32 + 255) / 256, 256, 0, s, bb.K, pos, cap, cnt, (const int*)start,
-               (const int*)tmp, ord, rank, org);
 }
 
 // Resident blocks per SM of one instantiation (queried once).

@@ -73,151 +73,6 @@ __device__ __forceinline__ void delta_axis(const Grid& g, int axis, double s, in
     i1 = a1;
 }
 
-// One Biot-Savart source record (layout in vlb_internal.cuh): rel = the
-// segment's start relative to its group origin (FP64), d = the segment.
-__device__ __forceinline__ void bs_write_record(float4* __restrict__ seg, long long k, const double rel[3],
-                                                const float d[3]) {
-    float h[3], l[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        h[a] = __double2float_rn(rel[a]);
-        l[a] = __double2float_rn(rel[a] - (double)h[a]);
-    }
-    const float val[16] = {h[0], h[1], h[2], d[0] * d[0] + d[1] * d[1] + d[2] * d[2], d[0], d[1], d[2],
-                           h[1] * d[2] - h[2] * d[1], h[2] * d[0] - h[0] * d[2], h[0] * d[1] - h[1] * d[0],
-                           l[0], l[1], l[2], 0.f, 0.f, 0.f};
-    float* r = reinterpret_cast<float*>(seg);
-#pragma unroll
-    for (int v = 0; v < 16; ++v) r[bs_value_index(k, v)] = val[v];
-}
-
-// Group origins in point order: a block of BS_GROUP threads covers group
-// blockIdx.x, whose origin is the cell of its first point (all threads of the
-// block must call this; N = live points).
-__device__ __forceinline__ void bs_point_order_origin(const BsOrder& o, const double* __restrict__ s, int cap,
-                                                      int N) {
-    if (o.sorted || threadIdx.x != 0) return;
-    const int i0 = blockIdx.x * BS_GROUP;
-    if (i0 >= N) return;
-    o.org[blockIdx.x] = make_int4((int)floor(s[i0]), (int)floor(s[(long long)cap + i0]),
-                                  (int)floor(s[2LL * cap + i0]), 0);
-}
-
-// Record position and group origin of point i in the order o.
-__device__ __forceinline__ long long bs_position(const BsOrder& o, int i, double O[3]) {
-    const int k = o.sorted ? o.rank[i] : i;
-    const int4 g = o.org[k / BS_GROUP];
-    O[0] = (double)g.x;
-    O[1] = (double)g.y;
-    O[2] = (double)g.z;
-    return k;
-}
-
-// Zero-length records at the padding positions [N, Np) of every record block:
-// thread i covers position i.
-__device__ __forceinline__ void bs_pad_records(int N, int nfaces, int i, float4* __restrict__ seg) {
-    const long long Np = bs_block(N, nfaces);
-    if (i < N || i >= Np) return;
-    const double z[3] = {0.0, 0.0, 0.0};
-    const float d[3] = {0.f, 0.f, 0.f};
-    for (int f = 0; f <= nfaces; ++f) bs_write_record(seg, (long long)f * Np + i, z, d);
-}
-
-// Stage geometry of point i for the equation of motion: the same quantities as
-// k_geometry, in FP64 (positions are up to ~1e3 cells), stored as float for
-// the FP32 equation of motion and Biot-Savart sum.  The remeshing decisions
-// use the FP64 k_geometry instead.  An open end pinned on a wall takes the mirror image
-// of its neighbour across that wall as its missing neighbour, represents half
-// of its segment, and carries its wall code (+1) to the equation of motion; a
-// line's last point has a zero-length source record.  The source records go
-// to the positions of the order o.
-__device__ __forceinline__ void geometry_point(const VfmParams& P, const double* __restrict__ s,
-                                               const int* __restrict__ next, const int* __restrict__ prev, int N,
-                                               int cap, int i, float4* __restrict__ geo, float4* __restrict__ seg,
-                                               double* __restrict__ s0_copy, const BsOrder& o) {
-    const int p = prev[i], q = next[i];
-    const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
-    double si[3], sp[3], sq[3];
-    float b[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        si[k] = s[(long long)k * cap + i];
-        sp[k] = s[(long long)k * cap + pl];
-        sq[k] = s[(long long)k * cap + ql];
-    }
-    int code = -1;
-    if (p < 0 || q < 0) {
-        code = touching_wall(P.g, P.dmin, si);
-        const int ax = code >> 1;
-        const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
-        const double w2 = 2.0 * ((code & 1) ? L - 0.5 : -0.5);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const double nb = p < 0 ? sq[k] : sp[k];
-            // mirror image across the wall; an end on no wall is continued straight
-            const double g = code < 0 ? 2.0 * si[k] - nb : (k == ax ? w2 - nb : nb);
-            if (p < 0) sp[k] = g;
-            else sq[k] = g;
-        }
-    }
-    // The local self-induced term is near-singular (its coefficient carries
-    // ln(l / a) with a ~ 1e-5 cells, and s'' comes from nearly cancelling
-    // differences on gently curved lines): it is formed in FP64 from the FP64
-    // neighbour differences, and only the result is rounded to float.
-    double da[3], db[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
-        da[k] = min_image(P.g, k, si[k] - sp[k]);
-        db[k] = min_image(P.g, k, sq[k] - si[k]);
-        b[k] = (float)db[k];
-    }
-    const double lm = sqrt(da[0] * da[0] + da[1] * da[1] + da[2] * da[2]);
-    const double lp = sqrt(db[0] * db[0] + db[1] * db[1] + db[2] * db[2]);
-    const double inv = 1.0 / (lp * lm * (lp + lm));
-    double t1[3], t2[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        t1[k] = (lm * lm * db[k] + lp * lp * da[k]) * inv;
-        t2[k] = 2.0 * (lm * db[k] - lp * da[k]) * inv;
-    }
-    // beta = kappa/4pi ln(2 sqrt(l+ l-) / (e^{1/4} a)) = kappa/4pi (C + ln(l+ l-) / 2) with
-    // C = ln(2 / (e^{1/4} a)) (~12 for a ~ 1e-5 cells) formed in FP64 on the host;
-    // the small ln(l+ l-) (|.| < 1 for remeshed segments) from logf changes beta by ~3e-9
-    const double beta = P.kq * (P.beta_c + 0.5 * (double)logf((float)(lp * lm)));
-    // geo[2i] = (s'.xyz, dxi), geo[2i+1] = (local velocity beta s' x s'', wall code + 1 of a pinned end)
-    const double dxi = p < 0 ? 0.5 * lp : (q < 0 ? 0.5 * lm : 0.5 * (lp + lm));
-    geo[2LL * i] = make_float4((float)t1[0], (float)t1[1], (float)t1[2], (float)dxi);
-    geo[2LL * i + 1] = make_float4((float)(beta * (t1[1] * t2[2] - t1[2] * t2[1])),
-                                   (float)(beta * (t1[2] * t2[0] - t1[0] * t2[2])),
-                                   (float)(beta * (t1[0] * t2[1] - t1[1] * t2[0])), (float)(code + 1));
-    if (q < 0) b[0] = b[1] = b[2] = 0.f;  // no segment leaves a line's last point
-    double O[3], rel[3];
-    const long long k = bs_position(o, i, O);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) rel[a] = min_image(P.g, a, si[a] - O[a]);
-    bs_write_record(seg, k, rel, b);
-    // Image of segment i -> q across each solid face: from M(s_q) to M(s_i),
-    // M mirroring the normal coordinate x_a -> w2 - x_a (record (1 + f) Np + k,
-    // relative to the mirrored origin w2 - O_a, an integer as w2 is).
-    const long long Np = bs_block(N, P.nfaces);
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        if (f >= P.nfaces) break;
-        const int code = P.face_code[f], ax = code >> 1;
-        float d[3];
-        double irel[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            // a line's last point starts no segment: a zero-length record at its own image
-            const double st = q >= 0 ? sq[a] : si[a];
-            irel[a] = a == ax ? O[a] - st : min_image(P.g, a, st - O[a]);
-            d[a] = a == ax ? b[a] : -b[a];
-        }
-        bs_write_record(seg, (long long)(1 + f) * Np + k, irel, d);
-    }
-}
-
 // Equation of motion (Eq. 4) at one RK4 stage, in FP32, with the
 // Biot-Savart partial sums reduced in a fixed order, the local term, V_s of
 // Eq. 18 as the applied superfluid flow and v_n interpolated with Eq. 11; the

@@ -1,0 +1,154 @@
+// Spatial order of the Biot-Savart sources (the points of the current step):
+// a Morton key per point from its bin of 8 cells (wider on lattices of more
+// than 65536 bins), a counting sort over the bins, and inside each bin the
+// points in ascending index, so that the order depends on nothing but the
+// positions.  Group g of BS_GROUP consecutive sorted points gets the integer
+// origin of its first point.  Built once per step from BS_SORT_MIN points on.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "vlb_internal.cuh"
+
+namespace vlb {
+
+namespace {
+
+__device__ __forceinline__ int bs_key_of(const Grid& g, const BsBins& bb, double x, double y, double z) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const double s[3] = {x, y, z};
+    int b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)floor(s[a]);
+        c = c < 0 ? 0 : (c > n[a] - 1 ? n[a] - 1 : c);
+        b[a] = c >> bb.shift;
+    }
+    int key = 0, pos = 0;
+    for (int l = 0; l < 16; ++l)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (l < bb.bits[a]) key |= ((b[a] >> l) & 1) << pos++;
+    return key;
+}
+
+// Key and bin count of every point (grid-stride beyond the grid).
+__global__ void k_sort_keys(Grid g, BsBins bb, const double* __restrict__ pos, int cap,
+                            const int* __restrict__ counters, int* __restrict__ key, int* __restrict__ cnt) {
+    pdl_wait_trigger();
+    const int N = counters[CNT_N];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const int k = bs_key_of(g, bb, pos[i], pos[(long long)cap + i], pos[2LL * cap + i]);
+        key[i] = k;
+        atomicAdd(&cnt[k], 1);
+    }
+}
+
+// Exclusive scan of the bin counts (one block of 1024 threads), 4096 bins
+// per round: each thread takes four consecutive bins with one 16-byte load
+// (a warp reads 512 contiguous bytes), the block scans the thread sums, and
+// a carry runs from round to round.  K is a power of two.
+__global__ void __launch_bounds__(1024) k_sort_scan(int K, const int* __restrict__ cnt, int* __restrict__ start) {
+    pdl_wait_trigger();
+    __shared__ int warp_sum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int carry = 0;
+    for (int base = 0; base < K; base += 4096) {
+        const int k0 = base + 4 * (int)threadIdx.x;
+        int4 v = make_int4(0, 0, 0, 0);
+        if (k0 + 3 < K) {
+            v = *reinterpret_cast<const int4*>(cnt + k0);
+        } else if (k0 < K) {
+            v.x = cnt[k0];
+            if (k0 + 1 < K) v.y = cnt[k0 + 1];
+            if (k0 + 2 < K) v.z = cnt[k0 + 2];
+        }
+        const int sum = v.x + v.y + v.z + v.w;
+        int x = sum;  // inclusive scan within the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_sum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int z = warp_sum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, z, off);
+                if (lane >= off) z += y;
+            }
+            warp_sum[lane] = z;  // inclusive over warps
+        }
+        __syncthreads();
+        const int excl = carry + (x - sum) + (w > 0 ? warp_sum[w - 1] : 0);
+        if (k0 + 3 < K) {
+            *reinterpret_cast<int4*>(start + k0) = make_int4(excl, excl + v.x, excl + v.x + v.y, excl + v.x + v.y + v.z);
+        } else if (k0 < K) {
+            start[k0] = excl;
+            if (k0 + 1 < K) start[k0 + 1] = excl + v.x;
+            if (k0 + 2 < K) start[k0 + 2] = excl + v.x + v.y;
+        }
+        carry += warp_sum[31];
+        __syncthreads();  // warp_sum is rewritten by the next round
+    }
+}
+
+// Every point into its bin (arbitrary order inside the bin; start[k] ends as
+// the bin's end).
+__global__ void k_sort_scatter(const int* __restrict__ counters, const int* __restrict__ key, int* __restrict__ start,
+                               int* __restrict__ tmp) {
+    pdl_wait_trigger();
+    const int N = counters[CNT_N];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        tmp[atomicAdd(&start[key[i]], 1)] = i;
+}
+
+// One warp per bin: the bin's points in ascending index (so the order is
+// deterministic), their ranks, the origin of every group that starts in the
+// bin, and the bin count cleared for the next sort.
+__global__ void k_sort_bins(int K, const double* __restrict__ pos, int cap, int* __restrict__ cnt,
+                            const int* __restrict__ start, const int* __restrict__ tmp, int* __restrict__ ord,
+                            int* __restrict__ rank, int4* __restrict__ org) {
+    pdl_wait_trigger();
+    const int lane = threadIdx.x & 31;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= K) return;
+    const int n = cnt[k];
+    if (n == 0) return;
+    const int e = start[k], s0 = e - n;
+    for (int c = 0; c < n; c += 32) {
+        const int my = c + lane < n ? tmp[s0 + c + lane] : 0x7fffffff;
+        int r = 0;
+        for (int m = 0; m < n; m += 32) {
+            const int other = m + lane < n ? tmp[s0 + m + lane] : 0x7fffffff;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) r += __shfl_sync(0xffffffffu, other, q) < my;
+        }
+        if (c + lane < n) {
+            const int p = s0 + r;
+            ord[p] = my;
+            rank[my] = p;
+            if (p % BS_GROUP == 0)
+                org[p / BS_GROUP] = make_int4((int)floor(pos[my]), (int)floor(pos[(long long)cap + my]),
+                                              (int)floor(pos[2LL * cap + my]), 0);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) cnt[k] = 0;
+}
+
+}  // namespace
+
+void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
+                    int* ord, int* rank, int4* org, int* cnt, int* start, cudaStream_t s) {
+    const BsBins bb = bs_bins(g.nx, g.ny, g.nz);
+    const int blocks = (span + 255) / 256 > 0 ? (span + 255) / 256 : 1;
+    launch_pdl(k_sort_keys, blocks, 256, 0, s, g, bb, pos, cap, counters, key, cnt);
+    launch_pdl(k_sort_scan, 1, 1024, 0, s, bb.K, (const int*)cnt, start);
+    launch_pdl(k_sort_scatter, blocks, 256, 0, s, counters, (const int*)key, start, tmp);
+    launch_pdl(k_sort_bins, (bb.K * 32 + 255) / 256, 256, 0, s, bb.K, pos, cap, cnt, (const int*)start,
+               (const int*)tmp, ord, rank, org);
+}
+
+}  // namespace vlb

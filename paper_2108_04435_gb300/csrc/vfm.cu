@@ -9,16 +9,126 @@
 #include <math.h>
 
 #include "eom.cuh"
+#include "records.cuh"
 #include "vlb_internal.cuh"
 
 namespace vlb {
 
 namespace {
 
+// Stage geometry of point i for the equation of motion: the same quantities as
+// k_geometry (remeshing decisions use that FP64 kernel instead), stored as
+// float for the FP32 equation of motion and Biot-Savart sum.  An open end pinned on a wall takes the mirror image
+// of its neighbour across that wall as its missing neighbour, represents half
+// of its segment, and carries its wall code (+1) to the equation of motion; a
+// line's last point has a zero-length source record.  The source records go
+// to the positions of the order o.
+struct StageRec {
+    long long k;   // record position
+    double O[3];   // group origin
+    double si[3];  // the point
+    double st[3];  // its successor (itself at a line's last point)
+    float b[3];    // the segment
+};
 
-// One thread per point (and per padding record position), one block per
-// group of BS_GROUP records in point order; thread 0 also resets the work
-// counter of the Biot-Savart launch that follows.
+__device__ __forceinline__ void geometry_point(const VfmParams& P, const double* __restrict__ s,
+                                               const int* __restrict__ next, const int* __restrict__ prev, int N,
+                                               int cap, int i, float4* __restrict__ geo, double* __restrict__ s0_copy,
+                                               const BsOrder& o, StageRec& out) {
+    const int p = prev[i], q = next[i];
+    const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
+    double si[3], sp[3], sq[3];
+    float b[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        si[k] = s[(long long)k * cap + i];
+        sp[k] = s[(long long)k * cap + pl];
+        sq[k] = s[(long long)k * cap + ql];
+    }
+    int code = -1;
+    if (p < 0 || q < 0) {
+        code = touching_wall(P.g, P.dmin, si);
+        const int ax = code >> 1;
+        const double L = (double)(ax == 0 ? P.g.nx : (ax == 1 ? P.g.ny : P.g.nz));
+        const double w2 = 2.0 * ((code & 1) ? L - 0.5 : -0.5);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double nb = p < 0 ? sq[k] : sp[k];
+            // mirror image across the wall; an end on no wall is continued straight
+            const double g = code < 0 ? 2.0 * si[k] - nb : (k == ax ? w2 - nb : nb);
+            if (p < 0) sp[k] = g;
+            else sq[k] = g;
+        }
+    }
+    // Neighbour differences a = s_i - s_p, b = s_q - s_i in FP64 (positions
+    // are up to ~1e3 cells).  With the 3-point derivatives on the non-uniform
+    // grid, s' = (l-^2 b + l+^2 a) / D and s'' = 2 (l- b - l+ a) / D,
+    // D = l+ l- (l+ + l-), the local term beta s' x s'' is exactly
+    // 2 beta (a x b) / D.  Its near-singular part is a x b: on a gently curved
+    // line a and b are nearly parallel and their cross product cancels, so it
+    // is formed in FP64; the lengths, beta and 1/D are smooth and stay FP32
+    // (relative error ~1e-7).
+    double da[3], db[3];
+    float a[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (s0_copy) s0_copy[(long long)k * cap + i] = si[k];  // first stage: RK4 base positions
+        da[k] = min_image(P.g, k, si[k] - sp[k]);
+        db[k] = min_image(P.g, k, sq[k] - si[k]);
+        a[k] = (float)da[k];
+        b[k] = (float)db[k];
+    }
+    const float lm = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const float lp = sqrtf(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    const float inv = 1.f / (lp * lm * (lp + lm));
+    float t1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t1[k] = (lm * lm * b[k] + lp * lp * a[k]) * inv;
+    const double ab[3] = {da[1] * db[2] - da[2] * db[1], da[2] * db[0] - da[0] * db[2], da[0] * db[1] - da[1] * db[0]};
+    // beta = kappa/4pi ln(2 sqrt(l+ l-) / (e^{1/4} a)) = kappa/4pi (C + ln(l+ l-) / 2), C = ln(2 / (e^{1/4} a))
+    const float beta = P.kq_f * (P.beta_c_f + 0.5f * logf(lp * lm));
+    const float fl = 2.f * beta * inv;
+    // geo[2i] = (s'.xyz, dxi), geo[2i+1] = (local velocity beta s' x s'', wall code + 1 of a pinned end)
+    const float dxi = p < 0 ? 0.5f * lp : (q < 0 ? 0.5f * lm : 0.5f * (lp + lm));
+    geo[2LL * i] = make_float4(t1[0], t1[1], t1[2], dxi);
+    geo[2LL * i + 1] = make_float4(fl * (float)ab[0], fl * (float)ab[1], fl * (float)ab[2], (float)(code + 1));
+    if (q < 0) b[0] = b[1] = b[2] = 0.f;  // no segment leaves a line's last point
+    out.k = bs_position(o, s, cap, i, out.O);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out.si[a] = si[a];
+        out.st[a] = q >= 0 ? sq[a] : si[a];  // a line's last point starts no segment: its image is zero-length
+        out.b[a] = b[a];
+    }
+}
+
+// Source record f of the point geometry_point described: f = 0 the segment
+// itself, f = 1 + face its image across that solid face, from M(s_q) to
+// M(s_i) with M mirroring the normal coordinate x_a -> w2 - x_a (record
+// (1 + face) Np + k, relative to the mirrored origin w2 - O_a, an integer as
+// w2 is).
+__device__ __forceinline__ void stage_record(const VfmParams& P, const StageRec& r, int f, float val[16]) {
+    double rel[3];
+    float d[3];
+    if (f == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            rel[a] = min_image(P.g, a, r.si[a] - r.O[a]);
+            d[a] = r.b[a];
+        }
+    } else {
+        const int ax = P.face_code[f - 1] >> 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            rel[a] = a == ax ? r.O[a] - r.st[a] : min_image(P.g, a, r.st[a] - r.O[a]);
+            d[a] = a == ax ? r.b[a] : -r.b[a];
+        }
+    }
+    bs_record_values(rel, d, val);
+}
+
+// One thread per point (and per padding record position); thread 0 also
+// resets the work counter of the Biot-Savart launch that follows.
 __global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const double* __restrict__ s,
                                                              const int* __restrict__ next,
                                                              const int* __restrict__ prev,
@@ -29,13 +139,38 @@ __global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const 
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch that follows takes items from 0
-    bs_point_order_origin(o, s, cap, N);
-    __syncthreads();
-    if (i >= N) {
-        bs_pad_records(N, P.nfaces, i, seg);
+    const long long Np = bs_block(N, P.nfaces);
+    if (o.sorted) {
+        // records at the positions of the order: stored one by one
+        if (i >= N) {
+            bs_pad_records(N, P.nfaces, i, seg);
+            return;
+        }
+        StageRec r;
+        geometry_point(P, s, next, prev, N, cap, i, geo, s0_copy, o, r);
+        for (int f = 0; f <= P.nfaces; ++f) {
+            float val[16];
+            stage_record(P, r, f, val);
+            bs_store_record(seg, (long long)f * Np + r.k, val);
+        }
         return;
     }
-    geometry_point(P, s, next, prev, N, cap, i, geo, seg, s0_copy, o);
+    // point order: record i, so the two records of a pair belong to this
+    // lane and its neighbour, which store the pair together (zero records at
+    // the padding positions [N, Np))
+    StageRec r = {};
+    r.k = i;
+    if (i < N) geometry_point(P, s, next, prev, N, cap, i, geo, s0_copy, o, r);
+    for (int f = 0; f <= P.nfaces; ++f) {
+        float val[16];
+        if (i < N) {
+            stage_record(P, r, f, val);
+        } else {
+#pragma unroll
+            for (int v = 0; v < 16; ++v) val[v] = 0.f;
+        }
+        bs_store_pair(seg, (long long)f * Np + i, val, i < Np);
+    }
 }
 
 // The equation of motion of each point as a kernel of its own (used when the

@@ -244,8 +244,8 @@ struct VfmParams {
     Grid g;
     double kappa, alpha, alpha_p, ratio, rho0, core_a, dmin, dmax;
     double dt;
-    double kq;       // kappa / (4 pi)
-    double beta_c;   // ln(2 / (e^{1/4} a)), the constant part of the local coefficient
+    float kq_f;      // kappa / (4 pi)
+    float beta_c_f;  // ln(2 / (e^{1/4} a)), the constant part of the local coefficient
     float alpha_f, alpha_p_f;
     float gscale_f;  // -(rho_s/rho_n) rho0 kappa
     int couple, force_form;
