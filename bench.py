@@ -58,13 +58,14 @@ def launches_per_step(n_points: int) -> int:
     """Kernels of one coupled step (1 RK4 sub-step): lattice 3 (velocity-tile
     flags, stream-collide, plane reduction with the force-grid reset),
     filaments 4 x 3 (per RK stage geometry, Biot-Savart, equation of motion),
-    remesh 2, reconnection 4 = 21.  From 8192 points on, 4 more build the
-    spatial order of the Biot-Savart sources once per step; from 24576 points
-    on the Biot-Savart kernel applies the equation of motion itself (4 fewer;
-    or as VLB_FUSED_EOM forces)."""
+    remesh 2, reconnection 4, and the 2 that assign the Biot-Savart source
+    slots once per step = 23.  From 8192 points on, 4 more build the spatial
+    order of the sources first; from 24576 points on the Biot-Savart kernel
+    applies the equation of motion itself (4 fewer; or as VLB_FUSED_EOM
+    forces)."""
     mode = os.environ.get("VLB_FUSED_EOM")
     fused = n_points >= 24576 if mode is None else mode != "0"
-    return (17 if fused else 21) + (4 if n_points >= 8192 else 0)
+    return (19 if fused else 23) + (4 if n_points >= 8192 else 0)
 
 
 def launches(n_points: int, steps: int, overlap: bool = True) -> int:
@@ -309,8 +310,8 @@ def run_vlb(args, ws, rank, local):
     e2e_block_units, e2e_block_secs = aggregate(cells * args.steps, e2e_block_s, ws)
     h2d = (xyz.size * 8 + nxt.size * 4) / args.steps
     # per step call: the status block (12 doubles of statistics, the line
-    # length among them, and 12 int counters); at the end, the filaments
-    d2h = 12 * 8 + 12 * 4 + final.nbytes / args.steps
+    # length among them, and 13 int counters); at the end, the filaments
+    d2h = 12 * 8 + 13 * 4 + final.nbytes / args.steps
 
     pk, pk_kind = peaks()
     # stream-collide: algorithmic bytes / mean event-timed launch
@@ -331,6 +332,8 @@ def run_vlb(args, ws, rank, local):
     fp32_peak_med = n_sm * FP32_LANES_PER_SM * 2 * f_med * 1e6 / 1e12
     bs_traffic = profile_traffic("k_biot_savart", args.config, ["bs.cu", "eom.cuh", "vlb_internal.cuh"])
     bs_share = bs_ms / (nograph_s * 1e3) if nograph_s > 0 else None
+    k1_f32 = lbm_pass_roofline(p, "f32", max(10, args.steps), pk, pk_kind, stream) \
+        if args.storage != "f32" else None
     config = workload_config(args.config, p, nxt, args.storage, ws)
     line = {
         "metric": "coupled-step MLUPS",
@@ -380,7 +383,38 @@ def run_vlb(args, ws, rank, local):
                          "avg_launch_us": round(k1_avg_s * 1e6, 3), "launches": k1_n},
         "clocks": clk,
     }
+    if k1_f32:
+        line["roofline_lbm_f32"] = k1_f32
     return line, p, xyz, nxt
+
+
+def lbm_pass_roofline(p, storage, passes, pk, pk_kind, stream):
+    """The stream-collide kernel alone on the same grid with another
+    population storage: a channel without filaments (so no force or velocity
+    tiles flagged), three untimed lattice passes, then `passes` passes with
+    CUDA events on the channel's stream around each launch."""
+    from paper_2108_04435_gb300 import vlb
+    q = dict(p)
+    q["storage"] = STORAGE[storage]
+    ch = vlb.Channel(q, stream=stream)
+    for _ in range(3):
+        ch.run_phases(vlb.PHASE_LBM)
+    ch.set_timing(True)
+    for _ in range(passes):
+        ch.run_phases(vlb.PHASE_LBM)
+    ms, n = ch.kernel_timing(vlb.TIMED_LBM)
+    ch.close()
+    cells = q["n"][0] * q["n"][1] * q["n"][2]
+    bpc = BYTES_PER_CELL[storage]
+    avg_s = ms / 1e3 / max(n, 1)
+    achieved = bpc * cells / avg_s / 1e9 if n else None
+    return {"kernel": "k_lbm_step", "storage": storage, "bound": "hbm",
+            "achieved": round(achieved, 1) if achieved else None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
+            "peak_source": f"{pk_kind} hbm_gbs (copy bandwidth)", "traffic": None,
+            "algorithmic_bytes_per_launch": bpc * cells, "bytes_per_cell": bpc,
+            "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
+            "note": "lattice passes alone on the benchmark grid (no filaments), populations stored in FP32"}
 
 
 class OracleSampler:

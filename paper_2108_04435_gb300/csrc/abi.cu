@@ -254,17 +254,22 @@ BsOrder bs_order(vlb_channel* ch) {
     o.sorted = ch->n_hint >= BS_SORT_MIN ? 1 : 0;
     o.ord = ch->d.bs_ord;
     o.rank = ch->d.bs_rank;
+    o.slot = ch->d.bs_slot;
     o.org = ch->d.bs_org;
     return o;
 }
 
-// The spatial order of the current points (before the first stage geometry
-// of a step; the order then serves every RK stage of the step).
+// The spatial order (in point order below BS_SORT_MIN points) and the source
+// slots of the current points, before the first stage geometry of a step;
+// they then serve every RK stage of the step.
 void bs_sort(vlb_channel* ch, const BsOrder& o, cudaStream_t s) {
-    if (!o.sorted) return;
     Dev& d = ch->d;
-    launch_bs_sort(ch->vp.g, d.pos[ch->cur_p], ch->cap, point_span(ch->n_hint, ch->cap), d.counters, d.bs_key,
-                   d.bs_tmp, d.bs_ord, d.bs_rank, d.bs_org, d.bs_cnt, d.bs_start, s);
+    const int span = point_span(ch->n_hint, ch->cap);
+    if (o.sorted)
+        launch_bs_sort(ch->vp.g, d.pos[ch->cur_p], ch->cap, span, d.counters, d.bs_key, d.bs_tmp, d.bs_ord,
+                       d.bs_rank, d.bs_cnt, d.bs_start, s);
+    launch_bs_slots(d.pos[ch->cur_p], d.next[ch->cur_p], ch->cap, span, d.counters, o, d.bs_bsum, d.seg,
+                    ch->vp.nfaces, s);
 }
 
 void vfm_pre(vlb_channel* ch, cudaStream_t s) {
@@ -449,33 +454,36 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
     for (int a = 0; a < 3; ++a) g.wall[a] = p->wall[a];
     g.ncell = (long long)g.nx * g.ny * g.nz;
     g.tnx = g.tny = g.tnz = 1;
-    const size_t groups = (size_t)((n + BS_GROUP - 1) / BS_GROUP);
+    const size_t slots = (size_t)bs_slot_cap(n);
     char* base = (char*)scratch;
     auto take = [&](size_t bytes) {
         char* q = base;
         base += bs_up256(bytes);
         return (void*)q;
     };
-    int* counters = (int*)take(sizeof(int) * 16);
+    int* counters = (int*)take(sizeof(int) * CNT_COUNT);
     int* prev = (int*)take(sizeof(int) * (size_t)n);
-    float4* seg = (float4*)take(sizeof(float4) * BS_REC * groups * BS_GROUP);
+    float4* seg = (float4*)take(sizeof(float4) * BS_REC * slots);
     int* key = (int*)take(sizeof(int) * (size_t)n);
     int* tmp = (int*)take(sizeof(int) * (size_t)n);
     int* ord = (int*)take(sizeof(int) * (size_t)n);
     int* rank = (int*)take(sizeof(int) * (size_t)n);
-    int4* org = (int4*)take(sizeof(int4) * groups);
+    int* slot = (int*)take(sizeof(int) * (size_t)n);
+    int4* org = (int4*)take(sizeof(int4) * (slots / BS_GROUP));
     int* cnt = (int*)take(sizeof(int) * BS_SORT_MAX_BINS);
     int* start = (int*)take(sizeof(int) * BS_SORT_MAX_BINS);
+    int* bsum = (int*)take(sizeof(int) * BS_SLOT_BLOCKS);
     long long* vacc = (long long*)take(sizeof(long long) * 3 * (size_t)n);
     cudaStream_t s = (cudaStream_t)stream;
     BsOrder o;
     o.sorted = n >= BS_SORT_MIN ? 1 : 0;
     o.ord = ord;
     o.rank = rank;
+    o.slot = slot;
     o.org = org;
     if (o.sorted) cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)bs_bins(g.nx, g.ny, g.nz).K, s);
     cudaMemsetAsync(vacc, 0, sizeof(long long) * 3 * (size_t)n, s);
-    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, o, key, tmp, cnt, start, s);
+    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, o, key, tmp, cnt, start, bsum, s);
     launch_biot_savart(g, p->kappa, seg, prev, counters, nullptr, n, n, nullptr, vel, s, o, nullptr, 0, nullptr,
                        nullptr, vacc);
     launch_bs_unfix(vacc, n, vel, s);
@@ -506,12 +514,13 @@ size_t vlb_channel_bytes(const vlb_params* p) {
     size_t nfaces = 0;
     if (p->wall_images)
         for (int a = 0; a < 3; ++a) nfaces += p->wall[a] ? 2 : 0;
-    const size_t capg = (size_t)bs_block((int)cap, 1);
+    const size_t capg = (size_t)bs_slot_cap((long long)cap);
     b += 2 * (up(24 * cap) + 2 * up(4 * cap)) + 6 * up(24 * cap) + up(8 * cap) + up(32 * cap) +
          up(sizeof(float4) * BS_REC * capg * (1 + nfaces));
     b += up(12 * cap * (size_t)bs_max_splits((int)cap, sm_count())) + up(12 * cap) + up(24 * cap) +
          up(4 * ((cap + 127) / 128));
-    b += 4 * up(4 * cap) + up(16 * (capg / BS_GROUP)) + 2 * up(4 * (size_t)bs_bins(p->n[0], p->n[1], p->n[2]).K);
+    b += 5 * up(4 * cap) + up(16 * (capg / BS_GROUP)) + 2 * up(4 * (size_t)bs_bins(p->n[0], p->n[1], p->n[2]).K) +
+         up(4 * BS_SLOT_BLOCKS);
     b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(16 * cap) + up(8 * cap);
     const size_t nc = cap / 2 + 1;
     b += 4 * up(4 * nc) + up(8 * nc) + up(4 * cap) + up(8 * ((cap + 255) / 256));
@@ -646,7 +655,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     const int nsm = bs_max_splits(cap, sm_count());
     ch->nsplit_max = nsm;
     const BsBins bins = bs_bins(g.nx, g.ny, g.nz);
-    const size_t capg = (size_t)bs_block(cap, 1);  // capacity rounded up to whole record groups
+    const size_t capg = (size_t)bs_slot_cap(cap);  // source slots: a point and a gap slot each, whole groups
     const int ntiles = g.tnx * g.tny * g.tnz;
     Dev& d = ch->d;
     bool ok = true;
@@ -688,6 +697,8 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.bs_ord = (int*)A(sizeof(int) * (size_t)cap);
     d.bs_rank = (int*)A(sizeof(int) * (size_t)cap);
     d.bs_org = (int4*)A(sizeof(int4) * (capg / BS_GROUP));
+    d.bs_slot = (int*)A(sizeof(int) * (size_t)cap);
+    d.bs_bsum = (int*)A(sizeof(int) * BS_SLOT_BLOCKS);
     d.bs_cnt = (int*)A(sizeof(int) * (size_t)bins.K);
     d.bs_start = (int*)A(sizeof(int) * (size_t)bins.K);
     d.bsp = (float*)A(sizeof(float) * 3 * (size_t)cap * (size_t)nsm);

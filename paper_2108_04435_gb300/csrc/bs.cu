@@ -125,24 +125,26 @@ __device__ __forceinline__ float mi_axis(float r, float L, float iL) { return fm
 constexpr float BS_NEAR = 8.f;
 
 // One target of a Biot-Savart pass (registers of one thread): its own
-// record (origin O, parts h + l, so that the point is O + h + l) and the
-// record positions of the segments that belong to its local term.
+// slot (origin O, parts h + l, so that the point is O + h + l) and the
+// slots of the segments that belong to its local term.
 struct BsTarget {
     float h[3], l[3], O[3];
     float v[3];      // sum over the sources, without the factor kappa / 4 pi
-    int self, prev;  // record positions of its own segment and of its predecessor's
+    int self, prev;  // slots of its own segment and of its predecessor's
     int excl;        // a pinned end: the image of its own segment across its wall
     int i;           // point index, -1 for an idle lane
 };
 
-// Bounding box and origin of one group of records in shared memory.
+// Bounding box and origin of one group of slots in shared memory.
 struct BsGroup {
-    float lo[3], hi[3];  // of the records' h, relative to the origin
+    float lo[3], hi[3];  // of the slots' h, relative to the origin
     float O[3];          // integer origin (exact in float)
+    float sign;          // -1 for a wall-image block: the image vortex turns the other way
 };
 
-// Integer origin of the group of record position j, mirrored onto the image
-// side for an image block: x_a -> w2 - x_a on the face axis a.
+// Integer origin of the group of slot j, mirrored onto the image side for an
+// image block: x_a -> w2 - x_a on the face axis a.  Returns the block index
+// (0: the segments, 1 + face: their images); jump: the group's chain flag.
 struct BsImages {
     int nfaces;
     int face_code[6];
@@ -150,13 +152,15 @@ struct BsImages {
     const float4* geo;   // pinned-end wall codes (+1) in geo[2i + 1].w
 };
 
-__device__ __forceinline__ void group_origin(const BsOrder& o, const BsImages& im, long long Np, int j, float O[3]) {
+__device__ __forceinline__ int group_origin(const BsOrder& o, const BsImages& im, long long Np, int j, float O[3],
+                                           bool* jump = nullptr) {
     const int f = (int)(j / Np);
     const int kk = (int)(j - (long long)f * Np);
     const int4 g = o.org[kk / BS_GROUP];
     O[0] = (float)g.x;
     O[1] = (float)g.y;
     O[2] = (float)g.z;
+    if (jump) *jump = g.w != 0;
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         if (q + 1 != f) continue;
@@ -166,9 +170,11 @@ __device__ __forceinline__ void group_origin(const BsOrder& o, const BsImages& i
         else if (ax == 1) O[1] = w2 - O[1];
         else O[2] = w2 - O[2];
     }
+    return f;
 }
 
-// Target at sorted position k of N (none when k >= N).
+// Target at sorted position k of N (none when k >= N): the point of the
+// slot slot[k].
 __device__ __forceinline__ BsTarget bs_target(const float4* __restrict__ seg, const int* __restrict__ prev,
                                               const BsOrder& o, const BsImages& im, long long Np, int N, int k) {
     BsTarget t;
@@ -177,61 +183,122 @@ __device__ __forceinline__ BsTarget bs_target(const float4* __restrict__ seg, co
     t.self = t.prev = t.excl = -1;
     t.i = -1;
     if (k < N) {
+        const int sl = o.slot[k];
         const float* r = reinterpret_cast<const float*>(seg);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            t.h[a] = r[bs_value_index(k, a)];
-            t.l[a] = r[bs_value_index(k, 10 + a)];
+            t.h[a] = r[bs_value_index(sl, a)];
+            t.l[a] = r[bs_value_index(sl, 10 + a)];
         }
-        group_origin(o, im, Np, k, t.O);
+        group_origin(o, im, Np, sl, t.O);
         const int i = o.sorted ? o.ord[k] : k;
         t.i = i;
-        t.self = k;
+        t.self = sl;
         const int p = prev[i];
-        t.prev = p >= 0 ? (o.sorted ? o.rank[p] : p) : -1;
+        t.prev = p >= 0 ? o.slot[o.sorted ? o.rank[p] : p] : -1;
         if (im.nfaces > 0) {
             const int pin = (int)im.geo[2LL * i + 1].w - 1;
 #pragma unroll
             for (int f = 0; f < 6; ++f)
-                if (f < im.nfaces && im.face_code[f] == pin) t.excl = (int)((1 + f) * Np) + (p < 0 ? k : t.prev);
+                if (f < im.nfaces && im.face_code[f] == pin) t.excl = (int)((1 + f) * Np) + (p < 0 ? sl : t.prev);
         }
     }
     return t;
 }
 
-__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+// The cheap pair path, along the chain of slots of one group.  Slot k's
+// segment runs from its point to slot k + 1's, so with R = h + t at every
+// slot (no low parts), ia = 1/|R| and rho = |R| serve the segment starting
+// there and the one ending there.  For a segment from R1 to R2 = R1 + d,
+// S = |R1| + |R2| and |R1||R2| + R1.R2 = (S^2 - |d|^2)/2, so the segment
+// factor (|R1| + |R2|)/(|R1||R2| (|R1||R2| + R1.R2)) of Eq. 3 is
+// 2 (ia1 + ia2) / (S^2 - |d|^2): one reciprocal square root per slot and one
+// reciprocal per segment.  The cross product R1 x R2 = R1 x d = h x d + t x d
+// is split into the slot's c = h x d and t x (sum of fac d), added once per
+// group.  A pair p (slots p and p + 32) is evaluated packed (FP32x2), so the
+// group's two halves walk their chains side by side.
 
-// The cheap pair path for the two records of a pair at once (packed FP32x2:
-// one instruction does the arithmetic of both): R1 = h + t (no low parts),
-// no guard, no minimum image; the cross product R1 x d = h x d + t x d is
-// split into the record's c = h x d and t x (sum of fac d), added once per
-// group.  With ia = 1/|R1|, ib = 1/|R2| and P = ia ib, the segment factor
-// (|R1| + |R2|)/(|R1||R2| (|R1||R2| + R1.R2)) of Eq. 3 is
-// (ia + ib) P / (1 + P R1.R2), with R1.R2 = |R1|^2 + R1.d.  q0..q4 are the
-// first five float4 of the pair (values 0-9 of both records).
-__device__ __forceinline__ void pair2_far(const float4& q0, const float4& q1, const float4& q2, const float4& q3,
-                                          const float4& q4, const float2 (&t)[3], float2 (&av)[3],
-                                          float2 (&aw)[3]) {
-    const float2 hx = make_float2(q0.x, q0.y), hy = make_float2(q0.z, q0.w), hz = make_float2(q1.x, q1.y);
-    const float2 dd = make_float2(q1.z, q1.w), dx = make_float2(q2.x, q2.y), dy = make_float2(q2.z, q2.w);
-    const float2 dz = make_float2(q3.x, q3.y), cx = make_float2(q3.z, q3.w), cy = make_float2(q4.x, q4.y);
-    const float2 cz = make_float2(q4.z, q4.w);
-    const float2 rx = __fadd2_rn(hx, t[0]), ry = __fadd2_rn(hy, t[1]), rz = __fadd2_rn(hz, t[2]);
-    const float2 a2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
-    const float2 rd = __ffma2_rn(rz, dz, __ffma2_rn(ry, dy, __fmul2_rn(rx, dx)));
-    const float2 b2 = __fadd2_rn(__ffma2_rn(f2(2.f), rd, a2), dd);
-    const float2 ia = make_float2(rsqrt_approx(a2.x), rsqrt_approx(a2.y));
-    const float2 ib = make_float2(rsqrt_approx(b2.x), rsqrt_approx(b2.y));
-    const float2 P = __fmul2_rn(ia, ib);
-    const float2 den = __ffma2_rn(P, __fadd2_rn(a2, rd), f2(1.f));
-    const float2 rc = make_float2(rcp_approx(den.x), rcp_approx(den.y));
-    const float2 fac = __fmul2_rn(__fmul2_rn(__fadd2_rn(ia, ib), P), rc);
-    av[0] = __ffma2_rn(fac, cx, av[0]);
-    av[1] = __ffma2_rn(fac, cy, av[1]);
-    av[2] = __ffma2_rn(fac, cz, av[2]);
-    aw[0] = __ffma2_rn(fac, dx, aw[0]);
-    aw[1] = __ffma2_rn(fac, dy, aw[1]);
-    aw[2] = __ffma2_rn(fac, dz, aw[2]);
+// ia and rho at the two slots of pair p, for each target offset t (R = h + t
+// by scalar adds: a packed add would need t twice, in registers the pair
+// loop cannot spare; the adds take the same FMA-pipe time either way).
+template <int TGT>
+__device__ __forceinline__ void chain_head(const float4* __restrict__ Q, const float (&t)[TGT][3],
+                                           float2 (&ia)[TGT], float2 (&rho)[TGT]) {
+    const float4 q0 = Q[0], q1 = Q[1];
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        const float2 rx = make_float2(q0.x + t[u][0], q0.y + t[u][0]);
+        const float2 ry = make_float2(q0.z + t[u][1], q0.w + t[u][1]);
+        const float2 rz = make_float2(q1.x + t[u][2], q1.y + t[u][2]);
+        const float2 a2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+        ia[u] = make_float2(rsqrt_approx(a2.x), rsqrt_approx(a2.y));
+        rho[u] = __fmul2_rn(a2, ia[u]);
+    }
+}
+
+// The segments of the slots of pair p, from (ia0, rho0) at their starts to
+// (ia1, rho1) at their ends, into the sums of fac c and fac d (fac halved).
+template <int TGT>
+__device__ __forceinline__ void chain_segments(const float4* __restrict__ Q, const float2 (&ia0)[TGT],
+                                               const float2 (&rho0)[TGT], const float2 (&ia1)[TGT],
+                                               const float2 (&rho1)[TGT], float2 (&av)[TGT][3],
+                                               float2 (&aw)[TGT][3]) {
+    const float4 q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
+    const float2 mdd = make_float2(-q1.z, -q1.w);
+    const float2 dx = make_float2(q2.x, q2.y), dy = make_float2(q2.z, q2.w), dz = make_float2(q3.x, q3.y);
+    const float2 cx = make_float2(q3.z, q3.w), cy = make_float2(q4.x, q4.y), cz = make_float2(q4.z, q4.w);
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        const float2 S = __fadd2_rn(rho0[u], rho1[u]);
+        const float2 den = __ffma2_rn(S, S, mdd);
+        const float2 fac = __fmul2_rn(__fadd2_rn(ia0[u], ia1[u]), make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+        av[u][0] = __ffma2_rn(fac, cx, av[u][0]);
+        av[u][1] = __ffma2_rn(fac, cy, av[u][1]);
+        av[u][2] = __ffma2_rn(fac, cz, av[u][2]);
+        aw[u][0] = __ffma2_rn(fac, dx, aw[u][0]);
+        aw[u][1] = __ffma2_rn(fac, dy, aw[u][1]);
+        aw[u][2] = __ffma2_rn(fac, dz, aw[u][2]);
+    }
+}
+
+// The chain of one group for TGT targets at offsets t: pair p's segments end at pair p + 1's slots, except slot 31's,
+// which ends at slot 32 (the first pair's other half), and slot 63's, which
+// ends at the end point its record stores (the next slot is in another
+// group).  Returns the sums of fac c and fac d with fac halved.
+template <int TGT>
+__device__ __forceinline__ void chain_group(const float4* __restrict__ T, const float (&t)[TGT][3],
+                                            float2 (&av)[TGT][3], float2 (&aw)[TGT][3]) {
+    float2 ia0[TGT], rho0[TGT];
+    chain_head<TGT>(T, t, ia0, rho0);
+    float ia32[TGT], rho32[TGT];
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        ia32[u] = ia0[u].y;
+        rho32[u] = rho0[u].y;
+    }
+#pragma unroll 2
+    for (int p = 0; p < BS_GROUP / 2 - 1; ++p) {
+        float2 ia1[TGT], rho1[TGT];
+        chain_head<TGT>(T + 8 * (p + 1), t, ia1, rho1);
+        chain_segments<TGT>(T + 8 * p, ia0, rho0, ia1, rho1, av, aw);
+#pragma unroll
+        for (int u = 0; u < TGT; ++u) {
+            ia0[u] = ia1[u];
+            rho0[u] = rho1[u];
+        }
+    }
+    const float4* Q = T + 8 * (BS_GROUP / 2 - 1);
+    const float4 q6 = Q[6], q7 = Q[7];  // values 13-15: the stored end point (slot 63 in the .y halves)
+    float2 ia1[TGT], rho1[TGT];
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        const float ex = q6.w + t[u][0], ey = q7.y + t[u][1], ez = q7.w + t[u][2];
+        const float b2 = ex * ex + ey * ey + ez * ez;
+        const float ib = rsqrt_approx(b2);
+        ia1[u] = make_float2(ia32[u], ib);
+        rho1[u] = make_float2(rho32[u], b2 * ib);
+    }
+    chain_segments<TGT>(Q, ia0, rho0, ia1, rho1, av, aw);
 }
 
 // Minimum image of one component of R1 on a periodic axis (L = 0 on wall
@@ -259,19 +326,29 @@ __device__ __forceinline__ float mi_exact(float r, float h, float th, float l, f
 // Pair paths with R1 in full precision: R1 = (h + t_hi) + (l + t_lo), the
 // minimum image on periodic axes.  GUARD (near groups): the on-segment guard
 // and the target's own segments (left to the local term) masked out by
-// record position j.  Without GUARD (groups some target sees across half a
+// slot number j.  Without GUARD (groups some target sees across half a
 // periodic box, none near): neither can occur.
 template <bool PERIODIC, bool GUARD>
 __device__ __forceinline__ void pair_precise(float hx, float hy, float hz, float dd, float dx, float dy, float dz,
                                              float lx, float ly, float lz, int j, const float th[3],
-                                             const float tl[3], const BsTarget& t, float v[3], const BoxF& box) {
+                                             const float tl[3], const BsTarget& t, float v[3], const BoxF& box,
+                                             float sign) {
     float r1x = (hx + th[0]) + (lx + tl[0]);
     float r1y = (hy + th[1]) + (ly + tl[1]);
     float r1z = (hz + th[2]) + (lz + tl[2]);
     if (PERIODIC) {
-        r1x = mi_exact(r1x, hx, th[0], lx, tl[0], box.Lx, box.iLx);
-        r1y = mi_exact(r1y, hy, th[1], ly, tl[1], box.Ly, box.iLy);
-        r1z = mi_exact(r1z, hz, th[2], lz, tl[2], box.Lz, box.iLz);
+        if (sign > 0.f) {
+            r1x = mi_exact(r1x, hx, th[0], lx, tl[0], box.Lx, box.iLx);
+            r1y = mi_exact(r1y, hy, th[1], ly, tl[1], box.Ly, box.iLy);
+            r1z = mi_exact(r1z, hz, th[2], lz, tl[2], box.Lz, box.iLz);
+        } else {
+            // a wall image runs from M(s_q) to M(s_i) (its slot stores it the
+            // other way round): its periodic image is that of M(s_q), the
+            // slot's end point (decided in FP32)
+            r1x = fmaf(-box.Lx, round_mul_fma(r1x + dx, box.iLx), r1x);
+            r1y = fmaf(-box.Ly, round_mul_fma(r1y + dy, box.iLy), r1y);
+            r1z = fmaf(-box.Lz, round_mul_fma(r1z + dz, box.iLz), r1z);
+        }
     }
     const float a2 = r1x * r1x + r1y * r1y + r1z * r1z;
     const float rd = r1x * dx + r1y * dy + r1z * dz;
@@ -279,12 +356,17 @@ __device__ __forceinline__ void pair_precise(float hx, float hy, float hz, float
     const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
     const float P = ia * ib;
     const float den = fmaf(P, a2 + rd, 1.f);
-    const float fac = (ia + ib) * P * rcp_approx(den);
+    const float fac = (ia + ib) * P * rcp_approx(den) * sign;
     float c = fac;
     if (GUARD) {
         // den <= 1e-6: the target lies on the segment (or coincides with an
-        // end point), where the integral is not defined; NaN and infinity fail too
-        const bool use = (den > 1e-6f) & (den < 3.0e38f) & (j != t.self) & (j != t.prev) & (j != t.excl);
+        // end point), where the integral is not defined; NaN and infinity
+        // fail too.  Slots without a segment (gap and padding slots, a
+        // line's last point) are skipped: a gap slot may hold the target's
+        // own point, ~1e-14 away in another group's origin, where fac
+        // overflows and fac * 0 would be NaN.
+        const bool use = (dd > 0.f) & (den > 1e-6f) & (den < 3.0e38f) & (j != t.self) & (j != t.prev) &
+                         (j != t.excl);
         c = use ? fac : 0.f;
     }
     v[0] = fmaf(c, r1y * dz - r1z * dy, v[0]);
@@ -292,17 +374,21 @@ __device__ __forceinline__ void pair_precise(float hx, float hy, float hz, float
     v[2] = fmaf(c, r1x * dy - r1y * dx, v[2]);
 }
 
-// Both records of a pair on the precise path (q0..q6: values 0-13 of both).
+// Both slots of a pair on the precise path (q0..q6: values 0-13 of both);
+// j is the first slot, j + 32 the second, Np the slots of a block (the
+// image blocks, j >= Np, turn the other way).
 template <bool PERIODIC, bool GUARD, int TGT>
 __device__ __forceinline__ void pair2_precise(const float4* __restrict__ Q, int j, const float (&th)[TGT][3],
-                                              const float (&tl)[TGT][3], BsTarget (&t)[TGT], const BoxF& box) {
+                                              const float (&tl)[TGT][3], BsTarget (&t)[TGT], const BoxF& box,
+                                              int Np) {
     const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q5 = Q[5], q6 = Q[6];
+    const float sign = j >= Np ? -1.f : 1.f;
 #pragma unroll
     for (int u = 0; u < TGT; ++u) {
         pair_precise<PERIODIC, GUARD>(q0.x, q0.z, q1.x, q1.z, q2.x, q2.z, q3.x, q5.x, q5.z, q6.x, j, th[u], tl[u], t[u],
-                                      t[u].v, box);
-        pair_precise<PERIODIC, GUARD>(q0.y, q0.w, q1.y, q1.w, q2.y, q2.w, q3.y, q5.y, q5.w, q6.y, j + 1, th[u], tl[u],
-                                      t[u], t[u].v, box);
+                                      t[u].v, box, sign);
+        pair_precise<PERIODIC, GUARD>(q0.y, q0.w, q1.y, q1.w, q2.y, q2.w, q3.y, q5.y, q5.w, q6.y, j + BS_GROUP / 2,
+                                      th[u], tl[u], t[u], t[u].v, box, sign);
     }
 }
 
@@ -329,7 +415,7 @@ __device__ __forceinline__ void group_offset(const BsGroup& G, const BsTarget& t
             // the box's neighbouring images may come closer (L = 0 on wall axes: the same box)
             da = fminf(da, fmaxf(fmaxf(lo - L[a], L[a] - hi), 0.f));
             da = fminf(da, fmaxf(fmaxf(lo + L[a], -(hi + L[a])), 0.f));
-            wrap |= (hi > 0.5f * L[a] - 0.01f) | (lo < 0.01f - 0.5f * L[a]);
+            wrap |= (L[a] > 0.f) & ((hi > 0.5f * L[a] - 0.01f) | (lo < 0.01f - 0.5f * L[a]));
         }
         dist = fmaxf(dist, da);
     }
@@ -380,19 +466,19 @@ __device__ __forceinline__ void bs_fill(const BsSmem& sm, const float4* seg, uin
     issue_tile(sm.tile[b], seg, jb, min(BS_TILE, j1 - jb), &sm.full[b]);
 }
 
-// Box and origin of one group of records (computed by every warp for
-// itself): lane l takes pair l (gcnt is even and at most 64).
-__device__ __forceinline__ BsGroup group_box(const float4* __restrict__ T, int gcnt, int j, const BsOrder& o,
+// Box, origin and sign of one group of slots (computed by every warp for
+// itself): lane l takes pair l.  A group whose chain jumps by a periodic box
+// gets an unbounded box, which sends it to the full-precision path (as a
+// near group).
+__device__ __forceinline__ BsGroup group_box(const float4* __restrict__ T, int j, const BsOrder& o,
                                              const BsImages& im, long long Np) {
     const int lane = threadIdx.x & 31;
     BsGroup G;
-    float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-    if (2 * lane < gcnt) {
-        const float4 q0 = T[8 * lane], q1 = T[8 * lane + 1];
-        lo[0] = fminf(q0.x, q0.y); hi[0] = fmaxf(q0.x, q0.y);
-        lo[1] = fminf(q0.z, q0.w); hi[1] = fmaxf(q0.z, q0.w);
-        lo[2] = fminf(q1.x, q1.y); hi[2] = fmaxf(q1.x, q1.y);
-    }
+    float lo[3], hi[3];
+    const float4 q0 = T[8 * lane], q1 = T[8 * lane + 1];
+    lo[0] = fminf(q0.x, q0.y); hi[0] = fmaxf(q0.x, q0.y);
+    lo[1] = fminf(q0.z, q0.w); hi[1] = fmaxf(q0.z, q0.w);
+    lo[2] = fminf(q1.x, q1.y); hi[2] = fmaxf(q1.x, q1.y);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -405,24 +491,32 @@ __device__ __forceinline__ BsGroup group_box(const float4* __restrict__ T, int g
         G.lo[a] = lo[a];
         G.hi[a] = hi[a];
     }
-    group_origin(o, im, Np, j, G.O);
+    bool jump;
+    G.sign = group_origin(o, im, Np, j, G.O, &jump) > 0 ? -1.f : 1.f;
+    if (jump) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            G.lo[a] = -3.0e38f;
+            G.hi[a] = 3.0e38f;
+        }
+    }
     return G;
 }
 
-// The sums of one group of records for TGT targets per thread, on the path
-// the warp's targets need.
+// The sums of one group of slots (slot numbers gbase ..) for TGT targets per
+// thread, on the path the warp's targets need.
 template <bool PERIODIC, int TGT>
-__device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gcnt, int gbase, const BsGroup& G,
-                                         BsTarget (&t)[TGT], const BoxF& box) {
+__device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase, const BsGroup& G,
+                                         BsTarget (&t)[TGT], const BoxF& box, int Np) {
     float D[TGT][3], th[TGT][3];
     bool nearL = false, wrapL = false;
 #pragma unroll
     for (int u = 0; u < TGT; ++u) {
         bool nu, wu;
         group_offset<PERIODIC>(G, t[u], box, D[u], th[u], nu, wu);
-        const bool own = (unsigned)(t[u].self - gbase) < (unsigned)gcnt ||
-                         (unsigned)(t[u].prev - gbase) < (unsigned)gcnt ||
-                         (unsigned)(t[u].excl - gbase) < (unsigned)gcnt;
+        const bool own = (unsigned)(t[u].self - gbase) < (unsigned)BS_GROUP ||
+                         (unsigned)(t[u].prev - gbase) < (unsigned)BS_GROUP ||
+                         (unsigned)(t[u].excl - gbase) < (unsigned)BS_GROUP;
         if (t[u].i >= 0) {
             nearL |= nu | own;
             wrapL |= wu;
@@ -444,33 +538,28 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gcnt,
         // kernel is latency-bound, and the pairs are independent chains
         if (nearW) {
 #pragma unroll(TGT == 1 ? 2 : 1)
-            for (int p = 0; 2 * p < gcnt; ++p) pair2_precise<PERIODIC, true, TGT>(T + 8 * p, gbase + 2 * p, th, tl, t, box);
+            for (int p = 0; p < BS_GROUP / 2; ++p)
+                pair2_precise<PERIODIC, true, TGT>(T + 8 * p, gbase + p, th, tl, t, box, Np);
         } else {
 #pragma unroll(TGT == 1 ? 2 : 1)
-            for (int p = 0; 2 * p < gcnt; ++p) pair2_precise<PERIODIC, false, TGT>(T + 8 * p, gbase + 2 * p, th, tl, t, box);
+            for (int p = 0; p < BS_GROUP / 2; ++p)
+                pair2_precise<PERIODIC, false, TGT>(T + 8 * p, gbase + p, th, tl, t, box, Np);
         }
     } else {
-        float2 t2[TGT][3], av[TGT][3], aw[TGT][3];
+        float2 av[TGT][3], aw[TGT][3];
 #pragma unroll
         for (int u = 0; u < TGT; ++u)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                t2[u][a] = f2(th[u][a]);
-                av[u][a] = aw[u][a] = make_float2(0.f, 0.f);
-            }
-#pragma unroll 2
-        for (int p = 0; 2 * p < gcnt; ++p) {
-            const float4* Q = T + 8 * p;
-            const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
-#pragma unroll
-            for (int u = 0; u < TGT; ++u) pair2_far(q0, q1, q2, q3, q4, t2[u], av[u], aw[u]);
-        }
+            for (int a = 0; a < 3; ++a) av[u][a] = aw[u][a] = make_float2(0.f, 0.f);
+        chain_group<TGT>(T, th, av, aw);
+        // the factor 2 of the halved segment factor, and the block's sign
+        const float sc = 2.f * G.sign;
 #pragma unroll
         for (int u = 0; u < TGT; ++u) {
             const float wx = aw[u][0].x + aw[u][0].y, wy = aw[u][1].x + aw[u][1].y, wz = aw[u][2].x + aw[u][2].y;
-            t[u].v[0] += (av[u][0].x + av[u][0].y) + (th[u][1] * wz - th[u][2] * wy);
-            t[u].v[1] += (av[u][1].x + av[u][1].y) + (th[u][2] * wx - th[u][0] * wz);
-            t[u].v[2] += (av[u][2].x + av[u][2].y) + (th[u][0] * wy - th[u][1] * wx);
+            t[u].v[0] = fmaf(sc, (av[u][0].x + av[u][0].y) + (th[u][1] * wz - th[u][2] * wy), t[u].v[0]);
+            t[u].v[1] = fmaf(sc, (av[u][1].x + av[u][1].y) + (th[u][2] * wx - th[u][0] * wz), t[u].v[1]);
+            t[u].v[2] = fmaf(sc, (av[u][2].x + av[u][2].y) + (th[u][0] * wy - th[u][1] * wx), t[u].v[2]);
         }
     }
 }
@@ -483,7 +572,7 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gcnt,
 // hence deterministic) into vel; with one split the item writes vel directly.
 // `q` counts the tiles the block has consumed across items (stage q %
 // stages, fill phase (q / stages) & 1).  A thread's TGT targets are
-// consecutive record positions, so that a warp's targets are as compact as
+// consecutive sorted positions, so that a warp's targets are as compact as
 // the order makes them.  Returns false after a timed-out tile copy (status
 // TIMEOUT set).
 template <bool PERIODIC, int TGT, bool EOM, bool ACC>
@@ -503,7 +592,7 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
     const int ns = bs_splits(N, TT, nsm);
     const int ntb = (N + TT - 1) / TT;
     const int nitems = ntb * ns;
-    const long long Np = bs_block(N, im.nfaces);
+    const long long Np = bs_block(counters[CNT_NSLOT]);
     const int nsrc = (int)(Np * (1 + im.nfaces));  // segments, then their wall images
     // splits start on group boundaries, so that every tile starts on one
     const int chunk = ((nsrc + ns - 1) / ns + BS_GROUP - 1) / BS_GROUP * BS_GROUP;
@@ -536,9 +625,8 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
             const float4* T = sm.tile[b];
 #pragma unroll 1
             for (int gi = 0; gi * BS_GROUP < cnt; ++gi) {
-                const int gcnt = min(BS_GROUP, cnt - gi * BS_GROUP);
-                const BsGroup G = group_box(T + BS_REC * BS_GROUP * gi, gcnt, jb + gi * BS_GROUP, o, im, Np);
-                bs_group<PERIODIC, TGT>(T + BS_REC * BS_GROUP * gi, gcnt, jb + gi * BS_GROUP, G, t, box);
+                const BsGroup G = group_box(T + BS_REC * BS_GROUP * gi, jb + gi * BS_GROUP, o, im, Np);
+                bs_group<PERIODIC, TGT>(T + BS_REC * BS_GROUP * gi, jb + gi * BS_GROUP, G, t, box, (int)Np);
             }
             // release the stage; the last warp out refills it with the tile NST on
             __syncwarp();
@@ -578,12 +666,12 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
                 }
             }
         } else {
-            // partial sums by record position, summed in split order by the
+            // partial sums by sorted position, summed in split order by the
             // last split of the target tile
 #pragma unroll
             for (int v = 0; v < TGT; ++v) {
-                const int k = t[v].self;
-                if (k >= 0) {
+                const int k = tb * TT + threadIdx.x * TGT + v;
+                if (t[v].i >= 0) {
                     part[((long long)split * 3 + 0) * cap + k] = t[v].v[0];
                     part[((long long)split * 3 + 1) * cap + k] = t[v].v[1];
                     part[((long long)split * 3 + 2) * cap + k] = t[v].v[2];
@@ -597,9 +685,9 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
                 __threadfence();
 #pragma unroll
                 for (int v = 0; v < TGT; ++v) {
-                    const int k = t[v].self, i = t[v].i;
+                    const int k = tb * TT + threadIdx.x * TGT + v, i = t[v].i;
                     float a[3] = {0.f, 0.f, 0.f};
-                    if (k >= 0) {
+                    if (i >= 0) {
                         for (int m = 0; m < ns; ++m)
 #pragma unroll
                             for (int c = 0; c < 3; ++c) a[c] += __ldcg(&part[((long long)m * 3 + c) * cap + k]);
@@ -627,7 +715,7 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
 // Resident blocks: the pair loop is issue-bound and needs the warps; more
 // targets per thread need more registers.
 template <bool PERIODIC, int TGT, bool EOM, bool ACC>
-__global__ void __launch_bounds__(BS_TPB, TGT == 1 ? (ACC ? 7 : 8) : 5)
+__global__ void __launch_bounds__(BS_TPB, TGT == 1 ? ((ACC || !EOM || PERIODIC) ? 7 : 8) : 5)
     k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev, int* __restrict__ counters,
                   int* __restrict__ tile_ticket, int cap, BoxF box, float kq, float* __restrict__ part,
                   float* __restrict__ vel, EomArgs ea, BsImages im, BsOrder o, int nsm,
@@ -651,39 +739,40 @@ __global__ void __launch_bounds__(BS_TPB, TGT == 1 ? (ACC ? 7 : 8) : 5)
     }
 }
 
-// Stand-alone entry: prev[] and the source records of a caller's point set.
-__global__ void __launch_bounds__(BS_GROUP) k_bs_prep(Grid g, const double* __restrict__ pos,
-                                                      const int* __restrict__ next, int n, int* __restrict__ prev,
-                                                      float4* __restrict__ seg, int* __restrict__ counters,
-                                                      BsOrder o) {
+// Stand-alone entry: a caller's successor index outside [-1, n) means no
+// segment (and sets the TOPOLOGY status).
+__device__ __forceinline__ int bs_checked_next(const int* __restrict__ next, int n, int i) {
+    const int q = next[i];
+    return (q < -1 || q >= n) ? -1 : q;
+}
+
+// Stand-alone entry: prev[] of a caller's point set.
+__global__ void k_bs_prev(const int* __restrict__ next, int n, int* __restrict__ prev, int* __restrict__ counters) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bs_pad_records(n, 0, i, seg);
     if (i >= n) return;
-    int q = next[i];
-    if (q < -1 || q >= n) {  // not a point index: no segment
-        atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
-        q = -1;
-    }
+    const int q = bs_checked_next(next, n, i);
+    if (q != next[i]) atomicOr(&counters[CNT_STATUS], ST_TOPOLOGY);
     if (q >= 0) prev[q] = i;
-    const int nn[3] = {g.nx, g.ny, g.nz};
-    double O[3], rel[3];
-    const long long k = bs_position(o, pos, n, i, O);
-    float d[3];
+}
+
+// Stand-alone entry: the source slots of a caller's point set (positions
+// [3][n]), one thread per point.
+__global__ void __launch_bounds__(BS_GROUP) k_bs_points(Grid g, const double* __restrict__ pos,
+                                                        const int* __restrict__ next, int n,
+                                                        const int* __restrict__ counters, float4* __restrict__ seg,
+                                                        BsOrder o) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int q = bs_checked_next(next, n, i);
+    double si[3], sq[3];
+    float b[3];
     for (int a = 0; a < 3; ++a) {
-        const double si = pos[(long long)a * n + i];
-        double dd = q >= 0 ? pos[(long long)a * n + q] - si : 0.0;
-        double r = si - O[a];
-        if (!g.wall[a]) {
-            const double L = (double)nn[a];
-            if (dd > 0.5 * L) dd -= L;
-            else if (dd < -0.5 * L) dd += L;
-            if (r > 0.5 * L) r -= L;
-            else if (r < -0.5 * L) r += L;
-        }
-        rel[a] = r;
-        d[a] = __double2float_rn(dd);
+        si[a] = pos[(long long)a * n + i];
+        sq[a] = q >= 0 ? pos[(long long)a * n + q] : si[a];
+        b[a] = q >= 0 ? __double2float_rn(min_image(g, a, sq[a] - si[a])) : 0.f;
     }
-    bs_write_record(seg, k, rel, d);
+    const BsPointSlots ps = bs_point_slots(o, o.sorted ? o.rank[i] : i, q);
+    bs_write_point_slots(g, o, ps, bs_block(counters[CNT_NSLOT]), 0, 0, si, sq, b, q >= 0, seg);
 }
 
 __global__ void k_bs_counters(int* __restrict__ counters, int n) {
@@ -774,21 +863,6 @@ void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int*
     launch_pdl(kern, grid, BS_TPB, 0, s, seg, prev, cnt, tile_ticket, cap, box, kq, part, vel, ea, im, o, nsm, vacc);
 }
 
-// Targets per thread from 8192 points on: 2 in a box with walls on every
-// axis (each shared-memory pair is then read once for both: 6.49 against
-// 6.69 ms per launch at 86k points in the 128x128x1024 channel), 1 with a
-// periodic axis (a warp's 32 targets then meet fewer groups across half the
-// box: 594 against 673 us at 18.5k points in the 128^3 box).
-// VLB_BS_TARGETS=1 or 2 overrides.  Below 8192 points: 1.
-int bs_targets(const Grid& g) {
-    static const int forced = [] {
-        const char* e = getenv("VLB_BS_TARGETS");
-        return e ? (e[0] == '2' ? 2 : (e[0] == '1' ? 1 : 0)) : 0;
-    }();
-    if (forced) return forced;
-    return (g.wall[0] && g.wall[1] && g.wall[2]) ? 2 : 1;
-}
-
 void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const int* prev, const int* counters,
                         int* tile_ticket, int cap, int n_hint, float* part, float* vel, cudaStream_t s,
                         const BsOrder& o, const EomArgs* eom, int nfaces, const int* face_code, const float4* geo,
@@ -808,33 +882,30 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
         im.w2[f] = (face_code[f] & 1) ? 2.f * (float)nn[ax] - 1.f : -1.f;
     }
     im.geo = geo;
+    // one target per thread: the chained pair loop has enough independent
+    // work per target, and two targets per thread need more registers than
+    // leave six blocks on an SM
     // without a partial-sum buffer the split sums always go to vacc
-    const int tgt = n >= 8192 ? bs_targets(g) : 1;
     if (vacc && !eom && (bs_uses_vacc(n) || !part)) {
-        if (tgt == 2) bs_launch<2, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
-        else bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
+        bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
         return;
     }
-    if (tgt == 2) {
-        if (eom) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
-        else bs_launch<2, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
-    } else {
-        if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
-        else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
-    }
+    if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
+    else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
 }
 
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
-                               int* counters, const BsOrder& o, int* key, int* tmp, int* cnt, int* start,
+                               int* counters, const BsOrder& o, int* key, int* tmp, int* cnt, int* start, int* bsum,
                                cudaStream_t s) {
     k_bs_counters<<<1, 1, 0, s>>>(counters, n);
     cudaMemsetAsync(prev, 0xff, sizeof(int) * (size_t)n, s);  // first points of open lines keep -1
-    if (o.sorted) {
-        // the caller's positions are SoA [3][n]
-        launch_bs_sort(g, pos, n, n, counters, key, tmp, const_cast<int*>(o.ord), const_cast<int*>(o.rank), o.org,
-                       cnt, start, s);
-    }
-    k_bs_prep<<<(n + BS_GROUP - 1) / BS_GROUP, BS_GROUP, 0, s>>>(g, pos, next, n, prev, seg, counters, o);
+    k_bs_prev<<<(n + 255) / 256, 256, 0, s>>>(next, n, prev, counters);
+    // the caller's positions are SoA [3][n]
+    if (o.sorted)
+        launch_bs_sort(g, pos, n, n, counters, key, tmp, const_cast<int*>(o.ord), const_cast<int*>(o.rank), cnt,
+                       start, s);
+    launch_bs_slots(pos, next, n, n, counters, o, bsum, seg, 0, s);
+    k_bs_points<<<(n + BS_GROUP - 1) / BS_GROUP, BS_GROUP, 0, s>>>(g, pos, next, n, counters, seg, o);
 }
 
 void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s) {
@@ -854,7 +925,7 @@ void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s) {
 namespace {
 
 constexpr int NOALLOC_MAX_POINTS = 65536;
-constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(8) << 20;
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(12) << 20;
 // the scratch of the stand-alone entry grows linearly with the point count,
 // so the array holds every call up to the point limit
 static_assert(vlb::bs_scratch_bytes(NOALLOC_MAX_POINTS) <= NOALLOC_SCRATCH_BYTES,

@@ -1,9 +1,15 @@
 // Spatial order of the Biot-Savart sources (the points of the current step):
-// a Morton key per point from its bin of 8 cells (wider on lattices of more
+// a Morton key per point from its bin of 16 cells (wider on lattices of more
 // than 65536 bins), a counting sort over the bins, and inside each bin the
 // points in ascending index, so that the order depends on nothing but the
-// positions.  Group g of BS_GROUP consecutive sorted points gets the integer
-// origin of its first point.  Built once per step from BS_SORT_MIN points on.
+// positions (and a line's points, numbered along it, mostly stay
+// consecutive).  Built once per step from BS_SORT_MIN points on.
+//
+// Then, in any order, the source slots: every sorted position k takes slot
+// k + (gap slots before it), a gap slot following k when the successor of
+// its point is not the point at k + 1; a two-kernel scan (gap counts per
+// block, then each block's prefix from the counts before it).  Group g of
+// BS_GROUP slots gets the integer origin of its first slot's point.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -105,11 +111,9 @@ __global__ void k_sort_scatter(const int* __restrict__ counters, const int* __re
 }
 
 // One warp per bin: the bin's points in ascending index (so the order is
-// deterministic), their ranks, the origin of every group that starts in the
-// bin, and the bin count cleared for the next sort.
-__global__ void k_sort_bins(int K, const double* __restrict__ pos, int cap, int* __restrict__ cnt,
-                            const int* __restrict__ start, const int* __restrict__ tmp, int* __restrict__ ord,
-                            int* __restrict__ rank, int4* __restrict__ org) {
+// deterministic), their ranks, and the bin count cleared for the next sort.
+__global__ void k_sort_bins(int K, int* __restrict__ cnt, const int* __restrict__ start, const int* __restrict__ tmp,
+                            int* __restrict__ ord, int* __restrict__ rank) {
     pdl_wait_trigger();
     const int lane = threadIdx.x & 31;
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -129,26 +133,138 @@ __global__ void k_sort_bins(int K, const double* __restrict__ pos, int cap, int*
             const int p = s0 + r;
             ord[p] = my;
             rank[my] = p;
-            if (p % BS_GROUP == 0)
-                org[p / BS_GROUP] = make_int4((int)floor(pos[my]), (int)floor(pos[(long long)cap + my]),
-                                              (int)floor(pos[2LL * cap + my]), 0);
         }
     }
     __syncwarp();
     if (lane == 0) cnt[k] = 0;
 }
 
+__device__ __forceinline__ int bs_point_at(const BsOrder& o, int k) { return o.sorted ? o.ord[k] : k; }
+
+// 1 when sorted position k needs a gap slot after its own: its point has a
+// successor (an index outside [0, N) counts as none) that is not the point
+// at k + 1.
+__device__ __forceinline__ int bs_gap_after(const BsOrder& o, const int* __restrict__ next, int N, int k) {
+    const int q = next[bs_point_at(o, k)];
+    if (q < 0 || q >= N) return 0;
+    return (k + 1 >= N || bs_point_at(o, k + 1) != q) ? 1 : 0;
+}
+
+// Sum of v over the block (1024 threads); every thread gets it.
+__device__ __forceinline__ int block_sum_1024(int v, int* warp_sum) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) warp_sum[w] = v;
+    __syncthreads();
+    int t = warp_sum[lane];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    __syncthreads();  // warp_sum may be rewritten next
+    return t;
+}
+
+// The contiguous range of sorted positions of this block.
+__device__ __forceinline__ void slot_range(int N, int& k0, int& k1) {
+    const int ch = (N + (int)gridDim.x - 1) / (int)gridDim.x;
+    k0 = min(N, (int)blockIdx.x * ch);
+    k1 = min(N, k0 + ch);
+}
+
+__global__ void __launch_bounds__(1024) k_slot_count(const int* __restrict__ next, const int* __restrict__ counters,
+                                                     BsOrder o, int* __restrict__ bsum) {
+    pdl_wait_trigger();
+    __shared__ int warp_sum[32];
+    const int N = counters[CNT_N];
+    int k0, k1;
+    slot_range(N, k0, k1);
+    int c = 0;
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) c += bs_gap_after(o, next, N, k);
+    c = block_sum_1024(c, warp_sum);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = c;
+}
+
+__device__ __forceinline__ int4 cell_of(const double* __restrict__ pos, int cap, int i) {
+    return make_int4((int)floor(pos[i]), (int)floor(pos[(long long)cap + i]), (int)floor(pos[2LL * cap + i]), 0);
+}
+
+__global__ void __launch_bounds__(1024) k_slot_assign(const double* __restrict__ pos, const int* __restrict__ next,
+                                                      int cap, int* __restrict__ counters, BsOrder o,
+                                                      const int* __restrict__ bsum, float4* __restrict__ seg,
+                                                      int nfaces) {
+    pdl_wait_trigger();
+    __shared__ int warp_sum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int N = counters[CNT_N];
+    int k0, k1;
+    slot_range(N, k0, k1);
+    int pre = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) pre += bsum[b];
+    int carry = block_sum_1024(pre, warp_sum);
+    int* slot = const_cast<int*>(o.slot);
+    for (int base = k0; base < k1; base += blockDim.x) {
+        const int k = base + (int)threadIdx.x;
+        const int gap = k < k1 ? bs_gap_after(o, next, N, k) : 0;
+        int x = gap;  // inclusive scan within the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) warp_sum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int z = warp_sum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, z, off);
+                if (lane >= off) z += y;
+            }
+            warp_sum[lane] = z;  // inclusive over warps
+        }
+        __syncthreads();
+        if (k < k1) {
+            const int sl = k + carry + (x - gap) + (w > 0 ? warp_sum[w - 1] : 0);
+            slot[k] = sl;
+            const int i = bs_point_at(o, k);
+            if (sl % BS_GROUP == 0) o.org[sl / BS_GROUP] = cell_of(pos, cap, i);
+            if (gap && (sl + 1) % BS_GROUP == 0) o.org[(sl + 1) / BS_GROUP] = cell_of(pos, cap, next[i]);
+        }
+        carry += warp_sum[31];
+        __syncthreads();  // warp_sum is rewritten by the next round
+    }
+    if (blockIdx.x != gridDim.x - 1) return;
+    // the last block: the slot count and zero padding slots up to whole groups
+    const int ns = N + carry;
+    if (threadIdx.x == 0) counters[CNT_NSLOT] = ns;
+    const long long Np = bs_block(ns);
+    const int npad = (int)(Np - ns);
+    float* r = reinterpret_cast<float*>(seg);
+    for (int e = threadIdx.x; e < npad * 16 * (1 + nfaces); e += blockDim.x) {
+        const int f = e / (npad * 16), rem = e - f * npad * 16;
+        r[bs_value_index((long long)f * Np + ns + rem / 16, rem % 16)] = 0.f;
+    }
+}
+
 }  // namespace
 
 void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
-                    int* ord, int* rank, int4* org, int* cnt, int* start, cudaStream_t s) {
+                    int* ord, int* rank, int* cnt, int* start, cudaStream_t s) {
     const BsBins bb = bs_bins(g.nx, g.ny, g.nz);
     const int blocks = (span + 255) / 256 > 0 ? (span + 255) / 256 : 1;
     launch_pdl(k_sort_keys, blocks, 256, 0, s, g, bb, pos, cap, counters, key, cnt);
     launch_pdl(k_sort_scan, 1, 1024, 0, s, bb.K, (const int*)cnt, start);
     launch_pdl(k_sort_scatter, blocks, 256, 0, s, counters, (const int*)key, start, tmp);
-    launch_pdl(k_sort_bins, (bb.K * 32 + 255) / 256, 256, 0, s, bb.K, pos, cap, cnt, (const int*)start,
-               (const int*)tmp, ord, rank, org);
+    launch_pdl(k_sort_bins, (bb.K * 32 + 255) / 256, 256, 0, s, bb.K, cnt, (const int*)start, (const int*)tmp, ord,
+               rank);
+}
+
+void launch_bs_slots(const double* pos, const int* next, int cap, int span, int* counters, const BsOrder& o,
+                     int* bsum, float4* seg, int nfaces, cudaStream_t s) {
+    int blocks = (span + 1023) / 1024;
+    blocks = blocks < 1 ? 1 : (blocks > BS_SLOT_BLOCKS ? BS_SLOT_BLOCKS : blocks);
+    launch_pdl(k_slot_count, blocks, 1024, 0, s, next, (const int*)counters, o, bsum);
+    launch_pdl(k_slot_assign, blocks, 1024, 0, s, pos, next, cap, counters, o, (const int*)bsum, seg, nfaces);
 }
 
 }  // namespace vlb

@@ -21,20 +21,19 @@ namespace {
 // float for the FP32 equation of motion and Biot-Savart sum.  An open end pinned on a wall takes the mirror image
 // of its neighbour across that wall as its missing neighbour, represents half
 // of its segment, and carries its wall code (+1) to the equation of motion; a
-// line's last point has a zero-length source record.  The source records go
-// to the positions of the order o.
+// line's last point starts no segment.  The source slots go where the slots
+// of the order o put them.
 struct StageRec {
-    long long k;   // record position
-    double O[3];   // group origin
+    int q;         // successor, -1 at a line's last point
     double si[3];  // the point
     double st[3];  // its successor (itself at a line's last point)
-    float b[3];    // the segment
+    float b[3];    // the segment (zero at a line's last point)
 };
 
 __device__ __forceinline__ void geometry_point(const VfmParams& P, const double* __restrict__ s,
                                                const int* __restrict__ next, const int* __restrict__ prev, int N,
                                                int cap, int i, float4* __restrict__ geo, double* __restrict__ s0_copy,
-                                               const BsOrder& o, StageRec& out) {
+                                               StageRec& out) {
     const int p = prev[i], q = next[i];
     const int pl = p >= 0 ? p : i, ql = q >= 0 ? q : i;  // an end loads itself in place of the missing one
     double si[3], sp[3], sq[3];
@@ -93,7 +92,7 @@ __device__ __forceinline__ void geometry_point(const VfmParams& P, const double*
     geo[2LL * i] = make_float4(t1[0], t1[1], t1[2], dxi);
     geo[2LL * i + 1] = make_float4(fl * (float)ab[0], fl * (float)ab[1], fl * (float)ab[2], (float)(code + 1));
     if (q < 0) b[0] = b[1] = b[2] = 0.f;  // no segment leaves a line's last point
-    out.k = bs_position(o, s, cap, i, out.O);
+    out.q = q;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         out.si[a] = si[a];
@@ -102,33 +101,9 @@ __device__ __forceinline__ void geometry_point(const VfmParams& P, const double*
     }
 }
 
-// Source record f of the point geometry_point described: f = 0 the segment
-// itself, f = 1 + face its image across that solid face, from M(s_q) to
-// M(s_i) with M mirroring the normal coordinate x_a -> w2 - x_a (record
-// (1 + face) Np + k, relative to the mirrored origin w2 - O_a, an integer as
-// w2 is).
-__device__ __forceinline__ void stage_record(const VfmParams& P, const StageRec& r, int f, float val[16]) {
-    double rel[3];
-    float d[3];
-    if (f == 0) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            rel[a] = min_image(P.g, a, r.si[a] - r.O[a]);
-            d[a] = r.b[a];
-        }
-    } else {
-        const int ax = P.face_code[f - 1] >> 1;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            rel[a] = a == ax ? r.O[a] - r.st[a] : min_image(P.g, a, r.st[a] - r.O[a]);
-            d[a] = a == ax ? r.b[a] : -r.b[a];
-        }
-    }
-    bs_record_values(rel, d, val);
-}
-
-// One thread per point (and per padding record position); thread 0 also
-// resets the work counter of the Biot-Savart launch that follows.
+// One thread per point; thread 0 also resets the work counter of the
+// Biot-Savart launch that follows.  The slots' padding is written by the
+// slot assignment at the step's start.
 __global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const double* __restrict__ s,
                                                              const int* __restrict__ next,
                                                              const int* __restrict__ prev,
@@ -139,38 +114,13 @@ __global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const 
     const int N = counters[CNT_N];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch that follows takes items from 0
-    const long long Np = bs_block(N, P.nfaces);
-    if (o.sorted) {
-        // records at the positions of the order: stored one by one
-        if (i >= N) {
-            bs_pad_records(N, P.nfaces, i, seg);
-            return;
-        }
-        StageRec r;
-        geometry_point(P, s, next, prev, N, cap, i, geo, s0_copy, o, r);
-        for (int f = 0; f <= P.nfaces; ++f) {
-            float val[16];
-            stage_record(P, r, f, val);
-            bs_store_record(seg, (long long)f * Np + r.k, val);
-        }
-        return;
-    }
-    // point order: record i, so the two records of a pair belong to this
-    // lane and its neighbour, which store the pair together (zero records at
-    // the padding positions [N, Np))
-    StageRec r = {};
-    r.k = i;
-    if (i < N) geometry_point(P, s, next, prev, N, cap, i, geo, s0_copy, o, r);
-    for (int f = 0; f <= P.nfaces; ++f) {
-        float val[16];
-        if (i < N) {
-            stage_record(P, r, f, val);
-        } else {
-#pragma unroll
-            for (int v = 0; v < 16; ++v) val[v] = 0.f;
-        }
-        bs_store_pair(seg, (long long)f * Np + i, val, i < Np);
-    }
+    if (i >= N) return;
+    const long long Np = bs_block(counters[CNT_NSLOT]);
+    StageRec r;
+    geometry_point(P, s, next, prev, N, cap, i, geo, s0_copy, r);
+    const BsPointSlots ps = bs_point_slots(o, o.sorted ? o.rank[i] : i, r.q);
+    for (int f = 0; f <= P.nfaces; ++f)
+        bs_write_point_slots(P.g, o, ps, Np, f, f > 0 ? P.face_code[f - 1] : 0, r.si, r.st, r.b, r.q >= 0, seg);
 }
 
 // The equation of motion of each point as a kernel of its own (used when the
@@ -262,10 +212,8 @@ __global__ void k_line_profile(Grid g, const double* __restrict__ pos, const int
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
                            int cap, float4* geo, float4* seg, double* s0_copy, const BsOrder& o, cudaStream_t st) {
     if (cap <= 0) return;
-    // padding positions reach the capacity rounded up to a whole group
-    const int span = (int)bs_block(cap, 1);
-    launch_pdl(k_geometry_stage, span / BS_GROUP, BS_GROUP, 0, st, P, s, next, prev, counters, cap, geo, seg,
-               s0_copy, o);
+    launch_pdl(k_geometry_stage, (cap + BS_GROUP - 1) / BS_GROUP, BS_GROUP, 0, st, P, s, next, prev, counters, cap,
+               geo, seg, s0_copy, o);
 }
 
 void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s, long long* vacc) {

@@ -33,7 +33,8 @@ enum : int {
     CNT_NCONTACT = 9,   // wall-contact candidates of the current reconnection pass
     CNT_DIRTY = 10,     // 1 after seeding: the next remesh checks for small components even without removals
     CNT_RFLAGS = 11,    // nonzero when the remesh geometry flagged a split or removal candidate (cleared by the finish)
-    CNT_COUNT = 12
+    CNT_NSLOT = 12,     // Biot-Savart source slots of the current step (points + gap slots)
+    CNT_COUNT = 13
 };
 
 // Device float64 statistics.
@@ -104,42 +105,63 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 constexpr int LBM_BLOCK = 256;  // cells per stream-collide block (one z plane)
 constexpr int BS_TPB = 128;     // threads per Biot-Savart block
-constexpr int BS_TILE = 128;    // source records per shared-memory tile
-constexpr int BS_GROUP = 64;    // source records that share one integer origin
-constexpr int BS_REC = 4;       // float4 per source record (64 bytes; records are stored in interleaved pairs)
+constexpr int BS_TILE = 128;    // source slots per shared-memory tile
+constexpr int BS_GROUP = 64;    // source slots that share one integer origin
+constexpr int BS_REC = 4;       // float4 per source slot (64 bytes; slots are stored in interleaved pairs)
 constexpr int MAX_SPLIT = 64;   // Biot-Savart source splits
 // From this many points on the Biot-Savart sources are put in a spatial order
-// once per step, so that a group of BS_GROUP records spans a small box
+// once per step, so that a group of BS_GROUP slots spans a small box
 constexpr int BS_SORT_MIN = 8192;
-constexpr int BS_SORT_MAX_BINS = 1 << 16;  // bins of the spatial order (bin edge 8 cells or more)
+constexpr int BS_SORT_MAX_BINS = 1 << 16;  // bins of the spatial order (bin edge 16 cells or more)
 
-// Biot-Savart source record of segment s_j -> s_j + d, stored relative to
-// the integer origin O of its group of BS_GROUP records (the cell of the
-// group's first point).  Its 16 values:
-//   0-2 h = fl(s_j - O) (minimum image on periodic axes), 3 |d|^2,
-//   4-6 d, 7-9 c = h x d (FP32), 10-12 l = fl(s_j - O - h), 13-15 zero;
-// h + l carries s_j - O to ~1e-14 cells.  Records come in pairs (2p, 2p + 1)
-// stored interleaved in 128 bytes: value v of record k is float
-// (k / 2) * 32 + 2 v + (k % 2), so that one float4 holds two values of both
-// records and one float2 the same value of both (the packed FP32 pair path).
-// A target r (its own record k: origin O_t, parts h_t, l_t) sees the group
-// at offset t = (O - O_t) - h_t - l_t, so R1 = s_j - r = h + l + t.
-__host__ __device__ inline long long bs_value_index(long long k, int v) { return (k >> 1) * 32 + 2 * v + (k & 1); }
+// Biot-Savart sources as a chain of slots.  Each point of the order
+// (sorted position k) owns one slot, slot[k], holding its segment
+// s_i -> s_next(i).  The slot after it holds the segment's end point: the
+// next point of the order when that is next(i) (the usual case: a line runs
+// through a bin as consecutive points), otherwise a gap slot inserted there
+// that holds a copy of s_next(i) and no segment.  A line's last point has no
+// segment and needs no gap.  So the pair sum can take |R| at a slot's point
+// as both the start of its own segment and the end of the one before, one
+// reciprocal square root per slot instead of two per segment.
+//
+// Slot record: 16 values relative to the integer origin O of its group of
+// BS_GROUP slots (the cell of the group's first slot at the step's start):
+//   0-2 h = fl(s - O) (minimum image on periodic axes), 3 |d|^2, 4-6 d,
+//   7-9 c = h x d (FP32), 10-12 l = fl(s - O - h), 13-15 fl(s - O + d), the
+//   segment's end (read for the group's last slot, whose end lies in the
+//   next group);
+// h + l carries s - O to ~1e-14 cells.  Gap and padding slots have d = 0.
+// Storage: slot p and slot p + 32 of a group form pair p, interleaved in
+// 128 bytes: value v of slot k is float
+//   (k / 64) * 1024 + (k % 32) * 32 + 2 v + (k / 32) % 2,
+// so that one float4 holds two values of both slots, one float2 the same
+// value of both (the packed FP32 pair path), and the pairs p = 0..31 of a
+// group walk its two halves along their chains side by side.
+// A target r (its own slot: origin O_t, parts h_t, l_t) sees the group at
+// offset t = (O - O_t) - h_t - l_t, so R1 = s - r = h + l + t.
+__host__ __device__ inline long long bs_value_index(long long k, int v) {
+    return (k >> 6) * 1024 + (k & 31) * 32 + 2 * v + ((k >> 5) & 1);
+}
 
-// Order of the Biot-Savart sources.  sorted = 0: record k is point k;
-// sorted = 1: record k is point ord[k] (rank is the inverse), a spatial order.
-// Either way group g of BS_GROUP records has the integer origin org[g] (the
-// cell of its first point), written by the sort or, in point order, by the
-// stage geometry.
+// Order of the Biot-Savart sources.  sorted = 0: sorted position k is
+// point k; sorted = 1: it is point ord[k] (rank is the inverse), a spatial
+// order.  slot[k] is the slot of sorted position k.  Group g of BS_GROUP
+// slots has the integer origin org[g].xyz; org[g].w is nonzero when its
+// chain jumps by a periodic box somewhere (the slots' minimum images about O
+// then disagree with a segment), and the group takes the full-precision path.
 struct BsOrder {
     int sorted;
     const int* ord;
     const int* rank;
+    const int* slot;
     int4* org;
 };
 
 // Bins of the spatial order: the cell floor(x) >> shift per axis, clamped to
 // the lattice, interleaved bit by bit (x, y, z) into a Morton key < K.
+// Bins of 16 cells: a line crosses fewer bin edges than with 8 (1.08 slots
+// per point instead of 1.14 on the 128x128x1024 channel), and a group of
+// slots spans the same ~30 cells.
 struct BsBins {
     int shift;
     int bits[3];
@@ -154,7 +176,7 @@ __host__ __device__ inline int bs_ceil_log2(int v) {
 
 __host__ __device__ inline BsBins bs_bins(int nx, int ny, int nz) {
     BsBins b;
-    b.shift = 3;
+    b.shift = 4;
     while (true) {
         const int e = 1 << b.shift;
         b.bits[0] = bs_ceil_log2((nx + e - 1) / e);
@@ -169,12 +191,13 @@ __host__ __device__ inline BsBins bs_bins(int nx, int ny, int nz) {
     }
 }
 
-// Records of a point set of n points with nfaces wall-image blocks: each
-// block is padded to a multiple of BS_GROUP records when images are on, and
-// to an even count (whole pairs) without them; padding records are zero.
-__host__ __device__ inline long long bs_block(int n, int nfaces) {
-    return nfaces > 0 ? (long long)((n + BS_GROUP - 1) / BS_GROUP) * BS_GROUP : (long long)(n + (n & 1));
-}
+// Slots of one block of sources (the segments, or their images across one
+// wall) for ns slots: whole groups, the padding slots zero.
+__host__ __device__ inline long long bs_block(int ns) { return (long long)((ns + BS_GROUP - 1) / BS_GROUP) * BS_GROUP; }
+// Slot capacity for up to n points: every point may need a gap slot.
+__host__ __device__ constexpr long long bs_slot_cap(long long n) { return ((2 * n + BS_GROUP - 1) / BS_GROUP) * BS_GROUP; }
+// Blocks of the slot scan (each takes a contiguous range of sorted positions).
+constexpr int BS_SLOT_BLOCKS = 256;
 
 // Geometry of the lattice, passed by value to kernels.
 struct Grid {
@@ -313,12 +336,14 @@ struct Dev {
     double* vel1;
     double* spp;        // FP64 curvature for remeshing
     double* seglen;     // FP64 segment lengths for remeshing
-    float4* seg;        // Biot-Savart source records, BS_REC float4 each (segments, then wall images)
+    float4* seg;        // Biot-Savart source slots, BS_REC float4 each (segments, then wall images)
     int* bs_key;        // spatial order: Morton key of each point
     int* bs_tmp;        // spatial order: points scattered by key, before the in-bin sort
     int* bs_ord;        // sorted position -> point
     int* bs_rank;       // point -> sorted position
-    int4* bs_org;       // integer origin of each group of BS_GROUP records
+    int4* bs_org;       // integer origin of each group of BS_GROUP slots (w: jump flag)
+    int* bs_slot;       // sorted position -> slot
+    int* bs_bsum;       // gap slots per block of the slot scan [BS_SLOT_BLOCKS]
     int* bs_cnt;        // points per bin (zero between sorts)
     int* bs_start;      // bin starts
     float* bsp;         // Biot-Savart partial sums [splits][3][cap]
@@ -381,10 +406,17 @@ void launch_line_length(const Grid& g, const double* pos, const int* next, int* 
 int sm_count();
 int bs_max_splits(int cap, int nsm);
 // Spatial order of the points pos[3][cap] (count from the device counters):
-// bs_ord, bs_rank and the group origins bs_org.  span: points one pass of the
-// per-point grids covers (they stride over any beyond).
+// bs_ord and bs_rank.  span: points one pass of the per-point grids covers
+// (they stride over any beyond).
 void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
-                    int* ord, int* rank, int4* org, int* cnt, int* start, cudaStream_t s);
+                    int* ord, int* rank, int* cnt, int* start, cudaStream_t s);
+// Slots of the order o for the points pos[3][cap] with successors next[]
+// (indices outside [-1, N) count as -1): o.slot, the group origins o.org
+// (jump flags cleared), counters[CNT_NSLOT], and the padding slots of every
+// record block (1 + nfaces blocks of bs_block(nslot) slots).  bsum: scratch
+// [BS_SLOT_BLOCKS].
+void launch_bs_slots(const double* pos, const int* next, int cap, int span, int* counters, const BsOrder& o,
+                     int* bsum, float4* seg, int nfaces, cudaStream_t s);
 // With eom != nullptr the kernel applies the equation of motion to each target
 // tile as soon as its sum is complete, and does not write vel.
 // Sources are the N segments, then with nfaces > 0 their images across each
@@ -406,24 +438,27 @@ constexpr int BS_ACC_MAX = 24576;
 // Whether launch_biot_savart, given vacc and no equation of motion, adds the
 // split sums of about n_hint points into vacc (else it writes vel).
 bool bs_uses_vacc(int n_hint);
-// Stand-alone entry: prev[], the spatial order (from BS_SORT_MIN points on)
-// and the source records of a caller's point set, into the scratch buffers.
+// Stand-alone entry: prev[], the spatial order (from BS_SORT_MIN points on),
+// the slots and the source records of a caller's point set, into the scratch
+// buffers.
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
-                               int* counters, const BsOrder& o, int* key, int* tmp, int* cnt, int* start,
+                               int* counters, const BsOrder& o, int* key, int* tmp, int* cnt, int* start, int* bsum,
                                cudaStream_t s);
 // vel[3][n] = the fixed-point sums vacc[3][n] (stand-alone entry)
 void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s);
 
 // Scratch of the stand-alone entry points for n points, each part 256-byte
-// aligned: counters | prev | source records | sort keys | scattered points |
-// ord | rank | group origins | bin counts | bin starts | fixed-point sums.
-// Linear in n, so its maximum over n <= m is its value at m.
+// aligned: counters | prev | source slots | sort keys | scattered points |
+// ord | rank | slots | group origins | bin counts | bin starts | slot-scan
+// sums | fixed-point sums.  Non-decreasing in n, so its maximum over n <= m
+// is its value at m.
 __host__ __device__ constexpr size_t bs_up256(size_t b) { return (b + 255) & ~size_t(255); }
 __host__ __device__ constexpr size_t bs_scratch_bytes(long long n) {
-    return bs_up256(sizeof(int) * 16) + bs_up256(sizeof(int) * (size_t)n) +
-           bs_up256(sizeof(float4) * BS_REC * (size_t)((n + BS_GROUP - 1) / BS_GROUP) * BS_GROUP) +
-           4 * bs_up256(sizeof(int) * (size_t)n) + bs_up256(sizeof(int4) * (size_t)((n + BS_GROUP - 1) / BS_GROUP)) +
-           2 * bs_up256(sizeof(int) * (size_t)BS_SORT_MAX_BINS) + bs_up256(sizeof(long long) * 3 * (size_t)n);
+    return bs_up256(sizeof(int) * CNT_COUNT) + bs_up256(sizeof(int) * (size_t)n) +
+           bs_up256(sizeof(float4) * BS_REC * (size_t)bs_slot_cap(n)) + 5 * bs_up256(sizeof(int) * (size_t)n) +
+           bs_up256(sizeof(int4) * (size_t)(bs_slot_cap(n) / BS_GROUP)) +
+           2 * bs_up256(sizeof(int) * (size_t)BS_SORT_MAX_BINS) + bs_up256(sizeof(int) * (size_t)BS_SLOT_BLOCKS) +
+           bs_up256(sizeof(long long) * 3 * (size_t)n);
 }
 
 // abi.cu
