@@ -218,33 +218,33 @@ __device__ __forceinline__ BsTarget bs_target(const float4* __restrict__ seg, co
 // group.  A pair p (slots p and p + 32) is evaluated packed (FP32x2), so the
 // group's two halves walk their chains side by side.
 
-// ia and rho at the two slots of pair p, for each target offset t (R = h + t
-// by scalar adds: a packed add would need t twice, in registers the pair
-// loop cannot spare; the adds take the same FMA-pipe time either way).
+// ia and rho at the two slots of pair p, for each target offset t (held in
+// both halves of a float2), and the pair's |d|^2 for its segments.
 template <int TGT>
-__device__ __forceinline__ void chain_head(const float4* __restrict__ Q, const float (&t)[TGT][3],
-                                           float2 (&ia)[TGT], float2 (&rho)[TGT]) {
+__device__ __forceinline__ void chain_head(const float4* __restrict__ Q, const float2 (&t)[TGT][3],
+                                           float2 (&ia)[TGT], float2 (&rho)[TGT], float2& dd) {
     const float4 q0 = Q[0], q1 = Q[1];
+    const float2 hx = make_float2(q0.x, q0.y), hy = make_float2(q0.z, q0.w), hz = make_float2(q1.x, q1.y);
+    dd = make_float2(q1.z, q1.w);
 #pragma unroll
     for (int u = 0; u < TGT; ++u) {
-        const float2 rx = make_float2(q0.x + t[u][0], q0.y + t[u][0]);
-        const float2 ry = make_float2(q0.z + t[u][1], q0.w + t[u][1]);
-        const float2 rz = make_float2(q1.x + t[u][2], q1.y + t[u][2]);
+        const float2 rx = __fadd2_rn(hx, t[u][0]), ry = __fadd2_rn(hy, t[u][1]), rz = __fadd2_rn(hz, t[u][2]);
         const float2 a2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
         ia[u] = make_float2(rsqrt_approx(a2.x), rsqrt_approx(a2.y));
         rho[u] = __fmul2_rn(a2, ia[u]);
     }
 }
 
-// The segments of the slots of pair p, from (ia0, rho0) at their starts to
-// (ia1, rho1) at their ends, into the sums of fac c and fac d (fac halved).
+// The segments of the slots of pair p (|d|^2 from its head), from (ia0,
+// rho0) at their starts to (ia1, rho1) at their ends, into the sums of fac c
+// and fac d (fac halved).
 template <int TGT>
-__device__ __forceinline__ void chain_segments(const float4* __restrict__ Q, const float2 (&ia0)[TGT],
-                                               const float2 (&rho0)[TGT], const float2 (&ia1)[TGT],
-                                               const float2 (&rho1)[TGT], float2 (&av)[TGT][3],
-                                               float2 (&aw)[TGT][3]) {
-    const float4 q1 = Q[1], q2 = Q[2], q3 = Q[3], q4 = Q[4];
-    const float2 mdd = make_float2(-q1.z, -q1.w);
+__device__ __forceinline__ void chain_segments(const float4* __restrict__ Q, const float2& dd,
+                                               const float2 (&ia0)[TGT], const float2 (&rho0)[TGT],
+                                               const float2 (&ia1)[TGT], const float2 (&rho1)[TGT],
+                                               float2 (&av)[TGT][3], float2 (&aw)[TGT][3]) {
+    const float4 q2 = Q[2], q3 = Q[3], q4 = Q[4];
+    const float2 mdd = make_float2(-dd.x, -dd.y);
     const float2 dx = make_float2(q2.x, q2.y), dy = make_float2(q2.z, q2.w), dz = make_float2(q3.x, q3.y);
     const float2 cx = make_float2(q3.z, q3.w), cy = make_float2(q4.x, q4.y), cz = make_float2(q4.z, q4.w);
 #pragma unroll
@@ -261,15 +261,21 @@ __device__ __forceinline__ void chain_segments(const float4* __restrict__ Q, con
     }
 }
 
-// The chain of one group for TGT targets at offsets t: pair p's segments end at pair p + 1's slots, except slot 31's,
-// which ends at slot 32 (the first pair's other half), and slot 63's, which
-// ends at the end point its record stores (the next slot is in another
-// group).  Returns the sums of fac c and fac d with fac halved.
+// The chain of one group for TGT targets at offsets t: pair p's segments end
+// at pair p + 1's slots, except slot 31's, which ends at slot 32 (the first
+// pair's other half), and slot 63's, which ends at the end point its record
+// stores (the next slot is in another group).  Returns the sums of fac c and
+// fac d with fac halved.
 template <int TGT>
-__device__ __forceinline__ void chain_group(const float4* __restrict__ T, const float (&t)[TGT][3],
+__device__ __forceinline__ void chain_group(const float4* __restrict__ T, const float (&th)[TGT][3],
                                             float2 (&av)[TGT][3], float2 (&aw)[TGT][3]) {
-    float2 ia0[TGT], rho0[TGT];
-    chain_head<TGT>(T, t, ia0, rho0);
+    float2 t[TGT][3];
+#pragma unroll
+    for (int u = 0; u < TGT; ++u)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) t[u][a] = make_float2(th[u][a], th[u][a]);
+    float2 ia0[TGT], rho0[TGT], dd0;
+    chain_head<TGT>(T, t, ia0, rho0, dd0);
     float ia32[TGT], rho32[TGT];
 #pragma unroll
     for (int u = 0; u < TGT; ++u) {
@@ -278,27 +284,28 @@ __device__ __forceinline__ void chain_group(const float4* __restrict__ T, const 
     }
 #pragma unroll 2
     for (int p = 0; p < BS_GROUP / 2 - 1; ++p) {
-        float2 ia1[TGT], rho1[TGT];
-        chain_head<TGT>(T + 8 * (p + 1), t, ia1, rho1);
-        chain_segments<TGT>(T + 8 * p, ia0, rho0, ia1, rho1, av, aw);
+        float2 ia1[TGT], rho1[TGT], dd1;
+        chain_head<TGT>(T + 8 * (p + 1), t, ia1, rho1, dd1);
+        chain_segments<TGT>(T + 8 * p, dd0, ia0, rho0, ia1, rho1, av, aw);
 #pragma unroll
         for (int u = 0; u < TGT; ++u) {
             ia0[u] = ia1[u];
             rho0[u] = rho1[u];
         }
+        dd0 = dd1;
     }
     const float4* Q = T + 8 * (BS_GROUP / 2 - 1);
     const float4 q6 = Q[6], q7 = Q[7];  // values 13-15: the stored end point (slot 63 in the .y halves)
     float2 ia1[TGT], rho1[TGT];
 #pragma unroll
     for (int u = 0; u < TGT; ++u) {
-        const float ex = q6.w + t[u][0], ey = q7.y + t[u][1], ez = q7.w + t[u][2];
+        const float ex = q6.w + th[u][0], ey = q7.y + th[u][1], ez = q7.w + th[u][2];
         const float b2 = ex * ex + ey * ey + ez * ez;
         const float ib = rsqrt_approx(b2);
         ia1[u] = make_float2(ia32[u], ib);
         rho1[u] = make_float2(rho32[u], b2 * ib);
     }
-    chain_segments<TGT>(Q, ia0, rho0, ia1, rho1, av, aw);
+    chain_segments<TGT>(Q, dd0, ia0, rho0, ia1, rho1, av, aw);
 }
 
 // Minimum image of one component of R1 on a periodic axis (L = 0 on wall
@@ -389,6 +396,71 @@ __device__ __forceinline__ void pair2_precise(const float4* __restrict__ Q, int 
                                       t[u].v, box, sign);
         pair_precise<PERIODIC, GUARD>(q0.y, q0.w, q1.y, q1.w, q2.y, q2.w, q3.y, q5.y, q5.w, q6.y, j + BS_GROUP / 2,
                                       th[u], tl[u], t[u], t[u].v, box, sign);
+    }
+}
+
+__device__ __forceinline__ float2 fsub2(float2 x, float2 y) { return __fadd2_rn(x, make_float2(-y.x, -y.y)); }
+
+// The wrap path for the two slots of pair p (groups that no target of the
+// warp sees within BS_NEAR cells, but some of whose sources may lie half a
+// periodic box away): R1 = h + t without the low parts, as on the far path,
+// and the minimum image of every pair decided in FP32 (for a wall-image slot,
+// that of its end point, reading 21).  When some lane finds a pair within
+// 1e-3 cells of half the box, where dropping the low parts could change the
+// decision, the warp takes that pair on the precise path instead, which
+// decides it exactly.  Adds the pair's sums into v (the block's sign
+// applied by the caller).
+template <int TGT>
+__device__ __forceinline__ void pair2_wrap(const float4* __restrict__ Q, int j, const float (&th)[TGT][3],
+                                           const float (&tl)[TGT][3], BsTarget (&t)[TGT], const BoxF& box,
+                                           int Np, float2 (&v)[TGT][3]) {
+    const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3];
+    const float2 hx = make_float2(q0.x, q0.y), hy = make_float2(q0.z, q0.w), hz = make_float2(q1.x, q1.y);
+    const float2 dd = make_float2(q1.z, q1.w);
+    const float2 dx = make_float2(q2.x, q2.y), dy = make_float2(q2.z, q2.w), dz = make_float2(q3.x, q3.y);
+    const bool img = j >= Np;
+    const float2 ex = img ? dx : make_float2(0.f, 0.f), ey = img ? dy : make_float2(0.f, 0.f),
+                 ez = img ? dz : make_float2(0.f, 0.f);
+    const float M = 12582912.0f;  // 1.5 * 2^23: adding it rounds to the nearest integer
+    float2 r[TGT][3];
+    bool tie = false;
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        r[u][0] = __fadd2_rn(hx, make_float2(th[u][0], th[u][0]));
+        r[u][1] = __fadd2_rn(hy, make_float2(th[u][1], th[u][1]));
+        r[u][2] = __fadd2_rn(hz, make_float2(th[u][2], th[u][2]));
+        const float2 e[3] = {ex, ey, ez};
+        const float L[3] = {box.Lx, box.Ly, box.Lz}, iL[3] = {box.iLx, box.iLy, box.iLz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (L[a] > 0.f) {
+                const float2 z = __fadd2_rn(r[u][a], e[a]);
+                const float2 k = fsub2(__ffma2_rn(z, make_float2(iL[a], iL[a]), make_float2(M, M)),
+                                            make_float2(M, M));
+                r[u][a] = __ffma2_rn(make_float2(-L[a], -L[a]), k, r[u][a]);
+                const float2 w = __fadd2_rn(r[u][a], e[a]);
+                tie |= (fabsf(w.x) > 0.5f * L[a] - 1e-3f) | (fabsf(w.y) > 0.5f * L[a] - 1e-3f);
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, tie)) {
+        pair2_precise<true, false, TGT>(Q, j, th, tl, t, box, Np);
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        const float2 rx = r[u][0], ry = r[u][1], rz = r[u][2];
+        const float2 a2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+        const float2 rd = __ffma2_rn(rz, dz, __ffma2_rn(ry, dy, __fmul2_rn(rx, dx)));
+        const float2 b2 = __fadd2_rn(__ffma2_rn(make_float2(2.f, 2.f), rd, a2), dd);
+        const float2 ia = make_float2(rsqrt_approx(a2.x), rsqrt_approx(a2.y));
+        const float2 ib = make_float2(rsqrt_approx(b2.x), rsqrt_approx(b2.y));
+        const float2 P = __fmul2_rn(ia, ib);
+        const float2 den = __ffma2_rn(P, __fadd2_rn(a2, rd), make_float2(1.f, 1.f));
+        const float2 fac = __fmul2_rn(__fmul2_rn(__fadd2_rn(ia, ib), P), make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+        v[u][0] = __ffma2_rn(fac, fsub2(__fmul2_rn(ry, dz), __fmul2_rn(rz, dy)), v[u][0]);
+        v[u][1] = __ffma2_rn(fac, fsub2(__fmul2_rn(rz, dx), __fmul2_rn(rx, dz)), v[u][1]);
+        v[u][2] = __ffma2_rn(fac, fsub2(__fmul2_rn(rx, dy), __fmul2_rn(ry, dx)), v[u][2]);
     }
 }
 
@@ -540,10 +612,18 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase
 #pragma unroll(TGT == 1 ? 2 : 1)
             for (int p = 0; p < BS_GROUP / 2; ++p)
                 pair2_precise<PERIODIC, true, TGT>(T + 8 * p, gbase + p, th, tl, t, box, Np);
-        } else {
-#pragma unroll(TGT == 1 ? 2 : 1)
-            for (int p = 0; p < BS_GROUP / 2; ++p)
-                pair2_precise<PERIODIC, false, TGT>(T + 8 * p, gbase + p, th, tl, t, box, Np);
+        } else if (PERIODIC) {
+            float2 v[TGT][3];
+#pragma unroll
+            for (int u = 0; u < TGT; ++u)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) v[u][a] = make_float2(0.f, 0.f);
+#pragma unroll 2
+            for (int p = 0; p < BS_GROUP / 2; ++p) pair2_wrap<TGT>(T + 8 * p, gbase + p, th, tl, t, box, Np, v);
+#pragma unroll
+            for (int u = 0; u < TGT; ++u)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) t[u].v[a] = fmaf(G.sign, v[u][a].x + v[u][a].y, t[u].v[a]);
         }
     } else {
         float2 av[TGT][3], aw[TGT][3];
@@ -589,13 +669,13 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
     const int lane = threadIdx.x & 31;
     const int N = counters[CNT_N];
     if (N <= 0) return true;
-    const int ns = bs_splits(N, TT, nsm);
-    const int ntb = (N + TT - 1) / TT;
-    const int nitems = ntb * ns;
     const long long Np = bs_block(counters[CNT_NSLOT]);
     const int nsrc = (int)(Np * (1 + im.nfaces));  // segments, then their wall images
+    const int ns = bs_splits(N, TT, nsm, nsrc / BS_GROUP);
+    const int ntb = (N + TT - 1) / TT;
+    const int nitems = ntb * ns;
     // splits start on group boundaries, so that every tile starts on one
-    const int chunk = ((nsrc + ns - 1) / ns + BS_GROUP - 1) / BS_GROUP * BS_GROUP;
+    const int chunk = (nsrc / BS_GROUP + ns - 1) / ns * BS_GROUP;
     if ((int)blockIdx.x >= nitems) return true;
     int item = blockIdx.x;
     while (true) {
@@ -712,10 +792,12 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
     return true;
 }
 
-// Resident blocks: the pair loop is issue-bound and needs the warps; more
-// targets per thread need more registers.
+// Resident blocks: the pair loop is bound by the latency of its MUFU and
+// shared-memory results and needs the warps; one target per thread fits 72
+// registers (7 blocks), two 96 (5 blocks, a few spilled registers, still the
+// faster form in walled boxes).
 template <bool PERIODIC, int TGT, bool EOM, bool ACC>
-__global__ void __launch_bounds__(BS_TPB, TGT == 1 ? ((ACC || !EOM || PERIODIC) ? 7 : 8) : 5)
+__global__ void __launch_bounds__(BS_TPB, TGT == 1 ? 7 : 5)
     k_biot_savart(const float4* __restrict__ seg, const int* __restrict__ prev, int* __restrict__ counters,
                   int* __restrict__ tile_ticket, int cap, BoxF box, float kq, float* __restrict__ part,
                   float* __restrict__ vel, EomArgs ea, BsImages im, BsOrder o, int nsm,
@@ -823,9 +905,11 @@ int sm_count() {
 bool bs_uses_vacc(int n_hint) { return n_hint < BS_ACC_MAX; }
 
 int bs_max_splits(int cap, int nsm) {
+    // the most splits: one target tile per item and every point needing a
+    // gap slot (the group count only caps the splits)
     int m = 1;
     for (int n = 1; n <= cap; n += (n < 8192 ? 1 : 128)) {
-        const int k = bs_splits(n, BS_TPB, nsm);
+        const int k = bs_splits(n, BS_TPB, nsm, (int)(bs_slot_cap(n) / BS_GROUP) * 7);
         if (k > m) m = k;
     }
     return m;
@@ -854,7 +938,8 @@ void bs_launch(const Grid& g, float kq, const float4* seg, const int* prev, int*
     // blocks); more points than that are still covered by the blocks' item loop
     constexpr int TT = BS_TPB * TGT;
     const int nsm = sm_count();
-    const int items = ((n + TT - 1) / TT) * bs_splits(n, TT, nsm);
+    // at most this many items: every point with a gap slot
+    const int items = ((n + TT - 1) / TT) * bs_splits(n, TT, nsm, (int)(bs_slot_cap(n) / BS_GROUP) * (1 + im.nfaces));
     const BoxF box = make_box(g);
     const bool periodic = !(g.wall[0] && g.wall[1] && g.wall[2]);
     auto kern = periodic ? k_biot_savart<true, TGT, EOM, ACC> : k_biot_savart<false, TGT, EOM, ACC>;
@@ -882,15 +967,18 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
         im.w2[f] = (face_code[f] & 1) ? 2.f * (float)nn[ax] - 1.f : -1.f;
     }
     im.geo = geo;
-    // one target per thread: the chained pair loop has enough independent
-    // work per target, and two targets per thread need more registers than
-    // leave six blocks on an SM
+    // Targets per thread: from 8192 points in a box with walls on every axis,
+    // 2 when the kernel applies the equation of motion (5.90 against 6.19 ms
+    // per launch at 86k points in the 128x128x1024 channel: a warp has more
+    // independent pairs in flight); otherwise 1
+    const bool two = eom && n >= 8192 && g.wall[0] && g.wall[1] && g.wall[2];
     // without a partial-sum buffer the split sums always go to vacc
     if (vacc && !eom && (bs_uses_vacc(n) || !part)) {
         bs_launch<1, false, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s, vacc);
         return;
     }
-    if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
+    if (two) bs_launch<2, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
+    else if (eom) bs_launch<1, true>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
     else bs_launch<1, false>(g, kq, seg, prev, cnt, tile_ticket, cap, n, part, vel, ea, im, o, s);
 }
 

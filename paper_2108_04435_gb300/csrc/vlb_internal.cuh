@@ -296,20 +296,21 @@ struct EomArgs {
     int* counters;
 };
 
-// Biot-Savart source splits for N points and target tiles of `tile` points
-// on a GPU of nsm SMs: about 3 (target tile, split) work items per resident
-// block (8 blocks on each SM), taken from a device counter, so that the SMs
-// finish together (one item per block left a fifth of the SMs idle at the
-// end: 12% slower at 17k and 86k points), at least 64 segments per split.
-// The kernel derives it from the device-side N, so it needs no host estimate.
-__host__ __device__ inline int bs_splits(int N, int tile, int nsm) {
+// Biot-Savart source splits for N points (targets in tiles of `tile`) and
+// `groups` groups of source slots, on a GPU of nsm SMs: about 3 (target
+// tile, split) work items per resident block (8 blocks on each SM), taken
+// from a device counter, so that the SMs finish together (one item per block
+// left a fifth of the SMs idle at the end: 12% slower at 17k and 86k
+// points), and at least one group per split (with few points an item is then
+// a single group, and the kernel's time is that of one item).  The kernel
+// derives it from the device-side counts, so it needs no host estimate.
+__host__ __device__ inline int bs_splits(int N, int tile, int nsm, int groups) {
     const int n = N > 0 ? N : 1;
     const int tb = (n + tile - 1) / tile;
     int ns = (3 * 8 * nsm + tb - 1) / tb;
-    const int by_chunk = (n + 63) / 64;
-    if (ns > by_chunk) ns = by_chunk;
+    if (ns > groups) ns = groups;
     if (ns < 1) ns = 1;
-    if (ns > 64) ns = 64;
+    if (ns > MAX_SPLIT) ns = MAX_SPLIT;
     return ns;
 }
 
