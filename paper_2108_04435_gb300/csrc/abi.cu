@@ -255,7 +255,9 @@ BsOrder bs_order(vlb_channel* ch) {
     o.ord = ch->d.bs_ord;
     o.rank = ch->d.bs_rank;
     o.slot = ch->d.bs_slot;
+    o.pt = ch->d.bs_pt;
     o.org = ch->d.bs_org;
+    o.tgt = ch->d.bs_tgt;
     return o;
 }
 
@@ -268,8 +270,7 @@ void bs_sort(vlb_channel* ch, const BsOrder& o, cudaStream_t s) {
     if (o.sorted)
         launch_bs_sort(ch->vp.g, d.pos[ch->cur_p], ch->cap, span, d.counters, d.bs_key, d.bs_tmp, d.bs_ord,
                        d.bs_rank, d.bs_cnt, d.bs_start, s);
-    launch_bs_slots(d.pos[ch->cur_p], d.next[ch->cur_p], ch->cap, span, d.counters, o, d.bs_bsum, d.seg,
-                    ch->vp.nfaces, s);
+    launch_bs_slots(d.pos[ch->cur_p], d.next[ch->cur_p], ch->cap, span, d.counters, o, d.bs_bsum, s);
 }
 
 void vfm_pre(vlb_channel* ch, cudaStream_t s) {
@@ -278,8 +279,8 @@ void vfm_pre(vlb_channel* ch, cudaStream_t s) {
     const int* prev = d.prev[ch->cur_p];
     const BsOrder o = bs_order(ch);
     bs_sort(ch, o, s);
-    launch_geometry_stage(V, d.pos[ch->cur_p], d.next[ch->cur_p], prev, d.counters, ch->cap, d.geo, d.seg, d.s0, o,
-                          s);
+    launch_geometry_stage(V, d.pos[ch->cur_p], d.next[ch->cur_p], prev, d.counters, ch->cap,
+                          point_span(ch->n_hint, ch->cap), d.geo, d.seg, d.s0, o, s);
     launch_biot_savart(V.g, V.kappa, d.seg, prev, d.counters, d.tile_ticket, ch->cap, ch->n_hint, d.bsp, d.vbs, s, o,
                        nullptr, V.nfaces, V.face_code, d.geo, d.vacc);
 }
@@ -330,8 +331,8 @@ void vfm_step(vlb_channel* ch, bool pre_done, cudaStream_t s) {
                 continue;
             }
             if (sub == 0 && stage == 0) bs_sort(ch, o, s);
-            launch_geometry_stage(V, stage == 0 ? ea.pos_out : d.st, next, prev, d.counters, ch->cap, d.geo, d.seg,
-                                  stage == 0 ? d.s0 : nullptr, o, s);
+            launch_geometry_stage(V, stage == 0 ? ea.pos_out : d.st, next, prev, d.counters, ch->cap,
+                                  point_span(ch->n_hint, ch->cap), d.geo, d.seg, stage == 0 ? d.s0 : nullptr, o, s);
             const bool timed = ch->timing && s == ch->stream;
             if (timed) record_event(ch, VLB_TIMED_BIOT_SAVART);
             if (fused_eom(ch->n_hint)) {
@@ -469,6 +470,8 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
     int* ord = (int*)take(sizeof(int) * (size_t)n);
     int* rank = (int*)take(sizeof(int) * (size_t)n);
     int* slot = (int*)take(sizeof(int) * (size_t)n);
+    int* pt = (int*)take(sizeof(int) * slots);
+    float4* tgt = (float4*)take(sizeof(float4) * 4 * (size_t)n);
     int4* org = (int4*)take(sizeof(int4) * (slots / BS_GROUP));
     int* cnt = (int*)take(sizeof(int) * BS_SORT_MAX_BINS);
     int* start = (int*)take(sizeof(int) * BS_SORT_MAX_BINS);
@@ -480,7 +483,9 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
     o.ord = ord;
     o.rank = rank;
     o.slot = slot;
+    o.pt = pt;
     o.org = org;
+    o.tgt = tgt;
     if (o.sorted) cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)bs_bins(g.nx, g.ny, g.nz).K, s);
     cudaMemsetAsync(vacc, 0, sizeof(long long) * 3 * (size_t)n, s);
     launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, o, key, tmp, cnt, start, bsum, s);
@@ -520,7 +525,7 @@ size_t vlb_channel_bytes(const vlb_params* p) {
     b += up(12 * cap * (size_t)bs_max_splits((int)cap, sm_count())) + up(12 * cap) + up(24 * cap) +
          up(4 * ((cap + 127) / 128));
     b += 5 * up(4 * cap) + up(16 * (capg / BS_GROUP)) + 2 * up(4 * (size_t)bs_bins(p->n[0], p->n[1], p->n[2]).K) +
-         up(4 * BS_SLOT_BLOCKS);
+         up(4 * BS_SLOT_BLOCKS) + up(4 * capg) + up(64 * cap);
     b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(16 * cap) + up(8 * cap);
     const size_t nc = cap / 2 + 1;
     b += 4 * up(4 * nc) + up(8 * nc) + up(4 * cap) + up(8 * ((cap + 255) / 256));
@@ -698,6 +703,8 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.bs_rank = (int*)A(sizeof(int) * (size_t)cap);
     d.bs_org = (int4*)A(sizeof(int4) * (capg / BS_GROUP));
     d.bs_slot = (int*)A(sizeof(int) * (size_t)cap);
+    d.bs_pt = (int*)A(sizeof(int) * capg);
+    d.bs_tgt = (float4*)A(sizeof(float4) * 4 * (size_t)cap);
     d.bs_bsum = (int*)A(sizeof(int) * BS_SLOT_BLOCKS);
     d.bs_cnt = (int*)A(sizeof(int) * (size_t)bins.K);
     d.bs_start = (int*)A(sizeof(int) * (size_t)bins.K);

@@ -144,23 +144,20 @@ struct BsGroup {
 
 // Integer origin of the group of slot j, mirrored onto the image side for an
 // image block: x_a -> w2 - x_a on the face axis a.  Returns the block index
-// (0: the segments, 1 + face: their images); jump: the group's chain flag.
+// (0: the segments, 1 + face: their images).
 struct BsImages {
     int nfaces;
     int face_code[6];
     float w2[6];         // twice the coordinate of the face
-    const float4* geo;   // pinned-end wall codes (+1) in geo[2i + 1].w
 };
 
-__device__ __forceinline__ int group_origin(const BsOrder& o, const BsImages& im, long long Np, int j, float O[3],
-                                           bool* jump = nullptr) {
+__device__ __forceinline__ int group_origin(const BsOrder& o, const BsImages& im, long long Np, int j, float O[3]) {
     const int f = (int)(j / Np);
     const int kk = (int)(j - (long long)f * Np);
     const int4 g = o.org[kk / BS_GROUP];
     O[0] = (float)g.x;
     O[1] = (float)g.y;
     O[2] = (float)g.z;
-    if (jump) *jump = g.w != 0;
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         if (q + 1 != f) continue;
@@ -173,35 +170,24 @@ __device__ __forceinline__ int group_origin(const BsOrder& o, const BsImages& im
     return f;
 }
 
-// Target at sorted position k of N (none when k >= N): the point of the
-// slot slot[k].
-__device__ __forceinline__ BsTarget bs_target(const float4* __restrict__ seg, const int* __restrict__ prev,
-                                              const BsOrder& o, const BsImages& im, long long Np, int N, int k) {
+// Target at sorted position k of N (none when k >= N), from its target
+// record (four 16-byte loads).
+__device__ __forceinline__ BsTarget bs_target(const BsOrder& o, int N, int k) {
     BsTarget t;
 #pragma unroll
     for (int a = 0; a < 3; ++a) t.h[a] = t.l[a] = t.O[a] = t.v[a] = 0.f;
     t.self = t.prev = t.excl = -1;
     t.i = -1;
     if (k < N) {
-        const int sl = o.slot[k];
-        const float* r = reinterpret_cast<const float*>(seg);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            t.h[a] = r[bs_value_index(sl, a)];
-            t.l[a] = r[bs_value_index(sl, 10 + a)];
-        }
-        group_origin(o, im, Np, sl, t.O);
-        const int i = o.sorted ? o.ord[k] : k;
-        t.i = i;
-        t.self = sl;
-        const int p = prev[i];
-        t.prev = p >= 0 ? o.slot[o.sorted ? o.rank[p] : p] : -1;
-        if (im.nfaces > 0) {
-            const int pin = (int)im.geo[2LL * i + 1].w - 1;
-#pragma unroll
-            for (int f = 0; f < 6; ++f)
-                if (f < im.nfaces && im.face_code[f] == pin) t.excl = (int)((1 + f) * Np) + (p < 0 ? sl : t.prev);
-        }
+        const float4* r = o.tgt + 4LL * k;
+        const float4 a = r[0], b = r[1], c = r[2], e = r[3];
+        t.h[0] = a.x; t.h[1] = a.y; t.h[2] = a.z;
+        t.l[0] = a.w; t.l[1] = b.x; t.l[2] = b.y;
+        t.O[0] = b.z; t.O[1] = b.w; t.O[2] = c.x;
+        t.self = __float_as_int(c.y);
+        t.prev = __float_as_int(c.z);
+        t.excl = __float_as_int(c.w);
+        t.i = __float_as_int(e.x);
     }
     return t;
 }
@@ -538,40 +524,17 @@ __device__ __forceinline__ void bs_fill(const BsSmem& sm, const float4* seg, uin
     issue_tile(sm.tile[b], seg, jb, min(BS_TILE, j1 - jb), &sm.full[b]);
 }
 
-// Box, origin and sign of one group of slots (computed by every warp for
-// itself): lane l takes pair l.  A group whose chain jumps by a periodic box
-// gets an unbounded box, which sends it to the full-precision path (as a
-// near group).
+// Box, origin and sign of one group of slots.  The box was stored by the
+// stage geometry in values 13-15 of slots 0 and 1 (the x halves of pairs 0
+// and 1); a group whose chain jumps by a periodic box has an unbounded one,
+// which sends it to the full-precision path (as a near group).
 __device__ __forceinline__ BsGroup group_box(const float4* __restrict__ T, int j, const BsOrder& o,
                                              const BsImages& im, long long Np) {
-    const int lane = threadIdx.x & 31;
     BsGroup G;
-    float lo[3], hi[3];
-    const float4 q0 = T[8 * lane], q1 = T[8 * lane + 1];
-    lo[0] = fminf(q0.x, q0.y); hi[0] = fmaxf(q0.x, q0.y);
-    lo[1] = fminf(q0.z, q0.w); hi[1] = fmaxf(q0.z, q0.w);
-    lo[2] = fminf(q1.x, q1.y); hi[2] = fmaxf(q1.x, q1.y);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
-            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
-        }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        G.lo[a] = lo[a];
-        G.hi[a] = hi[a];
-    }
-    bool jump;
-    G.sign = group_origin(o, im, Np, j, G.O, &jump) > 0 ? -1.f : 1.f;
-    if (jump) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            G.lo[a] = -3.0e38f;
-            G.hi[a] = 3.0e38f;
-        }
-    }
+    const float4 a6 = T[6], a7 = T[7], b6 = T[8 + 6], b7 = T[8 + 7];
+    G.lo[0] = a6.z; G.lo[1] = a7.x; G.lo[2] = a7.z;
+    G.hi[0] = b6.z; G.hi[1] = b7.x; G.hi[2] = b7.z;
+    G.sign = group_origin(o, im, Np, j, G.O) > 0 ? -1.f : 1.f;
     return G;
 }
 
@@ -688,7 +651,7 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
             for (int k = 0; k < min(NST, ntiles); ++k) bs_fill(sm, seg, q + (uint32_t)k, j0, j1, k);
         BsTarget t[TGT];
 #pragma unroll
-        for (int u = 0; u < TGT; ++u) t[u] = bs_target(seg, prev, o, im, Np, N, tb * TT + threadIdx.x * TGT + u);
+        for (int u = 0; u < TGT; ++u) t[u] = bs_target(o, N, tb * TT + threadIdx.x * TGT + u);
         for (int tt = 0; tt < ntiles; ++tt) {
             const uint32_t qt = q + (uint32_t)tt;
             const int b = (int)(qt % NST);
@@ -837,24 +800,45 @@ __global__ void k_bs_prev(const int* __restrict__ next, int n, int* __restrict__
     if (q >= 0) prev[q] = i;
 }
 
-// Stand-alone entry: the source slots of a caller's point set (positions
-// [3][n]), one thread per point.
+// Stand-alone entry: the source slots and target records of a caller's
+// point set (positions [3][n]), one block per group of slots as in the
+// stage geometry.
 __global__ void __launch_bounds__(BS_GROUP) k_bs_points(Grid g, const double* __restrict__ pos,
-                                                        const int* __restrict__ next, int n,
-                                                        const int* __restrict__ counters, float4* __restrict__ seg,
-                                                        BsOrder o) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int q = bs_checked_next(next, n, i);
-    double si[3], sq[3];
-    float b[3];
-    for (int a = 0; a < 3; ++a) {
-        si[a] = pos[(long long)a * n + i];
-        sq[a] = q >= 0 ? pos[(long long)a * n + q] : si[a];
-        b[a] = q >= 0 ? __double2float_rn(min_image(g, a, sq[a] - si[a])) : 0.f;
+                                                        const int* __restrict__ next, const int* __restrict__ prev,
+                                                        int n, const int* __restrict__ counters,
+                                                        float4* __restrict__ seg, BsOrder o) {
+    __shared__ BsGroupSmem sm;
+    const int ns = counters[CNT_NSLOT];
+    const long long Np = bs_block(ns);
+    const int ng = (int)(Np / BS_GROUP);
+    for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
+        const int sl = grp * BS_GROUP + threadIdx.x;
+        const int code = sl < ns ? o.pt[sl] : -1;
+        const int4 og = o.org[grp];
+        const double O[3] = {(double)og.x, (double)og.y, (double)og.z};
+        double rel[3] = {0.0, 0.0, 0.0};
+        float d[3] = {0.f, 0.f, 0.f};
+        bool jump = false;
+        if (code >= 0) {
+            const int q = bs_checked_next(next, n, code);
+            for (int a = 0; a < 3; ++a) {
+                const double si = pos[(long long)a * n + code];
+                rel[a] = min_image(g, a, si - O[a]);
+                if (q >= 0) {
+                    const double sq = pos[(long long)a * n + q];
+                    const double b = min_image(g, a, sq - si);
+                    d[a] = __double2float_rn(b);
+                    if (threadIdx.x != BS_GROUP - 1) jump |= fabs(min_image(g, a, sq - O[a]) - (rel[a] + b)) > 0.5;
+                }
+            }
+            bs_write_target(o.tgt, o.sorted ? o.rank[code] : code, rel, og, sl, bs_prev_slot(o, prev[code]), -1,
+                            code);
+        } else if (code <= -2) {
+            const int q = bs_checked_next(next, n, -2 - code);
+            for (int a = 0; a < 3; ++a) rel[a] = min_image(g, a, pos[(long long)a * n + q] - O[a]);
+        }
+        bs_write_group(0, nullptr, Np, grp, rel, d, jump, seg, sm);
     }
-    const BsPointSlots ps = bs_point_slots(o, o.sorted ? o.rank[i] : i, q);
-    bs_write_point_slots(g, o, ps, bs_block(counters[CNT_NSLOT]), 0, 0, si, sq, b, q >= 0, seg);
 }
 
 __global__ void k_bs_counters(int* __restrict__ counters, int n) {
@@ -966,7 +950,6 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
         const int ax = face_code[f] >> 1;
         im.w2[f] = (face_code[f] & 1) ? 2.f * (float)nn[ax] - 1.f : -1.f;
     }
-    im.geo = geo;
     // Targets per thread: from 8192 points in a box with walls on every axis,
     // 2 when the kernel applies the equation of motion (5.90 against 6.19 ms
     // per launch at 86k points in the 128x128x1024 channel: a warp has more
@@ -992,8 +975,8 @@ void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next
     if (o.sorted)
         launch_bs_sort(g, pos, n, n, counters, key, tmp, const_cast<int*>(o.ord), const_cast<int*>(o.rank), cnt,
                        start, s);
-    launch_bs_slots(pos, next, n, n, counters, o, bsum, seg, 0, s);
-    k_bs_points<<<(n + BS_GROUP - 1) / BS_GROUP, BS_GROUP, 0, s>>>(g, pos, next, n, counters, seg, o);
+    launch_bs_slots(pos, next, n, n, counters, o, bsum, s);
+    k_bs_points<<<(int)(bs_slot_cap(n) / BS_GROUP), BS_GROUP, 0, s>>>(g, pos, next, prev, n, counters, seg, o);
 }
 
 void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s) {
@@ -1013,7 +996,7 @@ void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s) {
 namespace {
 
 constexpr int NOALLOC_MAX_POINTS = 65536;
-constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(12) << 20;
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(17) << 20;
 // the scratch of the stand-alone entry grows linearly with the point count,
 // so the array holds every call up to the point limit
 static_assert(vlb::bs_scratch_bytes(NOALLOC_MAX_POINTS) <= NOALLOC_SCRATCH_BYTES,

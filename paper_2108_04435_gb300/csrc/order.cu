@@ -8,8 +8,9 @@
 // Then, in any order, the source slots: every sorted position k takes slot
 // k + (gap slots before it), a gap slot following k when the successor of
 // its point is not the point at k + 1; a two-kernel scan (gap counts per
-// block, then each block's prefix from the counts before it).  Group g of
-// BS_GROUP slots gets the integer origin of its first slot's point.
+// block, then each block's prefix from the counts before it), which also
+// records what every slot holds.  Group g of BS_GROUP slots gets the integer
+// origin of its first slot's point.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -190,8 +191,7 @@ __device__ __forceinline__ int4 cell_of(const double* __restrict__ pos, int cap,
 
 __global__ void __launch_bounds__(1024) k_slot_assign(const double* __restrict__ pos, const int* __restrict__ next,
                                                       int cap, int* __restrict__ counters, BsOrder o,
-                                                      const int* __restrict__ bsum, float4* __restrict__ seg,
-                                                      int nfaces) {
+                                                      const int* __restrict__ bsum) {
     pdl_wait_trigger();
     __shared__ int warp_sum[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -227,6 +227,8 @@ __global__ void __launch_bounds__(1024) k_slot_assign(const double* __restrict__
             const int sl = k + carry + (x - gap) + (w > 0 ? warp_sum[w - 1] : 0);
             slot[k] = sl;
             const int i = bs_point_at(o, k);
+            o.pt[sl] = i;
+            if (gap) o.pt[sl + 1] = -2 - i;
             if (sl % BS_GROUP == 0) o.org[sl / BS_GROUP] = cell_of(pos, cap, i);
             if (gap && (sl + 1) % BS_GROUP == 0) o.org[(sl + 1) / BS_GROUP] = cell_of(pos, cap, next[i]);
         }
@@ -234,16 +236,11 @@ __global__ void __launch_bounds__(1024) k_slot_assign(const double* __restrict__
         __syncthreads();  // warp_sum is rewritten by the next round
     }
     if (blockIdx.x != gridDim.x - 1) return;
-    // the last block: the slot count and zero padding slots up to whole groups
+    // the last block: the slot count, padding up to a whole group
     const int ns = N + carry;
     if (threadIdx.x == 0) counters[CNT_NSLOT] = ns;
-    const long long Np = bs_block(ns);
-    const int npad = (int)(Np - ns);
-    float* r = reinterpret_cast<float*>(seg);
-    for (int e = threadIdx.x; e < npad * 16 * (1 + nfaces); e += blockDim.x) {
-        const int f = e / (npad * 16), rem = e - f * npad * 16;
-        r[bs_value_index((long long)f * Np + ns + rem / 16, rem % 16)] = 0.f;
-    }
+    const int npad = (int)(bs_block(ns) - ns);
+    if ((int)threadIdx.x < npad) o.pt[ns + threadIdx.x] = -1;
 }
 
 }  // namespace
@@ -260,11 +257,11 @@ void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const i
 }
 
 void launch_bs_slots(const double* pos, const int* next, int cap, int span, int* counters, const BsOrder& o,
-                     int* bsum, float4* seg, int nfaces, cudaStream_t s) {
+                     int* bsum, cudaStream_t s) {
     int blocks = (span + 1023) / 1024;
     blocks = blocks < 1 ? 1 : (blocks > BS_SLOT_BLOCKS ? BS_SLOT_BLOCKS : blocks);
     launch_pdl(k_slot_count, blocks, 1024, 0, s, next, (const int*)counters, o, bsum);
-    launch_pdl(k_slot_assign, blocks, 1024, 0, s, pos, next, cap, counters, o, (const int*)bsum, seg, nfaces);
+    launch_pdl(k_slot_assign, blocks, 1024, 0, s, pos, next, cap, counters, o, (const int*)bsum);
 }
 
 }  // namespace vlb

@@ -1,5 +1,6 @@
-// Biot-Savart source slots (layout in vlb_internal.cuh): written by the
-// stage geometry (vfm.cu) and by the stand-alone entry (bs.cu).
+// Biot-Savart source slots and target records (layouts in vlb_internal.cuh):
+// written group by group by the stage geometry (vfm.cu) and by the
+// stand-alone entry (bs.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,79 +33,108 @@ __device__ __forceinline__ void bs_slot_values(const double rel[3], const float 
     for (int a = 0; a < 3; ++a) val[13 + a] = __double2float_rn(rel[a] + (double)d[a]);
 }
 
-// Store slot k (scalar stores: the other slot of its pair belongs to another
-// thread).
-__device__ __forceinline__ void bs_store_slot(float4* __restrict__ seg, long long k, const float val[16]) {
-    float* r = reinterpret_cast<float*>(seg);
-#pragma unroll
-    for (int v = 0; v < 16; ++v) r[bs_value_index(k, v)] = val[v];
-}
-
-// Where the slots of one point go: its own slot k in the origin O of its
-// group, and with `gap` the gap slot k + 1 (holding the successor) in the
-// origin Og of that slot's group.
-struct BsPointSlots {
-    long long k;
-    bool gap;
-    double O[3], Og[3];
-};
-
-// Slots of the point at sorted position kk (point i, successor q or -1).
-__device__ __forceinline__ BsPointSlots bs_point_slots(const BsOrder& o, int kk, int q) {
-    BsPointSlots p;
-    p.k = o.slot[kk];
-    const int qk = q >= 0 ? (o.sorted ? o.rank[q] : q) : -1;
-    p.gap = q >= 0 && o.slot[qk] != p.k + 1;
-    const int4 a = o.org[p.k / BS_GROUP];
-    p.O[0] = a.x; p.O[1] = a.y; p.O[2] = a.z;
-    // the gap slot's group (the next group when k ends one); without a gap
-    // the next slot of the same group starts the successor's own segment
-    const int4 b = p.gap ? o.org[(p.k + 1) / BS_GROUP] : a;
-    p.Og[0] = b.x; p.Og[1] = b.y; p.Og[2] = b.z;
-    return p;
-}
-
-// The slots of one point in record block f (0: the segment si -> si + b;
-// 1 + face: its image across that solid face, M(si) -> M(si) + M(b), with M
-// mirroring the face-axis coordinate x -> w2 - x and the origin with it;
-// the image vortex turns the other way, which the pair sum applies as the
-// block's sign).  sq: the successor's position (for the gap slot).  Flags
-// org[k / BS_GROUP].w when the next slot of the same group would not start
-// where this segment ends (a chain that jumps by a periodic box).
-__device__ __forceinline__ void bs_write_point_slots(const Grid& g, const BsOrder& o, const BsPointSlots& ps,
-                                                     long long Np, int f, int face_code, const double si[3],
-                                                     const double sq[3], const float b[3], bool has_seg,
-                                                     float4* __restrict__ seg) {
-    const int ax = f > 0 ? face_code >> 1 : -1;
-    double rel[3], relq[3];
-    float d[3];
+// The target record of the point at sorted position k (slot sl, parts h + l
+// of its position in the group origin O, predecessor's slot, excluded image
+// slot of a pinned end, point index i).
+__device__ __forceinline__ void bs_write_target(float4* __restrict__ tgt, int k, const double rel[3], const int4& O,
+                                                int sl, int prev_sl, int excl, int i) {
+    float h[3], l[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (a == ax) {
-            // mirrored origin w2 - O and point w2 - x: the difference is O - x
-            rel[a] = ps.O[a] - si[a];
-            relq[a] = ps.Og[a] - sq[a];
-            d[a] = -b[a];
-        } else {
-            rel[a] = min_image(g, a, si[a] - ps.O[a]);
-            relq[a] = min_image(g, a, sq[a] - ps.Og[a]);
-            d[a] = b[a];
-        }
+        h[a] = __double2float_rn(rel[a]);
+        l[a] = __double2float_rn(rel[a] - (double)h[a]);
     }
+    float4* r = tgt + 4LL * k;
+    r[0] = make_float4(h[0], h[1], h[2], l[0]);
+    r[1] = make_float4(l[1], l[2], (float)O.x, (float)O.y);
+    r[2] = make_float4((float)O.z, __int_as_float(sl), __int_as_float(prev_sl), __int_as_float(excl));
+    r[3] = make_float4(__int_as_float(i), 0.f, 0.f, 0.f);
+}
+
+// Slot of the predecessor's segment (-1 for none).
+__device__ __forceinline__ int bs_prev_slot(const BsOrder& o, int p) {
+    return p >= 0 ? o.slot[o.sorted ? o.rank[p] : p] : -1;
+}
+
+// Shared memory of the group writer: one group's records in their stored
+// layout, and the two warps' box partials.
+struct BsGroupSmem {
+    float stage[BS_GROUP * 16];
+    float red[2][6];
+};
+
+// One group of slots, written by one block of BS_GROUP threads, thread t =
+// slot t of group grp: rel = its point relative to the group origin (FP64),
+// d = its segment (zero for gap and padding slots), jump = the chain jumps
+// by a periodic box between this slot and the next.  Writes the records of
+// every record block (the segments, then one block per solid face:
+// M(s) -> M(s) + M(d) with M mirroring the face axis, so each mirrored
+// value is the direct one negated on that axis, exactly), with the group's
+// box of h in the spare values 13-15 of slots 0 and 1 (low, high corner;
+// unbounded when the chain jumps somewhere, which sends the group to the
+// full-precision path), through shared memory in whole 16-byte stores.
+__device__ __forceinline__ void bs_write_group(int nfaces, const int* face_code, long long Np, int grp,
+                                               const double rel[3], const float d[3], bool jump, float4* seg,
+                                               BsGroupSmem& sm) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     float val[16];
     bs_slot_values(rel, d, val);
-    bs_store_slot(seg, (long long)f * Np + ps.k, val);
-    if (f == 0 && has_seg && (ps.k % BS_GROUP) != BS_GROUP - 1) {
-        // the next slot (same group, origin O = Og) starts at min_image(sq - O)
-        bool jump = false;
+    float lo[3] = {val[0], val[1], val[2]}, hi[3] = {val[0], val[1], val[2]};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) jump |= fabs(relq[a] - (rel[a] + (double)b[a])) > 0.5;
-        if (jump) atomicOr(&o.org[ps.k / BS_GROUP].w, 1);
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            sm.red[w][a] = lo[a];
+            sm.red[w][3 + a] = hi[a];
+        }
+    const bool anyjump = __syncthreads_or(jump);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = anyjump ? -3.0e38f : fminf(sm.red[0][a], sm.red[1][a]);
+        hi[a] = anyjump ? 3.0e38f : fmaxf(sm.red[0][3 + a], sm.red[1][3 + a]);
     }
-    if (ps.gap) {
-        const float z[3] = {0.f, 0.f, 0.f};
-        bs_slot_values(relq, z, val);
-        bs_store_slot(seg, (long long)f * Np + ps.k + 1, val);
+    for (int f = 0; f <= nfaces; ++f) {
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = val[q];
+        float blo[3] = {lo[0], lo[1], lo[2]}, bhi[3] = {hi[0], hi[1], hi[2]};
+        if (f > 0) {
+            const int ax = face_code[f - 1] >> 1;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a != ax) continue;
+                v[a] = -v[a];
+                v[4 + a] = -v[4 + a];
+                v[10 + a] = -v[10 + a];
+                v[13 + a] = -v[13 + a];
+                const float l0 = blo[a];
+                blo[a] = -bhi[a];
+                bhi[a] = -l0;
+            }
+            v[7] = v[1] * v[6] - v[2] * v[5];
+            v[8] = v[2] * v[4] - v[0] * v[6];
+            v[9] = v[0] * v[5] - v[1] * v[4];
+        }
+        if (t == 0) {
+            v[13] = blo[0]; v[14] = blo[1]; v[15] = blo[2];
+        } else if (t == 1) {
+            v[13] = bhi[0]; v[14] = bhi[1]; v[15] = bhi[2];
+        }
+        // value q of slot t at (t % 32) * 32 + 2 q + (t / 32) of the group
+#pragma unroll
+        for (int q = 0; q < 16; ++q) sm.stage[lane * 32 + 2 * q + w] = v[q];
+        __syncthreads();
+        float4* dst = seg + ((long long)f * Np + (long long)grp * BS_GROUP) * BS_REC;
+        const float4* src = reinterpret_cast<const float4*>(sm.stage);
+#pragma unroll
+        for (int e = 0; e < BS_REC; ++e) dst[e * BS_GROUP + t] = src[e * BS_GROUP + t];
+        __syncthreads();  // the stage is rewritten for the next block
     }
 }
 

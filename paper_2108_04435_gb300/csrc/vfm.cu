@@ -24,7 +24,8 @@ namespace {
 // line's last point starts no segment.  The source slots go where the slots
 // of the order o put them.
 struct StageRec {
-    int q;         // successor, -1 at a line's last point
+    int p, q;      // predecessor and successor, -1 at a line's first / last point
+    int pin;       // wall code of a pinned end, -1 otherwise
     double si[3];  // the point
     double st[3];  // its successor (itself at a line's last point)
     float b[3];    // the segment (zero at a line's last point)
@@ -92,7 +93,9 @@ __device__ __forceinline__ void geometry_point(const VfmParams& P, const double*
     geo[2LL * i] = make_float4(t1[0], t1[1], t1[2], dxi);
     geo[2LL * i + 1] = make_float4(fl * (float)ab[0], fl * (float)ab[1], fl * (float)ab[2], (float)(code + 1));
     if (q < 0) b[0] = b[1] = b[2] = 0.f;  // no segment leaves a line's last point
+    out.p = p;
     out.q = q;
+    out.pin = code;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         out.si[a] = si[a];
@@ -101,9 +104,12 @@ __device__ __forceinline__ void geometry_point(const VfmParams& P, const double*
     }
 }
 
-// One thread per point; thread 0 also resets the work counter of the
-// Biot-Savart launch that follows.  The slots' padding is written by the
-// slot assignment at the step's start.
+// One block per group of source slots, thread t for slot t of the group:
+// the slot's point (its stage geometry, its target record and its slot), a
+// gap slot's copy of a successor, or a zero padding slot; the group's
+// records of every record block then go out together (records.cuh).
+// Block 0 also resets the work counter of the Biot-Savart launch that
+// follows.
 __global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const double* __restrict__ s,
                                                              const int* __restrict__ next,
                                                              const int* __restrict__ prev,
@@ -111,16 +117,43 @@ __global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const 
                                                              float4* __restrict__ geo, float4* __restrict__ seg,
                                                              double* __restrict__ s0_copy, BsOrder o) {
     pdl_wait_trigger();
+    __shared__ BsGroupSmem sm;
     const int N = counters[CNT_N];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch that follows takes items from 0
-    if (i >= N) return;
-    const long long Np = bs_block(counters[CNT_NSLOT]);
-    StageRec r;
-    geometry_point(P, s, next, prev, N, cap, i, geo, s0_copy, r);
-    const BsPointSlots ps = bs_point_slots(o, o.sorted ? o.rank[i] : i, r.q);
-    for (int f = 0; f <= P.nfaces; ++f)
-        bs_write_point_slots(P.g, o, ps, Np, f, f > 0 ? P.face_code[f - 1] : 0, r.si, r.st, r.b, r.q >= 0, seg);
+    const int ns = counters[CNT_NSLOT];
+    const long long Np = bs_block(ns);
+    if (blockIdx.x == 0 && threadIdx.x == 0) counters[CNT_BSWORK] = 0;  // the Biot-Savart launch takes items from 0
+    const int ng = (int)(Np / BS_GROUP);
+    for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
+        const int sl = grp * BS_GROUP + threadIdx.x;
+        const int code = sl < ns ? o.pt[sl] : -1;
+        const int4 og = o.org[grp];
+        const double O[3] = {(double)og.x, (double)og.y, (double)og.z};
+        double rel[3] = {0.0, 0.0, 0.0};
+        float d[3] = {0.f, 0.f, 0.f};
+        bool jump = false;
+        if (code >= 0) {
+            StageRec r;
+            geometry_point(P, s, next, prev, N, cap, code, geo, s0_copy, r);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                rel[a] = min_image(P.g, a, r.si[a] - O[a]);
+                d[a] = r.b[a];
+                // the next slot of the group holds the successor at min_image(s_q - O)
+                if (r.q >= 0 && threadIdx.x != BS_GROUP - 1)
+                    jump |= fabs(min_image(P.g, a, r.st[a] - O[a]) - (rel[a] + (double)r.b[a])) > 0.5;
+            }
+            const int prev_sl = bs_prev_slot(o, r.p);
+            int excl = -1;
+            for (int f = 0; f < P.nfaces; ++f)
+                if (r.pin >= 0 && P.face_code[f] == r.pin) excl = (int)((1 + f) * Np) + (r.p < 0 ? sl : prev_sl);
+            bs_write_target(o.tgt, o.sorted ? o.rank[code] : code, rel, og, sl, prev_sl, excl, code);
+        } else if (code <= -2) {
+            const int q = next[-2 - code];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) rel[a] = min_image(P.g, a, s[(long long)a * cap + q] - O[a]);
+        }
+        bs_write_group(P.nfaces, P.face_code, Np, grp, rel, d, jump, seg, sm);
+    }
 }
 
 // The equation of motion of each point as a kernel of its own (used when the
@@ -210,10 +243,11 @@ __global__ void k_line_profile(Grid g, const double* __restrict__ pos, const int
 }  // namespace
 
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
-                           int cap, float4* geo, float4* seg, double* s0_copy, const BsOrder& o, cudaStream_t st) {
+                           int cap, int span, float4* geo, float4* seg, double* s0_copy, const BsOrder& o,
+                           cudaStream_t st) {
     if (cap <= 0) return;
-    launch_pdl(k_geometry_stage, (cap + BS_GROUP - 1) / BS_GROUP, BS_GROUP, 0, st, P, s, next, prev, counters, cap,
-               geo, seg, s0_copy, o);
+    launch_pdl(k_geometry_stage, (int)(bs_slot_cap(span) / BS_GROUP), BS_GROUP, 0, st, P, s, next, prev, counters,
+               cap, geo, seg, s0_copy, o);
 }
 
 void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s, long long* vacc) {

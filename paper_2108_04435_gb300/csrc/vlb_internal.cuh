@@ -129,7 +129,9 @@ constexpr int BS_SORT_MAX_BINS = 1 << 16;  // bins of the spatial order (bin edg
 //   0-2 h = fl(s - O) (minimum image on periodic axes), 3 |d|^2, 4-6 d,
 //   7-9 c = h x d (FP32), 10-12 l = fl(s - O - h), 13-15 fl(s - O + d), the
 //   segment's end (read for the group's last slot, whose end lies in the
-//   next group);
+//   next group); slots 0 and 1 hold there instead the low and high corner
+//   of the group's box of h (unbounded when the chain jumps by a periodic
+//   box somewhere in the group);
 // h + l carries s - O to ~1e-14 cells.  Gap and padding slots have d = 0.
 // Storage: slot p and slot p + 32 of a group form pair p, interleaved in
 // 128 bytes: value v of slot k is float
@@ -145,16 +147,21 @@ __host__ __device__ inline long long bs_value_index(long long k, int v) {
 
 // Order of the Biot-Savart sources.  sorted = 0: sorted position k is
 // point k; sorted = 1: it is point ord[k] (rank is the inverse), a spatial
-// order.  slot[k] is the slot of sorted position k.  Group g of BS_GROUP
-// slots has the integer origin org[g].xyz; org[g].w is nonzero when its
-// chain jumps by a periodic box somewhere (the slots' minimum images about O
-// then disagree with a segment), and the group takes the full-precision path.
+// order.  slot[k] is the slot of sorted position k, and pt[s] what slot s
+// holds: point i >= 0 (its own slot), -2 - i (a gap slot, holding the
+// successor of point i) or -1 (padding).  Group g of BS_GROUP slots has the
+// integer origin org[g].xyz.  tgt[4k .. 4k + 3] is the target record of
+// sorted position k: its slot's parts h, l, origin O (as floats), its slot,
+// its predecessor's slot, the excluded image slot of a pinned end, and its
+// point index (ints by bit pattern).
 struct BsOrder {
     int sorted;
     const int* ord;
     const int* rank;
     const int* slot;
+    int* pt;
     int4* org;
+    float4* tgt;
 };
 
 // Bins of the spatial order: the cell floor(x) >> shift per axis, clamped to
@@ -344,6 +351,8 @@ struct Dev {
     int* bs_rank;       // point -> sorted position
     int4* bs_org;       // integer origin of each group of BS_GROUP slots (w: jump flag)
     int* bs_slot;       // sorted position -> slot
+    int* bs_pt;         // slot -> its point (or gap, padding) [slot capacity]
+    float4* bs_tgt;     // target records, 4 float4 per sorted position
     int* bs_bsum;       // gap slots per block of the slot scan [BS_SLOT_BLOCKS]
     int* bs_cnt;        // points per bin (zero between sorts)
     int* bs_start;      // bin starts
@@ -391,9 +400,12 @@ void launch_export(const LbmParams& P, const void* f, float* out, int i0, int i1
 void launch_import(const LbmParams& P, const float* in, void* f, int i0, int i1, cudaStream_t s);
 
 // vfm.cu
-// The stage geometry writes the Biot-Savart source records in the order `o`.
+// The stage geometry writes the Biot-Savart source slots and target records
+// of the order `o`, one block per group of slots; span: points one pass
+// covers (the groups of 2 span slots; it strides over any beyond).
 void launch_geometry_stage(const VfmParams& P, const double* s, const int* next, const int* prev, int* counters,
-                           int cap, float4* geo, float4* seg, double* s0_copy, const BsOrder& o, cudaStream_t st);
+                           int cap, int span, float4* geo, float4* seg, double* s0_copy, const BsOrder& o,
+                           cudaStream_t st);
 // vacc != nullptr: the Biot-Savart velocity is read from the fixed-point sums,
 // which the kernel clears again for the next pass.
 void launch_eom(const EomArgs& A, const float* vbs, cudaStream_t s, long long* vacc = nullptr);
@@ -412,12 +424,10 @@ int bs_max_splits(int cap, int nsm);
 void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
                     int* ord, int* rank, int* cnt, int* start, cudaStream_t s);
 // Slots of the order o for the points pos[3][cap] with successors next[]
-// (indices outside [-1, N) count as -1): o.slot, the group origins o.org
-// (jump flags cleared), counters[CNT_NSLOT], and the padding slots of every
-// record block (1 + nfaces blocks of bs_block(nslot) slots).  bsum: scratch
-// [BS_SLOT_BLOCKS].
+// (indices outside [-1, N) count as -1): o.slot, o.pt, the group origins
+// o.org and counters[CNT_NSLOT].  bsum: scratch [BS_SLOT_BLOCKS].
 void launch_bs_slots(const double* pos, const int* next, int cap, int span, int* counters, const BsOrder& o,
-                     int* bsum, float4* seg, int nfaces, cudaStream_t s);
+                     int* bsum, cudaStream_t s);
 // With eom != nullptr the kernel applies the equation of motion to each target
 // tile as soon as its sum is complete, and does not write vel.
 // Sources are the N segments, then with nfaces > 0 their images across each
@@ -450,13 +460,14 @@ void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s);
 
 // Scratch of the stand-alone entry points for n points, each part 256-byte
 // aligned: counters | prev | source slots | sort keys | scattered points |
-// ord | rank | slots | group origins | bin counts | bin starts | slot-scan
-// sums | fixed-point sums.  Non-decreasing in n, so its maximum over n <= m
-// is its value at m.
+// ord | rank | slots | slot contents | target records | group origins | bin
+// counts | bin starts | slot-scan sums | fixed-point sums.  Non-decreasing in
+// n, so its maximum over n <= m is its value at m.
 __host__ __device__ constexpr size_t bs_up256(size_t b) { return (b + 255) & ~size_t(255); }
 __host__ __device__ constexpr size_t bs_scratch_bytes(long long n) {
     return bs_up256(sizeof(int) * CNT_COUNT) + bs_up256(sizeof(int) * (size_t)n) +
            bs_up256(sizeof(float4) * BS_REC * (size_t)bs_slot_cap(n)) + 5 * bs_up256(sizeof(int) * (size_t)n) +
+           bs_up256(sizeof(int) * (size_t)bs_slot_cap(n)) + bs_up256(sizeof(float4) * 4 * (size_t)n) +
            bs_up256(sizeof(int4) * (size_t)(bs_slot_cap(n) / BS_GROUP)) +
            2 * bs_up256(sizeof(int) * (size_t)BS_SORT_MAX_BINS) + bs_up256(sizeof(int) * (size_t)BS_SLOT_BLOCKS) +
            bs_up256(sizeof(long long) * 3 * (size_t)n);
