@@ -260,7 +260,7 @@ int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next,
  * while they run, e.g. hosts that only hand out pre-registered buffers or
  * code that must not trigger the device synchronisation cudaMalloc implies).
  * Same arguments and result as vlb_biot_savart, without the scratch buffer:
- * the scratch lives in a fixed 17 MiB file-scope device array that every GPU
+ * the scratch lives in a fixed 19 MiB file-scope device array that every GPU
  * loading this library holds until the process exits, and no cudaMalloc,
  * cudaFree or allocating library routine is called.  A compile-time check
  * keeps the array at least as large as the scratch of a 65536-point call.

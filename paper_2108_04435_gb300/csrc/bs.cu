@@ -192,6 +192,38 @@ __device__ __forceinline__ BsTarget bs_target(const BsOrder& o, int N, int k) {
     return t;
 }
 
+// A 16-byte load the compiler may not move out of a loop (the target records
+// are read again for every group, so that their values need no registers
+// across the group's pair loop).
+__device__ __forceinline__ float4 ld_reload(const float4* p) {
+    float4 r;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+// The target of sorted position k again from its record (point index i
+// already known; an idle lane, i < 0, reads nothing), with its sum zero.
+__device__ __forceinline__ BsTarget bs_target_reload(const BsOrder& o, int k, int i) {
+    BsTarget t;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t.h[a] = t.l[a] = t.O[a] = t.v[a] = 0.f;
+    t.self = t.prev = t.excl = -1;
+    t.i = i;
+    if (i >= 0) {
+        const float4* r = o.tgt + 4LL * k;
+        const float4 a = ld_reload(r), b = ld_reload(r + 1), c = ld_reload(r + 2);
+        t.h[0] = a.x; t.h[1] = a.y; t.h[2] = a.z;
+        t.l[0] = a.w; t.l[1] = b.x; t.l[2] = b.y;
+        t.O[0] = b.z; t.O[1] = b.w; t.O[2] = c.x;
+        t.self = __float_as_int(c.y);
+        t.prev = __float_as_int(c.z);
+        t.excl = __float_as_int(c.w);
+    }
+    return t;
+}
+
 // The cheap pair path, along the chain of slots of one group.  Slot k's
 // segment runs from its point to slot k + 1's, so with R = h + t at every
 // slot (no low parts), ia = 1/|R| and rho = |R| serve the segment starting
@@ -204,18 +236,26 @@ __device__ __forceinline__ BsTarget bs_target(const BsOrder& o, int N, int k) {
 // group.  A pair p (slots p and p + 32) is evaluated packed (FP32x2), so the
 // group's two halves walk their chains side by side.
 
-// ia and rho at the two slots of pair p, for each target offset t (held in
-// both halves of a float2), and the pair's |d|^2 for its segments.
+// ia and rho at the two slots of pair p, for each target offset t, and the
+// pair's |d|^2 for its segments.  |R|^2 = |h + t|^2 is formed as
+// (|h|^2 + |t|^2) + 2 h.t with |h|^2 from the slot and 2t, |t|^2 per group
+// (t2, tt: held in both halves of a float2): three fused multiply-adds and
+// an add instead of three adds and three multiply-adds.  The group origin
+// sits at the centre of the group's box, so |h| is at most about half its
+// extent, and the far path's distance of 8 cells keeps the cancellation of
+// |t|^2 against 2 h.t to a few float ulps of |R|^2.
 template <int TGT>
-__device__ __forceinline__ void chain_head(const float4* __restrict__ Q, const float2 (&t)[TGT][3],
-                                           float2 (&ia)[TGT], float2 (&rho)[TGT], float2& dd) {
-    const float4 q0 = Q[0], q1 = Q[1];
+__device__ __forceinline__ void chain_head(const float4* __restrict__ Q, const float2 (&t2)[TGT][3],
+                                           const float2 (&tt)[TGT], float2 (&ia)[TGT], float2 (&rho)[TGT],
+                                           float2& dd) {
+    const float4 q0 = Q[0], q1 = Q[1], q8 = Q[8];
     const float2 hx = make_float2(q0.x, q0.y), hy = make_float2(q0.z, q0.w), hz = make_float2(q1.x, q1.y);
+    const float2 hh = make_float2(q8.x, q8.y);
     dd = make_float2(q1.z, q1.w);
 #pragma unroll
     for (int u = 0; u < TGT; ++u) {
-        const float2 rx = __fadd2_rn(hx, t[u][0]), ry = __fadd2_rn(hy, t[u][1]), rz = __fadd2_rn(hz, t[u][2]);
-        const float2 a2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+        const float2 a2 =
+            __ffma2_rn(hz, t2[u][2], __ffma2_rn(hy, t2[u][1], __ffma2_rn(hx, t2[u][0], __fadd2_rn(hh, tt[u]))));
         ia[u] = make_float2(rsqrt_approx(a2.x), rsqrt_approx(a2.y));
         rho[u] = __fmul2_rn(a2, ia[u]);
     }
@@ -250,18 +290,34 @@ __device__ __forceinline__ void chain_segments(const float4* __restrict__ Q, con
 // The chain of one group for TGT targets at offsets t: pair p's segments end
 // at pair p + 1's slots, except slot 31's, which ends at slot 32 (the first
 // pair's other half), and slot 63's, which ends at the end point its record
-// stores (the next slot is in another group).  Returns the sums of fac c and
-// fac d with fac halved.
+// stores (the next slot is in another group).  Returns the sums of fac c
+// and fac d with fac halved.
 template <int TGT>
 __device__ __forceinline__ void chain_group(const float4* __restrict__ T, const float (&th)[TGT][3],
                                             float2 (&av)[TGT][3], float2 (&aw)[TGT][3]) {
-    float2 t[TGT][3];
+    float2 t[TGT][3], tt[TGT];
 #pragma unroll
-    for (int u = 0; u < TGT; ++u)
+    for (int u = 0; u < TGT; ++u) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) t[u][a] = make_float2(th[u][a], th[u][a]);
+        for (int a = 0; a < 3; ++a) t[u][a] = make_float2(2.f * th[u][a], 2.f * th[u][a]);
+        const float q = fmaf(th[u][0], th[u][0], fmaf(th[u][1], th[u][1], th[u][2] * th[u][2]));
+        tt[u] = make_float2(q, q);
+    }
+    // the end of the group: slot 31 ends at slot 32, slot 63 at its stored end point
+    auto last_end = [&](float2 (&ia1)[TGT], float2 (&rho1)[TGT], float ia32[TGT], float rho32[TGT]) {
+        const float4* Q = T + BS_PAIR * (BS_GROUP / 2 - 1);
+        const float4 q6 = Q[6], q7 = Q[7];  // values 13-15 (slot 63 in the .y halves)
+#pragma unroll
+        for (int u = 0; u < TGT; ++u) {
+            const float ex = q6.w + th[u][0], ey = q7.y + th[u][1], ez = q7.w + th[u][2];
+            const float b2 = ex * ex + ey * ey + ez * ez;
+            const float ib = rsqrt_approx(b2);
+            ia1[u] = make_float2(ia32[u], ib);
+            rho1[u] = make_float2(rho32[u], b2 * ib);
+        }
+    };
     float2 ia0[TGT], rho0[TGT], dd0;
-    chain_head<TGT>(T, t, ia0, rho0, dd0);
+    chain_head<TGT>(T, t, tt, ia0, rho0, dd0);
     float ia32[TGT], rho32[TGT];
 #pragma unroll
     for (int u = 0; u < TGT; ++u) {
@@ -271,8 +327,8 @@ __device__ __forceinline__ void chain_group(const float4* __restrict__ T, const 
 #pragma unroll 2
     for (int p = 0; p < BS_GROUP / 2 - 1; ++p) {
         float2 ia1[TGT], rho1[TGT], dd1;
-        chain_head<TGT>(T + 8 * (p + 1), t, ia1, rho1, dd1);
-        chain_segments<TGT>(T + 8 * p, dd0, ia0, rho0, ia1, rho1, av, aw);
+        chain_head<TGT>(T + BS_PAIR * (p + 1), t, tt, ia1, rho1, dd1);
+        chain_segments<TGT>(T + BS_PAIR * p, dd0, ia0, rho0, ia1, rho1, av, aw);
 #pragma unroll
         for (int u = 0; u < TGT; ++u) {
             ia0[u] = ia1[u];
@@ -280,18 +336,9 @@ __device__ __forceinline__ void chain_group(const float4* __restrict__ T, const 
         }
         dd0 = dd1;
     }
-    const float4* Q = T + 8 * (BS_GROUP / 2 - 1);
-    const float4 q6 = Q[6], q7 = Q[7];  // values 13-15: the stored end point (slot 63 in the .y halves)
     float2 ia1[TGT], rho1[TGT];
-#pragma unroll
-    for (int u = 0; u < TGT; ++u) {
-        const float ex = q6.w + th[u][0], ey = q7.y + th[u][1], ez = q7.w + th[u][2];
-        const float b2 = ex * ex + ey * ey + ez * ez;
-        const float ib = rsqrt_approx(b2);
-        ia1[u] = make_float2(ia32[u], ib);
-        rho1[u] = make_float2(rho32[u], b2 * ib);
-    }
-    chain_segments<TGT>(Q, dd0, ia0, rho0, ia1, rho1, av, aw);
+    last_end(ia1, rho1, ia32, rho32);
+    chain_segments<TGT>(T + BS_PAIR * (BS_GROUP / 2 - 1), dd0, ia0, rho0, ia1, rho1, av, aw);
 }
 
 // Minimum image of one component of R1 on a periodic axis (L = 0 on wall
@@ -531,7 +578,7 @@ __device__ __forceinline__ void bs_fill(const BsSmem& sm, const float4* seg, uin
 __device__ __forceinline__ BsGroup group_box(const float4* __restrict__ T, int j, const BsOrder& o,
                                              const BsImages& im, long long Np) {
     BsGroup G;
-    const float4 a6 = T[6], a7 = T[7], b6 = T[8 + 6], b7 = T[8 + 7];
+    const float4 a6 = T[6], a7 = T[7], b6 = T[BS_PAIR + 6], b7 = T[BS_PAIR + 7];
     G.lo[0] = a6.z; G.lo[1] = a7.x; G.lo[2] = a7.z;
     G.hi[0] = b6.z; G.hi[1] = b7.x; G.hi[2] = b7.z;
     G.sign = group_origin(o, im, Np, j, G.O) > 0 ? -1.f : 1.f;
@@ -539,10 +586,16 @@ __device__ __forceinline__ BsGroup group_box(const float4* __restrict__ T, int j
 }
 
 // The sums of one group of slots (slot numbers gbase ..) for TGT targets per
-// thread, on the path the warp's targets need.
+// thread (sorted positions kbase ..), on the path the warp's targets need,
+// added into acc[].v.  The targets' positions and slots are read again from
+// their records here rather than kept in registers across groups.
 template <bool PERIODIC, int TGT>
 __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase, const BsGroup& G,
-                                         BsTarget (&t)[TGT], const BoxF& box, int Np) {
+                                         BsTarget (&acc)[TGT], const BsOrder& o, int kbase, const BoxF& box,
+                                         int Np) {
+    BsTarget t[TGT];
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) t[u] = bs_target_reload(o, kbase + u, acc[u].i);
     float D[TGT][3], th[TGT][3];
     bool nearL = false, wrapL = false;
 #pragma unroll
@@ -574,7 +627,7 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase
         if (nearW) {
 #pragma unroll(TGT == 1 ? 2 : 1)
             for (int p = 0; p < BS_GROUP / 2; ++p)
-                pair2_precise<PERIODIC, true, TGT>(T + 8 * p, gbase + p, th, tl, t, box, Np);
+                pair2_precise<PERIODIC, true, TGT>(T + BS_PAIR * p, gbase + p, th, tl, t, box, Np);
         } else if (PERIODIC) {
             float2 v[TGT][3];
 #pragma unroll
@@ -582,7 +635,7 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase
 #pragma unroll
                 for (int a = 0; a < 3; ++a) v[u][a] = make_float2(0.f, 0.f);
 #pragma unroll 2
-            for (int p = 0; p < BS_GROUP / 2; ++p) pair2_wrap<TGT>(T + 8 * p, gbase + p, th, tl, t, box, Np, v);
+            for (int p = 0; p < BS_GROUP / 2; ++p) pair2_wrap<TGT>(T + BS_PAIR * p, gbase + p, th, tl, t, box, Np, v);
 #pragma unroll
             for (int u = 0; u < TGT; ++u)
 #pragma unroll
@@ -605,6 +658,10 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase
             t[u].v[2] = fmaf(sc, (av[u][2].x + av[u][2].y) + (th[u][0] * wy - th[u][1] * wx), t[u].v[2]);
         }
     }
+#pragma unroll
+    for (int u = 0; u < TGT; ++u)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[u].v[a] += t[u].v[a];
 }
 
 // Work items are (target tile of BS_TPB * TGT points, source split).  Block b
@@ -669,7 +726,8 @@ __device__ bool bs_work(const float4* __restrict__ seg, const int* __restrict__ 
 #pragma unroll 1
             for (int gi = 0; gi * BS_GROUP < cnt; ++gi) {
                 const BsGroup G = group_box(T + BS_REC * BS_GROUP * gi, jb + gi * BS_GROUP, o, im, Np);
-                bs_group<PERIODIC, TGT>(T + BS_REC * BS_GROUP * gi, jb + gi * BS_GROUP, G, t, box, (int)Np);
+                bs_group<PERIODIC, TGT>(T + BS_REC * BS_GROUP * gi, jb + gi * BS_GROUP, G, t, o,
+                                        tb * TT + threadIdx.x * TGT, box, (int)Np);
             }
             // release the stage; the last warp out refills it with the tile NST on
             __syncwarp();
@@ -814,7 +872,7 @@ __global__ void __launch_bounds__(BS_GROUP) k_bs_points(Grid g, const double* __
     for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
         const int sl = grp * BS_GROUP + threadIdx.x;
         const int code = sl < ns ? o.pt[sl] : -1;
-        const int4 og = o.org[grp];
+        int4 og = o.org[grp];
         const double O[3] = {(double)og.x, (double)og.y, (double)og.z};
         double rel[3] = {0.0, 0.0, 0.0};
         float d[3] = {0.f, 0.f, 0.f};
@@ -831,12 +889,15 @@ __global__ void __launch_bounds__(BS_GROUP) k_bs_points(Grid g, const double* __
                     if (threadIdx.x != BS_GROUP - 1) jump |= fabs(min_image(g, a, sq - O[a]) - (rel[a] + b)) > 0.5;
                 }
             }
-            bs_write_target(o.tgt, o.sorted ? o.rank[code] : code, rel, og, sl, bs_prev_slot(o, prev[code]), -1,
-                            code);
         } else if (code <= -2) {
             const int q = bs_checked_next(next, n, -2 - code);
             for (int a = 0; a < 3; ++a) rel[a] = min_image(g, a, pos[(long long)a * n + q] - O[a]);
         }
+        og = bs_center_origin(rel, og, sm);
+        if (threadIdx.x == 0) o.org[grp] = og;
+        if (code >= 0)
+            bs_write_target(o.tgt, o.sorted ? o.rank[code] : code, rel, og, sl, bs_prev_slot(o, prev[code]), -1,
+                            code);
         bs_write_group(0, nullptr, Np, grp, rel, d, jump, seg, sm);
     }
 }
@@ -996,7 +1057,7 @@ void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s) {
 namespace {
 
 constexpr int NOALLOC_MAX_POINTS = 65536;
-constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(17) << 20;
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(19) << 20;
 // the scratch of the stand-alone entry grows linearly with the point count,
 // so the array holds every call up to the point limit
 static_assert(vlb::bs_scratch_bytes(NOALLOC_MAX_POINTS) <= NOALLOC_SCRATCH_BYTES,

@@ -13,9 +13,9 @@ namespace vlb {
 
 namespace {
 
-// The 16 values of one slot: rel = its point relative to the group origin
+// The values of one slot: rel = its point relative to the group origin
 // (FP64), d = its segment (zero for none).
-__device__ __forceinline__ void bs_slot_values(const double rel[3], const float d[3], float val[16]) {
+__device__ __forceinline__ void bs_slot_values(const double rel[3], const float d[3], float val[BS_VALS]) {
     float h[3], l[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -31,6 +31,8 @@ __device__ __forceinline__ void bs_slot_values(const double rel[3], const float 
     val[10] = l[0]; val[11] = l[1]; val[12] = l[2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) val[13 + a] = __double2float_rn(rel[a] + (double)d[a]);
+    val[16] = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    val[17] = val[18] = val[19] = 0.f;
 }
 
 // The target record of the point at sorted position k (slot sl, parts h + l
@@ -59,9 +61,43 @@ __device__ __forceinline__ int bs_prev_slot(const BsOrder& o, int p) {
 // Shared memory of the group writer: one group's records in their stored
 // layout, and the two warps' box partials.
 struct BsGroupSmem {
-    float stage[BS_GROUP * 16];
+    float stage[BS_GROUP * BS_VALS];
     float red[2][6];
 };
+
+// Centre a group's origin on its box of points (called by the whole block,
+// thread t holding slot t's position rel relative to O): the origin moves by
+// the integer cell nearest the box centre and rel with it (exactly), so
+// that |h| stays within about half the group's extent.  Returns the new
+// origin.
+__device__ __forceinline__ int4 bs_center_origin(double rel[3], const int4& O, BsGroupSmem& sm) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = (float)rel[a];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            sm.red[w][a] = lo[a];
+            sm.red[w][3 + a] = hi[a];
+        }
+    __syncthreads();
+    int sh[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        sh[a] = (int)rintf(0.5f * (fminf(sm.red[0][a], sm.red[1][a]) + fmaxf(sm.red[0][3 + a], sm.red[1][3 + a])));
+        rel[a] -= (double)sh[a];
+    }
+    __syncthreads();  // sm.red is used again by the group writer
+    return make_int4(O.x + sh[0], O.y + sh[1], O.z + sh[2], 0);
+}
 
 // One group of slots, written by one block of BS_GROUP threads, thread t =
 // slot t of group grp: rel = its point relative to the group origin (FP64),
@@ -77,7 +113,7 @@ __device__ __forceinline__ void bs_write_group(int nfaces, const int* face_code,
                                                const double rel[3], const float d[3], bool jump, float4* seg,
                                                BsGroupSmem& sm) {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    float val[16];
+    float val[BS_VALS];
     bs_slot_values(rel, d, val);
     float lo[3] = {val[0], val[1], val[2]}, hi[3] = {val[0], val[1], val[2]};
 #pragma unroll
@@ -100,9 +136,9 @@ __device__ __forceinline__ void bs_write_group(int nfaces, const int* face_code,
         hi[a] = anyjump ? 3.0e38f : fmaxf(sm.red[0][3 + a], sm.red[1][3 + a]);
     }
     for (int f = 0; f <= nfaces; ++f) {
-        float v[16];
+        float v[BS_VALS];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = val[q];
+        for (int q = 0; q < BS_VALS; ++q) v[q] = val[q];
         float blo[3] = {lo[0], lo[1], lo[2]}, bhi[3] = {hi[0], hi[1], hi[2]};
         if (f > 0) {
             const int ax = face_code[f - 1] >> 1;
@@ -126,9 +162,9 @@ __device__ __forceinline__ void bs_write_group(int nfaces, const int* face_code,
         } else if (t == 1) {
             v[13] = bhi[0]; v[14] = bhi[1]; v[15] = bhi[2];
         }
-        // value q of slot t at (t % 32) * 32 + 2 q + (t / 32) of the group
+        // value q of slot t at (t % 32) * 2 BS_VALS + 2 q + (t / 32) of the group
 #pragma unroll
-        for (int q = 0; q < 16; ++q) sm.stage[lane * 32 + 2 * q + w] = v[q];
+        for (int q = 0; q < BS_VALS; ++q) sm.stage[lane * 2 * BS_VALS + 2 * q + w] = v[q];
         __syncthreads();
         float4* dst = seg + ((long long)f * Np + (long long)grp * BS_GROUP) * BS_REC;
         const float4* src = reinterpret_cast<const float4*>(sm.stage);

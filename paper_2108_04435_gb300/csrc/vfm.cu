@@ -126,11 +126,12 @@ __global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const 
     for (int grp = blockIdx.x; grp < ng; grp += gridDim.x) {
         const int sl = grp * BS_GROUP + threadIdx.x;
         const int code = sl < ns ? o.pt[sl] : -1;
-        const int4 og = o.org[grp];
+        int4 og = o.org[grp];
         const double O[3] = {(double)og.x, (double)og.y, (double)og.z};
         double rel[3] = {0.0, 0.0, 0.0};
         float d[3] = {0.f, 0.f, 0.f};
         bool jump = false;
+        int prev_sl = -1, excl = -1;
         if (code >= 0) {
             StageRec r;
             geometry_point(P, s, next, prev, N, cap, code, geo, s0_copy, r);
@@ -142,16 +143,20 @@ __global__ void __launch_bounds__(BS_GROUP) k_geometry_stage(VfmParams P, const 
                 if (r.q >= 0 && threadIdx.x != BS_GROUP - 1)
                     jump |= fabs(min_image(P.g, a, r.st[a] - O[a]) - (rel[a] + (double)r.b[a])) > 0.5;
             }
-            const int prev_sl = bs_prev_slot(o, r.p);
-            int excl = -1;
+            prev_sl = bs_prev_slot(o, r.p);
             for (int f = 0; f < P.nfaces; ++f)
                 if (r.pin >= 0 && P.face_code[f] == r.pin) excl = (int)((1 + f) * Np) + (r.p < 0 ? sl : prev_sl);
-            bs_write_target(o.tgt, o.sorted ? o.rank[code] : code, rel, og, sl, prev_sl, excl, code);
         } else if (code <= -2) {
             const int q = next[-2 - code];
 #pragma unroll
             for (int a = 0; a < 3; ++a) rel[a] = min_image(P.g, a, s[(long long)a * cap + q] - O[a]);
         }
+        if (s0_copy) {
+            // the first stage of the step: the origin moves to the centre of the group's box
+            og = bs_center_origin(rel, og, sm);
+            if (threadIdx.x == 0) o.org[grp] = og;
+        }
+        if (code >= 0) bs_write_target(o.tgt, o.sorted ? o.rank[code] : code, rel, og, sl, prev_sl, excl, code);
         bs_write_group(P.nfaces, P.face_code, Np, grp, rel, d, jump, seg, sm);
     }
 }

@@ -107,7 +107,9 @@ constexpr int LBM_BLOCK = 256;  // cells per stream-collide block (one z plane)
 constexpr int BS_TPB = 128;     // threads per Biot-Savart block
 constexpr int BS_TILE = 128;    // source slots per shared-memory tile
 constexpr int BS_GROUP = 64;    // source slots that share one integer origin
-constexpr int BS_REC = 4;       // float4 per source slot (64 bytes; slots are stored in interleaved pairs)
+constexpr int BS_REC = 5;       // float4 per source slot (80 bytes; slots are stored in interleaved pairs)
+constexpr int BS_VALS = 4 * BS_REC;  // values per slot
+constexpr int BS_PAIR = 2 * BS_REC;  // float4 per pair of slots
 constexpr int MAX_SPLIT = 64;   // Biot-Savart source splits
 // From this many points on the Biot-Savart sources are put in a spatial order
 // once per step, so that a group of BS_GROUP slots spans a small box
@@ -124,25 +126,26 @@ constexpr int BS_SORT_MAX_BINS = 1 << 16;  // bins of the spatial order (bin edg
 // as both the start of its own segment and the end of the one before, one
 // reciprocal square root per slot instead of two per segment.
 //
-// Slot record: 16 values relative to the integer origin O of its group of
-// BS_GROUP slots (the cell of the group's first slot at the step's start):
+// Slot record: 20 values relative to the integer origin O of its group of
+// BS_GROUP slots (at the step's start, the integer cell nearest the centre
+// of the group's box):
 //   0-2 h = fl(s - O) (minimum image on periodic axes), 3 |d|^2, 4-6 d,
 //   7-9 c = h x d (FP32), 10-12 l = fl(s - O - h), 13-15 fl(s - O + d), the
 //   segment's end (read for the group's last slot, whose end lies in the
 //   next group); slots 0 and 1 hold there instead the low and high corner
 //   of the group's box of h (unbounded when the chain jumps by a periodic
-//   box somewhere in the group);
+//   box somewhere in the group); 16 |h|^2 (FP32), 17-19 zero;
 // h + l carries s - O to ~1e-14 cells.  Gap and padding slots have d = 0.
 // Storage: slot p and slot p + 32 of a group form pair p, interleaved in
-// 128 bytes: value v of slot k is float
-//   (k / 64) * 1024 + (k % 32) * 32 + 2 v + (k / 32) % 2,
+// 160 bytes: value v of slot k is float
+//   (k / 64) * 1280 + (k % 32) * 40 + 2 v + (k / 32) % 2,
 // so that one float4 holds two values of both slots, one float2 the same
 // value of both (the packed FP32 pair path), and the pairs p = 0..31 of a
 // group walk its two halves along their chains side by side.
 // A target r (its own slot: origin O_t, parts h_t, l_t) sees the group at
 // offset t = (O - O_t) - h_t - l_t, so R1 = s - r = h + l + t.
 __host__ __device__ inline long long bs_value_index(long long k, int v) {
-    return (k >> 6) * 1024 + (k & 31) * 32 + 2 * v + ((k >> 5) & 1);
+    return (k >> 6) * (BS_GROUP * BS_VALS) + (k & 31) * (2 * BS_VALS) + 2 * v + ((k >> 5) & 1);
 }
 
 // Order of the Biot-Savart sources.  sorted = 0: sorted position k is
