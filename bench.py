@@ -330,7 +330,7 @@ def run_vlb(args, ws, rank, local):
     f_med = float(clk.get("sm_mhz") or f_max)
     fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * f_max * 1e6 / 1e12
     fp32_peak_med = n_sm * FP32_LANES_PER_SM * 2 * f_med * 1e6 / 1e12
-    bs_traffic = profile_traffic("k_biot_savart", args.config, ["bs.cu", "eom.cuh", "vlb_internal.cuh"])
+    bs_traffic = profile_traffic("k_biot_savart", args.config, ["bs.cu", "eom.cuh", "records.cuh", "vlb_internal.cuh"])
     bs_share = bs_ms / (nograph_s * 1e3) if nograph_s > 0 else None
     k1_f32 = lbm_pass_roofline(p, "f32", max(10, args.steps), pk, pk_kind, stream) \
         if args.storage != "f32" else None
