@@ -438,7 +438,9 @@ __device__ __forceinline__ float2 fsub2(float2 x, float2 y) { return __fadd2_rn(
 // warp sees within BS_NEAR cells, but some of whose sources may lie half a
 // periodic box away): R1 = h + t without the low parts, as on the far path,
 // and the minimum image of every pair decided in FP32 (for a wall-image slot,
-// that of its end point, reading 21).  When some lane finds a pair within
+// that of its end point, reading 21) on the axes `axes` where the group may
+// reach half a box from some target of the warp (on the others every source
+// already lies within half a box, in the group's image).  When some lane finds a pair within
 // 1e-3 cells of half the box, where dropping the low parts could change the
 // decision, the warp takes that pair on the precise path instead, which
 // decides it exactly.  Adds the pair's sums into v (the block's sign
@@ -446,7 +448,7 @@ __device__ __forceinline__ float2 fsub2(float2 x, float2 y) { return __fadd2_rn(
 template <int TGT>
 __device__ __forceinline__ void pair2_wrap(const float4* __restrict__ Q, int j, const float (&th)[TGT][3],
                                            const float (&tl)[TGT][3], BsTarget (&t)[TGT], const BoxF& box,
-                                           int Np, float2 (&v)[TGT][3]) {
+                                           int Np, int axes, float2 (&v)[TGT][3]) {
     const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3];
     const float2 hx = make_float2(q0.x, q0.y), hy = make_float2(q0.z, q0.w), hz = make_float2(q1.x, q1.y);
     const float2 dd = make_float2(q1.z, q1.w);
@@ -466,7 +468,7 @@ __device__ __forceinline__ void pair2_wrap(const float4* __restrict__ Q, int j, 
         const float L[3] = {box.Lx, box.Ly, box.Lz}, iL[3] = {box.iLx, box.iLy, box.iLz};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if (L[a] > 0.f) {
+            if ((axes >> a) & 1) {
                 const float2 z = __fadd2_rn(r[u][a], e[a]);
                 const float2 k = fsub2(__ffma2_rn(z, make_float2(iL[a], iL[a]), make_float2(M, M)),
                                             make_float2(M, M));
@@ -505,10 +507,10 @@ __device__ __forceinline__ void pair2_wrap(const float4* __restrict__ Q, int j, 
 // a box away on a periodic axis in that image (wrap).
 template <bool PERIODIC>
 __device__ __forceinline__ void group_offset(const BsGroup& G, const BsTarget& t, const BoxF& box, float D[3],
-                                             float th[3], bool& near, bool& wrap) {
+                                             float th[3], bool& near, int& wrap) {
     const float L[3] = {box.Lx, box.Ly, box.Lz}, iL[3] = {box.iLx, box.iLy, box.iLz};
     float dist = 0.f;
-    wrap = false;
+    wrap = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         D[a] = G.O[a] - t.O[a];
@@ -520,7 +522,7 @@ __device__ __forceinline__ void group_offset(const BsGroup& G, const BsTarget& t
             // the box's neighbouring images may come closer (L = 0 on wall axes: the same box)
             da = fminf(da, fmaxf(fmaxf(lo - L[a], L[a] - hi), 0.f));
             da = fminf(da, fmaxf(fmaxf(lo + L[a], -(hi + L[a])), 0.f));
-            wrap |= (L[a] > 0.f) & ((hi > 0.5f * L[a] - 0.01f) | (lo < 0.01f - 0.5f * L[a]));
+            if ((L[a] > 0.f) & ((hi > 0.5f * L[a] - 0.01f) | (lo < 0.01f - 0.5f * L[a]))) wrap |= 1 << a;
         }
         dist = fmaxf(dist, da);
     }
@@ -597,10 +599,12 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase
 #pragma unroll
     for (int u = 0; u < TGT; ++u) t[u] = bs_target_reload(o, kbase + u, acc[u].i);
     float D[TGT][3], th[TGT][3];
-    bool nearL = false, wrapL = false;
+    bool nearL = false;
+    int wrapL = 0;
 #pragma unroll
     for (int u = 0; u < TGT; ++u) {
-        bool nu, wu;
+        bool nu;
+        int wu;
         group_offset<PERIODIC>(G, t[u], box, D[u], th[u], nu, wu);
         const bool own = (unsigned)(t[u].self - gbase) < (unsigned)BS_GROUP ||
                          (unsigned)(t[u].prev - gbase) < (unsigned)BS_GROUP ||
@@ -611,7 +615,9 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase
         }
     }
     const bool nearW = __any_sync(0xffffffffu, nearL);
-    if (nearW || (PERIODIC && __any_sync(0xffffffffu, wrapL))) {
+    // periodic axes on which some source may lie half a box away for some lane
+    const int wrapW = PERIODIC ? (int)__reduce_or_sync(0xffffffffu, (unsigned)wrapL) : 0;
+    if (nearW || wrapW) {
         // low part of the offset: t = D - h_t - l_t with D - h_t split exactly (TwoSum)
         float tl[TGT][3];
 #pragma unroll
@@ -635,7 +641,8 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase
 #pragma unroll
                 for (int a = 0; a < 3; ++a) v[u][a] = make_float2(0.f, 0.f);
 #pragma unroll 2
-            for (int p = 0; p < BS_GROUP / 2; ++p) pair2_wrap<TGT>(T + BS_PAIR * p, gbase + p, th, tl, t, box, Np, v);
+            for (int p = 0; p < BS_GROUP / 2; ++p)
+                pair2_wrap<TGT>(T + BS_PAIR * p, gbase + p, th, tl, t, box, Np, wrapW, v);
 #pragma unroll
             for (int u = 0; u < TGT; ++u)
 #pragma unroll
