@@ -395,23 +395,34 @@ __device__ __forceinline__ void pair_precise(float hx, float hy, float hz, float
     const float b2 = fmaf(2.f, rd, a2) + dd;
     const float ia = rsqrt_approx(a2), ib = rsqrt_approx(b2);
     const float P = ia * ib;
-    const float den = fmaf(P, a2 + rd, 1.f);
-    const float fac = (ia + ib) * P * rcp_approx(den) * sign;
+    const float cx = r1y * dz - r1z * dy, cy = r1z * dx - r1x * dz, cz = r1x * dy - r1y * dx;
+    // The factor's denominator e = |R1||R2| + R1.R2 (over |R1||R2|: 1 + P R1.R2)
+    // cancels when the target lies near the segment between its ends
+    // (R1.R2 < 0, the angle between R1 and R2 near pi).  There it is formed as
+    // |R1 x d|^2 / (|R1||R2| - R1.R2), exactly equal and free of
+    // cancellation: fac = (ia + ib)(1 - P R1.R2) / (P |R1 x d|^2).
+    const float s12 = a2 + rd;
+    const float cr2 = fmaf(cz, cz, fmaf(cy, cy, cx * cx));
+    const bool anti = s12 < 0.f;
+    const float num = (ia + ib) * (anti ? fmaf(-P, s12, 1.f) : P);
+    const float dn = anti ? P * cr2 : fmaf(P, s12, 1.f);
+    const float fac = num * rcp_approx(dn) * sign;
     float c = fac;
     if (GUARD) {
-        // den <= 1e-6: the target lies on the segment (or coincides with an
-        // end point), where the integral is not defined; NaN and infinity
-        // fail too.  Slots without a segment (gap and padding slots, a
-        // line's last point) are skipped: a gap slot may hold the target's
+        // 1 + P R1.R2 <= 1e-6: the target lies on the segment (or coincides
+        // with an end point), where the integral is not defined; NaN and
+        // infinity fail too.  Slots without a segment (gap and padding slots,
+        // a line's last point) are skipped: a gap slot may hold the target's
         // own point, ~1e-14 away in another group's origin, where fac
         // overflows and fac * 0 would be NaN.
-        const bool use = (dd > 0.f) & (den > 1e-6f) & (den < 3.0e38f) & (j != t.self) & (j != t.prev) &
-                         (j != t.excl);
+        const bool on = anti ? !(P * dn > 1e-6f * fmaf(-P, s12, 1.f)) : !(dn > 1e-6f);
+        const bool use = (dd > 0.f) & !on & (dn < 3.0e38f) & (fabsf(fac) < 3.0e38f) & (j != t.self) &
+                         (j != t.prev) & (j != t.excl);
         c = use ? fac : 0.f;
     }
-    v[0] = fmaf(c, r1y * dz - r1z * dy, v[0]);
-    v[1] = fmaf(c, r1z * dx - r1x * dz, v[1]);
-    v[2] = fmaf(c, r1x * dy - r1y * dx, v[2]);
+    v[0] = fmaf(c, cx, v[0]);
+    v[1] = fmaf(c, cy, v[1]);
+    v[2] = fmaf(c, cz, v[2]);
 }
 
 // Both slots of a pair on the precise path (q0..q6: values 0-13 of both);

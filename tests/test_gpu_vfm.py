@@ -103,7 +103,8 @@ def _bs_gpu(p, xyz, nxt):
 
 
 @pytest.mark.parametrize("case", ["ring", "periodic-tangle", "walls-tangle", "large", "sorted-periodic",
-                                  "sorted-walls", "half-box", "half-box-sorted"])
+                                  "sorted-walls", "half-box", "half-box-sorted", "tiny-rings", "tiny-rings-walls",
+                                  "tiny-rings-sorted"])
 def test_biot_savart_entry_point(case):
     import oracle
     from paper_2108_04435_gb300 import inputs
@@ -125,6 +126,17 @@ def test_biot_savart_entry_point(case):
     elif case == "sorted-walls":  # spatial order in a long walled channel: far groups, hi/lo coordinates up to 512
         n, wall = (128, 128, 512), (1, 1, 1)
         xyz, nxt = inputs.random_rings(n, wall, 400, 6.0, 20.0, 8)
+    elif case.startswith("tiny-rings"):
+        # rings of 5 to 12 points: every ring ends in a gap slot, so gap slots
+        # fall at every position of a group, its last one included, and most
+        # groups hold several short chains
+        if case == "tiny-rings":
+            n, wall, count = (32, 32, 32), (0, 0, 0), 400
+        elif case == "tiny-rings-walls":
+            n, wall, count = (48, 40, 64), (1, 1, 1), 500
+        else:
+            n, wall, count = (64, 64, 64), (0, 0, 0), 1500
+        xyz, nxt = inputs.random_rings(n, wall, count, 0.6, 1.5, 12, min_sep=0.0)
     else:
         # a ring and its copy shifted by half the box plus 2.5e-7 along x: every
         # point meets its twin's segment at |R1_x| = L/2 + 2.5e-7, where FP32
