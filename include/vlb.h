@@ -267,10 +267,9 @@ int vlb_biot_savart(const vlb_params* p, const double* pos, const int32_t* next,
  *   n        at most 65536 points; larger n returns VLB_ERR_INVALID_ARG
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and caches it for the
- * life of the process; make that first call before any stream capture, and
- * make no call after a cudaDeviceReset of that device.  All calls share the
- * one array, so calls whose work overlaps on the GPU (other streams, other
- * threads) race: serialise them.  Runs on `stream`; does not wait; reports
+ * life of the process; make no call after a cudaDeviceReset of that
+ * device.  All calls share the one array, so calls whose work overlaps on
+ * the GPU (other streams, other threads) race: serialise them.  Runs on `stream`; does not wait; reports
  * no device-side findings (as vlb_biot_savart). */
 int vlb_biot_savart_noalloc(const vlb_params* p, const double* pos, const int32_t* next, int32_t n, float* vel,
                             void* stream);
