@@ -49,7 +49,7 @@ struct vlb_channel {
     bool f_clean = true;  // force grid zero everywhere (each lattice pass consumes it)
     int cap = 0;
     int hsize = 0;
-    int bpp = 0;
+    int wpp = 0;  // stream-collide warps per z plane
     int nsplit_max = 1;
     int n_hint = 0;
     long long steps = 0;
@@ -513,8 +513,8 @@ size_t vlb_channel_bytes(const vlb_params* p) {
     size_t h = 1;
     while (h < 2 * cap) h <<= 1;
     const size_t esize = p->storage == VLB_STORE_F32 ? 4 : 2;
-    const size_t bpp = (size_t)((p->n[0] * p->n[1] + 127) / 128) + 1;
-    size_t b = 2 * up(esize * 19 * C) + up(8 * 3 * C) + up(4 * 3 * C) + 2 * up(nt) + up(8 * 3 * bpp * p->n[2]);
+    const size_t wpp = (size_t)((p->n[0] * p->n[1] + 255) / 256) * 8;  // warps per plane, any block shape
+    size_t b = 2 * up(esize * 19 * C) + up(8 * 3 * C) + up(4 * 3 * C) + 2 * up(nt) + up(4 * 3 * wpp * p->n[2]);
     b += 3 * up(8 * (size_t)p->n[2]) + up(4 * (size_t)p->n[2]) + up(8 * DS_COUNT) + up(4 * CNT_COUNT);
     size_t nfaces = 0;
     if (p->wall_images)
@@ -656,7 +656,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     int h = 1;
     while (h < 2 * cap) h <<= 1;
     ch->hsize = h;
-    ch->bpp = lbm_blocks_per_plane(L);
+    ch->wpp = lbm_warps_per_plane(L);
     const int nsm = bs_max_splits(cap, sm_count());
     ch->nsplit_max = nsm;
     const BsBins bins = bs_bins(g.nx, g.ny, g.nz);
@@ -677,7 +677,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.Vs = (double*)A(sizeof(double) * (size_t)g.nz);
     d.fmask = (uint8_t*)A((size_t)ntiles);
     d.umask = (uint8_t*)A((size_t)ntiles);
-    d.part = (double*)A(sizeof(double) * 3 * (size_t)ch->bpp * g.nz);
+    d.part = (float*)A(sizeof(float) * 3 * (size_t)ch->wpp * g.nz);
     d.plane = (double*)A(sizeof(double) * 3 * (size_t)g.nz);
     d.plane_ticket = (int*)A(sizeof(int) * (size_t)g.nz);
     // statistics and counters in one block, read back with one copy

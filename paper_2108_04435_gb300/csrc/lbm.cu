@@ -136,6 +136,26 @@ __device__ __forceinline__ float warp_reduce(float v) {
     return v;
 }
 
+// The stream-collide pass's sums for Eq. 18 and the mass and Mach checks,
+// one triple per warp of the launch: the warp's sum of rho - rho0 and of u_z
+// over its 32 (or 32 VEC) cells and its largest |u|^2, at
+// part[((z * gridDim.x + blockIdx.x) * warps per block + warp) * 3].  The
+// pass itself does no FP64 arithmetic (GB300 runs FP64 at a small fraction
+// of the FP32 rate, and the pass is issue-bound with 16-bit storage); the
+// plane reduction adds these partials up in FP64.
+__device__ __forceinline__ void warp_partials(float s_drho, float s_uz, float s_u2, float* __restrict__ part, int z) {
+    s_drho = warp_reduce<0>(s_drho);
+    s_uz = warp_reduce<0>(s_uz);
+    s_u2 = warp_reduce<1>(s_u2);
+    if ((threadIdx.x & 31) == 0) {
+        const long long w = ((long long)z * gridDim.x + blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        float* o = part + w * 3;
+        o[0] = s_drho;
+        o[1] = s_uz;
+        o[2] = s_u2;
+    }
+}
+
 // Source index of the population arriving along c_i (pull form of
 // Eq. 14d): 32-bit, from per-thread row/plane offsets (the host limits the
 // lattice to 19 C < 2^31).  A link leaving through a wall is replaced by the
@@ -194,7 +214,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
                                                         typename Pop<S>::T* __restrict__ fout,
                                                         const long long* __restrict__ F, float* __restrict__ U,
                                                         const uint8_t* __restrict__ fmask,
-                                                        const uint8_t* __restrict__ umask, double* __restrict__ part,
+                                                        const uint8_t* __restrict__ umask, float* __restrict__ part,
                                                         LbmParams P) {
     pdl_wait_trigger();
     const int nx = P.g.nx, ny = P.g.ny;
@@ -281,35 +301,15 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
         s_uz = uz;
         s_u2 = (usq == usq) ? usq : INFINITY;
     }
-    // per-block partials for Eq. 18 and the mass / Mach checks
-    __shared__ double red[3][LBM_BLOCK / 32];
-    s_drho = warp_reduce<0>(s_drho);
-    s_uz = warp_reduce<0>(s_uz);
-    s_u2 = warp_reduce<1>(s_u2);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][wid] = s_drho;
-        red[1][wid] = s_uz;
-        red[2][wid] = s_u2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, m = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            a += red[0][w];
-            b += red[1][w];
-            m = fmax(m, red[2][w]);
-        }
-        double* o = part + ((long long)z * gridDim.x + blockIdx.x) * 3;
-        o[0] = a;
-        o[1] = b;
-        o[2] = m;
-    }
+    // per-warp partials for Eq. 18 and the mass / Mach checks (summed in
+    // FP64 by the plane reduction)
+    warp_partials(s_drho, s_uz, s_u2, part, z);
 }
 
-// Eq. 18 per z plane from the stream-collide block partials, with the mass
-// and the Mach limit of Sec. II.B (|u|/c_s < 0.05).  One warp per plane
-// (lane-strided loads, fixed shuffle tree); the last block to finish reduces
+// Eq. 18 per z plane from the stream-collide warp partials (FP32, added up
+// here in FP64), with the mass and the Mach limit of Sec. II.B
+// (|u|/c_s < 0.05).  One warp per plane (lane-strided loads, fixed shuffle
+// tree); the last block to finish reduces
 // the planes in a fixed order.  FP64 work is spread over many SMs because
 // its per-SM rate is low on this GPU.  The stream-collide pass has consumed
 // the force grid: one warp per tile resets it in the flagged tiles, then
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(LBM_BLOCK) k_lbm_step(const typename Pop<S>::T
 // hold the plane warps; the grid has enough blocks beyond them for about
 // one tile per warp, since a warp that resets tile after tile is a long
 // chain of dependent address arithmetic and stores.
-__global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ part, int bpp, LbmParams P,
+__global__ void __launch_bounds__(256) k_plane_vs(const float* __restrict__ part, int wpp, LbmParams P,
                                                   long long* __restrict__ F, uint8_t* __restrict__ umask,
                                                   uint8_t* __restrict__ fmask, int ntiles, int nplane) {
     pdl_wait_trigger();
@@ -353,11 +353,11 @@ __global__ void __launch_bounds__(256) k_plane_vs(const double* __restrict__ par
     const int pz = blockIdx.x * 8 + wid;
     if (pz < nz) {
         double a = 0.0, b = 0.0, m = 0.0;
-        for (int k = lane; k < bpp; k += 32) {
-            const double* o = part + ((long long)pz * bpp + k) * 3;
-            a += o[0];
-            b += o[1];
-            m = fmax(m, o[2]);
+        for (int k = lane; k < wpp; k += 32) {
+            const float* o = part + ((long long)pz * wpp + k) * 3;
+            a += (double)o[0];
+            b += (double)o[1];
+            m = fmax(m, (double)o[2]);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -455,7 +455,7 @@ template <bool WX, bool WY, bool WZ, int VEC>
 __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ fin, float* __restrict__ fout,
                                                       const long long* __restrict__ F, float* __restrict__ U,
                                                       const uint8_t* __restrict__ fmask,
-                                                      const uint8_t* __restrict__ umask, double* __restrict__ part,
+                                                      const uint8_t* __restrict__ umask, float* __restrict__ part,
                                                       LbmParams P) {
     pdl_wait_trigger();
     const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz, nxy = nx * ny;
@@ -640,31 +640,8 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ 
             vstore<VEC>(fout + j * C + cell0, g[j]);
         }
     }
-    // per-block partials for Eq. 18 and the mass / Mach checks
-    __shared__ double red[3][4];
-    s_drho = warp_reduce<0>(s_drho);
-    s_uz = warp_reduce<0>(s_uz);
-    s_u2 = warp_reduce<1>(s_u2);
-    const int wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][wid] = s_drho;
-        red[1][wid] = s_uz;
-        red[2][wid] = s_u2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, m = 0.0;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            a += red[0][w];
-            b += red[1][w];
-            m = fmax(m, red[2][w]);
-        }
-        double* o = part + ((long long)z * gridDim.x + blockIdx.x) * 3;
-        o[0] = a;
-        o[1] = b;
-        o[2] = m;
-    }
+    // per-warp partials for Eq. 18 and the mass / Mach checks
+    warp_partials(s_drho, s_uz, s_u2, part, z);
 }
 
 // Density and velocity of the streamed populations of the current state
@@ -795,7 +772,7 @@ __global__ void k_force_import(const float* __restrict__ in, long long* __restri
 
 template <bool WX, bool WY, bool WZ, bool CS>
 void lbm_launch(const LbmParams& P, dim3 grid, const void* fin, void* fout, const long long* F, float* U,
-                const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s) {
+                const uint8_t* fmask, const uint8_t* umask, float* part, cudaStream_t s) {
     if (P.storage == STORE_F16)
         launch_pdl(k_lbm_step<WX, WY, WZ, STORE_F16, CS>, grid, P.block, 0, s, (const __half*)fin, (__half*)fout, F, U,
                    fmask, umask, part, P);
@@ -809,7 +786,7 @@ void lbm_launch(const LbmParams& P, dim3 grid, const void* fin, void* fout, cons
 
 template <bool WX, bool WY, bool WZ>
 void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U, const uint8_t* fmask,
-                  const uint8_t* umask, double* part, cudaStream_t s) {
+                  const uint8_t* umask, float* part, cudaStream_t s) {
     const int nxy = P.g.nx * P.g.ny;
     if (P.storage == STORE_F32 && (P.vec == 4 || P.vec == 2)) {
         const int groups = nxy / P.vec;
@@ -860,7 +837,7 @@ void moments_dispatch(const LbmParams& P, const void* f, const long long* F, con
     } while (0)
 
 void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U,
-                     const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s) {
+                     const uint8_t* fmask, const uint8_t* umask, float* part, cudaStream_t s) {
     VLB_WALL_DISPATCH(lbm_dispatch, P, fin, fout, F, U, fmask, umask, part, s);
 }
 
@@ -907,12 +884,16 @@ int lbm_blocks_per_plane(const LbmParams& P) {
     return (nxy + P.block - 1) / P.block;
 }
 
-void launch_plane_vs(const LbmParams& P, const double* part, long long* F, uint8_t* umask, uint8_t* fmask,
+int lbm_warps_per_plane(const LbmParams& P) {
+    return lbm_blocks_per_plane(P) * ((P.vec == 4 || P.vec == 2) ? 128 : P.block) / 32;
+}
+
+void launch_plane_vs(const LbmParams& P, const float* part, long long* F, uint8_t* umask, uint8_t* fmask,
                      cudaStream_t s) {
-    const int bpp = lbm_blocks_per_plane(P);
+    const int wpp = lbm_warps_per_plane(P);
     const int ntiles = P.g.tnx * P.g.tny * P.g.tnz, nplane = (P.g.nz + 7) / 8;
     const int nblk = std::max(nplane, std::min((ntiles + 7) / 8, 1216));  // at most 8 blocks per SM of 152
-    launch_pdl(k_plane_vs, nblk, 256, 0, s, part, bpp, P, F, umask, fmask, ntiles, nplane);
+    launch_pdl(k_plane_vs, nblk, 256, 0, s, part, wpp, P, F, umask, fmask, ntiles, nplane);
 }
 
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,

@@ -331,7 +331,7 @@ struct Dev {
     float* U;           // velocity of the last pass [3][C], valid in u-active tiles
     uint8_t* fmask;     // tiles where F may be non-zero
     uint8_t* umask;     // tiles where U must be written
-    double* part;       // stream-collide block partials [nz][bpp][3]
+    float* part;        // stream-collide warp partials [nz][warps per plane][3]
     double* plane;      // plane sums [nz][3]
     int* plane_ticket;  // [nz]
     double* Vs;         // [nz]
@@ -388,10 +388,11 @@ struct Dev {
 // lbm.cu
 void launch_lbm_init(const LbmParams& P, void* f, float* U, const double init_u[3], cudaStream_t s);
 void launch_lbm_step(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U,
-                     const uint8_t* fmask, const uint8_t* umask, double* part, cudaStream_t s);
-void launch_plane_vs(const LbmParams& P, const double* part, long long* F, uint8_t* umask, uint8_t* fmask,
+                     const uint8_t* fmask, const uint8_t* umask, float* part, cudaStream_t s);
+void launch_plane_vs(const LbmParams& P, const float* part, long long* F, uint8_t* umask, uint8_t* fmask,
                      cudaStream_t s);
 int lbm_blocks_per_plane(const LbmParams& P);
+int lbm_warps_per_plane(const LbmParams& P);
 void launch_moments(const LbmParams& P, const void* f, const long long* F, const uint8_t* fmask, float* rho,
                     float* U, cudaStream_t s);
 void launch_mark_umask(const Grid& g, const double* pos, const int* counters, int cap, uint8_t* umask,
