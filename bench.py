@@ -317,7 +317,8 @@ def run_vlb(args, ws, rank, local):
     # stream-collide: algorithmic bytes / mean event-timed launch
     k1_avg_s = (k1_ms / 1e3) / max(k1_n, 1)
     k1_achieved = bpc * cells / k1_avg_s / 1e9 if k1_n else None
-    k1_traffic = profile_traffic("k_lbm_step", args.config, ["lbm.cu"])
+    k1_name = k1_kernel(args.storage, p["n"][0])
+    k1_traffic = profile_traffic(k1_name, args.config, ["lbm.cu"])
     # Biot-Savart: N (N - 2) pairs per launch at the mean live count of the
     # event-timed steps, 45 FP32 flop each, against the FP32 peak of this
     # GPU (SMs x 128 lanes x 2 flop x clock) at the maximum clock and at the
@@ -334,6 +335,7 @@ def run_vlb(args, ws, rank, local):
     bs_share = bs_ms / (nograph_s * 1e3) if nograph_s > 0 else None
     k1_f32 = lbm_pass_roofline(p, "f32", max(10, args.steps), pk, pk_kind, stream) \
         if args.storage != "f32" else None
+    k1_alone = lbm_pass_roofline(p, args.storage, max(10, args.steps), pk, pk_kind, stream)
     config = workload_config(args.config, p, nxt, args.storage, ws)
     line = {
         "metric": "coupled-step MLUPS",
@@ -373,7 +375,7 @@ def run_vlb(args, ws, rank, local):
                      "pairs_per_s": round(pairs / bs_avg_s, 1) if bs_n else None,
                      "avg_launch_us": round(bs_avg_s * 1e6, 3), "launches": bs_n,
                      "share_of_event_timed_step": round(bs_share, 4) if bs_share else None},
-        "roofline_lbm": {"kernel": "k_lbm_step", "bound": "hbm",
+        "roofline_lbm": {"kernel": k1_name, "bound": "hbm",
                          "achieved": round(k1_achieved, 1) if k1_achieved else None,
                          "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": round(k1_achieved / pk["hbm_gbs"], 4) if k1_achieved else None,
@@ -383,9 +385,20 @@ def run_vlb(args, ws, rank, local):
                          "avg_launch_us": round(k1_avg_s * 1e6, 3), "launches": k1_n},
         "clocks": clk,
     }
+    line["roofline_lbm_alone"] = k1_alone
     if k1_f32:
         line["roofline_lbm_f32"] = k1_f32
     return line, p, xyz, nxt
+
+
+def k1_kernel(storage: str, nx: int) -> str:
+    """The stream-collide kernel the library launches for this storage: two
+    cells per thread with 16-bit populations on an even nx (unless
+    VLB_LBM_VEC says otherwise), else one."""
+    vec = os.environ.get("VLB_LBM_VEC")
+    if storage != "f32" and nx % 2 == 0 and vec in (None, "2"):
+        return "k_lbm_step_pair"
+    return "k_lbm_step"
 
 
 def lbm_pass_roofline(p, storage, passes, pk, pk_kind, stream):
@@ -408,13 +421,13 @@ def lbm_pass_roofline(p, storage, passes, pk, pk_kind, stream):
     bpc = BYTES_PER_CELL[storage]
     avg_s = ms / 1e3 / max(n, 1)
     achieved = bpc * cells / avg_s / 1e9 if n else None
-    return {"kernel": "k_lbm_step", "storage": storage, "bound": "hbm",
+    return {"kernel": k1_kernel(storage, q["n"][0]), "storage": storage, "bound": "hbm",
             "achieved": round(achieved, 1) if achieved else None, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": round(achieved / pk["hbm_gbs"], 4) if achieved else None,
             "peak_source": f"{pk_kind} hbm_gbs (copy bandwidth)", "traffic": None,
             "algorithmic_bytes_per_launch": bpc * cells, "bytes_per_cell": bpc,
             "avg_launch_us": round(avg_s * 1e6, 3), "launches": n,
-            "note": "lattice passes alone on the benchmark grid (no filaments), populations stored in FP32"}
+            "note": f"lattice passes alone on the benchmark grid (no filaments), populations stored in {storage.upper()}"}
 
 
 class OracleSampler:

@@ -566,20 +566,23 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     L.pin_on = p->pin_vn != 0.0 ? 1 : 0;
     {
         // Launch shape of the stream-collide kernel, chosen from measurements on
-        // GB300 (lattices of 32^3 to 128x128x1024): one cell per thread in
-        // 128-thread blocks was fastest everywhere.  VLB_LBM_VEC (1, 2, 4) and
+        // GB300 (lattices of 32^3 to 128x128x1024): with FP32 storage one cell
+        // per thread in 128-thread blocks was fastest everywhere; with 16-bit
+        // storage two cells per thread (packed loads, stores and arithmetic),
+        // when nx is even.  VLB_LBM_VEC (1, 2, 4; 16-bit storage: 1, 2) and
         // VLB_LBM_BLOCK (128, 256) override it.
-        int vec = 1;
+        const bool half = p->storage != VLB_STORE_F32;
+        int vec = half && g.nx % 2 == 0 ? 2 : 1;
         if (const char* e = getenv("VLB_LBM_VEC")) {
             const int v = atoi(e);
-            if ((v == 1 || v == 2 || v == 4) && g.nx % v == 0) vec = v;
+            if ((v == 1 || v == 2 || (v == 4 && !half)) && g.nx % v == 0) vec = v;
         }
         int blk = 128;
         if (const char* e = getenv("VLB_LBM_BLOCK")) {
             const int b = atoi(e);
             if (b == 128 || b == 256) blk = b;
         }
-        L.vec = p->storage == VLB_STORE_F32 ? vec : 1;
+        L.vec = vec;
         // exact division by nx through a multiply-high (Granlund-Montgomery),
         // checked here for every in-plane index the kernel can form
         {

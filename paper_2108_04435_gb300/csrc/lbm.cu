@@ -644,6 +644,238 @@ __global__ void __launch_bounds__(128) k_lbm_step_vec(const float* __restrict__ 
     warp_partials(s_drho, s_uz, s_u2, part, z);
 }
 
+// Two adjacent 16-bit populations (the first at an even x, so 4-byte
+// aligned) as floats, and back: one 32-bit load or store for both cells.
+template <int S>
+struct Pop2;
+template <>
+struct Pop2<STORE_F16> {
+    using T2 = __half2;
+    static __device__ __forceinline__ float2 ld(const __half* p, bool cs) {
+        const __half2* q = reinterpret_cast<const __half2*>(p);
+        return __fmul2_rn(__half22float2(cs ? __ldcs(q) : __ldg(q)), make_float2(1.f / 1024.f, 1.f / 1024.f));
+    }
+    static __device__ __forceinline__ void st(__half* p, float2 v, bool cs) {
+        const __half2 h = __float22half2_rn(__fmul2_rn(v, make_float2(1024.f, 1024.f)));
+        __half2* q = reinterpret_cast<__half2*>(p);
+        if (cs) __stcs(q, h);
+        else *q = h;
+    }
+};
+template <>
+struct Pop2<STORE_BF16> {
+    using T2 = __nv_bfloat162;
+    static __device__ __forceinline__ float2 ld(const __nv_bfloat16* p, bool cs) {
+        const __nv_bfloat162* q = reinterpret_cast<const __nv_bfloat162*>(p);
+        return __bfloat1622float2(cs ? __ldcs(q) : __ldg(q));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float2 v, bool cs) {
+        const __nv_bfloat162 h = __float22bfloat162_rn(v);
+        __nv_bfloat162* q = reinterpret_cast<__nv_bfloat162*>(p);
+        if (cs) __stcs(q, h);
+        else *q = h;
+    }
+};
+
+__device__ __forceinline__ float2 f2c(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// K1 for 16-bit population storage: two adjacent cells (x even) per thread.
+// With 16-bit populations the one-cell kernel is bound by instruction issue
+// (a 2-byte load, two conversions and their address arithmetic per value),
+// not by HBM; here each population of both cells is one aligned 32-bit load
+// and one 32-bit store, a +-x shifted population adds one 2-byte load of the
+// value beyond the pair (from L1: the neighbouring thread loads that line),
+// and the collision runs on both cells at once in packed FP32x2 arithmetic.
+// Same equations and operation order per cell as k_lbm_step.  Every load is
+// issued unconditionally from an address that is valid for every thread (a
+// link through a wall reads the cell's own opposite population; a thread
+// past the lattice reads the plane's first cells), so all 29 loads of a
+// thread are in flight together: with the loads under per-thread conditions
+// the walled kernel ran at half the speed of the periodic one.  Requires an
+// even nx; 128 threads (256 cells) per block.
+template <bool WX, bool WY, bool WZ, int S, bool CS>
+__device__ __forceinline__ void lbm_pair_cells(const typename Pop<S>::T* __restrict__ fin,
+                                               typename Pop<S>::T* __restrict__ fout,
+                                               const long long* __restrict__ F, float* __restrict__ U,
+                                               const uint8_t* __restrict__ fmask,
+                                               const uint8_t* __restrict__ umask, const LbmParams& P, int z, int q,
+                                               float& s_drho, float& s_uz, float& s_u2) {
+    const int nx = P.g.nx, ny = P.g.ny, nz = P.g.nz, nxy = nx * ny;
+    const int C = (int)P.g.ncell;
+    const int nq = nx / 2;  // cell pairs per row
+    const bool live = q < nq * ny;
+    const int y = live ? q / nq : 0;
+    const int x0 = live ? (q - y * nq) * 2 : 0;
+    const int cell0 = z * nxy + y * nx + x0;
+    int ym = y - 1, yp = y + 1, zm = z - 1, zp = z + 1;
+    bool oym = false, oyp = false, ozm = false, ozp = false;
+    if (ym < 0) { if (WY) oym = true; else ym += ny; }
+    if (yp >= ny) { if (WY) oyp = true; else yp -= ny; }
+    if (zm < 0) { if (WZ) ozm = true; else zm += nz; }
+    if (zp >= nz) { if (WZ) ozp = true; else zp -= nz; }
+    const int yo[3] = {yp * nx, y * nx, ym * nx};
+    const int zo[3] = {zp * nxy, z * nxy, zm * nxy};
+    const bool oy[3] = {oyp, false, oym};
+    const bool oz[3] = {ozp, false, ozm};
+    const bool row_first = x0 == 0, row_last = x0 + 2 == nx;
+
+    // every load first: the aligned pair of the source row (or, beyond a y or
+    // z wall, the opposite populations of the same two cells), and for a +-x
+    // shift the value beyond the pair (x0 - 1 or x0 + 2, the row's other end
+    // on a periodic x axis, the cell's own opposite population at an x wall)
+    float2 g[19];
+    float edge[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int row = i * C + zo[CZ(i) + 1] + yo[CY(i) + 1];
+        const bool rowout = (WY && oy[CY(i) + 1]) || (WZ && oz[CZ(i) + 1]);
+        const int src = rowout ? opp(i) * C + cell0 : row + x0;
+        g[i] = Pop2<S>::ld(fin + src, CS);
+        edge[i] = 0.f;
+        if (CX(i) == 1) {
+            int a = !row_first ? row + x0 - 1 : (WX ? opp(i) * C + cell0 : row + nx - 1);
+            a = rowout ? src : a;
+            edge[i] = pop_ld<S, CS>(&fin[a]);
+        } else if (CX(i) == -1) {
+            int a = !row_last ? row + x0 + 2 : (WX ? opp(i) * C + cell0 + 1 : row);
+            a = rowout ? src : a;
+            edge[i] = pop_ld<S, CS>(&fin[a]);
+        }
+    }
+    // moving-wall terms, then the +-x shifts
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const bool rowout = (WY && oy[CY(i) + 1]) || (WZ && oz[CZ(i) + 1]);
+        if (WZ && CZ(i) != 0 && oz[CZ(i) + 1]) g[i] = add2(g[i], f2c(6.f * wgt(i) * P.rho0 * (float)CZ(i) * P.heater));
+        if (CX(i) == 1) {
+            // cells x0, x0 + 1 pull from x0 - 1, x0
+            if (!rowout) g[i] = make_float2(edge[i], g[i].x);
+        } else if (CX(i) == -1) {
+            // cells x0, x0 + 1 pull from x0 + 1, x0 + 2
+            if (!rowout) g[i] = make_float2(g[i].y, edge[i]);
+        }
+    }
+    if (live) {
+        const int tile = tile_of(P.g, x0, y, z);  // both cells share a tile
+        const bool factive = fmask[tile] != 0;
+        const bool force = factive || P.body_on;
+        const bool uact = P.all_u || umask[tile] != 0;
+        float2 Fx = f2c(P.body[0]), Fy = f2c(P.body[1]), Fz = f2c(P.body[2]);
+        if (factive) {
+            const longlong2 fx = __ldg(reinterpret_cast<const longlong2*>(F + cell0));
+            const longlong2 fy = __ldg(reinterpret_cast<const longlong2*>(F + C + cell0));
+            const longlong2 fz = __ldg(reinterpret_cast<const longlong2*>(F + 2 * C + cell0));
+            Fx = add2(Fx, make_float2(force_value(fx.x), force_value(fx.y)));
+            Fy = add2(Fy, make_float2(force_value(fy.x), force_value(fy.y)));
+            Fz = add2(Fz, make_float2(force_value(fz.x), force_value(fz.y)));
+        }
+        // Eqs. 5-6 with the half-force shift: rho = rho0 + sum g, j = sum c g
+        float2 drho = f2c(P.dr0), jx = f2c(0.f), jy = f2c(0.f), jz = f2c(0.f);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            drho = add2(drho, g[i]);
+            if (CX(i)) jx = CX(i) > 0 ? add2(jx, g[i]) : sub2(jx, g[i]);
+            if (CY(i)) jy = CY(i) > 0 ? add2(jy, g[i]) : sub2(jy, g[i]);
+            if (CZ(i)) jz = CZ(i) > 0 ? add2(jz, g[i]) : sub2(jz, g[i]);
+        }
+        const float2 rho = add2(f2c(P.rho0), drho);
+        const float2 inv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
+        const float2 ux = mul2(fma2(f2c(0.5f), Fx, jx), inv);
+        const float2 uy = mul2(fma2(f2c(0.5f), Fy, jy), inv);
+        const float2 uz = mul2(fma2(f2c(0.5f), Fz, jz), inv);
+        const float2 usq = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
+        if (uact) {
+            *reinterpret_cast<float2*>(U + cell0) = ux;
+            *reinterpret_cast<float2*>(U + C + cell0) = uy;
+            *reinterpret_cast<float2*>(U + 2 * C + cell0) = uz;
+        }
+        const float2 om = f2c(P.omega);
+        const float2 A = fma2(mul2(f2c(-1.5f), rho), usq, drho);  // even part of f^eq/w - rho0 without (c.u)^2
+        const float2 B3 = mul2(f2c(3.f), rho), B45 = mul2(f2c(4.5f), rho);
+        const float2 uF = fma2(uz, Fz, fma2(uy, Fy, mul2(ux, Fx)));
+        const bool pinned = P.pin_on && z == 0;
+        s_drho = drho.x + drho.y;
+        s_uz = uz.x + uz.y;
+        s_u2 = fmaxf((usq.x == usq.x) ? usq.x : INFINITY, (usq.y == usq.y) ? usq.y : INFINITY);
+        // rest population
+        {
+            const float2 geq = fma2(f2c(wgt(0)), A, f2c(P.dw[0]));
+            float2 out = fma2(om, sub2(geq, g[0]), g[0]);
+            if (force) out = fma2(f2c(P.pref * wgt(0) * -3.f), uF, out);
+            if (pinned) {
+                const float2 pr = fma2(mul2(f2c(-1.5f * P.pin * P.pin), rho), f2c(1.f), drho);
+                out = fma2(f2c(wgt(0)), pr, f2c(P.dw[0]));
+            }
+            Pop2<S>::st(fout + cell0, out, CS);
+        }
+        // opposite pairs (i, i + 1): even parts of Eqs. 7 and 13 shared, odd parts change sign
+#pragma unroll
+        for (int i = 1; i < 19; i += 2) {
+            const int j = i + 1;
+            const float w = wgt(i);
+            float2 cu = f2c(0.f);
+            if (CX(i)) cu = CX(i) > 0 ? add2(cu, ux) : sub2(cu, ux);
+            if (CY(i)) cu = CY(i) > 0 ? add2(cu, uy) : sub2(cu, uy);
+            if (CZ(i)) cu = CZ(i) > 0 ? add2(cu, uz) : sub2(cu, uz);
+            const float2 sym = fma2(f2c(w), fma2(B45, mul2(cu, cu), A), f2c(P.dw[wclass(i)]));
+            const float2 asym = mul2(mul2(f2c(w), B3), cu);
+            float2 oi = fma2(om, sub2(add2(sym, asym), g[i]), g[i]);
+            float2 oj = fma2(om, sub2(sub2(sym, asym), g[j]), g[j]);
+            if (force) {
+                float2 cF = f2c(0.f);
+                if (CX(i)) cF = CX(i) > 0 ? add2(cF, Fx) : sub2(cF, Fx);
+                if (CY(i)) cF = CY(i) > 0 ? add2(cF, Fy) : sub2(cF, Fy);
+                if (CZ(i)) cF = CZ(i) > 0 ? add2(cF, Fz) : sub2(cF, Fz);
+                const float2 fs = mul2(f2c(P.pref * w), fma2(mul2(f2c(9.f), cu), cF, mul2(f2c(-3.f), uF)));
+                const float2 fa = mul2(f2c(P.pref * w * 3.f), cF);
+                oi = add2(oi, add2(fs, fa));
+                oj = add2(oj, sub2(fs, fa));
+            }
+            if (pinned) {
+                const float cp = (float)CZ(i) * P.pin;
+                const float2 ps = fma2(f2c(w), fma2(rho, f2c(4.5f * cp * cp - 1.5f * P.pin * P.pin), drho),
+                                       f2c(P.dw[wclass(i)]));
+                const float2 pa = mul2(mul2(f2c(w), B3), f2c(cp));
+                oi = add2(ps, pa);
+                oj = sub2(ps, pa);
+            }
+            Pop2<S>::st(fout + i * C + cell0, oi, CS);
+            Pop2<S>::st(fout + j * C + cell0, oj, CS);
+        }
+    }
+}
+
+// The kernel: a block whose two rows lie off the y faces, in a plane off the
+// z faces (block-uniform), takes the body without the y and z wall logic
+// (every link of its cells stays inside the lattice there, so the result is
+// the same); the blocks along those faces take the full body.
+template <bool WX, bool WY, bool WZ, int S, bool CS>
+__global__ void __launch_bounds__(128, 6) k_lbm_step_pair(const typename Pop<S>::T* __restrict__ fin,
+                                                       typename Pop<S>::T* __restrict__ fout,
+                                                       const long long* __restrict__ F, float* __restrict__ U,
+                                                       const uint8_t* __restrict__ fmask,
+                                                       const uint8_t* __restrict__ umask, float* __restrict__ part,
+                                                       LbmParams P) {
+    pdl_wait_trigger();
+    const int z = blockIdx.y;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    float s_drho = 0.f, s_uz = 0.f, s_u2 = 0.f;
+    bool inner = false;
+    if (WY || WZ) {
+        const int nq = P.g.nx / 2, q0 = blockIdx.x * blockDim.x;
+        const int q1 = min(q0 + (int)blockDim.x, nq * P.g.ny) - 1;
+        inner = q0 / nq >= 1 && q1 / nq <= P.g.ny - 2 && z >= 1 && z <= P.g.nz - 2;
+    }
+    if (inner) lbm_pair_cells<WX, false, false, S, CS>(fin, fout, F, U, fmask, umask, P, z, q, s_drho, s_uz, s_u2);
+    else lbm_pair_cells<WX, WY, WZ, S, CS>(fin, fout, F, U, fmask, umask, P, z, q, s_drho, s_uz, s_u2);
+    // per-warp partials for Eq. 18 and the mass / Mach checks
+    warp_partials(s_drho, s_uz, s_u2, part, z);
+}
+
 // Density and velocity of the streamed populations of the current state
 // (what the next pass will see), for read-out.
 template <bool WX, bool WY, bool WZ, int S>
@@ -788,6 +1020,25 @@ template <bool WX, bool WY, bool WZ>
 void lbm_dispatch(const LbmParams& P, const void* fin, void* fout, const long long* F, float* U, const uint8_t* fmask,
                   const uint8_t* umask, float* part, cudaStream_t s) {
     const int nxy = P.g.nx * P.g.ny;
+    if (P.storage != STORE_F32 && P.vec == 2) {
+        dim3 grid((nxy / 2 + 127) / 128, P.g.nz);
+        if (P.storage == STORE_F16) {
+            if (P.stream_hint)
+                launch_pdl(k_lbm_step_pair<WX, WY, WZ, STORE_F16, true>, grid, 128, 0, s, (const __half*)fin,
+                           (__half*)fout, F, U, fmask, umask, part, P);
+            else
+                launch_pdl(k_lbm_step_pair<WX, WY, WZ, STORE_F16, false>, grid, 128, 0, s, (const __half*)fin,
+                           (__half*)fout, F, U, fmask, umask, part, P);
+        } else {
+            if (P.stream_hint)
+                launch_pdl(k_lbm_step_pair<WX, WY, WZ, STORE_BF16, true>, grid, 128, 0, s,
+                           (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, F, U, fmask, umask, part, P);
+            else
+                launch_pdl(k_lbm_step_pair<WX, WY, WZ, STORE_BF16, false>, grid, 128, 0, s,
+                           (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, F, U, fmask, umask, part, P);
+        }
+        return;
+    }
     if (P.storage == STORE_F32 && (P.vec == 4 || P.vec == 2)) {
         const int groups = nxy / P.vec;
         dim3 grid((groups + 127) / 128, P.g.nz);
