@@ -12,7 +12,8 @@
   bit for bit: the single-block compactions then work through many chunks of
   1024 points.
 - One lattice pass of 128^3 with FP16 and BF16 storage within the bounds the
-  reduced formats are stated to keep.
+  reduced formats are stated to keep, periodic and with walls on every axis
+  (where most blocks take the two-cell body without the wall logic).
 - One whole coupled step of the 128^3 periodic counterflow box (~18.5k points).
 """
 import numpy as np
@@ -79,13 +80,14 @@ def test_topology_bit_exact_above_20k_points():
     assert s[5] > 0 and s[6] > 0 and s[7] > 0  # splits, merges and exchanges all happened
 
 
+@pytest.mark.parametrize("walls", [(0, 0, 0), (1, 1, 1)], ids=["periodic", "walls"])
 @pytest.mark.parametrize("storage,bound", [(1, 1e-3), (2, 8e-3)], ids=["f16", "bf16"])
-def test_reduced_storage_pass_128(storage, bound):
+def test_reduced_storage_pass_128(storage, bound, walls):
     import oracle
     from paper_2108_04435_gb300 import configs, vlb
     c, w, _ = oracle.lattice()
-    p = configs.base_params((128, 128, 128), (0, 0, 0), 1.9, couple=0, max_points=8, storage=storage,
-                            init_vn=[0.003, -0.002, 0.01])
+    p = configs.base_params((128, 128, 128), walls, 1.9, couple=0, max_points=8, storage=storage,
+                            heater_vn=0.01 if walls[2] else 0.0, init_vn=[0.003, -0.002, 0.01])
     g, r = pair(p)
     same_lattice_state(g, r, seed=43, amp=1e-2, force_amp=2e-4)
     g.run_phases(vlb.PHASE_LBM)

@@ -41,14 +41,24 @@ def lattice_errors(g, r):
 
 
 @pytest.mark.parametrize("storage", [1, 2], ids=["f16", "bf16"])
-@pytest.mark.parametrize("geom", ["periodic", "walls"])
+@pytest.mark.parametrize("geom", ["periodic", "walls", "walls-interior", "walls-odd-nx", "pinned"])
 def test_lattice_passes(storage, geom):
     import oracle
     from paper_2108_04435_gb300 import vlb
     if geom == "periodic":
         p = params((24, 20, 16), (0, 0, 0), storage, init_vn=[0.003, -0.002, 0.01])
-    else:
+    elif geom == "walls":
         p = params((22, 18, 36), (1, 1, 1), storage, heater_vn=0.01, init_vn=[0.0, 0.0, 0.01])
+    elif geom == "walls-interior":
+        # 16 cell pairs per row, 24 rows: the middle block of each plane
+        # (rows 8-15) lies off the y faces and takes the body without the
+        # wall logic in planes 1-18; the others keep it
+        p = params((32, 24, 20), (1, 1, 1), storage, heater_vn=0.01, init_vn=[0.0, 0.0, 0.01])
+    elif geom == "walls-odd-nx":
+        # an odd nx: one cell per thread with 16-bit storage
+        p = params((21, 18, 20), (1, 1, 1), storage, heater_vn=0.01, init_vn=[0.0, 0.0, 0.01])
+    else:
+        p = params((24, 20, 16), (0, 0, 0), storage, pin_vn=0.01, init_vn=[0.0, 0.0, 0.01])
     g, r = pair(p)
     same_lattice_state(g, r, seed=11, amp=1e-2, force_amp=2e-4)
     F = g.read(vlb.FIELD_FORCE)  # each pass consumes the force grid: give every pass the same one
