@@ -59,13 +59,13 @@ def launches_per_step(n_points: int) -> int:
     flags, stream-collide, plane reduction with the force-grid reset),
     filaments 4 x 3 (per RK stage geometry, Biot-Savart, equation of motion),
     remesh 2, reconnection 4, and the 2 that assign the Biot-Savart source
-    slots once per step = 23.  From 8192 points on, 4 more build the spatial
+    slots once per step = 23.  From 8192 points on, 3 more build the spatial
     order of the sources first; from 24576 points on the Biot-Savart kernel
     applies the equation of motion itself (4 fewer; or as VLB_FUSED_EOM
     forces)."""
     mode = os.environ.get("VLB_FUSED_EOM")
     fused = n_points >= 24576 if mode is None else mode != "0"
-    return (19 if fused else 23) + (4 if n_points >= 8192 else 0)
+    return (19 if fused else 23) + (3 if n_points >= 8192 else 0)
 
 
 def launches(n_points: int, steps: int, overlap: bool = True) -> int:
@@ -318,7 +318,7 @@ def run_vlb(args, ws, rank, local):
     k1_avg_s = (k1_ms / 1e3) / max(k1_n, 1)
     k1_achieved = bpc * cells / k1_avg_s / 1e9 if k1_n else None
     k1_name = k1_kernel(args.storage, p["n"][0])
-    k1_traffic = profile_traffic(k1_name, args.config, ["lbm.cu"])
+    k1_traffic = profile_traffic(k1_name, args.config, ["lbm.cu", "vlb_internal.cuh"])
     # Biot-Savart: N (N - 2) pairs per launch at the mean live count of the
     # event-timed steps, 45 FP32 flop each, against the FP32 peak of this
     # GPU (SMs x 128 lanes x 2 flop x clock) at the maximum clock and at the

@@ -268,8 +268,7 @@ void bs_sort(vlb_channel* ch, const BsOrder& o, cudaStream_t s) {
     Dev& d = ch->d;
     const int span = point_span(ch->n_hint, ch->cap);
     if (o.sorted)
-        launch_bs_sort(ch->vp.g, d.pos[ch->cur_p], ch->cap, span, d.counters, d.bs_key, d.bs_tmp, d.bs_ord,
-                       d.bs_rank, d.bs_cnt, d.bs_start, s);
+        launch_bs_sort(ch->vp.g, d.pos[ch->cur_p], ch->cap, d.counters, d.bs_key, d.bs_hist, d.bs_ord, d.bs_rank, s);
     launch_bs_slots(d.pos[ch->cur_p], d.next[ch->cur_p], ch->cap, span, d.counters, o, d.bs_bsum, s);
 }
 
@@ -466,15 +465,13 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
     int* prev = (int*)take(sizeof(int) * (size_t)n);
     float4* seg = (float4*)take(sizeof(float4) * BS_REC * slots);
     int* key = (int*)take(sizeof(int) * (size_t)n);
-    int* tmp = (int*)take(sizeof(int) * (size_t)n);
+    int* hist = (int*)take(sizeof(int) * (size_t)n);
     int* ord = (int*)take(sizeof(int) * (size_t)n);
     int* rank = (int*)take(sizeof(int) * (size_t)n);
     int* slot = (int*)take(sizeof(int) * (size_t)n);
     int* pt = (int*)take(sizeof(int) * slots);
     float4* tgt = (float4*)take(sizeof(float4) * 4 * (size_t)n);
     int4* org = (int4*)take(sizeof(int4) * (slots / BS_GROUP));
-    int* cnt = (int*)take(sizeof(int) * BS_SORT_MAX_BINS);
-    int* start = (int*)take(sizeof(int) * BS_SORT_MAX_BINS);
     int* bsum = (int*)take(sizeof(int) * BS_SLOT_BLOCKS);
     long long* vacc = (long long*)take(sizeof(long long) * 3 * (size_t)n);
     cudaStream_t s = (cudaStream_t)stream;
@@ -486,9 +483,8 @@ int bs_standalone(const vlb_params* p, const double* pos, const int32_t* next, i
     o.pt = pt;
     o.org = org;
     o.tgt = tgt;
-    if (o.sorted) cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)bs_bins(g.nx, g.ny, g.nz).K, s);
     cudaMemsetAsync(vacc, 0, sizeof(long long) * 3 * (size_t)n, s);
-    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, o, key, tmp, cnt, start, bsum, s);
+    launch_bs_standalone_prep(g, pos, next, n, prev, seg, counters, o, key, hist, bsum, s);
     launch_biot_savart(g, p->kappa, seg, prev, counters, nullptr, n, n, nullptr, vel, s, o, nullptr, 0, nullptr,
                        nullptr, vacc);
     launch_bs_unfix(vacc, n, vel, s);
@@ -524,7 +520,7 @@ size_t vlb_channel_bytes(const vlb_params* p) {
          up(sizeof(float4) * BS_REC * capg * (1 + nfaces));
     b += up(12 * cap * (size_t)bs_max_splits((int)cap, sm_count())) + up(12 * cap) + up(24 * cap) +
          up(4 * ((cap + 127) / 128));
-    b += 5 * up(4 * cap) + up(16 * (capg / BS_GROUP)) + 2 * up(4 * (size_t)bs_bins(p->n[0], p->n[1], p->n[2]).K) +
+    b += 5 * up(4 * cap) + up(16 * (capg / BS_GROUP)) +
          up(4 * BS_SLOT_BLOCKS) + up(4 * capg) + up(64 * cap);
     b += 2 * up(cap) + 4 * up(4 * cap) + up(4 * h) + 2 * up(4 * cap) + up(16 * cap) + up(8 * cap);
     const size_t nc = cap / 2 + 1;
@@ -662,7 +658,6 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     ch->wpp = lbm_warps_per_plane(L);
     const int nsm = bs_max_splits(cap, sm_count());
     ch->nsplit_max = nsm;
-    const BsBins bins = bs_bins(g.nx, g.ny, g.nz);
     const size_t capg = (size_t)bs_slot_cap(cap);  // source slots: a point and a gap slot each, whole groups
     const int ntiles = g.tnx * g.tny * g.tnz;
     Dev& d = ch->d;
@@ -701,7 +696,7 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.geo = (float4*)A(sizeof(float4) * 2 * (size_t)cap);
     d.seg = (float4*)A(sizeof(float4) * BS_REC * capg * (size_t)(1 + V.nfaces));  // segments, then wall images
     d.bs_key = (int*)A(sizeof(int) * (size_t)cap);
-    d.bs_tmp = (int*)A(sizeof(int) * (size_t)cap);
+    d.bs_hist = (int*)A(sizeof(int) * (size_t)cap);
     d.bs_ord = (int*)A(sizeof(int) * (size_t)cap);
     d.bs_rank = (int*)A(sizeof(int) * (size_t)cap);
     d.bs_org = (int4*)A(sizeof(int4) * (capg / BS_GROUP));
@@ -709,8 +704,6 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     d.bs_pt = (int*)A(sizeof(int) * capg);
     d.bs_tgt = (float4*)A(sizeof(float4) * 4 * (size_t)cap);
     d.bs_bsum = (int*)A(sizeof(int) * BS_SLOT_BLOCKS);
-    d.bs_cnt = (int*)A(sizeof(int) * (size_t)bins.K);
-    d.bs_start = (int*)A(sizeof(int) * (size_t)bins.K);
     d.bsp = (float*)A(sizeof(float) * 3 * (size_t)cap * (size_t)nsm);
     d.vbs = (float*)A(sizeof(float) * 3 * (size_t)cap);
     d.vacc = (long long*)A(sizeof(long long) * 3 * (size_t)cap);
@@ -765,7 +758,6 @@ int vlb_create_channel(const vlb_params* p, const vlb_allocator* alloc, void* st
     cudaMemsetAsync(d.vel1, 0, sizeof(double) * 3 * (size_t)cap, s);
     cudaMemsetAsync(d.bsp, 0, sizeof(float) * 3 * (size_t)cap * (size_t)nsm, s);
     cudaMemsetAsync(d.tile_ticket, 0, sizeof(int) * (size_t)((cap + BS_TPB - 1) / BS_TPB), s);
-    cudaMemsetAsync(d.bs_cnt, 0, sizeof(int) * (size_t)bins.K, s);  // the sort clears what it counts
     init_hash(d, h, s);
     launch_lbm_init(L, d.f[0], d.U, p->init_vn, s);
     std::vector<double> vs((size_t)g.nz, -(1.0 / p->rho_s_over_rho_n) * p->init_vn[2]);

@@ -1045,15 +1045,13 @@ void launch_biot_savart(const Grid& g, double kappa, const float4* seg, const in
 }
 
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
-                               int* counters, const BsOrder& o, int* key, int* tmp, int* cnt, int* start, int* bsum,
-                               cudaStream_t s) {
+                               int* counters, const BsOrder& o, int* key, int* hist, int* bsum, cudaStream_t s) {
     k_bs_counters<<<1, 1, 0, s>>>(counters, n);
     cudaMemsetAsync(prev, 0xff, sizeof(int) * (size_t)n, s);  // first points of open lines keep -1
     k_bs_prev<<<(n + 255) / 256, 256, 0, s>>>(next, n, prev, counters);
     // the caller's positions are SoA [3][n]
     if (o.sorted)
-        launch_bs_sort(g, pos, n, n, counters, key, tmp, const_cast<int*>(o.ord), const_cast<int*>(o.rank), cnt,
-                       start, s);
+        launch_bs_sort(g, pos, n, counters, key, hist, const_cast<int*>(o.ord), const_cast<int*>(o.rank), s);
     launch_bs_slots(pos, next, n, n, counters, o, bsum, s);
     k_bs_points<<<(int)(bs_slot_cap(n) / BS_GROUP), BS_GROUP, 0, s>>>(g, pos, next, prev, n, counters, seg, o);
 }

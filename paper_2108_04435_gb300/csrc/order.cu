@@ -1,9 +1,9 @@
 // Spatial order of the Biot-Savart sources (the points of the current step):
-// a Morton key per point from its bin of 16 cells (wider on lattices of more
-// than 65536 bins), a counting sort over the bins, and inside each bin the
-// points in ascending index, so that the order depends on nothing but the
-// positions (and a line's points, numbered along it, mostly stay
-// consecutive).  Built once per step from BS_SORT_MIN points on.
+// a Morton key per point from its bin (16 cells wide or more, see bs_bins),
+// a stable counting sort over the bins, so that inside each bin the points
+// keep ascending index and the order depends on nothing but the positions
+// (and a line's points, numbered along it, mostly stay consecutive).  Built
+// once per step from BS_SORT_MIN points on.
 //
 // Then, in any order, the source slots: every sorted position k takes slot
 // k + (gap slots before it), a gap slot following k when the successor of
@@ -38,38 +38,60 @@ __device__ __forceinline__ int bs_key_of(const Grid& g, const BsBins& bb, double
     return key;
 }
 
-// Key and bin count of every point (grid-stride beyond the grid).
-__global__ void k_sort_keys(Grid g, BsBins bb, const double* __restrict__ pos, int cap,
-                            const int* __restrict__ counters, int* __restrict__ key, int* __restrict__ cnt) {
+// The sort is a stable counting sort over the bins (a key has at most 8
+// bits, see bs_bins), in three launches over blocks of SORT_BLOCK
+// consecutive point indices: each block counts its points per bin; one block
+// scans the counts bin-major (bin 0 of every block, then bin 1, ...); each
+// block then places its points, a point's place being the scanned count of
+// its bin and block plus the points of its bin before it in the block (by
+// warp, then by lane).  Inside a bin the points so keep ascending index, and
+// the order depends on the positions alone.  No atomic touches global memory
+// (few wide bins would make atomic counters a hot spot) and no step
+// compares the points of a bin with each other (a wide bin can hold
+// thousands).
+constexpr int SORT_BLOCK = 1024;
+
+// Key of every point of block b, and the block's count per bin at
+// hist[key * nblk + b] (keys K and beyond: zero).
+__global__ void __launch_bounds__(SORT_BLOCK) k_sort_count(Grid g, BsBins bb, const double* __restrict__ pos, int cap,
+                                                           const int* __restrict__ counters, int* __restrict__ key,
+                                                           int* __restrict__ hist, int nblk) {
     pdl_wait_trigger();
+    __shared__ int h[256];
     const int N = counters[CNT_N];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int i = blockIdx.x * SORT_BLOCK + threadIdx.x;
+    if (threadIdx.x < 256) h[threadIdx.x] = 0;
+    __syncthreads();
+    if (i < N) {
         const int k = bs_key_of(g, bb, pos[i], pos[(long long)cap + i], pos[2LL * cap + i]);
         key[i] = k;
-        atomicAdd(&cnt[k], 1);
+        atomicAdd(&h[k], 1);
     }
+    __syncthreads();
+    if ((int)threadIdx.x < bb.K) hist[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of the bin counts (one block of 1024 threads), 4096 bins
-// per round: each thread takes four consecutive bins with one 16-byte load
+// Exclusive scan in place of L counts (one block of 1024 threads), 4096 per
+// round: each thread takes four consecutive counts with one 16-byte load
 // (a warp reads 512 contiguous bytes), the block scans the thread sums, and
-// a carry runs from round to round.  K is a power of two.
-__global__ void __launch_bounds__(1024) k_sort_scan(int K, const int* __restrict__ cnt, int* __restrict__ start) {
+// a carry runs from round to round.  Every thread writes back only the
+// counts it read, so the scan can run in place.
+__global__ void __launch_bounds__(1024) k_sort_scan(int L, int* v) {
     pdl_wait_trigger();
     __shared__ int warp_sum[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int carry = 0;
-    for (int base = 0; base < K; base += 4096) {
+    for (int base = 0; base < L; base += 4096) {
         const int k0 = base + 4 * (int)threadIdx.x;
-        int4 v = make_int4(0, 0, 0, 0);
-        if (k0 + 3 < K) {
-            v = *reinterpret_cast<const int4*>(cnt + k0);
-        } else if (k0 < K) {
-            v.x = cnt[k0];
-            if (k0 + 1 < K) v.y = cnt[k0 + 1];
-            if (k0 + 2 < K) v.z = cnt[k0 + 2];
+        int4 c = make_int4(0, 0, 0, 0);
+        if (k0 + 3 < L) {
+            c = *reinterpret_cast<const int4*>(v + k0);
+        } else if (k0 < L) {
+            c.x = v[k0];
+            if (k0 + 1 < L) c.y = v[k0 + 1];
+            if (k0 + 2 < L) c.z = v[k0 + 2];
         }
-        const int sum = v.x + v.y + v.z + v.w;
+        const int sum = c.x + c.y + c.z + c.w;
         int x = sum;  // inclusive scan within the warp
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -89,55 +111,55 @@ __global__ void __launch_bounds__(1024) k_sort_scan(int K, const int* __restrict
         }
         __syncthreads();
         const int excl = carry + (x - sum) + (w > 0 ? warp_sum[w - 1] : 0);
-        if (k0 + 3 < K) {
-            *reinterpret_cast<int4*>(start + k0) = make_int4(excl, excl + v.x, excl + v.x + v.y, excl + v.x + v.y + v.z);
-        } else if (k0 < K) {
-            start[k0] = excl;
-            if (k0 + 1 < K) start[k0 + 1] = excl + v.x;
-            if (k0 + 2 < K) start[k0 + 2] = excl + v.x + v.y;
+        if (k0 + 3 < L) {
+            *reinterpret_cast<int4*>(v + k0) = make_int4(excl, excl + c.x, excl + c.x + c.y, excl + c.x + c.y + c.z);
+        } else if (k0 < L) {
+            v[k0] = excl;
+            if (k0 + 1 < L) v[k0 + 1] = excl + c.x;
+            if (k0 + 2 < L) v[k0 + 2] = excl + c.x + c.y;
         }
         carry += warp_sum[31];
         __syncthreads();  // warp_sum is rewritten by the next round
     }
 }
 
-// Every point into its bin (arbitrary order inside the bin; start[k] ends as
-// the bin's end).
-__global__ void k_sort_scatter(const int* __restrict__ counters, const int* __restrict__ key, int* __restrict__ start,
-                               int* __restrict__ tmp) {
+// Place of every point of block b: the scanned count of its bin and block,
+// plus its rank among the points of its bin in the warps before its own
+// (per-warp counts in shared memory, summed over the warps per bin), plus
+// its rank among the lanes of its warp with the same bin (a match over the
+// warp).  Writes ord (point at each sorted position) and rank (sorted
+// position of each point).
+__global__ void __launch_bounds__(SORT_BLOCK) k_sort_place(int K, const int* __restrict__ counters,
+                                                           const int* __restrict__ key, const int* __restrict__ hist,
+                                                           int nblk, int* __restrict__ ord, int* __restrict__ rank) {
     pdl_wait_trigger();
+    constexpr int NW = SORT_BLOCK / 32;
+    __shared__ int wc[NW][256];
     const int N = counters[CNT_N];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        tmp[atomicAdd(&start[key[i]], 1)] = i;
-}
-
-// One warp per bin: the bin's points in ascending index (so the order is
-// deterministic), their ranks, and the bin count cleared for the next sort.
-__global__ void k_sort_bins(int K, int* __restrict__ cnt, const int* __restrict__ start, const int* __restrict__ tmp,
-                            int* __restrict__ ord, int* __restrict__ rank) {
-    pdl_wait_trigger();
-    const int lane = threadIdx.x & 31;
-    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (k >= K) return;
-    const int n = cnt[k];
-    if (n == 0) return;
-    const int e = start[k], s0 = e - n;
-    for (int c = 0; c < n; c += 32) {
-        const int my = c + lane < n ? tmp[s0 + c + lane] : 0x7fffffff;
-        int r = 0;
-        for (int m = 0; m < n; m += 32) {
-            const int other = m + lane < n ? tmp[s0 + m + lane] : 0x7fffffff;
-#pragma unroll 8
-            for (int q = 0; q < 32; ++q) r += __shfl_sync(0xffffffffu, other, q) < my;
-        }
-        if (c + lane < n) {
-            const int p = s0 + r;
-            ord[p] = my;
-            rank[my] = p;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * SORT_BLOCK + threadIdx.x;
+    const bool live = i < N;
+    const int k = live ? key[i] : K;  // dead lanes match only each other
+    for (int e = threadIdx.x; e < NW * 256; e += SORT_BLOCK) (&wc[0][0])[e] = 0;
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    const int before = __popc(peers & ((1u << lane) - 1u));
+    __syncthreads();
+    if (live && before == 0) wc[w][k] = __popc(peers);
+    __syncthreads();
+    if ((int)threadIdx.x < K) {
+        int run = 0;
+        for (int u = 0; u < NW; ++u) {
+            const int c = wc[u][threadIdx.x];
+            wc[u][threadIdx.x] = run;
+            run += c;
         }
     }
-    __syncwarp();
-    if (lane == 0) cnt[k] = 0;
+    __syncthreads();
+    if (live) {
+        const int p = hist[k * nblk + blockIdx.x] + wc[w][k] + before;
+        ord[p] = i;
+        rank[i] = p;
+    }
 }
 
 __device__ __forceinline__ int bs_point_at(const BsOrder& o, int k) { return o.sorted ? o.ord[k] : k; }
@@ -245,14 +267,13 @@ __global__ void __launch_bounds__(1024) k_slot_assign(const double* __restrict__
 
 }  // namespace
 
-void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
-                    int* ord, int* rank, int* cnt, int* start, cudaStream_t s) {
+void launch_bs_sort(const Grid& g, const double* pos, int cap, const int* counters, int* key, int* hist, int* ord,
+                    int* rank, cudaStream_t s) {
     const BsBins bb = bs_bins(g.nx, g.ny, g.nz);
-    const int blocks = (span + 255) / 256 > 0 ? (span + 255) / 256 : 1;
-    launch_pdl(k_sort_keys, blocks, 256, 0, s, g, bb, pos, cap, counters, key, cnt);
-    launch_pdl(k_sort_scan, 1, 1024, 0, s, bb.K, (const int*)cnt, start);
-    launch_pdl(k_sort_scatter, blocks, 256, 0, s, counters, (const int*)key, start, tmp);
-    launch_pdl(k_sort_bins, (bb.K * 32 + 255) / 256, 256, 0, s, bb.K, cnt, (const int*)start, (const int*)tmp, ord,
+    const int nblk = (cap + SORT_BLOCK - 1) / SORT_BLOCK > 0 ? (cap + SORT_BLOCK - 1) / SORT_BLOCK : 1;
+    launch_pdl(k_sort_count, nblk, SORT_BLOCK, 0, s, g, bb, pos, cap, counters, key, hist, nblk);
+    launch_pdl(k_sort_scan, 1, 1024, 0, s, bb.K * nblk, hist);
+    launch_pdl(k_sort_place, nblk, SORT_BLOCK, 0, s, bb.K, counters, (const int*)key, (const int*)hist, nblk, ord,
                rank);
 }
 

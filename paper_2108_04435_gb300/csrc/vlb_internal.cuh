@@ -62,7 +62,16 @@ constexpr int TILE_SHIFT = 3;   // force / velocity activity tiles of 8^3 cells
 // is bitwise reproducible.  A contribution is rounded to the grid once.
 constexpr int FORCE_FRAC = 44;
 __device__ __forceinline__ long long force_fixed(float v) { return __float2ll_rn(v * 0x1p44f); }
-__device__ __forceinline__ float force_value(long long a) { return __ll2float_rn(a) * 0x1p-44f; }
+// The grid value as a float from its two 32-bit words: the high word is exact
+// in FP32 while |a| < 2^56 (|F| < 4096), so the result carries at most two
+// roundings (the low word, the fused add) instead of one.  A 64-bit integer
+// conversion would run on GB300's FP64 pipe, which measured 22% busy in the
+// stream-collide pass from these conversions alone.
+__device__ __forceinline__ float force_value(long long a) {
+    const float hi = __int2float_rn((int)(a >> 32));
+    const float lo = __uint2float_rn((unsigned)(a & 0xffffffffll));
+    return fmaf(hi, 0x1p32f, lo) * 0x1p-44f;
+}
 
 // Biot-Savart split sums below the fused size, accumulated the same way: int64
 // with 40 fractional bits (resolution 9.1e-13, range 8.4e6 in lattice units),
@@ -114,7 +123,7 @@ constexpr int MAX_SPLIT = 64;   // Biot-Savart source splits
 // From this many points on the Biot-Savart sources are put in a spatial order
 // once per step, so that a group of BS_GROUP slots spans a small box
 constexpr int BS_SORT_MIN = 8192;
-constexpr int BS_SORT_MAX_BINS = 1 << 16;  // bins of the spatial order (bin edge 16 cells or more)
+constexpr int BS_SORT_MAX_BINS = 256;  // bins of the spatial order (a key of at most 8 bits)
 
 // Biot-Savart sources as a chain of slots.  Each point of the order
 // (sorted position k) owns one slot, slot[k], holding its segment
@@ -169,9 +178,16 @@ struct BsOrder {
 
 // Bins of the spatial order: the cell floor(x) >> shift per axis, clamped to
 // the lattice, interleaved bit by bit (x, y, z) into a Morton key < K.
-// Bins of 16 cells: a line crosses fewer bin edges than with 8 (1.08 slots
-// per point instead of 1.14 on the 128x128x1024 channel), and a group of
-// slots spans the same ~30 cells.
+// The bin edge is the widest of 64, 32 and 16 cells that still leaves at
+// least 64 bins: wider bins break the lines less often (a gap slot wherever
+// a line leaves its bin: 1.14 slots per point with 8-cell bins on the
+// 128x128x1024 channel, 1.08 with 16, 1.045 with 32, 1.025 with 64), and
+// enough bins keep each group of slots compact.  Measured per Biot-Savart
+// launch on GB300: the channel 5.71 ms with 16-cell bins, 5.56 with 32, 5.50
+// with 64 (64 bins); the 128^3 box 613, 603 and 648 us (8 bins at 64).
+// Lattices that would need more than 256 bins widen them further, so that a
+// key has at most 8 bits (the counting sort keeps a count per bin for each
+// block of points in shared memory).
 struct BsBins {
     int shift;
     int bits[3];
@@ -186,14 +202,19 @@ __host__ __device__ inline int bs_ceil_log2(int v) {
 
 __host__ __device__ inline BsBins bs_bins(int nx, int ny, int nz) {
     BsBins b;
-    b.shift = 4;
+    auto bins = [&](int sh) {
+        const int e = 1 << sh;
+        return (long long)((nx + e - 1) / e) * ((ny + e - 1) / e) * ((nz + e - 1) / e);
+    };
+    b.shift = 6;
+    while (b.shift > 4 && bins(b.shift) < 64) --b.shift;
     while (true) {
         const int e = 1 << b.shift;
         b.bits[0] = bs_ceil_log2((nx + e - 1) / e);
         b.bits[1] = bs_ceil_log2((ny + e - 1) / e);
         b.bits[2] = bs_ceil_log2((nz + e - 1) / e);
         const int tot = b.bits[0] + b.bits[1] + b.bits[2];
-        if (tot <= 16) {
+        if (tot <= 8) {
             b.K = 1 << tot;
             return b;
         }
@@ -349,7 +370,7 @@ struct Dev {
     double* seglen;     // FP64 segment lengths for remeshing
     float4* seg;        // Biot-Savart source slots, BS_REC float4 each (segments, then wall images)
     int* bs_key;        // spatial order: Morton key of each point
-    int* bs_tmp;        // spatial order: points scattered by key, before the in-bin sort
+    int* bs_hist;       // spatial order: per-block bin counts, then their scan
     int* bs_ord;        // sorted position -> point
     int* bs_rank;       // point -> sorted position
     int4* bs_org;       // integer origin of each group of BS_GROUP slots (w: jump flag)
@@ -357,8 +378,6 @@ struct Dev {
     int* bs_pt;         // slot -> its point (or gap, padding) [slot capacity]
     float4* bs_tgt;     // target records, 4 float4 per sorted position
     int* bs_bsum;       // gap slots per block of the slot scan [BS_SLOT_BLOCKS]
-    int* bs_cnt;        // points per bin (zero between sorts)
-    int* bs_start;      // bin starts
     float* bsp;         // Biot-Savart partial sums [splits][3][cap]
     float* vbs;         // Biot-Savart velocity [3][cap]
     long long* vacc;    // Biot-Savart velocity [3][cap], fixed point (bs_fixed), zero between uses
@@ -423,10 +442,12 @@ void launch_line_length(const Grid& g, const double* pos, const int* next, int* 
 int sm_count();
 int bs_max_splits(int cap, int nsm);
 // Spatial order of the points pos[3][cap] (count from the device counters):
-// bs_ord and bs_rank.  span: points one pass of the per-point grids covers
-// (they stride over any beyond).
-void launch_bs_sort(const Grid& g, const double* pos, int cap, int span, const int* counters, int* key, int* tmp,
-                    int* ord, int* rank, int* cnt, int* start, cudaStream_t s);
+// bs_ord and bs_rank.  hist: scratch of at least
+// BS_SORT_MAX_BINS * ceil(cap / 1024) ints (at most cap for every cap the
+// order is built for).  The grids cover all cap points, so a count that grew
+// within the step is ordered whole.
+void launch_bs_sort(const Grid& g, const double* pos, int cap, const int* counters, int* key, int* hist, int* ord,
+                    int* rank, cudaStream_t s);
 // Slots of the order o for the points pos[3][cap] with successors next[]
 // (indices outside [-1, N) count as -1): o.slot, o.pt, the group origins
 // o.org and counters[CNT_NSLOT].  bsum: scratch [BS_SLOT_BLOCKS].
@@ -457,8 +478,7 @@ bool bs_uses_vacc(int n_hint);
 // the slots and the source records of a caller's point set, into the scratch
 // buffers.
 void launch_bs_standalone_prep(const Grid& g, const double* pos, const int* next, int n, int* prev, float4* seg,
-                               int* counters, const BsOrder& o, int* key, int* tmp, int* cnt, int* start, int* bsum,
-                               cudaStream_t s);
+                               int* counters, const BsOrder& o, int* key, int* hist, int* bsum, cudaStream_t s);
 // vel[3][n] = the fixed-point sums vacc[3][n] (stand-alone entry)
 void launch_bs_unfix(const long long* vacc, int n, float* vel, cudaStream_t s);
 
@@ -473,7 +493,7 @@ __host__ __device__ constexpr size_t bs_scratch_bytes(long long n) {
            bs_up256(sizeof(float4) * BS_REC * (size_t)bs_slot_cap(n)) + 5 * bs_up256(sizeof(int) * (size_t)n) +
            bs_up256(sizeof(int) * (size_t)bs_slot_cap(n)) + bs_up256(sizeof(float4) * 4 * (size_t)n) +
            bs_up256(sizeof(int4) * (size_t)(bs_slot_cap(n) / BS_GROUP)) +
-           2 * bs_up256(sizeof(int) * (size_t)BS_SORT_MAX_BINS) + bs_up256(sizeof(int) * (size_t)BS_SLOT_BLOCKS) +
+           bs_up256(sizeof(int) * (size_t)BS_SLOT_BLOCKS) +
            bs_up256(sizeof(long long) * 3 * (size_t)n);
 }
 
