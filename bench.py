@@ -649,7 +649,7 @@ def main():
                 line["serving"] = {k: sv[k] for k in ("value", "unit", "speedup_vs_fp32_single_run", "p50_latency_s",
                                                       "p99_latency_s", "failed", "config")}
                 line["serving"]["forms"] = {f: {k: v[k] for k in ("throughput_req_per_s", "mlups", "failed",
-                                                                  "errors", "wall_s")}
+                                                                  "failed_ids", "errors", "wall_s")}
                                             for f, v in sv["forms"].items()}
             if not args.no_cpu_baseline:
                 v, desc, _ = oracle_sample(p, xyz, nxt, args.cpu_budget)

@@ -145,6 +145,7 @@ def summarize(results, wall_s: float):
         "throughput_req_per_s": len(ok) / wall_s, "mlups": cells_steps / wall_s / 1e6,
         "filament_pts_per_s": pts_steps / wall_s, "wall_s": wall_s,
         "errors": sorted({r.error for r in results if r.error})[:5],
+        "failed_ids": [r.id for r in results if r.error],
     }
 
 
