@@ -242,6 +242,21 @@ __device__ int block_small_components(const int* __restrict__ succ, uint8_t* __r
     return dead;
 }
 
+// Empty the hash buckets of points [0, N) (one block): eight points per
+// thread and round, their bucket indices loaded before the stores.
+__device__ __forceinline__ void block_clear_buckets(const int* __restrict__ hkey, int* __restrict__ hhead, int N) {
+    constexpr int PASS = 8;
+    const int stride = (int)blockDim.x;
+    for (int k0 = threadIdx.x; k0 < N; k0 += PASS * stride) {
+        int h[PASS];
+#pragma unroll
+        for (int u = 0; u < PASS; ++u) h[u] = k0 + u * stride < N ? hkey[k0 + u * stride] : -1;
+#pragma unroll
+        for (int u = 0; u < PASS; ++u)
+            if (h[u] >= 0) hhead[h[u]] = -1;
+    }
+}
+
 // One block: stable compaction of the alive points of [0, T) into the other
 // point buffer, successor indices renumbered, predecessors rebuilt.  The
 // points go in chunks of blockDim.x consecutive indices, one per thread: a
@@ -255,11 +270,37 @@ __device__ void block_compact(const double* __restrict__ pin, const int* __restr
                               double* __restrict__ pout, int* __restrict__ nout, int* __restrict__ pvout,
                               int* __restrict__ counters, int cap, const int* __restrict__ identity_prev = nullptr) {
     if (identity_prev) {
-        for (int k = threadIdx.x; k < T; k += blockDim.x) {
-            for (int c = 0; c < 3; ++c) pout[(long long)c * cap + k] = pin[(long long)c * cap + k];
-            nout[k] = succ[k];
-            pvout[k] = identity_prev[k];
-            newidx[k] = k;
+        // PASS points per thread and round, every load before the stores: one
+        // block moving the whole point set is bound by memory latency, and a
+        // round of one point each took ~2 us (170 us for 86k points)
+        constexpr int PASS = 8;
+        const int stride = (int)blockDim.x;
+        for (int k0 = threadIdx.x; k0 < T; k0 += PASS * stride) {
+            double px[PASS], py[PASS], pz[PASS];
+            int sn[PASS], pv[PASS];
+#pragma unroll
+            for (int u = 0; u < PASS; ++u) {
+                const int k = k0 + u * stride;
+                if (k < T) {
+                    px[u] = pin[k];
+                    py[u] = pin[(long long)cap + k];
+                    pz[u] = pin[2LL * cap + k];
+                    sn[u] = succ[k];
+                    pv[u] = identity_prev[k];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PASS; ++u) {
+                const int k = k0 + u * stride;
+                if (k < T) {
+                    pout[k] = px[u];
+                    pout[(long long)cap + k] = py[u];
+                    pout[2LL * cap + k] = pz[u];
+                    nout[k] = sn[u];
+                    pvout[k] = pv[u];
+                    newidx[k] = k;
+                }
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) counters[CNT_N] = T;
@@ -622,7 +663,7 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     if (s_quiet) {
         // no candidate exchange, no wall contact and nothing newly seeded:
         // empty the hash buckets and pass the points and links through
-        for (int k = threadIdx.x; k < N; k += blockDim.x) hhead[hkey[k]] = -1;
+        block_clear_buckets(hkey, hhead, N);
         if (threadIdx.x == 0) counters[CNT_STAMP] += 1;
         block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, prev);
         return;
@@ -637,10 +678,8 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
         }
         order[r] = c;
     }
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        alive[k] = 1;
-        hhead[hkey[k]] = -1;
-    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) alive[k] = 1;
+    block_clear_buckets(hkey, hhead, N);
     __shared__ int s_changed;  // an exchange or a cut happened: small components may have formed
     __syncthreads();
     if (threadIdx.x == 0) {
