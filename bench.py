@@ -58,14 +58,15 @@ def launches_per_step(n_points: int) -> int:
     """Kernels of one coupled step (1 RK4 sub-step): lattice 3 (velocity-tile
     flags, stream-collide, plane reduction with the force-grid reset),
     filaments 4 x 3 (per RK stage geometry, Biot-Savart, equation of motion),
-    remesh 2, reconnection 4, and the 2 that assign the Biot-Savart source
-    slots once per step = 23.  From 8192 points on, 3 more build the spatial
+    remesh 3, reconnection 5 (each ends with the kernel that copies the points
+    when its finish changed nothing), and the 2 that assign the Biot-Savart
+    source slots once per step = 25.  From 8192 points on, 3 more build the spatial
     order of the sources first; from 24576 points on the Biot-Savart kernel
     applies the equation of motion itself (4 fewer; or as VLB_FUSED_EOM
     forces)."""
     mode = os.environ.get("VLB_FUSED_EOM")
     fused = n_points >= 24576 if mode is None else mode != "0"
-    return (19 if fused else 23) + (3 if n_points >= 8192 else 0)
+    return (21 if fused else 25) + (3 if n_points >= 8192 else 0)
 
 
 def launches(n_points: int, steps: int, overlap: bool = True) -> int:
@@ -310,8 +311,8 @@ def run_vlb(args, ws, rank, local):
     e2e_block_units, e2e_block_secs = aggregate(cells * args.steps, e2e_block_s, ws)
     h2d = (xyz.size * 8 + nxt.size * 4) / args.steps
     # per step call: the status block (12 doubles of statistics, the line
-    # length among them, and 13 int counters); at the end, the filaments
-    d2h = 12 * 8 + 13 * 4 + final.nbytes / args.steps
+    # length among them, and 14 int counters); at the end, the filaments
+    d2h = 12 * 8 + 14 * 4 + final.nbytes / args.steps
 
     pk, pk_kind = peaks()
     # stream-collide: algorithmic bytes / mean event-timed launch

@@ -242,70 +242,16 @@ __device__ int block_small_components(const int* __restrict__ succ, uint8_t* __r
     return dead;
 }
 
-// Empty the hash buckets of points [0, N) (one block): eight points per
-// thread and round, their bucket indices loaded before the stores.
-__device__ __forceinline__ void block_clear_buckets(const int* __restrict__ hkey, int* __restrict__ hhead, int N) {
-    constexpr int PASS = 8;
-    const int stride = (int)blockDim.x;
-    for (int k0 = threadIdx.x; k0 < N; k0 += PASS * stride) {
-        int h[PASS];
-#pragma unroll
-        for (int u = 0; u < PASS; ++u) h[u] = k0 + u * stride < N ? hkey[k0 + u * stride] : -1;
-#pragma unroll
-        for (int u = 0; u < PASS; ++u)
-            if (h[u] >= 0) hhead[h[u]] = -1;
-    }
-}
-
 // One block: stable compaction of the alive points of [0, T) into the other
 // point buffer, successor indices renumbered, predecessors rebuilt.  The
 // points go in chunks of blockDim.x consecutive indices, one per thread: a
 // ballot per warp and a scan over the warps rank the alive points of a chunk,
 // so every load and store of a chunk is coalesced (per-thread ranges of
 // consecutive points made each warp access touch 32 lines).
-// identity_prev != nullptr (uniform): every point of [0, T) survives in place
-// and the links are unchanged, so the arrays are copied as they are.
 __device__ void block_compact(const double* __restrict__ pin, const int* __restrict__ succ,
                               const uint8_t* __restrict__ alive, int T, int* __restrict__ newidx,
                               double* __restrict__ pout, int* __restrict__ nout, int* __restrict__ pvout,
-                              int* __restrict__ counters, int cap, const int* __restrict__ identity_prev = nullptr) {
-    if (identity_prev) {
-        // PASS points per thread and round, every load before the stores: one
-        // block moving the whole point set is bound by memory latency, and a
-        // round of one point each took ~2 us (170 us for 86k points)
-        constexpr int PASS = 8;
-        const int stride = (int)blockDim.x;
-        for (int k0 = threadIdx.x; k0 < T; k0 += PASS * stride) {
-            double px[PASS], py[PASS], pz[PASS];
-            int sn[PASS], pv[PASS];
-#pragma unroll
-            for (int u = 0; u < PASS; ++u) {
-                const int k = k0 + u * stride;
-                if (k < T) {
-                    px[u] = pin[k];
-                    py[u] = pin[(long long)cap + k];
-                    pz[u] = pin[2LL * cap + k];
-                    sn[u] = succ[k];
-                    pv[u] = identity_prev[k];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < PASS; ++u) {
-                const int k = k0 + u * stride;
-                if (k < T) {
-                    pout[k] = px[u];
-                    pout[(long long)cap + k] = py[u];
-                    pout[2LL * cap + k] = pz[u];
-                    nout[k] = sn[u];
-                    pvout[k] = pv[u];
-                    newidx[k] = k;
-                }
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) counters[CNT_N] = T;
-        return;
-    }
+                              int* __restrict__ counters, int cap) {
     __shared__ int s_off[33];  // per-warp exclusive offsets of a chunk; [32] = the chunk's count
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)blockDim.x >> 5;
     int M = 0;
@@ -356,6 +302,27 @@ __device__ void block_compact(const double* __restrict__ pin, const int* __restr
     if (threadIdx.x == 0) counters[CNT_N] = M;
 }
 
+// The points and links of [0, N) copied unchanged into the other point
+// buffer, when the topology finish before found nothing to change
+// (counters[CNT_PASS], which that finish sets either way): the finish itself
+// is one block, and one block moving the whole point set is bound by memory
+// latency (~80 us for 86k points), a grid by bandwidth.
+__global__ void k_points_pass(const int* __restrict__ counters, const double* __restrict__ pin,
+                              const int* __restrict__ succ, const int* __restrict__ pred, double* __restrict__ pout,
+                              int* __restrict__ nout, int* __restrict__ pvout, int* __restrict__ newidx, int cap) {
+    pdl_wait_trigger();
+    if (!counters[CNT_PASS]) return;
+    const int N = counters[CNT_N];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        pout[k] = pin[k];
+        pout[(long long)cap + k] = pin[(long long)cap + k];
+        pout[2LL * cap + k] = pin[2LL * cap + k];
+        nout[k] = succ[k];
+        pvout[k] = pred[k];
+        newidx[k] = k;
+    }
+}
+
 __device__ int block_sum(int v) {
     __shared__ int s_red[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -392,8 +359,9 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
     __syncthreads();
     if (!s_any) {
         // no split, no removal candidate and nothing newly seeded: the points
-        // and links pass through unchanged (what the full pass concludes too)
-        block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, prev);
+        // and links pass through unchanged (what the full pass concludes
+        // too), copied by k_points_pass
+        if (threadIdx.x == 0) counters[CNT_PASS] = 1;
         return;
     }
     const int per = (N + (int)blockDim.x - 1) / (int)blockDim.x;
@@ -476,7 +444,9 @@ __global__ void __launch_bounds__(1024) k_remesh_finish(VfmParams P, double* __r
         s_same = S == 0 && removed_all == 0 && dead_all == 0;
     }
     __syncthreads();
-    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap, s_same ? prev : nullptr);
+    if (threadIdx.x == 0) counters[CNT_PASS] = s_same ? 1 : 0;
+    if (s_same) return;  // (nnext equals next then) copied by k_points_pass
+    block_compact(pos, nnext, alive, T, newidx, pout, nout, pvout, counters, cap);
 }
 
 // -------------------------------------------------------------- reconnect
@@ -596,10 +566,14 @@ __global__ void __launch_bounds__(128) k_nearest(VfmParams P, double dmax2, floa
 __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* __restrict__ next,
                         const int* __restrict__ prev, const int* __restrict__ nn, const double* __restrict__ nd2,
                         int* __restrict__ counters, int cap, int* __restrict__ cand_i, int* __restrict__ cand_a,
-                        int* __restrict__ cand_b, double* __restrict__ cand_d2, int* __restrict__ clist) {
+                        int* __restrict__ cand_b, double* __restrict__ cand_d2, int* __restrict__ clist,
+                        const int* __restrict__ hkey, int* __restrict__ hhead) {
     pdl_wait_trigger();
     const int N = counters[CNT_N];
     const int k = threadIdx.x & 3;
+    // the nearest-point search is done with the hash: empty its buckets for
+    // the next pass (a grid clears them at memory speed; one block would not)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) hhead[hkey[i]] = -1;
     const unsigned quad = 0xfu << (threadIdx.x & 28);
     const int nq = (int)((gridDim.x * blockDim.x) >> 2);
     // i is uniform over a quad, so each quad runs the loop and its shuffles together
@@ -662,10 +636,11 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     __syncthreads();
     if (s_quiet) {
         // no candidate exchange, no wall contact and nothing newly seeded:
-        // empty the hash buckets and pass the points and links through
-        block_clear_buckets(hkey, hhead, N);
-        if (threadIdx.x == 0) counters[CNT_STAMP] += 1;
-        block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, prev);
+        // the points and links pass through (copied by k_points_pass)
+        if (threadIdx.x == 0) {
+            counters[CNT_STAMP] += 1;
+            counters[CNT_PASS] = 1;
+        }
         return;
     }
     for (int c = threadIdx.x; c < K; c += blockDim.x) {
@@ -679,7 +654,6 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
         order[r] = c;
     }
     for (int k = threadIdx.x; k < N; k += blockDim.x) alive[k] = 1;
-    block_clear_buckets(hkey, hhead, N);
     __shared__ int s_changed;  // an exchange or a cut happened: small components may have formed
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -746,7 +720,10 @@ __global__ void __launch_bounds__(1024) k_reconnect_finish(
     if (threadIdx.x == 0) dstats[DS_SMALL] += (double)dead_all;
     __syncthreads();
     // no exchange and no cut: the points and links pass through unchanged
-    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap, s_changed ? nullptr : prev);
+    // (copied by k_points_pass)
+    if (threadIdx.x == 0) counters[CNT_PASS] = s_changed ? 0 : 1;
+    if (!s_changed) return;
+    block_compact(pos, next, alive, N, newidx, pout, nout, pvout, counters, cap);
 }
 
 }  // namespace
@@ -757,11 +734,20 @@ void launch_remesh_geometry(const VfmParams& P, Dev& d, int cur, int cap, int sp
                d.spp, d.seglen, d.flags);
 }
 
+// After a finish: the unchanged points into the other buffer, if the finish
+// passed them through (a grid-stride kernel of four blocks per SM).
+static void launch_points_pass(Dev& d, int cur, int cap, cudaStream_t s) {
+    launch_pdl(k_points_pass, 4 * sm_count(), 256, 0, s, (const int*)d.counters, (const double*)d.pos[cur],
+               (const int*)d.next[cur], (const int*)d.prev[cur], d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1],
+               d.newidx, cap);
+}
+
 void launch_remesh_finish(const VfmParams& P, Dev& d, int cur, int cap, cudaStream_t s) {
     if (cap <= 0) return;
     launch_pdl(k_remesh_finish, 1, 1024, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.spp, d.seglen, d.flags, d.nnext,
                                        d.alive, d.newidx, d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1],
                                        d.counters, d.dstats, cap);
+    launch_points_pass(d, cur, cap, s);
 }
 
 void launch_remesh(const VfmParams& P, Dev& d, int cur, int cap, int span, cudaStream_t s) {
@@ -803,11 +789,12 @@ void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int span, in
     launch_pdl(k_nearest, (span + 3) / 4, 128, 0, s, P, dmax2, nearest_filter_r2(P), d.pos[cur], d.next[cur], d.prev[cur],
                d.counters, cap, hmask, d.hhead, d.hpos, d.nn, d.nd2);
     launch_pdl(k_pairs, (4 * span + 127) / 128, 128, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2,
-               d.counters, cap, d.cand_i, d.cand_a, d.cand_b, d.cand_d2, d.hlink);
+               d.counters, cap, d.cand_i, d.cand_a, d.cand_b, d.cand_d2, d.hlink, d.hkey, d.hhead);
     launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.hlink, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
                                           d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
                                           cap);
+    launch_points_pass(d, cur, cap, s);
 }
 
 }  // namespace vlb

@@ -34,7 +34,8 @@ enum : int {
     CNT_DIRTY = 10,     // 1 after seeding: the next remesh checks for small components even without removals
     CNT_RFLAGS = 11,    // nonzero when the remesh geometry flagged a split or removal candidate (cleared by the finish)
     CNT_NSLOT = 12,     // Biot-Savart source slots of the current step (points + gap slots)
-    CNT_COUNT = 13
+    CNT_PASS = 13,      // 1 when the last topology finish changed nothing: the pass kernel copies the points
+    CNT_COUNT = 14
 };
 
 // Device float64 statistics.
