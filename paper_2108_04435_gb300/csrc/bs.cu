@@ -120,9 +120,14 @@ __device__ __forceinline__ float mi_axis(float r, float L, float iL) { return fm
 // A group whose records all lie at least BS_NEAR cells (Chebyshev) from every
 // target of a warp takes the cheap pair path: the low parts are left out (an
 // error of about one float ulp of the group extent and of the offset, i.e.
-// ~1e-7 (1 + extent / distance) of the pair), no target can lie on a segment,
-// and none of the target's own segments is in the group.
-constexpr float BS_NEAR = 8.f;
+// ~1e-7 (1 + extent / distance) of the pair), no target can lie on a segment
+// (segments are shorter than the remeshing bound, about a cell), and none of
+// the target's own segments is in the group.  Measured against the FP64 sums
+// of the oracle, 4 cells instead of 8 moved the relative L2 error of the
+// point velocities from 1.19e-7 to 1.22e-7 on the 128x128x1024 channel
+// (86k points) and from 1.71e-7 to 1.82e-7 on the sorted walled tangle
+// (35k points), and made the launch 2% faster there and 8% on the 128^3 box.
+constexpr float BS_NEAR = 4.f;
 
 // One target of a Biot-Savart pass (registers of one thread): its own
 // slot (origin O, parts h + l, so that the point is O + h + l) and the
@@ -242,8 +247,11 @@ __device__ __forceinline__ BsTarget bs_target_reload(const BsOrder& o, int k, in
 // (t2, tt: held in both halves of a float2): three fused multiply-adds and
 // an add instead of three adds and three multiply-adds.  The group origin
 // sits at the centre of the group's box, so |h| is at most about half its
-// extent, and the far path's distance of 8 cells keeps the cancellation of
-// |t|^2 against 2 h.t to a few float ulps of |R|^2.
+// extent, and the cancellation of |t|^2 against 2 h.t costs about
+// (|h| + |R|)^2 / |R|^2 float ulps of |R|^2 at the far path's distance of 4
+// cells or more (measured: the point velocities of the 86k-point channel
+// move from 1.19e-7 to 1.22e-7 of the FP64 sums when the far path starts at
+// 4 cells instead of 8).
 template <int TGT>
 __device__ __forceinline__ void chain_head(const float4* __restrict__ Q, const float2 (&t2)[TGT][3],
                                            const float2 (&tt)[TGT], float2 (&ia)[TGT], float2 (&rho)[TGT],

@@ -42,12 +42,14 @@ def test_largest_channel_advance_parity():
     same_lattice_state(g, r, seed=41, amp=2e-3)
     g.run_phases(vlb.PHASE_LBM | vlb.PHASE_VFM)
     r.run_phases(oracle.PHASE_LBM | oracle.PHASE_VFM)
-    assert rel_l2(g.read(vlb.FIELD_U), r.read(oracle.FIELD_U)) < 1e-5
-    assert rel_l2(g.read(vlb.FIELD_VEL), r.read(oracle.FIELD_VEL)) < 1e-5
+    e_u = rel_l2(g.read(vlb.FIELD_U), r.read(oracle.FIELD_U))
+    e_v = rel_l2(g.read(vlb.FIELD_VEL), r.read(oracle.FIELD_VEL))
     x0 = np.asarray(xyz)
     dg = unwrap(g.read(vlb.FIELD_POS) - x0, p["n"], p["wall"])
     dr = unwrap(r.read(oracle.FIELD_POS) - x0, p["n"], p["wall"])
-    assert rel_l2(dg, dr) < 1e-5
+    e_d = rel_l2(dg, dr)
+    print("benchmark channel: velocity field", e_u, "point velocity", e_v, "displacement", e_d)
+    assert e_u < 1e-5 and e_v < 1e-5 and e_d < 1e-5
     assert rel_l2(g.read(vlb.FIELD_FORCE), r.read(oracle.FIELD_FORCE)) < 1e-5
     # Eq. 18 per plane and the mass: FP64 sums of warp partials of the FP32
     # density and velocity deviations
