@@ -618,14 +618,15 @@ __global__ void k_pairs(VfmParams P, const double* __restrict__ pos, const int* 
 
 // One block finishes the reconnection: candidates in ascending (d^2, i)
 // order (keys are unique), the greedy pass in that order (an exchange that
-// touches a point already used is skipped), emptying the hash buckets, the
-// wall-contact cuts, small-component deletion and the compaction into the
-// other point buffer.
+// touches a point already used is skipped), the wall-contact cuts,
+// small-component deletion and the compaction into the other point buffer;
+// when nothing changes, k_points_pass copies the points instead (the hash
+// buckets were emptied by k_pairs).
 __global__ void __launch_bounds__(1024) k_reconnect_finish(
     VfmParams P, const int* __restrict__ clist, double* __restrict__ pos, int* __restrict__ next,
     int* __restrict__ prev, const int* __restrict__ cand_i,
     const int* __restrict__ cand_a, const int* __restrict__ cand_b, const double* __restrict__ cand_d2,
-    int* __restrict__ order, int* __restrict__ stamp, const int* __restrict__ hkey, int* __restrict__ hhead,
+    int* __restrict__ order, int* __restrict__ stamp,
     uint8_t* __restrict__ alive, int* __restrict__ newidx, double* __restrict__ pout, int* __restrict__ nout,
     int* __restrict__ pvout, int* __restrict__ counters, double* __restrict__ dstats, int cap) {
     pdl_wait_trigger();
@@ -791,7 +792,7 @@ void launch_reconnect(const VfmParams& P, Dev& d, int cur, int cap, int span, in
     launch_pdl(k_pairs, (4 * span + 127) / 128, 128, 0, s, P, d.pos[cur], d.next[cur], d.prev[cur], d.nn, d.nd2,
                d.counters, cap, d.cand_i, d.cand_a, d.cand_b, d.cand_d2, d.hlink, d.hkey, d.hhead);
     launch_pdl(k_reconnect_finish, 1, 1024, 0, s, P, d.hlink, d.pos[cur], d.next[cur], d.prev[cur], d.cand_i, d.cand_a, d.cand_b,
-                                          d.cand_d2, d.cand_order, d.stamp, d.hkey, d.hhead, d.alive, d.newidx,
+                                          d.cand_d2, d.cand_order, d.stamp, d.alive, d.newidx,
                                           d.pos[cur ^ 1], d.next[cur ^ 1], d.prev[cur ^ 1], d.counters, d.dstats,
                                           cap);
     launch_points_pass(d, cur, cap, s);
