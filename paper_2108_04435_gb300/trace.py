@@ -1,6 +1,6 @@
 """Kernel timeline of coupled steps from CUPTI activity records.
 
-    python -m paper_2108_04435_gb300.trace [--config NAME] [--warmup 16] [--steps 16] [--no-overlap]
+    python -m paper_2108_04435_gb300.trace [--config NAME] [--storage f32|f16|bf16] [--warmup 16] [--steps 16] [--no-overlap]
 
 Runs `warmup` steps, then records the start and end of every kernel of
 `steps` more (replayed from the 8-step graphs when steps is a multiple of 8)
@@ -48,12 +48,16 @@ def main(argv=None) -> None:
     ap.add_argument("--warmup", type=int, default=16)
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--no-overlap", action="store_true")
+    ap.add_argument("--storage", choices=("f32", "f16", "bf16"), default=None,
+                    help="population storage (default: the configuration's)")
     a = ap.parse_args(argv)
     lib = tracer()
     import torch
 
     from . import configs, vlb
     p, xyz, nxt = configs.config(a.config)
+    if a.storage:
+        p["storage"] = {"f32": 0, "f16": 1, "bf16": 2}[a.storage]
     ch = vlb.Channel(p)
     ch.set_overlap(not a.no_overlap)
     ch.seed(xyz, nxt)
