@@ -518,6 +518,87 @@ __device__ __forceinline__ void pair2_wrap(const float4* __restrict__ Q, int j, 
     }
 }
 
+// The near path for the two slots of pair p, packed: the arithmetic of
+// pair_precise (low parts, minimum image on periodic axes, the on-segment
+// and own-segment guard, the cancellation-free denominator) on both slots at
+// once in FP32x2, into the sums v (the block's sign applied by the caller).
+// Where some lane's minimum image falls within 1e-3 of half the box, the
+// warp takes this pair on the scalar precise path, which decides the image
+// from the exact float-float sum of the parts.
+template <bool PERIODIC, int TGT>
+__device__ __forceinline__ void pair2_near(const float4* __restrict__ Q, int j, const float (&th)[TGT][3],
+                                           const float (&tl)[TGT][3], BsTarget (&t)[TGT], const BoxF& box,
+                                           int Np, float2 (&v)[TGT][3]) {
+    const float4 q0 = Q[0], q1 = Q[1], q2 = Q[2], q3 = Q[3], q5 = Q[5], q6 = Q[6];
+    const float2 hh[3] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y)};
+    const float2 ll[3] = {make_float2(q5.x, q5.y), make_float2(q5.z, q5.w), make_float2(q6.x, q6.y)};
+    const float2 dd = make_float2(q1.z, q1.w);
+    const float2 dx = make_float2(q2.x, q2.y), dy = make_float2(q2.z, q2.w), dz = make_float2(q3.x, q3.y);
+    const float2 dv[3] = {dx, dy, dz};
+    const bool img = j >= Np;
+    const float L[3] = {box.Lx, box.Ly, box.Lz}, iL[3] = {box.iLx, box.iLy, box.iLz};
+    const float2 M2 = make_float2(12582912.0f, 12582912.0f);  // 1.5 * 2^23: adding it rounds to an integer
+    float2 r[TGT][3];
+    bool tie = false;
+#pragma unroll
+    for (int u = 0; u < TGT; ++u)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r[u][a] = __fadd2_rn(__fadd2_rn(hh[a], make_float2(th[u][a], th[u][a])),
+                                 __fadd2_rn(ll[a], make_float2(tl[u][a], tl[u][a])));
+            if (PERIODIC) {
+                const float2 z = img ? __fadd2_rn(r[u][a], dv[a]) : r[u][a];
+                const float2 k = fsub2(__ffma2_rn(z, make_float2(iL[a], iL[a]), M2), M2);
+                r[u][a] = __ffma2_rn(make_float2(-L[a], -L[a]), k, r[u][a]);
+                if (!img)
+                    tie |= (L[a] > 0.f) & ((fabsf(r[u][a].x) > 0.5f * L[a] - 1e-3f) |
+                                           (fabsf(r[u][a].y) > 0.5f * L[a] - 1e-3f));
+            }
+        }
+    if (PERIODIC && __any_sync(0xffffffffu, tie)) {
+        pair2_precise<PERIODIC, true, TGT>(Q, j, th, tl, t, box, Np);
+        return;
+    }
+    const float2 one = make_float2(1.f, 1.f);
+#pragma unroll
+    for (int u = 0; u < TGT; ++u) {
+        const float2 rx = r[u][0], ry = r[u][1], rz = r[u][2];
+        const float2 a2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+        const float2 rd = __ffma2_rn(rz, dz, __ffma2_rn(ry, dy, __fmul2_rn(rx, dx)));
+        const float2 b2 = __fadd2_rn(__ffma2_rn(make_float2(2.f, 2.f), rd, a2), dd);
+        const float2 ia = make_float2(rsqrt_approx(a2.x), rsqrt_approx(a2.y));
+        const float2 ib = make_float2(rsqrt_approx(b2.x), rsqrt_approx(b2.y));
+        const float2 P = __fmul2_rn(ia, ib);
+        const float2 cx = fsub2(__fmul2_rn(ry, dz), __fmul2_rn(rz, dy));
+        const float2 cy = fsub2(__fmul2_rn(rz, dx), __fmul2_rn(rx, dz));
+        const float2 cz = fsub2(__fmul2_rn(rx, dy), __fmul2_rn(ry, dx));
+        // the denominator as in pair_precise: 1 + P R1.R2, or where R1.R2 < 0
+        // P |R1 x d|^2 over 1 - P R1.R2 (exactly equal, free of cancellation)
+        const float2 s12 = __fadd2_rn(a2, rd);
+        const float2 cr2 = __ffma2_rn(cz, cz, __ffma2_rn(cy, cy, __fmul2_rn(cx, cx)));
+        const float2 alt = __ffma2_rn(make_float2(-P.x, -P.y), s12, one);
+        const float2 pos = __ffma2_rn(P, s12, one);
+        const float2 pcr = __fmul2_rn(P, cr2);
+        const bool ax = s12.x < 0.f, ay = s12.y < 0.f;
+        const float2 num = __fmul2_rn(__fadd2_rn(ia, ib), make_float2(ax ? alt.x : P.x, ay ? alt.y : P.y));
+        const float2 dn = make_float2(ax ? pcr.x : pos.x, ay ? pcr.y : pos.y);
+        const float2 fac = __fmul2_rn(num, make_float2(rcp_approx(dn.x), rcp_approx(dn.y)));
+        const float2 pdn = __fmul2_rn(P, dn);
+        // the guard of pair_precise, lane by lane
+        const bool onx = ax ? !(pdn.x > 1e-6f * alt.x) : !(dn.x > 1e-6f);
+        const bool ony = ay ? !(pdn.y > 1e-6f * alt.y) : !(dn.y > 1e-6f);
+        const int j1 = j + BS_GROUP / 2;
+        const bool ux = (dd.x > 0.f) & !onx & (dn.x < 3.0e38f) & (fabsf(fac.x) < 3.0e38f) & (j != t[u].self) &
+                        (j != t[u].prev) & (j != t[u].excl);
+        const bool uy = (dd.y > 0.f) & !ony & (dn.y < 3.0e38f) & (fabsf(fac.y) < 3.0e38f) & (j1 != t[u].self) &
+                        (j1 != t[u].prev) & (j1 != t[u].excl);
+        const float2 c = make_float2(ux ? fac.x : 0.f, uy ? fac.y : 0.f);
+        v[u][0] = __ffma2_rn(c, cx, v[u][0]);
+        v[u][1] = __ffma2_rn(c, cy, v[u][1]);
+        v[u][2] = __ffma2_rn(c, cz, v[u][2]);
+    }
+}
+
 // Offset of a group (origin O, record box [lo, hi]) from a target: the
 // integer part D = O - O_t is exact, and on periodic axes D is moved by a
 // whole box so that the group's centre is the nearest image.  Returns
@@ -650,9 +731,16 @@ __device__ __forceinline__ void bs_group(const float4* __restrict__ T, int gbase
         // two pairs per pass with one target per thread: with few points the
         // kernel is latency-bound, and the pairs are independent chains
         if (nearW) {
-#pragma unroll(TGT == 1 ? 2 : 1)
-            for (int p = 0; p < BS_GROUP / 2; ++p)
-                pair2_precise<PERIODIC, true, TGT>(T + BS_PAIR * p, gbase + p, th, tl, t, box, Np);
+            float2 v[TGT][3];
+#pragma unroll
+            for (int u = 0; u < TGT; ++u)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) v[u][a] = make_float2(0.f, 0.f);
+            for (int p = 0; p < BS_GROUP / 2; ++p) pair2_near<PERIODIC, TGT>(T + BS_PAIR * p, gbase + p, th, tl, t, box, Np, v);
+#pragma unroll
+            for (int u = 0; u < TGT; ++u)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) t[u].v[a] = fmaf(G.sign, v[u][a].x + v[u][a].y, t[u].v[a]);
         } else if (PERIODIC) {
             float2 v[TGT][3];
 #pragma unroll
