@@ -267,8 +267,12 @@ __global__ void __launch_bounds__(1024) k_slot_assign(const double* __restrict__
 
 }  // namespace
 
+// hist holds cap ints.  The counts take K * nblk of them, at most
+// 256 * ceil(cap / 1024) <= cap / 4 + 256, which is below cap from 342
+// points on; both callers sort only from BS_SORT_MIN points on.
 void launch_bs_sort(const Grid& g, const double* pos, int cap, const int* counters, int* key, int* hist, int* ord,
                     int* rank, cudaStream_t s) {
+    static_assert(BS_SORT_MIN >= 342 && BS_SORT_MAX_BINS <= 256, "the bin counts must fit in cap ints");
     const BsBins bb = bs_bins(g.nx, g.ny, g.nz);
     const int nblk = (cap + SORT_BLOCK - 1) / SORT_BLOCK > 0 ? (cap + SORT_BLOCK - 1) / SORT_BLOCK : 1;
     launch_pdl(k_sort_count, nblk, SORT_BLOCK, 0, s, g, bb, pos, cap, counters, key, hist, nblk);
