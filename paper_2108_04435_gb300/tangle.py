@@ -108,6 +108,28 @@ def run(vn_mm_s: float, seconds: float, seed: int = 0, sample_s: float = 0.05, u
 SIGMA_19K = 0.757e7  # entropy of He II at 1.9 K in erg/(g K), approximate tabulated value (not printed by the paper)
 
 
+def line_density_fit(z_mm, prof):
+    """Least-squares line through the averaged density profile, written as
+    L(z) = L0 (1 - z/z0) (Sec. IV): L0 in the profile's unit, z0 in z's."""
+    B, A = np.polyfit(np.asarray(z_mm, dtype=float), np.asarray(prof, dtype=float), 1)
+    return float(A), float(-A / B) if B != 0 else float("inf")
+
+
+def delta_T_mK_per_m(alpha: float, L0_cm2: float, V_ns_cm_s: float, sigma=SIGMA_19K) -> float:
+    """delta T = (alpha / sigma) kappa L0 V_ns, the gradient scale of Eq. 20
+    (the solution of Eq. 19 for L(z) = L0 (1 - z/z0)), from CGS inputs
+    (L0 in cm^-2, V_ns in cm/s, sigma in erg/(g K)) to mK/m."""
+    K_per_cm = alpha / sigma * KAPPA_CM2_S * L0_cm2 * V_ns_cm_s
+    return K_per_cm * 1e3 * 1e2  # K -> mK, 1/cm -> 1/m
+
+
+def temperature_profile(z, T0: float, dT: float, z0: float):
+    """Eq. 20: T(z) = T0 - dT (1 - z/(2 z0)) z, the temperature along the
+    channel for a linear line density, z measured from the heater wall."""
+    z = np.asarray(z, dtype=float)
+    return T0 - dT * (1.0 - z / (2.0 * z0)) * z
+
+
 def channel_params(vn_mm_s: float = 2.5, u=None, wall_images: int = 1, max_points: int = 65536, tau=None):
     """The closed channel of Sec. IV: the box of Sec. III.C with solid walls at
     the two ends of the counterflow axis (heater at z = 0, cooled wall at the
@@ -136,7 +158,7 @@ def channel_run(vn_mm_s: float = 2.5, seconds: float = 7.2, t_avg: float = 1.0, 
                 sample_s: float = 0.05, wall_images: int = 1, u=None, tau=None):
     """Sec. IV on the GPU: total line length L(t), the line density profile
     L(z) averaged over t >= t_avg, its linear fit L(z) = L0 (1 - z/z0), and the
-    temperature difference of Eq. 20, dT = (alpha / sigma) kappa L0 V_ns."""
+    temperature gradient scale delta T of Eq. 20, (alpha / sigma) kappa L0 V_ns."""
     from . import vlb
     u = u or units()
     p = channel_params(vn_mm_s, u, wall_images, tau=tau)
@@ -171,13 +193,12 @@ def channel_run(vn_mm_s: float = 2.5, seconds: float = 7.2, t_avg: float = 1.0, 
     ch.close()
     prof = prof / max(nprof, 1)
     z_mm = (np.arange(nz) + 0.5) * u["dx_cm"] * 10.0  # plane centres from the heater wall at -1/2
-    B, A = np.polyfit(z_mm, prof, 1)
     V_ns = float(np.mean(vns)) if vns else float("nan")
-    L0, z0 = float(A), float(-A / B) if B != 0 else float("inf")
-    dT_K_per_cm = p["alpha"] / SIGMA_19K * KAPPA_CM2_S * L0 * V_ns
+    L0, z0 = line_density_fit(z_mm, prof)
     return dict(vn_mm_s=vn_mm_s, seconds=seconds, steps=done, error=error, wall_images=wall_images, tau=p["tau"],
                 L_mean_cm2=float(np.mean(prof)), L0_cm2=L0, z0_mm=z0, V_ns_cm_s=V_ns,
-                dT_mK_per_m=dT_K_per_cm * 1e5, points=int(st[0]), wall_cuts=int(st[13]), status=int(st[1]),
+                dT_mK_per_m=delta_T_mK_per_m(p["alpha"], L0, V_ns), points=int(st[0]), wall_cuts=int(st[13]),
+                status=int(st[1]),
                 gpu_wall_s=wall, t=t, L_total=Ltot, z_mm=z_mm.tolist(), L_profile=prof.tolist())
 
 
