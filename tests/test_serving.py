@@ -80,3 +80,19 @@ def test_summary_percentiles():
     s = summarize(res, wall_s=10.0)
     assert abs(s["p50_latency_s"] - 50.5) < 1e-9 and abs(s["p99_latency_s"] - 99.01) < 1e-9
     assert s["mlups"] == 100 * 10 * 100 / 10.0 / 1e6
+
+
+def test_summary_counts_only_completed_requests():
+    # a failed request (CFL or Mach check) is listed, not counted in
+    # throughput, latency or lattice updates
+    from paper_2108_04435_gb300.serve import Result
+    res = [Result(id=k, arrival=0.0, finish=2.0, steps=10, cells=100) for k in range(4)]
+    res[1].error = "VLB_ERR_CFL: a filament point moved a cell within a step"
+    res[3].error = "VLB_ERR_MACH: lattice velocity exceeds the Mach limit"
+    res[3].finish = 100.0
+    s = summarize(res, wall_s=4.0)
+    assert s["requests"] == 4 and s["failed"] == 2 and s["failed_ids"] == [1, 3]
+    assert s["throughput_req_per_s"] == 2 / 4.0
+    assert s["mlups"] == 2 * 100 * 10 / 4.0 / 1e6
+    assert s["p99_latency_s"] == 2.0
+    assert len(s["errors"]) == 2
