@@ -393,13 +393,22 @@ def run_vlb(args, ws, rank, local):
 
 
 def k1_kernel(storage: str, nx: int) -> str:
-    """The stream-collide kernel the library launches for this storage: two
-    cells per thread with 16-bit populations on an even nx (unless
-    VLB_LBM_VEC says otherwise), else one."""
-    vec = os.environ.get("VLB_LBM_VEC")
-    if storage != "f32" and nx % 2 == 0 and vec in (None, "2"):
-        return "k_lbm_step_pair"
-    return "k_lbm_step"
+    """The stream-collide kernel the library launches for this storage and
+    x extent, by the library's own rule: two cells per thread with 16-bit
+    populations on an even nx, else one; VLB_LBM_VEC (read like C's atoi)
+    may ask for 1 or 2 cells per thread, or 4 with FP32 populations, where
+    nx divides by it."""
+    half = storage != "f32"
+    vec = 2 if half and nx % 2 == 0 else 1
+    e = os.environ.get("VLB_LBM_VEC")
+    if e is not None:
+        m = re.match(r"\s*([+-]?\d+)", e)
+        v = int(m.group(1)) if m else 0
+        if (v in (1, 2) or (v == 4 and not half)) and nx % v == 0:
+            vec = v
+    if half:
+        return "k_lbm_step_pair" if vec == 2 else "k_lbm_step"
+    return "k_lbm_step_vec" if vec in (2, 4) else "k_lbm_step"
 
 
 def lbm_pass_roofline(p, storage, passes, pk, pk_kind, stream):

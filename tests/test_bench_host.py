@@ -40,3 +40,14 @@ def test_stream_collide_kernel_name(monkeypatch):
     assert bench.k1_kernel("f32", 128) == "k_lbm_step"
     monkeypatch.setenv("VLB_LBM_VEC", "1")
     assert bench.k1_kernel("f16", 128) == "k_lbm_step"
+    # the switch the library ignores leaves its default (4 cells per thread
+    # only with FP32 populations, and only where nx divides)
+    monkeypatch.setenv("VLB_LBM_VEC", "4")
+    assert bench.k1_kernel("f16", 128) == "k_lbm_step_pair"
+    assert bench.k1_kernel("f32", 128) == "k_lbm_step_vec"
+    assert bench.k1_kernel("f32", 126) == "k_lbm_step"
+    monkeypatch.setenv("VLB_LBM_VEC", "2")
+    assert bench.k1_kernel("f32", 64) == "k_lbm_step_vec"
+    assert bench.k1_kernel("bf16", 21) == "k_lbm_step"
+    monkeypatch.setenv("VLB_LBM_VEC", "x")
+    assert bench.k1_kernel("f16", 128) == "k_lbm_step_pair"
