@@ -65,7 +65,7 @@ def launches_per_step(n_points: int) -> int:
     applies the equation of motion itself (4 fewer; or as VLB_FUSED_EOM
     forces)."""
     mode = os.environ.get("VLB_FUSED_EOM")
-    fused = n_points >= 24576 if mode is None else mode != "0"
+    fused = n_points >= 24576 if mode is None else not mode.startswith("0")  # the library reads the first character
     return (21 if fused else 25) + (3 if n_points >= 8192 else 0)
 
 

@@ -20,6 +20,10 @@ def test_launches_per_step(monkeypatch):
     assert bench.launches_per_step(85770) == 24  # equation of motion inside the Biot-Savart kernel
     monkeypatch.setenv("VLB_FUSED_EOM", "1")
     assert bench.launches_per_step(1148) == 21
+    monkeypatch.setenv("VLB_FUSED_EOM", "0")
+    assert bench.launches_per_step(85770) == 28
+    monkeypatch.setenv("VLB_FUSED_EOM", "00")
+    assert bench.launches_per_step(85770) == 28
 
 
 def test_launches_match_traced_graphs(monkeypatch):
