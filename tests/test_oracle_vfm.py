@@ -7,6 +7,8 @@
   constant that Schwarz's cutoff reproduces) and its direction;
 - mutual-friction shrink d(R^2)/dt = -2 alpha kappa/(4 pi)(ln(8R/a) - 1/4)
   (the form of Eq. 15 with the local-induction speed);
+- the two friction terms of Eq. 4 on a ring at rest in the normal fluid:
+  alpha' slows it by 1 - alpha'|s'|^2, alpha moves it inward at alpha|s'||v_s|;
 - coupling slows the shrink (Sec. III.A, Fig. 2d);
 - the 2-point delta interpolation (Eq. 11) reproduces affine fields, and
   spreading is its exact adjoint with partition of unity;
@@ -92,6 +94,31 @@ def test_ring_speed(oracle_mod):
     ch.seed(xyz, nxt)
     v, _ = ch.point_velocity()
     assert abs((v @ nrm).mean() / V - 1.0) < 0.01
+
+
+@pytest.mark.parametrize("alpha,alpha_p", [(0.0, 0.2), (0.1, 0.0), (0.1, 0.2)])
+def test_friction_terms_on_a_ring(oracle_mod, alpha, alpha_p):
+    # Eq. 4 with v_n = 0 on a regular 64-gon ring: v_s at every point is
+    # along the axis, perpendicular to s' (|s'| = cos(pi/N) for the central
+    # difference, exact for a regular polygon), so s' x (s' x v_s) = -|s'|^2 v_s
+    # and the alpha' term slows the ring by the factor 1 - alpha' |s'|^2
+    # without moving it radially, while the alpha term s' x (-v_s) points to
+    # the axis with magnitude alpha |s'| |v_s| (the ring shrinks) and leaves
+    # the axial speed alone.
+    def vel(a, ap):
+        ch = oracle_mod.Channel(vparams(alpha=a, alpha_p=ap))
+        xyz, nxt = inputs.ring((32, 32, 32), (0, 0, 1), 8.0, npts=64)
+        ch.seed(xyz, nxt)
+        v, _ = ch.point_velocity()
+        ch.close()
+        return xyz, np.asarray(v)
+
+    xyz, v0 = vel(0.0, 0.0)
+    _, v = vel(alpha, alpha_p)
+    sp = np.cos(np.pi / 64)
+    radial = (xyz - xyz.mean(axis=0)) / 8.0
+    assert np.abs(v[:, 2] / v0[:, 2] - (1.0 - alpha_p * sp * sp)).max() < 1e-12
+    assert np.abs((v * radial).sum(axis=1) / v0[:, 2] + alpha * sp).max() < 1e-12
 
 
 def ring_radius(pos):
