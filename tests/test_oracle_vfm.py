@@ -121,6 +121,30 @@ def test_friction_terms_on_a_ring(oracle_mod, alpha, alpha_p):
     assert np.abs((v * radial).sum(axis=1) / v0[:, 2] + alpha * sp).max() < 1e-12
 
 
+def test_ring_carried_by_the_normal_fluid_feels_no_friction(oracle_mod):
+    # A uniform normal flow w along the ring's axis sets V_s = -(rho_n/rho_s) w
+    # (Eq. 18, box mean on a periodic box), so the superfluid velocity at the
+    # ring is v_ring + V_s.  For w = v_ring r/(1 + r), r = rho_s/rho_n, that
+    # equals w: the ring moves with the normal fluid, v_n - v_s = 0 at every
+    # point, and both friction terms of Eq. 4 vanish, whatever alpha, alpha'.
+    def vel(a, ap, w):
+        p = vparams(alpha=a, alpha_p=ap, init_vn=[0.0, 0.0, w])
+        ch = oracle_mod.Channel(p)
+        xyz, nxt = inputs.ring((32, 32, 32), (0, 0, 1), 8.0, npts=64)
+        ch.seed(xyz, nxt)
+        v, _ = ch.point_velocity()
+        ch.close()
+        return np.asarray(v), p["rho_s_over_rho_n"]
+
+    v0, r = vel(0.0, 0.0, 0.0)
+    w = v0[:, 2].mean() * r / (1.0 + r)
+    v, _ = vel(0.3, 0.2, w)
+    assert np.abs(v - np.array([0.0, 0.0, w])).max() < 1e-12
+    # the same flow with the friction off: the ring is slower than in still fluid by w/r
+    vf, _ = vel(0.0, 0.0, w)
+    assert np.abs(vf[:, 2] - (v0[:, 2] - w / r)).max() < 1e-12
+
+
 def ring_radius(pos):
     c = pos.mean(axis=0)
     return np.linalg.norm(pos - c, axis=1).mean()
