@@ -1,7 +1,6 @@
 """Serving scheduler (host logic, no GPU): admission by slots and by the
 device-memory budget, arrival-order admission, slices of steps until each
 request has run all its steps."""
-import itertools
 
 from paper_2108_04435_gb300.serve import Scheduler, summarize
 
