@@ -12,6 +12,8 @@
 - coupling slows the shrink (Sec. III.A, Fig. 2d);
 - the 2-point delta interpolation (Eq. 11) reproduces affine fields, and
   spreading is its exact adjoint with partition of unity;
+- periodic translation invariance: rings shifted and wrapped across the
+  faces of a periodic box move exactly as before (the minimum image);
 - the RK4 integration of Eq. 4 converges at fourth order in the sub-step
   (a first-order-consistent slip in the stage weights passes the ring-speed
   and shrink-rate pins but fails this one).
@@ -143,6 +145,33 @@ def test_ring_carried_by_the_normal_fluid_feels_no_friction(oracle_mod):
     # the same flow with the friction off: the ring is slower than in still fluid by w/r
     vf, _ = vel(0.0, 0.0, w)
     assert np.abs(vf[:, 2] - (v0[:, 2] - w / r)).max() < 1e-12
+
+
+@pytest.mark.parametrize("shift", [(13.3, 0.0, 0.0), (5.1, 17.7, 29.2), (16.0, 16.0, 16.0)])
+def test_periodic_translation_invariance(oracle_mod, shift):
+    # On an all-periodic box the velocity of Eq. 4 (Biot-Savart with the
+    # minimum image, local term, friction) depends only on differences of
+    # positions modulo the box: rings shifted and wrapped, several of them
+    # then straddling a face, move exactly as before (to rounding).
+    p = vparams((32, 32, 32))
+    xyz, nxt = inputs.random_rings((32, 32, 32), (0, 0, 0), 6, 3.0, 6.0, 3)
+    xyz, nxt = np.asarray(xyz), np.asarray(nxt)
+    moved = (xyz + np.array(shift)) % 32.0
+    raw = moved[nxt] - moved
+    assert (np.abs(raw) > 16.0).any()  # some segment crosses a periodic face
+
+    def run(x):
+        ch = oracle_mod.Channel(p)
+        ch.seed(x, nxt)
+        v, _ = ch.point_velocity()
+        length = ch.line_length()
+        ch.close()
+        return np.asarray(v), length
+
+    v0, l0 = run(xyz)
+    v1, l1 = run(moved)
+    assert np.abs(v1 - v0).max() < 1e-11 * np.abs(v0).max()
+    assert abs(l1 - l0) < 1e-11 * l0
 
 
 def ring_radius(pos):
