@@ -10,8 +10,9 @@
 - the two friction terms of Eq. 4 on a ring at rest in the normal fluid:
   alpha' slows it by 1 - alpha'|s'|^2, alpha moves it inward at alpha|s'||v_s|;
 - coupling slows the shrink (Sec. III.A, Fig. 2d);
-- the 2-point delta interpolation (Eq. 11) reproduces affine fields, and
-  spreading is its exact adjoint with partition of unity;
+- the 2-point delta interpolation (Eq. 11) reproduces affine fields and
+  reaches one cell per axis, and spreading is its exact adjoint with
+  partition of unity;
 - periodic translation invariance: rings shifted and wrapped across the
   faces of a periodic box move exactly as before (the minimum image);
 - the RK4 integration of Eq. 4 converges at fourth order in the sub-step
@@ -223,6 +224,28 @@ def test_interp_reproduces_affine_fields(oracle_mod):
     pts = np.stack([rng.uniform(0, n[0] - 1, 50), rng.uniform(0, n[1] - 1, 50), rng.uniform(0, n[2] - 1, 50)], axis=1)
     got = ch.interp(pts)
     assert np.abs(got - (pts @ A.T + b)).max() < 1e-13
+
+
+def test_interp_support_is_one_cell(oracle_mod):
+    # Eq. 11's 2-point delta has support |r| < 1 on each axis: a unit value at
+    # one node reaches only points within one cell of it on every axis.  With
+    # the affine exactness above this fixes the weights (the hat function is
+    # the only kernel of that support reproducing linear fields); a 4-point
+    # kernel, also affine-exact, fails here.
+    n = (8, 8, 8)
+    ch = oracle_mod.Channel(vparams(n=n))
+    node = np.array([3, 4, 5])
+    U = np.zeros((3, n[0] * n[1] * n[2]))
+    U[:, node[0] + n[0] * (node[1] + n[1] * node[2])] = 1.0
+    ch.write(oracle_mod.FIELD_ULAST, U)
+    rng = np.random.default_rng(11)
+    pts = np.concatenate([node + rng.uniform(-2.0, 2.0, (300, 3)), node + rng.uniform(-0.999, 0.999, (50, 3))])
+    got = ch.interp(pts)
+    near = (np.abs(pts - node) < 1.0).all(axis=1)
+    assert near.sum() >= 50 and (~near).sum() >= 100
+    assert (got[~near] == 0.0).all()
+    assert (got[near] > 0.0).all()
+    assert got[:, 0] == pytest.approx(got[:, 1], abs=0) and got[:, 0] == pytest.approx(got[:, 2], abs=0)
 
 
 @pytest.mark.parametrize("wall", [(0, 0, 0), (1, 1, 1), (0, 1, 0)])
