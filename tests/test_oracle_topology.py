@@ -183,3 +183,43 @@ def test_tangle_topology_invariants(oracle_mod, seed):
     d = pos[nn] - pos
     d -= 32 * np.round(d / 32)
     assert np.linalg.norm(d, axis=1).max() <= p["dxi_max"] + 0.1
+
+
+@pytest.mark.parametrize("rel,split", [(-1e-9, False), (1e-9, True)])
+def test_split_threshold_is_dxi_max(oracle_mod, rel, split):
+    # Sec. III's upper spacing 0.95: a regular 64-gon whose chord lies just
+    # below it is left alone, just above it every segment is split
+    N = 64
+    R = 0.95 * (1 + rel) / (2 * np.sin(np.pi / N))
+    xyz, nxt = inputs.ring((16.0, 16.0, 16.0), (0, 0, 1), R, npts=N)
+    ch = oracle_mod.Channel(tparams(n=(32, 32, 32)))
+    ch.seed(xyz, nxt)
+    ch.run_phases(oracle_mod.PHASE_REMESH)
+    assert ch.n_points() == (2 * N if split else N)
+
+
+@pytest.mark.parametrize("rel,removed", [(-1e-9, True), (1e-9, False)])
+def test_removal_threshold_is_dxi_min(oracle_mod, rel, removed):
+    # Sec. III's lower spacing 0.70 on a sharp kink, where it is the binding
+    # condition: a tip point at distance L from both of its neighbours, which
+    # sit 0.8 apart on a regular ring (so the merged segment stays within
+    # 0.95).  L just below 0.70 removes the tip and nothing else; just above,
+    # the loop is unchanged.
+    N, chord = 40, 0.8
+    R = chord / (2 * np.sin(np.pi / N))
+    c = np.array([32.0, 32.0, 32.0])
+    th = 2 * np.pi * np.arange(N) / N
+    ring = np.stack([c[0] + R * np.cos(th), c[1] + R * np.sin(th), np.full(N, c[2])], axis=1)
+    mid = 0.5 * (ring[0] + ring[1])
+    out = (mid - c) / np.linalg.norm(mid - c)
+    L = 0.70 * (1 + rel)
+    tip = mid + np.sqrt(L * L - (chord / 2) ** 2) * out
+    xyz = np.concatenate([ring[:1], tip[None], ring[1:]])
+    nxt = (np.arange(N + 1) + 1) % (N + 1)
+    ch = oracle_mod.Channel(tparams(n=(64, 64, 64)))
+    ch.seed(xyz, nxt)
+    ch.run_phases(oracle_mod.PHASE_REMESH)
+    pos = ch.read(oracle_mod.FIELD_POS)
+    want = np.delete(xyz, 1, axis=0) if removed else xyz
+    assert np.array_equal(pos, want)
+    assert np.array_equal(ch.read(oracle_mod.FIELD_NEXT), (np.arange(len(want)) + 1) % len(want))
